@@ -1,0 +1,288 @@
+"""Registrations/s of the GB300 TurboReg path on the N=5000 indoor-shaped workload.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One step = one full registration (compatibility graph -> SC^2 -> pivots ->
+PGS -> Kabsch -> verification -> argmax) of one seeded synthetic problem:
+N = 5000 correspondences, source uniform in [0,4]x[0,4]x[0,3] m, R uniform on
+SO(3), t uniform in [-1,1]^3 m, 5% inliers with sigma = 0.01 m, outliers
+uniform in the transformed bounding box; tau = 0.1 m, K1 = 2000, K2 = 2,
+inlier threshold 0.1 m.  Eight problems (seeds 0..7) are cycled.
+
+value: registrations/s with inputs resident in device memory, CUDA events on
+       the library's stream around each call, L2 flushed (256 MB write)
+       between timed steps outside the events.
+e2e:   the same metric through the C ABI with pinned HOST inputs: the H2D
+       copies of x, y and the D2H copy of the result are inside the events.
+Multi-GPU: independent replicas per rank (the path does not shard); value is
+all ranks' registrations / the slowest rank's time.
+--impl reference: the FP64 CPU oracle as the reference arm, same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "registrations/s at N=5000 (plain PGS, indoor-shaped synthetic, 1 registration per step)"
+UNIT = "registrations/s"
+WORKLOAD = {"workload": "indoor-shaped single problem", "n": 5000, "inlier_ratio": 0.05, "sigma_m": 0.01,
+            "tau_m": 0.1, "k1": 2000, "k2": 2, "inlier_thresh_m": 0.1, "problems_cycled": 8,
+            "l2": "flushed between timed steps (256 MB write, outside the events)"}
+# kernels of ours launched per registration: pack, compat, sc2, hist, select, collect,
+# scan, emit, rank, pgs, kabsch, verify, finalize
+LAUNCHES_PER_STEP = 13
+# ncu per-launch DRAM traffic (bytes) of the SC^2 kernel on this workload; None until captured
+SC2_DRAM_BYTES = None
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return d, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _problems(count=8):
+    import synth
+    return [synth.make_problem("indoor", 5000, 0.05, s) for s in range(count)]
+
+
+def run_reference(args):
+    """FP64 oracle on host cores, same workload; each step = one registration."""
+    ws, rank, _ = _dist_env()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    probs = _problems(max(1, min(8, args.steps + args.warmup)))
+    for k in range(args.warmup):
+        p = probs[k % len(probs)]
+        oracle.register(p.x, p.y, p.tau, p.k1, p.theta)
+    times = []
+    for k in range(args.steps):
+        p = probs[k % len(probs)]
+        t0 = time.perf_counter()
+        oracle.register(p.x, p.y, p.tau, p.k1, p.theta)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    v = args.steps / tot
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": WORKLOAD,
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} registrations of the N=5000 workload, 1 host thread"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(budget_s=12.0):
+    import oracle
+    oracle.build()
+    probs = _problems(8)
+    t0 = time.perf_counter()
+    cnt = 0
+    while cnt < 3 or (time.perf_counter() - t0 < budget_s and cnt < len(probs)):
+        p = probs[cnt % len(probs)]
+        oracle.register(p.x, p.y, p.tau, p.k1, p.theta)
+        cnt += 1
+    dt = time.perf_counter() - t0
+    return {"value": cnt / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{cnt} registrations of the N=5000 workload (seeds 0..{cnt - 1}), "
+                      f"{dt:.1f} s on 1 host thread"}
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_2507_01439_gb300 as trg
+    from paper_2507_01439_gb300 import build as trbuild
+
+    ws, rank, local = _dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    trbuild.build() if rank == 0 else None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    stream = torch.cuda.Stream()
+    probs = _problems(8)
+    ctx = trg.TurboReg(max_n=5000, max_batch=1, device=local, stream=stream.cuda_stream)
+    dx = [torch.from_numpy(p.x).cuda() for p in probs]
+    dy = [torch.from_numpy(p.y).cuda() for p in probs]
+    hx = [torch.from_numpy(p.x).pin_memory() for p in probs]
+    hy = [torch.from_numpy(p.y).pin_memory() for p in probs]
+    prm = trg.default_params(0.1, 2000, 0.1, flags=trg.FLAG_STAGE_TIMES)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+
+    # correctness guard against the generator's ground truth (not timed)
+    import synth
+    ok = 0
+    for k, p in enumerate(probs):
+        r = ctx.register(dx[k], dy[k], prm)
+        ok += int(r.status == 0 and synth.rotation_error_deg(p.R_gt, r.R) < 15.0
+                  and synth.translation_error(p.t_gt, r.t) < 0.3)
+
+    def timed(kind, steps, warmup):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        sc2 = []
+        for k in range(warmup):
+            ctx.register(dx[k % 8], dy[k % 8], prm)
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        for k in range(steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+                ev[k][0].record(stream)
+            if kind == "device":
+                ctx.register(dx[k % 8], dy[k % 8], prm)
+            else:
+                ctx.register(hx[k % 8], hy[k % 8], prm)
+            ev[k][1].record(stream)
+            sc2.append(ctx.stage_times()["sc2"])
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        ms = [a.elapsed_time(b) for a, b in ev]
+        return ms, sc2
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    ms_dev, sc2_ms = timed("device", args.steps, args.warmup)
+    ms_host, _ = timed("host", args.steps, args.warmup)
+    clocks = sampler.stop()
+
+    tot_dev = sum(ms_dev) / 1e3
+    tot_host = sum(ms_host) / 1e3
+    if ws > 1:
+        t = torch.tensor([tot_dev, tot_host], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_dev, tot_host = float(t[0]), float(t[1])
+    value = ws * args.steps / tot_dev
+    e2e = ws * args.steps / tot_host
+
+    peaks, kind = _peaks()
+    # SC^2 GEMM: upper-triangle tiles x 2*BM*BN*N_pad dense FP8 MMA flops per launch
+    npad = 5120
+    nb = npad // 256
+    flops = nb * (nb + 1) * 2.0 * 128 * 256 * npad
+    sc2_avg_s = (sum(sc2_ms) / len(sc2_ms)) / 1e3
+    achieved = flops / sc2_avg_s / 1e12
+    peak = 2.0 * peaks["bf16_tflops_sustained"]    # FP8 dense = 2 x bf16 (nominal ratio)
+    roofline = {"bound": "tensor", "kernel": "sc2_tcgen05_kernel (FP8 E4M3 x E4M3 -> F32)",
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "peak_source": f"{kind}: 2 x bf16_tflops_sustained (FP8/BF16 nominal ratio 4.5/2.25)",
+                "traffic": SC2_DRAM_BYTES, "sc2_ms": sc2_avg_s * 1e3,
+                "flops_per_launch": flops}
+    if rank != 0:
+        return
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * tot_dev / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "fp8+f32", "data": "synthetic",
+            "config": dict(WORKLOAD, parallelism=f"replicas x{ws}"),
+            "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 2 * 5000 * 12,
+                    "d2h_bytes_per_step": 88},
+            "gpu_launches": LAUNCHES_PER_STEP * args.steps * 2,
+            "roofline": roofline, "clocks": clocks,
+            "success_rate_check": f"{ok}/8 problems RE<15deg TE<0.3m"}
+    if ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,139 @@
+/*
+ * turboreg.h -- C ABI of the GB300 (sm_103a) TurboReg registration library.
+ *
+ * Robust point-cloud registration from putative correspondences, following
+ * TurboReg (ICCV 2025): compatibility graph (Eq. 1), SC^2 graph (Eq. 2),
+ * O2Graph (Def. 2), Pivot-Guided Search for TurboCliques (Eq. 4-7, Alg. 1,
+ * Alg. 2), a Kabsch transform per TurboClique and selection of the
+ * transform with the largest inlier number (Sec. 3.5, Eq. 9).
+ *
+ * Problem (Sec. 3.1, App. A.1): N matches m_i = (x_i, y_i), x_i, y_i in R^3,
+ * with y_i = R x_i + t + r_i for inliers.  The library returns (R, t) in SE(3).
+ *
+ * Conventions shared by every entry point
+ *  - Points are float32, row-major [N][3] (x, y, z of match i at 3*i).
+ *  - Input pointers may be host or device memory; the kind is detected with
+ *    cudaPointerGetAttributes.  Device pointers must be readable from the
+ *    context's device and stay valid until the call returns.  Host inputs are
+ *    copied to the device inside the call.
+ *  - The caller owns every input and output buffer.  The library never keeps
+ *    a pointer to caller memory after a call returns.
+ *  - Every call is synchronous with respect to the host: it enqueues its work
+ *    on the context's stream and waits for it before returning.
+ *  - A context is not thread-safe.  Use one context per host thread / stream.
+ *  - Return values are turboreg_status codes.  Invalid arguments are rejected
+ *    before any device work is enqueued; the context is then unchanged.
+ */
+#ifndef TURBOREG_H
+#define TURBOREG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TURBOREG_ABI_VERSION 1
+
+/* Limits of one context (compile-time). */
+#define TURBOREG_MAX_N 32768   /* correspondences per problem */
+#define TURBOREG_K1_MAX 8192   /* pivots, Eq. 4 */
+#define TURBOREG_K2_MAX 16     /* TurboCliques per pivot, Eq. 7 */
+
+typedef struct turboreg_ctx turboreg_ctx;   /* opaque; owns the device workspace */
+
+typedef enum {
+    TURBOREG_OK = 0,
+    TURBOREG_ERR_INVALID_ARG = 1,   /* null pointer, N > max_n, K out of range, tau < 0, theta <= 0 */
+    TURBOREG_ERR_TOO_FEW = 2,       /* N < 3: no TurboClique can exist */
+    TURBOREG_ERR_NONFINITE = 3,     /* a NaN or Inf coordinate */
+    TURBOREG_ERR_OOM = 4,           /* device or pinned-host allocation failed */
+    TURBOREG_ERR_CUDA = 5,          /* a CUDA runtime error (the context should be destroyed) */
+    TURBOREG_ERR_TIMEOUT = 6,       /* a bounded device wait gave up */
+    TURBOREG_ERR_NO_HYPOTHESIS = 7  /* no edge, no TurboClique or no non-degenerate Kabsch */
+} turboreg_status;
+
+/* graph_mode */
+#define TURBOREG_GRAPH_O2 0          /* O2Graph (Def. 2), the paper's default */
+/* proposal */
+#define TURBOREG_PROPOSAL_PLAIN 0    /* pivots = top-K1 SC^2 edges (Eq. 4) */
+#define TURBOREG_PROPOSAL_LEARNED 1  /* pivots re-ranked by the learned inlier MLP */
+/* flags */
+#define TURBOREG_FLAG_SC2_BITSET 0x1u  /* SC^2 by bitset AND+popcount on CUDA cores
+                                          instead of the tcgen05 FP8 GEMM (same integers) */
+#define TURBOREG_FLAG_STAGE_TIMES 0x2u /* record per-stage CUDA-event times (turboreg_stage_times) */
+
+typedef struct {
+    float tau;            /* compatibility threshold of Eq. 1, metres, >= 0 */
+    int32_t k1;           /* pivot count K1 of Eq. 4, 1..TURBOREG_K1_MAX */
+    int32_t k2;           /* TurboCliques per pivot K2 of Eq. 7, 1..TURBOREG_K2_MAX (paper: 2) */
+    float inlier_thresh;  /* theta: a match is an inlier of (R,t) iff ||R x + t - y|| <= theta, > 0 */
+    int32_t graph_mode;   /* TURBOREG_GRAPH_O2 (only mode) */
+    int32_t proposal;     /* TURBOREG_PROPOSAL_PLAIN or _LEARNED */
+    float kappa_fp64;     /* Kabsch runs in FP64 when sigma1/sigma2 of the 3x3 cross-covariance
+                             exceeds this bound (0 selects the default 100) */
+    uint32_t flags;       /* TURBOREG_FLAG_* */
+} turboreg_params;
+
+typedef struct {
+    float R[9];             /* row-major rotation, y = R x + t */
+    float t[3];             /* translation, metres */
+    int32_t clique[3];      /* winning TurboClique (i < j < z), or -1 */
+    int32_t inlier_count;   /* inlier number of the winner (Eq. 9) */
+    int32_t hypothesis;     /* h* in Alg. 2 order h = r*|P| + p, lowest h on ties; -1 if none */
+    int32_t n_pivots;       /* |P| = min(K1, number of O2Graph edges) */
+    int32_t n_valid;        /* hypotheses with a TurboClique and a non-degenerate Kabsch */
+    int32_t used_fp64;      /* 1 if the winner's Kabsch ran in FP64 */
+    int32_t used_fallback;  /* learned proposal: 1 if the plain path decided the result */
+    int32_t status;         /* turboreg_status of this problem */
+} turboreg_result;
+
+/* Fill p with the paper's defaults (K2 = 2, O2Graph, plain proposal,
+ * kappa bound 100) and the given tau, K1 and inlier threshold. */
+void turboreg_default_params(turboreg_params* p, float tau, int32_t k1, float inlier_thresh);
+
+/* Create a context on CUDA device `device` sized for problems of up to
+ * max_n correspondences and batches of up to max_batch problems whose total
+ * correspondence count is at most max_n * max_batch.  `cuda_stream` is a
+ * cudaStream_t to run on, or NULL to let the context create its own.  The
+ * device workspace (about 3.1 * max_n^2 bytes plus 2.3 * max_n^2 bytes per
+ * batched problem slot) is allocated here, never inside register calls.
+ * On success *out receives the context.
+ * Errors: INVALID_ARG (out NULL, max_n < 3 or > TURBOREG_MAX_N, max_batch < 1),
+ *         OOM, CUDA. */
+int turboreg_create(int device, int32_t max_n, int32_t max_batch, void* cuda_stream,
+                    turboreg_ctx** out);
+
+/* Register one problem: src, dst = x, y as float32 [n][3]; writes the result
+ * to the host struct *out (out->status equals the return value).
+ * Errors: INVALID_ARG, TOO_FEW, NONFINITE, CUDA, TIMEOUT, NO_HYPOTHESIS
+ * (then R = I, t = 0, inlier_count = 0). */
+int turboreg_register(turboreg_ctx* ctx, const float* src, const float* dst, int32_t n,
+                      const turboreg_params* params, turboreg_result* out);
+
+/* Register `num` independent problems in one batched pass.  Problem b uses
+ * matches [offsets[b], offsets[b+1]) of src_cat / dst_cat (float32 [total][3]);
+ * offsets is a HOST array of num+1 non-decreasing int64 with offsets[0] = 0.
+ * params points to 1 struct (shared) or num structs (one per problem): pass
+ * params_count = 1 or num.  out is a HOST array of num results; each carries
+ * its own status.  Return value: OK if every problem was processed (per-problem
+ * failures such as NO_HYPOTHESIS are reported in out[b].status only), else the
+ * first argument / CUDA error.
+ * Errors: INVALID_ARG (num < 1 or > max_batch, a problem with n > max_n,
+ *         total > max_n * max_batch, bad offsets), NONFINITE is per problem,
+ *         CUDA, TIMEOUT. */
+int turboreg_register_batched(turboreg_ctx* ctx, const float* src_cat, const float* dst_cat,
+                              const int64_t* offsets, int32_t num,
+                              const turboreg_params* params, int32_t params_count,
+                              turboreg_result* out);
+
+/* Release the context and its device workspace.  NULL-safe. */
+void turboreg_destroy(turboreg_ctx* ctx);
+
+/* Human-readable name of a status code (static storage). */
+const char* turboreg_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TURBOREG_H */

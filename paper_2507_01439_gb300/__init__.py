@@ -1,0 +1,256 @@
+"""Python binding of the GB300 TurboReg registration library.
+
+Thin ctypes layer over ``libturboreg_gb300.so`` (C ABI in
+``include/turboreg.h``): it only marshals arguments.  Every step of the
+registration path runs in the library's CUDA kernels; there is no Python or
+CPU fallback, and importing the library raises if it has not been built.
+
+Inputs may be NumPy arrays (host memory, copied by the library) or CUDA
+torch tensors (device memory, read in place).  PyTorch is used only for
+device memory and streams.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libturboreg_gb300.so")
+
+TURBOREG_MAX_N = 32768
+TURBOREG_K1_MAX = 8192
+TURBOREG_K2_MAX = 16
+
+OK, ERR_INVALID_ARG, ERR_TOO_FEW, ERR_NONFINITE, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_NO_HYPOTHESIS = range(8)
+GRAPH_O2 = 0
+PROPOSAL_PLAIN, PROPOSAL_LEARNED = 0, 1
+FLAG_SC2_BITSET = 0x1
+FLAG_STAGE_TIMES = 0x2
+
+BUF_ADJ_BITS, BUF_ADJ_FP8, BUF_SC2, BUF_PIVOTS, BUF_CLIQUES, BUF_RT, BUF_INLIERS, BUF_ROWSCORE, BUF_DEGREE = range(1, 10)
+
+# symbols the library must export (declared in include/turboreg.h and include/turboreg_internal.h)
+EXPORTED = (
+    "turboreg_default_params", "turboreg_create", "turboreg_register", "turboreg_register_batched",
+    "turboreg_destroy", "turboreg_status_string", "turboreg_debug_shape", "turboreg_debug_copy",
+    "turboreg_stage_times", "turboreg_stage_name",
+)
+
+
+class turboreg_params(ctypes.Structure):
+    _fields_ = [("tau", ctypes.c_float), ("k1", ctypes.c_int32), ("k2", ctypes.c_int32),
+                ("inlier_thresh", ctypes.c_float), ("graph_mode", ctypes.c_int32),
+                ("proposal", ctypes.c_int32), ("kappa_fp64", ctypes.c_float), ("flags", ctypes.c_uint32)]
+
+
+class turboreg_result(ctypes.Structure):
+    _fields_ = [("R", ctypes.c_float * 9), ("t", ctypes.c_float * 3), ("clique", ctypes.c_int32 * 3),
+                ("inlier_count", ctypes.c_int32), ("hypothesis", ctypes.c_int32),
+                ("n_pivots", ctypes.c_int32), ("n_valid", ctypes.c_int32), ("used_fp64", ctypes.c_int32),
+                ("used_fallback", ctypes.c_int32), ("status", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load the CUDA library; raise if it is missing (no fallback exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"TurboReg CUDA library not built: {path} is missing "
+                           "(run __graft_entry__.build() or python -m paper_2507_01439_gb300.build)")
+    lib = ctypes.CDLL(path)
+    P, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    lib.turboreg_default_params.argtypes = [ctypes.POINTER(turboreg_params), ctypes.c_float, i32, ctypes.c_float]
+    lib.turboreg_default_params.restype = None
+    lib.turboreg_create.argtypes = [ctypes.c_int, i32, i32, P, ctypes.POINTER(P)]
+    lib.turboreg_create.restype = ctypes.c_int
+    lib.turboreg_register.argtypes = [P, P, P, i32, ctypes.POINTER(turboreg_params),
+                                      ctypes.POINTER(turboreg_result)]
+    lib.turboreg_register.restype = ctypes.c_int
+    lib.turboreg_register_batched.argtypes = [P, P, P, P, i32, ctypes.POINTER(turboreg_params), i32,
+                                              ctypes.POINTER(turboreg_result)]
+    lib.turboreg_register_batched.restype = ctypes.c_int
+    lib.turboreg_destroy.argtypes = [P]
+    lib.turboreg_destroy.restype = None
+    lib.turboreg_status_string.argtypes = [ctypes.c_int]
+    lib.turboreg_status_string.restype = ctypes.c_char_p
+    lib.turboreg_debug_shape.argtypes = [P, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                         ctypes.POINTER(i32)]
+    lib.turboreg_debug_shape.restype = ctypes.c_int
+    lib.turboreg_debug_copy.argtypes = [P, ctypes.c_int, P, i64]
+    lib.turboreg_debug_copy.restype = i64
+    lib.turboreg_stage_times.argtypes = [P, ctypes.POINTER(ctypes.c_float), i32]
+    lib.turboreg_stage_times.restype = ctypes.c_int
+    lib.turboreg_stage_name.argtypes = [i32]
+    lib.turboreg_stage_name.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _ptr(a):
+    """Raw address of a NumPy array or a torch tensor (host or CUDA)."""
+    if isinstance(a, np.ndarray):
+        return ctypes.c_void_p(a.ctypes.data)
+    if hasattr(a, "data_ptr"):
+        return ctypes.c_void_p(a.data_ptr())
+    raise TypeError("expected a numpy array or a torch tensor")
+
+
+def _check_points(a, n=None):
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float32 or a.ndim != 2 or a.shape[1] != 3 or not a.flags.c_contiguous:
+            raise ValueError("points must be C-contiguous float32 [N,3]")
+    else:
+        import torch
+        if a.dtype != torch.float32 or a.dim() != 2 or a.shape[1] != 3 or not a.is_contiguous():
+            raise ValueError("points must be contiguous float32 [N,3]")
+    if n is not None and a.shape[0] != n:
+        raise ValueError("src and dst must have the same number of rows")
+
+
+def default_params(tau, k1, inlier_thresh, k2=2, kappa_fp64=100.0, flags=0, proposal=PROPOSAL_PLAIN):
+    p = turboreg_params()
+    load_library().turboreg_default_params(ctypes.byref(p), float(tau), int(k1), float(inlier_thresh))
+    p.k2 = int(k2)
+    p.kappa_fp64 = float(kappa_fp64)
+    p.flags = int(flags)
+    p.proposal = int(proposal)
+    return p
+
+
+def status_string(code: int) -> str:
+    return load_library().turboreg_status_string(int(code)).decode()
+
+
+@dataclass
+class Result:
+    status: int
+    R: np.ndarray
+    t: np.ndarray
+    clique: tuple
+    inlier_count: int
+    hypothesis: int
+    n_pivots: int
+    n_valid: int
+    used_fp64: int
+    used_fallback: int
+
+    @staticmethod
+    def from_c(r: turboreg_result) -> "Result":
+        return Result(int(r.status), np.array(r.R[:], dtype=np.float32).reshape(3, 3),
+                      np.array(r.t[:], dtype=np.float32), tuple(r.clique[:]), int(r.inlier_count),
+                      int(r.hypothesis), int(r.n_pivots), int(r.n_valid), int(r.used_fp64),
+                      int(r.used_fallback))
+
+
+class TurboReg:
+    """One library context (device workspace sized for max_n); not thread-safe."""
+
+    def __init__(self, max_n=5000, max_batch=1, device=0, stream=None):
+        self._lib = load_library()
+        h = ctypes.c_void_p()
+        st = ctypes.c_void_p(stream) if stream else None
+        rc = self._lib.turboreg_create(int(device), int(max_n), int(max_batch), st, ctypes.byref(h))
+        if rc != OK:
+            raise RuntimeError(f"turboreg_create failed: {status_string(rc)}")
+        self.handle = h
+        self.max_n = max_n
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self._lib.turboreg_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def register(self, src, dst, params: turboreg_params) -> Result:
+        _check_points(src)
+        _check_points(dst, src.shape[0])
+        out = turboreg_result()
+        self._lib.turboreg_register(self.handle, _ptr(src), _ptr(dst), int(src.shape[0]),
+                                    ctypes.byref(params), ctypes.byref(out))
+        return Result.from_c(out)
+
+    def register_batched(self, src_cat, dst_cat, offsets, params) -> list:
+        _check_points(src_cat)
+        _check_points(dst_cat, src_cat.shape[0])
+        offs = np.ascontiguousarray(offsets, dtype=np.int64)
+        num = offs.shape[0] - 1
+        if isinstance(params, turboreg_params):
+            parr, pc = (turboreg_params * 1)(params), 1
+        else:
+            parr, pc = (turboreg_params * len(params))(*params), len(params)
+        out = (turboreg_result * num)()
+        rc = self._lib.turboreg_register_batched(self.handle, _ptr(src_cat), _ptr(dst_cat),
+                                                 ctypes.c_void_p(offs.ctypes.data), num, parr, pc, out)
+        if rc != OK:
+            raise RuntimeError(f"turboreg_register_batched failed: {status_string(rc)}")
+        return [Result.from_c(out[b]) for b in range(num)]
+
+    # ---- inspection (internal header) ----
+    def shape(self):
+        n, npad, npiv, nh = (ctypes.c_int32() for _ in range(4))
+        rc = self._lib.turboreg_debug_shape(self.handle, ctypes.byref(n), ctypes.byref(npad),
+                                            ctypes.byref(npiv), ctypes.byref(nh))
+        if rc != OK:
+            raise RuntimeError(status_string(rc))
+        return n.value, npad.value, npiv.value, nh.value
+
+    def buffer(self, which: int) -> np.ndarray:
+        n, npad, npiv, nh = self.shape()
+        spec = {
+            BUF_ADJ_BITS: (np.uint32, (npad, npad // 32)),
+            BUF_ADJ_FP8: (np.uint8, (npad, npad)),
+            BUF_SC2: (np.uint16, (npad, npad)),
+            BUF_PIVOTS: (np.int32, (npiv, 4)),
+            BUF_CLIQUES: (np.int32, (nh, 4)),
+            BUF_RT: (np.float32, (nh, 16)),
+            BUF_INLIERS: (np.int32, (nh,)),
+            BUF_ROWSCORE: (np.int32, (n,)),
+            BUF_DEGREE: (np.int32, (n,)),
+        }[which]
+        arr = np.zeros(spec[1], dtype=spec[0])
+        got = self._lib.turboreg_debug_copy(self.handle, int(which), ctypes.c_void_p(arr.ctypes.data),
+                                            arr.nbytes)
+        if got < 0:
+            raise RuntimeError(status_string(-got))
+        return arr
+
+    def stage_times(self):
+        buf = (ctypes.c_float * 16)()
+        k = self._lib.turboreg_stage_times(self.handle, buf, 16)
+        return {self._lib.turboreg_stage_name(i).decode(): float(buf[i]) for i in range(k)}
+
+
+# ---- the C ABI under its own names (argument marshalling only) ----
+
+def turboreg_create(device=0, max_n=5000, max_batch=1, stream=None) -> TurboReg:
+    return TurboReg(max_n=max_n, max_batch=max_batch, device=device, stream=stream)
+
+
+def turboreg_register(ctx: TurboReg, src, dst, params: turboreg_params) -> Result:
+    return ctx.register(src, dst, params)
+
+
+def turboreg_register_batched(ctx: TurboReg, src_cat, dst_cat, offsets, params) -> list:
+    return ctx.register_batched(src_cat, dst_cat, offsets, params)
+
+
+def turboreg_destroy(ctx: TurboReg) -> None:
+    ctx.close()

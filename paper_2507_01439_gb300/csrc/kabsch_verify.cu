@@ -1,0 +1,316 @@
+// Stages 5-7: model estimation (Sec. 3.5, Eq. 9).
+//
+// kabsch:   per TurboClique h, the proper rotation R and translation t that
+//           minimise sum_a ||R x_a + t - y_a||^2 over its 3 matches.
+// verify:   IN(h) = #{k : ||R_h x_k + t_h - y_k||^2 <= theta^2}.
+// finalize: h* = argmax IN (lowest h on ties) -> turboreg_result.
+//
+// Closed-form 3-point Kabsch.  With a_k = x_k - mean(x), b_k = y_k - mean(y)
+// the cross-covariance H = sum_k a_k b_k^T has rank <= 2 (three points are
+// coplanar).  Write a_k = E P_k, b_k = F Q_k with E = [e1 e2], F = [f1 f2]
+// orthonormal in-plane frames and n_x = e1 x e2, n_y = f1 x f2.  Then
+// H = E M F^T with the 2x2 M = sum_k P_k Q_k^T, and every proper rotation
+// maximising tr(R H) has the form R = F X E^T + det(X) n_y n_x^T with X in
+// O(2) maximising tr(X M):
+//   rotation   X = [[c,-s],[s,c]] : tr = c(m11+m22) + s(m12-m21)
+//   reflection X = [[c,s],[s,-c]] : tr = c(m11-m22) + s(m12+m21)
+// The larger of the two vector norms is sigma1 + sigma2, the smaller
+// |sigma1 - sigma2| (singular values of M, hence of H), and (c, s) is the
+// normalised winning vector.  No iteration, no atan2.
+//
+// Precision: FP32; the same closed form runs in FP64 when
+// kappa = sigma1/sigma2 exceeds the bound (default 100) or is not finite.  A
+// clique with sigma2 <= 1e-12 sigma1 (collinear or repeated points) is invalid.
+#include "tr_common.cuh"
+#include "tr_problem.h"
+
+namespace tr {
+
+namespace {
+
+template <typename T>
+__device__ __forceinline__ T tsqrt(T x);
+template <>
+__device__ __forceinline__ float tsqrt<float>(float x) { return sqrtf(x); }
+template <>
+__device__ __forceinline__ double tsqrt<double>(double x) { return sqrt(x); }
+
+template <typename T>
+struct KabschOut {
+    T R[9];
+    T t[3];
+    T kappa;
+    bool ok;    // frames defined and sigma1 > 0
+    T s1, s2;
+};
+
+template <typename T>
+__device__ __forceinline__ void cross3(const T a[3], const T b[3], T c[3])
+{
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+template <typename T>
+__device__ __forceinline__ T dot3(const T a[3], const T b[3])
+{
+    return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+}
+
+// In-plane orthonormal frame of a triangle: e1 along its longest edge,
+// n = unit normal of (p1 - p0) x (p2 - p0), e2 = n x e1.
+template <typename T>
+__device__ __forceinline__ bool frame3(const T p[3][3], T e1[3], T e2[3], T nrm[3])
+{
+    T d01[3], d02[3], d12[3];
+    for (int c = 0; c < 3; ++c) {
+        d01[c] = p[1][c] - p[0][c];
+        d02[c] = p[2][c] - p[0][c];
+        d12[c] = p[2][c] - p[1][c];
+    }
+    cross3(d01, d02, nrm);
+    const T nn = dot3(nrm, nrm);
+    const T l01 = dot3(d01, d01), l02 = dot3(d02, d02), l12 = dot3(d12, d12);
+    const T* e = d01;
+    T le = l01;
+    if (l02 > le) { e = d02; le = l02; }
+    if (l12 > le) { e = d12; le = l12; }
+    if (!(nn > T(0)) || !(le > T(0))) return false;
+    const T in = T(1) / tsqrt(nn), ie = T(1) / tsqrt(le);
+    for (int c = 0; c < 3; ++c) {
+        nrm[c] *= in;
+        e1[c] = e[c] * ie;
+    }
+    cross3(nrm, e1, e2);
+    return true;
+}
+
+template <typename T>
+__device__ void kabsch3(const T p[3][3], const T q[3][3], KabschOut<T>& o)
+{
+    T cx[3], cy[3];
+    for (int c = 0; c < 3; ++c) {
+        cx[c] = (p[0][c] + p[1][c] + p[2][c]) / T(3);
+        cy[c] = (q[0][c] + q[1][c] + q[2][c]) / T(3);
+    }
+    T e1[3], e2[3], nx[3], f1[3], f2[3], ny[3];
+    o.ok = frame3(p, e1, e2, nx) && frame3(q, f1, f2, ny);
+    if (!o.ok) {
+        o.kappa = T(INFINITY);
+        o.s1 = o.s2 = T(0);
+        return;
+    }
+    T m11 = 0, m12 = 0, m21 = 0, m22 = 0;
+    for (int k = 0; k < 3; ++k) {
+        T a[3], b[3];
+        for (int c = 0; c < 3; ++c) {
+            a[c] = p[k][c] - cx[c];
+            b[c] = q[k][c] - cy[c];
+        }
+        const T P1 = dot3(a, e1), P2 = dot3(a, e2);
+        const T Q1 = dot3(b, f1), Q2 = dot3(b, f2);
+        m11 += P1 * Q1; m12 += P1 * Q2;
+        m21 += P2 * Q1; m22 += P2 * Q2;
+    }
+    const T rx = m11 + m22, ry = m12 - m21;   // rotation candidate
+    const T fx = m11 - m22, fy = m12 + m21;   // reflection candidate
+    const T nr = tsqrt(rx * rx + ry * ry), nf = tsqrt(fx * fx + fy * fy);
+    const T hi = nr >= nf ? nr : nf, lo = nr >= nf ? nf : nr;
+    o.s1 = (hi + lo) * T(0.5);
+    o.s2 = (hi - lo) * T(0.5);
+    o.kappa = o.s2 > T(0) ? o.s1 / o.s2 : T(INFINITY);
+    if (!(hi > T(0))) {
+        o.ok = false;
+        return;
+    }
+    T X00, X01, X10, X11, sg;
+    if (nr >= nf) {
+        const T c = rx / nr, s = ry / nr;
+        X00 = c; X01 = -s; X10 = s; X11 = c; sg = T(1);
+    } else {
+        const T c = fx / nf, s = fy / nf;
+        X00 = c; X01 = s; X10 = s; X11 = -c; sg = T(-1);
+    }
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c)
+            o.R[r * 3 + c] = X00 * f1[r] * e1[c] + X01 * f1[r] * e2[c] + X10 * f2[r] * e1[c] +
+                             X11 * f2[r] * e2[c] + sg * ny[r] * nx[c];
+    for (int r = 0; r < 3; ++r)
+        o.t[r] = cy[r] - (o.R[r * 3 + 0] * cx[0] + o.R[r * 3 + 1] * cx[1] + o.R[r * 3 + 2] * cx[2]);
+}
+
+__global__ void __launch_bounds__(128) kabsch_kernel(ProbView v)
+{
+    const int h = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nh = v.ctl->n_pivots * v.k2;
+    if (h >= nh) return;
+    v.inl[h] = 0;
+    float* out = v.rt + (size_t)h * 16;
+    const int4 cl = v.cliques[h];
+    uint32_t flags = 0;
+    if (cl.w) {
+        const int idx[3] = {cl.x, cl.y, cl.z};
+        float p[3][3], q[3][3];
+        for (int a = 0; a < 3; ++a)
+            for (int c = 0; c < 3; ++c) {
+                p[a][c] = v.pts[(size_t)c * v.n_pad + idx[a]];
+                q[a][c] = v.pts[(size_t)(c + 3) * v.n_pad + idx[a]];
+            }
+        KabschOut<float> o;
+        kabsch3<float>(p, q, o);
+        const float kb = v.kappa_fp64;
+        if (o.ok && o.kappa <= kb) {
+            for (int r = 0; r < 9; ++r) out[r] = o.R[r];
+            for (int r = 0; r < 3; ++r) out[9 + r] = o.t[r];
+            out[12] = o.kappa;
+            flags = 1u;
+        } else {
+            double pd[3][3], qd[3][3];
+            for (int a = 0; a < 3; ++a)
+                for (int c = 0; c < 3; ++c) {
+                    pd[a][c] = p[a][c];
+                    qd[a][c] = q[a][c];
+                }
+            KabschOut<double> od;
+            kabsch3<double>(pd, qd, od);
+            const bool valid = od.ok && od.s1 > 0.0 && od.s2 > 1e-12 * od.s1;
+            for (int r = 0; r < 9; ++r) out[r] = static_cast<float>(od.R[r]);
+            for (int r = 0; r < 3; ++r) out[9 + r] = static_cast<float>(od.t[r]);
+            out[12] = static_cast<float>(od.kappa);
+            flags = (valid ? 1u : 0u) | 2u;
+        }
+    }
+    if (!(flags & 1u)) {
+        for (int r = 0; r < 13; ++r) out[r] = 0.f;
+    }
+    out[13] = __int_as_float(static_cast<int>(flags));
+}
+
+constexpr int kVerHyp = 256;   // hypotheses per block (one per thread)
+constexpr int kVerPts = 256;   // correspondences per block, staged in shared memory
+
+__global__ void __launch_bounds__(kVerHyp) verify_kernel(ProbView v)
+{
+    __shared__ __align__(16) float sp[6][kVerPts];
+    const int nh = v.ctl->n_pivots * v.k2;
+    const int h0 = blockIdx.x * kVerHyp;
+    if (h0 >= nh) return;
+    const int k0 = blockIdx.y * kVerPts;
+    const int cnt = min(kVerPts, v.n - k0);
+    for (int q = threadIdx.x; q < kVerPts; q += blockDim.x) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) sp[c][q] = v.pts[(size_t)c * v.n_pad + k0 + q];
+    }
+    __syncthreads();
+    const int h = h0 + threadIdx.x;
+    if (h >= nh) return;
+    const float* rt = v.rt + (size_t)h * 16;
+    const uint32_t flags = static_cast<uint32_t>(__float_as_int(rt[13]));
+    if (!(flags & 1u)) return;
+    const float r00 = rt[0], r01 = rt[1], r02 = rt[2];
+    const float r10 = rt[3], r11 = rt[4], r12 = rt[5];
+    const float r20 = rt[6], r21 = rt[7], r22 = rt[8];
+    const float t0 = rt[9], t1 = rt[10], t2 = rt[11];
+    const float th2 = v.theta * v.theta;
+    int in = 0;
+#pragma unroll 4
+    for (int k = 0; k < cnt; ++k) {
+        const float x0 = sp[0][k], x1 = sp[1][k], x2 = sp[2][k];
+        const float e0 = fmaf(r00, x0, fmaf(r01, x1, fmaf(r02, x2, t0 - sp[3][k])));
+        const float e1 = fmaf(r10, x0, fmaf(r11, x1, fmaf(r12, x2, t1 - sp[4][k])));
+        const float e2 = fmaf(r20, x0, fmaf(r21, x1, fmaf(r22, x2, t2 - sp[5][k])));
+        const float d2 = fmaf(e0, e0, fmaf(e1, e1, e2 * e2));
+        in += d2 <= th2 ? 1 : 0;
+    }
+    if (in) atomicAdd(&v.inl[h], in);
+}
+
+__global__ void __launch_bounds__(1024) finalize_kernel(ProbView v)
+{
+    __shared__ unsigned long long sbest[32];
+    __shared__ int scnt[32], sfp[32];
+    const int np = v.ctl->n_pivots;
+    const int nh = np * v.k2;
+    unsigned long long best = 0ull;
+    int nvalid = 0, nfp = 0;
+    for (int h = threadIdx.x; h < nh; h += blockDim.x) {
+        const uint32_t flags = static_cast<uint32_t>(__float_as_int(v.rt[(size_t)h * 16 + 13]));
+        if (flags & 2u) ++nfp;
+        if (!(flags & 1u)) continue;
+        ++nvalid;
+        const unsigned long long key =
+            (static_cast<unsigned long long>(static_cast<uint32_t>(v.inl[h]) + 1u) << 32) |
+            (0xFFFFFFFFull - static_cast<unsigned long long>(h));
+        best = key > best ? key : best;
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int off = 16; off >= 1; off >>= 1) {
+        const unsigned long long o = __shfl_xor_sync(0xffffffffu, best, off);
+        best = o > best ? o : best;
+        nvalid += __shfl_xor_sync(0xffffffffu, nvalid, off);
+        nfp += __shfl_xor_sync(0xffffffffu, nfp, off);
+    }
+    if (lane == 0) { sbest[warp] = best; scnt[warp] = nvalid; sfp[warp] = nfp; }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+        best = sbest[w] > best ? sbest[w] : best;
+        nvalid += scnt[w];
+        nfp += sfp[w];
+    }
+    best = sbest[0] > best ? sbest[0] : best;
+    v.ctl->n_valid = nvalid;
+    v.ctl->n_fp64 = nfp;
+    turboreg_result r;
+    for (int q = 0; q < 9; ++q) r.R[q] = (q % 4 == 0) ? 1.f : 0.f;
+    r.t[0] = r.t[1] = r.t[2] = 0.f;
+    r.clique[0] = r.clique[1] = r.clique[2] = -1;
+    r.inlier_count = 0;
+    r.hypothesis = -1;
+    r.n_pivots = np;
+    r.n_valid = nvalid;
+    r.used_fp64 = 0;
+    r.used_fallback = 0;
+    const uint32_t err = v.ctl->err;
+    if (err & TR_ERR_NONFINITE) {
+        r.status = TURBOREG_ERR_NONFINITE;
+    } else if (err & TR_ERR_TIMEOUT) {
+        r.status = TURBOREG_ERR_TIMEOUT;
+    } else if (err & TR_ERR_OVERFLOW) {
+        r.status = TURBOREG_ERR_CUDA;
+    } else if (best == 0ull) {
+        r.status = TURBOREG_ERR_NO_HYPOTHESIS;
+    } else {
+        const int h = static_cast<int>(0xFFFFFFFFull - (best & 0xFFFFFFFFull));
+        const float* rt = v.rt + (size_t)h * 16;
+        for (int q = 0; q < 9; ++q) r.R[q] = rt[q];
+        for (int q = 0; q < 3; ++q) r.t[q] = rt[9 + q];
+        const int4 cl = v.cliques[h];
+        r.clique[0] = cl.x; r.clique[1] = cl.y; r.clique[2] = cl.z;
+        r.inlier_count = static_cast<int>((best >> 32) - 1ull);
+        r.hypothesis = h;
+        r.used_fp64 = (static_cast<uint32_t>(__float_as_int(rt[13])) & 2u) ? 1 : 0;
+        r.status = TURBOREG_OK;
+    }
+    *v.res = r;
+}
+
+}  // namespace
+
+void launch_kabsch(const ProbView& v, cudaStream_t s)
+{
+    const int cap = v.k1 * v.k2;
+    kabsch_kernel<<<(cap + 127) / 128, 128, 0, s>>>(v);
+}
+
+void launch_verify(const ProbView& v, cudaStream_t s)
+{
+    const int cap = v.k1 * v.k2;
+    dim3 grid((cap + kVerHyp - 1) / kVerHyp, (v.n + kVerPts - 1) / kVerPts);
+    verify_kernel<<<grid, kVerHyp, 0, s>>>(v);
+}
+
+void launch_finalize(const ProbView& v, cudaStream_t s) { finalize_kernel<<<1, 1024, 0, s>>>(v); }
+
+}  // namespace tr

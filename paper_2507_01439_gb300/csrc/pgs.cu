@@ -1,0 +1,107 @@
+// Stage 4: Pivot-Guided Search (Eq. 5-7, Alg. 1) on the O2Graph.
+//
+// For pivot p = (i, j) (i < j):
+//   N(i,j) = { z : G~_iz > 0 and G~_jz > 0 }            (Eq. 5)
+// On the O2Graph G~_iz > 0 needs i < z, so z > j; and for a pivot edge,
+// G~_iz > 0 <=> G_iz = 1 (j is then a common neighbour of i and z).  So
+//   N(i,j) = { z > j : G_iz = G_jz = 1 } = bits of (row_i AND row_j) above j.
+//   S(z)   = W_ij + W_iz + W_jz                          (Eq. 6)
+// and the K2 largest S (ties: lower z) form the pivot's TurboCliques (Eq. 7),
+// written in the Alg. 2 layout h = r * |P| + p.  Empty slots are invalid.
+//
+// One warp per pivot: lane l ANDs bitset words l, l+32, ... of the two rows,
+// keeps a private top-K2 list, and the warp merges the 32 lists with K2
+// rounds of a 64-bit max-reduction over keys (S << 32 | ~z).
+#include "tr_common.cuh"
+#include "tr_problem.h"
+
+namespace tr {
+
+namespace {
+
+template <int K2C>
+__global__ void __launch_bounds__(256) pgs_kernel(ProbView v)
+{
+    const int lane = threadIdx.x & 31;
+    const int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int np = v.ctl->n_pivots;
+    if (p >= np) return;
+    const int k2 = K2C > 0 ? K2C : v.k2;
+    const int4 pv = v.piv[p];
+    const int i = pv.x, j = pv.y, wij = pv.z;
+    const uint32_t* bi = v.bits + (size_t)i * v.ldb;
+    const uint32_t* bj = v.bits + (size_t)j * v.ldb;
+    const uint16_t* wi = v.w + (size_t)i * v.n_pad;
+    const uint16_t* wj = v.w + (size_t)j * v.n_pad;
+
+    constexpr int L = K2C > 0 ? K2C : TURBOREG_K2_MAX;
+    uint64_t top[L];
+#pragma unroll
+    for (int r = 0; r < L; ++r) top[r] = 0ull;
+
+    const int zs = j + 1;
+    const int w0 = zs >> 5;
+    for (int wd = w0 + lane; wd < v.ldb; wd += 32) {
+        uint32_t m = bi[wd] & bj[wd];
+        if (wd == w0) m &= ~0u << (zs & 31);
+        while (m) {
+            const int b = __ffs(m) - 1;
+            m &= m - 1;
+            const int z = wd * 32 + b;
+            const int s = wij + static_cast<int>(wi[z]) + static_cast<int>(wj[z]);
+            const uint64_t key = (static_cast<uint64_t>(s) << 32) | (0xFFFFFFFFu - static_cast<uint32_t>(z));
+            // insertion into the descending list (keys are unique)
+            if (key > top[L - 1]) {
+                uint64_t cur = key;
+#pragma unroll
+                for (int r = 0; r < L; ++r) {
+                    if (cur > top[r]) {
+                        const uint64_t t = top[r];
+                        top[r] = cur;
+                        cur = t;
+                    }
+                }
+            }
+        }
+    }
+    // warp merge: k2 rounds of argmax over the lanes' list heads
+    int head = 0;
+    for (int r = 0; r < k2; ++r) {
+        uint64_t mine = 0ull;
+#pragma unroll
+        for (int q = 0; q < L; ++q)
+            if (q == head) mine = top[q];
+        uint64_t best = mine;
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) {
+            const uint64_t o = __shfl_xor_sync(0xffffffffu, best, off);
+            best = o > best ? o : best;
+        }
+        if (best == mine && mine != 0ull) ++head;
+        if (lane == 0) {
+            const size_t h = static_cast<size_t>(r) * np + p;
+            if (best != 0ull) {
+                const int z = static_cast<int>(0xFFFFFFFFu - static_cast<uint32_t>(best & 0xFFFFFFFFull));
+                v.cliques[h] = make_int4(i, j, z, 1);
+            } else {
+                v.cliques[h] = make_int4(i, j, -1, 0);
+            }
+        }
+    }
+}
+
+}  // namespace
+
+void launch_pgs(const ProbView& v, cudaStream_t s)
+{
+    const int blocks = (v.k1 * 32 + 255) / 256;
+    switch (v.k2) {
+        case 1: pgs_kernel<1><<<blocks, 256, 0, s>>>(v); break;
+        case 2: pgs_kernel<2><<<blocks, 256, 0, s>>>(v); break;
+        case 3: pgs_kernel<3><<<blocks, 256, 0, s>>>(v); break;
+        case 4: pgs_kernel<4><<<blocks, 256, 0, s>>>(v); break;
+        default: pgs_kernel<0><<<blocks, 256, 0, s>>>(v); break;
+    }
+}
+
+}  // namespace tr

@@ -1,0 +1,125 @@
+"""Stage-by-stage comparison of the CUDA path with the FP64 oracle.
+
+Bars (from the registration contract):
+  adjacency, SC^2, pivots, cliques: bit-exact;
+  per-hypothesis R, t: within a tolerance derived from FP32 rounding and the
+    conditioning kappa = sigma1/sigma2 of the 3-point cross-covariance;
+  inlier counts: a difference is allowed only for correspondences whose
+    oracle residual lies within delta(h) of the threshold, where delta(h) is
+    the residual perturbation the measured (R, t) difference and FP32
+    evaluation can cause (never less than 1e-5 m);
+  final R, t: within 1e-4 (Frobenius) and 1e-4 m of the oracle's hypothesis
+    at the GPU's h* (h* itself must equal the oracle's unless the inlier
+    numbers tie within the reported near-threshold points).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+import oracle
+import paper_2507_01439_gb300 as trg
+
+U32 = 2.0 ** -24
+
+
+def unpack_bits(bits, n):
+    b = np.unpackbits(bits.view(np.uint8), axis=1, bitorder="little")
+    return b[:n, :n]
+
+
+def oracle_stages(x, y, tau, k1, k2):
+    A = oracle.compat(x, y, tau)
+    S = oracle.sc2(A)
+    pi, pj, pw = oracle.pivots(S, k1)
+    cl, va = oracle.cliques(S, pi, pj, k2)
+    return A, S, (pi, pj, pw), (cl, va)
+
+
+def check_graph_stages(ctx: trg.TurboReg, A, S, n):
+    npad = ctx.shape()[1]
+    bits = ctx.buffer(trg.BUF_ADJ_BITS)
+    Ag = unpack_bits(bits, n)
+    assert np.array_equal(Ag, A), f"adjacency mismatch at {np.argwhere(Ag != A)[:5]}"
+    full = unpack_bits(bits, npad)
+    assert not full[n:, :].any() and not full[:, n:].any(), "padding bits set"
+    a8 = ctx.buffer(trg.BUF_ADJ_FP8)
+    assert np.array_equal(a8[:n, :n] == 0x38, A.astype(bool))
+    assert not a8[n:, :].any() and not a8[:, n:].any()
+    assert set(np.unique(a8[:n, :n]).tolist()) <= {0, 0x38}
+    assert np.array_equal(ctx.buffer(trg.BUF_DEGREE), A.sum(1).astype(np.int32))
+    W = ctx.buffer(trg.BUF_SC2)[:n, :n].astype(np.int32)
+    iu = np.triu_indices(n, 1)
+    bad = np.flatnonzero(W[iu] != S[iu])
+    assert bad.size == 0, f"SC2 mismatch at {[(iu[0][b], iu[1][b], W[iu][b], S[iu][b]) for b in bad[:5]]}"
+    assert np.array_equal(ctx.buffer(trg.BUF_ROWSCORE), S.sum(1).astype(np.int32))
+
+
+def check_pivots_cliques(ctx, piv, cliq, k2):
+    pi, pj, pw = piv
+    P = ctx.buffer(trg.BUF_PIVOTS)
+    assert P.shape[0] == len(pi)
+    assert np.array_equal(P[:, 0], pi) and np.array_equal(P[:, 1], pj) and np.array_equal(P[:, 2], pw)
+    cl, va = cliq
+    C = ctx.buffer(trg.BUF_CLIQUES)
+    assert C.shape[0] == len(va)
+    assert np.array_equal(C[:, 3].astype(bool), va)
+    assert np.array_equal(C[va, :3], cl[va])
+
+
+def check_hypotheses(ctx, x, y, theta, orc: oracle.OracleResult, rt_tol_scale=1.0):
+    """Per-hypothesis Kabsch and inlier parity; returns statistics."""
+    RT = ctx.buffer(trg.BUF_RT)
+    IN = ctx.buffer(trg.BUF_INLIERS)
+    nh = RT.shape[0]
+    flags = RT[:, 13].view(np.int32)
+    valid_g = (flags & 1).astype(bool)
+    valid_o = orc.hyp_valid[:nh]
+    assert np.array_equal(valid_g, valid_o), f"validity differs at {np.flatnonzero(valid_g != valid_o)[:5]}"
+    xmax = float(np.abs(x).max()) * np.sqrt(3)
+    ymax = float(np.abs(y).max()) * np.sqrt(3)
+    stats = {"n_hyp": nh, "n_valid": int(valid_g.sum()), "fp64": int(((flags & 2) != 0).sum()),
+             "count_mismatch_hyps": 0, "max_dR": 0.0, "max_dt": 0.0, "max_delta": 0.0}
+    for h in np.flatnonzero(valid_g):
+        Rg = RT[h, :9].astype(np.float64).reshape(3, 3)
+        tg = RT[h, 9:12].astype(np.float64)
+        kap = float(RT[h, 12])
+        Ro = orc.rt[h, :9].reshape(3, 3)
+        to = orc.rt[h, 9:12]
+        dR = float(np.linalg.norm(Rg - Ro))
+        dt = float(np.linalg.norm(tg - to))
+        tolR = rt_tol_scale * (4e-6 * (1.0 + kap) + 1e-6)
+        assert dR <= tolR, f"h={h} |dR|={dR:g} kappa={kap:g}"
+        tolt = tolR * (1.0 + xmax) + 8 * U32 * (1.0 + xmax + ymax)
+        assert dt <= tolt, f"h={h} |dt|={dt:g} kappa={kap:g}"
+        stats["max_dR"] = max(stats["max_dR"], dR)
+        stats["max_dt"] = max(stats["max_dt"], dt)
+        if IN[h] != orc.in_counts[h]:
+            delta = max(1e-5, dR * xmax + dt + 16 * U32 * (xmax + ymax + np.linalg.norm(tg)))
+            _, near = oracle.inliers(x, y, Ro, to, theta, band=delta)
+            stats["count_mismatch_hyps"] += 1
+            stats["max_delta"] = max(stats["max_delta"], delta)
+            assert abs(int(IN[h]) - int(orc.in_counts[h])) <= near, \
+                f"h={h}: IN gpu {IN[h]} oracle {orc.in_counts[h]}, only {near} within {delta:g} m"
+    return stats
+
+
+def check_final(res: trg.Result, ctx, orc: oracle.OracleResult):
+    assert res.status == orc.status
+    if orc.status != 0:
+        return "none"
+    IN = ctx.buffer(trg.BUF_INLIERS)
+    assert res.inlier_count == IN[res.hypothesis]
+    h = res.hypothesis
+    if h != orc.hypothesis:
+        # ambiguous: the GPU's winner must tie the oracle's best within the near-threshold points
+        gap = orc.inlier_count - orc.in_counts[h]
+        assert gap <= orc.near_counts[h] + orc.near_counts[orc.hypothesis] + 2, \
+            f"h* gpu {h} (IN_o {orc.in_counts[h]}) vs oracle {orc.hypothesis} (IN_o {orc.inlier_count})"
+        kind = "ambiguous"
+    else:
+        kind = "exact"
+    Ro = orc.rt[h, :9].reshape(3, 3)
+    to = orc.rt[h, 9:12]
+    assert np.linalg.norm(res.R.astype(np.float64) - Ro) <= 1e-4
+    assert np.linalg.norm(res.t.astype(np.float64) - to) <= 1e-4
+    return kind

@@ -1,0 +1,191 @@
+"""GPU parity of the CUDA registration path with the FP64 oracle (through the C ABI)."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2507_01439_gb300 as trg
+import synth
+from parity_util import (check_final, check_graph_stages, check_hypotheses, check_pivots_cliques,
+                         oracle_stages)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2507_01439_gb300 import build
+    build.build()
+    c = trg.TurboReg(max_n=5000, max_batch=8)
+    yield c
+    c.close()
+
+
+def _full_parity(ctx, p, k1, k2=2, flags=0, tau=None, theta=None):
+    tau = p.tau if tau is None else tau
+    theta = p.theta if theta is None else theta
+    prm = trg.default_params(tau, k1, theta, k2=k2, flags=flags)
+    res = ctx.register(p.x, p.y, prm)
+    A, S, piv, cliq = oracle_stages(p.x, p.y, tau, k1, k2)
+    n = p.n
+    assert ctx.shape()[0] == n
+    check_graph_stages(ctx, A, S, n)
+    check_pivots_cliques(ctx, piv, cliq, k2)
+    orc = oracle.register(p.x, p.y, tau, k1, theta, k2=k2)
+    assert res.n_pivots == orc.n_pivots
+    stats = check_hypotheses(ctx, p.x, p.y, theta, orc)
+    assert res.n_valid == orc.n_valid
+    kind = check_final(res, ctx, orc)
+    return res, orc, stats, kind
+
+
+@pytest.mark.parametrize("n,seed", [(3, 1), (7, 2), (33, 3), (127, 4), (128, 5), (129, 6),
+                                    (255, 7), (256, 8), (257, 9), (600, 10)])
+def test_small_ragged_sizes(ctx, n, seed):
+    # dense enough to have edges at tiny N: generous tau on a small cube
+    p = synth.make_problem("cube", n, 0.5, seed, tau=0.3, theta=0.1)
+    _full_parity(ctx, p, k1=min(200, 4 * n), k2=2)
+
+
+def test_config_cube_1000(ctx):
+    p = synth.make_problem("cube", 1000, 0.10, 0)
+    res, orc, stats, kind = _full_parity(ctx, p, k1=1000)
+    assert res.status == 0
+    assert synth.rotation_error_deg(p.R_gt, res.R) < 15 and synth.translation_error(p.t_gt, res.t) < 0.3
+
+
+def test_config_indoor_5000(ctx):
+    p = synth.make_problem("indoor", 5000, 0.05, 0)
+    res, orc, stats, kind = _full_parity(ctx, p, k1=2000)
+    print("indoor-5000", stats, kind)
+    assert res.status == 0
+    assert synth.rotation_error_deg(p.R_gt, res.R) < 15 and synth.translation_error(p.t_gt, res.t) < 0.3
+
+
+def test_config_outdoor_2500(ctx):
+    p = synth.make_problem("outdoor", 2500, 0.20, 0)
+    res, orc, stats, kind = _full_parity(ctx, p, k1=1000)
+    print("outdoor-2500", stats, kind)
+    assert res.status == 0
+    assert synth.rotation_error_deg(p.R_gt, res.R) < 5 and synth.translation_error(p.t_gt, res.t) < 0.6
+
+
+@pytest.mark.parametrize("k2", [1, 3, 5])
+def test_k2_variants(ctx, k2):
+    p = synth.make_problem("cube", 800, 0.2, 40 + k2)
+    _full_parity(ctx, p, k1=300, k2=k2)
+
+
+def test_bitset_sc2_matches(ctx):
+    p = synth.make_problem("indoor", 3000, 0.05, 11)
+    _full_parity(ctx, p, k1=1500, flags=trg.FLAG_SC2_BITSET)
+
+
+def test_complete_graph_exactness(ctx):
+    # tau huge: G is complete, every SC^2 entry is N-2 (largest integer the FP8 GEMM accumulates)
+    p = synth.make_problem("cube", 5000, 0.1, 12)
+    prm = trg.default_params(1e6, 50, 0.1)
+    res = ctx.register(p.x, p.y, prm)
+    n = p.n
+    W = ctx.buffer(trg.BUF_SC2)[:n, :n]
+    assert (W[np.triu_indices(n, 1)] == n - 2).all()
+    P = ctx.buffer(trg.BUF_PIVOTS)
+    # all edges tie: the first 50 in (i, j) order
+    assert P[:, 0].tolist() == [0] * 50 and P[:, 1].tolist() == list(range(1, 51))
+    assert (ctx.buffer(trg.BUF_ROWSCORE) == (n - 1) * (n - 2)).all()
+    assert res.status == 0
+
+
+def test_no_edges_gives_no_hypothesis(ctx):
+    p = synth.make_problem("cube", 500, 0.1, 13)
+    res = ctx.register(p.x, p.y, trg.default_params(0.0, 100, 0.1))
+    assert res.status == trg.ERR_NO_HYPOTHESIS and res.n_pivots == 0
+    assert np.array_equal(res.R, np.eye(3, dtype=np.float32)) and not res.t.any()
+
+
+def test_fewer_edges_than_k1(ctx):
+    p = synth.make_problem("cube", 400, 0.1, 14, tau=0.02)
+    _full_parity(ctx, p, k1=8000)
+
+
+def test_duplicate_and_collinear_points(ctx):
+    p = synth.make_problem("cube", 300, 0.5, 15, sigma=0.0, tau=0.05)
+    x, y = p.x.copy(), p.y.copy()
+    inl = np.flatnonzero(p.inlier)
+    x[inl[1]] = x[inl[0]]; y[inl[1]] = y[inl[0]]                 # duplicate match
+    for k in range(2, 6):                                         # collinear inlier run
+        x[inl[k]] = x[inl[0]] + k * (x[inl[20]] - x[inl[0]]) / 10
+        y[inl[k]] = y[inl[0]] + k * (y[inl[20]] - y[inl[0]]) / 10
+    q = synth.Problem(x, y, p.R_gt, p.t_gt, p.inlier, 0.05, 0.05, 300, 15, 0.3, "cube", 15)
+    _full_parity(ctx, q, k1=300)
+
+
+def test_invalid_inputs(ctx):
+    p = synth.make_problem("cube", 100, 0.1, 16)
+    prm = trg.default_params(0.1, 10, 0.1)
+    assert ctx.register(p.x[:2], p.y[:2], prm).status == trg.ERR_TOO_FEW
+    bad = p.x.copy(); bad[5, 1] = np.nan
+    assert ctx.register(bad, p.y, prm).status == trg.ERR_NONFINITE
+    assert ctx.register(p.x, p.y, trg.default_params(-1.0, 10, 0.1)).status == trg.ERR_INVALID_ARG
+    assert ctx.register(p.x, p.y, trg.default_params(0.1, 0, 0.1)).status == trg.ERR_INVALID_ARG
+    assert ctx.register(p.x, p.y, trg.default_params(0.1, 10, 0.0)).status == trg.ERR_INVALID_ARG
+    big = synth.make_problem("cube", 5001, 0.1, 16)
+    assert ctx.register(big.x, big.y, prm).status == trg.ERR_INVALID_ARG
+    # the context still works afterwards
+    assert ctx.register(p.x, p.y, trg.default_params(0.3, 50, 0.1)).status in (0, trg.ERR_NO_HYPOTHESIS)
+
+
+def test_device_inputs_and_nonfinite_on_device(ctx):
+    import torch
+    p = synth.make_problem("indoor", 2000, 0.1, 17)
+    prm = trg.default_params(p.tau, 500, p.theta)
+    r_host = ctx.register(p.x, p.y, prm)
+    xd = torch.from_numpy(p.x).cuda()
+    yd = torch.from_numpy(p.y).cuda()
+    torch.cuda.synchronize()
+    r_dev = ctx.register(xd, yd, prm)
+    assert r_dev.status == r_host.status == 0
+    assert r_dev.hypothesis == r_host.hypothesis and np.array_equal(r_dev.R, r_host.R)
+    yd[7, 2] = float("inf")
+    torch.cuda.synchronize()
+    assert ctx.register(xd, yd, prm).status == trg.ERR_NONFINITE
+
+
+def test_deterministic_repeats(ctx):
+    p = synth.make_problem("indoor", 5000, 0.05, 18)
+    prm = trg.default_params(p.tau, 2000, p.theta)
+    first = ctx.register(p.x, p.y, prm)
+    IN0 = ctx.buffer(trg.BUF_INLIERS).copy()
+    W0 = ctx.buffer(trg.BUF_SC2).copy()
+    for _ in range(5):
+        r = ctx.register(p.x, p.y, prm)
+        assert r.hypothesis == first.hypothesis and np.array_equal(r.R, first.R)
+        assert np.array_equal(ctx.buffer(trg.BUF_INLIERS), IN0)
+    n = p.n
+    iu = np.triu_indices(n, 1)
+    assert np.array_equal(ctx.buffer(trg.BUF_SC2)[:n, :n][iu], W0[:n, :n][iu])
+
+
+def test_batched_equals_plain(ctx):
+    probs = [synth.make_problem(s, n, r, 50 + b) for b, (s, n, r) in
+             enumerate([("indoor", 1200, 0.1), ("outdoor", 900, 0.2), ("indoor", 3000, 0.05),
+                        ("cube", 1000, 0.1), ("outdoor", 2500, 0.15)])]
+    params = [trg.default_params(p.tau, p.k1, p.theta) for p in probs]
+    offs = np.cumsum([0] + [p.n for p in probs]).astype(np.int64)
+    xs = np.concatenate([p.x for p in probs])
+    ys = np.concatenate([p.y for p in probs])
+    out = ctx.register_batched(xs, ys, offs, params)
+    for p, prm, rb in zip(probs, params, out):
+        rp = ctx.register(p.x, p.y, prm)
+        assert rb.status == rp.status and rb.hypothesis == rp.hypothesis
+        assert np.array_equal(rb.R, rp.R) and np.array_equal(rb.t, rp.t)
+        assert rb.inlier_count == rp.inlier_count
+
+
+def test_stage_times_reported(ctx):
+    p = synth.make_problem("indoor", 5000, 0.05, 19)
+    prm = trg.default_params(p.tau, 2000, p.theta, flags=trg.FLAG_STAGE_TIMES)
+    ctx.register(p.x, p.y, prm)
+    st = ctx.stage_times()
+    assert list(st) == ["pack", "compat", "sc2", "topk", "pgs", "kabsch", "verify", "finalize"]
+    assert all(v >= 0 for v in st.values())
+    print(st)
