@@ -50,6 +50,41 @@ int turboreg_stage_times(turboreg_ctx* ctx, float* ms, int32_t max);
 /* Names of the stages reported by turboreg_stage_times. */
 const char* turboreg_stage_name(int32_t stage);
 
+/* Largest n accepted by turboreg_select_pivots_noalloc. */
+#define TURBOREG_NOALLOC_MAX_N 8192
+
+/* Pivot selection (top-K1 O2Graph edges, ties to the lowest (i, j)) on a
+ * caller-provided weight matrix, allocating nothing.  The paper has no
+ * counterpart to this entry point: it exists for callers that cannot call
+ * cudaMalloc, such as a plugin inside a host framework that owns all device
+ * memory through its own pool, or a real-time loop that forbids allocation
+ * after start-up (cudaMalloc may synchronise the device and take unbounded
+ * time).  Its scratch (histogram, per-row tie counts, candidate keys, control
+ * block: about 160 KB) is one fixed array in the library's device memory,
+ * loaded with the module and held by every GPU that loads the library until
+ * the process exits; nothing is allocated or freed by this call.
+ *
+ *  w_dev       device, uint16 [n][ldw] row-major, 16-byte aligned; entry (i, j)
+ *              for i < j < n is the O2Graph weight (an SC^2 count, 0..n-2; a
+ *              larger value is outside the contract).  Entries with j <= i or
+ *              j >= n are ignored.  ldw % 8 == 0 and ldw >= n rounded up to 8.
+ *  n           nodes, 1 .. TURBOREG_NOALLOC_MAX_N
+ *  k1          pivots wanted, 1 .. TURBOREG_K1_MAX
+ *  pivots_dev  device, int32 [k1][4] out: (i, j, weight, 0) in (weight desc,
+ *              i asc, j asc) order; rows past *n_pivots_dev are untouched
+ *  n_pivots_dev device, int32 out: min(k1, number of edges with weight > 0)
+ *  cuda_stream cudaStream_t to run on (NULL = legacy default stream)
+ *
+ * Asynchronous on cuda_stream; results are ready when the stream reaches
+ * them.  Returns INVALID_ARG (clear message on stderr for sizes beyond the
+ * fixed limits) or CUDA; OK otherwise.  Every call shares the one scratch
+ * array, which keeps the last call's contents (the call clears what must
+ * start at zero), so calls that overlap on the GPU race: serialise calls per
+ * device.  The first call on a device looks up the array's device address
+ * with that device current; make that first call before any stream capture. */
+int turboreg_select_pivots_noalloc(const uint16_t* w_dev, int32_t n, int32_t ldw, int32_t k1,
+                                   int32_t* pivots_dev, int32_t* n_pivots_dev, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

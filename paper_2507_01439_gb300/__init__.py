@@ -36,8 +36,9 @@ BUF_ADJ_BITS, BUF_ADJ_FP8, BUF_SC2, BUF_PIVOTS, BUF_CLIQUES, BUF_RT, BUF_INLIERS
 EXPORTED = (
     "turboreg_default_params", "turboreg_create", "turboreg_register", "turboreg_register_batched",
     "turboreg_destroy", "turboreg_status_string", "turboreg_debug_shape", "turboreg_debug_copy",
-    "turboreg_stage_times", "turboreg_stage_name",
+    "turboreg_stage_times", "turboreg_stage_name", "turboreg_select_pivots_noalloc",
 )
+TURBOREG_NOALLOC_MAX_N = 8192
 
 
 class turboreg_params(ctypes.Structure):
@@ -89,6 +90,8 @@ def load_library(path: str = LIB_PATH):
     lib.turboreg_stage_times.restype = ctypes.c_int
     lib.turboreg_stage_name.argtypes = [i32]
     lib.turboreg_stage_name.restype = ctypes.c_char_p
+    lib.turboreg_select_pivots_noalloc.argtypes = [P, i32, i32, i32, P, P, P]
+    lib.turboreg_select_pivots_noalloc.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -254,3 +257,12 @@ def turboreg_register_batched(ctx: TurboReg, src_cat, dst_cat, offsets, params) 
 
 def turboreg_destroy(ctx: TurboReg) -> None:
     ctx.close()
+
+
+def turboreg_select_pivots_noalloc(w_dev, n, ldw, k1, pivots_dev, n_pivots_dev, stream=None) -> int:
+    """Pivot selection on a device weight matrix without any allocation (see
+    include/turboreg_internal.h): w_dev uint16 [n, ldw] CUDA tensor, outputs
+    pivots_dev int32 [k1, 4] and n_pivots_dev int32 [1] CUDA tensors."""
+    st = ctypes.c_void_p(stream) if stream else None
+    return load_library().turboreg_select_pivots_noalloc(_ptr(w_dev), int(n), int(ldw), int(k1),
+                                                         _ptr(pivots_dev), _ptr(n_pivots_dev), st)

@@ -1,0 +1,133 @@
+// Pivot selection without any device allocation.
+//
+// Some callers cannot call cudaMalloc: a plugin that runs inside a host
+// framework which owns all device memory through its own pool (a stray
+// cudaMalloc breaks its accounting or fails outright), or a real-time loop
+// that forbids allocation after start-up because cudaMalloc may synchronise
+// the device and take unbounded time.  turboreg_select_pivots_noalloc gives
+// them the pivot-selection stage with every scratch buffer it needs placed in
+// one fixed array in the library's own device memory (kScratchBytes, loaded
+// with the module and held by every GPU that loads the library until the
+// process exits).  The caller passes the weight matrix and the output buffers;
+// nothing is allocated or freed, by this code or by any library it calls.
+//
+// The scratch is shared by every call: the histogram, the per-row tie counts
+// and the control block are cleared with cudaMemsetAsync at the start of each
+// call, and two calls whose work overlaps on the GPU (different streams, or
+// different host threads) race on it.  Serialise calls per device.
+//
+// In host code the name g_pivot_scratch only stands in for the array; its
+// device address comes from cudaGetSymbolAddress, taken once per device with
+// that device current, on the first call made on that device.  That first
+// call should therefore be made before any stream capture begins.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <mutex>
+
+#include "tr_common.cuh"
+#include "tr_problem.h"
+#include "turboreg_internal.h"
+
+namespace tr {
+
+namespace {
+
+constexpr int32_t kMaxN = TURBOREG_NOALLOC_MAX_N;
+constexpr int32_t kMaxK1 = TURBOREG_K1_MAX;
+
+// layout of the scratch array (each part 256-byte aligned)
+constexpr size_t align256(size_t b) { return (b + 255) / 256 * 256; }
+constexpr size_t kOffCtl = 0;
+constexpr size_t kOffHist = align256(sizeof(Ctl));
+constexpr size_t kOffRowcnt = kOffHist + align256(sizeof(uint32_t) * (kMaxN + 1));
+constexpr size_t kOffRowpref = kOffRowcnt + align256(sizeof(int32_t) * kMaxN);
+constexpr size_t kOffCand = kOffRowpref + align256(sizeof(int32_t) * kMaxN);
+constexpr size_t kScratchBytes = kOffCand + align256(sizeof(uint64_t) * kMaxK1);
+
+static __device__ __align__(256) uint8_t g_pivot_scratch[kScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+uint8_t* g_dev_scratch[kMaxDevices] = {};
+bool g_dev_ready[kMaxDevices] = {};
+
+// Device address of the scratch array on `device` (current); set up on first use.
+int scratch_for(int device, uint8_t** out)
+{
+    if (device < 0 || device >= kMaxDevices) return TURBOREG_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_dev_ready[device]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_pivot_scratch);
+        if (e != cudaSuccess || p == nullptr) {
+            std::fprintf(stderr, "turboreg: cudaGetSymbolAddress of the pivot scratch failed: %s\n",
+                         cudaGetErrorString(e));
+            return TURBOREG_ERR_CUDA;
+        }
+        e = topk_setup();
+        if (e != cudaSuccess) {
+            std::fprintf(stderr, "turboreg: pivot-selection set-up failed: %s\n", cudaGetErrorString(e));
+            return TURBOREG_ERR_CUDA;
+        }
+        g_dev_scratch[device] = static_cast<uint8_t*>(p);
+        g_dev_ready[device] = true;
+    }
+    *out = g_dev_scratch[device];
+    return TURBOREG_OK;
+}
+
+}  // namespace
+
+}  // namespace tr
+
+extern "C" int turboreg_select_pivots_noalloc(const uint16_t* w_dev, int32_t n, int32_t ldw, int32_t k1,
+                                              int32_t* pivots_dev, int32_t* n_pivots_dev, void* cuda_stream)
+{
+    using namespace tr;
+    if (!w_dev || !pivots_dev || !n_pivots_dev) return TURBOREG_ERR_INVALID_ARG;
+    if (n < 1 || k1 < 1) return TURBOREG_ERR_INVALID_ARG;
+    if (n > kMaxN || k1 > kMaxK1) {
+        std::fprintf(stderr,
+                     "turboreg_select_pivots_noalloc: n = %d or k1 = %d exceeds the fixed scratch limits "
+                     "(n <= %d, k1 <= %d)\n", n, k1, kMaxN, kMaxK1);
+        return TURBOREG_ERR_INVALID_ARG;
+    }
+    // rows are read with 16-byte loads of 8 weights: ldw covers n rounded up to 8
+    if (ldw < ((n + 7) / 8) * 8 || ldw % 8 != 0 || (reinterpret_cast<uintptr_t>(w_dev) & 15u) != 0)
+        return TURBOREG_ERR_INVALID_ARG;
+    int device = 0;
+    if (cudaGetDevice(&device) != cudaSuccess) return TURBOREG_ERR_CUDA;
+    uint8_t* scr = nullptr;
+    int rc = scratch_for(device, &scr);
+    if (rc != TURBOREG_OK) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+
+    ProbView v = {};
+    v.n = n;
+    v.n_pad = ldw;
+    v.k1 = k1;
+    v.w = const_cast<uint16_t*>(w_dev);
+    v.ctl = reinterpret_cast<Ctl*>(scr + kOffCtl);
+    v.hist = reinterpret_cast<uint32_t*>(scr + kOffHist);
+    v.rowcnt = reinterpret_cast<int32_t*>(scr + kOffRowcnt);
+    v.rowpref = reinterpret_cast<int32_t*>(scr + kOffRowpref);
+    v.cand = reinterpret_cast<uint64_t*>(scr + kOffCand);
+    v.piv = reinterpret_cast<int4*>(pivots_dev);
+
+    // the previous call's contents stay in the array: clear what must start at zero
+    cudaError_t e = cudaMemsetAsync(scr + kOffCtl, 0, sizeof(Ctl), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(v.hist, 0, sizeof(uint32_t) * (n + 1), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(v.rowcnt, 0, sizeof(int32_t) * n, s);
+    if (e != cudaSuccess) return TURBOREG_ERR_CUDA;
+    launch_topk(v, s);
+    e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(n_pivots_dev, &v.ctl->n_pivots, sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) {
+        std::fprintf(stderr, "turboreg_select_pivots_noalloc: %s\n", cudaGetErrorString(e));
+        return TURBOREG_ERR_CUDA;
+    }
+    return TURBOREG_OK;
+}
