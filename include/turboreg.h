@@ -62,6 +62,8 @@ typedef enum {
 #define TURBOREG_FLAG_SC2_BITSET 0x1u  /* SC^2 by bitset AND+popcount on CUDA cores
                                           instead of the tcgen05 FP8 GEMM (same integers) */
 #define TURBOREG_FLAG_STAGE_TIMES 0x2u /* record per-stage CUDA-event times (turboreg_stage_times) */
+#define TURBOREG_FLAG_NO_GRAPH 0x4u    /* launch the stages one by one instead of replaying the
+                                          captured CUDA graph of this problem shape */
 
 typedef struct {
     float tau;            /* compatibility threshold of Eq. 1, metres, >= 0 */

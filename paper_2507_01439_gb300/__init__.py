@@ -29,6 +29,7 @@ GRAPH_O2 = 0
 PROPOSAL_PLAIN, PROPOSAL_LEARNED = 0, 1
 FLAG_SC2_BITSET = 0x1
 FLAG_STAGE_TIMES = 0x2
+FLAG_NO_GRAPH = 0x4
 
 BUF_ADJ_BITS, BUF_ADJ_FP8, BUF_SC2, BUF_PIVOTS, BUF_CLIQUES, BUF_RT, BUF_INLIERS, BUF_ROWSCORE, BUF_DEGREE = range(1, 10)
 

@@ -34,6 +34,8 @@ inline int32_t round_up(int32_t a, int32_t b) { return (a + b - 1) / b * b; }
 struct Workspace {
     int32_t n_pad_max = 0;
     float* pts = nullptr;
+    float* pts8 = nullptr;
+    int32_t* fp64_list = nullptr;
     uint8_t* a8 = nullptr;
     uint32_t* bits = nullptr;
     uint16_t* w = nullptr;
@@ -69,6 +71,27 @@ struct turboreg_ctx {
     float stage_ms[kNumStages] = {};
     int32_t last_n = 0, last_npad = 0, last_k1 = 0, last_k2 = 0;
     bool have_times = false;
+    // captured per-problem pipelines, replayed with cudaGraphLaunch; only the
+    // pack node's input pointers change between calls
+    struct GraphSlot {
+        bool used = false;
+        int32_t n = 0, k1 = 0, k2 = 0;
+        float tau = 0.f, theta = 0.f, kappa = 0.f;
+        uint32_t flags = 0;
+        turboreg_result* res = nullptr;
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        cudaGraphNode_t pack_node = nullptr;
+        cudaKernelNodeParams pack_params = {};
+        tr::ProbView pv = {};
+        const float* src = nullptr;
+        const float* dst = nullptr;
+        void* args[3] = {};
+        uint64_t stamp = 0;
+    };
+    static constexpr int kGraphSlots = 8;
+    GraphSlot gslot[kGraphSlots];
+    uint64_t gclock = 0;
 };
 
 namespace {
@@ -90,7 +113,7 @@ cudaError_t dalloc(T** p, size_t count)
 
 void free_ws(Workspace& ws)
 {
-    void* ptrs[] = {ws.pts, ws.a8, ws.bits, ws.w, ws.rowscore, ws.deg, ws.hist, ws.rowcnt, ws.rowpref,
+    void* ptrs[] = {ws.pts, ws.pts8, ws.fp64_list, ws.a8, ws.bits, ws.w, ws.rowscore, ws.deg, ws.hist, ws.rowcnt, ws.rowpref,
                     ws.cand, ws.piv, ws.cliques, ws.rt, ws.inl, ws.ctl, ws.res, ws.in_src, ws.in_dst};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -106,6 +129,8 @@ int alloc_ws(Workspace& ws, int32_t max_n, int32_t max_batch)
     ws.n_pad_max = np;
     cudaError_t e = cudaSuccess;
     if (e == cudaSuccess) e = dalloc(&ws.pts, 6 * static_cast<size_t>(np));
+    if (e == cudaSuccess) e = dalloc(&ws.pts8, 8 * static_cast<size_t>(np));
+    if (e == cudaSuccess) e = dalloc(&ws.fp64_list, nh);
     if (e == cudaSuccess) e = dalloc(&ws.a8, n2);
     if (e == cudaSuccess) e = dalloc(&ws.bits, n2 / 32);
     if (e == cudaSuccess) e = dalloc(&ws.w, n2);
@@ -204,6 +229,8 @@ ProbView make_view(turboreg_ctx* c, int32_t n, const turboreg_params* p, turbore
     v.theta = p->inlier_thresh;
     v.kappa_fp64 = p->kappa_fp64 > 0.f ? p->kappa_fp64 : 100.f;
     v.pts = ws.pts;
+    v.pts8 = ws.pts8;
+    v.fp64_list = ws.fp64_list;
     v.a8 = ws.a8;
     v.bits = ws.bits;
     v.w = ws.w;
@@ -234,25 +261,26 @@ int enqueue_problem(turboreg_ctx* c, const float* dsrc, const float* ddst, int32
         if (rc != TURBOREG_OK) return rc;
     }
     cudaStream_t s = c->stream;
-    if (timed) TR_CHECK(cudaEventRecord(c->ev[0], s));
+    if (timed) TR_CHECK(cudaEventRecordWithFlags(c->ev[0], s, cudaEventRecordExternal));
     TR_CHECK(cudaMemsetAsync(c->ws.ctl, 0, sizeof(Ctl), s));
     launch_pack(v, dsrc, ddst, s);
-    if (timed) TR_CHECK(cudaEventRecord(c->ev[1], s));
+    if (timed) TR_CHECK(cudaEventRecordWithFlags(c->ev[1], s, cudaEventRecordExternal));
     launch_compat(v, s);
-    if (timed) TR_CHECK(cudaEventRecord(c->ev[2], s));
+    if (timed) TR_CHECK(cudaEventRecordWithFlags(c->ev[2], s, cudaEventRecordExternal));
     if (bitset) launch_sc2_bitset(v, s);
-    else launch_sc2_tcgen05(v, c->tmA, c->tmB, s);
-    if (timed) TR_CHECK(cudaEventRecord(c->ev[3], s));
-    launch_topk(v, s);
-    if (timed) TR_CHECK(cudaEventRecord(c->ev[4], s));
+    else launch_sc2_tcgen05(v, c->tmA, c->tmB, s);   // also builds the weight histogram
+    if (timed) TR_CHECK(cudaEventRecordWithFlags(c->ev[3], s, cudaEventRecordExternal));
+    if (bitset) launch_topk(v, s);
+    else launch_topk_after_hist(v, s);
+    if (timed) TR_CHECK(cudaEventRecordWithFlags(c->ev[4], s, cudaEventRecordExternal));
     launch_pgs(v, s);
-    if (timed) TR_CHECK(cudaEventRecord(c->ev[5], s));
+    if (timed) TR_CHECK(cudaEventRecordWithFlags(c->ev[5], s, cudaEventRecordExternal));
     launch_kabsch(v, s);
-    if (timed) TR_CHECK(cudaEventRecord(c->ev[6], s));
+    if (timed) TR_CHECK(cudaEventRecordWithFlags(c->ev[6], s, cudaEventRecordExternal));
     launch_verify(v, s);
-    if (timed) TR_CHECK(cudaEventRecord(c->ev[7], s));
+    if (timed) TR_CHECK(cudaEventRecordWithFlags(c->ev[7], s, cudaEventRecordExternal));
     launch_finalize(v, s);
-    if (timed) TR_CHECK(cudaEventRecord(c->ev[8], s));
+    if (timed) TR_CHECK(cudaEventRecordWithFlags(c->ev[8], s, cudaEventRecordExternal));
     TR_CHECK(cudaGetLastError());
     c->last_n = n;
     c->last_npad = v.n_pad;
@@ -265,7 +293,106 @@ int enqueue_problem(turboreg_ctx* c, const float* dsrc, const float* ddst, int32
 int collect_times(turboreg_ctx* c)
 {
     if (!c->have_times) return TURBOREG_OK;
-    for (int k = 0; k < kNumStages; ++k) TR_CHECK(cudaEventElapsedTime(&c->stage_ms[k], c->ev[k], c->ev[k + 1]));
+    for (int k = 0; k < kNumStages; ++k) {
+        if (cudaEventElapsedTime(&c->stage_ms[k], c->ev[k], c->ev[k + 1]) != cudaSuccess) {
+            cudaGetLastError();   // not fatal: report the stage as unmeasured
+            c->stage_ms[k] = -1.f;
+        }
+    }
+    return TURBOREG_OK;
+}
+
+void drop_slot(turboreg_ctx::GraphSlot& g)
+{
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (g.graph) cudaGraphDestroy(g.graph);
+    g = turboreg_ctx::GraphSlot();
+}
+
+bool slot_matches(const turboreg_ctx::GraphSlot& g, int32_t n, const turboreg_params* p, turboreg_result* res)
+{
+    return g.used && g.n == n && g.k1 == p->k1 && g.k2 == p->k2 && g.tau == p->tau && g.theta == p->inlier_thresh &&
+           g.kappa == p->kappa_fp64 && g.flags == p->flags && g.res == res;
+}
+
+// Capture the pipeline for this shape once, then replay it; the pack node's
+// (src, dst) arguments are patched in the instantiated graph on every call.
+int run_problem(turboreg_ctx* c, const float* dsrc, const float* ddst, int32_t n, const turboreg_params* p,
+                turboreg_result* res_dev)
+{
+    if (p->flags & TURBOREG_FLAG_NO_GRAPH) return enqueue_problem(c, dsrc, ddst, n, p, res_dev);
+    turboreg_ctx::GraphSlot* g = nullptr;
+    for (auto& sl : c->gslot)
+        if (slot_matches(sl, n, p, res_dev)) g = &sl;
+    if (!g) {
+        g = &c->gslot[0];
+        for (auto& sl : c->gslot) {
+            if (!sl.used) { g = &sl; break; }
+            if (sl.stamp < g->stamp) g = &sl;
+        }
+        drop_slot(*g);
+        TR_CHECK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+        const int rc = enqueue_problem(c, dsrc, ddst, n, p, res_dev);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+        if (rc != TURBOREG_OK || e != cudaSuccess || !graph) {
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+            std::fprintf(stderr, "turboreg: graph capture failed: %s\n", cudaGetErrorString(e));
+            return rc != TURBOREG_OK ? rc : TURBOREG_ERR_CUDA;
+        }
+        size_t cnt = 0;
+        TR_CHECK(cudaGraphGetNodes(graph, nullptr, &cnt));
+        cudaGraphNode_t nodes[64];
+        if (cnt > 64) {
+            cudaGraphDestroy(graph);
+            return TURBOREG_ERR_CUDA;
+        }
+        TR_CHECK(cudaGraphGetNodes(graph, nodes, &cnt));
+        for (size_t k = 0; k < cnt; ++k) {
+            cudaGraphNodeType ty;
+            TR_CHECK(cudaGraphNodeGetType(nodes[k], &ty));
+            if (ty != cudaGraphNodeTypeKernel) continue;
+            cudaKernelNodeParams kp;
+            TR_CHECK(cudaGraphKernelNodeGetParams(nodes[k], &kp));
+            if (kp.func == pack_kernel_func()) {
+                g->pack_node = nodes[k];
+                g->pack_params = kp;
+            }
+        }
+        if (!g->pack_node) {
+            cudaGraphDestroy(graph);
+            return TURBOREG_ERR_CUDA;
+        }
+        g->graph = graph;
+        if (cudaGraphInstantiate(&g->exec, graph, 0) != cudaSuccess) {
+            cudaGetLastError();
+            drop_slot(*g);
+            return TURBOREG_ERR_CUDA;
+        }
+        g->used = true;
+        g->n = n; g->k1 = p->k1; g->k2 = p->k2;
+        g->tau = p->tau; g->theta = p->inlier_thresh; g->kappa = p->kappa_fp64;
+        g->flags = p->flags;
+        g->res = res_dev;
+        g->pv = make_view(c, n, p, res_dev);
+    }
+    g->stamp = ++c->gclock;
+    g->src = dsrc;
+    g->dst = ddst;
+    g->args[0] = &g->pv;
+    g->args[1] = &g->src;
+    g->args[2] = &g->dst;
+    cudaKernelNodeParams kp = g->pack_params;
+    kp.kernelParams = g->args;
+    kp.extra = nullptr;
+    TR_CHECK(cudaGraphExecKernelNodeSetParams(g->exec, g->pack_node, &kp));
+    TR_CHECK(cudaGraphLaunch(g->exec, c->stream));
+    c->last_n = n;
+    c->last_npad = g->pv.n_pad;
+    c->last_k1 = p->k1;
+    c->last_k2 = p->k2;
+    c->have_times = (p->flags & TURBOREG_FLAG_STAGE_TIMES) != 0;
     return TURBOREG_OK;
 }
 
@@ -371,6 +498,7 @@ void turboreg_destroy(turboreg_ctx* c)
     if (!c) return;
     cudaSetDevice(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
+    for (auto& sl : c->gslot) drop_slot(sl);
     for (int k = 0; k <= kNumStages; ++k)
         if (c->ev[k]) cudaEventDestroy(c->ev[k]);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
@@ -420,7 +548,7 @@ int turboreg_register(turboreg_ctx* c, const float* src, const float* dst, int32
         out->status = rc;
         return rc;
     }
-    rc = enqueue_problem(c, s_in, d_in, n, p, c->ws.res);
+    rc = run_problem(c, s_in, d_in, n, p, c->ws.res);
     if (rc != TURBOREG_OK) return rc;
     TR_CHECK(cudaMemcpyAsync(c->host_res, c->ws.res, sizeof(turboreg_result), cudaMemcpyDeviceToHost, c->stream));
     TR_CHECK(cudaStreamSynchronize(c->stream));

@@ -1,23 +1,33 @@
 // Stage 0 (pack) and stage 1 (compatibility graph, Eq. 1).
 //
-// pack:   [N][3] x, y (host-order float32, any 4-byte alignment) -> structure
-//         of arrays pts[6][n_pad] with zero padding; flags NaN/Inf; clears the
-//         per-call accumulators.
+// pack:   [N][3] x, y (float32, any 4-byte alignment) -> points in two device
+//         layouts with zero padding: structure of arrays pts[6][n_pad] and
+//         32-byte records pts8[n_pad] = (x0,x1,x2,y0 | y1,y2,0,0); flags
+//         NaN/Inf; clears the per-call accumulators.
 // compat: G_ij = [ | ||x_i - x_j|| - ||y_i - y_j|| | <= tau ], i != j, G_ii = 0
 //         (Eq. 1; zero diagonal because App. B equates G^_ij with the number
-//         of triangles on edge (i,j)).  Written twice: as FP8 E4M3 0/1 bytes
-//         (the operand of the SC^2 tensor-core GEMM) and as a row bitset
-//         (the operand of clique search), plus the degree of every node.
+//         of triangles on edge (i,j)).  Written as a row bitset (operand of the
+//         clique search), as FP8 E4M3 0/1 bytes (operand of the SC^2 GEMM) and
+//         as node degrees.
 //
-// Exactness: the decision is taken in FP32 and, for the few pairs whose FP32
-// |dX - dY| lies within a rounding guard band g of tau, retaken in FP64 with
-// the fixed operation order ((dx*dx + dy*dy) + dz*dz), correctly rounded
-// sqrt.  FP32 error analysis (u = 2^-24): each distance carries relative
-// error <= 3.5u, so |diff32 - diff_exact| <= 4.5u (dX + dY); the FP64
-// evaluation is within 4.5 * 2^-53 (dX + dY) of exact.  With
-// g = 2^-21 (dX + dY) + 1e-18 (absolute slack for underflowed squares) any
-// pair outside the band is decided identically in FP32 and FP64, so the
-// whole matrix equals the FP64 evaluation bit for bit.
+// Work decomposition: 128 x 128 tiles (I, J) with I <= J only.  A block
+// computes its tile once and writes it twice (rows i of tile (I, J) and,
+// transposed, rows j of tile (J, I)): G is symmetric bit for bit because
+// x_j - x_i = -(x_i - x_j) exactly in IEEE arithmetic.  The 128 row points
+// of a tile are staged in shared memory with one 1-D TMA bulk copy; every
+// thread keeps 4 column points in registers.
+//
+// Exactness: the decision is taken in FP32 (sqrt.approx) and retaken in FP64
+// with the fixed operation order ((dx*dx + dy*dy) + dz*dz), correctly
+// rounded sqrt, for the few pairs whose FP32 |dX - dY| lies within a guard
+// band g of tau.  Error bound (u = 2^-24): the squared distances carry
+// relative error <= 5u, the approximate square root adds <= e_s (measured
+// <= 2u on sm_103a; the band assumes 4u), so each distance is within
+// (2.5u + 4u) relative and |diff32 - diff_exact| <= 7.5u (dX + dY) + u diff.
+// The band g = 2^-20 (dX + dY) + 1e-18 (16u, about twice the bound, plus an
+// absolute slack for underflowed squares) therefore contains every pair whose
+// FP32 and FP64 decisions could differ, and the matrix equals the FP64
+// evaluation bit for bit.
 #include "tr_common.cuh"
 #include "tr_problem.h"
 
@@ -25,8 +35,8 @@ namespace tr {
 
 namespace {
 
-constexpr int kRows = 64;    // rows (i) per block, staged in shared memory by TMA
-constexpr int kCols = 256;   // columns (j) per block, one per thread
+constexpr int kT = 128;          // tile edge
+constexpr int kThreads = 256;    // 8 warps x 16 rows; each lane 4 columns
 
 __global__ void __launch_bounds__(256) pack_kernel(ProbView v, const float* __restrict__ src,
                                                    const float* __restrict__ dst)
@@ -44,6 +54,9 @@ __global__ void __launch_bounds__(256) pack_kernel(ProbView v, const float* __re
         }
 #pragma unroll
         for (int c = 0; c < 6; ++c) v.pts[(size_t)c * v.n_pad + k] = a[c];
+        float4* p8 = reinterpret_cast<float4*>(v.pts8 + (size_t)k * 8);
+        p8[0] = make_float4(a[0], a[1], a[2], a[3]);
+        p8[1] = make_float4(a[4], a[5], 0.f, 0.f);
         v.rowscore[k] = 0;
         v.deg[k] = 0;
         v.rowcnt[k] = 0;
@@ -52,96 +65,156 @@ __global__ void __launch_bounds__(256) pack_kernel(ProbView v, const float* __re
     if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(&v.ctl->err, TR_ERR_NONFINITE);
 }
 
-__device__ __forceinline__ bool compat_pair(const float xi[6], const float xj[6], float tau)
+__device__ __forceinline__ float sqrt_approx(float x)
 {
-    // FP32 evaluation, no contraction (explicit round-to-nearest intrinsics)
-    const float ax = __fsub_rn(xi[0], xj[0]), ay = __fsub_rn(xi[1], xj[1]), az = __fsub_rn(xi[2], xj[2]);
-    const float bx = __fsub_rn(xi[3], xj[3]), by = __fsub_rn(xi[4], xj[4]), bz = __fsub_rn(xi[5], xj[5]);
-    const float sX = __fadd_rn(__fadd_rn(__fmul_rn(ax, ax), __fmul_rn(ay, ay)), __fmul_rn(az, az));
-    const float sY = __fadd_rn(__fadd_rn(__fmul_rn(bx, bx), __fmul_rn(by, by)), __fmul_rn(bz, bz));
-    const float dX = __fsqrt_rn(sX), dY = __fsqrt_rn(sY);
-    const float diff = fabsf(__fsub_rn(dX, dY));
-    const float g = __fmaf_rn(__fadd_rn(dX, dY), 4.76837158203125e-07f, 1e-18f);  // 2^-21 (dX+dY) + slack
-    if (fabsf(__fsub_rn(diff, tau)) > g) return diff <= tau;   // false for NaN/Inf -> FP64 path
-    // FP64 re-evaluation in the reference operation order
-    const double dx = __dsub_rn((double)xi[0], (double)xj[0]);
-    const double dy = __dsub_rn((double)xi[1], (double)xj[1]);
-    const double dz = __dsub_rn((double)xi[2], (double)xj[2]);
-    const double ex = __dsub_rn((double)xi[3], (double)xj[3]);
-    const double ey = __dsub_rn((double)xi[4], (double)xj[4]);
-    const double ez = __dsub_rn((double)xi[5], (double)xj[5]);
+    float r;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+__device__ __noinline__ bool compat_fp64(float xi0, float xi1, float xi2, float yi0, float yi1, float yi2,
+                                         float xj0, float xj1, float xj2, float yj0, float yj1, float yj2,
+                                         float tau)
+{
+    const double dx = __dsub_rn((double)xi0, (double)xj0);
+    const double dy = __dsub_rn((double)xi1, (double)xj1);
+    const double dz = __dsub_rn((double)xi2, (double)xj2);
+    const double ex = __dsub_rn((double)yi0, (double)yj0);
+    const double ey = __dsub_rn((double)yi1, (double)yj1);
+    const double ez = __dsub_rn((double)yi2, (double)yj2);
     double s = __dmul_rn(dx, dx);
     s = __dadd_rn(s, __dmul_rn(dy, dy));
     s = __dadd_rn(s, __dmul_rn(dz, dz));
     double t = __dmul_rn(ex, ex);
     t = __dadd_rn(t, __dmul_rn(ey, ey));
     t = __dadd_rn(t, __dmul_rn(ez, ez));
-    const double DX = __dsqrt_rn(s), DY = __dsqrt_rn(t);
-    return fabs(__dsub_rn(DX, DY)) <= (double)tau;
+    return fabs(__dsub_rn(__dsqrt_rn(s), __dsqrt_rn(t))) <= (double)tau;
 }
 
-// Block = 256 threads = 8 warps; covers rows [i0, i0+64) x cols [j0, j0+256).
-// The 64 row points are staged in shared memory with 1-D TMA bulk copies;
-// each thread keeps its column point in registers.
-__global__ void __launch_bounds__(256) compat_kernel(ProbView v)
+__device__ __forceinline__ bool compat_pair(const float (&xi)[6], const float (&xj)[6], float tau)
 {
-    __shared__ __align__(128) float sx[6][kRows];
-    __shared__ __align__(16) uint8_t tile[kRows][kCols];
-    __shared__ int sdeg[kRows];
+    const float ax = xi[0] - xj[0], ay = xi[1] - xj[1], az = xi[2] - xj[2];
+    const float bx = xi[3] - xj[3], by = xi[4] - xj[4], bz = xi[5] - xj[5];
+    const float sX = fmaf(az, az, fmaf(ay, ay, ax * ax));
+    const float sY = fmaf(bz, bz, fmaf(by, by, bx * bx));
+    const float dX = sqrt_approx(sX), dY = sqrt_approx(sY);
+    const float diff = fabsf(dX - dY);
+    const float g = fmaf(dX + dY, 9.5367431640625e-07f, 1e-18f);   // 2^-20 (dX + dY) + slack
+    if (fabsf(diff - tau) > g) return diff <= tau;                 // NaN/Inf fall through
+    return compat_fp64(xi[0], xi[1], xi[2], xi[3], xi[4], xi[5], xj[0], xj[1], xj[2], xj[3], xj[4], xj[5], tau);
+}
+
+// 4 bits -> 4 bytes of FP8 E4M3 (0x38 = 1.0 for a set bit, 0x00 otherwise)
+__device__ __forceinline__ uint32_t nibble_to_fp8(uint32_t nib)
+{
+    return ((nib * 0x00204081u) & 0x01010101u) * 0x38u;
+}
+
+__device__ __forceinline__ uint4 bits16_to_fp8(uint32_t b16)
+{
+    return make_uint4(nibble_to_fp8(b16 & 0xF), nibble_to_fp8((b16 >> 4) & 0xF), nibble_to_fp8((b16 >> 8) & 0xF),
+                      nibble_to_fp8((b16 >> 12) & 0xF));
+}
+
+__global__ void __launch_bounds__(kThreads) compat_kernel(ProbView v)
+{
+    __shared__ __align__(128) float4 srow[kT][2];     // row points (x0,x1,x2,y0 | y1,y2,-,-)
+    __shared__ uint16_t colpart[8][kT];               // per warp: 16-row mask of each column
     __shared__ __align__(8) uint64_t bar;
 
-    const int j0 = blockIdx.x * kCols;
-    const int i0 = blockIdx.y * kRows;
+    // triangular tile index -> (I, J), I <= J
+    const int t = blockIdx.x;
+    int J = static_cast<int>((sqrtf(8.0f * t + 1.0f) - 1.0f) * 0.5f);
+    while (J * (J + 1) / 2 > t) --J;
+    while ((J + 1) * (J + 2) / 2 <= t) ++J;
+    const int I = t - J * (J + 1) / 2;
+    const int i0 = I * kT, j0 = J * kT;
+    const bool diag = (I == J);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
     if (threadIdx.x == 0) {
         mbar_init(&bar, 1);
         fence_mbar_init();
     }
-    if (threadIdx.x < kRows) sdeg[threadIdx.x] = 0;
     __syncthreads();
     if (threadIdx.x == 0) {
-        mbar_arrive_expect_tx(&bar, 6 * kRows * sizeof(float));
-#pragma unroll
-        for (int c = 0; c < 6; ++c)
-            bulk_g2s(&sx[c][0], v.pts + (size_t)c * v.n_pad + i0, kRows * sizeof(float), &bar);
+        mbar_arrive_expect_tx(&bar, kT * 32);
+        bulk_g2s(&srow[0][0], v.pts8 + (size_t)i0 * 8, kT * 32, &bar);
     }
-    const int j = j0 + threadIdx.x;
-    float xj[6];
+    // this thread's 4 column points: j = j0 + lane + 32 q
+    float xj[4][6];
+    bool jok[4];
 #pragma unroll
-    for (int c = 0; c < 6; ++c) xj[c] = v.pts[(size_t)c * v.n_pad + j];
-    const bool jok = j < v.n;
+    for (int q = 0; q < 4; ++q) {
+        const int j = j0 + lane + 32 * q;
+        const float4* p = reinterpret_cast<const float4*>(v.pts8 + (size_t)j * 8);
+        const float4 a = p[0], b = p[1];
+        xj[q][0] = a.x; xj[q][1] = a.y; xj[q][2] = a.z; xj[q][3] = a.w; xj[q][4] = b.x; xj[q][5] = b.y;
+        jok[q] = j < v.n;
+    }
     if (!mbar_wait(&bar, 0)) {
         if (threadIdx.x == 0) atomicOr(&v.ctl->err, TR_ERR_TIMEOUT);
         return;
     }
     const float tau = v.tau;
-    for (int r = 0; r < kRows; ++r) {
-        const int i = i0 + r;
-        bool a = false;
-        if (jok && i < v.n && i != j) {
-            float xi[6];
+    uint32_t cmask[4] = {0u, 0u, 0u, 0u};   // bit r: G(i0 + 16 warp + r, j_q)
+#pragma unroll 2
+    for (int r = 0; r < 16; ++r) {
+        const int rr = warp * 16 + r;
+        const int i = i0 + rr;
+        const float4 pa = srow[rr][0], pb = srow[rr][1];
+        const float xi[6] = {pa.x, pa.y, pa.z, pa.w, pb.x, pb.y};
+        uint32_t word[4];
+        const bool iok = i < v.n;
 #pragma unroll
-            for (int c = 0; c < 6; ++c) xi[c] = sx[c][r];
-            a = compat_pair(xi, xj, tau);
+        for (int q = 0; q < 4; ++q) {
+            const int j = j0 + lane + 32 * q;
+            const bool a = iok && jok[q] && (i != j) && compat_pair(xi, xj[q], tau);
+            cmask[q] |= static_cast<uint32_t>(a) << r;
+            word[q] = __ballot_sync(0xffffffffu, a);
         }
-        tile[r][threadIdx.x] = a ? 0x38 : 0x00;   // FP8 E4M3: 0x38 = 1.0
-        const unsigned bal = __ballot_sync(0xffffffffu, a);
+        // direct row i: 4 bitset words (16 B) and 128 FP8 bytes (lanes 0..7, 16 B each)
         if (lane == 0) {
-            v.bits[(size_t)i * v.ldb + (j0 >> 5) + warp] = bal;
-            if (bal) atomicAdd(&sdeg[r], __popc(bal));
+            *reinterpret_cast<uint4*>(v.bits + (size_t)i * v.ldb + (j0 >> 5)) =
+                make_uint4(word[0], word[1], word[2], word[3]);
+            const int d = __popc(word[0]) + __popc(word[1]) + __popc(word[2]) + __popc(word[3]);
+            if (d) atomicAdd(&v.deg[i], d);
+        }
+        if (lane < 8) {
+            const uint32_t w = (lane >> 1) == 0 ? word[0] : (lane >> 1) == 1 ? word[1] : (lane >> 1) == 2 ? word[2] : word[3];
+            *reinterpret_cast<uint4*>(v.a8 + (size_t)i * v.n_pad + j0 + lane * 16) =
+                bits16_to_fp8((w >> ((lane & 1) * 16)) & 0xFFFFu);
         }
     }
+    if (diag) return;
+    // mirrored tile: row j gets bits of rows i0 .. i0+127
+#pragma unroll
+    for (int q = 0; q < 4; ++q) colpart[warp][lane + 32 * q] = static_cast<uint16_t>(cmask[q]);
     __syncthreads();
-    for (int q = threadIdx.x; q < kRows * kCols / 16; q += blockDim.x) {
-        const int r = q / (kCols / 16), c16 = q % (kCols / 16);
-        *reinterpret_cast<uint4*>(v.a8 + (size_t)(i0 + r) * v.n_pad + j0 + c16 * 16) =
-            *reinterpret_cast<const uint4*>(&tile[r][c16 * 16]);
+    const int c = threadIdx.x & (kT - 1);   // column within the tile
+    const int half = threadIdx.x >> 7;      // two threads per column
+    const int j = j0 + c;
+    uint32_t w4[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        w4[k] = static_cast<uint32_t>(colpart[2 * k][c]) | (static_cast<uint32_t>(colpart[2 * k + 1][c]) << 16);
+    if (half == 0) {
+        *reinterpret_cast<uint4*>(v.bits + (size_t)j * v.ldb + (i0 >> 5)) = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+        const int d = __popc(w4[0]) + __popc(w4[1]) + __popc(w4[2]) + __popc(w4[3]);
+        if (d) atomicAdd(&v.deg[j], d);
     }
-    if (threadIdx.x < kRows && sdeg[threadIdx.x]) atomicAdd(&v.deg[i0 + threadIdx.x], sdeg[threadIdx.x]);
+    uint8_t* dstrow = v.a8 + (size_t)j * v.n_pad + i0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int seg = half * 4 + k;          // 16-byte segment 0..7 of the 128-byte row
+        const uint32_t w = w4[seg >> 1];
+        *reinterpret_cast<uint4*>(dstrow + seg * 16) = bits16_to_fp8((w >> ((seg & 1) * 16)) & 0xFFFFu);
+    }
 }
 
 }  // namespace
+
+const void* pack_kernel_func() { return reinterpret_cast<const void*>(&pack_kernel); }
 
 void launch_pack(const ProbView& v, const float* src, const float* dst, cudaStream_t s)
 {
@@ -151,8 +224,8 @@ void launch_pack(const ProbView& v, const float* src, const float* dst, cudaStre
 
 void launch_compat(const ProbView& v, cudaStream_t s)
 {
-    dim3 grid(v.n_pad / kCols, v.n_pad / kRows);
-    compat_kernel<<<grid, 256, 0, s>>>(v);
+    const int T = v.n_pad / kT;
+    compat_kernel<<<T * (T + 1) / 2, kThreads, 0, s>>>(v);
 }
 
 }  // namespace tr

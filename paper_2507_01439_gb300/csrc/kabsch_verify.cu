@@ -140,6 +140,19 @@ __device__ void kabsch3(const T p[3][3], const T q[3][3], KabschOut<T>& o)
         o.t[r] = cy[r] - (o.R[r * 3 + 0] * cx[0] + o.R[r * 3 + 1] * cx[1] + o.R[r * 3 + 2] * cx[2]);
 }
 
+__device__ __forceinline__ void load_clique(const ProbView& v, const int4 cl, float p[3][3], float q[3][3])
+{
+    const int idx[3] = {cl.x, cl.y, cl.z};
+    for (int a = 0; a < 3; ++a) {
+        const float4* r = reinterpret_cast<const float4*>(v.pts8 + (size_t)idx[a] * 8);
+        const float4 u = r[0], w = r[1];
+        p[a][0] = u.x; p[a][1] = u.y; p[a][2] = u.z;
+        q[a][0] = u.w; q[a][1] = w.x; q[a][2] = w.y;
+    }
+}
+
+// Phase 1: FP32 closed form for every hypothesis; cliques whose kappa exceeds
+// the bound (or whose FP32 frames are undefined) go to a compact list.
 __global__ void __launch_bounds__(128) kabsch_kernel(ProbView v)
 {
     const int h = blockIdx.x * blockDim.x + threadIdx.x;
@@ -149,81 +162,109 @@ __global__ void __launch_bounds__(128) kabsch_kernel(ProbView v)
     float* out = v.rt + (size_t)h * 16;
     const int4 cl = v.cliques[h];
     uint32_t flags = 0;
+    for (int r = 0; r < 13; ++r) out[r] = 0.f;
     if (cl.w) {
-        const int idx[3] = {cl.x, cl.y, cl.z};
         float p[3][3], q[3][3];
-        for (int a = 0; a < 3; ++a)
-            for (int c = 0; c < 3; ++c) {
-                p[a][c] = v.pts[(size_t)c * v.n_pad + idx[a]];
-                q[a][c] = v.pts[(size_t)(c + 3) * v.n_pad + idx[a]];
-            }
+        load_clique(v, cl, p, q);
         KabschOut<float> o;
         kabsch3<float>(p, q, o);
-        const float kb = v.kappa_fp64;
-        if (o.ok && o.kappa <= kb) {
+        if (o.ok && o.kappa <= v.kappa_fp64) {
             for (int r = 0; r < 9; ++r) out[r] = o.R[r];
             for (int r = 0; r < 3; ++r) out[9 + r] = o.t[r];
             out[12] = o.kappa;
             flags = 1u;
         } else {
-            double pd[3][3], qd[3][3];
-            for (int a = 0; a < 3; ++a)
-                for (int c = 0; c < 3; ++c) {
-                    pd[a][c] = p[a][c];
-                    qd[a][c] = q[a][c];
-                }
-            KabschOut<double> od;
-            kabsch3<double>(pd, qd, od);
-            const bool valid = od.ok && od.s1 > 0.0 && od.s2 > 1e-12 * od.s1;
-            for (int r = 0; r < 9; ++r) out[r] = static_cast<float>(od.R[r]);
-            for (int r = 0; r < 3; ++r) out[9 + r] = static_cast<float>(od.t[r]);
-            out[12] = static_cast<float>(od.kappa);
-            flags = (valid ? 1u : 0u) | 2u;
+            const uint32_t slot = atomicAdd(&v.ctl->fp64_slot, 1u);
+            v.fp64_list[slot] = h;
+            flags = 2u;   // pending FP64
         }
-    }
-    if (!(flags & 1u)) {
-        for (int r = 0; r < 13; ++r) out[r] = 0.f;
     }
     out[13] = __int_as_float(static_cast<int>(flags));
 }
 
-constexpr int kVerHyp = 256;   // hypotheses per block (one per thread)
-constexpr int kVerPts = 256;   // correspondences per block, staged in shared memory
-
-__global__ void __launch_bounds__(kVerHyp) verify_kernel(ProbView v)
+// Phase 2: the same closed form in FP64 for the listed hypotheses only, so the
+// slow FP64 pipe runs on dense warps instead of on every warp that holds one.
+__global__ void __launch_bounds__(32) kabsch_fp64_kernel(ProbView v)
 {
-    __shared__ __align__(16) float sp[6][kVerPts];
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= static_cast<int>(v.ctl->fp64_slot)) return;
+    const int h = v.fp64_list[k];
+    float* out = v.rt + (size_t)h * 16;
+    float p[3][3], q[3][3];
+    load_clique(v, v.cliques[h], p, q);
+    double pd[3][3], qd[3][3];
+    for (int a = 0; a < 3; ++a)
+        for (int c = 0; c < 3; ++c) {
+            pd[a][c] = p[a][c];
+            qd[a][c] = q[a][c];
+        }
+    KabschOut<double> od;
+    kabsch3<double>(pd, qd, od);
+    const bool valid = od.ok && od.s1 > 0.0 && od.s2 > 1e-12 * od.s1;
+    if (valid) {
+        for (int r = 0; r < 9; ++r) out[r] = static_cast<float>(od.R[r]);
+        for (int r = 0; r < 3; ++r) out[9 + r] = static_cast<float>(od.t[r]);
+    }
+    out[12] = static_cast<float>(od.kappa);
+    out[13] = __int_as_float(static_cast<int>((valid ? 1u : 0u) | 2u));
+}
+
+// Verification: each thread owns kVH hypotheses (R, t in registers); a block
+// stages kVPts correspondences as 32-byte records in shared memory and every
+// point read (two 16-byte broadcasts) feeds kVH residuals.
+constexpr int kVH = 4;
+constexpr int kVThreads = 64;
+constexpr int kVHyp = kVH * kVThreads;   // hypotheses per block
+constexpr int kVPts = 128;               // correspondences per block
+
+__global__ void __launch_bounds__(kVThreads) verify_kernel(ProbView v)
+{
+    __shared__ __align__(16) float4 sp[kVPts][2];
     const int nh = v.ctl->n_pivots * v.k2;
-    const int h0 = blockIdx.x * kVerHyp;
+    const int h0 = blockIdx.x * kVHyp;
     if (h0 >= nh) return;
-    const int k0 = blockIdx.y * kVerPts;
-    const int cnt = min(kVerPts, v.n - k0);
-    for (int q = threadIdx.x; q < kVerPts; q += blockDim.x) {
+    const int k0 = blockIdx.y * kVPts;
+    const int cnt = min(kVPts, v.n - k0);
+    const float4* src = reinterpret_cast<const float4*>(v.pts8 + (size_t)k0 * 8);
+    for (int q = threadIdx.x; q < 2 * kVPts; q += kVThreads) (&sp[0][0])[q] = src[q];
+    float R[kVH][9], T[kVH][3];
 #pragma unroll
-        for (int c = 0; c < 6; ++c) sp[c][q] = v.pts[(size_t)c * v.n_pad + k0 + q];
+    for (int a = 0; a < kVH; ++a) {
+        const int h = h0 + threadIdx.x + a * kVThreads;
+        bool ok = false;
+        if (h < nh) {
+            const float4* rt = reinterpret_cast<const float4*>(v.rt + (size_t)h * 16);
+            const float4 r0 = rt[0], r1 = rt[1], r2 = rt[2], r3 = rt[3];
+            R[a][0] = r0.x; R[a][1] = r0.y; R[a][2] = r0.z; R[a][3] = r0.w;
+            R[a][4] = r1.x; R[a][5] = r1.y; R[a][6] = r1.z; R[a][7] = r1.w;
+            R[a][8] = r2.x; T[a][0] = r2.y; T[a][1] = r2.z; T[a][2] = r2.w;
+            ok = (__float_as_int(r3.y) & 1) != 0;
+        }
+        if (!ok) {
+            for (int c = 0; c < 9; ++c) R[a][c] = 0.f;
+            T[a][0] = T[a][1] = T[a][2] = __int_as_float(0x7fc00000);   // NaN: never an inlier
+        }
     }
     __syncthreads();
-    const int h = h0 + threadIdx.x;
-    if (h >= nh) return;
-    const float* rt = v.rt + (size_t)h * 16;
-    const uint32_t flags = static_cast<uint32_t>(__float_as_int(rt[13]));
-    if (!(flags & 1u)) return;
-    const float r00 = rt[0], r01 = rt[1], r02 = rt[2];
-    const float r10 = rt[3], r11 = rt[4], r12 = rt[5];
-    const float r20 = rt[6], r21 = rt[7], r22 = rt[8];
-    const float t0 = rt[9], t1 = rt[10], t2 = rt[11];
     const float th2 = v.theta * v.theta;
-    int in = 0;
-#pragma unroll 4
+    int in[kVH] = {};
+#pragma unroll 2
     for (int k = 0; k < cnt; ++k) {
-        const float x0 = sp[0][k], x1 = sp[1][k], x2 = sp[2][k];
-        const float e0 = fmaf(r00, x0, fmaf(r01, x1, fmaf(r02, x2, t0 - sp[3][k])));
-        const float e1 = fmaf(r10, x0, fmaf(r11, x1, fmaf(r12, x2, t1 - sp[4][k])));
-        const float e2 = fmaf(r20, x0, fmaf(r21, x1, fmaf(r22, x2, t2 - sp[5][k])));
-        const float d2 = fmaf(e0, e0, fmaf(e1, e1, e2 * e2));
-        in += d2 <= th2 ? 1 : 0;
+        const float4 pa = sp[k][0], pb = sp[k][1];
+#pragma unroll
+        for (int a = 0; a < kVH; ++a) {
+            const float e0 = fmaf(R[a][0], pa.x, fmaf(R[a][1], pa.y, fmaf(R[a][2], pa.z, T[a][0] - pa.w)));
+            const float e1 = fmaf(R[a][3], pa.x, fmaf(R[a][4], pa.y, fmaf(R[a][5], pa.z, T[a][1] - pb.x)));
+            const float e2 = fmaf(R[a][6], pa.x, fmaf(R[a][7], pa.y, fmaf(R[a][8], pa.z, T[a][2] - pb.y)));
+            const float d2 = fmaf(e0, e0, fmaf(e1, e1, e2 * e2));
+            in[a] += d2 <= th2 ? 1 : 0;
+        }
     }
-    if (in) atomicAdd(&v.inl[h], in);
+#pragma unroll
+    for (int a = 0; a < kVH; ++a) {
+        const int h = h0 + threadIdx.x + a * kVThreads;
+        if (h < nh && in[a]) atomicAdd(&v.inl[h], in[a]);
+    }
 }
 
 __global__ void __launch_bounds__(1024) finalize_kernel(ProbView v)
@@ -302,13 +343,14 @@ void launch_kabsch(const ProbView& v, cudaStream_t s)
 {
     const int cap = v.k1 * v.k2;
     kabsch_kernel<<<(cap + 127) / 128, 128, 0, s>>>(v);
+    kabsch_fp64_kernel<<<(cap + 31) / 32, 32, 0, s>>>(v);
 }
 
 void launch_verify(const ProbView& v, cudaStream_t s)
 {
     const int cap = v.k1 * v.k2;
-    dim3 grid((cap + kVerHyp - 1) / kVerHyp, (v.n + kVerPts - 1) / kVerPts);
-    verify_kernel<<<grid, kVerHyp, 0, s>>>(v);
+    dim3 grid((cap + kVHyp - 1) / kVHyp, (v.n + kVPts - 1) / kVPts);
+    verify_kernel<<<grid, kVThreads, 0, s>>>(v);
 }
 
 void launch_finalize(const ProbView& v, cudaStream_t s) { finalize_kernel<<<1, 1024, 0, s>>>(v); }

@@ -31,8 +31,12 @@ namespace {
 constexpr int kStages = 4;
 constexpr int kABytes = kSc2BM * kSc2BK;   // 16 KB
 constexpr int kBBytes = kSc2BN * kSc2BK;   // 32 KB
-constexpr int kSmemBytes = kStages * (kABytes + kBBytes) + 1024 /*align*/ + 256 /*barriers*/;
-constexpr uint32_t kTmemCols = 256;
+constexpr int kEpiWarps = 8;               // 2 per TMEM lane quarter, each half the columns
+constexpr int kThreads = 64 + 32 * kEpiWarps;
+constexpr int kPipeBytes = kStages * (kABytes + kBBytes);
+constexpr int kBarBytes = 256;
+constexpr int kSmemMax = 232448;           // 227 KB opt-in limit per block
+constexpr uint32_t kTmemCols = 512;        // two 256-column FP32 accumulators
 // E4M3 x E4M3 -> F32, M = 128, N = 256, both K-major
 constexpr uint32_t kIdesc = idesc_f32acc(0u, 0u, kSc2BM, kSc2BN);
 
@@ -46,34 +50,52 @@ __device__ __forceinline__ void tile_of(int t, int& bm, int& bn)
     bm = t - b * (b + 1);
 }
 
-__global__ void __launch_bounds__(128, 1)
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Persistent, warp-specialised: CTA b handles tiles b, b + grid, ...
+//   warp 0 lane 0   TMA producer over all (tile, k) of this CTA
+//   warp 1 lane 0   MMA issuer; accumulator buffer (tile count & 1)
+//   warps 2..9      epilogue of the previous tile while the next one runs
+// kSmemHist: the edge-weight histogram lives in shared memory (else global).
+template <bool kSmemHist>
+__global__ void __launch_bounds__(kThreads, 1)
 sc2_tcgen05_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, ProbView v)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t* sA = smem;
     uint8_t* sB = smem + kStages * kABytes;
-    uint64_t* full = reinterpret_cast<uint64_t*>(sB + kStages * kBBytes);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + kPipeBytes);
     uint64_t* empty = full + kStages;
-    uint64_t* accf = empty + kStages;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accf + 1);
+    uint64_t* tfull = empty + kStages;      // [2] accumulator ready
+    uint64_t* tempty = tfull + 2;           // [2] accumulator drained
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
+    uint32_t* shist = reinterpret_cast<uint32_t*>(smem + kPipeBytes + kBarBytes);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int bm, bn;
-    tile_of(blockIdx.x, bm, bn);
-    const int m0 = bm * kSc2BM, n0 = bn * kSc2BN;
+    const int nb = v.n_pad / kSc2BN;
+    const int ntiles = nb * (nb + 1);
     const int KT = v.n_pad / kSc2BK;
+    const int nbins = v.n + 1;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        mbar_init(accf, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], kEpiWarps);
+        }
         fence_mbar_init();
         prefetch_tmap(&tmA);
         prefetch_tmap(&tmB);
     }
+    if (kSmemHist)
+        for (int b = threadIdx.x; b < nbins; b += blockDim.x) shist[b] = 0u;
     if (warp == 0) tmem_alloc(tmem_slot, kTmemCols);
     tc_fence_before();
     __syncthreads();
@@ -81,90 +103,132 @@ sc2_tcgen05_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
     const uint32_t tmem = *tmem_slot;
     bool ok = true;
 
-    if (warp == 0 && lane == 0) {
-        // ---------------- TMA producer ----------------
-        for (int it = 0; it < KT; ++it) {
-            const int s = it % kStages;
-            const uint32_t ph = (it / kStages) & 1u;
-            if (!mbar_wait(&empty[s], ph ^ 1u)) { ok = false; break; }
-            mbar_arrive_expect_tx(&full[s], kABytes + kBBytes);
-            tma_load_2d(sA + s * kABytes, &tmA, it * kSc2BK, m0, &full[s]);
-            tma_load_2d(sB + s * kBBytes, &tmB, it * kSc2BK, n0, &full[s]);
-        }
-    } else if (warp == 1 && lane == 0) {
-        // ---------------- MMA issuer ----------------
-        for (int it = 0; it < KT; ++it) {
-            const int s = it % kStages;
-            const uint32_t ph = (it / kStages) & 1u;
-            if (!mbar_wait(&full[s], ph)) { ok = false; break; }
-            tc_fence_after();
-            const uint32_t a0 = smem_u32(sA + s * kABytes);
-            const uint32_t b0 = smem_u32(sB + s * kBBytes);
-#pragma unroll
-            for (int k = 0; k < kSc2BK / 32; ++k) {
-                // advance 32 bytes (K = 32 FP8 elements) inside the 128-byte swizzle row
-                mma_f8f6f4(tmem, sdesc_k_sw128(a0 + k * 32), sdesc_k_sw128(b0 + k * 32), kIdesc,
-                           (it | k) != 0 ? 1u : 0u);
-            }
-            mma_commit(&empty[s]);   // frees this stage when its MMAs are done
-        }
-        mma_commit(accf);            // accumulator complete
-    }
-    __syncwarp();
-
-    // ---------------- epilogue (all 4 warps) ----------------
-    if (!mbar_wait(accf, 0)) ok = false;
-    if (!ok) {
-        if (lane == 0) atomicOr(&v.ctl->err, TR_ERR_TIMEOUT);
-    } else {
-        tc_fence_after();
-        const int row = m0 + warp * 32 + lane;
-        const uint32_t* brow = v.bits + (size_t)row * v.ldb;
-        uint16_t* wrow = v.w + (size_t)row * v.n_pad;
-        int rsum = 0;
-#pragma unroll 1
-        for (int c = 0; c < kSc2BN / 32; ++c) {
-            uint32_t acc[32];
-            tmem_ld32(tmem + (static_cast<uint32_t>(warp * 32) << 16) + c * 32, acc);
-            tmem_ld_wait();
-            const int col0 = n0 + c * 32;
-            const uint32_t word = brow[col0 >> 5];
-            int val[32];
-#pragma unroll
-            for (int q = 0; q < 32; ++q) {
-                const int j = col0 + q;
-                const bool keep = ((word >> q) & 1u) && (row < j);
-                val[q] = keep ? static_cast<int>(__uint_as_float(acc[q])) : 0;
-                rsum += val[q];
-            }
-            uint4* dst = reinterpret_cast<uint4*>(wrow + col0);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                uint4 p;
-                p.x = static_cast<uint32_t>(val[8 * q + 0]) | (static_cast<uint32_t>(val[8 * q + 1]) << 16);
-                p.y = static_cast<uint32_t>(val[8 * q + 2]) | (static_cast<uint32_t>(val[8 * q + 3]) << 16);
-                p.z = static_cast<uint32_t>(val[8 * q + 4]) | (static_cast<uint32_t>(val[8 * q + 5]) << 16);
-                p.w = static_cast<uint32_t>(val[8 * q + 6]) | (static_cast<uint32_t>(val[8 * q + 7]) << 16);
-                dst[q] = p;
-            }
-            // column sums over this warp's 32 rows: butterfly transpose-reduce,
-            // afterwards lane l holds the sum of column col0 + l
-#pragma unroll
-            for (int off = 16; off >= 1; off >>= 1) {
-                const bool upper = (lane & off) != 0;
-#pragma unroll
-                for (int q = 0; q < off; ++q) {
-                    const int send = upper ? val[q] : val[q + off];
-                    const int keepv = upper ? val[q + off] : val[q];
-                    val[q] = keepv + __shfl_xor_sync(0xffffffffu, send, off);
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- TMA producer ----------------
+            int it = 0;
+            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                int bm, bn;
+                tile_of(t, bm, bn);
+                for (int kb = 0; kb < KT; ++kb, ++it) {
+                    const int s = it % kStages;
+                    const uint32_t ph = (it / kStages) & 1u;
+                    if (!mbar_wait(&empty[s], ph ^ 1u)) { ok = false; break; }
+                    mbar_arrive_expect_tx(&full[s], kABytes + kBBytes);
+                    tma_load_2d(sA + s * kABytes, &tmA, kb * kSc2BK, bm * kSc2BM, &full[s]);
+                    tma_load_2d(sB + s * kBBytes, &tmB, kb * kSc2BK, bn * kSc2BN, &full[s]);
                 }
             }
-            if (val[0] != 0) atomicAdd(&v.rowscore[col0 + lane], val[0]);
         }
-        if (rsum != 0) atomicAdd(&v.rowscore[row], rsum);
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---------------- MMA issuer ----------------
+            int it = 0, tc = 0;
+            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++tc) {
+                const int buf = tc & 1;
+                const uint32_t use = static_cast<uint32_t>(tc >> 1);
+                if (!mbar_wait(&tempty[buf], (use & 1u) ^ 1u)) { ok = false; break; }
+                tc_fence_after();
+                const uint32_t d = tmem + static_cast<uint32_t>(buf * kSc2BN);
+                for (int kb = 0; kb < KT; ++kb, ++it) {
+                    const int s = it % kStages;
+                    const uint32_t ph = (it / kStages) & 1u;
+                    if (!mbar_wait(&full[s], ph)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t a0 = smem_u32(sA + s * kABytes);
+                    const uint32_t b0 = smem_u32(sB + s * kBBytes);
+#pragma unroll
+                    for (int k = 0; k < kSc2BK / 32; ++k)   // K = 32 FP8 per MMA, 32-byte steps in the swizzle row
+                        mma_f8f6f4(d, sdesc_k_sw128(a0 + k * 32), sdesc_k_sw128(b0 + k * 32), kIdesc,
+                                   (kb | k) != 0 ? 1u : 0u);
+                    mma_commit(&empty[s]);
+                }
+                if (!ok) break;
+                mma_commit(&tfull[buf]);
+            }
+        }
+        __syncwarp();
+    } else {
+        // ---------------- epilogue warps ----------------
+        const int quarter = warp & 3;              // TMEM lanes this warp may access
+        const int half = (warp - 2) >> 2;          // column half of the tile
+        int tc = 0;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++tc) {
+            int bm, bn;
+            tile_of(t, bm, bn);
+            const int buf = tc & 1;
+            const uint32_t use = static_cast<uint32_t>(tc >> 1);
+            const bool got = mbar_wait(&tfull[buf], use & 1u);
+            if (!__all_sync(0xffffffffu, got)) { ok = false; break; }
+            tc_fence_after();
+            const int row = bm * kSc2BM + quarter * 32 + lane;
+            const uint32_t* brow = v.bits + (size_t)row * v.ldb;
+            uint16_t* wrow = v.w + (size_t)row * v.n_pad;
+            int rsum = 0;
+#pragma unroll 1
+            for (int c = 0; c < 4; ++c) {
+                const int cc = half * 128 + c * 32;
+                uint32_t acc[32];
+                tmem_ld32(tmem + static_cast<uint32_t>(buf * kSc2BN + cc) + (static_cast<uint32_t>(quarter * 32) << 16),
+                          acc);
+                tmem_ld_wait();
+                const int col0 = bn * kSc2BN + cc;
+                uint32_t word = brow[col0 >> 5];
+                if (col0 + 31 <= row) word = 0u;                       // keep only j > row
+                else if (col0 <= row) word &= ~0u << (row - col0 + 1);
+                int val[32];
+#pragma unroll
+                for (int q = 0; q < 32; ++q) {
+                    val[q] = ((word >> q) & 1u) ? static_cast<int>(__uint_as_float(acc[q])) : 0;
+                    rsum += val[q];
+                }
+                if (word) {
+#pragma unroll
+                    for (int q = 0; q < 32; ++q)
+                        if (val[q] > 0) {
+                            if (kSmemHist) atomicAdd(&shist[val[q]], 1u);
+                            else atomicAdd(&v.hist[val[q]], 1u);
+                        }
+                }
+                uint4* dst = reinterpret_cast<uint4*>(wrow + col0);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    uint4 p;
+                    p.x = static_cast<uint32_t>(val[8 * q + 0]) | (static_cast<uint32_t>(val[8 * q + 1]) << 16);
+                    p.y = static_cast<uint32_t>(val[8 * q + 2]) | (static_cast<uint32_t>(val[8 * q + 3]) << 16);
+                    p.z = static_cast<uint32_t>(val[8 * q + 4]) | (static_cast<uint32_t>(val[8 * q + 5]) << 16);
+                    p.w = static_cast<uint32_t>(val[8 * q + 6]) | (static_cast<uint32_t>(val[8 * q + 7]) << 16);
+                    dst[q] = p;
+                }
+                // column sums over this warp's 32 rows (butterfly transpose-reduce):
+                // afterwards lane l holds the sum of column col0 + l
+                if (__any_sync(0xffffffffu, word != 0u)) {
+#pragma unroll
+                    for (int off = 16; off >= 1; off >>= 1) {
+                        const bool upper = (lane & off) != 0;
+#pragma unroll
+                        for (int q = 0; q < off; ++q) {
+                            const int send = upper ? val[q] : val[q + off];
+                            const int keepv = upper ? val[q + off] : val[q];
+                            val[q] = keepv + __shfl_xor_sync(0xffffffffu, send, off);
+                        }
+                    }
+                    if (val[0] != 0) atomicAdd(&v.rowscore[col0 + lane], val[0]);
+                }
+            }
+            if (rsum != 0) atomicAdd(&v.rowscore[row], rsum);
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[buf]);
+        }
     }
+    if (!ok && lane == 0) atomicOr(&v.ctl->err, TR_ERR_TIMEOUT);
     tc_fence_before();
     __syncthreads();
+    if (kSmemHist)
+        for (int b = threadIdx.x + 1; b < nbins; b += blockDim.x)
+            if (shist[b]) atomicAdd(&v.hist[b], shist[b]);
     if (warp == 0) {
         tc_fence_after();
         tmem_dealloc(tmem, kTmemCols);
@@ -207,18 +271,34 @@ __global__ void __launch_bounds__(256) sc2_bitset_kernel(ProbView v)
     }
 }
 
+int g_sc2_sms = 0;
+
 }  // namespace
 
 cudaError_t sc2_tcgen05_setup()
 {
-    return cudaFuncSetAttribute(sc2_tcgen05_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g_sc2_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(sc2_tcgen05_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(sc2_tcgen05_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kPipeBytes + kBarBytes + 1024);
+    return e;
 }
 
 void launch_sc2_tcgen05(const ProbView& v, const CUtensorMap& tmA, const CUtensorMap& tmB, cudaStream_t s)
 {
     const int nb = v.n_pad / kSc2BN;
     const int tiles = nb * (nb + 1);
-    sc2_tcgen05_kernel<<<tiles, 128, kSmemBytes, s>>>(tmA, tmB, v);
+    const int grid = tiles < g_sc2_sms ? tiles : (g_sc2_sms > 0 ? g_sc2_sms : 148);
+    const size_t base = kPipeBytes + kBarBytes + 1024;
+    const size_t hist = static_cast<size_t>(v.n + 1) * 4;
+    if (base + hist <= static_cast<size_t>(kSmemMax))
+        sc2_tcgen05_kernel<true><<<grid, kThreads, base + hist, s>>>(tmA, tmB, v);
+    else
+        sc2_tcgen05_kernel<false><<<grid, kThreads, base, s>>>(tmA, tmB, v);
 }
 
 void launch_sc2_bitset(const ProbView& v, cudaStream_t s)

@@ -32,20 +32,24 @@ __device__ __forceinline__ uint64_t edge_key(int w, int i, int j, int n)
 }
 
 // Iterate row i's upper-triangle entries j in (i, n) in chunks of 8 uint16
-// (16-byte loads); lane l takes chunks c0 + l, c0 + l + 32, ...
+// (16-byte loads); lane l takes chunks c0 + l, c0 + l + 32, ..., two loads in
+// flight per lane.
 template <typename F>
 __device__ __forceinline__ void for_row_chunks(const ProbView& v, int i, int lane, F&& f)
 {
     if (i + 1 >= v.n) return;
     const uint16_t* wrow = v.w + (size_t)i * v.n_pad;
     const int c0 = (i + 1) >> 3, c1 = (v.n - 1) >> 3;
-    for (int c = c0 + lane; c <= c1; c += 32) {
-        const uint4 q = *reinterpret_cast<const uint4*>(wrow + c * 8);
-        const uint32_t u[4] = {q.x, q.y, q.z, q.w};
+    for (int c = c0 + lane; c <= c1; c += 64) {
+        const int cb = c + 32;
+        const uint4 qa = *reinterpret_cast<const uint4*>(wrow + c * 8);
+        const uint4 qb = cb <= c1 ? *reinterpret_cast<const uint4*>(wrow + cb * 8) : make_uint4(0, 0, 0, 0);
+        const uint32_t u[8] = {qa.x, qa.y, qa.z, qa.w, qb.x, qb.y, qb.z, qb.w};
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
-            const int j = c * 8 + e;
+        for (int e = 0; e < 16; ++e) {
+            const int j = (e < 8 ? c : cb) * 8 + (e & 7);
             const int w = (u[e >> 1] >> ((e & 1) * 16)) & 0xFFFF;
+            if (u[e >> 1] == 0u) continue;
             f(j, (j > i && j < v.n) ? w : 0);
         }
     }
@@ -232,23 +236,31 @@ __global__ void __launch_bounds__(256) emit_ties_kernel(ProbView v)
     }
 }
 
+// 32 candidates per block (one per lane); the 8 warps split the comparison
+// range; all n_sel keys are staged in shared memory.
 __global__ void __launch_bounds__(256) rank_kernel(ProbView v)
 {
-    __shared__ uint64_t sk[2048];
+    extern __shared__ uint64_t sk[];
+    __shared__ int part[8][32];
     const int n_sel = v.ctl->n_sel;
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (blockIdx.x == 0 && threadIdx.x == 0) v.ctl->n_pivots = n_sel;
-    if (static_cast<int>(blockIdx.x * blockDim.x) >= n_sel) return;
-    const uint64_t key = (e < n_sel) ? v.cand[e] : 0ull;
-    int rank = 0;
-    for (int base = 0; base < n_sel; base += 2048) {
-        const int cnt = min(2048, n_sel - base);
-        __syncthreads();
-        for (int q = threadIdx.x; q < cnt; q += blockDim.x) sk[q] = v.cand[base + q];
-        __syncthreads();
-        for (int q = 0; q < cnt; ++q) rank += sk[q] > key;
-    }
-    if (e < n_sel) {
+    if (static_cast<int>(blockIdx.x * 32) >= n_sel) return;
+    for (int q = threadIdx.x; q < n_sel; q += blockDim.x) sk[q] = v.cand[q];
+    __syncthreads();
+    const int e = blockIdx.x * 32 + lane;
+    const uint64_t key = (e < n_sel) ? sk[e] : ~0ull;
+    const int chunk = (n_sel + 7) / 8;
+    const int f0 = warp * chunk, f1 = min(n_sel, f0 + chunk);
+    int cnt = 0;
+#pragma unroll 4
+    for (int f = f0; f < f1; ++f) cnt += sk[f] > key;
+    part[warp][lane] = cnt;
+    __syncthreads();
+    if (warp == 0 && e < n_sel) {
+        int rank = 0;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) rank += part[w][lane];
         const uint32_t lin = 0xFFFFFFFFu - static_cast<uint32_t>(key & 0xFFFFFFFFull);
         const int i = static_cast<int>(lin / static_cast<uint32_t>(v.n));
         const int j = static_cast<int>(lin % static_cast<uint32_t>(v.n));
@@ -267,23 +279,32 @@ cudaError_t topk_setup()
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(rank_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             TURBOREG_K1_MAX * 8);
+    if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(hist_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 kHistSmemMaxBins * 4);
+}
+
+void launch_topk_after_hist(const ProbView& v, cudaStream_t s)
+{
+    const int row_blocks = (v.n + 7) / 8;   // one row per warp
+    select_kernel<<<1, 1024, 0, s>>>(v);
+    collect_kernel<<<row_blocks, 256, 0, s>>>(v);
+    scan_rows_kernel<<<1, 1024, 0, s>>>(v);
+    emit_ties_kernel<<<row_blocks, 256, 0, s>>>(v);
+    rank_kernel<<<(v.k1 + 31) / 32, 256, v.k1 * 8, s>>>(v);
 }
 
 void launch_topk(const ProbView& v, cudaStream_t s)
 {
     const int sms = g_num_sms > 0 ? g_num_sms : 148;
-    const int row_blocks = min((v.n + 7) / 8, 2 * sms);   // 8 warps = 8 rows per block per sweep
+    const int hist_blocks = min((v.n + 7) / 8, 4 * sms);
     if (v.n + 1 <= kHistSmemMaxBins)
-        hist_kernel<true><<<row_blocks, 256, (v.n + 1) * 4, s>>>(v);
+        hist_kernel<true><<<hist_blocks, 256, (v.n + 1) * 4, s>>>(v);
     else
-        hist_kernel<false><<<row_blocks, 256, 0, s>>>(v);
-    select_kernel<<<1, 1024, 0, s>>>(v);
-    collect_kernel<<<row_blocks, 256, 0, s>>>(v);
-    scan_rows_kernel<<<1, 1024, 0, s>>>(v);
-    emit_ties_kernel<<<row_blocks, 256, 0, s>>>(v);
-    rank_kernel<<<(v.k1 + 255) / 256, 256, 0, s>>>(v);
+        hist_kernel<false><<<hist_blocks, 256, 0, s>>>(v);
+    launch_topk_after_hist(v, s);
 }
 
 }  // namespace tr

@@ -32,7 +32,9 @@ struct Ctl {
     int32_t n_pivots;    // |P|
     int32_t n_valid;     // valid hypotheses (clique + non-degenerate Kabsch)
     int32_t n_fp64;      // hypotheses whose Kabsch ran in FP64
-    int32_t pad[6];
+    uint32_t fp64_slot;  // atomic counter of the FP64 Kabsch list
+    uint32_t done_blocks;  // completion counter for last-block epilogues
+    int32_t pad[4];
 };
 
 // ---------------------------------------------------------------------------

@@ -23,6 +23,7 @@ struct ProbView {
     float theta;         // inlier threshold
     float kappa_fp64;    // FP64 Kabsch above this sigma1/sigma2
     float* pts;          // [6][n_pad]
+    float* pts8;         // [n_pad][8] = (x0, x1, x2, y0, y1, y2, 0, 0)
     uint8_t* a8;         // [n_pad][n_pad] FP8 E4M3 0/1 adjacency
     uint32_t* bits;      // [n_pad][ldb] adjacency bitset
     uint16_t* w;         // [n_pad][n_pad] O2Graph weights (i < j only)
@@ -36,16 +37,19 @@ struct ProbView {
     int4* cliques;       // [K1_MAX*K2_MAX] (i, j, z, valid) in Alg. 2 order
     float* rt;           // [K1_MAX*K2_MAX][16] R, t, kappa, flags
     int32_t* inl;        // [K1_MAX*K2_MAX] inlier numbers
+    int32_t* fp64_list;  // [K1_MAX*K2_MAX] hypotheses whose Kabsch needs FP64
     Ctl* ctl;            // device scalars
     turboreg_result* res;  // device result
 };
 
 // stage launchers (all asynchronous on `s`)
 void launch_pack(const ProbView& v, const float* src, const float* dst, cudaStream_t s);
+const void* pack_kernel_func();   // identifies the pack node inside a captured graph
 void launch_compat(const ProbView& v, cudaStream_t s);
 void launch_sc2_tcgen05(const ProbView& v, const CUtensorMap& tmA, const CUtensorMap& tmB, cudaStream_t s);
 void launch_sc2_bitset(const ProbView& v, cudaStream_t s);
-void launch_topk(const ProbView& v, cudaStream_t s);
+void launch_topk(const ProbView& v, cudaStream_t s);             // histogram pass + selection
+void launch_topk_after_hist(const ProbView& v, cudaStream_t s);  // selection (histogram already built)
 void launch_pgs(const ProbView& v, cudaStream_t s);
 void launch_kabsch(const ProbView& v, cudaStream_t s);
 void launch_verify(const ProbView& v, cudaStream_t s);

@@ -189,3 +189,25 @@ def test_stage_times_reported(ctx):
     assert list(st) == ["pack", "compat", "sc2", "topk", "pgs", "kabsch", "verify", "finalize"]
     assert all(v >= 0 for v in st.values())
     print(st)
+
+
+def test_graph_replay_equals_direct_launches(ctx):
+    # same shape, different inputs: the captured graph is replayed with patched input pointers
+    for seed in (60, 61, 62):
+        p = synth.make_problem("indoor", 4000, 0.05, seed)
+        direct = ctx.register(p.x, p.y, trg.default_params(p.tau, 1500, p.theta, flags=trg.FLAG_NO_GRAPH))
+        IN_d = ctx.buffer(trg.BUF_INLIERS).copy()
+        graph = ctx.register(p.x, p.y, trg.default_params(p.tau, 1500, p.theta))
+        assert graph.status == direct.status and graph.hypothesis == direct.hypothesis
+        assert np.array_equal(graph.R, direct.R) and np.array_equal(graph.t, direct.t)
+        assert np.array_equal(ctx.buffer(trg.BUF_INLIERS), IN_d)
+
+
+def test_kappa_distribution_report(ctx):
+    p = synth.make_problem("indoor", 5000, 0.05, 0)
+    res = ctx.register(p.x, p.y, trg.default_params(p.tau, 2000, p.theta))
+    RT = ctx.buffer(trg.BUF_RT)
+    flags = RT[:, 13].view(np.int32)
+    kap = RT[(flags & 1) != 0, 12]
+    print("kappa quantiles", np.quantile(kap, [0.5, 0.9, 0.99]).round(2), "fp64", int(((flags & 2) != 0).sum()),
+          ">1e3", int((kap > 1e3).sum()), "winner kappa", RT[res.hypothesis, 12])
