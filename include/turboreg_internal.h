@@ -60,7 +60,7 @@ const char* turboreg_stage_name(int32_t stage);
  * memory through its own pool, or a real-time loop that forbids allocation
  * after start-up (cudaMalloc may synchronise the device and take unbounded
  * time).  Its scratch (histogram, per-row tie counts, candidate keys, control
- * block: about 160 KB) is one fixed array in the library's device memory,
+ * block: about 225 KB) is one fixed array in the library's device memory,
  * loaded with the module and held by every GPU that loads the library until
  * the process exits; nothing is allocated or freed by this call.
  *

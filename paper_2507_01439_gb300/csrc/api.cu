@@ -44,6 +44,8 @@ struct Workspace {
     uint32_t* hist = nullptr;
     int32_t* rowcnt = nullptr;
     int32_t* rowpref = nullptr;
+    int32_t* rowcnt_gt = nullptr;
+    int32_t* rowpref_gt = nullptr;
     uint64_t* cand = nullptr;
     int4* piv = nullptr;
     int4* cliques = nullptr;
@@ -62,6 +64,8 @@ struct turboreg_ctx {
     int32_t max_n = 0, max_batch = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    cudaStream_t side = nullptr;               // FP64 Kabsch + its verification run here,
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;  // concurrently with the main verification
     Workspace ws;
     turboreg_result* host_res = nullptr;   // pinned [max_batch]
     EncodeTiledFn encode = nullptr;
@@ -113,7 +117,7 @@ cudaError_t dalloc(T** p, size_t count)
 
 void free_ws(Workspace& ws)
 {
-    void* ptrs[] = {ws.pts, ws.pts8, ws.fp64_list, ws.a8, ws.bits, ws.w, ws.rowscore, ws.deg, ws.hist, ws.rowcnt, ws.rowpref,
+    void* ptrs[] = {ws.pts, ws.pts8, ws.fp64_list, ws.a8, ws.bits, ws.w, ws.rowscore, ws.deg, ws.hist, ws.rowcnt, ws.rowpref, ws.rowcnt_gt, ws.rowpref_gt,
                     ws.cand, ws.piv, ws.cliques, ws.rt, ws.inl, ws.ctl, ws.res, ws.in_src, ws.in_dst};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -139,6 +143,8 @@ int alloc_ws(Workspace& ws, int32_t max_n, int32_t max_batch)
     if (e == cudaSuccess) e = dalloc(&ws.hist, np + 1);
     if (e == cudaSuccess) e = dalloc(&ws.rowcnt, np);
     if (e == cudaSuccess) e = dalloc(&ws.rowpref, np);
+    if (e == cudaSuccess) e = dalloc(&ws.rowcnt_gt, np);
+    if (e == cudaSuccess) e = dalloc(&ws.rowpref_gt, np);
     if (e == cudaSuccess) e = dalloc(&ws.cand, TURBOREG_K1_MAX);
     if (e == cudaSuccess) e = dalloc(&ws.piv, TURBOREG_K1_MAX);
     if (e == cudaSuccess) e = dalloc(&ws.cliques, nh);
@@ -239,6 +245,8 @@ ProbView make_view(turboreg_ctx* c, int32_t n, const turboreg_params* p, turbore
     v.hist = ws.hist;
     v.rowcnt = ws.rowcnt;
     v.rowpref = ws.rowpref;
+    v.rowcnt_gt = ws.rowcnt_gt;
+    v.rowpref_gt = ws.rowpref_gt;
     v.cand = ws.cand;
     v.piv = ws.piv;
     v.cliques = ws.cliques;
@@ -271,13 +279,19 @@ int enqueue_problem(turboreg_ctx* c, const float* dsrc, const float* ddst, int32
     else launch_sc2_tcgen05(v, c->tmA, c->tmB, s);   // also builds the weight histogram
     if (timed) TR_CHECK(cudaEventRecordWithFlags(c->ev[3], s, cudaEventRecordExternal));
     if (bitset) launch_topk(v, s);
-    else launch_topk_after_hist(v, s);
+    else launch_topk_after_select(v, s);   // the GEMM's last CTA chose alpha
     if (timed) TR_CHECK(cudaEventRecordWithFlags(c->ev[4], s, cudaEventRecordExternal));
     launch_pgs(v, s);
     if (timed) TR_CHECK(cudaEventRecordWithFlags(c->ev[5], s, cudaEventRecordExternal));
     launch_kabsch(v, s);
     if (timed) TR_CHECK(cudaEventRecordWithFlags(c->ev[6], s, cudaEventRecordExternal));
+    // fork: ill-conditioned cliques (FP64 list) on the side stream, the rest here
+    TR_CHECK(cudaEventRecord(c->fork_ev, s));
+    TR_CHECK(cudaStreamWaitEvent(c->side, c->fork_ev, 0));
+    launch_kabsch_fp64_verify(v, c->side);
+    TR_CHECK(cudaEventRecord(c->join_ev, c->side));
     launch_verify(v, s);
+    TR_CHECK(cudaStreamWaitEvent(s, c->join_ev, 0));
     if (timed) TR_CHECK(cudaEventRecordWithFlags(c->ev[7], s, cudaEventRecordExternal));
     launch_finalize(v, s);
     if (timed) TR_CHECK(cudaEventRecordWithFlags(c->ev[8], s, cudaEventRecordExternal));
@@ -475,6 +489,12 @@ int turboreg_create(int device, int32_t max_n, int32_t max_batch, void* cuda_str
             return TURBOREG_ERR_CUDA;
         }
     }
+    if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->join_ev, cudaEventDisableTiming) != cudaSuccess) {
+        turboreg_destroy(c);
+        return TURBOREG_ERR_CUDA;
+    }
     cudaDriverEntryPointQueryResult q;
     void* fn = nullptr;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
@@ -484,7 +504,10 @@ int turboreg_create(int device, int32_t max_n, int32_t max_batch, void* cuda_str
         return TURBOREG_ERR_CUDA;
     }
     c->encode = reinterpret_cast<EncodeTiledFn>(fn);
-    if (sc2_tcgen05_setup() != cudaSuccess || topk_setup() != cudaSuccess) {
+    cudaError_t se = sc2_tcgen05_setup();
+    if (se == cudaSuccess) se = topk_setup();
+    if (se != cudaSuccess) {
+        std::fprintf(stderr, "turboreg: kernel set-up failed: %s\n", cudaGetErrorString(se));
         cudaGetLastError();
         turboreg_destroy(c);
         return TURBOREG_ERR_CUDA;
@@ -498,9 +521,13 @@ void turboreg_destroy(turboreg_ctx* c)
     if (!c) return;
     cudaSetDevice(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->side) cudaStreamSynchronize(c->side);
     for (auto& sl : c->gslot) drop_slot(sl);
     for (int k = 0; k <= kNumStages; ++k)
         if (c->ev[k]) cudaEventDestroy(c->ev[k]);
+    if (c->fork_ev) cudaEventDestroy(c->fork_ev);
+    if (c->join_ev) cudaEventDestroy(c->join_ev);
+    if (c->side) cudaStreamDestroy(c->side);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     free_ws(c->ws);
     if (c->host_res) cudaFreeHost(c->host_res);

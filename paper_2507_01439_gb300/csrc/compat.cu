@@ -91,7 +91,9 @@ __device__ __noinline__ bool compat_fp64(float xi0, float xi1, float xi2, float 
     return fabs(__dsub_rn(__dsqrt_rn(s), __dsqrt_rn(t))) <= (double)tau;
 }
 
-__device__ __forceinline__ bool compat_pair(const float (&xi)[6], const float (&xj)[6], float tau)
+// FP32 decision; *near is set when |diff - tau| is inside the guard band (or
+// the arithmetic produced NaN/Inf) and the FP64 evaluation must decide.
+__device__ __forceinline__ bool compat_fast(const float (&xi)[6], const float (&xj)[6], float tau, bool* near)
 {
     const float ax = xi[0] - xj[0], ay = xi[1] - xj[1], az = xi[2] - xj[2];
     const float bx = xi[3] - xj[3], by = xi[4] - xj[4], bz = xi[5] - xj[5];
@@ -100,8 +102,8 @@ __device__ __forceinline__ bool compat_pair(const float (&xi)[6], const float (&
     const float dX = sqrt_approx(sX), dY = sqrt_approx(sY);
     const float diff = fabsf(dX - dY);
     const float g = fmaf(dX + dY, 9.5367431640625e-07f, 1e-18f);   // 2^-20 (dX + dY) + slack
-    if (fabsf(diff - tau) > g) return diff <= tau;                 // NaN/Inf fall through
-    return compat_fp64(xi[0], xi[1], xi[2], xi[3], xi[4], xi[5], xj[0], xj[1], xj[2], xj[3], xj[4], xj[5], tau);
+    *near = !(fabsf(diff - tau) > g);
+    return diff <= tau;
 }
 
 // 4 bits -> 4 bytes of FP8 E4M3 (0x38 = 1.0 for a set bit, 0x00 otherwise)
@@ -158,33 +160,65 @@ __global__ void __launch_bounds__(kThreads) compat_kernel(ProbView v)
     }
     const float tau = v.tau;
     uint32_t cmask[4] = {0u, 0u, 0u, 0u};   // bit r: G(i0 + 16 warp + r, j_q)
+    uint32_t wrow_bits[4] = {0u, 0u, 0u, 0u};
 #pragma unroll 2
     for (int r = 0; r < 16; ++r) {
         const int rr = warp * 16 + r;
         const int i = i0 + rr;
         const float4 pa = srow[rr][0], pb = srow[rr][1];
         const float xi[6] = {pa.x, pa.y, pa.z, pa.w, pb.x, pb.y};
-        uint32_t word[4];
         const bool iok = i < v.n;
+        uint32_t word[4];
+        uint32_t nearm = 0u;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int j = j0 + lane + 32 * q;
-            const bool a = iok && jok[q] && (i != j) && compat_pair(xi, xj[q], tau);
-            cmask[q] |= static_cast<uint32_t>(a) << r;
-            word[q] = __ballot_sync(0xffffffffu, a);
+            bool nq;
+            bool a = compat_fast(xi, xj[q], tau, &nq);
+            const bool valid = iok & jok[q] & (i != j);
+            a = a & valid;
+            nearm |= static_cast<uint32_t>(nq & valid) << q;
+            word[q] = static_cast<uint32_t>(a);
         }
-        // direct row i: 4 bitset words (16 B) and 128 FP8 bytes (lanes 0..7, 16 B each)
-        if (lane == 0) {
-            *reinterpret_cast<uint4*>(v.bits + (size_t)i * v.ldb + (j0 >> 5)) =
-                make_uint4(word[0], word[1], word[2], word[3]);
-            const int d = __popc(word[0]) + __popc(word[1]) + __popc(word[2]) + __popc(word[3]);
-            if (d) atomicAdd(&v.deg[i], d);
+        if (nearm) {                      // rare: decide in FP64 with the reference operation order
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if ((nearm >> q) & 1u)
+                    word[q] = compat_fp64(xi[0], xi[1], xi[2], xi[3], xi[4], xi[5], xj[q][0], xj[q][1],
+                                          xj[q][2], xj[q][3], xj[q][4], xj[q][5], tau) ? 1u : 0u;
         }
-        if (lane < 8) {
-            const uint32_t w = (lane >> 1) == 0 ? word[0] : (lane >> 1) == 1 ? word[1] : (lane >> 1) == 2 ? word[2] : word[3];
-            *reinterpret_cast<uint4*>(v.a8 + (size_t)i * v.n_pad + j0 + lane * 16) =
-                bits16_to_fp8((w >> ((lane & 1) * 16)) & 0xFFFFu);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            cmask[q] |= word[q] << r;
+            word[q] = __ballot_sync(0xffffffffu, word[q] != 0u);
         }
+        // lane r of the warp keeps row r's four bitset words for the stores below
+        if (lane == r) {
+            wrow_bits[0] = word[0]; wrow_bits[1] = word[1]; wrow_bits[2] = word[2]; wrow_bits[3] = word[3];
+        }
+    }
+    // direct rows i0 + 16 warp + r (r = 0..15): lanes 0..15 store the bitset words
+    // (16 B each); all 32 lanes expand two 64-byte halves of the FP8 rows
+    if (lane < 16) {
+        const int i = i0 + warp * 16 + lane;
+        *reinterpret_cast<uint4*>(v.bits + (size_t)i * v.ldb + (j0 >> 5)) =
+            make_uint4(wrow_bits[0], wrow_bits[1], wrow_bits[2], wrow_bits[3]);
+        const int d = __popc(wrow_bits[0]) + __popc(wrow_bits[1]) + __popc(wrow_bits[2]) + __popc(wrow_bits[3]);
+        if (d) atomicAdd(&v.deg[i], d);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        // row r = lane & 15, 16-byte segment seg = 4 (lane >> 4) + k of the 8 in a 128-byte row
+        const int r = lane & 15;
+        const int seg = 4 * (lane >> 4) + k;
+        const uint32_t w0 = __shfl_sync(0xffffffffu, wrow_bits[0], r);
+        const uint32_t w1 = __shfl_sync(0xffffffffu, wrow_bits[1], r);
+        const uint32_t w2 = __shfl_sync(0xffffffffu, wrow_bits[2], r);
+        const uint32_t w3 = __shfl_sync(0xffffffffu, wrow_bits[3], r);
+        const uint32_t w = (seg >> 1) == 0 ? w0 : (seg >> 1) == 1 ? w1 : (seg >> 1) == 2 ? w2 : w3;
+        const int i = i0 + warp * 16 + r;
+        *reinterpret_cast<uint4*>(v.a8 + (size_t)i * v.n_pad + j0 + seg * 16) =
+            bits16_to_fp8((w >> ((seg & 1) * 16)) & 0xFFFFu);
     }
     if (diag) return;
     // mirrored tile: row j gets bits of rows i0 .. i0+127

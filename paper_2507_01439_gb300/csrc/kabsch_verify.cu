@@ -29,11 +29,22 @@ namespace tr {
 namespace {
 
 template <typename T>
-__device__ __forceinline__ T tsqrt(T x);
+__device__ __forceinline__ T inv_sqrt(T x);
 template <>
-__device__ __forceinline__ float tsqrt<float>(float x) { return sqrtf(x); }
+__device__ __forceinline__ float inv_sqrt<float>(float x) { return 1.0f / sqrtf(x); }
+// FP64 1/sqrt(x) without the long FP64 divide and square-root sequences: an
+// FP32 seed refined by two Newton steps y <- y (3 - x y^2) / 2 (each step
+// squares the relative error: ~1e-7 -> 1e-14 -> below FP64 rounding).
 template <>
-__device__ __forceinline__ double tsqrt<double>(double x) { return sqrt(x); }
+__device__ __forceinline__ double inv_sqrt<double>(double x)
+{
+    if (!(x > 1e-30 && x < 1e30)) return 1.0 / sqrt(x);
+    double y = static_cast<double>(rsqrtf(static_cast<float>(x)));
+    const double hx = 0.5 * x;
+    y = y * fma(-hx * y, y, 1.5);
+    y = y * fma(-hx * y, y, 1.5);
+    return y;
+}
 
 template <typename T>
 struct KabschOut {
@@ -77,7 +88,7 @@ __device__ __forceinline__ bool frame3(const T p[3][3], T e1[3], T e2[3], T nrm[
     if (l02 > le) { e = d02; le = l02; }
     if (l12 > le) { e = d12; le = l12; }
     if (!(nn > T(0)) || !(le > T(0))) return false;
-    const T in = T(1) / tsqrt(nn), ie = T(1) / tsqrt(le);
+    const T in = inv_sqrt(nn), ie = inv_sqrt(le);
     for (int c = 0; c < 3; ++c) {
         nrm[c] *= in;
         e1[c] = e[c] * ie;
@@ -91,8 +102,8 @@ __device__ void kabsch3(const T p[3][3], const T q[3][3], KabschOut<T>& o)
 {
     T cx[3], cy[3];
     for (int c = 0; c < 3; ++c) {
-        cx[c] = (p[0][c] + p[1][c] + p[2][c]) / T(3);
-        cy[c] = (q[0][c] + q[1][c] + q[2][c]) / T(3);
+        cx[c] = (p[0][c] + p[1][c] + p[2][c]) * T(1.0 / 3.0);
+        cy[c] = (q[0][c] + q[1][c] + q[2][c]) * T(1.0 / 3.0);
     }
     T e1[3], e2[3], nx[3], f1[3], f2[3], ny[3];
     o.ok = frame3(p, e1, e2, nx) && frame3(q, f1, f2, ny);
@@ -115,21 +126,27 @@ __device__ void kabsch3(const T p[3][3], const T q[3][3], KabschOut<T>& o)
     }
     const T rx = m11 + m22, ry = m12 - m21;   // rotation candidate
     const T fx = m11 - m22, fy = m12 + m21;   // reflection candidate
-    const T nr = tsqrt(rx * rx + ry * ry), nf = tsqrt(fx * fx + fy * fy);
-    const T hi = nr >= nf ? nr : nf, lo = nr >= nf ? nf : nr;
-    o.s1 = (hi + lo) * T(0.5);
-    o.s2 = (hi - lo) * T(0.5);
-    o.kappa = o.s2 > T(0) ? o.s1 / o.s2 : T(INFINITY);
-    if (!(hi > T(0))) {
+    const T r2 = rx * rx + ry * ry, q2 = fx * fx + fy * fy;
+    if (!(r2 > T(0) || q2 > T(0))) {
         o.ok = false;
+        o.kappa = T(INFINITY);
+        o.s1 = o.s2 = T(0);
         return;
     }
+    const bool rot = r2 >= q2;
+    const T ih = inv_sqrt(rot ? r2 : q2);               // 1 / (sigma1 + sigma2)
+    const T hi = (rot ? r2 : q2) * ih;
+    const T lo2 = rot ? q2 : r2;
+    const T lo = lo2 > T(0) ? lo2 * inv_sqrt(lo2) : T(0);
+    o.s1 = (hi + lo) * T(0.5);
+    o.s2 = (hi - lo) * T(0.5);
+    o.kappa = o.s2 > T(0) ? static_cast<T>(static_cast<float>(o.s1) / static_cast<float>(o.s2)) : T(INFINITY);
     T X00, X01, X10, X11, sg;
-    if (nr >= nf) {
-        const T c = rx / nr, s = ry / nr;
+    if (rot) {
+        const T c = rx * ih, s = ry * ih;
         X00 = c; X01 = -s; X10 = s; X11 = c; sg = T(1);
     } else {
-        const T c = fx / nf, s = fy / nf;
+        const T c = fx * ih, s = fy * ih;
         X00 = c; X01 = s; X10 = s; X11 = -c; sg = T(-1);
     }
     for (int r = 0; r < 3; ++r)
@@ -209,62 +226,121 @@ __global__ void __launch_bounds__(32) kabsch_fp64_kernel(ProbView v)
     out[13] = __int_as_float(static_cast<int>((valid ? 1u : 0u) | 2u));
 }
 
-// Verification: each thread owns kVH hypotheses (R, t in registers); a block
-// stages kVPts correspondences as 32-byte records in shared memory and every
-// point read (two 16-byte broadcasts) feeds kVH residuals.
-constexpr int kVH = 4;
-constexpr int kVThreads = 64;
-constexpr int kVHyp = kVH * kVThreads;   // hypotheses per block
-constexpr int kVPts = 128;               // correspondences per block
+// ---- packed FP32 pairs (two hypotheses per instruction) -----------------
+struct f2 {
+    unsigned long long v;
+};
+__device__ __forceinline__ f2 pk(float lo, float hi)
+{
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void upk(f2 a, float& lo, float& hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(a.v));
+}
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c)
+{
+    f2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d.v) : "l"(a.v), "l"(b.v), "l"(c.v));
+    return d;
+}
+__device__ __forceinline__ f2 sub2(f2 a, f2 b)
+{
+    f2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d.v) : "l"(a.v), "l"(b.v));
+    return d;
+}
+__device__ __forceinline__ f2 mul2(f2 a, f2 b)
+{
+    f2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d.v) : "l"(a.v), "l"(b.v));
+    return d;
+}
 
-__global__ void __launch_bounds__(kVThreads) verify_kernel(ProbView v)
+// Verification.  A block holds 128 hypotheses (R, t staged in shared memory)
+// and 256 correspondences (32-byte records); each of its 4 warps takes 64 of
+// the correspondences for all 128 hypotheses, 4 per lane, evaluated as two
+// packed pairs: e = R x + (t - y), d2 = |e|^2 with fma.rn.f32x2 (the same
+// rounding as the scalar expression, two hypotheses per instruction).  The
+// warps' counts are summed in shared memory; one atomic per hypothesis.
+// kList: hypotheses are the entries of the FP64 Kabsch list; otherwise the
+// hypotheses whose FP32 Kabsch is valid (flags == 1).
+constexpr int kVWarps = 4;
+constexpr int kVHyp = 128;
+constexpr int kVPtsWarp = 64;
+constexpr int kVPts = kVWarps * kVPtsWarp;
+
+template <bool kList>
+__global__ void __launch_bounds__(128) verify_kernel(ProbView v)
 {
     __shared__ __align__(16) float4 sp[kVPts][2];
-    const int nh = v.ctl->n_pivots * v.k2;
+    __shared__ __align__(16) float4 srt[kVHyp][4];
+    __shared__ int scnt[kVWarps][kVHyp];
+    const int nh = kList ? static_cast<int>(v.ctl->fp64_slot) : v.ctl->n_pivots * v.k2;
     const int h0 = blockIdx.x * kVHyp;
     if (h0 >= nh) return;
     const int k0 = blockIdx.y * kVPts;
-    const int cnt = min(kVPts, v.n - k0);
-    const float4* src = reinterpret_cast<const float4*>(v.pts8 + (size_t)k0 * 8);
-    for (int q = threadIdx.x; q < 2 * kVPts; q += kVThreads) (&sp[0][0])[q] = src[q];
-    float R[kVH][9], T[kVH][3];
-#pragma unroll
-    for (int a = 0; a < kVH; ++a) {
-        const int h = h0 + threadIdx.x + a * kVThreads;
-        bool ok = false;
-        if (h < nh) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    {
+        const float4* src = reinterpret_cast<const float4*>(v.pts8 + (size_t)k0 * 8);
+        for (int q = threadIdx.x; q < 2 * kVPts; q += blockDim.x) (&sp[0][0])[q] = src[q];
+        const int slot = h0 + threadIdx.x;
+        float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0, r3 = r0;
+        if (slot < nh) {
+            const int h = kList ? v.fp64_list[slot] : slot;
             const float4* rt = reinterpret_cast<const float4*>(v.rt + (size_t)h * 16);
-            const float4 r0 = rt[0], r1 = rt[1], r2 = rt[2], r3 = rt[3];
-            R[a][0] = r0.x; R[a][1] = r0.y; R[a][2] = r0.z; R[a][3] = r0.w;
-            R[a][4] = r1.x; R[a][5] = r1.y; R[a][6] = r1.z; R[a][7] = r1.w;
-            R[a][8] = r2.x; T[a][0] = r2.y; T[a][1] = r2.z; T[a][2] = r2.w;
-            ok = (__float_as_int(r3.y) & 1) != 0;
+            r0 = rt[0]; r1 = rt[1]; r2 = rt[2]; r3 = rt[3];
+            const int flags = __float_as_int(r3.y);
+            const bool ok = kList ? (flags & 1) != 0 : flags == 1;
+            if (!ok) r2.y = r2.z = r2.w = __int_as_float(0x7fc00000);   // NaN t: never an inlier
+        } else {
+            r2.y = r2.z = r2.w = __int_as_float(0x7fc00000);
         }
-        if (!ok) {
-            for (int c = 0; c < 9; ++c) R[a][c] = 0.f;
-            T[a][0] = T[a][1] = T[a][2] = __int_as_float(0x7fc00000);   // NaN: never an inlier
-        }
+        srt[threadIdx.x][0] = r0; srt[threadIdx.x][1] = r1; srt[threadIdx.x][2] = r2; srt[threadIdx.x][3] = r3;
     }
     __syncthreads();
+    // this lane's hypotheses: slots lane + 32 a, a = 0..3, as packed pairs (0,1), (2,3)
+    f2 R[2][9], T[2][3];
+#pragma unroll
+    for (int pr = 0; pr < 2; ++pr) {
+        const float* A = reinterpret_cast<const float*>(&srt[lane + 64 * pr][0]);
+        const float* B = reinterpret_cast<const float*>(&srt[lane + 64 * pr + 32][0]);
+#pragma unroll
+        for (int c = 0; c < 9; ++c) R[pr][c] = pk(A[c], B[c]);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) T[pr][c] = pk(A[9 + c], B[9 + c]);
+    }
     const float th2 = v.theta * v.theta;
-    int in[kVH] = {};
+    const int kb = warp * kVPtsWarp;
+    const int cnt = max(0, min(kVPtsWarp, v.n - k0 - kb));
+    int in[4] = {0, 0, 0, 0};
 #pragma unroll 2
     for (int k = 0; k < cnt; ++k) {
-        const float4 pa = sp[k][0], pb = sp[k][1];
+        const float4 pa = sp[kb + k][0], pb = sp[kb + k][1];
+        const f2 X0 = pk(pa.x, pa.x), X1 = pk(pa.y, pa.y), X2 = pk(pa.z, pa.z);
+        const f2 Y0 = pk(pa.w, pa.w), Y1 = pk(pb.x, pb.x), Y2 = pk(pb.y, pb.y);
 #pragma unroll
-        for (int a = 0; a < kVH; ++a) {
-            const float e0 = fmaf(R[a][0], pa.x, fmaf(R[a][1], pa.y, fmaf(R[a][2], pa.z, T[a][0] - pa.w)));
-            const float e1 = fmaf(R[a][3], pa.x, fmaf(R[a][4], pa.y, fmaf(R[a][5], pa.z, T[a][1] - pb.x)));
-            const float e2 = fmaf(R[a][6], pa.x, fmaf(R[a][7], pa.y, fmaf(R[a][8], pa.z, T[a][2] - pb.y)));
-            const float d2 = fmaf(e0, e0, fmaf(e1, e1, e2 * e2));
-            in[a] += d2 <= th2 ? 1 : 0;
+        for (int pr = 0; pr < 2; ++pr) {
+            const f2 e0 = fma2(R[pr][0], X0, fma2(R[pr][1], X1, fma2(R[pr][2], X2, sub2(T[pr][0], Y0))));
+            const f2 e1 = fma2(R[pr][3], X0, fma2(R[pr][4], X1, fma2(R[pr][5], X2, sub2(T[pr][1], Y1))));
+            const f2 e2 = fma2(R[pr][6], X0, fma2(R[pr][7], X1, fma2(R[pr][8], X2, sub2(T[pr][2], Y2))));
+            const f2 d2 = fma2(e0, e0, fma2(e1, e1, mul2(e2, e2)));
+            float lo, hi;
+            upk(d2, lo, hi);
+            in[2 * pr] += lo <= th2 ? 1 : 0;
+            in[2 * pr + 1] += hi <= th2 ? 1 : 0;
         }
     }
-#pragma unroll
-    for (int a = 0; a < kVH; ++a) {
-        const int h = h0 + threadIdx.x + a * kVThreads;
-        if (h < nh && in[a]) atomicAdd(&v.inl[h], in[a]);
-    }
+    scnt[warp][lane] = in[0];
+    scnt[warp][lane + 32] = in[1];
+    scnt[warp][lane + 64] = in[2];
+    scnt[warp][lane + 96] = in[3];
+    __syncthreads();
+    const int slot = h0 + threadIdx.x;
+    const int tot = scnt[0][threadIdx.x] + scnt[1][threadIdx.x] + scnt[2][threadIdx.x] + scnt[3][threadIdx.x];
+    if (slot < nh && tot) atomicAdd(&v.inl[kList ? v.fp64_list[slot] : slot], tot);
 }
 
 __global__ void __launch_bounds__(1024) finalize_kernel(ProbView v)
@@ -343,14 +419,21 @@ void launch_kabsch(const ProbView& v, cudaStream_t s)
 {
     const int cap = v.k1 * v.k2;
     kabsch_kernel<<<(cap + 127) / 128, 128, 0, s>>>(v);
-    kabsch_fp64_kernel<<<(cap + 31) / 32, 32, 0, s>>>(v);
 }
 
 void launch_verify(const ProbView& v, cudaStream_t s)
 {
     const int cap = v.k1 * v.k2;
     dim3 grid((cap + kVHyp - 1) / kVHyp, (v.n + kVPts - 1) / kVPts);
-    verify_kernel<<<grid, kVThreads, 0, s>>>(v);
+    verify_kernel<false><<<grid, 128, 0, s>>>(v);
+}
+
+void launch_kabsch_fp64_verify(const ProbView& v, cudaStream_t s)
+{
+    const int cap = v.k1 * v.k2;
+    kabsch_fp64_kernel<<<(cap + 31) / 32, 32, 0, s>>>(v);
+    dim3 grid((cap + kVHyp - 1) / kVHyp, (v.n + kVPts - 1) / kVPts);
+    verify_kernel<true><<<grid, 128, 0, s>>>(v);
 }
 
 void launch_finalize(const ProbView& v, cudaStream_t s) { finalize_kernel<<<1, 1024, 0, s>>>(v); }

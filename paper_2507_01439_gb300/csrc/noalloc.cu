@@ -6,9 +6,9 @@
 // that forbids allocation after start-up because cudaMalloc may synchronise
 // the device and take unbounded time.  turboreg_select_pivots_noalloc gives
 // them the pivot-selection stage with every scratch buffer it needs placed in
-// one fixed array in the library's own device memory (kScratchBytes, loaded
-// with the module and held by every GPU that loads the library until the
-// process exits).  The caller passes the weight matrix and the output buffers;
+// one fixed array in the library's own device memory (kScratchBytes, about
+// 225 KB, loaded with the module and held by every GPU that loads the library
+// until the process exits).  The caller passes the weight matrix and the output buffers;
 // nothing is allocated or freed, by this code or by any library it calls.
 //
 // The scratch is shared by every call: the histogram, the per-row tie counts
@@ -43,7 +43,9 @@ constexpr size_t kOffCtl = 0;
 constexpr size_t kOffHist = align256(sizeof(Ctl));
 constexpr size_t kOffRowcnt = kOffHist + align256(sizeof(uint32_t) * (kMaxN + 1));
 constexpr size_t kOffRowpref = kOffRowcnt + align256(sizeof(int32_t) * kMaxN);
-constexpr size_t kOffCand = kOffRowpref + align256(sizeof(int32_t) * kMaxN);
+constexpr size_t kOffRowcntGt = kOffRowpref + align256(sizeof(int32_t) * kMaxN);
+constexpr size_t kOffRowprefGt = kOffRowcntGt + align256(sizeof(int32_t) * kMaxN);
+constexpr size_t kOffCand = kOffRowprefGt + align256(sizeof(int32_t) * kMaxN);
 constexpr size_t kScratchBytes = kOffCand + align256(sizeof(uint64_t) * kMaxK1);
 
 static __device__ __align__(256) uint8_t g_pivot_scratch[kScratchBytes];
@@ -113,6 +115,8 @@ extern "C" int turboreg_select_pivots_noalloc(const uint16_t* w_dev, int32_t n, 
     v.hist = reinterpret_cast<uint32_t*>(scr + kOffHist);
     v.rowcnt = reinterpret_cast<int32_t*>(scr + kOffRowcnt);
     v.rowpref = reinterpret_cast<int32_t*>(scr + kOffRowpref);
+    v.rowcnt_gt = reinterpret_cast<int32_t*>(scr + kOffRowcntGt);
+    v.rowpref_gt = reinterpret_cast<int32_t*>(scr + kOffRowprefGt);
     v.cand = reinterpret_cast<uint64_t*>(scr + kOffCand);
     v.piv = reinterpret_cast<int4*>(pivots_dev);
 

@@ -39,19 +39,22 @@ __global__ void __launch_bounds__(256) pgs_kernel(ProbView v)
 #pragma unroll
     for (int r = 0; r < L; ++r) top[r] = 0ull;
 
-    const int zs = j + 1;
-    const int w0 = zs >> 5;
-    for (int wd = w0 + lane; wd < v.ldb; wd += 32) {
-        uint32_t m = bi[wd] & bj[wd];
-        if (wd == w0) m &= ~0u << (zs & 31);
-        while (m) {
-            const int b = __ffs(m) - 1;
-            m &= m - 1;
-            const int z = wd * 32 + b;
-            const int s = wij + static_cast<int>(wi[z]) + static_cast<int>(wj[z]);
-            const uint64_t key = (static_cast<uint64_t>(s) << 32) | (0xFFFFFFFFu - static_cast<uint32_t>(z));
-            // insertion into the descending list (keys are unique)
-            if (key > top[L - 1]) {
+    // candidate z are gathered 8 at a time so their 16 weight loads are in flight together
+    int zb[8];
+    int nz = 0;
+    auto flush = [&]() {
+        int wa[8], wb[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            wa[q] = q < nz ? static_cast<int>(wi[zb[q]]) : 0;
+            wb[q] = q < nz ? static_cast<int>(wj[zb[q]]) : 0;
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            if (q >= nz) break;
+            const int sz = wij + wa[q] + wb[q];
+            const uint64_t key = (static_cast<uint64_t>(sz) << 32) | (0xFFFFFFFFu - static_cast<uint32_t>(zb[q]));
+            if (key > top[L - 1]) {          // insertion into the descending list (keys are unique)
                 uint64_t cur = key;
 #pragma unroll
                 for (int r = 0; r < L; ++r) {
@@ -63,7 +66,20 @@ __global__ void __launch_bounds__(256) pgs_kernel(ProbView v)
                 }
             }
         }
+        nz = 0;
+    };
+    const int zs = j + 1;
+    const int w0 = zs >> 5;
+    for (int wd = w0 + lane; wd < v.ldb; wd += 32) {
+        uint32_t m = bi[wd] & bj[wd];
+        if (wd == w0) m &= ~0u << (zs & 31);
+        while (m) {
+            zb[nz++] = wd * 32 + __ffs(m) - 1;
+            m &= m - 1;
+            if (nz == 8) flush();
+        }
     }
+    if (nz) flush();
     // warp merge: k2 rounds of argmax over the lanes' list heads
     int head = 0;
     for (int r = 0; r < k2; ++r) {

@@ -23,6 +23,7 @@
 // adjacency bitset with AND + popcount on CUDA cores, one block per row.
 #include "tr_common.cuh"
 #include "tr_problem.h"
+#include "tr_select.cuh"
 
 namespace tr {
 
@@ -34,7 +35,7 @@ constexpr int kBBytes = kSc2BN * kSc2BK;   // 32 KB
 constexpr int kEpiWarps = 8;               // 2 per TMEM lane quarter, each half the columns
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr int kPipeBytes = kStages * (kABytes + kBBytes);
-constexpr int kBarBytes = 256;
+constexpr int kBarBytes = 512;            // mbarriers, TMEM slot, select scratch
 constexpr int kSmemMax = 232448;           // 227 KB opt-in limit per block
 constexpr uint32_t kTmemCols = 512;        // two 256-column FP32 accumulators
 // E4M3 x E4M3 -> F32, M = 128, N = 256, both K-major
@@ -73,6 +74,7 @@ sc2_tcgen05_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
     uint64_t* tfull = empty + kStages;      // [2] accumulator ready
     uint64_t* tempty = tfull + 2;           // [2] accumulator drained
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
+    int* sel_buf = reinterpret_cast<int*>(smem + kPipeBytes + 256);   // 33 ints + last-CTA flag
     uint32_t* shist = reinterpret_cast<uint32_t*>(smem + kPipeBytes + kBarBytes);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -233,6 +235,14 @@ sc2_tcgen05_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
         tc_fence_after();
         tmem_dealloc(tmem, kTmemCols);
     }
+    // the last CTA to finish sees the complete histogram: choose the pivot threshold
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) sel_buf[40] = atomicAdd(&v.ctl->done_blocks, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!sel_buf[40]) return;
+    __threadfence();
+    select_alpha(v, sel_buf);
 }
 
 // CUDA-core alternative: block per row i; W_ij = popc(row_i & row_j) for j > i with G_ij.

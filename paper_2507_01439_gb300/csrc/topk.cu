@@ -4,20 +4,22 @@
 // the threshold weight alpha broken by the lowest (i, j) (row-major linear
 // index), listed in (W desc, i asc, j asc) order.
 //
-// Exact radix-style selection in five passes over the upper triangle of W
-// (uint16, L2/HBM bound):
-//   hist    histogram of edge weights (shared-memory bins per block)
+// Exact radix-style selection (no atomics on shared counters, so the result
+// and its cost do not depend on contention):
+//   hist    histogram of edge weights (built by the SC^2 GEMM epilogue, or
+//           by hist_kernel for the CUDA-core SC^2 path)
 //   select  one block: alpha = K1-th largest weight, c_gt = #{W > alpha},
 //           m = K1' - c_gt ties still needed (K1' = min(K1, |E+|))
-//   collect warp per row: every W > alpha edge into a candidate slot (order
-//           free), and the number of W == alpha edges of the row
-//   scan    one block: exclusive prefix of the per-row tie counts
-//   emit    warp per row: the row's ties in column order get global tie
-//           ranks prefix[i] + rank-in-row; ranks < m are kept
+//   count   warp per row: #{j : W_ij > alpha} and #{j : W_ij == alpha}
+//   scan    one block: exclusive prefixes of both per-row counts
+//   emit    block per row that holds a selected edge: W > alpha edges go to
+//           slots prefix_gt[i] + rank-in-row; ties get global tie ranks
+//           prefix_eq[i] + rank-in-row (column order) and ranks < m are kept
 //   rank    candidate keys (W << 32 | ~(i*n+j)) are unique; each pivot's
 //           position is the number of larger keys.
 #include "tr_common.cuh"
 #include "tr_problem.h"
+#include "tr_select.cuh"
 
 namespace tr {
 
@@ -82,76 +84,15 @@ __global__ void __launch_bounds__(256) hist_kernel(ProbView v)
     }
 }
 
-// block-wide inclusive scan of one int per thread (blockDim.x = 1024)
-__device__ __forceinline__ int block_incl_scan(int x, int* sbuf)
-{
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, x, off);
-        if (lane >= off) x += y;
-    }
-    if (lane == 31) sbuf[warp] = x;
-    __syncthreads();
-    if (warp == 0) {
-        int s = (lane < (int)(blockDim.x >> 5)) ? sbuf[lane] : 0;
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, s, off);
-            if (lane >= off) s += y;
-        }
-        sbuf[lane] = s;
-    }
-    __syncthreads();
-    const int r = x + (warp > 0 ? sbuf[warp - 1] : 0);
-    __syncthreads();
-    return r;
-}
-
 __global__ void __launch_bounds__(1024) select_kernel(ProbView v)
 {
-    __shared__ int sbuf[32];
-    const int nb = v.n;                       // weights 1..n (W <= n - 2)
-    const int per = (nb + blockDim.x - 1) / blockDim.x;
-    // thread t owns weights (hi - per, hi], hi = n - t*per, scanned from the top
-    const int hi = nb - static_cast<int>(threadIdx.x) * per;
-    int mine = 0;
-    for (int q = 0; q < per; ++q) {
-        const int wv = hi - q;
-        if (wv >= 1) mine += static_cast<int>(v.hist[wv]);
-    }
-    const int incl = block_incl_scan(mine, sbuf);
-    __shared__ int total;
-    if (threadIdx.x == blockDim.x - 1) total = incl;
-    __syncthreads();
-    const int n_edges = total;
-    const int n_sel = n_edges < v.k1 ? n_edges : v.k1;
-    if (threadIdx.x == 0) {
-        v.ctl->n_edges = n_edges;
-        v.ctl->n_sel = n_sel;
-        v.ctl->gt_slot = 0;
-        if (n_sel == 0) { v.ctl->alpha = 0x7FFFFFFF; v.ctl->c_gt = 0; v.ctl->m_ties = 0; }
-    }
-    if (n_sel == 0) return;
-    const int excl = incl - mine;
-    if (excl < n_sel && n_sel <= incl) {
-        int run = excl;
-        for (int q = 0; q < per; ++q) {
-            const int wv = hi - q;
-            if (wv < 1) break;
-            const int h = static_cast<int>(v.hist[wv]);
-            if (run + h >= n_sel) {
-                v.ctl->alpha = wv;
-                v.ctl->c_gt = run;
-                v.ctl->m_ties = n_sel - run;
-                break;
-            }
-            run += h;
-        }
-    }
+    __shared__ int sbuf[33];
+    select_alpha(v, sbuf);
 }
 
-__global__ void __launch_bounds__(256) collect_kernel(ProbView v)
+// per-row counts of the weight > alpha and weight == alpha edges
+// Per-row counts of the weight > alpha and weight == alpha edges.
+__global__ void __launch_bounds__(256) count_kernel(ProbView v)
 {
     const int lane = threadIdx.x & 31;
     const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -159,80 +100,128 @@ __global__ void __launch_bounds__(256) collect_kernel(ProbView v)
     if (v.ctl->n_sel == 0) return;
     const int alpha = v.ctl->alpha;
     for (int i = wid; i < v.n; i += nw) {
-        int ties = 0;
-        for_row_chunks(v, i, lane, [&](int j, int w) {
-            if (w > alpha) {
-                const uint32_t slot = atomicAdd(&v.ctl->gt_slot, 1u);
-                if (slot < static_cast<uint32_t>(v.k1)) v.cand[slot] = edge_key(w, i, j, v.n);
-                else atomicOr(&v.ctl->err, TR_ERR_OVERFLOW);
-            } else if (w == alpha) {
-                ++ties;
-            }
+        int gt = 0, eq = 0;
+        for_row_chunks(v, i, lane, [&](int, int w) {
+            gt += w > alpha;
+            eq += w == alpha;
         });
 #pragma unroll
-        for (int off = 16; off >= 1; off >>= 1) ties += __shfl_xor_sync(0xffffffffu, ties, off);
-        if (lane == 0) v.rowcnt[i] = ties;
+        for (int off = 16; off >= 1; off >>= 1) {
+            gt += __shfl_xor_sync(0xffffffffu, gt, off);
+            eq += __shfl_xor_sync(0xffffffffu, eq, off);
+        }
+        if (lane == 0) {
+            v.rowcnt[i] = eq;
+            v.rowcnt_gt[i] = gt;
+        }
     }
 }
 
+// Exclusive prefixes of both per-row counts; thread t owns rows
+// [t*per, (t+1)*per), per <= 32, loaded with all loads in flight.
 __global__ void __launch_bounds__(1024) scan_rows_kernel(ProbView v)
 {
-    __shared__ int sbuf[32];
+    __shared__ int sbuf[33];
     if (v.ctl->n_sel == 0) return;
     const int per = (v.n + blockDim.x - 1) / blockDim.x;
     const int lo = threadIdx.x * per;
-    int mine = 0;
-    for (int q = 0; q < per; ++q)
-        if (lo + q < v.n) mine += v.rowcnt[lo + q];
-    const int incl = block_incl_scan(mine, sbuf);
-    int run = incl - mine;
-    for (int q = 0; q < per; ++q)
-        if (lo + q < v.n) { v.rowpref[lo + q] = run; run += v.rowcnt[lo + q]; }
+    int se = 0, sg = 0;
+#pragma unroll
+    for (int q = 0; q < 32; ++q) {
+        if (q < per && lo + q < v.n) {
+            se += v.rowcnt[lo + q];
+            sg += v.rowcnt_gt[lo + q];
+        }
+    }
+    const int ie = block_incl_scan(se, sbuf);
+    const int ig = block_incl_scan(sg, sbuf);
+    int re = ie - se, rg = ig - sg;
+#pragma unroll
+    for (int q = 0; q < 32; ++q) {
+        if (q < per && lo + q < v.n) {
+            const int a = v.rowcnt[lo + q], b = v.rowcnt_gt[lo + q];
+            v.rowpref[lo + q] = re;
+            v.rowpref_gt[lo + q] = rg;
+            re += a;
+            rg += b;
+        }
+    }
 }
 
-__global__ void __launch_bounds__(256) emit_ties_kernel(ProbView v)
+// One block (256 threads) per row; a thread takes 16-byte chunks tid, tid+256, ...
+// (all of a 32K-wide row's loads are in flight at once).  Blocks whose row
+// holds nothing selected exit at once.
+__global__ void __launch_bounds__(256) emit_kernel(ProbView v)
 {
-    const int lane = threadIdx.x & 31;
-    const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nw = (gridDim.x * blockDim.x) >> 5;
+    __shared__ int sg[8], se[8];
     if (v.ctl->n_sel == 0) return;
-    const int alpha = v.ctl->alpha, m = v.ctl->m_ties, c_gt = v.ctl->c_gt;
-    for (int i = wid; i < v.n; i += nw) {
-        if (v.rowcnt[i] == 0 || v.rowpref[i] >= m) continue;
-        int base = v.rowpref[i];
-        const uint16_t* wrow = v.w + (size_t)i * v.n_pad;
-        const int c0 = (i + 1) >> 3, c1 = (v.n - 1) >> 3;
-        // chunk-major sweep in column order: the warp covers 32 chunks (256 columns) per step
-        for (int cb = c0; cb <= c1 && base < m; cb += 32) {
-            const int c = cb + lane;
-            uint32_t tmask = 0;
-            if (c <= c1) {
-                const uint4 q = *reinterpret_cast<const uint4*>(wrow + c * 8);
-                const uint32_t u[4] = {q.x, q.y, q.z, q.w};
+    const int i = blockIdx.x;
+    if (i + 1 >= v.n) return;
+    const int m = v.ctl->m_ties;
+    const int ng = v.rowcnt_gt[i];
+    const int ne = v.rowcnt[i];
+    const int pe = v.rowpref[i];
+    const bool want_eq = ne > 0 && pe < m;
+    if (ng == 0 && !want_eq) return;
+    const int alpha = v.ctl->alpha, c_gt = v.ctl->c_gt;
+    const int pg = v.rowpref_gt[i];
+    const uint16_t* wrow = v.w + (size_t)i * v.n_pad;
+    const int c0 = (i + 1) >> 3, c1 = (v.n - 1) >> 3;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int base_g = pg, base_e = pe;
+    for (int cb = c0; cb <= c1; cb += blockDim.x * 4) {
+        // 4 consecutive chunks per thread per sweep keep column order within the thread
+        uint32_t gm = 0, em = 0;   // bit 8*k + e: chunk k, element e
+        const int cfirst = cb + threadIdx.x * 4;
 #pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    const int j = c * 8 + e;
-                    const int w = (u[e >> 1] >> ((e & 1) * 16)) & 0xFFFF;
-                    if (j > i && j < v.n && w == alpha) tmask |= 1u << e;
-                }
-            }
-            const int cnt = __popc(tmask);
-            int pre = cnt;
+        for (int k = 0; k < 4; ++k) {
+            const int c = cfirst + k;
+            if (c > c1) break;
+            const uint4 q = *reinterpret_cast<const uint4*>(wrow + c * 8);
+            const uint32_t u[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
-            for (int off = 1; off < 32; off <<= 1) {
-                const int y = __shfl_up_sync(0xffffffffu, pre, off);
-                if (lane >= off) pre += y;
+            for (int e = 0; e < 8; ++e) {
+                const int j = c * 8 + e;
+                const int w = (u[e >> 1] >> ((e & 1) * 16)) & 0xFFFF;
+                const bool in = j > i && j < v.n;
+                gm |= static_cast<uint32_t>(in && w > alpha) << (8 * k + e);
+                em |= static_cast<uint32_t>(in && w == alpha) << (8 * k + e);
             }
-            const int tot = __shfl_sync(0xffffffffu, pre, 31);
-            int r = base + pre - cnt;
-            while (tmask) {
-                const int e = __ffs(tmask) - 1;
-                tmask &= tmask - 1;
-                if (r < m) v.cand[c_gt + r] = edge_key(alpha, i, c * 8 + e, v.n);
-                ++r;
-            }
-            base += tot;
         }
+        // block exclusive scans of the two counts (thread order = column order)
+        int g = __popc(gm), eN = __popc(em);
+        int gi = g, ei = eN;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int a = __shfl_up_sync(0xffffffffu, gi, off);
+            const int b = __shfl_up_sync(0xffffffffu, ei, off);
+            if (lane >= off) { gi += a; ei += b; }
+        }
+        if (lane == 31) { sg[warp] = gi; se[warp] = ei; }
+        __syncthreads();
+        int wg = 0, we = 0, tg = 0, te = 0;
+        for (int w8 = 0; w8 < 8; ++w8) {
+            if (w8 < warp) { wg += sg[w8]; we += se[w8]; }
+            tg += sg[w8];
+            te += se[w8];
+        }
+        __syncthreads();
+        int rg = base_g + wg + gi - g, re = base_e + we + ei - eN;
+        while (gm) {
+            const int b = __ffs(gm) - 1;
+            gm &= gm - 1;
+            const int j = (cfirst + (b >> 3)) * 8 + (b & 7);
+            v.cand[rg++] = edge_key((wrow[j]), i, j, v.n);
+        }
+        while (em) {
+            const int b = __ffs(em) - 1;
+            em &= em - 1;
+            if (re < m) v.cand[c_gt + re] = edge_key(alpha, i, (cfirst + (b >> 3)) * 8 + (b & 7), v.n);
+            ++re;
+        }
+        base_g += tg;
+        base_e += te;
+        if (base_g - pg >= ng && (!want_eq || base_e >= m || base_e - pe >= ne)) break;
     }
 }
 
@@ -253,7 +242,7 @@ __global__ void __launch_bounds__(256) rank_kernel(ProbView v)
     const int chunk = (n_sel + 7) / 8;
     const int f0 = warp * chunk, f1 = min(n_sel, f0 + chunk);
     int cnt = 0;
-#pragma unroll 4
+#pragma unroll 8
     for (int f = f0; f < f1; ++f) cnt += sk[f] > key;
     part[warp][lane] = cnt;
     __syncthreads();
@@ -286,14 +275,19 @@ cudaError_t topk_setup()
                                 kHistSmemMaxBins * 4);
 }
 
-void launch_topk_after_hist(const ProbView& v, cudaStream_t s)
+void launch_topk_after_select(const ProbView& v, cudaStream_t s)
 {
     const int row_blocks = (v.n + 7) / 8;   // one row per warp
-    select_kernel<<<1, 1024, 0, s>>>(v);
-    collect_kernel<<<row_blocks, 256, 0, s>>>(v);
+    count_kernel<<<row_blocks, 256, 0, s>>>(v);
     scan_rows_kernel<<<1, 1024, 0, s>>>(v);
-    emit_ties_kernel<<<row_blocks, 256, 0, s>>>(v);
+    emit_kernel<<<v.n, 256, 0, s>>>(v);
     rank_kernel<<<(v.k1 + 31) / 32, 256, v.k1 * 8, s>>>(v);
+}
+
+void launch_topk_after_hist(const ProbView& v, cudaStream_t s)
+{
+    select_kernel<<<1, 1024, 0, s>>>(v);
+    launch_topk_after_select(v, s);
 }
 
 void launch_topk(const ProbView& v, cudaStream_t s)

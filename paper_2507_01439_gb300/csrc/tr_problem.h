@@ -32,6 +32,8 @@ struct ProbView {
     uint32_t* hist;      // [n_pad + 1] histogram of O2Graph edge weights
     int32_t* rowcnt;     // [n_pad] per-row count of edges with weight == alpha
     int32_t* rowpref;    // [n_pad] exclusive prefix of rowcnt
+    int32_t* rowcnt_gt;  // [n_pad] per-row count of edges with weight > alpha
+    int32_t* rowpref_gt; // [n_pad] exclusive prefix of rowcnt_gt
     uint64_t* cand;      // [K1_MAX] selected edge keys (weight << 32 | ~(i*n+j))
     int4* piv;           // [K1_MAX] pivots (i, j, w, 0) in Eq. 4 order
     int4* cliques;       // [K1_MAX*K2_MAX] (i, j, z, valid) in Alg. 2 order
@@ -50,9 +52,11 @@ void launch_sc2_tcgen05(const ProbView& v, const CUtensorMap& tmA, const CUtenso
 void launch_sc2_bitset(const ProbView& v, cudaStream_t s);
 void launch_topk(const ProbView& v, cudaStream_t s);             // histogram pass + selection
 void launch_topk_after_hist(const ProbView& v, cudaStream_t s);  // selection (histogram already built)
+void launch_topk_after_select(const ProbView& v, cudaStream_t s);  // selection (alpha already chosen)
 void launch_pgs(const ProbView& v, cudaStream_t s);
-void launch_kabsch(const ProbView& v, cudaStream_t s);
-void launch_verify(const ProbView& v, cudaStream_t s);
+void launch_kabsch(const ProbView& v, cudaStream_t s);             // FP32 closed form, FP64 list
+void launch_verify(const ProbView& v, cudaStream_t s);             // hypotheses with a valid FP32 Kabsch
+void launch_kabsch_fp64_verify(const ProbView& v, cudaStream_t s); // FP64 list: Kabsch + verification
 void launch_finalize(const ProbView& v, cudaStream_t s);
 
 // set kernel attributes (dynamic shared memory limits) once per device

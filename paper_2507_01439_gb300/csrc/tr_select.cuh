@@ -1,0 +1,91 @@
+// Threshold step of the exact top-K1 pivot selection (Eq. 4), shared by the
+// standalone select kernel and the last CTA of the SC^2 GEMM.
+#pragma once
+
+#include "tr_common.cuh"
+#include "tr_problem.h"
+
+namespace tr {
+
+// Block-wide inclusive scan of one int per thread (blockDim.x a multiple of
+// 32, at most 1024); sbuf holds 33 ints of shared memory.
+__device__ __forceinline__ int block_incl_scan(int x, int* sbuf)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = static_cast<int>(blockDim.x >> 5);
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, off);
+        if (lane >= off) x += y;
+    }
+    if (lane == 31) sbuf[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int t = lane < nwarps ? sbuf[lane] : 0;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, t, off);
+            if (lane >= off) t += y;
+        }
+        sbuf[lane] = t;
+    }
+    __syncthreads();
+    const int r = x + (warp > 0 ? sbuf[warp - 1] : 0);
+    __syncthreads();
+    return r;
+}
+
+// From the weight histogram: |E+|, n_sel = min(K1, |E+|), alpha = the K1-th
+// largest weight, c_gt = #{W > alpha}, m = n_sel - c_gt ties still needed.
+// Every thread of the block must call it.
+__device__ __forceinline__ void select_alpha(const ProbView& v, int* sbuf)
+{
+    const int nb = v.n;                       // weights 1..n (W <= n - 2)
+    const int per = (nb + blockDim.x - 1) / blockDim.x;
+    // thread t owns weights (hi - per, hi], hi = n - t*per, scanned from the top
+    const int hi = nb - static_cast<int>(threadIdx.x) * per;
+    int mine = 0;
+    for (int q0 = 0; q0 < per; q0 += 8) {       // 8 loads in flight per step
+        uint32_t h8[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int wv = hi - q0 - q;
+            h8[q] = (q0 + q < per && wv >= 1) ? v.hist[wv] : 0u;
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) mine += static_cast<int>(h8[q]);
+    }
+    const int incl = block_incl_scan(mine, sbuf);
+    if (threadIdx.x == blockDim.x - 1) sbuf[32] = incl;
+    __syncthreads();
+    const int n_edges = sbuf[32];
+    const int n_sel = n_edges < v.k1 ? n_edges : v.k1;
+    if (threadIdx.x == 0) {
+        v.ctl->n_edges = n_edges;
+        v.ctl->n_sel = n_sel;
+        if (n_sel == 0) {
+            v.ctl->alpha = 0x7FFFFFFF;
+            v.ctl->c_gt = 0;
+            v.ctl->m_ties = 0;
+        }
+    }
+    if (n_sel == 0) return;
+    const int excl = incl - mine;
+    if (excl < n_sel && n_sel <= incl) {
+        int run = excl;
+        for (int q = 0; q < per; ++q) {
+            const int wv = hi - q;
+            if (wv < 1) break;
+            const int h = static_cast<int>(v.hist[wv]);
+            if (run + h >= n_sel) {
+                v.ctl->alpha = wv;
+                v.ctl->c_gt = run;
+                v.ctl->m_ties = n_sel - run;
+                break;
+            }
+            run += h;
+        }
+    }
+}
+
+}  // namespace tr
