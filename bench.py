@@ -37,11 +37,13 @@ UNIT = "registrations/s"
 WORKLOAD = {"workload": "indoor-shaped single problem", "n": 5000, "inlier_ratio": 0.05, "sigma_m": 0.01,
             "tau_m": 0.1, "k1": 2000, "k2": 2, "inlier_thresh_m": 0.1, "problems_cycled": 8,
             "l2": "flushed between timed steps (256 MB write, outside the events)"}
-# kernels of ours launched per registration: pack, compat, sc2, hist, select, collect,
-# scan, emit, rank, pgs, kabsch, verify, finalize
+# kernels of ours launched per registration: pack, compat, sc2 (with the histogram and
+# the threshold choice), count, scan, emit, rank, pgs, kabsch, kabsch_fp64, verify (main
+# and FP64 list), finalize
 LAUNCHES_PER_STEP = 13
-# ncu per-launch DRAM traffic (bytes) of the SC^2 kernel on this workload; None until captured
-SC2_DRAM_BYTES = None
+# DRAM bytes (read + write) of one SC^2 kernel launch on this workload, from one ncu
+# capture of the current kernel (profiles/sc2_tcgen05_indoor5000.txt)
+SC2_DRAM_BYTES = 28328704
 
 
 def _peaks():
