@@ -1,8 +1,12 @@
 // Host runtime and C ABI of the GB300 TurboReg library (see include/turboreg.h).
 //
-// A context owns one device workspace sized for max_n at creation; register
-// calls only enqueue kernels on the context's stream, copy the 88-byte result
-// back and synchronise.  No host round trip happens between stages: pivot
+// A context owns a device workspace sized at creation: max_batch problem
+// slots, each sized for max_n.  A register call builds a plan (per-problem
+// views, per-stage block prefixes, tensor maps), enqueues one launch per
+// stage for all of its problems on the context's stream, copies the 88-byte
+// results back and synchronises.  The enqueued pipeline is captured once per
+// plan shape as a CUDA graph and replayed; the pack node's input pointers are
+// patched per call.  No host round trip happens between stages: pivot
 // counts, thresholds and validity stay on the device (Ctl block).
 #include <cuda.h>
 #include <cuda_runtime.h>
@@ -12,6 +16,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "tr_common.cuh"
 #include "tr_problem.h"
@@ -24,6 +29,7 @@ namespace {
 
 constexpr int kNumStages = 8;
 const char* kStageNames[kNumStages] = {"pack", "compat", "sc2", "topk", "pgs", "kabsch", "verify", "finalize"};
+constexpr int kGraphSlots = 8;
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
@@ -31,31 +37,51 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
 
 inline int32_t round_up(int32_t a, int32_t b) { return (a + b - 1) / b * b; }
 
+// Per-slot workspace: slot s of every buffer starts at s * (per-slot size).
 struct Workspace {
-    int32_t n_pad_max = 0;
-    float* pts = nullptr;
-    float* pts8 = nullptr;
-    int32_t* fp64_list = nullptr;
-    uint8_t* a8 = nullptr;
-    uint32_t* bits = nullptr;
-    uint16_t* w = nullptr;
-    int32_t* rowscore = nullptr;
-    int32_t* deg = nullptr;
-    uint32_t* hist = nullptr;
-    int32_t* rowcnt = nullptr;
-    int32_t* rowpref = nullptr;
-    int32_t* rowcnt_gt = nullptr;
-    int32_t* rowpref_gt = nullptr;
-    uint64_t* cand = nullptr;
-    int4* piv = nullptr;
-    int4* cliques = nullptr;
-    float* rt = nullptr;
-    int32_t* inl = nullptr;
-    Ctl* ctl = nullptr;
-    turboreg_result* res = nullptr;   // [max_batch]
-    float* in_src = nullptr;          // staging for host inputs [max_n*max_batch*3]
+    int32_t slots = 0;
+    int32_t np = 0;          // n_pad of max_n
+    size_t nh = 0;           // K1_MAX * K2_MAX
+    float* pts = nullptr;            // [slots][6 np]
+    float* pts8 = nullptr;           // [slots][8 np]
+    uint8_t* a8 = nullptr;           // [slots][np^2]
+    uint32_t* bits = nullptr;        // [slots][np^2 / 32]
+    uint16_t* w = nullptr;           // [slots][np^2]
+    int32_t* rows = nullptr;         // [slots][6][np]: rowscore, deg, rowcnt, rowpref, rowcnt_gt, rowpref_gt
+    uint32_t* hist = nullptr;        // [slots][np + 1]
+    uint64_t* cand = nullptr;        // [slots][K1_MAX]
+    int4* piv = nullptr;             // [slots][K1_MAX]
+    int4* cliques = nullptr;         // [slots][nh]
+    float* rt = nullptr;             // [slots][nh * 16]
+    int32_t* inl = nullptr;          // [slots][nh]
+    int32_t* fp64_list = nullptr;    // [slots][nh]
+    Ctl* ctl = nullptr;              // [slots]
+    turboreg_result* res = nullptr;  // [slots]
+    float* in_src = nullptr;         // staging for host inputs [max_n * slots * 3]
     float* in_dst = nullptr;
+    // descriptors for direct (non-graph) launches, and pinned host mirrors
+    uint8_t* desc = nullptr;
+    ProbView* h_views = nullptr;
+    int32_t* h_pre = nullptr;
+    CUtensorMap* h_maps = nullptr;
+    int32_t* map_npad = nullptr;     // host: n_pad each slot's maps were encoded for
+    CUtensorMap* map_cache = nullptr;  // host: encoded maps per slot
 };
+
+// A plan: the problems of one call (in slots 0..num-1) and per-stage block totals.
+struct Plan {
+    int32_t num = 0;
+    int32_t max_n = 0, max_k1 = 0, k2_common = 0;
+    int32_t bitset = 0, timed = 0;
+    int32_t tot[kNumBatchStages] = {};
+};
+
+size_t desc_bytes(int32_t num)
+{
+    const size_t v = sizeof(ProbView) * num;
+    const size_t p = sizeof(int32_t) * kNumBatchStages * (num + 1);
+    return (v + 127) / 128 * 128 + (p + 127) / 128 * 128 + sizeof(CUtensorMap) * 2 * num;
+}
 
 }  // namespace
 
@@ -64,49 +90,44 @@ struct turboreg_ctx {
     int32_t max_n = 0, max_batch = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
-    cudaStream_t side = nullptr;               // FP64 Kabsch + its verification run here,
+    cudaStream_t side = nullptr;                       // FP64 Kabsch + its verification run here,
     cudaEvent_t fork_ev = nullptr, join_ev = nullptr;  // concurrently with the main verification
     Workspace ws;
     turboreg_result* host_res = nullptr;   // pinned [max_batch]
     EncodeTiledFn encode = nullptr;
-    CUtensorMap tmA, tmB;
-    int32_t tm_npad = 0;
     cudaEvent_t ev[kNumStages + 1] = {};
     float stage_ms[kNumStages] = {};
     int32_t last_n = 0, last_npad = 0, last_k1 = 0, last_k2 = 0;
     bool have_times = false;
-    // captured per-problem pipelines, replayed with cudaGraphLaunch; only the
-    // pack node's input pointers change between calls
+    // Captured pipelines.  Each slot owns a private copy of its descriptors in
+    // device memory, so replays of different shapes never see each other's.
     struct GraphSlot {
         bool used = false;
-        int32_t n = 0, k1 = 0, k2 = 0;
-        float tau = 0.f, theta = 0.f, kappa = 0.f;
-        uint32_t flags = 0;
-        turboreg_result* res = nullptr;
+        std::vector<uint8_t> key;          // plan signature
         cudaGraph_t graph = nullptr;
         cudaGraphExec_t exec = nullptr;
         cudaGraphNode_t pack_node = nullptr;
         cudaKernelNodeParams pack_params = {};
-        tr::ProbView pv = {};
+        tr::Batch batch = {};
         const float* src = nullptr;
         const float* dst = nullptr;
         void* args[3] = {};
+        void* desc = nullptr;
         uint64_t stamp = 0;
     };
-    static constexpr int kGraphSlots = 8;
     GraphSlot gslot[kGraphSlots];
     uint64_t gclock = 0;
 };
 
 namespace {
 
-#define TR_CHECK(expr)                                      \
-    do {                                                    \
-        cudaError_t e_ = (expr);                            \
-        if (e_ != cudaSuccess) {                            \
-            std::fprintf(stderr, "turboreg: %s failed: %s\n", #expr, cudaGetErrorString(e_)); \
-            return TURBOREG_ERR_CUDA;                       \
-        }                                                   \
+#define TR_CHECK(expr)                                                                         \
+    do {                                                                                       \
+        cudaError_t e_ = (expr);                                                               \
+        if (e_ != cudaSuccess) {                                                               \
+            std::fprintf(stderr, "turboreg: %s failed: %s\n", #expr, cudaGetErrorString(e_));  \
+            return TURBOREG_ERR_CUDA;                                                          \
+        }                                                                                      \
     } while (0)
 
 template <typename T>
@@ -115,78 +136,67 @@ cudaError_t dalloc(T** p, size_t count)
     return cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T) + 256);
 }
 
+template <typename T>
+cudaError_t halloc(T** p, size_t count)
+{
+    return cudaMallocHost(reinterpret_cast<void**>(p), count * sizeof(T) + 64);
+}
+
 void free_ws(Workspace& ws)
 {
-    void* ptrs[] = {ws.pts, ws.pts8, ws.fp64_list, ws.a8, ws.bits, ws.w, ws.rowscore, ws.deg, ws.hist, ws.rowcnt, ws.rowpref, ws.rowcnt_gt, ws.rowpref_gt,
-                    ws.cand, ws.piv, ws.cliques, ws.rt, ws.inl, ws.ctl, ws.res, ws.in_src, ws.in_dst};
-    for (void* p : ptrs)
+    void* dptrs[] = {ws.pts, ws.pts8, ws.a8, ws.bits, ws.w, ws.rows, ws.hist, ws.cand, ws.piv, ws.cliques,
+                     ws.rt, ws.inl, ws.fp64_list, ws.ctl, ws.res, ws.in_src, ws.in_dst, ws.desc};
+    for (void* p : dptrs)
         if (p) cudaFree(p);
+    void* hptrs[] = {ws.h_views, ws.h_pre, ws.h_maps};
+    for (void* p : hptrs)
+        if (p) cudaFreeHost(p);
+    std::free(ws.map_npad);
+    std::free(ws.map_cache);
     ws = Workspace();
 }
 
-int alloc_ws(Workspace& ws, int32_t max_n, int32_t max_batch)
+int alloc_ws(Workspace& ws, int32_t max_n, int32_t slots)
 {
     const int32_t np = round_up(max_n, kSc2BN);
     const size_t n2 = static_cast<size_t>(np) * np;
     const size_t nh = static_cast<size_t>(TURBOREG_K1_MAX) * TURBOREG_K2_MAX;
-    const size_t tot = static_cast<size_t>(max_n) * max_batch;
-    ws.n_pad_max = np;
+    const size_t S = static_cast<size_t>(slots);
+    ws.slots = slots;
+    ws.np = np;
+    ws.nh = nh;
     cudaError_t e = cudaSuccess;
-    if (e == cudaSuccess) e = dalloc(&ws.pts, 6 * static_cast<size_t>(np));
-    if (e == cudaSuccess) e = dalloc(&ws.pts8, 8 * static_cast<size_t>(np));
-    if (e == cudaSuccess) e = dalloc(&ws.fp64_list, nh);
-    if (e == cudaSuccess) e = dalloc(&ws.a8, n2);
-    if (e == cudaSuccess) e = dalloc(&ws.bits, n2 / 32);
-    if (e == cudaSuccess) e = dalloc(&ws.w, n2);
-    if (e == cudaSuccess) e = dalloc(&ws.rowscore, np);
-    if (e == cudaSuccess) e = dalloc(&ws.deg, np);
-    if (e == cudaSuccess) e = dalloc(&ws.hist, np + 1);
-    if (e == cudaSuccess) e = dalloc(&ws.rowcnt, np);
-    if (e == cudaSuccess) e = dalloc(&ws.rowpref, np);
-    if (e == cudaSuccess) e = dalloc(&ws.rowcnt_gt, np);
-    if (e == cudaSuccess) e = dalloc(&ws.rowpref_gt, np);
-    if (e == cudaSuccess) e = dalloc(&ws.cand, TURBOREG_K1_MAX);
-    if (e == cudaSuccess) e = dalloc(&ws.piv, TURBOREG_K1_MAX);
-    if (e == cudaSuccess) e = dalloc(&ws.cliques, nh);
-    if (e == cudaSuccess) e = dalloc(&ws.rt, nh * 16);
-    if (e == cudaSuccess) e = dalloc(&ws.inl, nh);
-    if (e == cudaSuccess) e = dalloc(&ws.ctl, 1);
-    if (e == cudaSuccess) e = dalloc(&ws.res, max_batch);
-    if (e == cudaSuccess) e = dalloc(&ws.in_src, tot * 3);
-    if (e == cudaSuccess) e = dalloc(&ws.in_dst, tot * 3);
+    if (e == cudaSuccess) e = dalloc(&ws.pts, S * 6 * np);
+    if (e == cudaSuccess) e = dalloc(&ws.pts8, S * 8 * np);
+    if (e == cudaSuccess) e = dalloc(&ws.a8, S * n2);
+    if (e == cudaSuccess) e = dalloc(&ws.bits, S * n2 / 32);
+    if (e == cudaSuccess) e = dalloc(&ws.w, S * n2);
+    if (e == cudaSuccess) e = dalloc(&ws.rows, S * 6 * np);
+    if (e == cudaSuccess) e = dalloc(&ws.hist, S * (np + 1));
+    if (e == cudaSuccess) e = dalloc(&ws.cand, S * TURBOREG_K1_MAX);
+    if (e == cudaSuccess) e = dalloc(&ws.piv, S * TURBOREG_K1_MAX);
+    if (e == cudaSuccess) e = dalloc(&ws.cliques, S * nh);
+    if (e == cudaSuccess) e = dalloc(&ws.rt, S * nh * 16);
+    if (e == cudaSuccess) e = dalloc(&ws.inl, S * nh);
+    if (e == cudaSuccess) e = dalloc(&ws.fp64_list, S * nh);
+    if (e == cudaSuccess) e = dalloc(&ws.ctl, S);
+    if (e == cudaSuccess) e = dalloc(&ws.res, S);
+    if (e == cudaSuccess) e = dalloc(&ws.in_src, S * max_n * 3);
+    if (e == cudaSuccess) e = dalloc(&ws.in_dst, S * max_n * 3);
+    if (e == cudaSuccess) e = dalloc(&ws.desc, desc_bytes(slots));
+    if (e == cudaSuccess) e = halloc(&ws.h_views, S);
+    if (e == cudaSuccess) e = halloc(&ws.h_pre, static_cast<size_t>(kNumBatchStages) * (S + 1));
+    if (e == cudaSuccess) e = halloc(&ws.h_maps, 2 * S);
+    if (e == cudaSuccess) {
+        ws.map_npad = static_cast<int32_t*>(std::calloc(S, sizeof(int32_t)));
+        ws.map_cache = static_cast<CUtensorMap*>(std::calloc(2 * S, sizeof(CUtensorMap)));
+        if (!ws.map_npad || !ws.map_cache) e = cudaErrorMemoryAllocation;
+    }
     if (e != cudaSuccess) {
         cudaGetLastError();
         free_ws(ws);
         return e == cudaErrorMemoryAllocation ? TURBOREG_ERR_OOM : TURBOREG_ERR_CUDA;
     }
-    // zero the FP8 adjacency and W once so padding is defined even before the first call
-    if (cudaMemset(ws.a8, 0, n2) != cudaSuccess || cudaMemset(ws.w, 0, n2 * 2) != cudaSuccess) {
-        free_ws(ws);
-        return TURBOREG_ERR_CUDA;
-    }
-    return TURBOREG_OK;
-}
-
-int encode_maps(turboreg_ctx* c, int32_t n_pad)
-{
-    if (c->tm_npad == n_pad) return TURBOREG_OK;
-    const cuuint64_t dims[2] = {static_cast<cuuint64_t>(n_pad), static_cast<cuuint64_t>(n_pad)};
-    const cuuint64_t strides[1] = {static_cast<cuuint64_t>(n_pad)};   // bytes between rows
-    const cuuint32_t boxA[2] = {static_cast<cuuint32_t>(kSc2BK), static_cast<cuuint32_t>(kSc2BM)};
-    const cuuint32_t boxB[2] = {static_cast<cuuint32_t>(kSc2BK), static_cast<cuuint32_t>(kSc2BN)};
-    const cuuint32_t estr[2] = {1, 1};
-    CUresult r1 = c->encode(&c->tmA, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, c->ws.a8, dims, strides, boxA, estr,
-                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    CUresult r2 = c->encode(&c->tmB, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, c->ws.a8, dims, strides, boxB, estr,
-                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r1 != CUDA_SUCCESS || r2 != CUDA_SUCCESS) {
-        std::fprintf(stderr, "turboreg: cuTensorMapEncodeTiled failed (%d, %d)\n", (int)r1, (int)r2);
-        c->tm_npad = 0;
-        return TURBOREG_ERR_CUDA;
-    }
-    c->tm_npad = n_pad;
     return TURBOREG_OK;
 }
 
@@ -222,10 +232,21 @@ bool host_finite(const float* p, size_t cnt)
     return true;
 }
 
-ProbView make_view(turboreg_ctx* c, int32_t n, const turboreg_params* p, turboreg_result* res_dev)
+void fail_result(turboreg_result* out, int rc)
+{
+    std::memset(out, 0, sizeof(*out));
+    out->R[0] = out->R[4] = out->R[8] = 1.f;
+    out->hypothesis = -1;
+    out->clique[0] = out->clique[1] = out->clique[2] = -1;
+    out->status = rc;
+}
+
+ProbView make_view(turboreg_ctx* c, int slot, int64_t in_off, int32_t n, const turboreg_params* p)
 {
     Workspace& ws = c->ws;
-    ProbView v;
+    const size_t np = ws.np, n2 = np * np, s = static_cast<size_t>(slot);
+    ProbView v = {};
+    v.in_off = in_off;
     v.n = n;
     v.n_pad = round_up(n, kSc2BN);
     v.ldb = v.n_pad / 32;
@@ -234,73 +255,254 @@ ProbView make_view(turboreg_ctx* c, int32_t n, const turboreg_params* p, turbore
     v.tau = p->tau;
     v.theta = p->inlier_thresh;
     v.kappa_fp64 = p->kappa_fp64 > 0.f ? p->kappa_fp64 : 100.f;
-    v.pts = ws.pts;
-    v.pts8 = ws.pts8;
-    v.fp64_list = ws.fp64_list;
-    v.a8 = ws.a8;
-    v.bits = ws.bits;
-    v.w = ws.w;
-    v.rowscore = ws.rowscore;
-    v.deg = ws.deg;
-    v.hist = ws.hist;
-    v.rowcnt = ws.rowcnt;
-    v.rowpref = ws.rowpref;
-    v.rowcnt_gt = ws.rowcnt_gt;
-    v.rowpref_gt = ws.rowpref_gt;
-    v.cand = ws.cand;
-    v.piv = ws.piv;
-    v.cliques = ws.cliques;
-    v.rt = ws.rt;
-    v.inl = ws.inl;
-    v.ctl = ws.ctl;
-    v.res = res_dev;
+    v.pts = ws.pts + s * 6 * np;
+    v.pts8 = ws.pts8 + s * 8 * np;
+    v.a8 = ws.a8 + s * n2;
+    v.bits = ws.bits + s * n2 / 32;
+    v.w = ws.w + s * n2;
+    int32_t* rows = ws.rows + s * 6 * np;
+    v.rowscore = rows;
+    v.deg = rows + np;
+    v.rowcnt = rows + 2 * np;
+    v.rowpref = rows + 3 * np;
+    v.rowcnt_gt = rows + 4 * np;
+    v.rowpref_gt = rows + 5 * np;
+    v.hist = ws.hist + s * (np + 1);
+    v.cand = ws.cand + s * TURBOREG_K1_MAX;
+    v.piv = ws.piv + s * TURBOREG_K1_MAX;
+    v.cliques = ws.cliques + s * ws.nh;
+    v.rt = ws.rt + s * ws.nh * 16;
+    v.inl = ws.inl + s * ws.nh;
+    v.fp64_list = ws.fp64_list + s * ws.nh;
+    v.ctl = ws.ctl + s;
+    v.res = ws.res + s;
     return v;
 }
 
-// Enqueue the whole path for one problem whose points are already on the device.
-int enqueue_problem(turboreg_ctx* c, const float* dsrc, const float* ddst, int32_t n, const turboreg_params* p,
-                    turboreg_result* res_dev)
+// TMA descriptors of slot `slot` for the operand tiles of its FP8 adjacency.
+int encode_maps(turboreg_ctx* c, int slot, int32_t n_pad, CUtensorMap* out2)
 {
-    ProbView v = make_view(c, n, p, res_dev);
-    const bool timed = (p->flags & TURBOREG_FLAG_STAGE_TIMES) != 0;
-    const bool bitset = (p->flags & TURBOREG_FLAG_SC2_BITSET) != 0;
-    if (!bitset) {
-        int rc = encode_maps(c, v.n_pad);
-        if (rc != TURBOREG_OK) return rc;
+    Workspace& ws = c->ws;
+    if (ws.map_npad[slot] != n_pad) {
+        void* base = ws.a8 + static_cast<size_t>(slot) * ws.np * ws.np;
+        const cuuint64_t dims[2] = {static_cast<cuuint64_t>(n_pad), static_cast<cuuint64_t>(n_pad)};
+        const cuuint64_t strides[1] = {static_cast<cuuint64_t>(n_pad)};   // bytes between rows
+        const cuuint32_t boxA[2] = {static_cast<cuuint32_t>(kSc2BK), static_cast<cuuint32_t>(kSc2BM)};
+        const cuuint32_t boxB[2] = {static_cast<cuuint32_t>(kSc2BK), static_cast<cuuint32_t>(kSc2BN)};
+        const cuuint32_t estr[2] = {1, 1};
+        CUtensorMap* m = ws.map_cache + 2 * slot;
+        CUresult r1 = c->encode(&m[0], CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, base, dims, strides, boxA, estr,
+                                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        CUresult r2 = c->encode(&m[1], CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, base, dims, strides, boxB, estr,
+                                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r1 != CUDA_SUCCESS || r2 != CUDA_SUCCESS) {
+            std::fprintf(stderr, "turboreg: cuTensorMapEncodeTiled failed (%d, %d)\n", (int)r1, (int)r2);
+            ws.map_npad[slot] = 0;
+            return TURBOREG_ERR_CUDA;
+        }
+        ws.map_npad[slot] = n_pad;
     }
+    out2[0] = ws.map_cache[2 * slot];
+    out2[1] = ws.map_cache[2 * slot + 1];
+    return TURBOREG_OK;
+}
+
+// Fill the host mirrors (h_views, h_pre, h_maps) for problems in slots
+// [0, num) and compute the plan's block totals.
+int build_plan(turboreg_ctx* c, int32_t num, const int64_t* in_off, const int32_t* n,
+               const turboreg_params* const* prm, Plan& plan)
+{
+    Workspace& ws = c->ws;
+    plan = Plan();
+    plan.num = num;
+    plan.bitset = (prm[0]->flags & TURBOREG_FLAG_SC2_BITSET) != 0;
+    plan.timed = num == 1 && (prm[0]->flags & TURBOREG_FLAG_STAGE_TIMES) != 0;
+    plan.k2_common = prm[0]->k2;
+    for (int st = 0; st < kNumBatchStages; ++st) ws.h_pre[st * (num + 1)] = 0;
+    for (int32_t b = 0; b < num; ++b) {
+        ws.h_views[b] = make_view(c, b, in_off[b], n[b], prm[b]);
+        int32_t blocks[kNumBatchStages];
+        stage_blocks(n[b], prm[b]->k1, prm[b]->k2, blocks);
+        for (int st = 0; st < kNumBatchStages; ++st) {
+            plan.tot[st] += blocks[st];
+            ws.h_pre[st * (num + 1) + b + 1] = plan.tot[st];
+        }
+        if (n[b] > plan.max_n) plan.max_n = n[b];
+        if (prm[b]->k1 > plan.max_k1) plan.max_k1 = prm[b]->k1;
+        if (prm[b]->k2 != plan.k2_common) plan.k2_common = 0;
+        if (!plan.bitset) {
+            const int rc = encode_maps(c, b, ws.h_views[b].n_pad, ws.h_maps + 2 * b);
+            if (rc != TURBOREG_OK) return rc;
+        }
+    }
+    return TURBOREG_OK;
+}
+
+// Copy the plan's descriptors to `dev` (views | pre | maps, 128-byte aligned parts).
+int upload_desc(turboreg_ctx* c, int32_t num, void* dev, Batch& bt, cudaStream_t s)
+{
+    Workspace& ws = c->ws;
+    uint8_t* d = static_cast<uint8_t*>(dev);
+    const size_t v = sizeof(ProbView) * num;
+    const size_t p = sizeof(int32_t) * kNumBatchStages * (num + 1);
+    const size_t po = (v + 127) / 128 * 128, mo = po + (p + 127) / 128 * 128;
+    TR_CHECK(cudaMemcpyAsync(d, ws.h_views, v, cudaMemcpyHostToDevice, s));
+    TR_CHECK(cudaMemcpyAsync(d + po, ws.h_pre, p, cudaMemcpyHostToDevice, s));
+    TR_CHECK(cudaMemcpyAsync(d + mo, ws.h_maps, sizeof(CUtensorMap) * 2 * num, cudaMemcpyHostToDevice, s));
+    bt.views = reinterpret_cast<const ProbView*>(d);
+    bt.pre = reinterpret_cast<const int32_t*>(d + po);
+    bt.maps = reinterpret_cast<const CUtensorMap*>(d + mo);
+    bt.num = num;
+    return TURBOREG_OK;
+}
+
+// Enqueue the whole path for the plan's problems (inputs on the device).
+int enqueue_plan(turboreg_ctx* c, const Plan& pl, const Batch& bt, const float* dsrc, const float* ddst)
+{
     cudaStream_t s = c->stream;
-    if (timed) TR_CHECK(cudaEventRecordWithFlags(c->ev[0], s, cudaEventRecordExternal));
-    TR_CHECK(cudaMemsetAsync(c->ws.ctl, 0, sizeof(Ctl), s));
-    launch_pack(v, dsrc, ddst, s);
-    if (timed) TR_CHECK(cudaEventRecordWithFlags(c->ev[1], s, cudaEventRecordExternal));
-    launch_compat(v, s);
-    if (timed) TR_CHECK(cudaEventRecordWithFlags(c->ev[2], s, cudaEventRecordExternal));
-    if (bitset) launch_sc2_bitset(v, s);
-    else launch_sc2_tcgen05(v, c->tmA, c->tmB, s);   // also builds the weight histogram
-    if (timed) TR_CHECK(cudaEventRecordWithFlags(c->ev[3], s, cudaEventRecordExternal));
-    if (bitset) launch_topk(v, s);
-    else launch_topk_after_select(v, s);   // the GEMM's last CTA chose alpha
-    if (timed) TR_CHECK(cudaEventRecordWithFlags(c->ev[4], s, cudaEventRecordExternal));
-    launch_pgs(v, s);
-    if (timed) TR_CHECK(cudaEventRecordWithFlags(c->ev[5], s, cudaEventRecordExternal));
-    launch_kabsch(v, s);
-    if (timed) TR_CHECK(cudaEventRecordWithFlags(c->ev[6], s, cudaEventRecordExternal));
+    const bool timed = pl.timed != 0;
+#define TR_EV(k) \
+    if (timed) TR_CHECK(cudaEventRecordWithFlags(c->ev[k], s, cudaEventRecordExternal))
+    TR_EV(0);
+    TR_CHECK(cudaMemsetAsync(c->ws.ctl, 0, sizeof(Ctl) * pl.num, s));
+    launch_pack(bt, pl.tot[ST_PACK], dsrc, ddst, s);
+    TR_EV(1);
+    launch_compat(bt, pl.tot[ST_COMPAT], s);
+    TR_EV(2);
+    if (pl.bitset) {
+        launch_sc2_bitset(bt, pl.tot[ST_BITSET], s);
+        launch_hist(bt, pl.tot[ST_HIST], pl.max_n, s);
+        launch_select(bt, s);
+    } else {
+        // one problem: the GEMM builds the histogram in shared memory and its
+        // last CTA chooses the threshold; a batch adds a select launch
+        launch_sc2_tcgen05(bt, pl.tot[ST_GEMM], pl.max_n, s);
+        if (pl.num > 1) launch_select(bt, s);
+    }
+    TR_EV(3);
+    launch_topk_rest(bt, pl.tot, pl.max_k1, s);
+    TR_EV(4);
+    launch_pgs(bt, pl.tot[ST_PGS], pl.k2_common, s);
+    TR_EV(5);
+    launch_kabsch(bt, pl.tot[ST_KABSCH], s);
+    TR_EV(6);
     // fork: ill-conditioned cliques (FP64 list) on the side stream, the rest here
     TR_CHECK(cudaEventRecord(c->fork_ev, s));
     TR_CHECK(cudaStreamWaitEvent(c->side, c->fork_ev, 0));
-    launch_kabsch_fp64_verify(v, c->side);
+    launch_kabsch_fp64_verify(bt, pl.tot[ST_KABSCH64], pl.tot[ST_VERIFY], c->side);
     TR_CHECK(cudaEventRecord(c->join_ev, c->side));
-    launch_verify(v, s);
+    launch_verify(bt, pl.tot[ST_VERIFY], s);
     TR_CHECK(cudaStreamWaitEvent(s, c->join_ev, 0));
-    if (timed) TR_CHECK(cudaEventRecordWithFlags(c->ev[7], s, cudaEventRecordExternal));
-    launch_finalize(v, s);
-    if (timed) TR_CHECK(cudaEventRecordWithFlags(c->ev[8], s, cudaEventRecordExternal));
+    TR_EV(7);
+    launch_finalize(bt, s);
+    TR_EV(8);
+#undef TR_EV
     TR_CHECK(cudaGetLastError());
-    c->last_n = n;
-    c->last_npad = v.n_pad;
-    c->last_k1 = p->k1;
-    c->last_k2 = p->k2;
-    c->have_times = timed;
+    return TURBOREG_OK;
+}
+
+void drop_slot(turboreg_ctx::GraphSlot& g)
+{
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (g.graph) cudaGraphDestroy(g.graph);
+    if (g.desc) cudaFree(g.desc);
+    g = turboreg_ctx::GraphSlot();
+}
+
+// Signature of a plan: everything the captured graph bakes in.
+std::vector<uint8_t> plan_key(turboreg_ctx* c, const Plan& pl)
+{
+    std::vector<uint8_t> k;
+    auto put = [&](const void* p, size_t b) {
+        const uint8_t* q = static_cast<const uint8_t*>(p);
+        k.insert(k.end(), q, q + b);
+    };
+    put(&pl, sizeof(pl));
+    for (int32_t b = 0; b < pl.num; ++b) {
+        const ProbView& v = c->ws.h_views[b];
+        put(&v.in_off, sizeof(v.in_off));
+        put(&v.n, sizeof(v.n));
+        put(&v.k1, sizeof(v.k1));
+        put(&v.k2, sizeof(v.k2));
+        put(&v.tau, sizeof(v.tau));
+        put(&v.theta, sizeof(v.theta));
+        put(&v.kappa_fp64, sizeof(v.kappa_fp64));
+    }
+    return k;
+}
+
+// Run a plan: replay its captured graph (capturing it on first use) with the
+// given input pointers; TURBOREG_FLAG_NO_GRAPH launches the stages directly.
+int run_plan(turboreg_ctx* c, const Plan& pl, bool no_graph, const float* dsrc, const float* ddst)
+{
+    if (no_graph) {
+        Batch bt;
+        const int rc = upload_desc(c, pl.num, c->ws.desc, bt, c->stream);
+        if (rc != TURBOREG_OK) return rc;
+        return enqueue_plan(c, pl, bt, dsrc, ddst);
+    }
+    const std::vector<uint8_t> key = plan_key(c, pl);
+    turboreg_ctx::GraphSlot* g = nullptr;
+    for (auto& sl : c->gslot)
+        if (sl.used && sl.key == key) g = &sl;
+    if (!g) {
+        g = &c->gslot[0];
+        for (auto& sl : c->gslot) {
+            if (!sl.used) { g = &sl; break; }
+            if (sl.stamp < g->stamp) g = &sl;
+        }
+        drop_slot(*g);
+        TR_CHECK(cudaMalloc(&g->desc, desc_bytes(pl.num)));
+        int rc = upload_desc(c, pl.num, g->desc, g->batch, c->stream);
+        if (rc != TURBOREG_OK) return rc;
+        TR_CHECK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+        rc = enqueue_plan(c, pl, g->batch, dsrc, ddst);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+        if (rc != TURBOREG_OK || e != cudaSuccess || !graph) {
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+            drop_slot(*g);
+            std::fprintf(stderr, "turboreg: graph capture failed: %s\n", cudaGetErrorString(e));
+            return rc != TURBOREG_OK ? rc : TURBOREG_ERR_CUDA;
+        }
+        g->graph = graph;
+        size_t cnt = 0;
+        TR_CHECK(cudaGraphGetNodes(graph, nullptr, &cnt));
+        std::vector<cudaGraphNode_t> nodes(cnt);
+        TR_CHECK(cudaGraphGetNodes(graph, nodes.data(), &cnt));
+        for (size_t k = 0; k < cnt; ++k) {
+            cudaGraphNodeType ty;
+            TR_CHECK(cudaGraphNodeGetType(nodes[k], &ty));
+            if (ty != cudaGraphNodeTypeKernel) continue;
+            cudaKernelNodeParams kp;
+            TR_CHECK(cudaGraphKernelNodeGetParams(nodes[k], &kp));
+            if (kp.func == pack_kernel_func()) {
+                g->pack_node = nodes[k];
+                g->pack_params = kp;
+            }
+        }
+        if (!g->pack_node || cudaGraphInstantiate(&g->exec, graph, 0) != cudaSuccess) {
+            cudaGetLastError();
+            drop_slot(*g);
+            return TURBOREG_ERR_CUDA;
+        }
+        g->used = true;
+        g->key = key;
+    }
+    g->stamp = ++c->gclock;
+    g->src = dsrc;
+    g->dst = ddst;
+    g->args[0] = &g->batch;
+    g->args[1] = &g->src;
+    g->args[2] = &g->dst;
+    cudaKernelNodeParams kp = g->pack_params;
+    kp.kernelParams = g->args;
+    kp.extra = nullptr;
+    TR_CHECK(cudaGraphExecKernelNodeSetParams(g->exec, g->pack_node, &kp));
+    TR_CHECK(cudaGraphLaunch(g->exec, c->stream));
     return TURBOREG_OK;
 }
 
@@ -313,100 +515,6 @@ int collect_times(turboreg_ctx* c)
             c->stage_ms[k] = -1.f;
         }
     }
-    return TURBOREG_OK;
-}
-
-void drop_slot(turboreg_ctx::GraphSlot& g)
-{
-    if (g.exec) cudaGraphExecDestroy(g.exec);
-    if (g.graph) cudaGraphDestroy(g.graph);
-    g = turboreg_ctx::GraphSlot();
-}
-
-bool slot_matches(const turboreg_ctx::GraphSlot& g, int32_t n, const turboreg_params* p, turboreg_result* res)
-{
-    return g.used && g.n == n && g.k1 == p->k1 && g.k2 == p->k2 && g.tau == p->tau && g.theta == p->inlier_thresh &&
-           g.kappa == p->kappa_fp64 && g.flags == p->flags && g.res == res;
-}
-
-// Capture the pipeline for this shape once, then replay it; the pack node's
-// (src, dst) arguments are patched in the instantiated graph on every call.
-int run_problem(turboreg_ctx* c, const float* dsrc, const float* ddst, int32_t n, const turboreg_params* p,
-                turboreg_result* res_dev)
-{
-    if (p->flags & TURBOREG_FLAG_NO_GRAPH) return enqueue_problem(c, dsrc, ddst, n, p, res_dev);
-    turboreg_ctx::GraphSlot* g = nullptr;
-    for (auto& sl : c->gslot)
-        if (slot_matches(sl, n, p, res_dev)) g = &sl;
-    if (!g) {
-        g = &c->gslot[0];
-        for (auto& sl : c->gslot) {
-            if (!sl.used) { g = &sl; break; }
-            if (sl.stamp < g->stamp) g = &sl;
-        }
-        drop_slot(*g);
-        TR_CHECK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-        const int rc = enqueue_problem(c, dsrc, ddst, n, p, res_dev);
-        cudaGraph_t graph = nullptr;
-        const cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
-        if (rc != TURBOREG_OK || e != cudaSuccess || !graph) {
-            if (graph) cudaGraphDestroy(graph);
-            cudaGetLastError();
-            std::fprintf(stderr, "turboreg: graph capture failed: %s\n", cudaGetErrorString(e));
-            return rc != TURBOREG_OK ? rc : TURBOREG_ERR_CUDA;
-        }
-        size_t cnt = 0;
-        TR_CHECK(cudaGraphGetNodes(graph, nullptr, &cnt));
-        cudaGraphNode_t nodes[64];
-        if (cnt > 64) {
-            cudaGraphDestroy(graph);
-            return TURBOREG_ERR_CUDA;
-        }
-        TR_CHECK(cudaGraphGetNodes(graph, nodes, &cnt));
-        for (size_t k = 0; k < cnt; ++k) {
-            cudaGraphNodeType ty;
-            TR_CHECK(cudaGraphNodeGetType(nodes[k], &ty));
-            if (ty != cudaGraphNodeTypeKernel) continue;
-            cudaKernelNodeParams kp;
-            TR_CHECK(cudaGraphKernelNodeGetParams(nodes[k], &kp));
-            if (kp.func == pack_kernel_func()) {
-                g->pack_node = nodes[k];
-                g->pack_params = kp;
-            }
-        }
-        if (!g->pack_node) {
-            cudaGraphDestroy(graph);
-            return TURBOREG_ERR_CUDA;
-        }
-        g->graph = graph;
-        if (cudaGraphInstantiate(&g->exec, graph, 0) != cudaSuccess) {
-            cudaGetLastError();
-            drop_slot(*g);
-            return TURBOREG_ERR_CUDA;
-        }
-        g->used = true;
-        g->n = n; g->k1 = p->k1; g->k2 = p->k2;
-        g->tau = p->tau; g->theta = p->inlier_thresh; g->kappa = p->kappa_fp64;
-        g->flags = p->flags;
-        g->res = res_dev;
-        g->pv = make_view(c, n, p, res_dev);
-    }
-    g->stamp = ++c->gclock;
-    g->src = dsrc;
-    g->dst = ddst;
-    g->args[0] = &g->pv;
-    g->args[1] = &g->src;
-    g->args[2] = &g->dst;
-    cudaKernelNodeParams kp = g->pack_params;
-    kp.kernelParams = g->args;
-    kp.extra = nullptr;
-    TR_CHECK(cudaGraphExecKernelNodeSetParams(g->exec, g->pack_node, &kp));
-    TR_CHECK(cudaGraphLaunch(g->exec, c->stream));
-    c->last_n = n;
-    c->last_npad = g->pv.n_pad;
-    c->last_k1 = p->k1;
-    c->last_k2 = p->k2;
-    c->have_times = (p->flags & TURBOREG_FLAG_STAGE_TIMES) != 0;
     return TURBOREG_OK;
 }
 
@@ -540,11 +648,7 @@ int turboreg_register(turboreg_ctx* c, const float* src, const float* dst, int32
     if (!c || !src || !dst || !out) return TURBOREG_ERR_INVALID_ARG;
     int rc = check_params(c, n, p);
     if (rc != TURBOREG_OK) {
-        std::memset(out, 0, sizeof(*out));
-        out->R[0] = out->R[4] = out->R[8] = 1.f;
-        out->hypothesis = -1;
-        out->clique[0] = out->clique[1] = out->clique[2] = -1;
-        out->status = rc;
+        fail_result(out, rc);
         return rc;
     }
     TR_CHECK(cudaSetDevice(c->device));
@@ -568,17 +672,22 @@ int turboreg_register(turboreg_ctx* c, const float* src, const float* dst, int32
     }
     if (rc != TURBOREG_OK) {
         TR_CHECK(cudaStreamSynchronize(c->stream));
-        std::memset(out, 0, sizeof(*out));
-        out->R[0] = out->R[4] = out->R[8] = 1.f;
-        out->hypothesis = -1;
-        out->clique[0] = out->clique[1] = out->clique[2] = -1;
-        out->status = rc;
+        fail_result(out, rc);
         return rc;
     }
-    rc = run_problem(c, s_in, d_in, n, p, c->ws.res);
+    Plan pl;
+    const int64_t off0 = 0;
+    rc = build_plan(c, 1, &off0, &n, &p, pl);
+    if (rc != TURBOREG_OK) return rc;
+    rc = run_plan(c, pl, (p->flags & TURBOREG_FLAG_NO_GRAPH) != 0, s_in, d_in);
     if (rc != TURBOREG_OK) return rc;
     TR_CHECK(cudaMemcpyAsync(c->host_res, c->ws.res, sizeof(turboreg_result), cudaMemcpyDeviceToHost, c->stream));
     TR_CHECK(cudaStreamSynchronize(c->stream));
+    c->last_n = n;
+    c->last_npad = round_up(n, kSc2BN);
+    c->last_k1 = p->k1;
+    c->last_k2 = p->k2;
+    c->have_times = pl.timed != 0;
     rc = collect_times(c);
     if (rc != TURBOREG_OK) return rc;
     *out = c->host_res[0];
@@ -599,6 +708,10 @@ int turboreg_register_batched(turboreg_ctx* c, const float* src_cat, const float
     }
     const int64_t total = offsets[num];
     if (total > static_cast<int64_t>(c->max_n) * c->max_batch) return TURBOREG_ERR_INVALID_ARG;
+    const uint32_t mode = params->flags & (TURBOREG_FLAG_SC2_BITSET | TURBOREG_FLAG_NO_GRAPH);
+    for (int32_t b = 0; b < params_count; ++b)
+        if ((params[b].flags & (TURBOREG_FLAG_SC2_BITSET | TURBOREG_FLAG_NO_GRAPH)) != mode)
+            return TURBOREG_ERR_INVALID_ARG;   // one SC^2 path and launch mode per batch
     TR_CHECK(cudaSetDevice(c->device));
     const bool dsrc = is_device_ptr(src_cat), ddst = is_device_ptr(dst_cat);
     const size_t bytes = static_cast<size_t>(total) * 3 * sizeof(float);
@@ -612,8 +725,11 @@ int turboreg_register_batched(turboreg_ctx* c, const float* src_cat, const float
         TR_CHECK(cudaMemcpyAsync(c->ws.in_dst, dst_cat, bytes, cudaMemcpyHostToDevice, c->stream));
         d_in = c->ws.in_dst;
     }
-    int32_t* pre = static_cast<int32_t*>(std::calloc(num, sizeof(int32_t)));
-    if (!pre) return TURBOREG_ERR_OOM;
+    // problems that fail host-side checks are reported without device work
+    std::vector<int> pre(num);
+    std::vector<int32_t> nn;
+    std::vector<int64_t> off;
+    std::vector<const turboreg_params*> pp;
     for (int32_t b = 0; b < num; ++b) {
         const turboreg_params* p = params_count == 1 ? params : params + b;
         const int32_t n = static_cast<int32_t>(offsets[b + 1] - offsets[b]);
@@ -624,32 +740,32 @@ int turboreg_register_batched(turboreg_ctx* c, const float* src_cat, const float
             rc = TURBOREG_ERR_NONFINITE;
         pre[b] = rc;
         if (rc != TURBOREG_OK) continue;
-        rc = enqueue_problem(c, s_in + 3 * offsets[b], d_in + 3 * offsets[b], n, p, c->ws.res + b);
-        if (rc != TURBOREG_OK) {
-            std::free(pre);
-            return rc;
-        }
+        nn.push_back(n);
+        off.push_back(offsets[b]);
+        pp.push_back(p);
     }
-    cudaError_t e = cudaMemcpyAsync(c->host_res, c->ws.res, sizeof(turboreg_result) * num, cudaMemcpyDeviceToHost,
-                                    c->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-    if (e != cudaSuccess) {
-        std::free(pre);
-        std::fprintf(stderr, "turboreg: batched copy-back failed: %s\n", cudaGetErrorString(e));
-        return TURBOREG_ERR_CUDA;
+    const int32_t m = static_cast<int32_t>(nn.size());
+    if (m > 0) {
+        Plan pl;
+        int rc = build_plan(c, m, off.data(), nn.data(), pp.data(), pl);
+        if (rc == TURBOREG_OK) rc = run_plan(c, pl, (mode & TURBOREG_FLAG_NO_GRAPH) != 0, s_in, d_in);
+        if (rc != TURBOREG_OK) return rc;
+        TR_CHECK(cudaMemcpyAsync(c->host_res, c->ws.res, sizeof(turboreg_result) * m, cudaMemcpyDeviceToHost,
+                                 c->stream));
     }
+    TR_CHECK(cudaStreamSynchronize(c->stream));
+    int32_t q = 0;
     for (int32_t b = 0; b < num; ++b) {
-        if (pre[b] != TURBOREG_OK) {
-            std::memset(&out[b], 0, sizeof(out[b]));
-            out[b].R[0] = out[b].R[4] = out[b].R[8] = 1.f;
-            out[b].hypothesis = -1;
-            out[b].clique[0] = out[b].clique[1] = out[b].clique[2] = -1;
-            out[b].status = pre[b];
-        } else {
-            out[b] = c->host_res[b];
-        }
+        if (pre[b] != TURBOREG_OK) fail_result(&out[b], pre[b]);
+        else out[b] = c->host_res[q++];
     }
-    std::free(pre);
+    if (m > 0) {   // inspection buffers refer to the first processed problem (slot 0)
+        c->last_n = nn[0];
+        c->last_npad = round_up(nn[0], kSc2BN);
+        c->last_k1 = pp[0]->k1;
+        c->last_k2 = pp[0]->k2;
+        c->have_times = false;
+    }
     return TURBOREG_OK;
 }
 
@@ -672,20 +788,24 @@ int64_t turboreg_debug_copy(turboreg_ctx* c, int which, void* dst, int64_t max_b
     if (cudaSetDevice(c->device) != cudaSuccess) return -TURBOREG_ERR_CUDA;
     Ctl h;
     if (cudaMemcpy(&h, c->ws.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost) != cudaSuccess) return -TURBOREG_ERR_CUDA;
+    turboreg_params p0;
+    turboreg_default_params(&p0, 0.f, c->last_k1 > 0 ? c->last_k1 : 1, 1.f);
+    p0.k2 = c->last_k2 > 0 ? c->last_k2 : 1;
+    const ProbView v = make_view(c, 0, 0, c->last_n, &p0);   // slot 0
     const size_t np = static_cast<size_t>(c->last_npad);
     const size_t nh = static_cast<size_t>(h.n_pivots) * c->last_k2;
     const void* src = nullptr;
     size_t bytes = 0;
     switch (which) {
-        case TURBOREG_BUF_ADJ_BITS: src = c->ws.bits; bytes = np * np / 8; break;
-        case TURBOREG_BUF_ADJ_FP8: src = c->ws.a8; bytes = np * np; break;
-        case TURBOREG_BUF_SC2: src = c->ws.w; bytes = np * np * 2; break;
-        case TURBOREG_BUF_PIVOTS: src = c->ws.piv; bytes = static_cast<size_t>(h.n_pivots) * 16; break;
-        case TURBOREG_BUF_CLIQUES: src = c->ws.cliques; bytes = nh * 16; break;
-        case TURBOREG_BUF_RT: src = c->ws.rt; bytes = nh * 64; break;
-        case TURBOREG_BUF_INLIERS: src = c->ws.inl; bytes = nh * 4; break;
-        case TURBOREG_BUF_ROWSCORE: src = c->ws.rowscore; bytes = static_cast<size_t>(c->last_n) * 4; break;
-        case TURBOREG_BUF_DEGREE: src = c->ws.deg; bytes = static_cast<size_t>(c->last_n) * 4; break;
+        case TURBOREG_BUF_ADJ_BITS: src = v.bits; bytes = np * np / 8; break;
+        case TURBOREG_BUF_ADJ_FP8: src = v.a8; bytes = np * np; break;
+        case TURBOREG_BUF_SC2: src = v.w; bytes = np * np * 2; break;
+        case TURBOREG_BUF_PIVOTS: src = v.piv; bytes = static_cast<size_t>(h.n_pivots) * 16; break;
+        case TURBOREG_BUF_CLIQUES: src = v.cliques; bytes = nh * 16; break;
+        case TURBOREG_BUF_RT: src = v.rt; bytes = nh * 64; break;
+        case TURBOREG_BUF_INLIERS: src = v.inl; bytes = nh * 4; break;
+        case TURBOREG_BUF_ROWSCORE: src = v.rowscore; bytes = static_cast<size_t>(c->last_n) * 4; break;
+        case TURBOREG_BUF_DEGREE: src = v.deg; bytes = static_cast<size_t>(c->last_n) * 4; break;
         default: return -TURBOREG_ERR_INVALID_ARG;
     }
     if (bytes > static_cast<size_t>(max_bytes)) bytes = static_cast<size_t>(max_bytes);

@@ -38,13 +38,18 @@ namespace {
 constexpr int kT = 128;          // tile edge
 constexpr int kThreads = 256;    // 8 warps x 16 rows; each lane 4 columns
 
-__global__ void __launch_bounds__(256) pack_kernel(ProbView v, const float* __restrict__ src,
-                                                   const float* __restrict__ dst)
+// One block per 256 points of one problem; src/dst are the (concatenated)
+// inputs, the problem's matches start at v.in_off.
+__global__ void __launch_bounds__(256) pack_kernel(ManyViews vs, const float* __restrict__ src_cat,
+                                                   const float* __restrict__ dst_cat)
 {
-    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-    const int stride = gridDim.x * blockDim.x;
+    int lb;
+    const ProbView v = vs.get(ST_PACK, blockIdx.x, lb);
+    const float* src = src_cat + 3 * v.in_off;
+    const float* dst = dst_cat + 3 * v.in_off;
     bool bad = false;
-    for (int k = tid; k < v.n_pad; k += stride) {
+    const int k = lb * 256 + threadIdx.x;
+    if (k < v.n_pad) {
         float a[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         if (k < v.n) {
             a[0] = src[3 * k + 0]; a[1] = src[3 * k + 1]; a[2] = src[3 * k + 2];
@@ -60,8 +65,9 @@ __global__ void __launch_bounds__(256) pack_kernel(ProbView v, const float* __re
         v.rowscore[k] = 0;
         v.deg[k] = 0;
         v.rowcnt[k] = 0;
+        v.hist[k] = 0;
     }
-    for (int k = tid; k <= v.n_pad; k += stride) v.hist[k] = 0;
+    if (k == 0) v.hist[v.n_pad] = 0;
     if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(&v.ctl->err, TR_ERR_NONFINITE);
 }
 
@@ -118,14 +124,15 @@ __device__ __forceinline__ uint4 bits16_to_fp8(uint32_t b16)
                       nibble_to_fp8((b16 >> 12) & 0xF));
 }
 
-__global__ void __launch_bounds__(kThreads) compat_kernel(ProbView v)
+__global__ void __launch_bounds__(kThreads) compat_kernel(ManyViews vs)
 {
     __shared__ __align__(128) float4 srow[kT][2];     // row points (x0,x1,x2,y0 | y1,y2,-,-)
     __shared__ uint16_t colpart[8][kT];               // per warp: 16-row mask of each column
     __shared__ __align__(8) uint64_t bar;
 
     // triangular tile index -> (I, J), I <= J
-    const int t = blockIdx.x;
+    int t;
+    const ProbView v = vs.get(ST_COMPAT, blockIdx.x, t);
     int J = static_cast<int>((sqrtf(8.0f * t + 1.0f) - 1.0f) * 0.5f);
     while (J * (J + 1) / 2 > t) --J;
     while ((J + 1) * (J + 2) / 2 <= t) ++J;
@@ -250,16 +257,14 @@ __global__ void __launch_bounds__(kThreads) compat_kernel(ProbView v)
 
 const void* pack_kernel_func() { return reinterpret_cast<const void*>(&pack_kernel); }
 
-void launch_pack(const ProbView& v, const float* src, const float* dst, cudaStream_t s)
+void launch_pack(const Batch& b, int total, const float* src, const float* dst, cudaStream_t s)
 {
-    const int blocks = (v.n_pad + 255) / 256;
-    pack_kernel<<<blocks, 256, 0, s>>>(v, src, dst);
+    pack_kernel<<<total, 256, 0, s>>>(ManyViews{b}, src, dst);
 }
 
-void launch_compat(const ProbView& v, cudaStream_t s)
+void launch_compat(const Batch& b, int total, cudaStream_t s)
 {
-    const int T = v.n_pad / kT;
-    compat_kernel<<<T * (T + 1) / 2, kThreads, 0, s>>>(v);
+    compat_kernel<<<total, kThreads, 0, s>>>(ManyViews{b});
 }
 
 }  // namespace tr

@@ -170,9 +170,11 @@ __device__ __forceinline__ void load_clique(const ProbView& v, const int4 cl, fl
 
 // Phase 1: FP32 closed form for every hypothesis; cliques whose kappa exceeds
 // the bound (or whose FP32 frames are undefined) go to a compact list.
-__global__ void __launch_bounds__(128) kabsch_kernel(ProbView v)
+__global__ void __launch_bounds__(128) kabsch_kernel(ManyViews vs)
 {
-    const int h = blockIdx.x * blockDim.x + threadIdx.x;
+    int lb;
+    const ProbView v = vs.get(ST_KABSCH, blockIdx.x, lb);
+    const int h = lb * blockDim.x + threadIdx.x;
     const int nh = v.ctl->n_pivots * v.k2;
     if (h >= nh) return;
     v.inl[h] = 0;
@@ -201,9 +203,11 @@ __global__ void __launch_bounds__(128) kabsch_kernel(ProbView v)
 
 // Phase 2: the same closed form in FP64 for the listed hypotheses only, so the
 // slow FP64 pipe runs on dense warps instead of on every warp that holds one.
-__global__ void __launch_bounds__(32) kabsch_fp64_kernel(ProbView v)
+__global__ void __launch_bounds__(32) kabsch_fp64_kernel(ManyViews vs)
 {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    int lb;
+    const ProbView v = vs.get(ST_KABSCH64, blockIdx.x, lb);
+    const int k = lb * blockDim.x + threadIdx.x;
     if (k >= static_cast<int>(v.ctl->fp64_slot)) return;
     const int h = v.fp64_list[k];
     float* out = v.rt + (size_t)h * 16;
@@ -273,15 +277,18 @@ constexpr int kVPtsWarp = 64;
 constexpr int kVPts = kVWarps * kVPtsWarp;
 
 template <bool kList>
-__global__ void __launch_bounds__(128) verify_kernel(ProbView v)
+__global__ void __launch_bounds__(128) verify_kernel(ManyViews vs)
 {
     __shared__ __align__(16) float4 sp[kVPts][2];
     __shared__ __align__(16) float4 srt[kVHyp][4];
     __shared__ int scnt[kVWarps][kVHyp];
+    int lb;
+    const ProbView v = vs.get(ST_VERIFY, blockIdx.x, lb);
+    const int npb = (v.n + kVPts - 1) / kVPts;          // point blocks of this problem
     const int nh = kList ? static_cast<int>(v.ctl->fp64_slot) : v.ctl->n_pivots * v.k2;
-    const int h0 = blockIdx.x * kVHyp;
+    const int h0 = (lb / npb) * kVHyp;
     if (h0 >= nh) return;
-    const int k0 = blockIdx.y * kVPts;
+    const int k0 = (lb % npb) * kVPts;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     {
         const float4* src = reinterpret_cast<const float4*>(v.pts8 + (size_t)k0 * 8);
@@ -343,8 +350,10 @@ __global__ void __launch_bounds__(128) verify_kernel(ProbView v)
     if (slot < nh && tot) atomicAdd(&v.inl[kList ? v.fp64_list[slot] : slot], tot);
 }
 
-__global__ void __launch_bounds__(1024) finalize_kernel(ProbView v)
+__global__ void __launch_bounds__(1024) finalize_kernel(ManyViews vs)
 {
+    int lb;
+    const ProbView v = vs.get(ST_FINAL, blockIdx.x, lb);
     __shared__ unsigned long long sbest[32];
     __shared__ int scnt[32], sfp[32];
     const int np = v.ctl->n_pivots;
@@ -415,27 +424,46 @@ __global__ void __launch_bounds__(1024) finalize_kernel(ProbView v)
 
 }  // namespace
 
-void launch_kabsch(const ProbView& v, cudaStream_t s)
+void launch_kabsch(const Batch& b, int total, cudaStream_t s)
 {
-    const int cap = v.k1 * v.k2;
-    kabsch_kernel<<<(cap + 127) / 128, 128, 0, s>>>(v);
+    kabsch_kernel<<<total, 128, 0, s>>>(ManyViews{b});
 }
 
-void launch_verify(const ProbView& v, cudaStream_t s)
+void launch_verify(const Batch& b, int total, cudaStream_t s)
 {
-    const int cap = v.k1 * v.k2;
-    dim3 grid((cap + kVHyp - 1) / kVHyp, (v.n + kVPts - 1) / kVPts);
-    verify_kernel<false><<<grid, 128, 0, s>>>(v);
+    verify_kernel<false><<<total, 128, 0, s>>>(ManyViews{b});
 }
 
-void launch_kabsch_fp64_verify(const ProbView& v, cudaStream_t s)
+void launch_kabsch_fp64_verify(const Batch& b, int total64, int total_verify, cudaStream_t s)
 {
-    const int cap = v.k1 * v.k2;
-    kabsch_fp64_kernel<<<(cap + 31) / 32, 32, 0, s>>>(v);
-    dim3 grid((cap + kVHyp - 1) / kVHyp, (v.n + kVPts - 1) / kVPts);
-    verify_kernel<true><<<grid, 128, 0, s>>>(v);
+    kabsch_fp64_kernel<<<total64, 32, 0, s>>>(ManyViews{b});
+    verify_kernel<true><<<total_verify, 128, 0, s>>>(ManyViews{b});
 }
 
-void launch_finalize(const ProbView& v, cudaStream_t s) { finalize_kernel<<<1, 1024, 0, s>>>(v); }
+void launch_finalize(const Batch& b, cudaStream_t s) { finalize_kernel<<<b.num, 1024, 0, s>>>(ManyViews{b}); }
+
+// Per-problem block counts of every stage.
+void stage_blocks(int32_t n, int32_t k1, int32_t k2, int32_t blocks[kNumBatchStages])
+{
+    const int32_t n_pad = (n + kSc2BN - 1) / kSc2BN * kSc2BN;
+    const int32_t T = n_pad / 128;
+    const int32_t nb = n_pad / kSc2BN;
+    const int32_t nh = k1 * k2;
+    blocks[ST_PACK] = n_pad / 256;
+    blocks[ST_COMPAT] = T * (T + 1) / 2;
+    blocks[ST_SELECT] = 1;
+    blocks[ST_COUNT] = (n + 7) / 8;
+    blocks[ST_SCAN] = 1;
+    blocks[ST_EMIT] = n;
+    blocks[ST_RANK] = (k1 + 31) / 32;
+    blocks[ST_PGS] = (k1 + 7) / 8;
+    blocks[ST_KABSCH] = (nh + 127) / 128;
+    blocks[ST_KABSCH64] = (nh + 31) / 32;
+    blocks[ST_VERIFY] = ((nh + kVHyp - 1) / kVHyp) * ((n + kVPts - 1) / kVPts);
+    blocks[ST_FINAL] = 1;
+    blocks[ST_HIST] = (n + 63) / 64;
+    blocks[ST_BITSET] = n_pad;
+    blocks[ST_GEMM] = nb * (nb + 1);
+}
 
 }  // namespace tr

@@ -125,7 +125,7 @@ extern "C" int turboreg_select_pivots_noalloc(const uint16_t* w_dev, int32_t n, 
     if (e == cudaSuccess) e = cudaMemsetAsync(v.hist, 0, sizeof(uint32_t) * (n + 1), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(v.rowcnt, 0, sizeof(int32_t) * n, s);
     if (e != cudaSuccess) return TURBOREG_ERR_CUDA;
-    launch_topk(v, s);
+    launch_topk_single(v, s);
     e = cudaGetLastError();
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(n_pivots_dev, &v.ctl->n_pivots, sizeof(int32_t), cudaMemcpyDeviceToDevice, s);

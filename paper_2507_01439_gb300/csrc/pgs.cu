@@ -20,10 +20,12 @@ namespace tr {
 namespace {
 
 template <int K2C>
-__global__ void __launch_bounds__(256) pgs_kernel(ProbView v)
+__global__ void __launch_bounds__(256) pgs_kernel(ManyViews vs)
 {
+    int lb;
+    const ProbView v = vs.get(ST_PGS, blockIdx.x, lb);
     const int lane = threadIdx.x & 31;
-    const int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int p = lb * 8 + (threadIdx.x >> 5);
     const int np = v.ctl->n_pivots;
     if (p >= np) return;
     const int k2 = K2C > 0 ? K2C : v.k2;
@@ -108,15 +110,16 @@ __global__ void __launch_bounds__(256) pgs_kernel(ProbView v)
 
 }  // namespace
 
-void launch_pgs(const ProbView& v, cudaStream_t s)
+// k2 is the common K2 of the batch, or 0 when problems differ (generic list)
+void launch_pgs(const Batch& b, int total, int k2, cudaStream_t s)
 {
-    const int blocks = (v.k1 * 32 + 255) / 256;
-    switch (v.k2) {
-        case 1: pgs_kernel<1><<<blocks, 256, 0, s>>>(v); break;
-        case 2: pgs_kernel<2><<<blocks, 256, 0, s>>>(v); break;
-        case 3: pgs_kernel<3><<<blocks, 256, 0, s>>>(v); break;
-        case 4: pgs_kernel<4><<<blocks, 256, 0, s>>>(v); break;
-        default: pgs_kernel<0><<<blocks, 256, 0, s>>>(v); break;
+    const ManyViews vs{b};
+    switch (k2) {
+        case 1: pgs_kernel<1><<<total, 256, 0, s>>>(vs); break;
+        case 2: pgs_kernel<2><<<total, 256, 0, s>>>(vs); break;
+        case 3: pgs_kernel<3><<<total, 256, 0, s>>>(vs); break;
+        case 4: pgs_kernel<4><<<total, 256, 0, s>>>(vs); break;
+        default: pgs_kernel<0><<<total, 256, 0, s>>>(vs); break;
     }
 }
 

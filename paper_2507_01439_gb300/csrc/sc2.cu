@@ -56,14 +56,16 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar)
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// Persistent, warp-specialised: CTA b handles tiles b, b + grid, ...
+// Persistent, warp-specialised: CTA b handles global tiles b, b + grid, ...
+// of all problems of the batch (problem p's tiles are [pre[p], pre[p+1]) of
+// stage ST_GEMM; tensor maps of problem p at maps[2p], maps[2p+1]).
 //   warp 0 lane 0   TMA producer over all (tile, k) of this CTA
 //   warp 1 lane 0   MMA issuer; accumulator buffer (tile count & 1)
 //   warps 2..9      epilogue of the previous tile while the next one runs
-// kSmemHist: the edge-weight histogram lives in shared memory (else global).
-template <bool kSmemHist>
-__global__ void __launch_bounds__(kThreads, 1)
-sc2_tcgen05_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, ProbView v)
+// kSingle: one problem: the edge-weight histogram is kept in shared memory
+// and the last CTA to finish chooses the pivot threshold.
+template <bool kSingle>
+__global__ void __launch_bounds__(kThreads, 1) sc2_tcgen05_kernel(Batch bt, int total)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -78,10 +80,7 @@ sc2_tcgen05_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
     uint32_t* shist = reinterpret_cast<uint32_t*>(smem + kPipeBytes + kBarBytes);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nb = v.n_pad / kSc2BN;
-    const int ntiles = nb * (nb + 1);
-    const int KT = v.n_pad / kSc2BK;
-    const int nbins = v.n + 1;
+    const int nbins = kSingle ? bt.views[0].n + 1 : 0;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
@@ -93,10 +92,8 @@ sc2_tcgen05_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
             mbar_init(&tempty[b], kEpiWarps);
         }
         fence_mbar_init();
-        prefetch_tmap(&tmA);
-        prefetch_tmap(&tmB);
     }
-    if (kSmemHist)
+    if (kSingle)
         for (int b = threadIdx.x; b < nbins; b += blockDim.x) shist[b] = 0u;
     if (warp == 0) tmem_alloc(tmem_slot, kTmemCols);
     tc_fence_before();
@@ -109,16 +106,21 @@ sc2_tcgen05_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
         if (lane == 0) {
             // ---------------- TMA producer ----------------
             int it = 0;
-            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+            for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
+                int lt;
+                const int p = locate(bt, ST_GEMM, t, lt);
+                const int KT = bt.views[p].n_pad / kSc2BK;
+                const CUtensorMap* mA = bt.maps + 2 * p;
+                const CUtensorMap* mB = mA + 1;
                 int bm, bn;
-                tile_of(t, bm, bn);
+                tile_of(lt, bm, bn);
                 for (int kb = 0; kb < KT; ++kb, ++it) {
                     const int s = it % kStages;
                     const uint32_t ph = (it / kStages) & 1u;
                     if (!mbar_wait(&empty[s], ph ^ 1u)) { ok = false; break; }
                     mbar_arrive_expect_tx(&full[s], kABytes + kBBytes);
-                    tma_load_2d(sA + s * kABytes, &tmA, kb * kSc2BK, bm * kSc2BM, &full[s]);
-                    tma_load_2d(sB + s * kBBytes, &tmB, kb * kSc2BK, bn * kSc2BN, &full[s]);
+                    tma_load_2d(sA + s * kABytes, mA, kb * kSc2BK, bm * kSc2BM, &full[s]);
+                    tma_load_2d(sB + s * kBBytes, mB, kb * kSc2BK, bn * kSc2BN, &full[s]);
                 }
             }
         }
@@ -127,7 +129,10 @@ sc2_tcgen05_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
         if (lane == 0) {
             // ---------------- MMA issuer ----------------
             int it = 0, tc = 0;
-            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++tc) {
+            for (int t = blockIdx.x; t < total && ok; t += gridDim.x, ++tc) {
+                int lt;
+                const int p = locate(bt, ST_GEMM, t, lt);
+                const int KT = bt.views[p].n_pad / kSc2BK;
                 const int buf = tc & 1;
                 const uint32_t use = static_cast<uint32_t>(tc >> 1);
                 if (!mbar_wait(&tempty[buf], (use & 1u) ^ 1u)) { ok = false; break; }
@@ -156,9 +161,12 @@ sc2_tcgen05_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
         const int quarter = warp & 3;              // TMEM lanes this warp may access
         const int half = (warp - 2) >> 2;          // column half of the tile
         int tc = 0;
-        for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++tc) {
+        for (int t = blockIdx.x; t < total; t += gridDim.x, ++tc) {
+            int lt;
+            const int p = locate(bt, ST_GEMM, t, lt);
+            const ProbView v = bt.views[p];
             int bm, bn;
-            tile_of(t, bm, bn);
+            tile_of(lt, bm, bn);
             const int buf = tc & 1;
             const uint32_t use = static_cast<uint32_t>(tc >> 1);
             const bool got = mbar_wait(&tfull[buf], use & 1u);
@@ -189,19 +197,19 @@ sc2_tcgen05_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
 #pragma unroll
                     for (int q = 0; q < 32; ++q)
                         if (val[q] > 0) {
-                            if (kSmemHist) atomicAdd(&shist[val[q]], 1u);
+                            if (kSingle) atomicAdd(&shist[val[q]], 1u);
                             else atomicAdd(&v.hist[val[q]], 1u);
                         }
                 }
                 uint4* dst = reinterpret_cast<uint4*>(wrow + col0);
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    uint4 p;
-                    p.x = static_cast<uint32_t>(val[8 * q + 0]) | (static_cast<uint32_t>(val[8 * q + 1]) << 16);
-                    p.y = static_cast<uint32_t>(val[8 * q + 2]) | (static_cast<uint32_t>(val[8 * q + 3]) << 16);
-                    p.z = static_cast<uint32_t>(val[8 * q + 4]) | (static_cast<uint32_t>(val[8 * q + 5]) << 16);
-                    p.w = static_cast<uint32_t>(val[8 * q + 6]) | (static_cast<uint32_t>(val[8 * q + 7]) << 16);
-                    dst[q] = p;
+                    uint4 pk;
+                    pk.x = static_cast<uint32_t>(val[8 * q + 0]) | (static_cast<uint32_t>(val[8 * q + 1]) << 16);
+                    pk.y = static_cast<uint32_t>(val[8 * q + 2]) | (static_cast<uint32_t>(val[8 * q + 3]) << 16);
+                    pk.z = static_cast<uint32_t>(val[8 * q + 4]) | (static_cast<uint32_t>(val[8 * q + 5]) << 16);
+                    pk.w = static_cast<uint32_t>(val[8 * q + 6]) | (static_cast<uint32_t>(val[8 * q + 7]) << 16);
+                    dst[q] = pk;
                 }
                 // column sums over this warp's 32 rows (butterfly transpose-reduce):
                 // afterwards lane l holds the sum of column col0 + l
@@ -225,31 +233,33 @@ sc2_tcgen05_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
             if (lane == 0) mbar_arrive(&tempty[buf]);
         }
     }
-    if (!ok && lane == 0) atomicOr(&v.ctl->err, TR_ERR_TIMEOUT);
+    if (!ok && lane == 0) atomicOr(&bt.views[0].ctl->err, TR_ERR_TIMEOUT);
     tc_fence_before();
     __syncthreads();
-    if (kSmemHist)
-        for (int b = threadIdx.x + 1; b < nbins; b += blockDim.x)
-            if (shist[b]) atomicAdd(&v.hist[b], shist[b]);
     if (warp == 0) {
         tc_fence_after();
         tmem_dealloc(tmem, kTmemCols);
     }
+    if (!kSingle) return;
+    const ProbView v0 = bt.views[0];
+    for (int b = threadIdx.x + 1; b < nbins; b += blockDim.x)
+        if (shist[b]) atomicAdd(&v0.hist[b], shist[b]);
     // the last CTA to finish sees the complete histogram: choose the pivot threshold
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) sel_buf[40] = atomicAdd(&v.ctl->done_blocks, 1u) == gridDim.x - 1;
+    if (threadIdx.x == 0) sel_buf[40] = atomicAdd(&v0.ctl->done_blocks, 1u) == gridDim.x - 1;
     __syncthreads();
     if (!sel_buf[40]) return;
     __threadfence();
-    select_alpha(v, sel_buf);
+    select_alpha(v0, sel_buf);
 }
 
 // CUDA-core alternative: block per row i; W_ij = popc(row_i & row_j) for j > i with G_ij.
-__global__ void __launch_bounds__(256) sc2_bitset_kernel(ProbView v)
+__global__ void __launch_bounds__(256) sc2_bitset_kernel(ManyViews vs)
 {
     extern __shared__ uint32_t srow[];
-    const int i = blockIdx.x;
+    int i;
+    const ProbView v = vs.get(ST_BITSET, blockIdx.x, i);
     const uint32_t* bi = v.bits + (size_t)i * v.ldb;
     for (int q = threadIdx.x; q < v.ldb; q += blockDim.x) srow[q] = bi[q];
     __syncthreads();
@@ -295,25 +305,29 @@ cudaError_t sc2_tcgen05_setup()
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(sc2_tcgen05_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  kPipeBytes + kBarBytes + 1024);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(sc2_bitset_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 TURBOREG_MAX_N / 8);
     return e;
 }
 
-void launch_sc2_tcgen05(const ProbView& v, const CUtensorMap& tmA, const CUtensorMap& tmB, cudaStream_t s)
+// A single problem keeps its histogram in shared memory when it fits; a
+// batch (or a very large problem) uses global atomics.
+void launch_sc2_tcgen05(const Batch& b, int total_tiles, int max_n, cudaStream_t s)
 {
-    const int nb = v.n_pad / kSc2BN;
-    const int tiles = nb * (nb + 1);
-    const int grid = tiles < g_sc2_sms ? tiles : (g_sc2_sms > 0 ? g_sc2_sms : 148);
+    const int sms = g_sc2_sms > 0 ? g_sc2_sms : 148;
+    const int grid = total_tiles < sms ? total_tiles : sms;
     const size_t base = kPipeBytes + kBarBytes + 1024;
-    const size_t hist = static_cast<size_t>(v.n + 1) * 4;
-    if (base + hist <= static_cast<size_t>(kSmemMax))
-        sc2_tcgen05_kernel<true><<<grid, kThreads, base + hist, s>>>(tmA, tmB, v);
+    const size_t hist = static_cast<size_t>(max_n + 1) * 4;
+    if (b.num == 1 && base + hist <= static_cast<size_t>(kSmemMax))
+        sc2_tcgen05_kernel<true><<<grid, kThreads, base + hist, s>>>(b, total_tiles);
     else
-        sc2_tcgen05_kernel<false><<<grid, kThreads, base, s>>>(tmA, tmB, v);
+        sc2_tcgen05_kernel<false><<<grid, kThreads, base, s>>>(b, total_tiles);
 }
 
-void launch_sc2_bitset(const ProbView& v, cudaStream_t s)
+void launch_sc2_bitset(const Batch& b, int total, cudaStream_t s)
 {
-    sc2_bitset_kernel<<<v.n_pad, 256, v.ldb * sizeof(uint32_t), s>>>(v);
+    sc2_bitset_kernel<<<total, 256, TURBOREG_MAX_N / 8, s>>>(ManyViews{b});
 }
 
 }  // namespace tr

@@ -7,7 +7,7 @@
 // Exact radix-style selection (no atomics on shared counters, so the result
 // and its cost do not depend on contention):
 //   hist    histogram of edge weights (built by the SC^2 GEMM epilogue, or
-//           by hist_kernel for the CUDA-core SC^2 path)
+//           by hist_kernel for the CUDA-core SC^2 path and for callers)
 //   select  one block: alpha = K1-th largest weight, c_gt = #{W > alpha},
 //           m = K1' - c_gt ties still needed (K1' = min(K1, |E+|))
 //   count   warp per row: #{j : W_ij > alpha} and #{j : W_ij == alpha}
@@ -26,6 +26,7 @@ namespace tr {
 namespace {
 
 constexpr int kHistSmemMaxBins = 24576;   // 96 KB of shared bins; larger N uses global atomics
+constexpr int kHistRowsPerBlock = 64;     // 8 warps x 8 rows
 
 __device__ __forceinline__ uint64_t edge_key(int w, int i, int j, int n)
 {
@@ -35,7 +36,7 @@ __device__ __forceinline__ uint64_t edge_key(int w, int i, int j, int n)
 
 // Iterate row i's upper-triangle entries j in (i, n) in chunks of 8 uint16
 // (16-byte loads); lane l takes chunks c0 + l, c0 + l + 32, ..., two loads in
-// flight per lane.
+// flight per lane.  Chunks whose 8 weights are all zero are skipped.
 template <typename F>
 __device__ __forceinline__ void for_row_chunks(const ProbView& v, int i, int lane, F&& f)
 {
@@ -57,19 +58,23 @@ __device__ __forceinline__ void for_row_chunks(const ProbView& v, int i, int lan
     }
 }
 
-template <bool kSmem>
-__global__ void __launch_bounds__(256) hist_kernel(ProbView v)
+// Histogram of edge weights (used when SC^2 comes from the CUDA-core path or
+// from a caller): 64 rows per block, shared-memory bins when they fit.
+template <class VS, bool kSmem>
+__global__ void __launch_bounds__(256) hist_kernel(VS vs)
 {
     extern __shared__ uint32_t sh[];
+    int lb;
+    const ProbView v = vs.get(ST_HIST, blockIdx.x, lb);
     const int nb = v.n + 1;
     if (kSmem) {
         for (int q = threadIdx.x; q < nb; q += blockDim.x) sh[q] = 0;
         __syncthreads();
     }
-    const int lane = threadIdx.x & 31;
-    const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nw = (gridDim.x * blockDim.x) >> 5;
-    for (int i = wid; i < v.n; i += nw) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int r = 0; r < kHistRowsPerBlock / 8; ++r) {
+        const int i = lb * kHistRowsPerBlock + warp * (kHistRowsPerBlock / 8) + r;
+        if (i >= v.n) break;
         for_row_chunks(v, i, lane, [&](int, int w) {
             if (w > 0) {
                 if (kSmem) atomicAdd(&sh[w], 1u);
@@ -84,44 +89,50 @@ __global__ void __launch_bounds__(256) hist_kernel(ProbView v)
     }
 }
 
-__global__ void __launch_bounds__(1024) select_kernel(ProbView v)
+template <class VS>
+__global__ void __launch_bounds__(1024) select_kernel(VS vs)
 {
     __shared__ int sbuf[33];
+    int lb;
+    const ProbView v = vs.get(ST_SELECT, blockIdx.x, lb);
     select_alpha(v, sbuf);
 }
 
-// per-row counts of the weight > alpha and weight == alpha edges
-// Per-row counts of the weight > alpha and weight == alpha edges.
-__global__ void __launch_bounds__(256) count_kernel(ProbView v)
+// Per-row counts of the weight > alpha and weight == alpha edges; 8 rows per
+// block, one per warp.
+template <class VS>
+__global__ void __launch_bounds__(256) count_kernel(VS vs)
 {
+    int lb;
+    const ProbView v = vs.get(ST_COUNT, blockIdx.x, lb);
     const int lane = threadIdx.x & 31;
-    const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nw = (gridDim.x * blockDim.x) >> 5;
-    if (v.ctl->n_sel == 0) return;
+    const int i = lb * 8 + (threadIdx.x >> 5);
+    if (v.ctl->n_sel == 0 || i >= v.n) return;
     const int alpha = v.ctl->alpha;
-    for (int i = wid; i < v.n; i += nw) {
-        int gt = 0, eq = 0;
-        for_row_chunks(v, i, lane, [&](int, int w) {
-            gt += w > alpha;
-            eq += w == alpha;
-        });
+    int gt = 0, eq = 0;
+    for_row_chunks(v, i, lane, [&](int, int w) {
+        gt += w > alpha;
+        eq += w == alpha;
+    });
 #pragma unroll
-        for (int off = 16; off >= 1; off >>= 1) {
-            gt += __shfl_xor_sync(0xffffffffu, gt, off);
-            eq += __shfl_xor_sync(0xffffffffu, eq, off);
-        }
-        if (lane == 0) {
-            v.rowcnt[i] = eq;
-            v.rowcnt_gt[i] = gt;
-        }
+    for (int off = 16; off >= 1; off >>= 1) {
+        gt += __shfl_xor_sync(0xffffffffu, gt, off);
+        eq += __shfl_xor_sync(0xffffffffu, eq, off);
+    }
+    if (lane == 0) {
+        v.rowcnt[i] = eq;
+        v.rowcnt_gt[i] = gt;
     }
 }
 
 // Exclusive prefixes of both per-row counts; thread t owns rows
-// [t*per, (t+1)*per), per <= 32, loaded with all loads in flight.
-__global__ void __launch_bounds__(1024) scan_rows_kernel(ProbView v)
+// [t*per, (t+1)*per), per <= 32, with its loads in flight together.
+template <class VS>
+__global__ void __launch_bounds__(1024) scan_rows_kernel(VS vs)
 {
     __shared__ int sbuf[33];
+    int lb;
+    const ProbView v = vs.get(ST_SCAN, blockIdx.x, lb);
     if (v.ctl->n_sel == 0) return;
     const int per = (v.n + blockDim.x - 1) / blockDim.x;
     const int lo = threadIdx.x * per;
@@ -148,14 +159,16 @@ __global__ void __launch_bounds__(1024) scan_rows_kernel(ProbView v)
     }
 }
 
-// One block (256 threads) per row; a thread takes 16-byte chunks tid, tid+256, ...
-// (all of a 32K-wide row's loads are in flight at once).  Blocks whose row
-// holds nothing selected exit at once.
-__global__ void __launch_bounds__(256) emit_kernel(ProbView v)
+// One block (256 threads) per row; a thread takes 4 consecutive 16-byte
+// chunks per sweep (all of a row's loads are in flight at once, thread order
+// = column order).  Blocks whose row holds nothing selected exit at once.
+template <class VS>
+__global__ void __launch_bounds__(256) emit_kernel(VS vs)
 {
     __shared__ int sg[8], se[8];
+    int i;
+    const ProbView v = vs.get(ST_EMIT, blockIdx.x, i);
     if (v.ctl->n_sel == 0) return;
-    const int i = blockIdx.x;
     if (i + 1 >= v.n) return;
     const int m = v.ctl->m_ties;
     const int ng = v.rowcnt_gt[i];
@@ -170,7 +183,6 @@ __global__ void __launch_bounds__(256) emit_kernel(ProbView v)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int base_g = pg, base_e = pe;
     for (int cb = c0; cb <= c1; cb += blockDim.x * 4) {
-        // 4 consecutive chunks per thread per sweep keep column order within the thread
         uint32_t gm = 0, em = 0;   // bit 8*k + e: chunk k, element e
         const int cfirst = cb + threadIdx.x * 4;
 #pragma unroll
@@ -189,7 +201,7 @@ __global__ void __launch_bounds__(256) emit_kernel(ProbView v)
             }
         }
         // block exclusive scans of the two counts (thread order = column order)
-        int g = __popc(gm), eN = __popc(em);
+        const int g = __popc(gm), eN = __popc(em);
         int gi = g, ei = eN;
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
@@ -211,7 +223,7 @@ __global__ void __launch_bounds__(256) emit_kernel(ProbView v)
             const int b = __ffs(gm) - 1;
             gm &= gm - 1;
             const int j = (cfirst + (b >> 3)) * 8 + (b & 7);
-            v.cand[rg++] = edge_key((wrow[j]), i, j, v.n);
+            v.cand[rg++] = edge_key(wrow[j], i, j, v.n);
         }
         while (em) {
             const int b = __ffs(em) - 1;
@@ -226,18 +238,21 @@ __global__ void __launch_bounds__(256) emit_kernel(ProbView v)
 }
 
 // 32 candidates per block (one per lane); the 8 warps split the comparison
-// range; all n_sel keys are staged in shared memory.
-__global__ void __launch_bounds__(256) rank_kernel(ProbView v)
+// range; all n_sel keys of the problem are staged in shared memory.
+template <class VS>
+__global__ void __launch_bounds__(256) rank_kernel(VS vs)
 {
     extern __shared__ uint64_t sk[];
     __shared__ int part[8][32];
+    int lb;
+    const ProbView v = vs.get(ST_RANK, blockIdx.x, lb);
     const int n_sel = v.ctl->n_sel;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (blockIdx.x == 0 && threadIdx.x == 0) v.ctl->n_pivots = n_sel;
-    if (static_cast<int>(blockIdx.x * 32) >= n_sel) return;
+    if (lb == 0 && threadIdx.x == 0) v.ctl->n_pivots = n_sel;
+    if (lb * 32 >= n_sel) return;
     for (int q = threadIdx.x; q < n_sel; q += blockDim.x) sk[q] = v.cand[q];
     __syncthreads();
-    const int e = blockIdx.x * 32 + lane;
+    const int e = lb * 32 + lane;
     const uint64_t key = (e < n_sel) ? sk[e] : ~0ull;
     const int chunk = (n_sel + 7) / 8;
     const int f0 = warp * chunk, f1 = min(n_sel, f0 + chunk);
@@ -259,6 +274,25 @@ __global__ void __launch_bounds__(256) rank_kernel(ProbView v)
 
 int g_num_sms = 0;
 
+template <class VS>
+cudaError_t set_attrs()
+{
+    cudaError_t e = cudaFuncSetAttribute(rank_kernel<VS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         TURBOREG_K1_MAX * 8);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(hist_kernel<VS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                kHistSmemMaxBins * 4);
+}
+
+template <class VS>
+void launch_hist_vs(const VS& vs, int total, int max_n, cudaStream_t s)
+{
+    if (max_n + 1 <= kHistSmemMaxBins)
+        hist_kernel<VS, true><<<total, 256, (max_n + 1) * 4, s>>>(vs);
+    else
+        hist_kernel<VS, false><<<total, 256, 0, s>>>(vs);
+}
+
 }  // namespace
 
 cudaError_t topk_setup()
@@ -268,37 +302,37 @@ cudaError_t topk_setup()
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(rank_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             TURBOREG_K1_MAX * 8);
+    e = set_attrs<ManyViews>();
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(hist_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                kHistSmemMaxBins * 4);
+    return set_attrs<OneView>();
 }
 
-void launch_topk_after_select(const ProbView& v, cudaStream_t s)
+void launch_hist(const Batch& b, int total, int max_n, cudaStream_t s)
 {
-    const int row_blocks = (v.n + 7) / 8;   // one row per warp
-    count_kernel<<<row_blocks, 256, 0, s>>>(v);
-    scan_rows_kernel<<<1, 1024, 0, s>>>(v);
-    emit_kernel<<<v.n, 256, 0, s>>>(v);
-    rank_kernel<<<(v.k1 + 31) / 32, 256, v.k1 * 8, s>>>(v);
+    launch_hist_vs(ManyViews{b}, total, max_n, s);
 }
 
-void launch_topk_after_hist(const ProbView& v, cudaStream_t s)
+void launch_select(const Batch& b, cudaStream_t s) { select_kernel<<<b.num, 1024, 0, s>>>(ManyViews{b}); }
+
+void launch_topk_rest(const Batch& b, const int32_t tot[kNumBatchStages], int max_k1, cudaStream_t s)
 {
-    select_kernel<<<1, 1024, 0, s>>>(v);
-    launch_topk_after_select(v, s);
+    const ManyViews vs{b};
+    count_kernel<<<tot[ST_COUNT], 256, 0, s>>>(vs);
+    scan_rows_kernel<<<b.num, 1024, 0, s>>>(vs);
+    emit_kernel<<<tot[ST_EMIT], 256, 0, s>>>(vs);
+    rank_kernel<<<tot[ST_RANK], 256, max_k1 * 8, s>>>(vs);
 }
 
-void launch_topk(const ProbView& v, cudaStream_t s)
+// One problem passed by value (no device-side problem table).
+void launch_topk_single(const ProbView& v, cudaStream_t s)
 {
-    const int sms = g_num_sms > 0 ? g_num_sms : 148;
-    const int hist_blocks = min((v.n + 7) / 8, 4 * sms);
-    if (v.n + 1 <= kHistSmemMaxBins)
-        hist_kernel<true><<<hist_blocks, 256, (v.n + 1) * 4, s>>>(v);
-    else
-        hist_kernel<false><<<hist_blocks, 256, 0, s>>>(v);
-    launch_topk_after_hist(v, s);
+    const OneView vs{v};
+    launch_hist_vs(vs, (v.n + kHistRowsPerBlock - 1) / kHistRowsPerBlock, v.n, s);
+    select_kernel<<<1, 1024, 0, s>>>(vs);
+    count_kernel<<<(v.n + 7) / 8, 256, 0, s>>>(vs);
+    scan_rows_kernel<<<1, 1024, 0, s>>>(vs);
+    emit_kernel<<<v.n, 256, 0, s>>>(vs);
+    rank_kernel<<<(v.k1 + 31) / 32, 256, v.k1 * 8, s>>>(vs);
 }
 
 }  // namespace tr

@@ -15,6 +15,7 @@ struct Ctl;
 // Points are kept structure-of-arrays: pts[c * n_pad + k] for c in
 // {x0, x1, x2, y0, y1, y2}; padding entries are zero.
 struct ProbView {
+    int64_t in_off;      // first match of this problem in the (concatenated) input arrays
     int32_t n;           // correspondences
     int32_t n_pad;       // n rounded up to 256 (GEMM tile multiple); leading dimension of a8 and w
     int32_t ldb;         // words per bitset row = n_pad / 32
@@ -44,24 +45,79 @@ struct ProbView {
     turboreg_result* res;  // device result
 };
 
-// stage launchers (all asynchronous on `s`)
-void launch_pack(const ProbView& v, const float* src, const float* dst, cudaStream_t s);
+// A group of problems processed by one launch per stage.  Stage k's blocks
+// are numbered consecutively over the problems: problem p owns blocks
+// [pre[k*(num+1) + p], pre[k*(num+1) + p + 1]).
+enum Stage {
+    ST_PACK = 0, ST_COMPAT, ST_SELECT, ST_COUNT, ST_SCAN, ST_EMIT, ST_RANK, ST_PGS, ST_KABSCH, ST_KABSCH64,
+    ST_VERIFY, ST_FINAL, ST_HIST, ST_BITSET, ST_GEMM, kNumBatchStages
+};
+
+struct Batch {
+    const ProbView* views;   // [num] device
+    const int32_t* pre;      // [kNumBatchStages][num + 1] device
+    const CUtensorMap* maps; // [num][2] device (A box 128 rows, B box 256 rows)
+    int32_t num;
+};
+
+#ifdef __CUDACC__
+// Problem owning block b of stage st, and the block's index within it.
+__device__ __forceinline__ int locate(const Batch& bt, int st, int b, int& local)
+{
+    const int32_t* pr = bt.pre + st * (bt.num + 1);
+    int lo = 0, hi = bt.num;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(pr + mid) <= b) lo = mid;
+        else hi = mid;
+    }
+    local = b - __ldg(pr + lo);
+    return lo;
+}
+
+// Where a kernel finds its problem: one problem passed by value ...
+struct OneView {
+    ProbView v;
+    __device__ __forceinline__ ProbView get(int, int b, int& local) const
+    {
+        local = b;
+        return v;
+    }
+};
+// ... or a group of problems, located per block.
+struct ManyViews {
+    Batch bt;
+    __device__ __forceinline__ ProbView get(int st, int b, int& local) const
+    {
+        return bt.views[locate(bt, st, b, local)];
+    }
+};
+#endif
+
+// per-problem block counts of each stage (host side, from n, k1, k2)
+void stage_blocks(int32_t n, int32_t k1, int32_t k2, int32_t blocks[kNumBatchStages]);
+
+// stage launchers (all asynchronous on `s`); total = sum of the stage's blocks
+void launch_pack(const Batch& b, int total, const float* src, const float* dst, cudaStream_t s);
 const void* pack_kernel_func();   // identifies the pack node inside a captured graph
-void launch_compat(const ProbView& v, cudaStream_t s);
-void launch_sc2_tcgen05(const ProbView& v, const CUtensorMap& tmA, const CUtensorMap& tmB, cudaStream_t s);
-void launch_sc2_bitset(const ProbView& v, cudaStream_t s);
-void launch_topk(const ProbView& v, cudaStream_t s);             // histogram pass + selection
-void launch_topk_after_hist(const ProbView& v, cudaStream_t s);  // selection (histogram already built)
-void launch_topk_after_select(const ProbView& v, cudaStream_t s);  // selection (alpha already chosen)
-void launch_pgs(const ProbView& v, cudaStream_t s);
-void launch_kabsch(const ProbView& v, cudaStream_t s);             // FP32 closed form, FP64 list
-void launch_verify(const ProbView& v, cudaStream_t s);             // hypotheses with a valid FP32 Kabsch
-void launch_kabsch_fp64_verify(const ProbView& v, cudaStream_t s); // FP64 list: Kabsch + verification
-void launch_finalize(const ProbView& v, cudaStream_t s);
+void launch_compat(const Batch& b, int total, cudaStream_t s);
+void launch_sc2_tcgen05(const Batch& b, int total_tiles, int max_n, cudaStream_t s);
+void launch_sc2_bitset(const Batch& b, int total, cudaStream_t s);
+void launch_hist(const Batch& b, int total, int max_n, cudaStream_t s);
+void launch_select(const Batch& b, cudaStream_t s);
+void launch_topk_rest(const Batch& b, const int32_t tot[kNumBatchStages], int max_k1, cudaStream_t s);
+void launch_pgs(const Batch& b, int total, int k2_max, cudaStream_t s);
+void launch_kabsch(const Batch& b, int total, cudaStream_t s);
+void launch_kabsch_fp64_verify(const Batch& b, int total64, int total_verify, cudaStream_t s);
+void launch_verify(const Batch& b, int total, cudaStream_t s);
+void launch_finalize(const Batch& b, cudaStream_t s);
 
 // set kernel attributes (dynamic shared memory limits) once per device
 cudaError_t sc2_tcgen05_setup();
 cudaError_t topk_setup();
+
+// single-problem pivot selection used by the allocation-free entry point
+void launch_topk_single(const ProbView& v, cudaStream_t s);
 
 constexpr int kSc2BM = 128;   // GEMM tile rows  (TMEM lanes)
 constexpr int kSc2BN = 256;   // GEMM tile cols  (TMEM columns)

@@ -211,3 +211,41 @@ def test_kappa_distribution_report(ctx):
     kap = RT[(flags & 1) != 0, 12]
     print("kappa quantiles", np.quantile(kap, [0.5, 0.9, 0.99]).round(2), "fp64", int(((flags & 2) != 0).sum()),
           ">1e3", int((kap > 1e3).sum()), "winner kappa", RT[res.hypothesis, 12])
+
+
+def test_batched_uneven_sizes_equal_plain():
+    # a batch of mixed indoor/outdoor problems of uneven N, one launch per stage for all of them
+    probs = synth.make_batch(12, seed=7, n_lo=300, n_hi=3000)
+    c = trg.TurboReg(max_n=3000, max_batch=12)
+    try:
+        params = [trg.default_params(p.tau, p.k1, p.theta) for p in probs]
+        offs = np.cumsum([0] + [p.n for p in probs]).astype(np.int64)
+        xs = np.concatenate([p.x for p in probs])
+        ys = np.concatenate([p.y for p in probs])
+        out = c.register_batched(xs, ys, offs, params)
+        out2 = c.register_batched(xs, ys, offs, params)          # replay of the captured batch graph
+        for p, prm, rb, rb2 in zip(probs, params, out, out2):
+            rp = c.register(p.x, p.y, prm)
+            assert rb.status == rp.status and rb.hypothesis == rp.hypothesis, (p.n, p.shape)
+            assert np.array_equal(rb.R, rp.R) and np.array_equal(rb.t, rp.t)
+            assert rb.inlier_count == rp.inlier_count and rb.n_pivots == rp.n_pivots
+            assert rb2.hypothesis == rb.hypothesis and np.array_equal(rb2.R, rb.R)
+        # the first problem's stage buffers match the oracle after a batched call
+        c.register_batched(xs, ys, offs, params)
+        p = probs[0]
+        A, S, piv, cl = oracle_stages(p.x, p.y, p.tau, p.k1, 2)
+        check_graph_stages(c, A, S, p.n)
+        check_pivots_cliques(c, piv, cl, 2)
+    finally:
+        c.close()
+
+
+def test_batched_direct_launch_mode(ctx):
+    probs = [synth.make_problem("cube", n, 0.1, 80 + n) for n in (700, 1500, 400)]
+    params = [trg.default_params(p.tau, 500, p.theta, flags=trg.FLAG_NO_GRAPH) for p in probs]
+    offs = np.cumsum([0] + [p.n for p in probs]).astype(np.int64)
+    out = ctx.register_batched(np.concatenate([p.x for p in probs]), np.concatenate([p.y for p in probs]),
+                               offs, params)
+    for p, rb in zip(probs, out):
+        rp = ctx.register(p.x, p.y, trg.default_params(p.tau, 500, p.theta))
+        assert rb.hypothesis == rp.hypothesis and np.array_equal(rb.R, rp.R)
