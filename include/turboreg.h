@@ -57,7 +57,8 @@ typedef enum {
 #define TURBOREG_GRAPH_O2 0          /* O2Graph (Def. 2), the paper's default */
 /* proposal */
 #define TURBOREG_PROPOSAL_PLAIN 0    /* pivots = top-K1 SC^2 edges (Eq. 4) */
-#define TURBOREG_PROPOSAL_LEARNED 1  /* pivots re-ranked by the learned inlier MLP */
+#define TURBOREG_PROPOSAL_LEARNED 1  /* pivots ranked by floor(W_ij p_i p_j), p = inlier probability
+                                        of the proposal MLP (set with turboreg_set_proposal_model) */
 /* flags */
 #define TURBOREG_FLAG_SC2_BITSET 0x1u  /* SC^2 by bitset AND+popcount on CUDA cores
                                           instead of the tcgen05 FP8 GEMM (same integers) */
@@ -75,6 +76,9 @@ typedef struct {
     float kappa_fp64;     /* Kabsch runs in FP64 when sigma1/sigma2 of the 3x3 cross-covariance
                              exceeds this bound (0 selects the default 100) */
     uint32_t flags;       /* TURBOREG_FLAG_* */
+    int32_t learned_min_inliers; /* learned proposal: if its best inlier number is below this (or it
+                                    finds no hypothesis) the plain proposal decides the result;
+                                    0 selects max(10, N / 200) */
 } turboreg_params;
 
 typedef struct {

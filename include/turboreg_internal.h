@@ -30,7 +30,9 @@ typedef enum {
                                    flags (as int32 bits: 1 valid, 2 fp64), 2 unused */
     TURBOREG_BUF_INLIERS = 7,   /* int32 [k2*n_pivots]: inlier number per hypothesis */
     TURBOREG_BUF_ROWSCORE = 8,  /* int32 [n]: sum_j G^_ij (SC^2 row score) */
-    TURBOREG_BUF_DEGREE = 9     /* int32 [n]: sum_j G_ij (degree in the compatibility graph) */
+    TURBOREG_BUF_DEGREE = 9,    /* int32 [n]: sum_j G_ij (degree in the compatibility graph) */
+    TURBOREG_BUF_FEATURES = 10, /* float [n][8]: proposal features (learned proposal) */
+    TURBOREG_BUF_PROB = 11      /* float [n]: proposal inlier probabilities (learned proposal) */
 } turboreg_buffer;
 
 /* Shape of the most recent turboreg_register call: n, n_pad, |P| and the
@@ -49,6 +51,47 @@ int turboreg_stage_times(turboreg_ctx* ctx, float* ms, int32_t max);
 
 /* Names of the stages reported by turboreg_stage_times. */
 const char* turboreg_stage_name(int32_t stage);
+
+/* ---- learned proposal (project extension; the paper ranks pivots by SC^2 alone) ----
+ * A per-correspondence inlier-scoring MLP 8 -> 64 -> 128 -> 64 -> 1 (ReLU,
+ * sigmoid output), BF16 weights and activations, FP32 accumulation.  Its
+ * parameters are one FP32 vector of TURBOREG_MLP_PARAMS values, row-major
+ * [out][in]: W1[64][8] b1[64] W2[128][64] b2[128] W3[64][128] b3[64] W4[64] b4[1].
+ * Features of correspondence i (8 floats): (x_i - mean x)/rms_x (3),
+ * (y_i - mean y)/rms_y (3), degree_i / N, SC^2 row score_i / max row score. */
+#define TURBOREG_MLP_PARAMS 17217
+
+/* Set the proposal model of a context (host FP32 parameter vector, copied). */
+int turboreg_set_proposal_model(turboreg_ctx* ctx, const float* params);
+
+/* Features of one problem: runs the compatibility graph and SC^2 and writes
+ * feat[n][8] (float32; host or device pointer). */
+int turboreg_features(turboreg_ctx* ctx, const float* src, const float* dst, int32_t n,
+                      const turboreg_params* params, float* feat);
+
+typedef struct turboreg_mlp turboreg_mlp;   /* trainer: FP32 master weights, Adam moments, scratch */
+
+/* Create a trainer on `device` for mini-batches of up to max_samples rows;
+ * weights are He-initialised from `seed`.  cuda_stream: cudaStream_t or NULL. */
+int turboreg_mlp_create(int device, int32_t max_samples, uint64_t seed, void* cuda_stream, turboreg_mlp** out);
+void turboreg_mlp_destroy(turboreg_mlp* t);   /* NULL-safe */
+/* Parameters (host FP32 [TURBOREG_MLP_PARAMS]). */
+int turboreg_mlp_get_params(turboreg_mlp* t, float* params);
+int turboreg_mlp_set_params(turboreg_mlp* t, const float* params);
+/* Adam state (host FP32 [TURBOREG_MLP_PARAMS] each, and the step count). */
+int turboreg_mlp_get_state(turboreg_mlp* t, float* m, float* v, int32_t* step);
+int turboreg_mlp_set_state(turboreg_mlp* t, const float* m, const float* v, int32_t step);
+/* Inference: prob[k] = p(inlier) for feat[k][8], k < m (device pointers). */
+int turboreg_mlp_forward(turboreg_mlp* t, const float* feat, int32_t m, float* prob);
+/* Gradient of the mean binary cross-entropy over (feat, label) (device
+ * pointers, labels 0/1 as float) w.r.t. the parameters: grad (host
+ * [TURBOREG_MLP_PARAMS]) and loss (host). */
+int turboreg_mlp_grad(turboreg_mlp* t, const float* feat, const float* label, int32_t m, float* grad,
+                      float* loss);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on the mean BCE of the
+ * mini-batch; loss (host, may be NULL) receives the loss before the step. */
+int turboreg_mlp_train_step(turboreg_mlp* t, const float* feat, const float* label, int32_t m, float lr,
+                            float* loss);
 
 /* Largest n accepted by turboreg_select_pivots_noalloc. */
 #define TURBOREG_NOALLOC_MAX_N 8192

@@ -31,21 +31,27 @@ FLAG_SC2_BITSET = 0x1
 FLAG_STAGE_TIMES = 0x2
 FLAG_NO_GRAPH = 0x4
 
-BUF_ADJ_BITS, BUF_ADJ_FP8, BUF_SC2, BUF_PIVOTS, BUF_CLIQUES, BUF_RT, BUF_INLIERS, BUF_ROWSCORE, BUF_DEGREE = range(1, 10)
+(BUF_ADJ_BITS, BUF_ADJ_FP8, BUF_SC2, BUF_PIVOTS, BUF_CLIQUES, BUF_RT, BUF_INLIERS, BUF_ROWSCORE, BUF_DEGREE,
+ BUF_FEATURES, BUF_PROB) = range(1, 12)
 
 # symbols the library must export (declared in include/turboreg.h and include/turboreg_internal.h)
 EXPORTED = (
     "turboreg_default_params", "turboreg_create", "turboreg_register", "turboreg_register_batched",
     "turboreg_destroy", "turboreg_status_string", "turboreg_debug_shape", "turboreg_debug_copy",
     "turboreg_stage_times", "turboreg_stage_name", "turboreg_select_pivots_noalloc",
+    "turboreg_set_proposal_model", "turboreg_features", "turboreg_mlp_create", "turboreg_mlp_destroy",
+    "turboreg_mlp_get_params", "turboreg_mlp_set_params", "turboreg_mlp_get_state", "turboreg_mlp_set_state",
+    "turboreg_mlp_forward", "turboreg_mlp_grad", "turboreg_mlp_train_step",
 )
+TURBOREG_MLP_PARAMS = 17217
 TURBOREG_NOALLOC_MAX_N = 8192
 
 
 class turboreg_params(ctypes.Structure):
     _fields_ = [("tau", ctypes.c_float), ("k1", ctypes.c_int32), ("k2", ctypes.c_int32),
                 ("inlier_thresh", ctypes.c_float), ("graph_mode", ctypes.c_int32),
-                ("proposal", ctypes.c_int32), ("kappa_fp64", ctypes.c_float), ("flags", ctypes.c_uint32)]
+                ("proposal", ctypes.c_int32), ("kappa_fp64", ctypes.c_float), ("flags", ctypes.c_uint32),
+                ("learned_min_inliers", ctypes.c_int32)]
 
 
 class turboreg_result(ctypes.Structure):
@@ -93,6 +99,23 @@ def load_library(path: str = LIB_PATH):
     lib.turboreg_stage_name.restype = ctypes.c_char_p
     lib.turboreg_select_pivots_noalloc.argtypes = [P, i32, i32, i32, P, P, P]
     lib.turboreg_select_pivots_noalloc.restype = ctypes.c_int
+    F = ctypes.POINTER(ctypes.c_float)
+    lib.turboreg_set_proposal_model.argtypes = [P, P]
+    lib.turboreg_features.argtypes = [P, P, P, i32, ctypes.POINTER(turboreg_params), P]
+    lib.turboreg_mlp_create.argtypes = [ctypes.c_int, i32, ctypes.c_uint64, P, ctypes.POINTER(P)]
+    lib.turboreg_mlp_destroy.argtypes = [P]
+    lib.turboreg_mlp_destroy.restype = None
+    lib.turboreg_mlp_get_params.argtypes = [P, P]
+    lib.turboreg_mlp_set_params.argtypes = [P, P]
+    lib.turboreg_mlp_get_state.argtypes = [P, P, P, ctypes.POINTER(i32)]
+    lib.turboreg_mlp_set_state.argtypes = [P, P, P, i32]
+    lib.turboreg_mlp_forward.argtypes = [P, P, i32, P]
+    lib.turboreg_mlp_grad.argtypes = [P, P, P, i32, P, F]
+    lib.turboreg_mlp_train_step.argtypes = [P, P, P, i32, ctypes.c_float, F]
+    for nm in ("turboreg_set_proposal_model", "turboreg_features", "turboreg_mlp_create", "turboreg_mlp_get_params",
+               "turboreg_mlp_set_params", "turboreg_mlp_get_state", "turboreg_mlp_set_state",
+               "turboreg_mlp_forward", "turboreg_mlp_grad", "turboreg_mlp_train_step"):
+        getattr(lib, nm).restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -118,13 +141,15 @@ def _check_points(a, n=None):
         raise ValueError("src and dst must have the same number of rows")
 
 
-def default_params(tau, k1, inlier_thresh, k2=2, kappa_fp64=100.0, flags=0, proposal=PROPOSAL_PLAIN):
+def default_params(tau, k1, inlier_thresh, k2=2, kappa_fp64=100.0, flags=0, proposal=PROPOSAL_PLAIN,
+                   learned_min_inliers=0):
     p = turboreg_params()
     load_library().turboreg_default_params(ctypes.byref(p), float(tau), int(k1), float(inlier_thresh))
     p.k2 = int(k2)
     p.kappa_fp64 = float(kappa_fp64)
     p.flags = int(flags)
     p.proposal = int(proposal)
+    p.learned_min_inliers = int(learned_min_inliers)
     return p
 
 
@@ -228,6 +253,8 @@ class TurboReg:
             BUF_INLIERS: (np.int32, (nh,)),
             BUF_ROWSCORE: (np.int32, (n,)),
             BUF_DEGREE: (np.int32, (n,)),
+            BUF_FEATURES: (np.float32, (n, 8)),
+            BUF_PROB: (np.float32, (n,)),
         }[which]
         arr = np.zeros(spec[1], dtype=spec[0])
         got = self._lib.turboreg_debug_copy(self.handle, int(which), ctypes.c_void_p(arr.ctypes.data),
@@ -235,6 +262,26 @@ class TurboReg:
         if got < 0:
             raise RuntimeError(status_string(-got))
         return arr
+
+    def set_proposal_model(self, params):
+        w = np.ascontiguousarray(params, dtype=np.float32)
+        if w.shape != (TURBOREG_MLP_PARAMS,):
+            raise ValueError("proposal model needs TURBOREG_MLP_PARAMS float32 values")
+        rc = self._lib.turboreg_set_proposal_model(self.handle, ctypes.c_void_p(w.ctypes.data))
+        if rc != OK:
+            raise RuntimeError(f"turboreg_set_proposal_model failed: {status_string(rc)}")
+
+    def features(self, src, dst, params, out=None):
+        """Proposal features [n, 8] (float32); `out` may be a CUDA tensor."""
+        _check_points(src)
+        _check_points(dst, src.shape[0])
+        n = int(src.shape[0])
+        if out is None:
+            out = np.zeros((n, 8), dtype=np.float32)
+        rc = self._lib.turboreg_features(self.handle, _ptr(src), _ptr(dst), n, ctypes.byref(params), _ptr(out))
+        if rc != OK:
+            raise RuntimeError(f"turboreg_features failed: {status_string(rc)}")
+        return out
 
     def stage_times(self):
         buf = (ctypes.c_float * 16)()
@@ -267,3 +314,97 @@ def turboreg_select_pivots_noalloc(w_dev, n, ldw, k1, pivots_dev, n_pivots_dev, 
     st = ctypes.c_void_p(stream) if stream else None
     return load_library().turboreg_select_pivots_noalloc(_ptr(w_dev), int(n), int(ldw), int(k1),
                                                          _ptr(pivots_dev), _ptr(n_pivots_dev), st)
+
+
+class MLPTrainer:
+    """Device-side trainer of the proposal MLP (forward/backward/Adam kernels)."""
+
+    def __init__(self, max_samples=65536, seed=0, device=0, stream=None):
+        self._lib = load_library()
+        h = ctypes.c_void_p()
+        st = ctypes.c_void_p(stream) if stream else None
+        rc = self._lib.turboreg_mlp_create(int(device), int(max_samples), int(seed), st, ctypes.byref(h))
+        if rc != OK:
+            raise RuntimeError(f"turboreg_mlp_create failed: {status_string(rc)}")
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self._lib.turboreg_mlp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _chk(self, rc, what):
+        if rc != OK:
+            raise RuntimeError(f"{what} failed: {status_string(rc)}")
+
+    def get_params(self):
+        w = np.zeros(TURBOREG_MLP_PARAMS, dtype=np.float32)
+        self._chk(self._lib.turboreg_mlp_get_params(self.handle, ctypes.c_void_p(w.ctypes.data)), "get_params")
+        return w
+
+    def set_params(self, w):
+        w = np.ascontiguousarray(w, dtype=np.float32)
+        self._chk(self._lib.turboreg_mlp_set_params(self.handle, ctypes.c_void_p(w.ctypes.data)), "set_params")
+
+    def get_state(self):
+        m = np.zeros(TURBOREG_MLP_PARAMS, dtype=np.float32)
+        v = np.zeros_like(m)
+        st = ctypes.c_int32()
+        self._chk(self._lib.turboreg_mlp_get_state(self.handle, ctypes.c_void_p(m.ctypes.data),
+                                                   ctypes.c_void_p(v.ctypes.data), ctypes.byref(st)), "get_state")
+        return m, v, int(st.value)
+
+    def set_state(self, m, v, step):
+        m = np.ascontiguousarray(m, dtype=np.float32)
+        v = np.ascontiguousarray(v, dtype=np.float32)
+        self._chk(self._lib.turboreg_mlp_set_state(self.handle, ctypes.c_void_p(m.ctypes.data),
+                                                   ctypes.c_void_p(v.ctypes.data), int(step)), "set_state")
+
+    def forward(self, feat_dev, prob_dev):
+        self._chk(self._lib.turboreg_mlp_forward(self.handle, _ptr(feat_dev), int(feat_dev.shape[0]),
+                                                 _ptr(prob_dev)), "forward")
+
+    def grad(self, feat_dev, label_dev):
+        g = np.zeros(TURBOREG_MLP_PARAMS, dtype=np.float32)
+        loss = ctypes.c_float()
+        self._chk(self._lib.turboreg_mlp_grad(self.handle, _ptr(feat_dev), _ptr(label_dev), int(feat_dev.shape[0]),
+                                              ctypes.c_void_p(g.ctypes.data), ctypes.byref(loss)), "grad")
+        return g, float(loss.value)
+
+    def train_step(self, feat_dev, label_dev, lr, want_loss=False):
+        loss = ctypes.c_float()
+        self._chk(self._lib.turboreg_mlp_train_step(self.handle, _ptr(feat_dev), _ptr(label_dev),
+                                                    int(feat_dev.shape[0]), float(lr),
+                                                    ctypes.byref(loss) if want_loss else None), "train_step")
+        return float(loss.value) if want_loss else None
+
+    # checkpoint: flat binary with a header (magic, version, params, step, seed) + weights + Adam moments
+    def save(self, path, seed=0):
+        w = self.get_params()
+        m, v, step = self.get_state()
+        hdr = np.array([0x54524D4C, 1, TURBOREG_MLP_PARAMS, step, seed], dtype=np.int64)
+        with open(path, "wb") as f:
+            f.write(hdr.tobytes()); f.write(w.tobytes()); f.write(m.tobytes()); f.write(v.tobytes())
+
+    def load(self, path):
+        w, m, v, step = load_checkpoint(path)
+        self.set_params(w)
+        self.set_state(m, v, step)
+        return step
+
+
+def load_checkpoint(path):
+    """(params, adam_m, adam_v, step) of a checkpoint written by MLPTrainer.save."""
+    raw = open(path, "rb").read()
+    hdr = np.frombuffer(raw[:40], dtype=np.int64)
+    if hdr[0] != 0x54524D4C or hdr[2] != TURBOREG_MLP_PARAMS:
+        raise ValueError(f"{path}: not a proposal-MLP checkpoint")
+    P = TURBOREG_MLP_PARAMS
+    body = np.frombuffer(raw[40:], dtype=np.float32)
+    return body[:P].copy(), body[P:2 * P].copy(), body[2 * P:3 * P].copy(), int(hdr[3])

@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "tr_common.cuh"
+#include "tr_mlp.h"
 #include "tr_problem.h"
 #include "turboreg.h"
 #include "turboreg_internal.h"
@@ -55,6 +56,8 @@ struct Workspace {
     float* rt = nullptr;             // [slots][nh * 16]
     int32_t* inl = nullptr;          // [slots][nh]
     int32_t* fp64_list = nullptr;    // [slots][nh]
+    float* feat = nullptr;           // [slots][np][8] proposal features
+    float* prob = nullptr;           // [slots][np] proposal probabilities
     Ctl* ctl = nullptr;              // [slots]
     turboreg_result* res = nullptr;  // [slots]
     float* in_src = nullptr;         // staging for host inputs [max_n * slots * 3]
@@ -72,7 +75,7 @@ struct Workspace {
 struct Plan {
     int32_t num = 0;
     int32_t max_n = 0, max_k1 = 0, k2_common = 0;
-    int32_t bitset = 0, timed = 0;
+    int32_t bitset = 0, timed = 0, learned = 0;
     int32_t tot[kNumBatchStages] = {};
 };
 
@@ -94,6 +97,8 @@ struct turboreg_ctx {
     cudaEvent_t fork_ev = nullptr, join_ev = nullptr;  // concurrently with the main verification
     Workspace ws;
     turboreg_result* host_res = nullptr;   // pinned [max_batch]
+    float* mlp_wbf = nullptr;              // proposal model (BF16-rounded FP32 values), device
+    bool has_model = false;
     EncodeTiledFn encode = nullptr;
     cudaEvent_t ev[kNumStages + 1] = {};
     float stage_ms[kNumStages] = {};
@@ -145,7 +150,8 @@ cudaError_t halloc(T** p, size_t count)
 void free_ws(Workspace& ws)
 {
     void* dptrs[] = {ws.pts, ws.pts8, ws.a8, ws.bits, ws.w, ws.rows, ws.hist, ws.cand, ws.piv, ws.cliques,
-                     ws.rt, ws.inl, ws.fp64_list, ws.ctl, ws.res, ws.in_src, ws.in_dst, ws.desc};
+                     ws.rt, ws.inl, ws.fp64_list, ws.feat, ws.prob, ws.ctl, ws.res, ws.in_src, ws.in_dst,
+                     ws.desc};
     for (void* p : dptrs)
         if (p) cudaFree(p);
     void* hptrs[] = {ws.h_views, ws.h_pre, ws.h_maps};
@@ -179,6 +185,8 @@ int alloc_ws(Workspace& ws, int32_t max_n, int32_t slots)
     if (e == cudaSuccess) e = dalloc(&ws.rt, S * nh * 16);
     if (e == cudaSuccess) e = dalloc(&ws.inl, S * nh);
     if (e == cudaSuccess) e = dalloc(&ws.fp64_list, S * nh);
+    if (e == cudaSuccess) e = dalloc(&ws.feat, S * np * 8);
+    if (e == cudaSuccess) e = dalloc(&ws.prob, S * np);
     if (e == cudaSuccess) e = dalloc(&ws.ctl, S);
     if (e == cudaSuccess) e = dalloc(&ws.res, S);
     if (e == cudaSuccess) e = dalloc(&ws.in_src, S * max_n * 3);
@@ -210,7 +218,10 @@ int check_params(const turboreg_ctx* c, int32_t n, const turboreg_params* p)
     if (!(p->tau >= 0.f) || !std::isfinite(p->tau) || !(p->inlier_thresh > 0.f) || !std::isfinite(p->inlier_thresh))
         return TURBOREG_ERR_INVALID_ARG;
     if (p->graph_mode != TURBOREG_GRAPH_O2) return TURBOREG_ERR_INVALID_ARG;
-    if (p->proposal != TURBOREG_PROPOSAL_PLAIN) return TURBOREG_ERR_INVALID_ARG;
+    if (p->proposal != TURBOREG_PROPOSAL_PLAIN &&
+        !(p->proposal == TURBOREG_PROPOSAL_LEARNED && c->has_model))
+        return TURBOREG_ERR_INVALID_ARG;
+    if (p->learned_min_inliers < 0) return TURBOREG_ERR_INVALID_ARG;
     if (p->kappa_fp64 < 0.f || std::isnan(p->kappa_fp64)) return TURBOREG_ERR_INVALID_ARG;
     return TURBOREG_OK;
 }
@@ -274,6 +285,8 @@ ProbView make_view(turboreg_ctx* c, int slot, int64_t in_off, int32_t n, const t
     v.rt = ws.rt + s * ws.nh * 16;
     v.inl = ws.inl + s * ws.nh;
     v.fp64_list = ws.fp64_list + s * ws.nh;
+    v.feat = ws.feat + s * np * 8;
+    v.prob = p->proposal == TURBOREG_PROPOSAL_LEARNED ? ws.prob + s * np : nullptr;
     v.ctl = ws.ctl + s;
     v.res = ws.res + s;
     return v;
@@ -319,6 +332,7 @@ int build_plan(turboreg_ctx* c, int32_t num, const int64_t* in_off, const int32_
     plan.num = num;
     plan.bitset = (prm[0]->flags & TURBOREG_FLAG_SC2_BITSET) != 0;
     plan.timed = num == 1 && (prm[0]->flags & TURBOREG_FLAG_STAGE_TIMES) != 0;
+    plan.learned = prm[0]->proposal == TURBOREG_PROPOSAL_LEARNED;
     plan.k2_common = prm[0]->k2;
     for (int st = 0; st < kNumBatchStages; ++st) ws.h_pre[st * (num + 1)] = 0;
     for (int32_t b = 0; b < num; ++b) {
@@ -379,7 +393,15 @@ int enqueue_plan(turboreg_ctx* c, const Plan& pl, const Batch& bt, const float* 
         // one problem: the GEMM builds the histogram in shared memory and its
         // last CTA chooses the threshold; a batch adds a select launch
         launch_sc2_tcgen05(bt, pl.tot[ST_GEMM], pl.max_n, s);
-        if (pl.num > 1) launch_select(bt, s);
+        if (pl.num > 1 && !pl.learned) launch_select(bt, s);
+    }
+    if (pl.learned) {
+        // learned proposal: features -> MLP -> histogram of floor(W p_i p_j) -> threshold
+        TR_CHECK(cudaMemsetAsync(c->ws.hist, 0, sizeof(uint32_t) * (c->ws.np + 1) * pl.num, s));
+        launch_features(bt, s);
+        launch_mlp_proposal(bt, pl.tot[ST_MLP], c->mlp_wbf, s);
+        launch_hist(bt, pl.tot[ST_HIST], pl.max_n, s);
+        launch_select(bt, s);
     }
     TR_EV(3);
     launch_topk_rest(bt, pl.tot, pl.max_k1, s);
@@ -518,6 +540,17 @@ int collect_times(turboreg_ctx* c)
     return TURBOREG_OK;
 }
 
+// Learned proposal fallback rule: the plain proposal decides when the learned
+// run found no hypothesis or its best inlier number is below the floor.
+bool needs_fallback(const turboreg_result& r, int32_t n, const turboreg_params* p)
+{
+    if (p->proposal != TURBOREG_PROPOSAL_LEARNED) return false;
+    if (r.status == TURBOREG_ERR_NO_HYPOTHESIS) return true;
+    if (r.status != TURBOREG_OK) return false;
+    const int32_t floor_in = p->learned_min_inliers > 0 ? p->learned_min_inliers : (n / 200 > 10 ? n / 200 : 10);
+    return r.inlier_count < floor_in;
+}
+
 }  // namespace
 
 extern "C" {
@@ -614,6 +647,7 @@ int turboreg_create(int device, int32_t max_n, int32_t max_batch, void* cuda_str
     c->encode = reinterpret_cast<EncodeTiledFn>(fn);
     cudaError_t se = sc2_tcgen05_setup();
     if (se == cudaSuccess) se = topk_setup();
+    if (se == cudaSuccess) se = mlp_setup();
     if (se != cudaSuccess) {
         std::fprintf(stderr, "turboreg: kernel set-up failed: %s\n", cudaGetErrorString(se));
         cudaGetLastError();
@@ -639,6 +673,7 @@ void turboreg_destroy(turboreg_ctx* c)
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     free_ws(c->ws);
     if (c->host_res) cudaFreeHost(c->host_res);
+    if (c->mlp_wbf) cudaFree(c->mlp_wbf);
     delete c;
 }
 
@@ -691,6 +726,14 @@ int turboreg_register(turboreg_ctx* c, const float* src, const float* dst, int32
     rc = collect_times(c);
     if (rc != TURBOREG_OK) return rc;
     *out = c->host_res[0];
+    if (needs_fallback(*out, n, p)) {
+        turboreg_params q = *p;
+        q.proposal = TURBOREG_PROPOSAL_PLAIN;
+        q.flags &= ~TURBOREG_FLAG_STAGE_TIMES;
+        const int rc2 = turboreg_register(c, s_in, d_in, n, &q, out);
+        out->used_fallback = 1;
+        return rc2;
+    }
     return out->status;
 }
 
@@ -710,8 +753,9 @@ int turboreg_register_batched(turboreg_ctx* c, const float* src_cat, const float
     if (total > static_cast<int64_t>(c->max_n) * c->max_batch) return TURBOREG_ERR_INVALID_ARG;
     const uint32_t mode = params->flags & (TURBOREG_FLAG_SC2_BITSET | TURBOREG_FLAG_NO_GRAPH);
     for (int32_t b = 0; b < params_count; ++b)
-        if ((params[b].flags & (TURBOREG_FLAG_SC2_BITSET | TURBOREG_FLAG_NO_GRAPH)) != mode)
-            return TURBOREG_ERR_INVALID_ARG;   // one SC^2 path and launch mode per batch
+        if ((params[b].flags & (TURBOREG_FLAG_SC2_BITSET | TURBOREG_FLAG_NO_GRAPH)) != mode ||
+            params[b].proposal != params->proposal)
+            return TURBOREG_ERR_INVALID_ARG;   // one SC^2 path, launch mode and proposal per batch
     TR_CHECK(cudaSetDevice(c->device));
     const bool dsrc = is_device_ptr(src_cat), ddst = is_device_ptr(dst_cat);
     const size_t bytes = static_cast<size_t>(total) * 3 * sizeof(float);
@@ -755,9 +799,39 @@ int turboreg_register_batched(turboreg_ctx* c, const float* src_cat, const float
     }
     TR_CHECK(cudaStreamSynchronize(c->stream));
     int32_t q = 0;
+    std::vector<int32_t> fb;   // problems the plain proposal must decide (learned fallback)
     for (int32_t b = 0; b < num; ++b) {
         if (pre[b] != TURBOREG_OK) fail_result(&out[b], pre[b]);
-        else out[b] = c->host_res[q++];
+        else {
+            out[b] = c->host_res[q++];
+            const turboreg_params* p = params_count == 1 ? params : params + b;
+            if (needs_fallback(out[b], static_cast<int32_t>(offsets[b + 1] - offsets[b]), p)) fb.push_back(b);
+        }
+    }
+    if (!fb.empty()) {
+        std::vector<int32_t> fn;
+        std::vector<int64_t> fo;
+        std::vector<turboreg_params> fq;
+        for (int32_t b : fb) {
+            turboreg_params pq = params_count == 1 ? params[0] : params[b];
+            pq.proposal = TURBOREG_PROPOSAL_PLAIN;
+            fq.push_back(pq);
+            fn.push_back(static_cast<int32_t>(offsets[b + 1] - offsets[b]));
+            fo.push_back(offsets[b]);
+        }
+        std::vector<const turboreg_params*> fp(fq.size());
+        for (size_t k = 0; k < fq.size(); ++k) fp[k] = &fq[k];
+        Plan pl;
+        int rc = build_plan(c, static_cast<int32_t>(fb.size()), fo.data(), fn.data(), fp.data(), pl);
+        if (rc == TURBOREG_OK) rc = run_plan(c, pl, (mode & TURBOREG_FLAG_NO_GRAPH) != 0, s_in, d_in);
+        if (rc != TURBOREG_OK) return rc;
+        TR_CHECK(cudaMemcpyAsync(c->host_res, c->ws.res, sizeof(turboreg_result) * fb.size(),
+                                 cudaMemcpyDeviceToHost, c->stream));
+        TR_CHECK(cudaStreamSynchronize(c->stream));
+        for (size_t k = 0; k < fb.size(); ++k) {
+            out[fb[k]] = c->host_res[k];
+            out[fb[k]].used_fallback = 1;
+        }
     }
     if (m > 0) {   // inspection buffers refer to the first processed problem (slot 0)
         c->last_n = nn[0];
@@ -806,6 +880,8 @@ int64_t turboreg_debug_copy(turboreg_ctx* c, int which, void* dst, int64_t max_b
         case TURBOREG_BUF_INLIERS: src = v.inl; bytes = nh * 4; break;
         case TURBOREG_BUF_ROWSCORE: src = v.rowscore; bytes = static_cast<size_t>(c->last_n) * 4; break;
         case TURBOREG_BUF_DEGREE: src = v.deg; bytes = static_cast<size_t>(c->last_n) * 4; break;
+        case TURBOREG_BUF_FEATURES: src = v.feat; bytes = static_cast<size_t>(c->last_n) * 32; break;
+        case TURBOREG_BUF_PROB: src = c->ws.prob; bytes = static_cast<size_t>(c->last_n) * 4; break;
         default: return -TURBOREG_ERR_INVALID_ARG;
     }
     if (bytes > static_cast<size_t>(max_bytes)) bytes = static_cast<size_t>(max_bytes);
@@ -824,6 +900,78 @@ int turboreg_stage_times(turboreg_ctx* c, float* ms, int32_t max)
 const char* turboreg_stage_name(int32_t stage)
 {
     return (stage >= 0 && stage < kNumStages) ? kStageNames[stage] : "";
+}
+
+int turboreg_set_proposal_model(turboreg_ctx* c, const float* params)
+{
+    if (!c || !params) return TURBOREG_ERR_INVALID_ARG;
+    for (int k = 0; k < kMlpParams; ++k)
+        if (!std::isfinite(params[k])) return TURBOREG_ERR_NONFINITE;
+    TR_CHECK(cudaSetDevice(c->device));
+    if (!c->mlp_wbf) TR_CHECK(cudaMalloc(&c->mlp_wbf, sizeof(float) * kMlpParams));
+    float* tmp = nullptr;
+    TR_CHECK(cudaMalloc(&tmp, sizeof(float) * kMlpParams));
+    cudaError_t e = cudaMemcpyAsync(tmp, params, sizeof(float) * kMlpParams, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) {
+        launch_mlp_round(tmp, c->mlp_wbf, c->stream);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(tmp);
+    if (e != cudaSuccess) {
+        std::fprintf(stderr, "turboreg: setting the proposal model failed: %s\n", cudaGetErrorString(e));
+        return TURBOREG_ERR_CUDA;
+    }
+    c->has_model = true;
+    for (auto& sl : c->gslot) drop_slot(sl);   // captured graphs bake the model pointer in: recapture
+    return TURBOREG_OK;
+}
+
+int turboreg_features(turboreg_ctx* c, const float* src, const float* dst, int32_t n, const turboreg_params* p,
+                      float* feat)
+{
+    if (!c || !src || !dst || !p || !feat) return TURBOREG_ERR_INVALID_ARG;
+    turboreg_params q = *p;
+    q.proposal = TURBOREG_PROPOSAL_PLAIN;
+    q.flags &= ~(TURBOREG_FLAG_SC2_BITSET | TURBOREG_FLAG_STAGE_TIMES);
+    int rc = check_params(c, n, &q);
+    if (rc != TURBOREG_OK) return rc;
+    TR_CHECK(cudaSetDevice(c->device));
+    const size_t bytes = static_cast<size_t>(n) * 3 * sizeof(float);
+    const float* s_in = src;
+    const float* d_in = dst;
+    if (!is_device_ptr(src)) {
+        if (!host_finite(src, static_cast<size_t>(n) * 3)) return TURBOREG_ERR_NONFINITE;
+        TR_CHECK(cudaMemcpyAsync(c->ws.in_src, src, bytes, cudaMemcpyHostToDevice, c->stream));
+        s_in = c->ws.in_src;
+    }
+    if (!is_device_ptr(dst)) {
+        if (!host_finite(dst, static_cast<size_t>(n) * 3)) return TURBOREG_ERR_NONFINITE;
+        TR_CHECK(cudaMemcpyAsync(c->ws.in_dst, dst, bytes, cudaMemcpyHostToDevice, c->stream));
+        d_in = c->ws.in_dst;
+    }
+    Plan pl;
+    const int64_t off0 = 0;
+    const turboreg_params* pq = &q;
+    rc = build_plan(c, 1, &off0, &n, &pq, pl);
+    if (rc != TURBOREG_OK) return rc;
+    Batch bt;
+    rc = upload_desc(c, 1, c->ws.desc, bt, c->stream);
+    if (rc != TURBOREG_OK) return rc;
+    TR_CHECK(cudaMemsetAsync(c->ws.ctl, 0, sizeof(Ctl), c->stream));
+    launch_pack(bt, pl.tot[ST_PACK], s_in, d_in, c->stream);
+    launch_compat(bt, pl.tot[ST_COMPAT], c->stream);
+    launch_sc2_tcgen05(bt, pl.tot[ST_GEMM], pl.max_n, c->stream);
+    launch_features(bt, c->stream);
+    TR_CHECK(cudaGetLastError());
+    TR_CHECK(cudaMemcpyAsync(feat, c->ws.feat, static_cast<size_t>(n) * 8 * sizeof(float), cudaMemcpyDefault,
+                             c->stream));
+    Ctl h;
+    TR_CHECK(cudaMemcpyAsync(&h, c->ws.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, c->stream));
+    TR_CHECK(cudaStreamSynchronize(c->stream));
+    if (h.err & TR_ERR_NONFINITE) return TURBOREG_ERR_NONFINITE;
+    if (h.err) return TURBOREG_ERR_TIMEOUT;
+    return TURBOREG_OK;
 }
 
 }  // extern "C"

@@ -464,6 +464,8 @@ void stage_blocks(int32_t n, int32_t k1, int32_t k2, int32_t blocks[kNumBatchSta
     blocks[ST_HIST] = (n + 63) / 64;
     blocks[ST_BITSET] = n_pad;
     blocks[ST_GEMM] = nb * (nb + 1);
+    blocks[ST_FEAT] = 1;
+    blocks[ST_MLP] = (n + 127) / 128;
 }
 
 }  // namespace tr

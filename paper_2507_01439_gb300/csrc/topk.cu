@@ -2,7 +2,8 @@
 //
 // P = the min(K1, |E+|) edges (i < j, W_ij > 0) of largest weight, ties at
 // the threshold weight alpha broken by the lowest (i, j) (row-major linear
-// index), listed in (W desc, i asc, j asc) order.
+// index), listed in (W desc, i asc, j asc) order.  With the learned
+// proposal the competing weight is floor(W_ij p_i p_j) (pivot_weight).
 //
 // Exact radix-style selection (no atomics on shared counters, so the result
 // and its cost do not depend on contention):
@@ -53,7 +54,7 @@ __device__ __forceinline__ void for_row_chunks(const ProbView& v, int i, int lan
             const int j = (e < 8 ? c : cb) * 8 + (e & 7);
             const int w = (u[e >> 1] >> ((e & 1) * 16)) & 0xFFFF;
             if (u[e >> 1] == 0u) continue;
-            f(j, (j > i && j < v.n) ? w : 0);
+            f(j, (j > i && j < v.n) ? pivot_weight(v, i, j, w) : 0);
         }
     }
 }
@@ -194,8 +195,8 @@ __global__ void __launch_bounds__(256) emit_kernel(VS vs)
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
                 const int j = c * 8 + e;
-                const int w = (u[e >> 1] >> ((e & 1) * 16)) & 0xFFFF;
                 const bool in = j > i && j < v.n;
+                const int w = in ? pivot_weight(v, i, j, (u[e >> 1] >> ((e & 1) * 16)) & 0xFFFF) : 0;
                 gm |= static_cast<uint32_t>(in && w > alpha) << (8 * k + e);
                 em |= static_cast<uint32_t>(in && w == alpha) << (8 * k + e);
             }
@@ -223,7 +224,7 @@ __global__ void __launch_bounds__(256) emit_kernel(VS vs)
             const int b = __ffs(gm) - 1;
             gm &= gm - 1;
             const int j = (cfirst + (b >> 3)) * 8 + (b & 7);
-            v.cand[rg++] = edge_key(wrow[j], i, j, v.n);
+            v.cand[rg++] = edge_key(pivot_weight(v, i, j, wrow[j]), i, j, v.n);
         }
         while (em) {
             const int b = __ffs(em) - 1;

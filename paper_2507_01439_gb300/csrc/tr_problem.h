@@ -41,6 +41,8 @@ struct ProbView {
     float* rt;           // [K1_MAX*K2_MAX][16] R, t, kappa, flags
     int32_t* inl;        // [K1_MAX*K2_MAX] inlier numbers
     int32_t* fp64_list;  // [K1_MAX*K2_MAX] hypotheses whose Kabsch needs FP64
+    float* feat;         // [n_pad][8] proposal features (learned proposal only)
+    float* prob;         // [n_pad] inlier probabilities; non-null selects the learned pivot weight
     Ctl* ctl;            // device scalars
     turboreg_result* res;  // device result
 };
@@ -50,7 +52,7 @@ struct ProbView {
 // [pre[k*(num+1) + p], pre[k*(num+1) + p + 1]).
 enum Stage {
     ST_PACK = 0, ST_COMPAT, ST_SELECT, ST_COUNT, ST_SCAN, ST_EMIT, ST_RANK, ST_PGS, ST_KABSCH, ST_KABSCH64,
-    ST_VERIFY, ST_FINAL, ST_HIST, ST_BITSET, ST_GEMM, kNumBatchStages
+    ST_VERIFY, ST_FINAL, ST_HIST, ST_BITSET, ST_GEMM, ST_FEAT, ST_MLP, kNumBatchStages
 };
 
 struct Batch {
@@ -73,6 +75,15 @@ __device__ __forceinline__ int locate(const Batch& bt, int st, int b, int& local
     }
     local = b - __ldg(pr + lo);
     return lo;
+}
+
+// Weight an edge competes with for a pivot slot (Eq. 4): the O2Graph weight,
+// or with the learned proposal floor(W_ij p_i p_j) (the same integer range,
+// so the exact integer top-K applies unchanged).
+__device__ __forceinline__ int pivot_weight(const ProbView& v, int i, int j, int w)
+{
+    if (v.prob == nullptr || w == 0) return w;
+    return static_cast<int>(__fmul_rn(__fmul_rn(static_cast<float>(w), v.prob[i]), v.prob[j]));
 }
 
 // Where a kernel finds its problem: one problem passed by value ...
