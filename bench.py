@@ -202,6 +202,53 @@ def run_batched(trg, torch, stream, steps, warmup, flush):
             "gpu_launches_per_call": 16}
 
 
+def run_learned(trg, torch, stream, flush, ks=(1, 2, 4, 8, 100, 250, 500, 1000)):
+    """Learned-proposal form vs plain PGS: 256 indoor-shaped problems, N = 5000,
+    inlier ratio uniform in 1..5%, K1 swept; success (RE < 15 deg, TE < 0.3 m)
+    and registrations/s of one batched call per (method, K1)."""
+    import numpy as np
+    import synth
+    from paper_2507_01439_gb300 import train_proposal as tp
+    rng = np.random.Generator(np.random.PCG64(5))
+    probs = [synth.make_problem("indoor", 5000, float(rng.uniform(0.01, 0.05)), 50_000 + s) for s in range(256)]
+    offs = np.cumsum([0] + [p.n for p in probs]).astype(np.int64)
+    xs = torch.from_numpy(np.concatenate([p.x for p in probs])).cuda()
+    ys = torch.from_numpy(np.concatenate([p.y for p in probs])).cuda()
+    ctx = trg.TurboReg(max_n=5000, max_batch=256, stream=stream.cuda_stream)
+    rows = []
+    try:
+        ctx.set_proposal_model(tp.load_model())
+        for k1 in ks:
+            row = {"k1": k1}
+            for name, prop in (("plain", trg.PROPOSAL_PLAIN), ("learned", trg.PROPOSAL_LEARNED)):
+                prm = [trg.default_params(p.tau, k1, p.theta, proposal=prop) for p in probs]
+                out = ctx.register_batched(xs, ys, offs, prm)            # warm-up / capture
+                ok = sum(int(r.status == 0 and synth.rotation_error_deg(p.R_gt, r.R) < 15
+                             and synth.translation_error(p.t_gt, r.t) < 0.3) for p, r in zip(probs, out))
+                fb = sum(r.used_fallback for r in out)
+                ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(2)]
+                for a, b in ev:
+                    with torch.cuda.stream(stream):
+                        flush.zero_()
+                        a.record(stream)
+                    ctx.register_batched(xs, ys, offs, prm)
+                    b.record(stream)
+                torch.cuda.synchronize()
+                ms = sum(a.elapsed_time(b) for a, b in ev) / len(ev)
+                row[name] = {"success": ok / 256, "regs_per_s": 256 / (ms / 1e3), "fallbacks": fb}
+            rows.append(row)
+    finally:
+        ctx.close()
+    full = max(r["plain"]["success"] for r in rows)
+    def smallest(name):
+        for r in rows:
+            if r[name]["success"] >= full:
+                return r["k1"]
+        return None
+    return {"workload": "256 indoor problems, N=5000, inlier ratio U[1%,5%]", "k_sweep": rows,
+            "k1_reaching_best_plain_success": {"plain": smallest("plain"), "learned": smallest("learned")}}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -306,6 +353,8 @@ def run_ours(args):
     if not args.no_batched:
         line["batched"] = run_batched(trg, torch, stream, steps=max(3, args.steps // 20), warmup=2, flush=flush)
         line["gpu_launches"] += line["batched"]["gpu_launches_per_call"] * line["batched"]["calls"]
+    if not args.no_learned:
+        line["learned"] = run_learned(trg, torch, stream, flush)
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)
@@ -319,6 +368,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-learned", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
