@@ -43,7 +43,8 @@ def build(force: bool = False) -> str:
 
 class OrcParams(ctypes.Structure):
     _fields_ = [("tau", ctypes.c_float), ("k1", ctypes.c_int32), ("k2", ctypes.c_int32),
-                ("theta", ctypes.c_float), ("near_band", ctypes.c_double)]
+                ("theta", ctypes.c_float), ("near_band", ctypes.c_double),
+                ("graph_mode", ctypes.c_int32), ("scoring", ctypes.c_int32)]
 
 
 class OrcResult(ctypes.Structure):
@@ -51,7 +52,10 @@ class OrcResult(ctypes.Structure):
                 ("clique", ctypes.c_int32 * 3), ("inlier_count", ctypes.c_int32),
                 ("hypothesis", ctypes.c_int32), ("n_pivots", ctypes.c_int32),
                 ("n_valid", ctypes.c_int32), ("status", ctypes.c_int32),
-                ("kappa", ctypes.c_double)]
+                ("kappa", ctypes.c_double), ("score", ctypes.c_double)]
+
+GRAPH_O2, GRAPH_SC2 = 0, 1
+SCORE_IN, SCORE_MAE, SCORE_MSE = 0, 1, 2
 
 
 def _load():
@@ -64,14 +68,16 @@ def _load():
         lib.orc_sc2.argtypes = [P, i32, P]
         lib.orc_pivots.argtypes = [P, i32, i32, P, P, P]
         lib.orc_pivots.restype = i32
-        lib.orc_cliques.argtypes = [P, i32, P, P, i32, i32, P, P]
+        lib.orc_cliques.argtypes = [P, i32, P, P, i32, i32, i32, P, P]
         lib.orc_kabsch.argtypes = [P, P, P, P, P]
         lib.orc_kabsch.restype = i32
         lib.orc_svd3.argtypes = [P, P, P, P]
         lib.orc_inliers.argtypes = [P, P, i32, P, P, ctypes.c_float, ctypes.c_double, P]
         lib.orc_inliers.restype = i32
+        lib.orc_score.argtypes = [P, P, i32, P, P, ctypes.c_float, i32]
+        lib.orc_score.restype = ctypes.c_double
         lib.orc_register.argtypes = [P, P, i32, ctypes.POINTER(OrcParams),
-                                     ctypes.POINTER(OrcResult), P, P, P, P]
+                                     ctypes.POINTER(OrcResult), P, P, P, P, P]
         lib.orc_register.restype = i32
         _lib = lib
     return _lib
@@ -118,15 +124,16 @@ def pivots(S, k1):
     return pi[:m].copy(), pj[:m].copy(), pw[:m].copy()
 
 
-def cliques(S, pi, pj, k2):
-    """Eq. 5-7: (cliques int32 [k2*|P|, 3], valid bool [k2*|P|]) in Alg. 2 order."""
+def cliques(S, pi, pj, k2, graph_mode=GRAPH_O2):
+    """Eq. 5-7: (cliques int32 [k2*|P|, 3], valid bool [k2*|P|]) in Alg. 2 order,
+    searched on the O2Graph (graph_mode 0) or the undirected SC^2 graph (1)."""
     S = np.ascontiguousarray(S, dtype=np.int32)
     pi = np.ascontiguousarray(pi, dtype=np.int32)
     pj = np.ascontiguousarray(pj, dtype=np.int32)
     np_ = pi.shape[0]
     cl = np.zeros((max(np_ * k2, 1), 3), dtype=np.int32)
     va = np.zeros(max(np_ * k2, 1), dtype=np.uint8)
-    _load().orc_cliques(_p(S), S.shape[0], _p(pi), _p(pj), np_, k2, _p(cl), _p(va))
+    _load().orc_cliques(_p(S), S.shape[0], _p(pi), _p(pj), np_, k2, int(graph_mode), _p(cl), _p(va))
     return cl[:np_ * k2].copy(), va[:np_ * k2].astype(bool)
 
 
@@ -157,6 +164,17 @@ def inliers(x, y, R, t, theta, band=0.0):
     return int(c), int(near[0])
 
 
+def score(x, y, R, t, theta, mode):
+    """Selection score of one hypothesis: IN (mode 0), or the mean residual
+    capped at theta (MAE, mode 1) / mean squared residual capped at theta^2
+    (MSE, mode 2)."""
+    x, y = _pts(x), _pts(y)
+    R = np.ascontiguousarray(R, dtype=np.float64)
+    t = np.ascontiguousarray(t, dtype=np.float64)
+    return float(_load().orc_score(_p(x), _p(y), x.shape[0], _p(R), _p(t),
+                                   float(np.float32(theta)), int(mode)))
+
+
 @dataclass
 class OracleResult:
     status: int
@@ -172,25 +190,30 @@ class OracleResult:
     near_counts: np.ndarray    # int32 [k1*k2]
     rt: np.ndarray             # float64 [k1*k2, 12]
     hyp_valid: np.ndarray      # bool [k1*k2]
+    score: float = 0.0         # the winner's selection score
+    scores: np.ndarray = None  # float64 [k1*k2], NaN where no valid hypothesis
 
 
-def register(x, y, tau, k1, theta, k2=2, near_band=1e-5) -> OracleResult:
+def register(x, y, tau, k1, theta, k2=2, near_band=1e-5, graph_mode=GRAPH_O2,
+             scoring=SCORE_IN) -> OracleResult:
     """The whole path (Eq. 1 -> Eq. 9) in FP64 on one host core."""
     x, y = _pts(x), _pts(y)
     n = x.shape[0]
     prm = OrcParams(float(np.float32(tau)), int(k1), int(k2),
-                    float(np.float32(theta)), float(near_band))
+                    float(np.float32(theta)), float(near_band), int(graph_mode), int(scoring))
     res = OrcResult()
     nh = max(int(k1) * int(k2), 1)
     inc = np.zeros(nh, dtype=np.int32)
     nec = np.zeros(nh, dtype=np.int32)
     rt = np.zeros((nh, 12), dtype=np.float64)
     hv = np.zeros(nh, dtype=np.uint8)
+    sc = np.zeros(nh, dtype=np.float64)
     _load().orc_register(_p(x), _p(y), n, ctypes.byref(prm), ctypes.byref(res),
-                         _p(inc), _p(nec), _p(rt), _p(hv))
+                         _p(inc), _p(nec), _p(rt), _p(hv), _p(sc))
     return OracleResult(
         status=int(res.status), R=np.array(res.R[:]).reshape(3, 3), t=np.array(res.t[:]),
         clique=tuple(res.clique[:]), inlier_count=int(res.inlier_count),
         hypothesis=int(res.hypothesis), n_pivots=int(res.n_pivots),
         n_valid=int(res.n_valid), kappa=float(res.kappa),
-        in_counts=inc, near_counts=nec, rt=rt, hyp_valid=hv.astype(bool))
+        in_counts=inc, near_counts=nec, rt=rt, hyp_valid=hv.astype(bool),
+        score=float(res.score), scores=sc)

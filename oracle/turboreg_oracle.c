@@ -128,18 +128,24 @@ static int32_t o2(const int32_t* S, int32_t n, int32_t a, int32_t b)
     return (a < b) ? S[(size_t)a * n + b] : 0;   /* Def. 2 */
 }
 
+/* The graph G- that Alg. 1 searches: the O2Graph or the undirected SC^2 graph. */
+static int32_t gbar(const int32_t* S, int32_t n, int32_t mode, int32_t a, int32_t b)
+{
+    return (mode == 1) ? S[(size_t)a * n + b] : o2(S, n, a, b);
+}
+
 void orc_cliques(const int32_t* S, int32_t n, const int32_t* pi, const int32_t* pj,
-                 int32_t np, int32_t k2, int32_t* cliques, uint8_t* valid)
+                 int32_t np, int32_t k2, int32_t graph_mode, int32_t* cliques, uint8_t* valid)
 {
     int32_t* topz = (int32_t*)malloc(sizeof(int32_t) * (size_t)k2);
     int32_t* tops = (int32_t*)malloc(sizeof(int32_t) * (size_t)k2);
     for (int32_t p = 0; p < np; ++p) {
         const int32_t i = pi[p], j = pj[p];
-        const int32_t gij = o2(S, n, i, j);
+        const int32_t gij = gbar(S, n, graph_mode, i, j);
         int32_t cnt = 0;
         for (int32_t z = 0; z < n; ++z) {
             if (z == i || z == j) continue;
-            const int32_t giz = o2(S, n, i, z), gjz = o2(S, n, j, z);
+            const int32_t giz = gbar(S, n, graph_mode, i, z), gjz = gbar(S, n, graph_mode, j, z);
             if (!(giz > 0 && gjz > 0)) continue;            /* Eq. 5 */
             const int32_t s = gij + giz + gjz;              /* Eq. 6 */
             /* Eq. 7: keep the K2 largest; z ascends, so a later z only
@@ -299,20 +305,42 @@ int32_t orc_inliers(const float* x, const float* y, int32_t n, const double* R,
     return cnt;
 }
 
+double orc_score(const float* x, const float* y, int32_t n, const double* R, const double* t,
+                 float theta, int32_t mode)
+{
+    const double th = (double)theta;
+    double acc = 0.0;
+    for (int32_t k = 0; k < n; ++k) {
+        const float* xk = x + 3 * (size_t)k;
+        const float* yk = y + 3 * (size_t)k;
+        double r2 = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            double ra = R[a * 3 + 0] * (double)xk[0] + R[a * 3 + 1] * (double)xk[1]
+                      + R[a * 3 + 2] * (double)xk[2] + t[a] - (double)yk[a];
+            r2 += ra * ra;
+        }
+        if (mode == 0) acc += (r2 <= th * th) ? 1.0 : 0.0;
+        else if (mode == 1) acc += fmin(sqrt(r2), th);
+        else acc += fmin(r2, th * th);
+    }
+    return (mode == 0) ? acc : acc / (double)n;
+}
+
 /* ------------------------------------------------------------------ */
 /* Whole path                                                          */
 /* ------------------------------------------------------------------ */
 
 int32_t orc_register(const float* x, const float* y, int32_t n, const orc_params* prm,
                      orc_result* res, int32_t* in_counts, int32_t* near_counts,
-                     double* rt, uint8_t* hyp_valid)
+                     double* rt, uint8_t* hyp_valid, double* scores)
 {
     memset(res, 0, sizeof(*res));
     res->R[0] = res->R[4] = res->R[8] = 1.0;
     res->hypothesis = -1;
     res->clique[0] = res->clique[1] = res->clique[2] = -1;
     if (n < 3) { res->status = 2; return 2; }
-    if (prm->k1 < 1 || prm->k2 < 1 || !(prm->tau >= 0) || !(prm->theta > 0)) {
+    if (prm->k1 < 1 || prm->k2 < 1 || !(prm->tau >= 0) || !(prm->theta > 0) ||
+        prm->graph_mode < 0 || prm->graph_mode > 1 || prm->scoring < 0 || prm->scoring > 2) {
         res->status = 1; return 1;
     }
     const int32_t k1 = prm->k1, k2 = prm->k2;
@@ -332,13 +360,14 @@ int32_t orc_register(const float* x, const float* y, int32_t n, const orc_params
     const int32_t nh = np * k2;
     int32_t* cl = (int32_t*)malloc(sizeof(int32_t) * 3 * (size_t)(nh ? nh : 1));
     uint8_t* va = (uint8_t*)malloc((size_t)(nh ? nh : 1));
-    orc_cliques(S, n, pi, pj, np, k2, cl, va);             /* Eq. 5-7 */
+    orc_cliques(S, n, pi, pj, np, k2, prm->graph_mode, cl, va);   /* Eq. 5-7 */
     int32_t best = -1, best_in = -1, nvalid = 0;
-    double bestR[9], bestt[3], bestk = 0;
+    double bestR[9], bestt[3], bestk = 0, best_sc = 0;
     for (int32_t h = 0; h < k1 * k2; ++h) {
         if (in_counts) in_counts[h] = -1;
         if (near_counts) near_counts[h] = 0;
         if (hyp_valid) hyp_valid[h] = 0;
+        if (scores) scores[h] = NAN;
     }
     for (int32_t h = 0; h < nh; ++h) {
         if (!va[h]) continue;
@@ -356,8 +385,13 @@ int32_t orc_register(const float* x, const float* y, int32_t n, const orc_params
         if (near_counts) near_counts[h] = near;
         if (hyp_valid) hyp_valid[h] = 1;
         if (rt) { memcpy(rt + (size_t)h * 12, R, sizeof(R)); memcpy(rt + (size_t)h * 12 + 9, t, sizeof(t)); }
-        if (in > best_in) {                                /* Eq. 9, lowest h on ties */
-            best_in = in; best = h;
+        const double sc = (prm->scoring == 0) ? (double)in
+                                              : orc_score(x, y, n, R, t, prm->theta, prm->scoring);
+        if (scores) scores[h] = sc;
+        /* Eq. 9 (largest IN) or the smallest capped error; lowest h on ties */
+        const int better = (best < 0) || (prm->scoring == 0 ? sc > best_sc : sc < best_sc);
+        if (better) {
+            best_in = in; best = h; best_sc = sc;
             memcpy(bestR, R, sizeof(R)); memcpy(bestt, t, sizeof(t)); bestk = kap;
         }
     }
@@ -371,6 +405,7 @@ int32_t orc_register(const float* x, const float* y, int32_t n, const orc_params
         res->inlier_count = best_in;
         res->hypothesis = best;
         res->kappa = bestk;
+        res->score = best_sc;
         res->status = 0;
     } else {
         res->status = 7;

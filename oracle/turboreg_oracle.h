@@ -11,9 +11,11 @@
  *   orc_compat   Eq. 1  compatibility graph G (0/1, zero diagonal)
  *   orc_sc2      Eq. 2  SC^2 graph  G^_ij = G_ij * sum_k G_ik G_jk
  *   orc_pivots   Eq. 4 + Def. 2  top-K1 edges of the O2Graph
- *   orc_cliques  Eq. 5-7, Alg. 1  per-pivot top-K2 TurboCliques, Alg. 2 layout
+ *   orc_cliques  Eq. 5-7, Alg. 1  per-pivot top-K2 TurboCliques, Alg. 2 layout,
+ *                on the O2Graph (Def. 2) or the undirected SC^2 graph
  *   orc_kabsch   Sec. 3.5  least-squares rigid transform from 3 matches (SVD)
  *   orc_inliers  Sec. 3.5 / Eq. 9  inlier number of one hypothesis
+ *   orc_score    App. (ranking study, Table 6)  IN, MAE or MSE of one hypothesis
  *   orc_register the whole path, Eq. 1 -> Eq. 9
  *
  * Inputs are float32 and are promoted exactly to double.  Everything after
@@ -39,6 +41,8 @@ typedef struct {
     int32_t k2;         /* TurboCliques per pivot, Eq. 7 */
     float theta;        /* inlier threshold of the inlier number, Eq. 9 */
     double near_band;   /* report residuals with | ||r|| - theta | <= near_band */
+    int32_t graph_mode; /* 0: O2Graph (Def. 2), 1: undirected SC^2 graph (Eq. 2) */
+    int32_t scoring;    /* hypothesis selection: 0 IN (Eq. 9), 1 MAE, 2 MSE (see orc_score) */
 } orc_params;
 
 typedef struct {
@@ -51,6 +55,7 @@ typedef struct {
     int32_t n_valid;    /* hypotheses with a clique and a non-degenerate Kabsch */
     int32_t status;     /* 0 ok, 7 no hypothesis */
     double kappa;       /* sigma1/sigma2 of the winning clique */
+    double score;       /* the winner's selection score (IN as a number, or MAE / MSE) */
 } orc_result;
 
 /* Eq. 1.  A[i*n+j] = 1 iff | ||x_i-x_j|| - ||y_i-y_j|| | <= tau, i != j; A_ii = 0. */
@@ -65,11 +70,13 @@ void orc_sc2(const uint8_t* A, int32_t n, int32_t* S);
 int32_t orc_pivots(const int32_t* S, int32_t n, int32_t k1,
                    int32_t* pi, int32_t* pj, int32_t* pw);
 
-/* Eq. 5-7 / Alg. 1 on the O2Graph.  cliques[(r*np+p)*3 + {0,1,2}] = (i,j,z)
- * of the rank-r TurboClique of pivot p (Alg. 2 layout), valid[h] = 1 if it
- * exists.  Ties of the aggregated weight go to the lower z. */
+/* Eq. 5-7 / Alg. 1 on the graph G- chosen by graph_mode: 0 the O2Graph
+ * (G-_ab = S_ab for a < b, else 0), 1 the undirected SC^2 graph (G-_ab =
+ * S_ab).  cliques[(r*np+p)*3 + {0,1,2}] = (i,j,z) of the rank-r TurboClique
+ * of pivot p (Alg. 2 layout), valid[h] = 1 if it exists.  Ties of the
+ * aggregated weight go to the lower z. */
 void orc_cliques(const int32_t* S, int32_t n, const int32_t* pi, const int32_t* pj,
-                 int32_t np, int32_t k2, int32_t* cliques, uint8_t* valid);
+                 int32_t np, int32_t k2, int32_t graph_mode, int32_t* cliques, uint8_t* valid);
 
 /* Kabsch on 3 matches: R,t minimise sum_a ||R xa + t - ya||^2 over proper
  * rotations.  xs, ys: 3 points each, row-major [3][3].  kappa = s1/s2 of the
@@ -85,14 +92,26 @@ void orc_svd3(const double* H, double* U, double* s, double* V);
 int32_t orc_inliers(const float* x, const float* y, int32_t n, const double* R,
                     const double* t, float theta, double band, int32_t* n_near);
 
+/* Selection score of one hypothesis over all n matches, e_k = ||R x_k + t - y_k||:
+ *   mode 0 (IN):  #{k : e_k^2 <= theta^2}                 (larger is better)
+ *   mode 1 (MAE): (1/n) sum_k min(e_k, theta)             (smaller is better)
+ *   mode 2 (MSE): (1/n) sum_k min(e_k^2, theta^2)         (smaller is better)
+ * MAE and MSE are the mean absolute / squared residuals with every residual
+ * capped at theta, so an outlier costs theta (or theta^2) whatever its size. */
+double orc_score(const float* x, const float* y, int32_t n, const double* R, const double* t,
+                 float theta, int32_t mode);
+
 /* Whole path.  Optional outputs (may be NULL): per-hypothesis inlier counts
  * in_counts[k1*k2], near counts near_counts[k1*k2], per-hypothesis R,t
- * (rt[h*12 .. +12] = R row-major then t), valid flags hyp_valid[k1*k2].
+ * (rt[h*12 .. +12] = R row-major then t), valid flags hyp_valid[k1*k2],
+ * selection scores scores[k1*k2] (orc_score with prm->scoring; NaN where no
+ * valid hypothesis).  The winner is the largest IN (scoring 0) or the
+ * smallest MAE / MSE (scoring 1, 2); ties go to the lowest h.
  * Returns 0 on success, 7 if no valid hypothesis, 1 on bad arguments,
  * 4 on allocation failure. */
 int32_t orc_register(const float* x, const float* y, int32_t n, const orc_params* prm,
                      orc_result* res, int32_t* in_counts, int32_t* near_counts,
-                     double* rt, uint8_t* hyp_valid);
+                     double* rt, uint8_t* hyp_valid, double* scores);
 
 #ifdef __cplusplus
 }

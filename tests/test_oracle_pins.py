@@ -28,7 +28,7 @@ def _random_graph(n, p, seed):
 
 
 def _load_golden(golden_dir):
-    g = {"edge": [], "pivot": [], "clique": []}
+    g = {"edge": [], "pivot": [], "clique": [], "uclique": []}
     with open(os.path.join(golden_dir, "appE1_graph.txt")) as f:
         for line in f:
             line = line.split("#")[0].split()
@@ -264,6 +264,72 @@ def test_cliques_appendix_graph(golden_dir):
     assert [[h] + (cl[h] + 1).tolist() for h in range(len(cl))] == g["clique"]
 
 
+def test_cliques_appendix_graph_undirected(golden_dir):
+    g = _load_golden(golden_dir)
+    n = g["n"]
+    A = np.zeros((n, n), dtype=np.uint8)
+    for u, v, _ in g["edge"]:
+        A[u - 1, v - 1] = A[v - 1, u - 1] = 1
+    S = oracle.sc2(A)
+    pi, pj, _ = oracle.pivots(S, g["k1"])
+    cl, va = oracle.cliques(S, pi, pj, g["k2"], graph_mode=oracle.GRAPH_SC2)
+    assert va.all()
+    assert [[h] + (cl[h] + 1).tolist() for h in range(len(cl))] == g["uclique"]
+
+
+def _exhaustive_cliques_undirected(A, S, pi, pj, k2):
+    """Every 3-clique containing the pivot edge, ranked by Eq. 6 on the
+    symmetric SC^2 graph (ties: lower z)."""
+    n = A.shape[0]
+    tri = [(a, b, c) for a, b, c in itertools.combinations(range(n), 3)
+           if A[a, b] and A[a, c] and A[b, c]]
+    out = []
+    for i, j in zip(pi.tolist(), pj.tolist()):
+        lst = []
+        for t in tri:
+            if i in t and j in t:
+                z = [v for v in t if v not in (i, j)][0]
+                lst.append((-(S[i, j] + S[i, z] + S[j, z]), z))
+        out.append([z for _, z in sorted(lst)[:k2]])
+    return out
+
+
+@pytest.mark.parametrize("n,p,k1,k2,seed", [(20, 0.5, 15, 2, 0), (40, 0.3, 60, 3, 1),
+                                            (60, 0.25, 200, 2, 2), (33, 0.9, 500, 5, 4)])
+def test_cliques_undirected_exhaustive_small(n, p, k1, k2, seed):
+    A = _random_graph(n, p, seed)
+    S = oracle.sc2(A)
+    pi, pj, pw = oracle.pivots(S, k1)
+    cl, va = oracle.cliques(S, pi, pj, k2, graph_mode=oracle.GRAPH_SC2)
+    want = _exhaustive_cliques_undirected(A, S, pi, pj, k2)
+    np_ = len(pi)
+    for p_ in range(np_):
+        got = [int(cl[r * np_ + p_, 2]) for r in range(k2) if va[r * np_ + p_]]
+        assert got == want[p_]
+        for r in range(k2):
+            h = r * np_ + p_
+            if va[h]:
+                i, j, z = cl[h]
+                assert A[i, j] * A[i, z] * A[j, z] > 0             # Eq. 8
+                assert z not in (i, j)
+
+
+def test_undirected_search_finds_at_least_the_o2_cliques():
+    # with K2 at least the largest common-neighbour count, every O2Graph clique
+    # of a pivot is also one of its undirected cliques (z > j is a subset)
+    A = _random_graph(45, 0.35, 11)
+    S = oracle.sc2(A)
+    pi, pj, _ = oracle.pivots(S, 80)
+    k2 = 45
+    co, vo = oracle.cliques(S, pi, pj, k2)
+    cu, vu = oracle.cliques(S, pi, pj, k2, graph_mode=oracle.GRAPH_SC2)
+    so = {tuple(sorted(c)) for c, v in zip(co.tolist(), vo) if v}
+    su = {tuple(sorted(c)) for c, v in zip(cu.tolist(), vu) if v}
+    assert so <= su
+    # every triangle through a pivot edge appears, and the O2Graph finds each once
+    assert sum(vo) == len(so)
+
+
 def test_cliques_missing_slots_are_invalid():
     # a pivot with one common neighbour cannot fill K2 = 3 slots
     A = np.zeros((4, 4), dtype=np.uint8)
@@ -400,6 +466,103 @@ def test_inliers_ground_truth_counts_noiseless_inliers():
     p = synth.make_problem("cube", 500, 0.2, 15, sigma=0.0)
     c, _ = oracle.inliers(p.x, p.y, p.R_gt, p.t_gt, 1e-4)
     assert c >= p.inlier.sum()
+
+
+# --------------------------------------------------------------------------
+# Hypothesis scores of the ranking study (Table 6): IN, MAE, MSE
+# --------------------------------------------------------------------------
+
+def test_score_hand_example():
+    # y = Rz x + t + offsets with residuals 0.5, 0.25, 2 and 0 m (all exact in
+    # binary); theta = 1:  IN = 3, MAE = (0.5 + 0.25 + 1 + 0) / 4 = 0.4375,
+    # MSE = (0.25 + 0.0625 + 1 + 0) / 4 = 0.328125  (the 2 m residual is capped at theta)
+    Rz = np.array([[0, -1, 0], [1, 0, 0], [0, 0, 1.0]])
+    t = np.array([1.0, -2.0, 4.0])
+    x = np.array([[1, 2, 3], [-4, 0, 1], [2, 2, -2], [0, 5, 1]], dtype=np.float32)
+    y = (x.astype(np.float64) @ Rz.T + t).astype(np.float32)
+    y[0, 0] += 0.5
+    y[1, 1] -= 0.25
+    y[2, 2] += 2.0
+    assert oracle.score(x, y, Rz, t, 1.0, oracle.SCORE_IN) == 3.0
+    assert oracle.score(x, y, Rz, t, 1.0, oracle.SCORE_MAE) == 0.4375
+    assert oracle.score(x, y, Rz, t, 1.0, oracle.SCORE_MSE) == 0.328125
+    # theta = 0.5: the 0.5 m residual sits exactly on the threshold
+    assert oracle.score(x, y, Rz, t, 0.5, oracle.SCORE_IN) == 3.0
+    assert oracle.score(x, y, Rz, t, 0.5, oracle.SCORE_MAE) == (0.5 + 0.25 + 0.5) / 4
+    assert oracle.score(x, y, Rz, t, 0.5, oracle.SCORE_MSE) == (0.25 + 0.0625 + 0.25) / 4
+
+
+def test_score_bounds_and_extremes():
+    rng = _rng(17)
+    p = synth.make_problem("cube", 400, 0.3, 17)
+    th = p.theta
+    for _ in range(30):
+        R = _rand_rot(rng) if rng.random() < 0.5 else p.R_gt
+        t = p.t_gt + rng.normal(scale=0.05, size=3)
+        inn = oracle.score(p.x, p.y, R, t, th, oracle.SCORE_IN)
+        mae = oracle.score(p.x, p.y, R, t, th, oracle.SCORE_MAE)
+        mse = oracle.score(p.x, p.y, R, t, th, oracle.SCORE_MSE)
+        n = p.n
+        # every residual is capped at theta; an outlier of (R,t) costs exactly theta
+        th64 = float(np.float32(th))
+        assert 0 <= mse <= th64 * mae + 1e-15 and mae <= th64 + 1e-15
+        assert mae >= th64 * (n - inn) / n - 1e-15
+        assert mse >= th64 * th64 * (n - inn) / n - 1e-15
+        assert inn == oracle.inliers(p.x, p.y, R, t, th)[0]
+    # exact fit: zero error; everything far away: theta and theta^2
+    x = p.x[:50]
+    y = (x.astype(np.float64) @ p.R_gt.T + p.t_gt).astype(np.float32)
+    assert oracle.score(x, x, np.eye(3), np.zeros(3), 0.1, oracle.SCORE_MAE) == 0.0
+    assert oracle.score(x, x, np.eye(3), np.zeros(3), 0.1, oracle.SCORE_MSE) == 0.0
+    far = np.array([1e3, 0, 0])
+    assert oracle.score(x, y, p.R_gt, p.t_gt + far, 0.1, oracle.SCORE_MAE) == float(np.float32(0.1))
+    assert oracle.score(x, y, p.R_gt, p.t_gt + far, 0.1, oracle.SCORE_MSE) == float(np.float32(0.1)) ** 2
+
+
+@pytest.mark.parametrize("scoring", [1, 2])
+def test_register_scoring_selects_smallest_error(scoring):
+    p = synth.make_problem("indoor", 600, 0.08, 23)
+    r = oracle.register(p.x, p.y, p.tau, 120, p.theta, scoring=scoring)
+    r0 = oracle.register(p.x, p.y, p.tau, 120, p.theta)
+    assert r.status == 0
+    # the same hypotheses as the inlier-number run; the winner minimises the score
+    assert np.array_equal(r.hyp_valid, r0.hyp_valid)
+    assert np.array_equal(r.in_counts, r0.in_counts)
+    sc = np.where(r.hyp_valid, r.scores, np.inf)
+    assert r.hypothesis == int(np.argmin(sc))           # argmin returns the lowest h on ties
+    h = r.hypothesis
+    assert r.score == sc[h]
+    assert r.score == oracle.score(p.x, p.y, r.rt[h, :9].reshape(3, 3), r.rt[h, 9:], p.theta, scoring)
+    assert r.inlier_count == r.in_counts[h]
+    # IN-mode scores are the inlier numbers
+    assert np.array_equal(np.where(r0.hyp_valid, r0.scores, -1).astype(np.int64), r0.in_counts.astype(np.int64))
+    assert synth.rotation_error_deg(p.R_gt, r.R) < p.re_deg
+    assert synth.translation_error(p.t_gt, r.t) < p.te_m
+
+
+def test_register_scoring_noiseless_reaches_ground_truth_error():
+    # sigma = 0: a clique of three inliers reproduces (R_gt, t_gt), whose capped
+    # error is the smallest any hypothesis can reach on these matches up to rounding
+    p = synth.make_problem("cube", 300, 0.3, 29, sigma=0.0)
+    for scoring in (1, 2):
+        r = oracle.register(p.x, p.y, 1e-4, 150, 1e-3, scoring=scoring)
+        gt = oracle.score(p.x, p.y, p.R_gt, p.t_gt, 1e-3, scoring)
+        assert r.status == 0
+        assert r.score <= gt + 1e-9
+        assert np.abs(r.R - p.R_gt).max() < 1e-5
+
+
+def test_register_undirected_graph_mode():
+    # same pivots as the O2Graph run; every clique is a 3-clique of G
+    p = synth.make_problem("cube", 200, 0.3, 37)
+    ro = oracle.register(p.x, p.y, p.tau, 60, p.theta)
+    ru = oracle.register(p.x, p.y, p.tau, 60, p.theta, graph_mode=oracle.GRAPH_SC2)
+    assert ru.status == 0 and ru.n_pivots == ro.n_pivots
+    assert ru.n_valid >= ro.n_valid
+    assert synth.rotation_error_deg(p.R_gt, ru.R) < p.re_deg
+    A = oracle.compat(p.x, p.y, p.tau)
+    i, j, z = ru.clique
+    assert A[i, j] and A[i, z] and A[j, z]
 
 
 # --------------------------------------------------------------------------
