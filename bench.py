@@ -21,6 +21,7 @@ all ranks' registrations / the slowest rank's time.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
 import os
 import statistics
@@ -249,6 +250,101 @@ def run_learned(trg, torch, stream, flush, ks=(1, 2, 4, 8, 100, 250, 500, 1000))
             "k1_reaching_best_plain_success": {"plain": smallest("plain"), "learned": smallest("learned")}}
 
 
+def _batched_success(probs, out):
+    import synth
+    ok, re_s, te_s = 0, [], []
+    for p, r in zip(probs, out):
+        if r.status != 0:
+            continue
+        re = synth.rotation_error_deg(p.R_gt, r.R)
+        te = synth.translation_error(p.t_gt, r.t)
+        if re < p.re_deg and te < p.te_m:
+            ok += 1
+            re_s.append(re)
+            te_s.append(te)
+    return ok, (sum(re_s) / len(re_s) if re_s else None), (100 * sum(te_s) / len(te_s) if te_s else None)
+
+
+def run_ablation(trg, torch, stream, flush):
+    """The ablation axes of Table 5 on synthetic data: the compatibility
+    threshold tau, the searched graph (O2Graph vs undirected SC^2 graph), K1
+    and K2, one at a time around the default (tau = 0.1 m, O2Graph, K1 = 2000,
+    K2 = 2).  256 indoor-shaped problems, N = 5000, inlier ratio U[2%, 10%];
+    RR = success rate (RE < 15 deg, TE < 0.3 m), mean RE / TE over the
+    successes, registrations/s of one batched call."""
+    import numpy as np
+    import synth
+    rng = np.random.Generator(np.random.PCG64(6))
+    probs = [synth.make_problem("indoor", 5000, float(rng.uniform(0.02, 0.10)), 60_000 + s) for s in range(256)]
+    offs = np.cumsum([0] + [p.n for p in probs]).astype(np.int64)
+    xs = torch.from_numpy(np.concatenate([p.x for p in probs])).cuda()
+    ys = torch.from_numpy(np.concatenate([p.y for p in probs])).cuda()
+    ctx = trg.TurboReg(max_n=5000, max_batch=256, stream=stream.cuda_stream)
+    base = {"tau": 0.1, "graph": "O2Graph", "k1": 2000, "k2": 2}
+    rows = []
+    configs = ([dict(base, tau=t) for t in (0.01, 0.02, 0.05, 0.1, 0.2, 0.5)]
+               + [dict(base, graph="SC2 graph")]
+               + [dict(base, k1=k) for k in (10, 50, 250, 500, 1000)]
+               + [dict(base, k2=k) for k in (1, 3)])
+    try:
+        for c in configs:
+            gm = trg.GRAPH_SC2 if c["graph"] != "O2Graph" else trg.GRAPH_O2
+            prm = [trg.default_params(c["tau"], c["k1"], p.theta, k2=c["k2"], graph_mode=gm) for p in probs]
+            out = ctx.register_batched(xs, ys, offs, prm)
+            ok, re_m, te_m = _batched_success(probs, out)
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(2)]
+            for a_, b_ in ev:
+                with torch.cuda.stream(stream):
+                    flush.zero_()
+                    a_.record(stream)
+                ctx.register_batched(xs, ys, offs, prm)
+                b_.record(stream)
+            torch.cuda.synchronize()
+            ms = sum(a_.elapsed_time(b_) for a_, b_ in ev) / len(ev)
+            rows.append(dict(c, rr=100.0 * ok / 256, re_deg=re_m, te_cm=te_m, regs_per_s=256 / (ms / 1e3)))
+    finally:
+        ctx.close()
+    return {"workload": "256 indoor problems, N=5000, inlier ratio U[2%,10%]; one axis varied at a time",
+            "rows": rows}
+
+
+def run_ranking(trg, num=192):
+    """The ranking study of Table 6 on synthetic problems: RR, TQRR, ICRR and
+    TKRR@{2,3,5,50} of the K1*K2 hypotheses ranked by IN, MAE and MSE.
+    Problems: indoor- or outdoor-shaped, N U[1000, 5000], inlier ratio
+    U[2%, 10%], K1 = 1000, K2 = 2."""
+    import synth
+    from paper_2507_01439_gb300 import ranking
+    probs = synth.make_batch(num, seed=7, n_lo=1000, n_hi=5000, ratio_lo=0.02, ratio_hi=0.10)
+    out = {}
+    with trg.TurboReg(max_n=5000, max_batch=1) as ctx:
+        for name, sc in (("IN", trg.SCORE_IN), ("MAE", trg.SCORE_MAE), ("MSE", trg.SCORE_MSE)):
+            recs = []
+            for p in probs:
+                prm = trg.default_params(p.tau, 1000, p.theta, scoring=sc)
+                recs.append(ranking.evaluate(ctx, p.x, p.y, prm, p.R_gt, p.t_gt, p.inlier, p.re_deg, p.te_m))
+            out[name] = {k: round(v, 2) for k, v in ranking.summarize(recs).items()}
+    return {"workload": f"{num} problems, indoor/outdoor, N U[1000,5000], inlier ratio U[2%,10%], K1=1000, K2=2",
+            "percent": out}
+
+
+def run_sc2_paths(trg, probs, dx, dy):
+    """SC^2 stage (with the edge-weight histogram and the pivot threshold) on
+    the benchmark workload: the tcgen05 FP8 GEMM vs the CUDA-core bitset
+    AND + popcount path (same integers); in-graph CUDA-event times."""
+    out = {}
+    with trg.TurboReg(max_n=5000, max_batch=1) as ctx:
+        for name, fl in (("tcgen05_gemm", 0), ("bitset_popcount", trg.FLAG_SC2_BITSET)):
+            prm = trg.default_params(0.1, 2000, 0.1, flags=trg.FLAG_STAGE_TIMES | fl)
+            ms = []
+            for k in range(24):
+                ctx.register(dx[k % 8], dy[k % 8], prm)
+                if k >= 4:
+                    ms.append(ctx.stage_times()["sc2"])
+            out[name + "_ms"] = sum(ms) / len(ms)
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -346,7 +442,7 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "fp8+f32", "data": "synthetic",
             "config": dict(WORKLOAD, parallelism=f"replicas x{ws}"),
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 2 * 5000 * 12,
-                    "d2h_bytes_per_step": 88},
+                    "d2h_bytes_per_step": ctypes.sizeof(trg.turboreg_result)},
             "gpu_launches": LAUNCHES_PER_STEP * args.steps * 2,
             "roofline": roofline, "clocks": clocks,
             "success_rate_check": f"{ok}/8 problems RE<15deg TE<0.3m"}
@@ -355,6 +451,10 @@ def run_ours(args):
         line["gpu_launches"] += line["batched"]["gpu_launches_per_call"] * line["batched"]["calls"]
     if not args.no_learned:
         line["learned"] = run_learned(trg, torch, stream, flush)
+    if not args.no_studies:
+        line["sc2_paths"] = run_sc2_paths(trg, probs, dx, dy)
+        line["ablation"] = run_ablation(trg, torch, stream, flush)
+        line["ranking"] = run_ranking(trg)
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)
@@ -369,6 +469,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--no-studies", action="store_true",
+                    help="skip the SC^2 path comparison, the ablation sweep and the ranking study")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

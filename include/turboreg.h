@@ -53,8 +53,18 @@ typedef enum {
     TURBOREG_ERR_NO_HYPOTHESIS = 7  /* no edge, no TurboClique or no non-degenerate Kabsch */
 } turboreg_status;
 
-/* graph_mode */
-#define TURBOREG_GRAPH_O2 0          /* O2Graph (Def. 2), the paper's default */
+/* graph_mode: the graph G- that Pivot-Guided Search runs on (Alg. 1 accepts either) */
+#define TURBOREG_GRAPH_O2 0          /* O2Graph (Def. 2), the paper's default: the third match z of
+                                        pivot (i, j) ranges over z > j, so every TurboClique is
+                                        found by at most one pivot (App. C) */
+#define TURBOREG_GRAPH_SC2 1         /* undirected SC^2 graph (Eq. 2): z ranges over every common
+                                        neighbour of i and j, so a 3-clique can be found from up
+                                        to three pivots (the ablation of Table 5) */
+/* scoring: how the winning hypothesis is chosen (Eq. 9 and the ranking study of Table 6).
+   e_k = ||R x_k + t - y_k|| over all N matches, theta = inlier_thresh. */
+#define TURBOREG_SCORE_IN 0          /* largest inlier number #{k : e_k <= theta} (Eq. 9) */
+#define TURBOREG_SCORE_MAE 1         /* smallest (1/N) sum_k min(e_k, theta) */
+#define TURBOREG_SCORE_MSE 2         /* smallest (1/N) sum_k min(e_k^2, theta^2) */
 /* proposal */
 #define TURBOREG_PROPOSAL_PLAIN 0    /* pivots = top-K1 SC^2 edges (Eq. 4) */
 #define TURBOREG_PROPOSAL_LEARNED 1  /* pivots ranked by floor(W_ij p_i p_j), p = inlier probability
@@ -71,7 +81,7 @@ typedef struct {
     int32_t k1;           /* pivot count K1 of Eq. 4, 1..TURBOREG_K1_MAX */
     int32_t k2;           /* TurboCliques per pivot K2 of Eq. 7, 1..TURBOREG_K2_MAX (paper: 2) */
     float inlier_thresh;  /* theta: a match is an inlier of (R,t) iff ||R x + t - y|| <= theta, > 0 */
-    int32_t graph_mode;   /* TURBOREG_GRAPH_O2 (only mode) */
+    int32_t graph_mode;   /* TURBOREG_GRAPH_O2 or TURBOREG_GRAPH_SC2 */
     int32_t proposal;     /* TURBOREG_PROPOSAL_PLAIN or _LEARNED */
     float kappa_fp64;     /* Kabsch runs in FP64 when sigma1/sigma2 of the 3x3 cross-covariance
                              exceeds this bound (0 selects the default 100) */
@@ -79,12 +89,13 @@ typedef struct {
     int32_t learned_min_inliers; /* learned proposal: if its best inlier number is below this (or it
                                     finds no hypothesis) the plain proposal decides the result;
                                     0 selects max(10, N / 200) */
+    int32_t scoring;      /* TURBOREG_SCORE_IN, _MAE or _MSE; ties go to the lowest h */
 } turboreg_params;
 
 typedef struct {
     float R[9];             /* row-major rotation, y = R x + t */
     float t[3];             /* translation, metres */
-    int32_t clique[3];      /* winning TurboClique (i < j < z), or -1 */
+    int32_t clique[3];      /* winning TurboClique: pivot (i < j) then z (z > j on the O2Graph), or -1 */
     int32_t inlier_count;   /* inlier number of the winner (Eq. 9) */
     int32_t hypothesis;     /* h* in Alg. 2 order h = r*|P| + p, lowest h on ties; -1 if none */
     int32_t n_pivots;       /* |P| = min(K1, number of O2Graph edges) */
@@ -92,10 +103,14 @@ typedef struct {
     int32_t used_fp64;      /* 1 if the winner's Kabsch ran in FP64 */
     int32_t used_fallback;  /* learned proposal: 1 if the plain path decided the result */
     int32_t status;         /* turboreg_status of this problem */
+    float score;            /* the winner's selection score: the inlier number (SCORE_IN), or its
+                               capped mean error in metres (MAE) or square metres (MSE), computed
+                               in FP32 with each term rounded to 2^-22 theta (theta^2) */
 } turboreg_result;
 
 /* Fill p with the paper's defaults (K2 = 2, O2Graph, plain proposal,
- * kappa bound 100) and the given tau, K1 and inlier threshold. */
+ * inlier-number scoring, kappa bound 100) and the given tau, K1 and inlier
+ * threshold. */
 void turboreg_default_params(turboreg_params* p, float tau, int32_t k1, float inlier_thresh);
 
 /* Create a context on CUDA device `device` sized for problems of up to

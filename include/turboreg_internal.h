@@ -32,7 +32,9 @@ typedef enum {
     TURBOREG_BUF_ROWSCORE = 8,  /* int32 [n]: sum_j G^_ij (SC^2 row score) */
     TURBOREG_BUF_DEGREE = 9,    /* int32 [n]: sum_j G_ij (degree in the compatibility graph) */
     TURBOREG_BUF_FEATURES = 10, /* float [n][8]: proposal features (learned proposal) */
-    TURBOREG_BUF_PROB = 11      /* float [n]: proposal inlier probabilities (learned proposal) */
+    TURBOREG_BUF_PROB = 11,     /* float [n]: proposal inlier probabilities (learned proposal) */
+    TURBOREG_BUF_SCORES = 12    /* uint64 [k2*n_pivots]: capped error sum per hypothesis in units of
+                                   2^-22 theta (MAE) or 2^-22 theta^2 (MSE); zero in SCORE_IN mode */
 } turboreg_buffer;
 
 /* Shape of the most recent turboreg_register call: n, n_pad, |P| and the
@@ -51,6 +53,23 @@ int turboreg_stage_times(turboreg_ctx* ctx, float* ms, int32_t max);
 
 /* Names of the stages reported by turboreg_stage_times. */
 const char* turboreg_stage_name(int32_t stage);
+
+/* Score caller-given rigid transforms on one problem with the library's
+ * verification kernel (the inlier number of Eq. 9 and the capped errors of
+ * the ranking study, Table 6), e.g. to compare the selected hypothesis with
+ * a reference transform.  src, dst: float32 [n][3], host or device.
+ * rt: HOST float32 [m][12], transform k = R (row-major 3x3) then t; 1 <= m <=
+ * TURBOREG_K1_MAX.  params: tau, K1, K2, graph_mode and proposal are
+ * ignored; inlier_thresh and scoring are used.  Outputs (HOST): out_in[m] the
+ * inlier numbers; out_units[m] (may be NULL) the capped-error sums in the
+ * units of TURBOREG_BUF_SCORES (all zero under TURBOREG_SCORE_IN).  The call
+ * reuses problem slot 0, so the inspection buffers of the previous register
+ * call are overwritten.
+ * Errors: INVALID_ARG (null pointer, m out of range, bad params, non-finite
+ * rt), TOO_FEW, NONFINITE, CUDA. */
+int turboreg_score_transforms(turboreg_ctx* ctx, const float* src, const float* dst, int32_t n,
+                              const turboreg_params* params, const float* rt, int32_t m,
+                              int32_t* out_in, uint64_t* out_units);
 
 /* ---- learned proposal (project extension; the paper ranks pivots by SC^2 alone) ----
  * A per-correspondence inlier-scoring MLP 8 -> 64 -> 128 -> 64 -> 1 (ReLU,

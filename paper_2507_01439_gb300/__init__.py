@@ -25,14 +25,16 @@ TURBOREG_K1_MAX = 8192
 TURBOREG_K2_MAX = 16
 
 OK, ERR_INVALID_ARG, ERR_TOO_FEW, ERR_NONFINITE, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_NO_HYPOTHESIS = range(8)
-GRAPH_O2 = 0
+GRAPH_O2, GRAPH_SC2 = 0, 1
+SCORE_IN, SCORE_MAE, SCORE_MSE = 0, 1, 2
 PROPOSAL_PLAIN, PROPOSAL_LEARNED = 0, 1
 FLAG_SC2_BITSET = 0x1
 FLAG_STAGE_TIMES = 0x2
 FLAG_NO_GRAPH = 0x4
 
 (BUF_ADJ_BITS, BUF_ADJ_FP8, BUF_SC2, BUF_PIVOTS, BUF_CLIQUES, BUF_RT, BUF_INLIERS, BUF_ROWSCORE, BUF_DEGREE,
- BUF_FEATURES, BUF_PROB) = range(1, 12)
+ BUF_FEATURES, BUF_PROB, BUF_SCORES) = range(1, 13)
+SCORE_UNITS = 1 << 22   # BUF_SCORES units per theta (MAE) or theta^2 (MSE)
 
 # symbols the library must export (declared in include/turboreg.h and include/turboreg_internal.h)
 EXPORTED = (
@@ -41,7 +43,7 @@ EXPORTED = (
     "turboreg_stage_times", "turboreg_stage_name", "turboreg_select_pivots_noalloc",
     "turboreg_set_proposal_model", "turboreg_features", "turboreg_mlp_create", "turboreg_mlp_destroy",
     "turboreg_mlp_get_params", "turboreg_mlp_set_params", "turboreg_mlp_get_state", "turboreg_mlp_set_state",
-    "turboreg_mlp_forward", "turboreg_mlp_grad", "turboreg_mlp_train_step",
+    "turboreg_mlp_forward", "turboreg_mlp_grad", "turboreg_mlp_train_step", "turboreg_score_transforms",
 )
 TURBOREG_MLP_PARAMS = 17217
 TURBOREG_NOALLOC_MAX_N = 8192
@@ -51,14 +53,14 @@ class turboreg_params(ctypes.Structure):
     _fields_ = [("tau", ctypes.c_float), ("k1", ctypes.c_int32), ("k2", ctypes.c_int32),
                 ("inlier_thresh", ctypes.c_float), ("graph_mode", ctypes.c_int32),
                 ("proposal", ctypes.c_int32), ("kappa_fp64", ctypes.c_float), ("flags", ctypes.c_uint32),
-                ("learned_min_inliers", ctypes.c_int32)]
+                ("learned_min_inliers", ctypes.c_int32), ("scoring", ctypes.c_int32)]
 
 
 class turboreg_result(ctypes.Structure):
     _fields_ = [("R", ctypes.c_float * 9), ("t", ctypes.c_float * 3), ("clique", ctypes.c_int32 * 3),
                 ("inlier_count", ctypes.c_int32), ("hypothesis", ctypes.c_int32),
                 ("n_pivots", ctypes.c_int32), ("n_valid", ctypes.c_int32), ("used_fp64", ctypes.c_int32),
-                ("used_fallback", ctypes.c_int32), ("status", ctypes.c_int32)]
+                ("used_fallback", ctypes.c_int32), ("status", ctypes.c_int32), ("score", ctypes.c_float)]
 
 
 _lib = None
@@ -100,6 +102,8 @@ def load_library(path: str = LIB_PATH):
     lib.turboreg_select_pivots_noalloc.argtypes = [P, i32, i32, i32, P, P, P]
     lib.turboreg_select_pivots_noalloc.restype = ctypes.c_int
     F = ctypes.POINTER(ctypes.c_float)
+    lib.turboreg_score_transforms.argtypes = [P, P, P, i32, ctypes.POINTER(turboreg_params), P, i32, P, P]
+    lib.turboreg_score_transforms.restype = ctypes.c_int
     lib.turboreg_set_proposal_model.argtypes = [P, P]
     lib.turboreg_features.argtypes = [P, P, P, i32, ctypes.POINTER(turboreg_params), P]
     lib.turboreg_mlp_create.argtypes = [ctypes.c_int, i32, ctypes.c_uint64, P, ctypes.POINTER(P)]
@@ -142,7 +146,7 @@ def _check_points(a, n=None):
 
 
 def default_params(tau, k1, inlier_thresh, k2=2, kappa_fp64=100.0, flags=0, proposal=PROPOSAL_PLAIN,
-                   learned_min_inliers=0):
+                   learned_min_inliers=0, graph_mode=GRAPH_O2, scoring=SCORE_IN):
     p = turboreg_params()
     load_library().turboreg_default_params(ctypes.byref(p), float(tau), int(k1), float(inlier_thresh))
     p.k2 = int(k2)
@@ -150,7 +154,20 @@ def default_params(tau, k1, inlier_thresh, k2=2, kappa_fp64=100.0, flags=0, prop
     p.flags = int(flags)
     p.proposal = int(proposal)
     p.learned_min_inliers = int(learned_min_inliers)
+    p.graph_mode = int(graph_mode)
+    p.scoring = int(scoring)
     return p
+
+
+def score_values(units, inl, params, n):
+    """Selection scores from the library's integer outputs: the inlier
+    number (SCORE_IN), or the capped error sums (BUF_SCORES units) as means
+    in metres (MAE) or square metres (MSE)."""
+    if params.scoring == SCORE_IN:
+        return np.asarray(inl, dtype=np.float64)
+    th = float(np.float32(params.inlier_thresh))
+    unit = th if params.scoring == SCORE_MAE else th * th
+    return np.asarray(units, dtype=np.float64) * unit / (SCORE_UNITS * n)
 
 
 def status_string(code: int) -> str:
@@ -169,13 +186,14 @@ class Result:
     n_valid: int
     used_fp64: int
     used_fallback: int
+    score: float = 0.0
 
     @staticmethod
     def from_c(r: turboreg_result) -> "Result":
         return Result(int(r.status), np.array(r.R[:], dtype=np.float32).reshape(3, 3),
                       np.array(r.t[:], dtype=np.float32), tuple(r.clique[:]), int(r.inlier_count),
                       int(r.hypothesis), int(r.n_pivots), int(r.n_valid), int(r.used_fp64),
-                      int(r.used_fallback))
+                      int(r.used_fallback), float(r.score))
 
 
 class TurboReg:
@@ -255,6 +273,7 @@ class TurboReg:
             BUF_DEGREE: (np.int32, (n,)),
             BUF_FEATURES: (np.float32, (n, 8)),
             BUF_PROB: (np.float32, (n,)),
+            BUF_SCORES: (np.uint64, (nh,)),
         }[which]
         arr = np.zeros(spec[1], dtype=spec[0])
         got = self._lib.turboreg_debug_copy(self.handle, int(which), ctypes.c_void_p(arr.ctypes.data),
@@ -262,6 +281,25 @@ class TurboReg:
         if got < 0:
             raise RuntimeError(status_string(-got))
         return arr
+
+    def score_transforms(self, src, dst, params, rt):
+        """Score transforms rt [m, 12] (R row-major, t) on one problem with the
+        library's verification kernel: (inlier numbers int32 [m], selection
+        scores float64 [m]: the inlier number, or the capped MAE / MSE)."""
+        _check_points(src)
+        _check_points(dst, src.shape[0])
+        rt = np.ascontiguousarray(rt, dtype=np.float32).reshape(-1, 12)
+        m = rt.shape[0]
+        n = int(src.shape[0])
+        inl = np.zeros(m, dtype=np.int32)
+        units = np.zeros(m, dtype=np.uint64)
+        rc = self._lib.turboreg_score_transforms(self.handle, _ptr(src), _ptr(dst), n, ctypes.byref(params),
+                                                 ctypes.c_void_p(rt.ctypes.data), m,
+                                                 ctypes.c_void_p(inl.ctypes.data),
+                                                 ctypes.c_void_p(units.ctypes.data))
+        if rc != OK:
+            raise RuntimeError(f"turboreg_score_transforms failed: {status_string(rc)}")
+        return inl, score_values(units, inl, params, n)
 
     def set_proposal_model(self, params):
         w = np.ascontiguousarray(params, dtype=np.float32)

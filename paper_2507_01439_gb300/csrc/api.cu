@@ -3,7 +3,7 @@
 // A context owns a device workspace sized at creation: max_batch problem
 // slots, each sized for max_n.  A register call builds a plan (per-problem
 // views, per-stage block prefixes, tensor maps), enqueues one launch per
-// stage for all of its problems on the context's stream, copies the 88-byte
+// stage for all of its problems on the context's stream, copies the 92-byte
 // results back and synchronises.  The enqueued pipeline is captured once per
 // plan shape as a CUDA graph and replayed; the pack node's input pointers are
 // patched per call.  No host round trip happens between stages: pivot
@@ -55,6 +55,7 @@ struct Workspace {
     int4* cliques = nullptr;         // [slots][nh]
     float* rt = nullptr;             // [slots][nh * 16]
     int32_t* inl = nullptr;          // [slots][nh]
+    unsigned long long* score = nullptr;  // [slots][nh]
     int32_t* fp64_list = nullptr;    // [slots][nh]
     float* feat = nullptr;           // [slots][np][8] proposal features
     float* prob = nullptr;           // [slots][np] proposal probabilities
@@ -150,7 +151,7 @@ cudaError_t halloc(T** p, size_t count)
 void free_ws(Workspace& ws)
 {
     void* dptrs[] = {ws.pts, ws.pts8, ws.a8, ws.bits, ws.w, ws.rows, ws.hist, ws.cand, ws.piv, ws.cliques,
-                     ws.rt, ws.inl, ws.fp64_list, ws.feat, ws.prob, ws.ctl, ws.res, ws.in_src, ws.in_dst,
+                     ws.rt, ws.inl, ws.score, ws.fp64_list, ws.feat, ws.prob, ws.ctl, ws.res, ws.in_src, ws.in_dst,
                      ws.desc};
     for (void* p : dptrs)
         if (p) cudaFree(p);
@@ -184,6 +185,7 @@ int alloc_ws(Workspace& ws, int32_t max_n, int32_t slots)
     if (e == cudaSuccess) e = dalloc(&ws.cliques, S * nh);
     if (e == cudaSuccess) e = dalloc(&ws.rt, S * nh * 16);
     if (e == cudaSuccess) e = dalloc(&ws.inl, S * nh);
+    if (e == cudaSuccess) e = dalloc(&ws.score, S * nh);
     if (e == cudaSuccess) e = dalloc(&ws.fp64_list, S * nh);
     if (e == cudaSuccess) e = dalloc(&ws.feat, S * np * 8);
     if (e == cudaSuccess) e = dalloc(&ws.prob, S * np);
@@ -217,7 +219,8 @@ int check_params(const turboreg_ctx* c, int32_t n, const turboreg_params* p)
         return TURBOREG_ERR_INVALID_ARG;
     if (!(p->tau >= 0.f) || !std::isfinite(p->tau) || !(p->inlier_thresh > 0.f) || !std::isfinite(p->inlier_thresh))
         return TURBOREG_ERR_INVALID_ARG;
-    if (p->graph_mode != TURBOREG_GRAPH_O2) return TURBOREG_ERR_INVALID_ARG;
+    if (p->graph_mode != TURBOREG_GRAPH_O2 && p->graph_mode != TURBOREG_GRAPH_SC2) return TURBOREG_ERR_INVALID_ARG;
+    if (p->scoring < TURBOREG_SCORE_IN || p->scoring > TURBOREG_SCORE_MSE) return TURBOREG_ERR_INVALID_ARG;
     if (p->proposal != TURBOREG_PROPOSAL_PLAIN &&
         !(p->proposal == TURBOREG_PROPOSAL_LEARNED && c->has_model))
         return TURBOREG_ERR_INVALID_ARG;
@@ -266,6 +269,8 @@ ProbView make_view(turboreg_ctx* c, int slot, int64_t in_off, int32_t n, const t
     v.tau = p->tau;
     v.theta = p->inlier_thresh;
     v.kappa_fp64 = p->kappa_fp64 > 0.f ? p->kappa_fp64 : 100.f;
+    v.graph_mode = p->graph_mode;
+    v.scoring = p->scoring;
     v.pts = ws.pts + s * 6 * np;
     v.pts8 = ws.pts8 + s * 8 * np;
     v.a8 = ws.a8 + s * n2;
@@ -284,6 +289,7 @@ ProbView make_view(turboreg_ctx* c, int slot, int64_t in_off, int32_t n, const t
     v.cliques = ws.cliques + s * ws.nh;
     v.rt = ws.rt + s * ws.nh * 16;
     v.inl = ws.inl + s * ws.nh;
+    v.score = ws.score + s * ws.nh;
     v.fp64_list = ws.fp64_list + s * ws.nh;
     v.feat = ws.feat + s * np * 8;
     v.prob = p->proposal == TURBOREG_PROPOSAL_LEARNED ? ws.prob + s * np : nullptr;
@@ -451,6 +457,8 @@ std::vector<uint8_t> plan_key(turboreg_ctx* c, const Plan& pl)
         put(&v.tau, sizeof(v.tau));
         put(&v.theta, sizeof(v.theta));
         put(&v.kappa_fp64, sizeof(v.kappa_fp64));
+        put(&v.graph_mode, sizeof(v.graph_mode));
+        put(&v.scoring, sizeof(v.scoring));
     }
     return k;
 }
@@ -878,6 +886,7 @@ int64_t turboreg_debug_copy(turboreg_ctx* c, int which, void* dst, int64_t max_b
         case TURBOREG_BUF_CLIQUES: src = v.cliques; bytes = nh * 16; break;
         case TURBOREG_BUF_RT: src = v.rt; bytes = nh * 64; break;
         case TURBOREG_BUF_INLIERS: src = v.inl; bytes = nh * 4; break;
+        case TURBOREG_BUF_SCORES: src = v.score; bytes = nh * 8; break;
         case TURBOREG_BUF_ROWSCORE: src = v.rowscore; bytes = static_cast<size_t>(c->last_n) * 4; break;
         case TURBOREG_BUF_DEGREE: src = v.deg; bytes = static_cast<size_t>(c->last_n) * 4; break;
         case TURBOREG_BUF_FEATURES: src = v.feat; bytes = static_cast<size_t>(c->last_n) * 32; break;
@@ -924,6 +933,72 @@ int turboreg_set_proposal_model(turboreg_ctx* c, const float* params)
     }
     c->has_model = true;
     for (auto& sl : c->gslot) drop_slot(sl);   // captured graphs bake the model pointer in: recapture
+    return TURBOREG_OK;
+}
+
+int turboreg_score_transforms(turboreg_ctx* c, const float* src, const float* dst, int32_t n,
+                              const turboreg_params* p, const float* rt, int32_t m, int32_t* out_in,
+                              uint64_t* out_units)
+{
+    if (!c || !src || !dst || !p || !rt || !out_in) return TURBOREG_ERR_INVALID_ARG;
+    if (m < 1 || m > TURBOREG_K1_MAX) return TURBOREG_ERR_INVALID_ARG;
+    if (!host_finite(rt, static_cast<size_t>(m) * 12)) return TURBOREG_ERR_INVALID_ARG;
+    turboreg_params q = *p;
+    q.proposal = TURBOREG_PROPOSAL_PLAIN;
+    q.flags = 0;
+    q.k1 = m;
+    q.k2 = 1;
+    q.graph_mode = TURBOREG_GRAPH_O2;
+    if (!(q.tau >= 0.f) || !std::isfinite(q.tau)) q.tau = 0.f;
+    int rc = check_params(c, n, &q);
+    if (rc != TURBOREG_OK) return rc;
+    TR_CHECK(cudaSetDevice(c->device));
+    const size_t bytes = static_cast<size_t>(n) * 3 * sizeof(float);
+    const float* s_in = src;
+    const float* d_in = dst;
+    if (!is_device_ptr(src)) {
+        if (!host_finite(src, static_cast<size_t>(n) * 3)) return TURBOREG_ERR_NONFINITE;
+        TR_CHECK(cudaMemcpyAsync(c->ws.in_src, src, bytes, cudaMemcpyHostToDevice, c->stream));
+        s_in = c->ws.in_src;
+    }
+    if (!is_device_ptr(dst)) {
+        if (!host_finite(dst, static_cast<size_t>(n) * 3)) return TURBOREG_ERR_NONFINITE;
+        TR_CHECK(cudaMemcpyAsync(c->ws.in_dst, dst, bytes, cudaMemcpyHostToDevice, c->stream));
+        d_in = c->ws.in_dst;
+    }
+    Plan pl;
+    const int64_t off0 = 0;
+    const turboreg_params* pq = &q;
+    rc = build_plan(c, 1, &off0, &n, &pq, pl);
+    if (rc != TURBOREG_OK) return rc;
+    Batch bt;
+    rc = upload_desc(c, 1, c->ws.desc, bt, c->stream);
+    if (rc != TURBOREG_OK) return rc;
+    const ProbView& v = c->ws.h_views[0];
+    // hypotheses in the verification layout: R (9), t (3), kappa, flags = 1 (valid)
+    std::vector<float> h(static_cast<size_t>(m) * 16, 0.f);
+    const int32_t valid = 1;
+    for (int32_t k = 0; k < m; ++k) {
+        std::memcpy(&h[static_cast<size_t>(k) * 16], rt + static_cast<size_t>(k) * 12, 12 * sizeof(float));
+        std::memcpy(&h[static_cast<size_t>(k) * 16 + 13], &valid, sizeof(valid));
+    }
+    TR_CHECK(cudaMemsetAsync(c->ws.ctl, 0, sizeof(Ctl), c->stream));
+    launch_pack(bt, pl.tot[ST_PACK], s_in, d_in, c->stream);
+    TR_CHECK(cudaMemcpyAsync(v.rt, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+    TR_CHECK(cudaMemcpyAsync(&v.ctl->n_pivots, &m, sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
+    TR_CHECK(cudaMemsetAsync(v.inl, 0, sizeof(int32_t) * m, c->stream));
+    TR_CHECK(cudaMemsetAsync(v.score, 0, sizeof(unsigned long long) * m, c->stream));
+    launch_verify(bt, pl.tot[ST_VERIFY], c->stream);
+    TR_CHECK(cudaGetLastError());
+    TR_CHECK(cudaMemcpyAsync(out_in, v.inl, sizeof(int32_t) * m, cudaMemcpyDeviceToHost, c->stream));
+    if (out_units)
+        TR_CHECK(cudaMemcpyAsync(out_units, v.score, sizeof(unsigned long long) * m, cudaMemcpyDeviceToHost,
+                                 c->stream));
+    Ctl hc;
+    TR_CHECK(cudaMemcpyAsync(&hc, c->ws.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, c->stream));
+    TR_CHECK(cudaStreamSynchronize(c->stream));
+    if (hc.err & TR_ERR_NONFINITE) return TURBOREG_ERR_NONFINITE;
+    if (hc.err) return TURBOREG_ERR_TIMEOUT;
     return TURBOREG_OK;
 }
 

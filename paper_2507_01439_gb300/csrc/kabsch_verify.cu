@@ -178,6 +178,7 @@ __global__ void __launch_bounds__(128) kabsch_kernel(ManyViews vs)
     const int nh = v.ctl->n_pivots * v.k2;
     if (h >= nh) return;
     v.inl[h] = 0;
+    v.score[h] = 0ull;
     float* out = v.rt + (size_t)h * 16;
     const int4 cl = v.cliques[h];
     uint32_t flags = 0;
@@ -271,19 +272,29 @@ __device__ __forceinline__ f2 mul2(f2 a, f2 b)
 // warps' counts are summed in shared memory; one atomic per hypothesis.
 // kList: hypotheses are the entries of the FP64 Kabsch list; otherwise the
 // hypotheses whose FP32 Kabsch is valid (flags == 1).
+//
+// Capped-error scores (MAE, MSE of the ranking study, Table 6): each match
+// adds min(e, theta) or min(e^2, theta^2), rounded to an integer number of
+// units of 2^-22 theta (theta^2).  Integer sums are independent of the order
+// in which blocks add them, so a problem's scores do not depend on how the
+// work was split (one problem or a batch).
 constexpr int kVWarps = 4;
 constexpr int kVHyp = 128;
 constexpr int kVPtsWarp = 64;
 constexpr int kVPts = kVWarps * kVPtsWarp;
+constexpr float kScoreUnits = 4194304.f;   // 2^22 units per theta (MAE) or theta^2 (MSE)
 
-template <bool kList>
-__global__ void __launch_bounds__(128) verify_kernel(ManyViews vs)
+struct VerifyShared {
+    float4 sp[kVPts][2];
+    float4 srt[kVHyp][4];
+    int scnt[kVWarps][kVHyp];
+    uint32_t ssc[kVWarps][kVHyp];
+    int sok[kVHyp];
+};
+
+template <bool kList, int kScore>
+__device__ __forceinline__ void verify_body(const ProbView& v, int lb, VerifyShared& sh)
 {
-    __shared__ __align__(16) float4 sp[kVPts][2];
-    __shared__ __align__(16) float4 srt[kVHyp][4];
-    __shared__ int scnt[kVWarps][kVHyp];
-    int lb;
-    const ProbView v = vs.get(ST_VERIFY, blockIdx.x, lb);
     const int npb = (v.n + kVPts - 1) / kVPts;          // point blocks of this problem
     const int nh = kList ? static_cast<int>(v.ctl->fp64_slot) : v.ctl->n_pivots * v.k2;
     const int h0 = (lb / npb) * kVHyp;
@@ -292,40 +303,46 @@ __global__ void __launch_bounds__(128) verify_kernel(ManyViews vs)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     {
         const float4* src = reinterpret_cast<const float4*>(v.pts8 + (size_t)k0 * 8);
-        for (int q = threadIdx.x; q < 2 * kVPts; q += blockDim.x) (&sp[0][0])[q] = src[q];
+        for (int q = threadIdx.x; q < 2 * kVPts; q += blockDim.x) (&sh.sp[0][0])[q] = src[q];
         const int slot = h0 + threadIdx.x;
         float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0, r3 = r0;
+        bool ok = false;
         if (slot < nh) {
             const int h = kList ? v.fp64_list[slot] : slot;
             const float4* rt = reinterpret_cast<const float4*>(v.rt + (size_t)h * 16);
             r0 = rt[0]; r1 = rt[1]; r2 = rt[2]; r3 = rt[3];
             const int flags = __float_as_int(r3.y);
-            const bool ok = kList ? (flags & 1) != 0 : flags == 1;
+            ok = kList ? (flags & 1) != 0 : flags == 1;
             if (!ok) r2.y = r2.z = r2.w = __int_as_float(0x7fc00000);   // NaN t: never an inlier
         } else {
             r2.y = r2.z = r2.w = __int_as_float(0x7fc00000);
         }
-        srt[threadIdx.x][0] = r0; srt[threadIdx.x][1] = r1; srt[threadIdx.x][2] = r2; srt[threadIdx.x][3] = r3;
+        sh.srt[threadIdx.x][0] = r0; sh.srt[threadIdx.x][1] = r1;
+        sh.srt[threadIdx.x][2] = r2; sh.srt[threadIdx.x][3] = r3;
+        sh.sok[threadIdx.x] = ok ? 1 : 0;
     }
     __syncthreads();
     // this lane's hypotheses: slots lane + 32 a, a = 0..3, as packed pairs (0,1), (2,3)
     f2 R[2][9], T[2][3];
 #pragma unroll
     for (int pr = 0; pr < 2; ++pr) {
-        const float* A = reinterpret_cast<const float*>(&srt[lane + 64 * pr][0]);
-        const float* B = reinterpret_cast<const float*>(&srt[lane + 64 * pr + 32][0]);
+        const float* A = reinterpret_cast<const float*>(&sh.srt[lane + 64 * pr][0]);
+        const float* B = reinterpret_cast<const float*>(&sh.srt[lane + 64 * pr + 32][0]);
 #pragma unroll
         for (int c = 0; c < 9; ++c) R[pr][c] = pk(A[c], B[c]);
 #pragma unroll
         for (int c = 0; c < 3; ++c) T[pr][c] = pk(A[9 + c], B[9 + c]);
     }
-    const float th2 = v.theta * v.theta;
+    const float th = v.theta;
+    const float th2 = th * th;
+    const float qs = kScore == TURBOREG_SCORE_MAE ? kScoreUnits / th : kScoreUnits / th2;
     const int kb = warp * kVPtsWarp;
     const int cnt = max(0, min(kVPtsWarp, v.n - k0 - kb));
     int in[4] = {0, 0, 0, 0};
+    uint32_t sc[4] = {0u, 0u, 0u, 0u};
 #pragma unroll 2
     for (int k = 0; k < cnt; ++k) {
-        const float4 pa = sp[kb + k][0], pb = sp[kb + k][1];
+        const float4 pa = sh.sp[kb + k][0], pb = sh.sp[kb + k][1];
         const f2 X0 = pk(pa.x, pa.x), X1 = pk(pa.y, pa.y), X2 = pk(pa.z, pa.z);
         const f2 Y0 = pk(pa.w, pa.w), Y1 = pk(pb.x, pb.x), Y2 = pk(pb.y, pb.y);
 #pragma unroll
@@ -338,16 +355,69 @@ __global__ void __launch_bounds__(128) verify_kernel(ManyViews vs)
             upk(d2, lo, hi);
             in[2 * pr] += lo <= th2 ? 1 : 0;
             in[2 * pr + 1] += hi <= th2 ? 1 : 0;
+            if (kScore == TURBOREG_SCORE_MAE) {
+                // fminf(NaN, theta) = theta: an invalid hypothesis is never selected anyway
+                sc[2 * pr] += __float2uint_rn(fminf(sqrtf(lo), th) * qs);
+                sc[2 * pr + 1] += __float2uint_rn(fminf(sqrtf(hi), th) * qs);
+            } else if (kScore == TURBOREG_SCORE_MSE) {
+                sc[2 * pr] += __float2uint_rn(fminf(lo, th2) * qs);
+                sc[2 * pr + 1] += __float2uint_rn(fminf(hi, th2) * qs);
+            }
         }
     }
-    scnt[warp][lane] = in[0];
-    scnt[warp][lane + 32] = in[1];
-    scnt[warp][lane + 64] = in[2];
-    scnt[warp][lane + 96] = in[3];
+    sh.scnt[warp][lane] = in[0];
+    sh.scnt[warp][lane + 32] = in[1];
+    sh.scnt[warp][lane + 64] = in[2];
+    sh.scnt[warp][lane + 96] = in[3];
+    if (kScore != TURBOREG_SCORE_IN) {
+        sh.ssc[warp][lane] = sc[0];
+        sh.ssc[warp][lane + 32] = sc[1];
+        sh.ssc[warp][lane + 64] = sc[2];
+        sh.ssc[warp][lane + 96] = sc[3];
+    }
     __syncthreads();
-    const int slot = h0 + threadIdx.x;
-    const int tot = scnt[0][threadIdx.x] + scnt[1][threadIdx.x] + scnt[2][threadIdx.x] + scnt[3][threadIdx.x];
-    if (slot < nh && tot) atomicAdd(&v.inl[kList ? v.fp64_list[slot] : slot], tot);
+    const int t = threadIdx.x;
+    const int slot = h0 + t;
+    if (slot >= nh) return;
+    const int hh = kList ? v.fp64_list[slot] : slot;
+    const int tot = sh.scnt[0][t] + sh.scnt[1][t] + sh.scnt[2][t] + sh.scnt[3][t];
+    if (tot) atomicAdd(&v.inl[hh], tot);
+    if (kScore != TURBOREG_SCORE_IN && sh.sok[t]) {
+        // per block at most 256 terms of <= 2^22 + 1 units: fits 32 bits
+        const uint32_t s = sh.ssc[0][t] + sh.ssc[1][t] + sh.ssc[2][t] + sh.ssc[3][t];
+        atomicAdd(&v.score[hh], static_cast<unsigned long long>(s));
+    }
+}
+
+template <bool kList>
+__global__ void __launch_bounds__(128) verify_kernel(ManyViews vs)
+{
+    __shared__ __align__(16) VerifyShared sh;
+    int lb;
+    const ProbView v = vs.get(ST_VERIFY, blockIdx.x, lb);
+    switch (v.scoring) {      // uniform over the block: a block serves one problem
+        case TURBOREG_SCORE_MAE: verify_body<kList, TURBOREG_SCORE_MAE>(v, lb, sh); break;
+        case TURBOREG_SCORE_MSE: verify_body<kList, TURBOREG_SCORE_MSE>(v, lb, sh); break;
+        default: verify_body<kList, TURBOREG_SCORE_IN>(v, lb, sh); break;
+    }
+}
+
+// Selection key of hypothesis h (larger wins; distinct h give distinct keys,
+// and ties of the score go to the lower h).  Inlier number: (IN + 1) << 32 |
+// ~h.  Capped error: (2^40 - 1 - units) << 20 | (2^20 - 1 - h); the unit sum
+// is at most N (2^22 + 1) < 2^38 and h < K1_MAX * K2_MAX = 2^17.
+__device__ __forceinline__ unsigned long long select_key(const ProbView& v, int h)
+{
+    if (v.scoring == TURBOREG_SCORE_IN)
+        return (static_cast<unsigned long long>(static_cast<uint32_t>(v.inl[h]) + 1u) << 32) |
+               (0xFFFFFFFFull - static_cast<unsigned long long>(h));
+    return ((0xFFFFFFFFFFull - v.score[h]) << 20) | (0xFFFFFull - static_cast<unsigned long long>(h));
+}
+
+__device__ __forceinline__ int key_hypothesis(const ProbView& v, unsigned long long key)
+{
+    if (v.scoring == TURBOREG_SCORE_IN) return static_cast<int>(0xFFFFFFFFull - (key & 0xFFFFFFFFull));
+    return static_cast<int>(0xFFFFFull - (key & 0xFFFFFull));
 }
 
 __global__ void __launch_bounds__(1024) finalize_kernel(ManyViews vs)
@@ -365,9 +435,7 @@ __global__ void __launch_bounds__(1024) finalize_kernel(ManyViews vs)
         if (flags & 2u) ++nfp;
         if (!(flags & 1u)) continue;
         ++nvalid;
-        const unsigned long long key =
-            (static_cast<unsigned long long>(static_cast<uint32_t>(v.inl[h]) + 1u) << 32) |
-            (0xFFFFFFFFull - static_cast<unsigned long long>(h));
+        const unsigned long long key = select_key(v, h);
         best = key > best ? key : best;
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -393,6 +461,7 @@ __global__ void __launch_bounds__(1024) finalize_kernel(ManyViews vs)
     r.t[0] = r.t[1] = r.t[2] = 0.f;
     r.clique[0] = r.clique[1] = r.clique[2] = -1;
     r.inlier_count = 0;
+    r.score = 0.f;
     r.hypothesis = -1;
     r.n_pivots = np;
     r.n_valid = nvalid;
@@ -408,13 +477,19 @@ __global__ void __launch_bounds__(1024) finalize_kernel(ManyViews vs)
     } else if (best == 0ull) {
         r.status = TURBOREG_ERR_NO_HYPOTHESIS;
     } else {
-        const int h = static_cast<int>(0xFFFFFFFFull - (best & 0xFFFFFFFFull));
+        const int h = key_hypothesis(v, best);
         const float* rt = v.rt + (size_t)h * 16;
         for (int q = 0; q < 9; ++q) r.R[q] = rt[q];
         for (int q = 0; q < 3; ++q) r.t[q] = rt[9 + q];
         const int4 cl = v.cliques[h];
         r.clique[0] = cl.x; r.clique[1] = cl.y; r.clique[2] = cl.z;
-        r.inlier_count = static_cast<int>((best >> 32) - 1ull);
+        r.inlier_count = v.inl[h];
+        if (v.scoring == TURBOREG_SCORE_IN) {
+            r.score = static_cast<float>(r.inlier_count);
+        } else {
+            const double unit = v.scoring == TURBOREG_SCORE_MAE ? (double)v.theta : (double)v.theta * v.theta;
+            r.score = static_cast<float>((double)v.score[h] * unit / (4194304.0 * v.n));
+        }
         r.hypothesis = h;
         r.used_fp64 = (static_cast<uint32_t>(__float_as_int(rt[13])) & 2u) ? 1 : 0;
         r.status = TURBOREG_OK;

@@ -1,6 +1,7 @@
-// Stage 4: Pivot-Guided Search (Eq. 5-7, Alg. 1) on the O2Graph.
+// Stage 4: Pivot-Guided Search (Eq. 5-7, Alg. 1) on the O2Graph or on the
+// undirected SC^2 graph.
 //
-// For pivot p = (i, j) (i < j):
+// O2Graph (Def. 2), pivot p = (i, j) (i < j):
 //   N(i,j) = { z : G~_iz > 0 and G~_jz > 0 }            (Eq. 5)
 // On the O2Graph G~_iz > 0 needs i < z, so z > j; and for a pivot edge,
 // G~_iz > 0 <=> G_iz = 1 (j is then a common neighbour of i and z).  So
@@ -8,6 +9,9 @@
 //   S(z)   = W_ij + W_iz + W_jz                          (Eq. 6)
 // and the K2 largest S (ties: lower z) form the pivot's TurboCliques (Eq. 7),
 // written in the Alg. 2 layout h = r * |P| + p.  Empty slots are invalid.
+// Undirected SC^2 graph: the same with z over every common neighbour
+// (z != i, j follows from the zero diagonal) and W read symmetrically,
+// W_ab = W_min(a,b),max(a,b) (only the upper triangle is stored).
 //
 // One warp per pivot: lane l ANDs bitset words l, l+32, ... of the two rows,
 // keeps a private top-K2 list, and the warp merges the 32 lists with K2
@@ -35,6 +39,7 @@ __global__ void __launch_bounds__(256) pgs_kernel(ManyViews vs)
     const uint32_t* bj = v.bits + (size_t)j * v.ldb;
     const uint16_t* wi = v.w + (size_t)i * v.n_pad;
     const uint16_t* wj = v.w + (size_t)j * v.n_pad;
+    const bool undirected = v.graph_mode == TURBOREG_GRAPH_SC2;
 
     constexpr int L = K2C > 0 ? K2C : TURBOREG_K2_MAX;
     uint64_t top[L];
@@ -48,8 +53,14 @@ __global__ void __launch_bounds__(256) pgs_kernel(ManyViews vs)
         int wa[8], wb[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-            wa[q] = q < nz ? static_cast<int>(wi[zb[q]]) : 0;
-            wb[q] = q < nz ? static_cast<int>(wj[zb[q]]) : 0;
+            const int z = zb[q];
+            if (q < nz) {
+                // z > j > i on the O2Graph; the undirected search also meets z < j
+                wa[q] = static_cast<int>(z > i ? wi[z] : v.w[(size_t)z * v.n_pad + i]);
+                wb[q] = static_cast<int>(z > j ? wj[z] : v.w[(size_t)z * v.n_pad + j]);
+            } else {
+                wa[q] = wb[q] = 0;
+            }
         }
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
@@ -70,7 +81,7 @@ __global__ void __launch_bounds__(256) pgs_kernel(ManyViews vs)
         }
         nz = 0;
     };
-    const int zs = j + 1;
+    const int zs = undirected ? 0 : j + 1;
     const int w0 = zs >> 5;
     for (int wd = w0 + lane; wd < v.ldb; wd += 32) {
         uint32_t m = bi[wd] & bj[wd];

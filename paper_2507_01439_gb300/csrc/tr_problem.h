@@ -23,6 +23,8 @@ struct ProbView {
     float tau;           // Eq. 1 threshold
     float theta;         // inlier threshold
     float kappa_fp64;    // FP64 Kabsch above this sigma1/sigma2
+    int32_t graph_mode;  // TURBOREG_GRAPH_O2 / _SC2: the graph the clique search runs on
+    int32_t scoring;     // TURBOREG_SCORE_IN / _MAE / _MSE
     float* pts;          // [6][n_pad]
     float* pts8;         // [n_pad][8] = (x0, x1, x2, y0, y1, y2, 0, 0)
     uint8_t* a8;         // [n_pad][n_pad] FP8 E4M3 0/1 adjacency
@@ -40,6 +42,7 @@ struct ProbView {
     int4* cliques;       // [K1_MAX*K2_MAX] (i, j, z, valid) in Alg. 2 order
     float* rt;           // [K1_MAX*K2_MAX][16] R, t, kappa, flags
     int32_t* inl;        // [K1_MAX*K2_MAX] inlier numbers
+    unsigned long long* score;  // [K1_MAX*K2_MAX] capped error sums in units of 2^-22 theta (^2)
     int32_t* fp64_list;  // [K1_MAX*K2_MAX] hypotheses whose Kabsch needs FP64
     float* feat;         // [n_pad][8] proposal features (learned proposal only)
     float* prob;         // [n_pad] inlier probabilities; non-null selects the learned pivot weight

@@ -27,11 +27,11 @@ def unpack_bits(bits, n):
     return b[:n, :n]
 
 
-def oracle_stages(x, y, tau, k1, k2):
+def oracle_stages(x, y, tau, k1, k2, graph_mode=0):
     A = oracle.compat(x, y, tau)
     S = oracle.sc2(A)
     pi, pj, pw = oracle.pivots(S, k1)
-    cl, va = oracle.cliques(S, pi, pj, k2)
+    cl, va = oracle.cliques(S, pi, pj, k2, graph_mode=graph_mode)
     return A, S, (pi, pj, pw), (cl, va)
 
 
@@ -123,3 +123,55 @@ def check_final(res: trg.Result, ctx, orc: oracle.OracleResult):
     assert np.linalg.norm(res.R.astype(np.float64) - Ro) <= 1e-4
     assert np.linalg.norm(res.t.astype(np.float64) - to) <= 1e-4
     return kind
+
+
+def score_tolerances(ctx, x, y, theta, orc: oracle.OracleResult, scoring):
+    """Per-hypothesis bound on |GPU score - oracle score| for the capped-error
+    scores: each term min(e, theta) (MAE) or min(e^2, theta^2) (MSE) moves by
+    at most what the residual perturbation delta(h) allows (delta as in the
+    inlier check), plus one rounding unit (2^-22 theta or theta^2) and FP32
+    evaluation; the mean over matches keeps the per-term bound."""
+    RT = ctx.buffer(trg.BUF_RT)
+    nh = RT.shape[0]
+    xmax = float(np.abs(x).max()) * np.sqrt(3)
+    ymax = float(np.abs(y).max()) * np.sqrt(3)
+    th = float(np.float32(theta))
+    unit = th if scoring == oracle.SCORE_MAE else th * th
+    tol = np.full(nh, np.inf)
+    for h in np.flatnonzero(orc.hyp_valid[:nh]):
+        Rg = RT[h, :9].astype(np.float64).reshape(3, 3)
+        tg = RT[h, 9:12].astype(np.float64)
+        dR = float(np.linalg.norm(Rg - orc.rt[h, :9].reshape(3, 3)))
+        dt = float(np.linalg.norm(tg - orc.rt[h, 9:12]))
+        delta = dR * xmax + dt + 16 * U32 * (xmax + ymax + np.linalg.norm(tg))
+        if scoring == oracle.SCORE_MAE:
+            tol[h] = delta + 2.0 ** -22 * unit + 4 * U32 * th
+        else:
+            tol[h] = 2 * th * delta + delta * delta + 2.0 ** -22 * unit + 4 * U32 * unit
+    return tol
+
+
+def check_scores(ctx, x, y, theta, orc: oracle.OracleResult, scoring, res: trg.Result):
+    """Per-hypothesis scores within tolerance; the GPU's winner is a minimiser
+    of the oracle's scores within the tolerances (equal to the oracle's unless
+    the two are that close).  Returns "exact" or "ambiguous"."""
+    n = x.shape[0]
+    RT = ctx.buffer(trg.BUF_RT)
+    valid = (RT[:, 13].view(np.int32) & 1).astype(bool)
+    raw = ctx.buffer(trg.BUF_SCORES)
+    th = float(np.float32(theta))
+    unit = th if scoring == oracle.SCORE_MAE else th * th
+    got = raw.astype(np.float64) * unit / (trg.SCORE_UNITS * n)
+    tol = score_tolerances(ctx, x, y, theta, orc, scoring)
+    so = orc.scores[:len(got)]
+    for h in np.flatnonzero(valid):
+        assert abs(got[h] - so[h]) <= tol[h], f"h={h}: score gpu {got[h]:.9g} oracle {so[h]:.9g} tol {tol[h]:.3g}"
+    assert res.status == orc.status
+    if orc.status != 0:
+        return "none"
+    hg, ho = res.hypothesis, orc.hypothesis
+    assert abs(res.score - got[hg]) <= 1e-6 * max(got[hg], 1e-30)
+    assert so[hg] <= so[ho] + tol[hg] + tol[ho], f"h* gpu {hg} ({so[hg]:.9g}) vs oracle {ho} ({so[ho]:.9g})"
+    if hg != ho:
+        return "ambiguous"
+    return "exact"

@@ -1,0 +1,216 @@
+"""GPU parity of the graph and scoring variants with the FP64 oracle:
+the clique search on the undirected SC^2 graph (Alg. 1 with G- = G^, the
+Table 5 ablation) and hypothesis selection by capped MAE / MSE (the ranking
+study of Table 6)."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2507_01439_gb300 as trg
+import synth
+from parity_util import (check_final, check_graph_stages, check_hypotheses, check_pivots_cliques,
+                         check_scores, oracle_stages)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2507_01439_gb300 import build
+    build.build()
+    c = trg.TurboReg(max_n=5000, max_batch=8)
+    yield c
+    c.close()
+
+
+def _parity(ctx, p, k1, k2=2, graph_mode=0, scoring=0, flags=0):
+    prm = trg.default_params(p.tau, k1, p.theta, k2=k2, flags=flags, graph_mode=graph_mode, scoring=scoring)
+    res = ctx.register(p.x, p.y, prm)
+    A, S, piv, cliq = oracle_stages(p.x, p.y, p.tau, k1, k2, graph_mode=graph_mode)
+    check_graph_stages(ctx, A, S, p.n)
+    check_pivots_cliques(ctx, piv, cliq, k2)
+    orc = oracle.register(p.x, p.y, p.tau, k1, p.theta, k2=k2, graph_mode=graph_mode, scoring=scoring)
+    assert res.n_pivots == orc.n_pivots and res.n_valid == orc.n_valid
+    stats = check_hypotheses(ctx, p.x, p.y, p.theta, orc)
+    if scoring == 0:
+        kind = check_final(res, ctx, orc)
+        if res.status == 0:
+            assert res.score == float(res.inlier_count)
+    else:
+        kind = check_scores(ctx, p.x, p.y, p.theta, orc, scoring, res)
+        if res.status == 0:
+            assert res.inlier_count == ctx.buffer(trg.BUF_INLIERS)[res.hypothesis]
+    return res, orc, stats, kind
+
+
+@pytest.mark.parametrize("n,seed", [(7, 1), (129, 2), (257, 3), (900, 4)])
+def test_undirected_small_ragged(ctx, n, seed):
+    p = synth.make_problem("cube", n, 0.5, seed, tau=0.3, theta=0.1)
+    _parity(ctx, p, k1=min(200, 4 * n), graph_mode=trg.GRAPH_SC2)
+
+
+def test_undirected_indoor_5000(ctx):
+    p = synth.make_problem("indoor", 5000, 0.05, 0)
+    res, orc, stats, kind = _parity(ctx, p, k1=2000, graph_mode=trg.GRAPH_SC2)
+    print("undirected indoor-5000", stats, kind)
+    assert res.status == 0
+    assert synth.rotation_error_deg(p.R_gt, res.R) < 15 and synth.translation_error(p.t_gt, res.t) < 0.3
+
+
+@pytest.mark.parametrize("k2", [1, 4])
+def test_undirected_k2(ctx, k2):
+    p = synth.make_problem("outdoor", 1500, 0.2, 50 + k2)
+    _parity(ctx, p, k1=500, k2=k2, graph_mode=trg.GRAPH_SC2)
+
+
+@pytest.mark.parametrize("scoring", [trg.SCORE_MAE, trg.SCORE_MSE])
+@pytest.mark.parametrize("shape,n,ratio,k1,seed", [("cube", 1000, 0.1, 1000, 0), ("indoor", 5000, 0.05, 2000, 1),
+                                                    ("outdoor", 2500, 0.2, 1000, 2), ("cube", 300, 0.4, 200, 3)])
+def test_scoring_parity(ctx, scoring, shape, n, ratio, k1, seed):
+    p = synth.make_problem(shape, n, ratio, seed)
+    res, orc, stats, kind = _parity(ctx, p, k1=k1, scoring=scoring)
+    print(shape, n, "scoring", scoring, kind)
+    assert res.status == 0
+    assert synth.rotation_error_deg(p.R_gt, res.R) < p.re_deg and synth.translation_error(p.t_gt, res.t) < p.te_m
+
+
+def test_scoring_with_undirected_graph_and_bitset(ctx):
+    p = synth.make_problem("indoor", 2000, 0.08, 5)
+    _parity(ctx, p, k1=800, graph_mode=trg.GRAPH_SC2, scoring=trg.SCORE_MSE, flags=trg.FLAG_SC2_BITSET)
+
+
+def test_score_is_zero_for_an_exact_fit_and_capped_for_outliers(ctx):
+    # sigma = 0 and 100% inliers: the winner fits every match to rounding, so the
+    # capped errors are a few FP32 units; IN counts all matches
+    p = synth.make_problem("cube", 400, 1.0, 6, sigma=0.0)
+    for scoring in (trg.SCORE_MAE, trg.SCORE_MSE):
+        r = ctx.register(p.x, p.y, trg.default_params(p.tau, 100, p.theta, scoring=scoring))
+        assert r.status == 0 and r.inlier_count == 400
+        assert r.score < 1e-5 * (p.theta if scoring == trg.SCORE_MAE else p.theta ** 2)
+
+
+def test_batched_mixed_variants_equal_single_calls(ctx):
+    """One batch mixing graph modes and scorings gives, problem by problem,
+    exactly the single-call results."""
+    probs = [synth.make_problem("indoor" if b % 2 else "outdoor", 700 + 500 * b, 0.05 + 0.03 * b, 300 + b)
+             for b in range(6)]
+    modes = [(0, 0), (1, 0), (0, 1), (1, 2), (0, 2), (1, 1)]
+    prms = [trg.default_params(p.tau, 400, p.theta, graph_mode=g, scoring=s) for p, (g, s) in zip(probs, modes)]
+    offs = np.cumsum([0] + [p.n for p in probs]).astype(np.int64)
+    xs = np.concatenate([p.x for p in probs])
+    ys = np.concatenate([p.y for p in probs])
+    out = ctx.register_batched(xs, ys, offs, prms)
+    for p, prm, rb in zip(probs, prms, out):
+        rs = ctx.register(p.x, p.y, prm)
+        assert rb.status == rs.status and rb.hypothesis == rs.hypothesis and rb.clique == rs.clique
+        assert rb.inlier_count == rs.inlier_count and rb.score == rs.score
+        assert np.array_equal(rb.R, rs.R) and np.array_equal(rb.t, rs.t)
+
+
+def test_invalid_variant_arguments_rejected(ctx):
+    p = synth.make_problem("cube", 100, 0.3, 7)
+    for field, bad in (("graph_mode", 2), ("graph_mode", -1), ("scoring", 3), ("scoring", -1)):
+        prm = trg.default_params(p.tau, 50, p.theta)
+        setattr(prm, field, bad)
+        r = ctx.register(p.x, p.y, prm)
+        assert r.status == trg.ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("scoring", [trg.SCORE_IN, trg.SCORE_MAE, trg.SCORE_MSE])
+def test_score_transforms_matches_oracle(ctx, scoring):
+    """The verification kernel scores caller-given transforms: the ground truth
+    and perturbed copies of it, against the oracle's FP64 scores."""
+    p = synth.make_problem("indoor", 3000, 0.1, 8)
+    rng = np.random.default_rng(8)
+    rts, mats = [], []
+    for k in range(40):
+        a = rng.normal(scale=0.02 * (k % 5), size=3)
+        K = np.array([[0, -a[2], a[1]], [a[2], 0, -a[0]], [-a[1], a[0], 0]])
+        R = p.R_gt @ (np.eye(3) + np.sin(np.linalg.norm(a)) / max(np.linalg.norm(a), 1e-12) * K
+                      + (1 - np.cos(np.linalg.norm(a))) / max(np.linalg.norm(a), 1e-12) ** 2 * K @ K)
+        t = p.t_gt + rng.normal(scale=0.01 * (k % 3), size=3)
+        R32, t32 = R.astype(np.float32), t.astype(np.float32)
+        rts.append(np.concatenate([R32.ravel(), t32]))
+        mats.append((R32.astype(np.float64), t32.astype(np.float64)))
+    prm = trg.default_params(p.tau, 10, p.theta, scoring=scoring)
+    inl, sc = ctx.score_transforms(p.x, p.y, prm, np.stack(rts))
+    xmax = float(np.abs(p.x).max()) * np.sqrt(3)
+    ymax = float(np.abs(p.y).max()) * np.sqrt(3)
+    th = float(np.float32(p.theta))
+    for k, (R, t) in enumerate(mats):
+        # the oracle evaluates the same FP32 transform in FP64: only FP32 evaluation differs
+        delta = 16 * 2.0 ** -24 * (xmax + ymax + np.linalg.norm(t))
+        cnt, near = oracle.inliers(p.x, p.y, R, t, p.theta, band=max(delta, 1e-6))
+        assert abs(int(inl[k]) - cnt) <= near
+        want = oracle.score(p.x, p.y, R, t, p.theta, scoring)
+        if scoring == trg.SCORE_IN:
+            assert abs(sc[k] - want) <= near
+        else:
+            unit = th if scoring == trg.SCORE_MAE else th * th
+            tol = (delta if scoring == trg.SCORE_MAE else 2 * th * delta + delta ** 2) + 2.0 ** -22 * unit + 4 * 2.0 ** -24 * unit
+            assert abs(sc[k] - want) <= tol, (k, sc[k], want, tol)
+
+
+def _oracle_hypotheses(p, k1, scoring, graph_mode=0):
+    _, _, _, (cl, va) = oracle_stages(p.x, p.y, p.tau, k1, 2, graph_mode=graph_mode)
+    orc = oracle.register(p.x, p.y, p.tau, k1, p.theta, graph_mode=graph_mode, scoring=scoring)
+    m = len(va)
+    return orc, {"valid": orc.hyp_valid[:m], "R": orc.rt[:m, :9].reshape(-1, 3, 3), "t": orc.rt[:m, 9:12],
+                 "cliques": cl, "inliers": orc.in_counts[:m], "score": orc.scores[:m]}
+
+
+@pytest.mark.parametrize("scoring", [trg.SCORE_IN, trg.SCORE_MAE, trg.SCORE_MSE])
+def test_ranking_records_match_oracle(ctx, scoring):
+    """TQRR / ICRR / RR / TKRR@K of the GPU hypotheses equal those of the
+    oracle's hypotheses wherever the oracle's ranking is not decided by
+    differences below the parity tolerance."""
+    from paper_2507_01439_gb300 import ranking
+    ks = (2, 3, 5, 50)
+    stable_cmp = 0
+    for seed in range(10):
+        shape = "indoor" if seed % 2 else "outdoor"
+        p = synth.make_problem(shape, 1200 + 300 * seed, 0.03 + 0.02 * seed, 900 + seed)
+        prm = trg.default_params(p.tau, 300, p.theta, scoring=scoring)
+        rec_g = ranking.evaluate(ctx, p.x, p.y, prm, p.R_gt, p.t_gt, p.inlier, p.re_deg, p.te_m, ks)
+        # re-register so the stage buffers are this problem's (evaluate scored the ground truth after it)
+        ctx.register(p.x, p.y, prm)
+        hg = ranking.hypotheses(ctx, prm)
+        orc, ho = _oracle_hypotheses(p, 300, scoring)
+        gt_o = oracle.score(p.x, p.y, p.R_gt.astype(np.float32), p.t_gt.astype(np.float32), p.theta, scoring)
+        order_o = ranking.rank(ho["score"], ho["valid"], scoring)
+        rec_o = ranking.problem_record(ho, order_o, gt_o, scoring, p.R_gt, p.t_gt, p.inlier, p.re_deg, p.te_m, ks)
+        if scoring == trg.SCORE_IN:
+            tol = orc.near_counts[:len(ho["valid"])].astype(np.float64)
+        else:
+            from parity_util import score_tolerances
+            tol = score_tolerances(ctx, p.x, p.y, p.theta, orc, scoring)
+        so = ho["score"]
+        # the GPU order is an order of the oracle's scores up to the tolerances
+        order_g = ranking.rank(hg["score"], hg["valid"], scoring)
+        for a, b in zip(order_g[:-1], order_g[1:]):
+            if scoring == trg.SCORE_IN:
+                assert so[a] + tol[a] + tol[b] >= so[b]
+            else:
+                assert so[a] <= so[b] + tol[a] + tol[b]
+        if scoring == trg.SCORE_IN:
+            # equal inlier numbers give equal orders (same tie rule); otherwise skip the problem
+            if not np.array_equal(hg["inliers"][ho["valid"]], ho["inliers"][ho["valid"]]):
+                continue
+            assert np.array_equal(order_g, order_o)
+            stable = lambda k: True
+        else:
+            T = float(np.max(tol[ho["valid"]]))
+            def stable(k):
+                # no hypothesis can cross the boundary after position k
+                return k >= len(order_o) or so[order_o[k]] - so[order_o[k - 1]] > 2 * T
+        top = order_o[0]
+        for key in ["RR", "ICRR"] + [f"TKRR@{k}" for k in ks]:
+            k = 1 if key in ("RR", "ICRR") else int(key.split("@")[1])
+            if stable(k):
+                assert rec_g[key] == rec_o[key], (seed, key)
+                stable_cmp += 1
+        if stable(1) and abs(so[top] - gt_o) > tol[top] + 1e-6 * abs(gt_o) + (0 if scoring else 0.5):
+            assert rec_g["TQRR"] == rec_o["TQRR"], seed
+            stable_cmp += 1
+    print("ranking scoring", scoring, "stable comparisons", stable_cmp)
+    assert stable_cmp >= 15
