@@ -71,6 +71,8 @@ def _load():
         lib.orc_cliques.argtypes = [P, i32, P, P, i32, i32, i32, P, P]
         lib.orc_kabsch.argtypes = [P, P, P, P, P]
         lib.orc_kabsch.restype = i32
+        lib.orc_kabsch_n.argtypes = [P, P, i32, P, P, P]
+        lib.orc_kabsch_n.restype = i32
         lib.orc_svd3.argtypes = [P, P, P, P]
         lib.orc_inliers.argtypes = [P, P, i32, P, P, ctypes.c_float, ctypes.c_double, P]
         lib.orc_inliers.restype = i32
@@ -150,6 +152,15 @@ def kabsch(xs, ys):
     ys = np.ascontiguousarray(ys, dtype=np.float64)
     R = np.zeros((3, 3)); t = np.zeros(3); k = np.zeros(1)
     ok = _load().orc_kabsch(_p(xs), _p(ys), _p(R), _p(t), _p(k))
+    return bool(ok), R, t, float(k[0])
+
+
+def kabsch_n(xs, ys):
+    """Kabsch on m >= 3 matches: (valid, R [3,3], t [3], kappa)."""
+    xs = np.ascontiguousarray(xs, dtype=np.float64)
+    ys = np.ascontiguousarray(ys, dtype=np.float64)
+    R = np.zeros((3, 3)); t = np.zeros(3); k = np.zeros(1)
+    ok = _load().orc_kabsch_n(_p(xs), _p(ys), xs.shape[0], _p(R), _p(t), _p(k))
     return bool(ok), R, t, float(k[0])
 
 

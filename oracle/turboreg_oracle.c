@@ -252,16 +252,21 @@ static double det3(const double* M)
          + M[2] * (M[3] * M[7] - M[4] * M[6]);
 }
 
-int32_t orc_kabsch(const double* xs, const double* ys, double* R, double* t, double* kappa)
+int32_t orc_kabsch_n(const double* xs, const double* ys, int32_t m, double* R, double* t, double* kappa)
 {
-    double cx[3], cy[3];
+    double cx[3] = {0, 0, 0}, cy[3] = {0, 0, 0};
+    for (int32_t a = 0; a < m; ++a)
+        for (int d = 0; d < 3; ++d) {
+            cx[d] += xs[a * 3 + d];
+            cy[d] += ys[a * 3 + d];
+        }
     for (int d = 0; d < 3; ++d) {
-        cx[d] = ((xs[0 * 3 + d] + xs[1 * 3 + d]) + xs[2 * 3 + d]) / 3.0;
-        cy[d] = ((ys[0 * 3 + d] + ys[1 * 3 + d]) + ys[2 * 3 + d]) / 3.0;
+        cx[d] /= (double)m;
+        cy[d] /= (double)m;
     }
     /* cross-covariance H = sum_a (x_a - cx)(y_a - cy)^T */
     double H[9] = {0};
-    for (int a = 0; a < 3; ++a)
+    for (int32_t a = 0; a < m; ++a)
         for (int r = 0; r < 3; ++r)
             for (int c = 0; c < 3; ++c)
                 H[r * 3 + c] += (xs[a * 3 + r] - cx[r]) * (ys[a * 3 + c] - cy[c]);
@@ -277,7 +282,12 @@ int32_t orc_kabsch(const double* xs, const double* ys, double* R, double* t, dou
                          + d * V[r * 3 + 2] * U[c * 3 + 2];
     for (int r = 0; r < 3; ++r)
         t[r] = cy[r] - (R[r * 3 + 0] * cx[0] + R[r * 3 + 1] * cx[1] + R[r * 3 + 2] * cx[2]);
-    return (s[0] > 0 && s[1] > 1e-12 * s[0]) ? 1 : 0;
+    return (m >= 3 && s[0] > 0 && s[1] > 1e-12 * s[0]) ? 1 : 0;
+}
+
+int32_t orc_kabsch(const double* xs, const double* ys, double* R, double* t, double* kappa)
+{
+    return orc_kabsch_n(xs, ys, 3, R, t, kappa);
 }
 
 /* ------------------------------------------------------------------ */

@@ -14,6 +14,7 @@
  *   orc_cliques  Eq. 5-7, Alg. 1  per-pivot top-K2 TurboCliques, Alg. 2 layout,
  *                on the O2Graph (Def. 2) or the undirected SC^2 graph
  *   orc_kabsch   Sec. 3.5  least-squares rigid transform from 3 matches (SVD)
+ *   orc_kabsch_n the same over m matches (App. A.2 compares 3- and 10-cliques)
  *   orc_inliers  Sec. 3.5 / Eq. 9  inlier number of one hypothesis
  *   orc_score    App. (ranking study, Table 6)  IN, MAE or MSE of one hypothesis
  *   orc_register the whole path, Eq. 1 -> Eq. 9
@@ -83,6 +84,12 @@ void orc_cliques(const int32_t* S, int32_t n, const int32_t* pi, const int32_t* 
  * centred cross-covariance.  Returns 1 if valid (s2 > 1e-12 s1), else 0. */
 int32_t orc_kabsch(const double* xs, const double* ys, double* R, double* t,
                    double* kappa);
+
+/* Kabsch on m >= 3 matches (the same least-squares problem over a larger
+ * clique, as in the 3-clique vs 10-clique comparison of the appendix):
+ * xs, ys row-major [m][3].  Valid if s2 > 1e-12 s1 (not collinear). */
+int32_t orc_kabsch_n(const double* xs, const double* ys, int32_t m, double* R, double* t,
+                     double* kappa);
 
 /* Jacobi SVD of a 3x3 matrix H = U diag(s) V^T, s descending. */
 void orc_svd3(const double* H, double* U, double* s, double* V);

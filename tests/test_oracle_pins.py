@@ -442,6 +442,44 @@ def test_kabsch_degenerate_triangles_invalid():
     assert not ok
 
 
+def test_kabsch_n_recovers_noiseless_and_agrees_with_horn():
+    rng = _rng(19)
+    for m in (4, 10, 25):
+        for _ in range(40):
+            R = _rand_rot(rng)
+            t = rng.uniform(-3, 3, 3)
+            xs = rng.uniform(-5, 5, (m, 3))
+            ok, Re, te, _ = oracle.kabsch_n(xs, xs @ R.T + t)
+            assert ok and np.abs(Re - R).max() < 1e-9 and np.abs(te - t).max() < 1e-9
+            ys = xs @ R.T + t + rng.normal(scale=0.3, size=(m, 3))
+            ok, Re, te, kappa = oracle.kabsch_n(xs, ys)
+            Rh, th = _horn(xs, ys)
+            assert ok and np.abs(Re - Rh).max() < 1e-9 * max(1.0, kappa)
+            assert np.abs(te - th).max() < 1e-8 * max(1.0, kappa)
+            assert abs(np.linalg.det(Re) - 1) < 1e-12
+            # the matches' order does not matter
+            perm = rng.permutation(m)
+            ok2, Rp, tp, _ = oracle.kabsch_n(xs[perm], ys[perm])
+            assert ok2 and np.abs(Rp - Re).max() < 1e-9 * max(1.0, kappa)
+
+
+def test_kabsch_n_mirrored_cloud_and_degenerate():
+    rng = _rng(20)
+    xs = rng.uniform(-5, 5, (10, 3))
+    ys = xs.copy()
+    ys[:, 2] *= -1                         # a reflection: no proper rotation fits 10 generic points
+    ok, Re, te, _ = oracle.kabsch_n(xs, ys)
+    Rh, th = _horn(xs, ys)
+    assert ok and abs(np.linalg.det(Re) - 1) < 1e-12 and np.abs(Re - Rh).max() < 1e-8
+    line = np.outer(np.arange(10.0), [1.0, 2.0, -1.0])
+    assert not oracle.kabsch_n(line, line + 1)[0]
+    # three points: identical to the 3-point routine
+    tri = rng.uniform(-5, 5, (3, 3))
+    tri_y = tri @ _rand_rot(rng).T + rng.normal(scale=0.1, size=(3, 3))
+    a, b = oracle.kabsch(tri, tri_y), oracle.kabsch_n(tri, tri_y)
+    assert a[0] == b[0] and np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
+
+
 # --------------------------------------------------------------------------
 # Sec. 3.5: inlier number
 # --------------------------------------------------------------------------
