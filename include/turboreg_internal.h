@@ -71,6 +71,24 @@ int turboreg_score_transforms(turboreg_ctx* ctx, const float* src, const float* 
                               const turboreg_params* params, const float* rt, int32_t m,
                               int32_t* out_in, uint64_t* out_units);
 
+/* Kabsch of caller-given cliques (Sec. 3.5; the 3-clique vs 10-clique
+ * comparison of App. A.2): for each of m tuples of k match indices, the
+ * proper rotation R and translation t minimising sum ||R x + t - y||^2 over
+ * the tuple's matches.  k = 3 runs the registration path's kernels (FP32
+ * closed form, FP64 above params->kappa_fp64); 4 <= k <= 32 runs Horn's
+ * quaternion method with Jacobi eigen-decomposition in FP64.
+ * src, dst: float32 [n][3], host or device.  idx: HOST int32 [m][k], every
+ * index in [0, n).  m >= 1 and m * k <= 4 * TURBOREG_K1_MAX * TURBOREG_K2_MAX.
+ * Outputs (HOST): out_rt[m][12] = R (row-major) then t; out_valid[m] = 1 for
+ * a valid transform, 0 for a degenerate tuple (collinear or repeated points,
+ * s2 <= 1e-12 s1), in which case out_rt is unspecified.  Reuses problem slot 0
+ * (overwrites the inspection buffers of the previous register call).
+ * Errors: INVALID_ARG (null pointer, k or m out of range, index out of range,
+ * bad params), TOO_FEW, NONFINITE, CUDA. */
+int turboreg_kabsch_cliques(turboreg_ctx* ctx, const float* src, const float* dst, int32_t n,
+                            const turboreg_params* params, const int32_t* idx, int32_t k, int32_t m,
+                            float* out_rt, int32_t* out_valid);
+
 /* ---- learned proposal (project extension; the paper ranks pivots by SC^2 alone) ----
  * A per-correspondence inlier-scoring MLP 8 -> 64 -> 128 -> 64 -> 1 (ReLU,
  * sigmoid output), BF16 weights and activations, FP32 accumulation.  Its

@@ -44,6 +44,7 @@ EXPORTED = (
     "turboreg_set_proposal_model", "turboreg_features", "turboreg_mlp_create", "turboreg_mlp_destroy",
     "turboreg_mlp_get_params", "turboreg_mlp_set_params", "turboreg_mlp_get_state", "turboreg_mlp_set_state",
     "turboreg_mlp_forward", "turboreg_mlp_grad", "turboreg_mlp_train_step", "turboreg_score_transforms",
+    "turboreg_kabsch_cliques",
 )
 TURBOREG_MLP_PARAMS = 17217
 TURBOREG_NOALLOC_MAX_N = 8192
@@ -104,6 +105,8 @@ def load_library(path: str = LIB_PATH):
     F = ctypes.POINTER(ctypes.c_float)
     lib.turboreg_score_transforms.argtypes = [P, P, P, i32, ctypes.POINTER(turboreg_params), P, i32, P, P]
     lib.turboreg_score_transforms.restype = ctypes.c_int
+    lib.turboreg_kabsch_cliques.argtypes = [P, P, P, i32, ctypes.POINTER(turboreg_params), P, i32, i32, P, P]
+    lib.turboreg_kabsch_cliques.restype = ctypes.c_int
     lib.turboreg_set_proposal_model.argtypes = [P, P]
     lib.turboreg_features.argtypes = [P, P, P, i32, ctypes.POINTER(turboreg_params), P]
     lib.turboreg_mlp_create.argtypes = [ctypes.c_int, i32, ctypes.c_uint64, P, ctypes.POINTER(P)]
@@ -300,6 +303,26 @@ class TurboReg:
         if rc != OK:
             raise RuntimeError(f"turboreg_score_transforms failed: {status_string(rc)}")
         return inl, score_values(units, inl, params, n)
+
+    def kabsch_cliques(self, src, dst, idx, params=None):
+        """Kabsch of index tuples idx [m, k] (3 <= k <= 32): (rt float32 [m, 12]
+        = R row-major then t, valid bool [m]).  k = 3 runs the registration
+        path's closed form; k >= 4 runs Horn's method in FP64."""
+        _check_points(src)
+        _check_points(dst, src.shape[0])
+        idx = np.ascontiguousarray(idx, dtype=np.int32)
+        if idx.ndim != 2:
+            raise ValueError("idx must be [m, k]")
+        m, k = idx.shape
+        prm = params if params is not None else default_params(0.0, 1, 1.0)
+        rt = np.zeros((m, 12), dtype=np.float32)
+        valid = np.zeros(m, dtype=np.int32)
+        rc = self._lib.turboreg_kabsch_cliques(self.handle, _ptr(src), _ptr(dst), int(src.shape[0]),
+                                               ctypes.byref(prm), ctypes.c_void_p(idx.ctypes.data), k, m,
+                                               ctypes.c_void_p(rt.ctypes.data), ctypes.c_void_p(valid.ctypes.data))
+        if rc != OK:
+            raise RuntimeError(f"turboreg_kabsch_cliques failed: {status_string(rc)}")
+        return rt, valid.astype(bool)
 
     def set_proposal_model(self, params):
         w = np.ascontiguousarray(params, dtype=np.float32)

@@ -1002,6 +1002,93 @@ int turboreg_score_transforms(turboreg_ctx* c, const float* src, const float* ds
     return TURBOREG_OK;
 }
 
+int turboreg_kabsch_cliques(turboreg_ctx* c, const float* src, const float* dst, int32_t n,
+                            const turboreg_params* p, const int32_t* idx, int32_t k, int32_t m, float* out_rt,
+                            int32_t* out_valid)
+{
+    if (!c || !src || !dst || !p || !idx || !out_rt || !out_valid) return TURBOREG_ERR_INVALID_ARG;
+    const int64_t cap = 4ll * TURBOREG_K1_MAX * TURBOREG_K2_MAX;
+    if (k < 3 || k > 32 || m < 1 || static_cast<int64_t>(m) * k > cap) return TURBOREG_ERR_INVALID_ARG;
+    if (k == 3 && static_cast<int64_t>(m) > static_cast<int64_t>(TURBOREG_K1_MAX) * TURBOREG_K2_MAX)
+        return TURBOREG_ERR_INVALID_ARG;
+    if (n < 3) return TURBOREG_ERR_TOO_FEW;
+    for (int64_t q = 0; q < static_cast<int64_t>(m) * k; ++q)
+        if (idx[q] < 0 || idx[q] >= n) return TURBOREG_ERR_INVALID_ARG;
+    turboreg_params q = *p;
+    q.proposal = TURBOREG_PROPOSAL_PLAIN;
+    q.flags = 0;
+    q.graph_mode = TURBOREG_GRAPH_O2;
+    q.scoring = TURBOREG_SCORE_IN;
+    // k = 3 uses the path's hypothesis layout: m cliques as m pivots with K2 = 1
+    q.k1 = k == 3 ? (m < TURBOREG_K1_MAX ? m : TURBOREG_K1_MAX) : 1;
+    q.k2 = k == 3 ? (m + q.k1 - 1) / q.k1 : 1;
+    if (!(q.tau >= 0.f) || !std::isfinite(q.tau)) q.tau = 0.f;
+    if (!(q.inlier_thresh > 0.f) || !std::isfinite(q.inlier_thresh)) q.inlier_thresh = 1.f;
+    int rc = check_params(c, n, &q);
+    if (rc != TURBOREG_OK) return rc;
+    TR_CHECK(cudaSetDevice(c->device));
+    const size_t bytes = static_cast<size_t>(n) * 3 * sizeof(float);
+    const float* s_in = src;
+    const float* d_in = dst;
+    if (!is_device_ptr(src)) {
+        if (!host_finite(src, static_cast<size_t>(n) * 3)) return TURBOREG_ERR_NONFINITE;
+        TR_CHECK(cudaMemcpyAsync(c->ws.in_src, src, bytes, cudaMemcpyHostToDevice, c->stream));
+        s_in = c->ws.in_src;
+    }
+    if (!is_device_ptr(dst)) {
+        if (!host_finite(dst, static_cast<size_t>(n) * 3)) return TURBOREG_ERR_NONFINITE;
+        TR_CHECK(cudaMemcpyAsync(c->ws.in_dst, dst, bytes, cudaMemcpyHostToDevice, c->stream));
+        d_in = c->ws.in_dst;
+    }
+    Plan pl;
+    const int64_t off0 = 0;
+    const turboreg_params* pq = &q;
+    rc = build_plan(c, 1, &off0, &n, &pq, pl);
+    if (rc != TURBOREG_OK) return rc;
+    Batch bt;
+    rc = upload_desc(c, 1, c->ws.desc, bt, c->stream);
+    if (rc != TURBOREG_OK) return rc;
+    const ProbView& v = c->ws.h_views[0];
+    TR_CHECK(cudaMemsetAsync(c->ws.ctl, 0, sizeof(Ctl), c->stream));
+    launch_pack(bt, pl.tot[ST_PACK], s_in, d_in, c->stream);
+    if (k == 3) {
+        // cliques (i, j, z, valid) in slots 0..m-1; slots up to k1*k2 are empty
+        const int32_t slots = q.k1 * q.k2;
+        std::vector<int32_t> cl(static_cast<size_t>(slots) * 4, 0);
+        for (int32_t h = 0; h < m; ++h) {
+            cl[4 * h + 0] = idx[3 * h + 0];
+            cl[4 * h + 1] = idx[3 * h + 1];
+            cl[4 * h + 2] = idx[3 * h + 2];
+            cl[4 * h + 3] = 1;
+        }
+        TR_CHECK(cudaMemcpyAsync(v.cliques, cl.data(), cl.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+                                 c->stream));
+        TR_CHECK(cudaMemcpyAsync(&v.ctl->n_pivots, &q.k1, sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
+        launch_kabsch(bt, pl.tot[ST_KABSCH], c->stream);
+        launch_kabsch_fp64(bt, pl.tot[ST_KABSCH64], c->stream);
+    } else {
+        // the tuples go to the (otherwise unused here) clique buffer, as int32 [m][k]
+        int32_t* didx = reinterpret_cast<int32_t*>(v.cliques);
+        TR_CHECK(cudaMemcpyAsync(didx, idx, sizeof(int32_t) * m * k, cudaMemcpyHostToDevice, c->stream));
+        launch_kabsch_n(v, didx, k, m, c->stream);
+    }
+    TR_CHECK(cudaGetLastError());
+    std::vector<float> rt(static_cast<size_t>(m) * 16);
+    TR_CHECK(cudaMemcpyAsync(rt.data(), v.rt, rt.size() * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+    Ctl hc;
+    TR_CHECK(cudaMemcpyAsync(&hc, c->ws.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, c->stream));
+    TR_CHECK(cudaStreamSynchronize(c->stream));
+    if (hc.err & TR_ERR_NONFINITE) return TURBOREG_ERR_NONFINITE;
+    if (hc.err) return TURBOREG_ERR_TIMEOUT;
+    for (int32_t h = 0; h < m; ++h) {
+        int32_t flags;
+        std::memcpy(&flags, &rt[static_cast<size_t>(h) * 16 + 13], sizeof(flags));
+        out_valid[h] = (flags & 1) ? 1 : 0;
+        std::memcpy(out_rt + static_cast<size_t>(h) * 12, &rt[static_cast<size_t>(h) * 16], 12 * sizeof(float));
+    }
+    return TURBOREG_OK;
+}
+
 int turboreg_features(turboreg_ctx* c, const float* src, const float* dst, int32_t n, const turboreg_params* p,
                       float* feat)
 {

@@ -509,6 +509,11 @@ void launch_verify(const Batch& b, int total, cudaStream_t s)
     verify_kernel<false><<<total, 128, 0, s>>>(ManyViews{b});
 }
 
+void launch_kabsch_fp64(const Batch& b, int total64, cudaStream_t s)
+{
+    kabsch_fp64_kernel<<<total64, 32, 0, s>>>(ManyViews{b});
+}
+
 void launch_kabsch_fp64_verify(const Batch& b, int total64, int total_verify, cudaStream_t s)
 {
     kabsch_fp64_kernel<<<total64, 32, 0, s>>>(ManyViews{b});

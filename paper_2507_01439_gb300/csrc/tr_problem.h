@@ -123,6 +123,9 @@ void launch_topk_rest(const Batch& b, const int32_t tot[kNumBatchStages], int ma
 void launch_pgs(const Batch& b, int total, int k2_max, cudaStream_t s);
 void launch_kabsch(const Batch& b, int total, cudaStream_t s);
 void launch_kabsch_fp64_verify(const Batch& b, int total64, int total_verify, cudaStream_t s);
+void launch_kabsch_fp64(const Batch& b, int total64, cudaStream_t s);
+// Kabsch of caller-given k-cliques (k >= 4) into v.rt; idx [m][k] on the device.
+void launch_kabsch_n(const ProbView& v, const int32_t* idx, int k, int m, cudaStream_t s);
 void launch_verify(const Batch& b, int total, cudaStream_t s);
 void launch_finalize(const Batch& b, cudaStream_t s);
 

@@ -214,3 +214,42 @@ def test_ranking_records_match_oracle(ctx, scoring):
             stable_cmp += 1
     print("ranking scoring", scoring, "stable comparisons", stable_cmp)
     assert stable_cmp >= 15
+
+
+@pytest.mark.parametrize("k", [3, 4, 10, 32])
+def test_kabsch_cliques_matches_oracle(ctx, k):
+    """Kabsch of caller-given k-tuples (App. A.2 compares 3- and 10-cliques):
+    k = 3 through the path's FP32 closed form, k >= 4 through Horn's method in
+    FP64, against the oracle's FP64 SVD."""
+    p = synth.make_problem("indoor", 2000, 0.2, 21 + k)
+    rng = np.random.default_rng(k)
+    m = 700
+    idx = np.stack([rng.choice(p.n, k, replace=False) for _ in range(m)]).astype(np.int32)
+    # inlier-only tuples too (small residuals, the regime of the study)
+    inl = np.flatnonzero(p.inlier)
+    idx[:200] = np.stack([rng.choice(inl, k, replace=False) for _ in range(200)])
+    # degenerate tuples: all matches of the tuple on one line (x and y)
+    for r in range(200, 210):
+        a, b = p.x[idx[r, 0]], p.x[idx[r, 1]]
+        for c in range(2, k):
+            p.x[idx[r, c]] = a + (b - a) * (c / k)
+            p.y[idx[r, c]] = p.y[idx[r, 0]] + (p.y[idx[r, 1]] - p.y[idx[r, 0]]) * (c / k)
+    rt, valid = ctx.kabsch_cliques(p.x, p.y, idx, trg.default_params(p.tau, 10, p.theta))
+    xmax = float(np.abs(p.x).max()) * np.sqrt(3)
+    worst = 0.0
+    for h in range(m):
+        ok, Ro, to, kap = oracle.kabsch_n(p.x[idx[h]].astype(np.float64), p.y[idx[h]].astype(np.float64))
+        assert bool(valid[h]) == ok, (h, kap)
+        if not ok:
+            continue
+        dR = float(np.linalg.norm(rt[h, :9].reshape(3, 3).astype(np.float64) - Ro))
+        dt = float(np.linalg.norm(rt[h, 9:].astype(np.float64) - to))
+        tolR = 4e-6 * (1 + kap) + 1e-6 if k == 3 else 1e-6 + 1e-12 * kap
+        assert dR <= tolR, (h, dR, kap)
+        assert dt <= tolR * (1 + xmax) + 1e-5, (h, dt)
+        worst = max(worst, dR)
+    print("kabsch k", k, "max |dR|", worst)
+    bad = idx.copy()
+    bad[3, 1] = p.n
+    with pytest.raises(RuntimeError):
+        ctx.kabsch_cliques(p.x, p.y, bad)
