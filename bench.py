@@ -14,6 +14,10 @@ value: registrations/s with inputs resident in device memory, CUDA events on
        between timed steps outside the events.
 e2e:   the same metric through the C ABI with pinned HOST inputs: the H2D
        copies of x, y and the D2H copy of the result are inside the events.
+roofline: the SC^2 GEMM's mean duration from CUDA events recorded inside the
+       replayed graph around that stage, in a third timed pass of the same
+       workload (those in-graph events add ~40 us per registration, so the
+       two throughput passes run without them).
 Multi-GPU: independent replicas per rank (the path does not shard); value is
 all ranks' registrations / the slowest rank's time.
 --impl reference: the FP64 CPU oracle as the reference arm, same workload.
@@ -406,11 +410,13 @@ def run_clique_stability(trg, per_tau=240):
 
 def run_sc2_paths(trg, probs, dx, dy):
     """SC^2 stage (with the edge-weight histogram and the pivot threshold) on
-    the benchmark workload: the tcgen05 FP8 GEMM vs the CUDA-core bitset
-    AND + popcount path (same integers); in-graph CUDA-event times."""
+    the benchmark workload: the tcgen05 FP8 GEMM (2-CTA clusters sharing B,
+    the default; and independent CTAs) vs the CUDA-core bitset AND + popcount
+    path (same integers); in-graph CUDA-event times."""
     out = {}
     with trg.TurboReg(max_n=5000, max_batch=1) as ctx:
-        for name, fl in (("tcgen05_gemm", 0), ("bitset_popcount", trg.FLAG_SC2_BITSET)):
+        for name, fl in (("tcgen05_gemm", 0), ("tcgen05_gemm_single_cta", trg.FLAG_SC2_SINGLE_CTA),
+                         ("bitset_popcount", trg.FLAG_SC2_BITSET)):
             prm = trg.default_params(0.1, 2000, 0.1, flags=trg.FLAG_STAGE_TIMES | fl)
             ms = []
             for k in range(24):
@@ -444,7 +450,10 @@ def run_ours(args):
     dy = [torch.from_numpy(p.y).cuda() for p in probs]
     hx = [torch.from_numpy(p.x).pin_memory() for p in probs]
     hy = [torch.from_numpy(p.y).pin_memory() for p in probs]
-    prm = trg.default_params(0.1, 2000, 0.1, flags=trg.FLAG_STAGE_TIMES)
+    prm = trg.default_params(0.1, 2000, 0.1)
+    # roofline pass only: CUDA events inside the graph around every stage (they cost
+    # ~40 us per registration, so the throughput passes run without them)
+    prm_ev = trg.default_params(0.1, 2000, 0.1, flags=trg.FLAG_STAGE_TIMES)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     torch.cuda.synchronize()
 
@@ -459,8 +468,9 @@ def run_ours(args):
     def timed(kind, steps, warmup):
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         sc2 = []
+        p_k = prm_ev if kind == "stages" else prm
         for k in range(warmup):
-            ctx.register(dx[k % 8], dy[k % 8], prm)
+            ctx.register(dx[k % 8], dy[k % 8], p_k)
         torch.cuda.synchronize()
         if ws > 1:
             dist.barrier()
@@ -469,12 +479,13 @@ def run_ours(args):
             with torch.cuda.stream(stream):
                 flush.zero_()
                 ev[k][0].record(stream)
-            if kind == "device":
-                ctx.register(dx[k % 8], dy[k % 8], prm)
+            if kind == "host":
+                ctx.register(hx[k % 8], hy[k % 8], p_k)
             else:
-                ctx.register(hx[k % 8], hy[k % 8], prm)
+                ctx.register(dx[k % 8], dy[k % 8], p_k)
             ev[k][1].record(stream)
-            sc2.append(ctx.stage_times()["sc2"])
+            if kind == "stages":
+                sc2.append(ctx.stage_times()["sc2"])
         torch.cuda.synchronize()
         if ws > 1:
             dist.barrier()
@@ -485,8 +496,9 @@ def run_ours(args):
     sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.3)
-    ms_dev, sc2_ms = timed("device", args.steps, args.warmup)
+    ms_dev, _ = timed("device", args.steps, args.warmup)
     ms_host, _ = timed("host", args.steps, args.warmup)
+    ms_stages, sc2_ms = timed("stages", max(20, args.steps // 4), args.warmup)
     clocks = sampler.stop()
 
     tot_dev = sum(ms_dev) / 1e3
@@ -519,7 +531,7 @@ def run_ours(args):
             "config": dict(WORKLOAD, parallelism=f"replicas x{ws}"),
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 2 * 5000 * 12,
                     "d2h_bytes_per_step": ctypes.sizeof(trg.turboreg_result)},
-            "gpu_launches": LAUNCHES_PER_STEP * args.steps * 2,
+            "gpu_launches": LAUNCHES_PER_STEP * (2 * args.steps + len(ms_stages)),
             "roofline": roofline, "clocks": clocks,
             "success_rate_check": f"{ok}/8 problems RE<15deg TE<0.3m"}
     if not args.no_batched:

@@ -75,6 +75,9 @@ typedef enum {
 #define TURBOREG_FLAG_STAGE_TIMES 0x2u /* record per-stage CUDA-event times (turboreg_stage_times) */
 #define TURBOREG_FLAG_NO_GRAPH 0x4u    /* launch the stages one by one instead of replaying the
                                           captured CUDA graph of this problem shape */
+#define TURBOREG_FLAG_SC2_SINGLE_CTA 0x8u /* SC^2 GEMM on independent CTAs; by default pairs of CTAs
+                                             (thread-block clusters) share the B operand tile by TMA
+                                             multicast (same integers either way) */
 
 typedef struct {
     float tau;            /* compatibility threshold of Eq. 1, metres, >= 0 */

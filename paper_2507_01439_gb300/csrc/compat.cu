@@ -126,6 +126,7 @@ __device__ __forceinline__ uint4 bits16_to_fp8(uint32_t b16)
 
 __global__ void __launch_bounds__(kThreads) compat_kernel(ManyViews vs)
 {
+    pdl_wait();
     __shared__ __align__(128) float4 srow[kT][2];     // row points (x0,x1,x2,y0 | y1,y2,-,-)
     __shared__ uint16_t colpart[8][kT];               // per warp: 16-row mask of each column
     __shared__ __align__(8) uint64_t bar;
@@ -264,7 +265,7 @@ void launch_pack(const Batch& b, int total, const float* src, const float* dst, 
 
 void launch_compat(const Batch& b, int total, cudaStream_t s)
 {
-    compat_kernel<<<total, kThreads, 0, s>>>(ManyViews{b});
+    launch_pdl(compat_kernel, total, kThreads, 0, s, ManyViews{b});
 }
 
 }  // namespace tr

@@ -172,6 +172,7 @@ __device__ __forceinline__ void load_clique(const ProbView& v, const int4 cl, fl
 // the bound (or whose FP32 frames are undefined) go to a compact list.
 __global__ void __launch_bounds__(128) kabsch_kernel(ManyViews vs)
 {
+    pdl_wait();
     int lb;
     const ProbView v = vs.get(ST_KABSCH, blockIdx.x, lb);
     const int h = lb * blockDim.x + threadIdx.x;
@@ -206,6 +207,7 @@ __global__ void __launch_bounds__(128) kabsch_kernel(ManyViews vs)
 // slow FP64 pipe runs on dense warps instead of on every warp that holds one.
 __global__ void __launch_bounds__(32) kabsch_fp64_kernel(ManyViews vs)
 {
+    pdl_wait();
     int lb;
     const ProbView v = vs.get(ST_KABSCH64, blockIdx.x, lb);
     const int k = lb * blockDim.x + threadIdx.x;
@@ -392,6 +394,7 @@ __device__ __forceinline__ void verify_body(const ProbView& v, int lb, VerifySha
 template <bool kList>
 __global__ void __launch_bounds__(128) verify_kernel(ManyViews vs)
 {
+    pdl_wait();
     __shared__ __align__(16) VerifyShared sh;
     int lb;
     const ProbView v = vs.get(ST_VERIFY, blockIdx.x, lb);
@@ -422,6 +425,7 @@ __device__ __forceinline__ int key_hypothesis(const ProbView& v, unsigned long l
 
 __global__ void __launch_bounds__(1024) finalize_kernel(ManyViews vs)
 {
+    pdl_wait();
     int lb;
     const ProbView v = vs.get(ST_FINAL, blockIdx.x, lb);
     __shared__ unsigned long long sbest[32];
@@ -501,26 +505,26 @@ __global__ void __launch_bounds__(1024) finalize_kernel(ManyViews vs)
 
 void launch_kabsch(const Batch& b, int total, cudaStream_t s)
 {
-    kabsch_kernel<<<total, 128, 0, s>>>(ManyViews{b});
+    launch_pdl(kabsch_kernel, total, 128, 0, s, ManyViews{b});
 }
 
 void launch_verify(const Batch& b, int total, cudaStream_t s)
 {
-    verify_kernel<false><<<total, 128, 0, s>>>(ManyViews{b});
+    launch_pdl(verify_kernel<false>, total, 128, 0, s, ManyViews{b});
 }
 
 void launch_kabsch_fp64(const Batch& b, int total64, cudaStream_t s)
 {
-    kabsch_fp64_kernel<<<total64, 32, 0, s>>>(ManyViews{b});
+    launch_pdl(kabsch_fp64_kernel, total64, 32, 0, s, ManyViews{b});
 }
 
 void launch_kabsch_fp64_verify(const Batch& b, int total64, int total_verify, cudaStream_t s)
 {
-    kabsch_fp64_kernel<<<total64, 32, 0, s>>>(ManyViews{b});
-    verify_kernel<true><<<total_verify, 128, 0, s>>>(ManyViews{b});
+    launch_pdl(kabsch_fp64_kernel, total64, 32, 0, s, ManyViews{b});
+    launch_pdl(verify_kernel<true>, total_verify, 128, 0, s, ManyViews{b});
 }
 
-void launch_finalize(const Batch& b, cudaStream_t s) { finalize_kernel<<<b.num, 1024, 0, s>>>(ManyViews{b}); }
+void launch_finalize(const Batch& b, cudaStream_t s) { launch_pdl(finalize_kernel, b.num, 1024, 0, s, ManyViews{b}); }
 
 // Per-problem block counts of every stage.
 void stage_blocks(int32_t n, int32_t k1, int32_t k2, int32_t blocks[kNumBatchStages])

@@ -240,6 +240,7 @@ __global__ void __launch_bounds__(kRows, 1) mlp_fwd_kernel(const float* feat, in
 // Registration path: per problem, rows of its feature buffer -> its prob buffer.
 __global__ void __launch_bounds__(kRows, 1) mlp_proposal_kernel(ManyViews vs, const float* wbf)
 {
+    pdl_wait();
     extern __shared__ uint8_t smem_raw[];
     int lb;
     const ProbView v = vs.get(ST_MLP, blockIdx.x, lb);
@@ -250,6 +251,7 @@ __global__ void __launch_bounds__(kRows, 1) mlp_proposal_kernel(ManyViews vs, co
 // Features of one problem (one block of 1024 threads per problem).
 __global__ void __launch_bounds__(1024) features_kernel(ManyViews vs)
 {
+    pdl_wait();
     __shared__ float red[32][8];
     __shared__ float tot[8];
     int lb;
@@ -466,11 +468,11 @@ void launch_mlp_round(const float* w, float* wbf, cudaStream_t s)
     mlp_round_kernel<<<(kMlpParams + 255) / 256, 256, 0, s>>>(w, wbf);
 }
 
-void launch_features(const Batch& b, cudaStream_t s) { features_kernel<<<b.num, 1024, 0, s>>>(ManyViews{b}); }
+void launch_features(const Batch& b, cudaStream_t s) { launch_pdl(features_kernel, b.num, 1024, 0, s, ManyViews{b}); }
 
 void launch_mlp_proposal(const Batch& b, int total, const float* wbf, cudaStream_t s)
 {
-    mlp_proposal_kernel<<<total, kRows, kFwdSmem, s>>>(ManyViews{b}, wbf);
+    launch_pdl(mlp_proposal_kernel, total, kRows, kFwdSmem, s, ManyViews{b}, wbf);
 }
 
 void launch_mlp_forward(const float* feat, int m, const float* wbf, float* prob, float* z4, __nv_bfloat16* h1,

@@ -26,6 +26,7 @@ namespace {
 template <int K2C>
 __global__ void __launch_bounds__(256) pgs_kernel(ManyViews vs)
 {
+    pdl_wait();
     int lb;
     const ProbView v = vs.get(ST_PGS, blockIdx.x, lb);
     const int lane = threadIdx.x & 31;
@@ -126,11 +127,11 @@ void launch_pgs(const Batch& b, int total, int k2, cudaStream_t s)
 {
     const ManyViews vs{b};
     switch (k2) {
-        case 1: pgs_kernel<1><<<total, 256, 0, s>>>(vs); break;
-        case 2: pgs_kernel<2><<<total, 256, 0, s>>>(vs); break;
-        case 3: pgs_kernel<3><<<total, 256, 0, s>>>(vs); break;
-        case 4: pgs_kernel<4><<<total, 256, 0, s>>>(vs); break;
-        default: pgs_kernel<0><<<total, 256, 0, s>>>(vs); break;
+        case 1: launch_pdl(pgs_kernel<1>, total, 256, 0, s, vs); break;
+        case 2: launch_pdl(pgs_kernel<2>, total, 256, 0, s, vs); break;
+        case 3: launch_pdl(pgs_kernel<3>, total, 256, 0, s, vs); break;
+        case 4: launch_pdl(pgs_kernel<4>, total, 256, 0, s, vs); break;
+        default: launch_pdl(pgs_kernel<0>, total, 256, 0, s, vs); break;
     }
 }
 

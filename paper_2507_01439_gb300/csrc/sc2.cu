@@ -64,9 +64,19 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar)
 //   warps 2..9      epilogue of the previous tile while the next one runs
 // kSingle: one problem: the edge-weight histogram is kept in shared memory
 // and the last CTA to finish chooses the pivot threshold.
-template <bool kSingle>
+// kPair: clusters of two CTAs take the two 128-row halves (tiles 2u, 2u + 1)
+// of one 256 x 256 output block, which share the B operand: each CTA loads
+// one 128-row half of B and multicasts it into both CTAs' shared memory, so
+// each CTA reads 32 KB per K stage from L2 instead of 48 KB.  A stage may be
+// refilled only when both CTAs' MMAs have read it: the MMA issuers commit to
+// the `empty` barriers of both CTAs (count 2), and before exit each producer
+// waits for the last releases so no arrival targets a finished CTA.  Every
+// problem's tile count nb(nb + 1) is even and its two halves are adjacent,
+// so pairs never straddle problems or column blocks.
+template <bool kSingle, bool kPair>
 __global__ void __launch_bounds__(kThreads, 1) sc2_tcgen05_kernel(Batch bt, int total)
 {
+    pdl_wait();
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t* sA = smem;
@@ -85,7 +95,7 @@ __global__ void __launch_bounds__(kThreads, 1) sc2_tcgen05_kernel(Batch bt, int 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], 1);
+            mbar_init(&empty[s], kPair ? 2 : 1);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&tfull[b], 1);
@@ -98,15 +108,22 @@ __global__ void __launch_bounds__(kThreads, 1) sc2_tcgen05_kernel(Batch bt, int 
     if (warp == 0) tmem_alloc(tmem_slot, kTmemCols);
     tc_fence_before();
     __syncthreads();
+    if (kPair) cluster_sync_all();   // the peer's barriers are initialised before any multicast
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
     bool ok = true;
+    // work units: single tiles, or tile pairs (2u, 2u + 1) of a cluster
+    const int rank = kPair ? static_cast<int>(cluster_ctarank()) : 0;
+    const int u0 = kPair ? static_cast<int>(blockIdx.x >> 1) : static_cast<int>(blockIdx.x);
+    const int us = kPair ? static_cast<int>(gridDim.x >> 1) : static_cast<int>(gridDim.x);
+    const int nu = kPair ? total >> 1 : total;
 
     if (warp == 0) {
         if (lane == 0) {
             // ---------------- TMA producer ----------------
             int it = 0;
-            for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
+            for (int u = u0; u < nu && ok; u += us) {
+                const int t = kPair ? 2 * u + rank : u;
                 int lt;
                 const int p = locate(bt, ST_GEMM, t, lt);
                 const int KT = bt.views[p].n_pad / kSc2BK;
@@ -120,7 +137,20 @@ __global__ void __launch_bounds__(kThreads, 1) sc2_tcgen05_kernel(Batch bt, int 
                     if (!mbar_wait(&empty[s], ph ^ 1u)) { ok = false; break; }
                     mbar_arrive_expect_tx(&full[s], kABytes + kBBytes);
                     tma_load_2d(sA + s * kABytes, mA, kb * kSc2BK, bm * kSc2BM, &full[s]);
-                    tma_load_2d(sB + s * kBBytes, mB, kb * kSc2BK, bn * kSc2BN, &full[s]);
+                    if (kPair)   // this CTA's 128-row half of B, into both CTAs (A's map has 128-row boxes)
+                        tma_load_2d_mc(sB + s * kBBytes + rank * kABytes, mA, kb * kSc2BK,
+                                       bn * kSc2BN + rank * kSc2BM, &full[s], 0x3);
+                    else
+                        tma_load_2d(sB + s * kBBytes, mB, kb * kSc2BK, bn * kSc2BN, &full[s]);
+                }
+            }
+            if (kPair) {
+                // producer tail: wait for both MMAs' releases of the last uses of
+                // every stage, so no commit arrives after this CTA has exited
+                for (int q = 0; q < kStages; ++q, ++it) {
+                    const int s = it % kStages;
+                    const uint32_t ph = (it / kStages) & 1u;
+                    if (!mbar_wait(&empty[s], ph ^ 1u)) { ok = false; break; }
                 }
             }
         }
@@ -129,7 +159,8 @@ __global__ void __launch_bounds__(kThreads, 1) sc2_tcgen05_kernel(Batch bt, int 
         if (lane == 0) {
             // ---------------- MMA issuer ----------------
             int it = 0, tc = 0;
-            for (int t = blockIdx.x; t < total && ok; t += gridDim.x, ++tc) {
+            for (int u = u0; u < nu && ok; u += us, ++tc) {
+                const int t = kPair ? 2 * u + rank : u;
                 int lt;
                 const int p = locate(bt, ST_GEMM, t, lt);
                 const int KT = bt.views[p].n_pad / kSc2BK;
@@ -149,7 +180,10 @@ __global__ void __launch_bounds__(kThreads, 1) sc2_tcgen05_kernel(Batch bt, int 
                     for (int k = 0; k < kSc2BK / 32; ++k)   // K = 32 FP8 per MMA, 32-byte steps in the swizzle row
                         mma_f8f6f4(d, sdesc_k_sw128(a0 + k * 32), sdesc_k_sw128(b0 + k * 32), kIdesc,
                                    (kb | k) != 0 ? 1u : 0u);
-                    mma_commit(&empty[s]);
+                    if (kPair)
+                        mma_commit_mc(&empty[s], 0x3);   // releases the stage in both CTAs
+                    else
+                        mma_commit(&empty[s]);
                 }
                 if (!ok) break;
                 mma_commit(&tfull[buf]);
@@ -161,7 +195,8 @@ __global__ void __launch_bounds__(kThreads, 1) sc2_tcgen05_kernel(Batch bt, int 
         const int quarter = warp & 3;              // TMEM lanes this warp may access
         const int half = (warp - 2) >> 2;          // column half of the tile
         int tc = 0;
-        for (int t = blockIdx.x; t < total; t += gridDim.x, ++tc) {
+        for (int u = u0; u < nu; u += us, ++tc) {
+            const int t = kPair ? 2 * u + rank : u;
             int lt;
             const int p = locate(bt, ST_GEMM, t, lt);
             const ProbView v = bt.views[p];
@@ -236,6 +271,7 @@ __global__ void __launch_bounds__(kThreads, 1) sc2_tcgen05_kernel(Batch bt, int 
     if (!ok && lane == 0) atomicOr(&bt.views[0].ctl->err, TR_ERR_TIMEOUT);
     tc_fence_before();
     __syncthreads();
+    if (kPair) cluster_sync_all();   // neither CTA exits while the other may still signal it
     if (warp == 0) {
         tc_fence_after();
         tmem_dealloc(tmem, kTmemCols);
@@ -257,6 +293,7 @@ __global__ void __launch_bounds__(kThreads, 1) sc2_tcgen05_kernel(Batch bt, int 
 // CUDA-core alternative: block per row i; W_ij = popc(row_i & row_j) for j > i with G_ij.
 __global__ void __launch_bounds__(256) sc2_bitset_kernel(ManyViews vs)
 {
+    pdl_wait();
     extern __shared__ uint32_t srow[];
     int i;
     const ProbView v = vs.get(ST_BITSET, blockIdx.x, i);
@@ -292,6 +329,29 @@ __global__ void __launch_bounds__(256) sc2_bitset_kernel(ManyViews vs)
 }
 
 int g_sc2_sms = 0;
+int g_sc2_pair_clusters = 0;   // co-resident 2-CTA clusters of the pair kernel (0: use single CTAs)
+
+template <bool kSingle>
+cudaError_t launch_pair(const Batch& b, int total_tiles, size_t smem, cudaStream_t s)
+{
+    int grid = 2 * g_sc2_pair_clusters;
+    if (grid > total_tiles) grid = total_tiles;   // total_tiles is even
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(static_cast<unsigned>(grid));
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[2];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 2;
+    return cudaLaunchKernelEx(&cfg, sc2_tcgen05_kernel<kSingle, true>, b, total_tiles);
+}
 
 }  // namespace
 
@@ -301,10 +361,36 @@ cudaError_t sc2_tcgen05_setup()
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g_sc2_sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(sc2_tcgen05_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax);
+        e = cudaFuncSetAttribute(sc2_tcgen05_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kSmemMax);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(sc2_tcgen05_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(sc2_tcgen05_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  kPipeBytes + kBarBytes + 1024);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(sc2_tcgen05_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kSmemMax);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(sc2_tcgen05_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kPipeBytes + kBarBytes + 1024);
+    if (e == cudaSuccess) {
+        // how many 2-CTA clusters fit at once with the largest shared-memory request
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(2 * 256);
+        cfg.blockDim = dim3(kThreads);
+        cfg.dynamicSmemBytes = kSmemMax;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = 2;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int nc = 0;
+        if (cudaOccupancyMaxActiveClusters(&nc, sc2_tcgen05_kernel<true, true>, &cfg) == cudaSuccess)
+            g_sc2_pair_clusters = nc;
+        else
+            cudaGetLastError();   // no cluster support: the single-CTA kernel is used
+    }
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(sc2_bitset_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  TURBOREG_MAX_N / 8);
@@ -313,21 +399,28 @@ cudaError_t sc2_tcgen05_setup()
 
 // A single problem keeps its histogram in shared memory when it fits; a
 // batch (or a very large problem) uses global atomics.
-void launch_sc2_tcgen05(const Batch& b, int total_tiles, int max_n, cudaStream_t s)
+void launch_sc2_tcgen05(const Batch& b, int total_tiles, int max_n, bool pair, cudaStream_t s)
 {
     const int sms = g_sc2_sms > 0 ? g_sc2_sms : 148;
     const int grid = total_tiles < sms ? total_tiles : sms;
     const size_t base = kPipeBytes + kBarBytes + 1024;
     const size_t hist = static_cast<size_t>(max_n + 1) * 4;
-    if (b.num == 1 && base + hist <= static_cast<size_t>(kSmemMax))
-        sc2_tcgen05_kernel<true><<<grid, kThreads, base + hist, s>>>(b, total_tiles);
-    else
-        sc2_tcgen05_kernel<false><<<grid, kThreads, base, s>>>(b, total_tiles);
+    const bool single = b.num == 1 && base + hist <= static_cast<size_t>(kSmemMax);
+    if (pair && g_sc2_pair_clusters > 0) {
+        if (single)
+            launch_pair<true>(b, total_tiles, base + hist, s);
+        else
+            launch_pair<false>(b, total_tiles, base, s);
+    } else if (single) {
+        launch_pdl(sc2_tcgen05_kernel<true, false>, grid, kThreads, base + hist, s, b, total_tiles);
+    } else {
+        launch_pdl(sc2_tcgen05_kernel<false, false>, grid, kThreads, base, s, b, total_tiles);
+    }
 }
 
 void launch_sc2_bitset(const Batch& b, int total, cudaStream_t s)
 {
-    sc2_bitset_kernel<<<total, 256, TURBOREG_MAX_N / 8, s>>>(ManyViews{b});
+    launch_pdl(sc2_bitset_kernel, total, 256, TURBOREG_MAX_N / 8, s, ManyViews{b});
 }
 
 }  // namespace tr

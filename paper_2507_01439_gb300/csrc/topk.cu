@@ -64,6 +64,7 @@ __device__ __forceinline__ void for_row_chunks(const ProbView& v, int i, int lan
 template <class VS, bool kSmem>
 __global__ void __launch_bounds__(256) hist_kernel(VS vs)
 {
+    pdl_wait();
     extern __shared__ uint32_t sh[];
     int lb;
     const ProbView v = vs.get(ST_HIST, blockIdx.x, lb);
@@ -93,6 +94,7 @@ __global__ void __launch_bounds__(256) hist_kernel(VS vs)
 template <class VS>
 __global__ void __launch_bounds__(1024) select_kernel(VS vs)
 {
+    pdl_wait();
     __shared__ int sbuf[33];
     int lb;
     const ProbView v = vs.get(ST_SELECT, blockIdx.x, lb);
@@ -104,6 +106,7 @@ __global__ void __launch_bounds__(1024) select_kernel(VS vs)
 template <class VS>
 __global__ void __launch_bounds__(256) count_kernel(VS vs)
 {
+    pdl_wait();
     int lb;
     const ProbView v = vs.get(ST_COUNT, blockIdx.x, lb);
     const int lane = threadIdx.x & 31;
@@ -131,6 +134,7 @@ __global__ void __launch_bounds__(256) count_kernel(VS vs)
 template <class VS>
 __global__ void __launch_bounds__(1024) scan_rows_kernel(VS vs)
 {
+    pdl_wait();
     __shared__ int sbuf[33];
     int lb;
     const ProbView v = vs.get(ST_SCAN, blockIdx.x, lb);
@@ -166,6 +170,7 @@ __global__ void __launch_bounds__(1024) scan_rows_kernel(VS vs)
 template <class VS>
 __global__ void __launch_bounds__(256) emit_kernel(VS vs)
 {
+    pdl_wait();
     __shared__ int sg[8], se[8];
     int i;
     const ProbView v = vs.get(ST_EMIT, blockIdx.x, i);
@@ -243,6 +248,7 @@ __global__ void __launch_bounds__(256) emit_kernel(VS vs)
 template <class VS>
 __global__ void __launch_bounds__(256) rank_kernel(VS vs)
 {
+    pdl_wait();
     extern __shared__ uint64_t sk[];
     __shared__ int part[8][32];
     int lb;
@@ -289,9 +295,9 @@ template <class VS>
 void launch_hist_vs(const VS& vs, int total, int max_n, cudaStream_t s)
 {
     if (max_n + 1 <= kHistSmemMaxBins)
-        hist_kernel<VS, true><<<total, 256, (max_n + 1) * 4, s>>>(vs);
+        launch_pdl(hist_kernel<VS, true>, total, 256, (max_n + 1) * 4, s, vs);
     else
-        hist_kernel<VS, false><<<total, 256, 0, s>>>(vs);
+        launch_pdl(hist_kernel<VS, false>, total, 256, 0, s, vs);
 }
 
 }  // namespace
@@ -313,15 +319,15 @@ void launch_hist(const Batch& b, int total, int max_n, cudaStream_t s)
     launch_hist_vs(ManyViews{b}, total, max_n, s);
 }
 
-void launch_select(const Batch& b, cudaStream_t s) { select_kernel<<<b.num, 1024, 0, s>>>(ManyViews{b}); }
+void launch_select(const Batch& b, cudaStream_t s) { launch_pdl(select_kernel<ManyViews>, b.num, 1024, 0, s, ManyViews{b}); }
 
 void launch_topk_rest(const Batch& b, const int32_t tot[kNumBatchStages], int max_k1, cudaStream_t s)
 {
     const ManyViews vs{b};
-    count_kernel<<<tot[ST_COUNT], 256, 0, s>>>(vs);
-    scan_rows_kernel<<<b.num, 1024, 0, s>>>(vs);
-    emit_kernel<<<tot[ST_EMIT], 256, 0, s>>>(vs);
-    rank_kernel<<<tot[ST_RANK], 256, max_k1 * 8, s>>>(vs);
+    launch_pdl(count_kernel<ManyViews>, tot[ST_COUNT], 256, 0, s, vs);
+    launch_pdl(scan_rows_kernel<ManyViews>, b.num, 1024, 0, s, vs);
+    launch_pdl(emit_kernel<ManyViews>, tot[ST_EMIT], 256, 0, s, vs);
+    launch_pdl(rank_kernel<ManyViews>, tot[ST_RANK], 256, max_k1 * 8, s, vs);
 }
 
 // One problem passed by value (no device-side problem table).
@@ -329,11 +335,11 @@ void launch_topk_single(const ProbView& v, cudaStream_t s)
 {
     const OneView vs{v};
     launch_hist_vs(vs, (v.n + kHistRowsPerBlock - 1) / kHistRowsPerBlock, v.n, s);
-    select_kernel<<<1, 1024, 0, s>>>(vs);
-    count_kernel<<<(v.n + 7) / 8, 256, 0, s>>>(vs);
-    scan_rows_kernel<<<1, 1024, 0, s>>>(vs);
-    emit_kernel<<<v.n, 256, 0, s>>>(vs);
-    rank_kernel<<<(v.k1 + 31) / 32, 256, v.k1 * 8, s>>>(vs);
+    launch_pdl(select_kernel<OneView>, 1, 1024, 0, s, vs);
+    launch_pdl(count_kernel<OneView>, (v.n + 7) / 8, 256, 0, s, vs);
+    launch_pdl(scan_rows_kernel<OneView>, 1, 1024, 0, s, vs);
+    launch_pdl(emit_kernel<OneView>, v.n, 256, 0, s, vs);
+    launch_pdl(rank_kernel<OneView>, (v.k1 + 31) / 32, 256, v.k1 * 8, s, vs);
 }
 
 }  // namespace tr

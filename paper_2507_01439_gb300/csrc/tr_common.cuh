@@ -96,6 +96,36 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
 }
 
 // ---------------------------------------------------------------------------
+// Programmatic dependent launch.  Pipeline kernels are launched with
+// cudaLaunchAttributeProgrammaticStreamSerialization, so a kernel's launch
+// is processed while its predecessor drains; each kernel calls pdl_wait()
+// before it touches memory, which returns once the predecessor grid has
+// completed and its writes are visible (immediately when there is no
+// programmatic predecessor).  No kernel triggers its successor early: blocks
+// of the next stage waiting on the device slowed the step down (measured).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+#ifdef __CUDACC__
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+#endif
+
+// ---------------------------------------------------------------------------
 // TMA
 // ---------------------------------------------------------------------------
 // 1-D bulk copy global -> shared; dst, src 16-byte aligned, bytes % 16 == 0.
@@ -117,6 +147,31 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
         "[%4];" ::"r"(smem_u32(dst)),
         "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(smem_u32(bar))
         : "memory");
+}
+
+// The same copy delivered to every CTA of the cluster in `mask` (same CTA-relative
+// destination offset and mbarrier in each); the source tile is read from L2 once.
+__device__ __forceinline__ void tma_load_2d_mc(void* dst, const CUtensorMap* map, int32_t c0, int32_t c1,
+                                               uint64_t* bar, uint16_t mask)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster "
+        "[%0], [%1, {%2, %3}], [%4], %5;" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(smem_u32(bar)), "h"(mask)
+        : "memory");
+}
+
+__device__ __forceinline__ uint32_t cluster_ctarank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+// All threads of all CTAs of the cluster (release / acquire).
+__device__ __forceinline__ void cluster_sync_all()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
 __device__ __forceinline__ void prefetch_tmap(const CUtensorMap* map)
@@ -190,6 +245,15 @@ __device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t adesc, uint64_
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
         "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
         : "memory");
+}
+
+// Arrive once on the mbarrier at `bar`'s offset in every CTA of the cluster in
+// `mask` when all previously issued tcgen05.mma of this thread complete.
+__device__ __forceinline__ void mma_commit_mc(uint64_t* bar, uint16_t mask)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;"
+                 ::"r"(smem_u32(bar)), "h"(mask)
+                 : "memory");
 }
 
 // Arrive once on `bar` when all previously issued tcgen05.mma of this thread complete.

@@ -80,6 +80,13 @@ def test_bitset_sc2_matches(ctx):
     _full_parity(ctx, p, k1=1500, flags=trg.FLAG_SC2_BITSET)
 
 
+@pytest.mark.parametrize("shape,n", [("indoor", 3000), ("cube", 777)])
+def test_single_cta_sc2_matches(ctx, shape, n):
+    # the GEMM on independent CTAs (no clusters sharing B) gives the same integers
+    p = synth.make_problem(shape, n, 0.05, 17)
+    _full_parity(ctx, p, k1=min(1500, 2 * n), flags=trg.FLAG_SC2_SINGLE_CTA)
+
+
 def test_complete_graph_exactness(ctx):
     # tau huge: G is complete, every SC^2 entry is N-2 (largest integer the FP8 GEMM accumulates)
     p = synth.make_problem("cube", 5000, 0.1, 12)
