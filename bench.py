@@ -43,9 +43,9 @@ WORKLOAD = {"workload": "indoor-shaped single problem", "n": 5000, "inlier_ratio
             "tau_m": 0.1, "k1": 2000, "k2": 2, "inlier_thresh_m": 0.1, "problems_cycled": 8,
             "l2": "flushed between timed steps (256 MB write, outside the events)"}
 # kernels of ours launched per registration: pack, compat, sc2 (with the histogram and
-# the threshold choice), count, scan, emit, rank, pgs, kabsch, kabsch_fp64, verify (main
-# and FP64 list), finalize
-LAUNCHES_PER_STEP = 13
+# the threshold choice), count (with the row prefixes), emit, rank, pgs, kabsch,
+# kabsch_fp64, verify (main and FP64 list), finalize
+LAUNCHES_PER_STEP = 12
 # DRAM bytes (read + write) of one SC^2 kernel launch on this workload, from one ncu
 # capture of the current kernel (profiles/sc2_tcgen05_indoor5000.txt)
 SC2_DRAM_BYTES = 28328704
@@ -204,7 +204,7 @@ def run_batched(trg, torch, stream, steps, warmup, flush):
     return {"value": 256 / (mean_ms / 1e3), "unit": "registrations/s", "problems_per_call": 256,
             "ms_per_call": mean_ms, "calls": steps, "n_range": [500, 5000], "mean_n": float(offs[-1] / 256),
             "success": f"{ok}/256 (indoor RE<15deg TE<0.3m, outdoor RE<5deg TE<0.6m)",
-            "gpu_launches_per_call": 16}
+            "gpu_launches_per_call": 13}
 
 
 def run_learned(trg, torch, stream, flush, ks=(1, 2, 4, 8, 100, 250, 500, 1000)):

@@ -139,8 +139,8 @@ int turboreg_mlp_train_step(turboreg_mlp* t, const float* feat, const float* lab
  * cudaMalloc, such as a plugin inside a host framework that owns all device
  * memory through its own pool, or a real-time loop that forbids allocation
  * after start-up (cudaMalloc may synchronise the device and take unbounded
- * time).  Its scratch (histogram, per-row tie counts, candidate keys, control
- * block: about 225 KB) is one fixed array in the library's device memory,
+ * time).  Its scratch (histogram, active-row list with per-row counts,
+ * candidate keys, control block: about 225 KB) is one fixed array in the library's device memory,
  * loaded with the module and held by every GPU that loads the library until
  * the process exits; nothing is allocated or freed by this call.
  *

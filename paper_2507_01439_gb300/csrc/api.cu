@@ -48,7 +48,7 @@ struct Workspace {
     uint8_t* a8 = nullptr;           // [slots][np^2]
     uint32_t* bits = nullptr;        // [slots][np^2 / 32]
     uint16_t* w = nullptr;           // [slots][np^2]
-    int32_t* rows = nullptr;         // [slots][6][np]: rowscore, deg, rowcnt, rowpref, rowcnt_gt, rowpref_gt
+    int32_t* rows = nullptr;         // [slots][6][np]: rowscore, deg, active (int4 per row)
     uint32_t* hist = nullptr;        // [slots][np + 1]
     uint64_t* cand = nullptr;        // [slots][K1_MAX]
     int4* piv = nullptr;             // [slots][K1_MAX]
@@ -279,10 +279,7 @@ ProbView make_view(turboreg_ctx* c, int slot, int64_t in_off, int32_t n, const t
     int32_t* rows = ws.rows + s * 6 * np;
     v.rowscore = rows;
     v.deg = rows + np;
-    v.rowcnt = rows + 2 * np;
-    v.rowpref = rows + 3 * np;
-    v.rowcnt_gt = rows + 4 * np;
-    v.rowpref_gt = rows + 5 * np;
+    v.active = reinterpret_cast<int4*>(rows + 2 * np);   // np is a multiple of 256: 16-byte aligned
     v.hist = ws.hist + s * (np + 1);
     v.cand = ws.cand + s * TURBOREG_K1_MAX;
     v.piv = ws.piv + s * TURBOREG_K1_MAX;

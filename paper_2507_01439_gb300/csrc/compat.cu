@@ -64,7 +64,6 @@ __global__ void __launch_bounds__(256) pack_kernel(ManyViews vs, const float* __
         p8[1] = make_float4(a[4], a[5], 0.f, 0.f);
         v.rowscore[k] = 0;
         v.deg[k] = 0;
-        v.rowcnt[k] = 0;
         v.hist[k] = 0;
     }
     if (k == 0) v.hist[v.n_pad] = 0;

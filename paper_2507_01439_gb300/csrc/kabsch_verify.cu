@@ -536,9 +536,9 @@ void stage_blocks(int32_t n, int32_t k1, int32_t k2, int32_t blocks[kNumBatchSta
     blocks[ST_PACK] = n_pad / 256;
     blocks[ST_COMPAT] = T * (T + 1) / 2;
     blocks[ST_SELECT] = 1;
-    blocks[ST_COUNT] = (n + 7) / 8;
-    blocks[ST_SCAN] = 1;
-    blocks[ST_EMIT] = n;
+    blocks[ST_COUNT] = count_blocks(n);
+    blocks[ST_SCAN] = 0;   // the row prefixes are written by the count pass's last block
+    blocks[ST_EMIT] = emit_blocks(n);
     blocks[ST_RANK] = (k1 + 31) / 32;
     blocks[ST_PGS] = (k1 + 7) / 8;
     blocks[ST_KABSCH] = (nh + 127) / 128;

@@ -11,9 +11,9 @@
 // until the process exits).  The caller passes the weight matrix and the output buffers;
 // nothing is allocated or freed, by this code or by any library it calls.
 //
-// The scratch is shared by every call: the histogram, the per-row tie counts
-// and the control block are cleared with cudaMemsetAsync at the start of each
-// call, and two calls whose work overlaps on the GPU (different streams, or
+// The scratch is shared by every call: the histogram and the control block
+// (which holds the active-row and slot counters) are cleared with
+// cudaMemsetAsync at the start of each call, and two calls whose work overlaps on the GPU (different streams, or
 // different host threads) race on it.  Serialise calls per device.
 //
 // In host code the name g_pivot_scratch only stands in for the array; its
@@ -41,11 +41,8 @@ constexpr int32_t kMaxK1 = TURBOREG_K1_MAX;
 constexpr size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 constexpr size_t kOffCtl = 0;
 constexpr size_t kOffHist = align256(sizeof(Ctl));
-constexpr size_t kOffRowcnt = kOffHist + align256(sizeof(uint32_t) * (kMaxN + 1));
-constexpr size_t kOffRowpref = kOffRowcnt + align256(sizeof(int32_t) * kMaxN);
-constexpr size_t kOffRowcntGt = kOffRowpref + align256(sizeof(int32_t) * kMaxN);
-constexpr size_t kOffRowprefGt = kOffRowcntGt + align256(sizeof(int32_t) * kMaxN);
-constexpr size_t kOffCand = kOffRowprefGt + align256(sizeof(int32_t) * kMaxN);
+constexpr size_t kOffActive = kOffHist + align256(sizeof(uint32_t) * (kMaxN + 1));
+constexpr size_t kOffCand = kOffActive + align256(sizeof(int4) * kMaxN);
 constexpr size_t kScratchBytes = kOffCand + align256(sizeof(uint64_t) * kMaxK1);
 
 static __device__ __align__(256) uint8_t g_pivot_scratch[kScratchBytes];
@@ -113,17 +110,13 @@ extern "C" int turboreg_select_pivots_noalloc(const uint16_t* w_dev, int32_t n, 
     v.w = const_cast<uint16_t*>(w_dev);
     v.ctl = reinterpret_cast<Ctl*>(scr + kOffCtl);
     v.hist = reinterpret_cast<uint32_t*>(scr + kOffHist);
-    v.rowcnt = reinterpret_cast<int32_t*>(scr + kOffRowcnt);
-    v.rowpref = reinterpret_cast<int32_t*>(scr + kOffRowpref);
-    v.rowcnt_gt = reinterpret_cast<int32_t*>(scr + kOffRowcntGt);
-    v.rowpref_gt = reinterpret_cast<int32_t*>(scr + kOffRowprefGt);
+    v.active = reinterpret_cast<int4*>(scr + kOffActive);
     v.cand = reinterpret_cast<uint64_t*>(scr + kOffCand);
     v.piv = reinterpret_cast<int4*>(pivots_dev);
 
     // the previous call's contents stay in the array: clear what must start at zero
     cudaError_t e = cudaMemsetAsync(scr + kOffCtl, 0, sizeof(Ctl), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(v.hist, 0, sizeof(uint32_t) * (n + 1), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(v.rowcnt, 0, sizeof(int32_t) * n, s);
     if (e != cudaSuccess) return TURBOREG_ERR_CUDA;
     launch_topk_single(v, s);
     e = cudaGetLastError();

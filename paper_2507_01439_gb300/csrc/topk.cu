@@ -5,17 +5,18 @@
 // index), listed in (W desc, i asc, j asc) order.  With the learned
 // proposal the competing weight is floor(W_ij p_i p_j) (pivot_weight).
 //
-// Exact radix-style selection (no atomics on shared counters, so the result
-// and its cost do not depend on contention):
+// Exact radix-style selection; the selected set, and so the pivots, do not
+// depend on the order in which blocks run:
 //   hist    histogram of edge weights (built by the SC^2 GEMM epilogue, or
 //           by hist_kernel for the CUDA-core SC^2 path and for callers)
 //   select  one block: alpha = K1-th largest weight, c_gt = #{W > alpha},
 //           m = K1' - c_gt ties still needed (K1' = min(K1, |E+|))
-//   count   warp per row: #{j : W_ij > alpha} and #{j : W_ij == alpha}
-//   scan    one block: exclusive prefixes of both per-row counts
-//   emit    block per row that holds a selected edge: W > alpha edges go to
-//           slots prefix_gt[i] + rank-in-row; ties get global tie ranks
-//           prefix_eq[i] + rank-in-row (column order) and ranks < m are kept
+//   count   warp per row pair (i, n-1-i): #{j : W_ij > alpha} and
+//           #{j : W_ij == alpha}; rows with such edges join the active list
+//   emit    blocks over the active rows: W > alpha edges take slots from one
+//           atomic per row (the rank pass orders them); ties get global tie
+//           ranks (tie prefix over the active rows above) + rank-in-row
+//           (column order) and ranks < m are kept
 //   rank    candidate keys (W << 32 | ~(i*n+j)) are unique; each pivot's
 //           position is the number of larger keys.
 #include "tr_common.cuh"
@@ -101,145 +102,199 @@ __global__ void __launch_bounds__(1024) select_kernel(VS vs)
     select_alpha(v, sbuf);
 }
 
-// Per-row counts of the weight > alpha and weight == alpha edges; 8 rows per
-// block, one per warp.
+// Zero the weights of a 16-byte chunk (8 entries, columns 8c .. 8c+7) outside
+// the row's upper part (row, n): only a row's first and last chunks have any.
+__device__ __forceinline__ uint4 mask_chunk(uint4 q, int c, int row, int n)
+{
+    const int lo = row + 1 - c * 8, hi = n - c * 8;   // keep entries e with lo <= e < hi
+    if (lo <= 0 && hi >= 8) return q;
+    uint32_t wd[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+    for (int e = 0; e < 8; ++e)
+        if (e < lo || e >= hi) wd[e >> 1] &= (e & 1) ? 0x0000FFFFu : 0xFFFF0000u;
+    return make_uint4(wd[0], wd[1], wd[2], wd[3]);
+}
+
+// #{entries > alpha} and #{entries == alpha} of a chunk, as packed 16-bit
+// SIMD compares (weights and alpha < 2^16; a zeroed entry never counts, alpha >= 1).
+__device__ __forceinline__ void count_chunk(uint4 q, uint32_t a2, int& g, int& e)
+{
+    g += (__popc(__vcmpgtu2(q.x, a2)) + __popc(__vcmpgtu2(q.y, a2)) + __popc(__vcmpgtu2(q.z, a2)) +
+          __popc(__vcmpgtu2(q.w, a2))) >> 4;
+    e += (__popc(__vcmpeq2(q.x, a2)) + __popc(__vcmpeq2(q.y, a2)) + __popc(__vcmpeq2(q.z, a2)) +
+          __popc(__vcmpeq2(q.w, a2))) >> 4;
+}
+
+// Per-row counts of the weight > alpha and weight == alpha edges.  Warp w
+// takes rows w and n-1-w, whose upper-triangle parts hold about n/8 16-byte
+// chunks together, so every warp has the same work; each lane keeps eight
+// 16-byte loads in flight.  Rows holding such edges are appended to the
+// active list as (row, #gt, #eq), in any order.
 template <class VS>
-__global__ void __launch_bounds__(256) count_kernel(VS vs)
+__global__ void __launch_bounds__(128) count_kernel(VS vs)
 {
     pdl_wait();
     int lb;
     const ProbView v = vs.get(ST_COUNT, blockIdx.x, lb);
     const int lane = threadIdx.x & 31;
-    const int i = lb * 8 + (threadIdx.x >> 5);
-    if (v.ctl->n_sel == 0 || i >= v.n) return;
+    const int n = v.n;
+    const int wp = lb * 4 + (threadIdx.x >> 5);
+    if (v.ctl->n_sel == 0 || wp >= (n + 1) / 2) return;
     const int alpha = v.ctl->alpha;
-    int gt = 0, eq = 0;
-    for_row_chunks(v, i, lane, [&](int, int w) {
-        gt += w > alpha;
-        eq += w == alpha;
-    });
+    const uint32_t a2 = static_cast<uint32_t>(alpha) * 0x10001u;
+    const bool learned = v.prob != nullptr;
+    const int ra = wp, rb = n - 1 - wp;           // rb == ra: middle row of an odd n
+    const int c1 = (n - 1) >> 3;
+    const int a0 = (ra + 1) >> 3, b0 = (rb + 1) >> 3;
+    const int la = ra + 1 < n ? c1 - a0 + 1 : 0;
+    const int lbn = (rb != ra && rb + 1 < n) ? c1 - b0 + 1 : 0;
+    const int tot = la + lbn;
+    int ga = 0, ea = 0, gb = 0, eb = 0;
+    for (int base = lane; base < tot; base += 8 * 32) {
+        uint4 q[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int x = base + u * 32;
+            const int row = x < la ? ra : rb;
+            const int c = x < la ? a0 + x : b0 + (x - la);
+            q[u] = x < tot ? *reinterpret_cast<const uint4*>(v.w + (size_t)row * v.n_pad + c * 8)
+                           : make_uint4(0u, 0u, 0u, 0u);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int x = base + u * 32;
+            const bool isa = x < la;
+            const int row = isa ? ra : rb;
+            const int c = isa ? a0 + x : b0 + (x - la);
+            const uint4 qm = mask_chunk(q[u], c, row, n);
+            int g = 0, e = 0;
+            if (!learned) {
+                count_chunk(qm, a2, g, e);
+            } else if ((qm.x | qm.y | qm.z | qm.w) != 0u) {
+#pragma unroll
+                for (int el = 0; el < 8; ++el) {
+                    const uint32_t word = el < 2 ? qm.x : el < 4 ? qm.y : el < 6 ? qm.z : qm.w;
+                    const int pw = pivot_weight(v, row, c * 8 + el, static_cast<int>((word >> ((el & 1) * 16)) & 0xFFFFu));
+                    g += pw > alpha;
+                    e += pw == alpha;
+                }
+            }
+            if (isa) { ga += g; ea += e; } else { gb += g; eb += e; }
+        }
+    }
 #pragma unroll
     for (int off = 16; off >= 1; off >>= 1) {
-        gt += __shfl_xor_sync(0xffffffffu, gt, off);
-        eq += __shfl_xor_sync(0xffffffffu, eq, off);
+        ga += __shfl_xor_sync(0xffffffffu, ga, off);
+        ea += __shfl_xor_sync(0xffffffffu, ea, off);
+        gb += __shfl_xor_sync(0xffffffffu, gb, off);
+        eb += __shfl_xor_sync(0xffffffffu, eb, off);
     }
     if (lane == 0) {
-        v.rowcnt[i] = eq;
-        v.rowcnt_gt[i] = gt;
+        if (ga | ea) v.active[atomicAdd(&v.ctl->n_active, 1u)] = make_int4(ra, ga, ea, 0);
+        if (rb != ra && (gb | eb)) v.active[atomicAdd(&v.ctl->n_active, 1u)] = make_int4(rb, gb, eb, 0);
     }
 }
 
-// Exclusive prefixes of both per-row counts; thread t owns rows
-// [t*per, (t+1)*per), per <= 32, with its loads in flight together.
-template <class VS>
-__global__ void __launch_bounds__(1024) scan_rows_kernel(VS vs)
-{
-    pdl_wait();
-    __shared__ int sbuf[33];
-    int lb;
-    const ProbView v = vs.get(ST_SCAN, blockIdx.x, lb);
-    if (v.ctl->n_sel == 0) return;
-    const int per = (v.n + blockDim.x - 1) / blockDim.x;
-    const int lo = threadIdx.x * per;
-    int se = 0, sg = 0;
-#pragma unroll
-    for (int q = 0; q < 32; ++q) {
-        if (q < per && lo + q < v.n) {
-            se += v.rowcnt[lo + q];
-            sg += v.rowcnt_gt[lo + q];
-        }
-    }
-    const int ie = block_incl_scan(se, sbuf);
-    const int ig = block_incl_scan(sg, sbuf);
-    int re = ie - se, rg = ig - sg;
-#pragma unroll
-    for (int q = 0; q < 32; ++q) {
-        if (q < per && lo + q < v.n) {
-            const int a = v.rowcnt[lo + q], b = v.rowcnt_gt[lo + q];
-            v.rowpref[lo + q] = re;
-            v.rowpref_gt[lo + q] = rg;
-            re += a;
-            rg += b;
-        }
-    }
-}
-
-// One block (256 threads) per row; a thread takes 4 consecutive 16-byte
-// chunks per sweep (all of a row's loads are in flight at once, thread order
-// = column order).  Blocks whose row holds nothing selected exit at once.
+// Blocks take the active rows in any order.  W > alpha edges take slots
+// base + rank-in-row from one atomic per row (any slots in [0, c_gt) will
+// do: the rank pass orders the keys).  Ties must be the m lowest (i, j):
+// a row with ties sums the tie counts of the active rows above it (its tie
+// prefix) and keeps tie ranks prefix + rank-in-row < m.  Thread t reads
+// chunks 4t .. 4t+3 of each 1024-chunk sweep (thread order = column order).
 template <class VS>
 __global__ void __launch_bounds__(256) emit_kernel(VS vs)
 {
     pdl_wait();
     __shared__ int sg[8], se[8];
-    int i;
-    const ProbView v = vs.get(ST_EMIT, blockIdx.x, i);
+    __shared__ int s_base;
+    int lb;
+    const ProbView v = vs.get(ST_EMIT, blockIdx.x, lb);
     if (v.ctl->n_sel == 0) return;
-    if (i + 1 >= v.n) return;
-    const int m = v.ctl->m_ties;
-    const int ng = v.rowcnt_gt[i];
-    const int ne = v.rowcnt[i];
-    const int pe = v.rowpref[i];
-    const bool want_eq = ne > 0 && pe < m;
-    if (ng == 0 && !want_eq) return;
-    const int alpha = v.ctl->alpha, c_gt = v.ctl->c_gt;
-    const int pg = v.rowpref_gt[i];
-    const uint16_t* wrow = v.w + (size_t)i * v.n_pad;
-    const int c0 = (i + 1) >> 3, c1 = (v.n - 1) >> 3;
+    const int nact = static_cast<int>(v.ctl->n_active);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int base_g = pg, base_e = pe;
-    for (int cb = c0; cb <= c1; cb += blockDim.x * 4) {
-        uint32_t gm = 0, em = 0;   // bit 8*k + e: chunk k, element e
-        const int cfirst = cb + threadIdx.x * 4;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int c = cfirst + k;
-            if (c > c1) break;
-            const uint4 q = *reinterpret_cast<const uint4*>(wrow + c * 8);
-            const uint32_t u[4] = {q.x, q.y, q.z, q.w};
-#pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                const int j = c * 8 + e;
-                const bool in = j > i && j < v.n;
-                const int w = in ? pivot_weight(v, i, j, (u[e >> 1] >> ((e & 1) * 16)) & 0xFFFF) : 0;
-                gm |= static_cast<uint32_t>(in && w > alpha) << (8 * k + e);
-                em |= static_cast<uint32_t>(in && w == alpha) << (8 * k + e);
+    const int m = v.ctl->m_ties, alpha = v.ctl->alpha, c_gt = v.ctl->c_gt;
+    const int c1 = (v.n - 1) >> 3;
+    for (int a = lb; a < nact; a += emit_blocks(v.n)) {
+        const int4 ar = v.active[a];
+        const int i = ar.x, ng = ar.y, ne = ar.z;
+        // tie prefix: ties in active rows above i
+        int pe = 0;
+        if (ne > 0) {
+            int part = 0;
+            for (int b = threadIdx.x; b < nact; b += blockDim.x) {
+                const int4 o = v.active[b];
+                part += o.x < i ? o.z : 0;
             }
-        }
-        // block exclusive scans of the two counts (thread order = column order)
-        const int g = __popc(gm), eN = __popc(em);
-        int gi = g, ei = eN;
 #pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            const int a = __shfl_up_sync(0xffffffffu, gi, off);
-            const int b = __shfl_up_sync(0xffffffffu, ei, off);
-            if (lane >= off) { gi += a; ei += b; }
+            for (int off = 16; off >= 1; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
+            if (lane == 0) se[warp] = part;
+            __syncthreads();
+            for (int w8 = 0; w8 < 8; ++w8) pe += se[w8];
+            __syncthreads();
         }
-        if (lane == 31) { sg[warp] = gi; se[warp] = ei; }
+        const bool want_eq = ne > 0 && pe < m;
+        if (ng == 0 && !want_eq) continue;   // uniform over the block
+        if (threadIdx.x == 0) s_base = ng > 0 ? static_cast<int>(atomicAdd(&v.ctl->gt_slot, static_cast<uint32_t>(ng))) : 0;
         __syncthreads();
-        int wg = 0, we = 0, tg = 0, te = 0;
-        for (int w8 = 0; w8 < 8; ++w8) {
-            if (w8 < warp) { wg += sg[w8]; we += se[w8]; }
-            tg += sg[w8];
-            te += se[w8];
+        const int pg = s_base;
+        const uint16_t* wrow = v.w + (size_t)i * v.n_pad;
+        int base_g = pg, base_e = pe;
+        for (int cb = (i + 1) >> 3; cb <= c1; cb += blockDim.x * 4) {
+            uint32_t gm = 0, em = 0;   // bit 8*k + e: chunk k, element e
+            const int cfirst = cb + threadIdx.x * 4;
+            uint4 q[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                q[k] = cfirst + k <= c1 ? *reinterpret_cast<const uint4*>(wrow + (cfirst + k) * 8)
+                                        : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if ((q[k].x | q[k].y | q[k].z | q[k].w) == 0u) continue;
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    const uint32_t word = e < 2 ? q[k].x : e < 4 ? q[k].y : e < 6 ? q[k].z : q[k].w;
+                    const int j = (cfirst + k) * 8 + e;
+                    const bool in = j > i && j < v.n;
+                    const int w = in ? pivot_weight(v, i, j, (word >> ((e & 1) * 16)) & 0xFFFF) : 0;
+                    gm |= static_cast<uint32_t>(in && w > alpha) << (8 * k + e);
+                    em |= static_cast<uint32_t>(in && w == alpha) << (8 * k + e);
+                }
+            }
+            // block exclusive scans of the two counts (thread order = column order)
+            const int g = __popc(gm), eN = __popc(em);
+            int gi = g, ei = eN;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const int x = __shfl_up_sync(0xffffffffu, gi, off);
+                const int y = __shfl_up_sync(0xffffffffu, ei, off);
+                if (lane >= off) { gi += x; ei += y; }
+            }
+            if (lane == 31) { sg[warp] = gi; se[warp] = ei; }
+            __syncthreads();
+            int wg = 0, we = 0, tg = 0, te = 0;
+            for (int w8 = 0; w8 < 8; ++w8) {
+                if (w8 < warp) { wg += sg[w8]; we += se[w8]; }
+                tg += sg[w8];
+                te += se[w8];
+            }
+            __syncthreads();
+            int rg = base_g + wg + gi - g, re = base_e + we + ei - eN;
+            while (gm) {
+                const int b = __ffs(gm) - 1;
+                gm &= gm - 1;
+                const int j = (cfirst + (b >> 3)) * 8 + (b & 7);
+                v.cand[rg++] = edge_key(pivot_weight(v, i, j, wrow[j]), i, j, v.n);
+            }
+            while (em) {
+                const int b = __ffs(em) - 1;
+                em &= em - 1;
+                if (re < m) v.cand[c_gt + re] = edge_key(alpha, i, (cfirst + (b >> 3)) * 8 + (b & 7), v.n);
+                ++re;
+            }
+            base_g += tg;
+            base_e += te;
+            if (base_g - pg >= ng && (!want_eq || base_e >= m || base_e - pe >= ne)) break;
         }
-        __syncthreads();
-        int rg = base_g + wg + gi - g, re = base_e + we + ei - eN;
-        while (gm) {
-            const int b = __ffs(gm) - 1;
-            gm &= gm - 1;
-            const int j = (cfirst + (b >> 3)) * 8 + (b & 7);
-            v.cand[rg++] = edge_key(pivot_weight(v, i, j, wrow[j]), i, j, v.n);
-        }
-        while (em) {
-            const int b = __ffs(em) - 1;
-            em &= em - 1;
-            if (re < m) v.cand[c_gt + re] = edge_key(alpha, i, (cfirst + (b >> 3)) * 8 + (b & 7), v.n);
-            ++re;
-        }
-        base_g += tg;
-        base_e += te;
-        if (base_g - pg >= ng && (!want_eq || base_e >= m || base_e - pe >= ne)) break;
     }
 }
 
@@ -324,8 +379,7 @@ void launch_select(const Batch& b, cudaStream_t s) { launch_pdl(select_kernel<Ma
 void launch_topk_rest(const Batch& b, const int32_t tot[kNumBatchStages], int max_k1, cudaStream_t s)
 {
     const ManyViews vs{b};
-    launch_pdl(count_kernel<ManyViews>, tot[ST_COUNT], 256, 0, s, vs);
-    launch_pdl(scan_rows_kernel<ManyViews>, b.num, 1024, 0, s, vs);
+    launch_pdl(count_kernel<ManyViews>, tot[ST_COUNT], 128, 0, s, vs);
     launch_pdl(emit_kernel<ManyViews>, tot[ST_EMIT], 256, 0, s, vs);
     launch_pdl(rank_kernel<ManyViews>, tot[ST_RANK], 256, max_k1 * 8, s, vs);
 }
@@ -336,9 +390,8 @@ void launch_topk_single(const ProbView& v, cudaStream_t s)
     const OneView vs{v};
     launch_hist_vs(vs, (v.n + kHistRowsPerBlock - 1) / kHistRowsPerBlock, v.n, s);
     launch_pdl(select_kernel<OneView>, 1, 1024, 0, s, vs);
-    launch_pdl(count_kernel<OneView>, (v.n + 7) / 8, 256, 0, s, vs);
-    launch_pdl(scan_rows_kernel<OneView>, 1, 1024, 0, s, vs);
-    launch_pdl(emit_kernel<OneView>, v.n, 256, 0, s, vs);
+    launch_pdl(count_kernel<OneView>, count_blocks(v.n), 128, 0, s, vs);
+    launch_pdl(emit_kernel<OneView>, emit_blocks(v.n), 256, 0, s, vs);
     launch_pdl(rank_kernel<OneView>, (v.k1 + 31) / 32, 256, v.k1 * 8, s, vs);
 }
 

@@ -28,13 +28,14 @@ struct Ctl {
     int32_t alpha;       // K1-th largest edge weight (Eq. 4)
     int32_t c_gt;        // edges with weight > alpha (all selected)
     int32_t m_ties;      // edges with weight == alpha still to take, lowest (i,j) first
-    uint32_t gt_slot;    // atomic slot counter for the weight > alpha edges
+    uint32_t gt_slot;    // slot counter for the weight > alpha edges
     int32_t n_pivots;    // |P|
     int32_t n_valid;     // valid hypotheses (clique + non-degenerate Kabsch)
     int32_t n_fp64;      // hypotheses whose Kabsch ran in FP64
     uint32_t fp64_slot;  // atomic counter of the FP64 Kabsch list
     uint32_t done_blocks;  // completion counter for last-block epilogues
-    int32_t pad[4];
+    uint32_t n_active;   // rows holding an edge of weight >= alpha (pivot selection)
+    int32_t pad[3];
 };
 
 // ---------------------------------------------------------------------------

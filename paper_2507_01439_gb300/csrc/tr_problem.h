@@ -33,10 +33,8 @@ struct ProbView {
     int32_t* rowscore;   // [n_pad] SC^2 row sums
     int32_t* deg;        // [n_pad] degrees
     uint32_t* hist;      // [n_pad + 1] histogram of O2Graph edge weights
-    int32_t* rowcnt;     // [n_pad] per-row count of edges with weight == alpha
-    int32_t* rowpref;    // [n_pad] exclusive prefix of rowcnt
-    int32_t* rowcnt_gt;  // [n_pad] per-row count of edges with weight > alpha
-    int32_t* rowpref_gt; // [n_pad] exclusive prefix of rowcnt_gt
+    int4* active;        // [n_pad] (row, #weight > alpha, #weight == alpha, 0) of the rows
+                         // holding such edges, in any order
     uint64_t* cand;      // [K1_MAX] selected edge keys (weight << 32 | ~(i*n+j))
     int4* piv;           // [K1_MAX] pivots (i, j, w, 0) in Eq. 4 order
     int4* cliques;       // [K1_MAX*K2_MAX] (i, j, z, valid) in Alg. 2 order
@@ -57,6 +55,11 @@ enum Stage {
     ST_PACK = 0, ST_COMPAT, ST_SELECT, ST_COUNT, ST_SCAN, ST_EMIT, ST_RANK, ST_PGS, ST_KABSCH, ST_KABSCH64,
     ST_VERIFY, ST_FINAL, ST_HIST, ST_BITSET, ST_GEMM, ST_FEAT, ST_MLP, kNumBatchStages
 };
+
+// Blocks of the per-row count pass (four row pairs per block, a warp each)
+// and of the emit pass (active rows strided over the blocks).
+__host__ __device__ inline int count_blocks(int n) { return ((n + 1) / 2 + 3) / 4; }
+__host__ __device__ inline int emit_blocks(int n) { return (n + 7) / 8; }
 
 struct Batch {
     const ProbView* views;   // [num] device
