@@ -205,6 +205,11 @@ __global__ void __launch_bounds__(128) kabsch_kernel(ManyViews vs)
 
 // Phase 2: the same closed form in FP64 for the listed hypotheses only, so the
 // slow FP64 pipe runs on dense warps instead of on every warp that holds one.
+// On this GPU one FP64 FMA warp instruction occupies the FP64 pipe for about
+// 69 cycles whatever the number of active lanes (measured), so the kernel is
+// latency-bound at ~15 us per warp; a float-float (paired FP32) version of the
+// same closed form measured no faster (its longer straight-line code stalls
+// on instruction fetch), so FP64 stays.
 __global__ void __launch_bounds__(32) kabsch_fp64_kernel(ManyViews vs)
 {
     pdl_wait();

@@ -13,9 +13,11 @@
 // (z != i, j follows from the zero diagonal) and W read symmetrically,
 // W_ab = W_min(a,b),max(a,b) (only the upper triangle is stored).
 //
-// One warp per pivot: lane l ANDs bitset words l, l+32, ... of the two rows,
-// keeps a private top-K2 list, and the warp merges the 32 lists with K2
-// rounds of a 64-bit max-reduction over keys (S << 32 | ~z).
+// One warp per pivot: lane l ANDs bitset words l, l+32, ... of the two rows
+// (four words of each row in flight per sweep), looks up the weights of its
+// candidates eight at a time, keeps a private top-K2 list, and the warp
+// merges the 32 lists with K2 rounds of a 64-bit max-reduction over keys
+// (S << 32 | ~z).
 #include "tr_common.cuh"
 #include "tr_problem.h"
 
@@ -84,13 +86,24 @@ __global__ void __launch_bounds__(256) pgs_kernel(ManyViews vs)
     };
     const int zs = undirected ? 0 : j + 1;
     const int w0 = zs >> 5;
-    for (int wd = w0 + lane; wd < v.ldb; wd += 32) {
-        uint32_t m = bi[wd] & bj[wd];
-        if (wd == w0) m &= ~0u << (zs & 31);
-        while (m) {
-            zb[nz++] = wd * 32 + __ffs(m) - 1;
-            m &= m - 1;
-            if (nz == 8) flush();
+    // lane l takes words w0 + l + 32 t; the 2 x 4 word loads of a sweep are in flight together
+    for (int wb = w0 + lane; wb < v.ldb; wb += 32 * 4) {
+        uint32_t mw[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int wd = wb + 32 * t;
+            mw[t] = wd < v.ldb ? (bi[wd] & bj[wd]) : 0u;
+        }
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int wd = wb + 32 * t;
+            uint32_t m = mw[t];
+            if (wd == w0) m &= ~0u << (zs & 31);
+            while (m) {
+                zb[nz++] = wd * 32 + __ffs(m) - 1;
+                m &= m - 1;
+                if (nz == 8) flush();
+            }
         }
     }
     if (nz) flush();
