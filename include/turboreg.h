@@ -78,6 +78,10 @@ typedef enum {
 #define TURBOREG_FLAG_SC2_SINGLE_CTA 0x8u /* SC^2 GEMM on independent CTAs; by default pairs of CTAs
                                              (thread-block clusters) share the B operand tile by TMA
                                              multicast (same integers either way) */
+#define TURBOREG_FLAG_VERIFY_PTS32 0x10u   /* verification tile of 128 hypotheses x 128 matches per block */
+#define TURBOREG_FLAG_VERIFY_PTS128 0x20u  /* ... x 512 matches per block (default: 256); tile shapes are
+                                              chosen by the autotuner (same results either way); in a
+                                              batch the first problem's tile flags apply to all */
 
 typedef struct {
     float tau;            /* compatibility threshold of Eq. 1, metres, >= 0 */

@@ -32,6 +32,8 @@ FLAG_SC2_BITSET = 0x1
 FLAG_STAGE_TIMES = 0x2
 FLAG_NO_GRAPH = 0x4
 FLAG_SC2_SINGLE_CTA = 0x8
+FLAG_VERIFY_PTS32 = 0x10
+FLAG_VERIFY_PTS128 = 0x20
 
 (BUF_ADJ_BITS, BUF_ADJ_FP8, BUF_SC2, BUF_PIVOTS, BUF_CLIQUES, BUF_RT, BUF_INLIERS, BUF_ROWSCORE, BUF_DEGREE,
  BUF_FEATURES, BUF_PROB, BUF_SCORES) = range(1, 13)

@@ -77,6 +77,7 @@ struct Plan {
     int32_t num = 0;
     int32_t max_n = 0, max_k1 = 0, k2_common = 0;
     int32_t bitset = 0, timed = 0, learned = 0, pair = 1;
+    int32_t vpw = 64;        // verification tile: points per warp
     int32_t tot[kNumBatchStages] = {};
 };
 
@@ -337,12 +338,13 @@ int build_plan(turboreg_ctx* c, int32_t num, const int64_t* in_off, const int32_
     plan.timed = num == 1 && (prm[0]->flags & TURBOREG_FLAG_STAGE_TIMES) != 0;
     plan.learned = prm[0]->proposal == TURBOREG_PROPOSAL_LEARNED;
     plan.pair = (prm[0]->flags & TURBOREG_FLAG_SC2_SINGLE_CTA) ? 0 : 1;
+    plan.vpw = (prm[0]->flags & TURBOREG_FLAG_VERIFY_PTS32) ? 32 : (prm[0]->flags & TURBOREG_FLAG_VERIFY_PTS128) ? 128 : 64;
     plan.k2_common = prm[0]->k2;
     for (int st = 0; st < kNumBatchStages; ++st) ws.h_pre[st * (num + 1)] = 0;
     for (int32_t b = 0; b < num; ++b) {
         ws.h_views[b] = make_view(c, b, in_off[b], n[b], prm[b]);
         int32_t blocks[kNumBatchStages];
-        stage_blocks(n[b], prm[b]->k1, prm[b]->k2, blocks);
+        stage_blocks(n[b], prm[b]->k1, prm[b]->k2, plan.vpw, blocks);
         for (int st = 0; st < kNumBatchStages; ++st) {
             plan.tot[st] += blocks[st];
             ws.h_pre[st * (num + 1) + b + 1] = plan.tot[st];
@@ -417,9 +419,9 @@ int enqueue_plan(turboreg_ctx* c, const Plan& pl, const Batch& bt, const float* 
     // fork: ill-conditioned cliques (FP64 list) on the side stream, the rest here
     TR_CHECK(cudaEventRecord(c->fork_ev, s));
     TR_CHECK(cudaStreamWaitEvent(c->side, c->fork_ev, 0));
-    launch_kabsch_fp64_verify(bt, pl.tot[ST_KABSCH64], pl.tot[ST_VERIFY], c->side);
+    launch_kabsch_fp64_verify(bt, pl.tot[ST_KABSCH64], pl.tot[ST_VERIFY], pl.vpw, c->side);
     TR_CHECK(cudaEventRecord(c->join_ev, c->side));
-    launch_verify(bt, pl.tot[ST_VERIFY], s);
+    launch_verify(bt, pl.tot[ST_VERIFY], pl.vpw, s);
     TR_CHECK(cudaStreamWaitEvent(s, c->join_ev, 0));
     TR_EV(7);
     launch_finalize(bt, s);
@@ -986,7 +988,7 @@ int turboreg_score_transforms(turboreg_ctx* c, const float* src, const float* ds
     TR_CHECK(cudaMemcpyAsync(&v.ctl->n_pivots, &m, sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
     TR_CHECK(cudaMemsetAsync(v.inl, 0, sizeof(int32_t) * m, c->stream));
     TR_CHECK(cudaMemsetAsync(v.score, 0, sizeof(unsigned long long) * m, c->stream));
-    launch_verify(bt, pl.tot[ST_VERIFY], c->stream);
+    launch_verify(bt, pl.tot[ST_VERIFY], pl.vpw, c->stream);
     TR_CHECK(cudaGetLastError());
     TR_CHECK(cudaMemcpyAsync(out_in, v.inl, sizeof(int32_t) * m, cudaMemcpyDeviceToHost, c->stream));
     if (out_units)

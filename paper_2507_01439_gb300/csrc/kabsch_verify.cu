@@ -285,23 +285,26 @@ __device__ __forceinline__ f2 mul2(f2 a, f2 b)
 // units of 2^-22 theta (theta^2).  Integer sums are independent of the order
 // in which blocks add them, so a problem's scores do not depend on how the
 // work was split (one problem or a batch).
+// The points per warp of a block (PW, 32/64/128; the block then holds
+// 4 PW points) are a tile-shape choice of the caller (TURBOREG_FLAG_VERIFY_*).
 constexpr int kVWarps = 4;
 constexpr int kVHyp = 128;
-constexpr int kVPtsWarp = 64;
-constexpr int kVPts = kVWarps * kVPtsWarp;
 constexpr float kScoreUnits = 4194304.f;   // 2^22 units per theta (MAE) or theta^2 (MSE)
 
+template <int PW>
 struct VerifyShared {
-    float4 sp[kVPts][2];
+    float4 sp[kVWarps * PW][2];
     float4 srt[kVHyp][4];
     int scnt[kVWarps][kVHyp];
     uint32_t ssc[kVWarps][kVHyp];
     int sok[kVHyp];
 };
 
-template <bool kList, int kScore>
-__device__ __forceinline__ void verify_body(const ProbView& v, int lb, VerifyShared& sh)
+template <bool kList, int kScore, int PW>
+__device__ __forceinline__ void verify_body(const ProbView& v, int lb, VerifyShared<PW>& sh)
 {
+    constexpr int kVPtsWarp = PW;
+    constexpr int kVPts = kVWarps * PW;
     const int npb = (v.n + kVPts - 1) / kVPts;          // point blocks of this problem
     const int nh = kList ? static_cast<int>(v.ctl->fp64_slot) : v.ctl->n_pivots * v.k2;
     const int h0 = (lb / npb) * kVHyp;
@@ -396,17 +399,17 @@ __device__ __forceinline__ void verify_body(const ProbView& v, int lb, VerifySha
     }
 }
 
-template <bool kList>
+template <bool kList, int PW>
 __global__ void __launch_bounds__(128) verify_kernel(ManyViews vs)
 {
     pdl_wait();
-    __shared__ __align__(16) VerifyShared sh;
+    __shared__ __align__(16) VerifyShared<PW> sh;
     int lb;
     const ProbView v = vs.get(ST_VERIFY, blockIdx.x, lb);
     switch (v.scoring) {      // uniform over the block: a block serves one problem
-        case TURBOREG_SCORE_MAE: verify_body<kList, TURBOREG_SCORE_MAE>(v, lb, sh); break;
-        case TURBOREG_SCORE_MSE: verify_body<kList, TURBOREG_SCORE_MSE>(v, lb, sh); break;
-        default: verify_body<kList, TURBOREG_SCORE_IN>(v, lb, sh); break;
+        case TURBOREG_SCORE_MAE: verify_body<kList, TURBOREG_SCORE_MAE, PW>(v, lb, sh); break;
+        case TURBOREG_SCORE_MSE: verify_body<kList, TURBOREG_SCORE_MSE, PW>(v, lb, sh); break;
+        default: verify_body<kList, TURBOREG_SCORE_IN, PW>(v, lb, sh); break;
     }
 }
 
@@ -513,9 +516,11 @@ void launch_kabsch(const Batch& b, int total, cudaStream_t s)
     launch_pdl(kabsch_kernel, total, 128, 0, s, ManyViews{b});
 }
 
-void launch_verify(const Batch& b, int total, cudaStream_t s)
+void launch_verify(const Batch& b, int total, int pw, cudaStream_t s)
 {
-    launch_pdl(verify_kernel<false>, total, 128, 0, s, ManyViews{b});
+    if (pw == 32) launch_pdl(verify_kernel<false, 32>, total, 128, 0, s, ManyViews{b});
+    else if (pw == 128) launch_pdl(verify_kernel<false, 128>, total, 128, 0, s, ManyViews{b});
+    else launch_pdl(verify_kernel<false, 64>, total, 128, 0, s, ManyViews{b});
 }
 
 void launch_kabsch_fp64(const Batch& b, int total64, cudaStream_t s)
@@ -523,17 +528,20 @@ void launch_kabsch_fp64(const Batch& b, int total64, cudaStream_t s)
     launch_pdl(kabsch_fp64_kernel, total64, 32, 0, s, ManyViews{b});
 }
 
-void launch_kabsch_fp64_verify(const Batch& b, int total64, int total_verify, cudaStream_t s)
+void launch_kabsch_fp64_verify(const Batch& b, int total64, int total_verify, int pw, cudaStream_t s)
 {
     launch_pdl(kabsch_fp64_kernel, total64, 32, 0, s, ManyViews{b});
-    launch_pdl(verify_kernel<true>, total_verify, 128, 0, s, ManyViews{b});
+    if (pw == 32) launch_pdl(verify_kernel<true, 32>, total_verify, 128, 0, s, ManyViews{b});
+    else if (pw == 128) launch_pdl(verify_kernel<true, 128>, total_verify, 128, 0, s, ManyViews{b});
+    else launch_pdl(verify_kernel<true, 64>, total_verify, 128, 0, s, ManyViews{b});
 }
 
 void launch_finalize(const Batch& b, cudaStream_t s) { launch_pdl(finalize_kernel, b.num, 1024, 0, s, ManyViews{b}); }
 
 // Per-problem block counts of every stage.
-void stage_blocks(int32_t n, int32_t k1, int32_t k2, int32_t blocks[kNumBatchStages])
+void stage_blocks(int32_t n, int32_t k1, int32_t k2, int32_t verify_pw, int32_t blocks[kNumBatchStages])
 {
+    const int32_t vpts = kVWarps * verify_pw;
     const int32_t n_pad = (n + kSc2BN - 1) / kSc2BN * kSc2BN;
     const int32_t T = n_pad / 128;
     const int32_t nb = n_pad / kSc2BN;
@@ -542,13 +550,13 @@ void stage_blocks(int32_t n, int32_t k1, int32_t k2, int32_t blocks[kNumBatchSta
     blocks[ST_COMPAT] = T * (T + 1) / 2;
     blocks[ST_SELECT] = 1;
     blocks[ST_COUNT] = count_blocks(n);
-    blocks[ST_SCAN] = 0;   // the row prefixes are written by the count pass's last block
+    blocks[ST_SCAN] = 0;   // no separate row-scan pass
     blocks[ST_EMIT] = emit_blocks(n);
     blocks[ST_RANK] = (k1 + 31) / 32;
     blocks[ST_PGS] = (k1 + 7) / 8;
     blocks[ST_KABSCH] = (nh + 127) / 128;
     blocks[ST_KABSCH64] = (nh + 31) / 32;
-    blocks[ST_VERIFY] = ((nh + kVHyp - 1) / kVHyp) * ((n + kVPts - 1) / kVPts);
+    blocks[ST_VERIFY] = ((nh + kVHyp - 1) / kVHyp) * ((n + vpts - 1) / vpts);
     blocks[ST_FINAL] = 1;
     blocks[ST_HIST] = (n + 63) / 64;
     blocks[ST_BITSET] = n_pad;

@@ -112,7 +112,8 @@ struct ManyViews {
 #endif
 
 // per-problem block counts of each stage (host side, from n, k1, k2)
-void stage_blocks(int32_t n, int32_t k1, int32_t k2, int32_t blocks[kNumBatchStages]);
+// verify_pw: points per warp of the verification tile (32, 64 or 128)
+void stage_blocks(int32_t n, int32_t k1, int32_t k2, int32_t verify_pw, int32_t blocks[kNumBatchStages]);
 
 // stage launchers (all asynchronous on `s`); total = sum of the stage's blocks
 void launch_pack(const Batch& b, int total, const float* src, const float* dst, cudaStream_t s);
@@ -126,11 +127,11 @@ void launch_select(const Batch& b, cudaStream_t s);
 void launch_topk_rest(const Batch& b, const int32_t tot[kNumBatchStages], int max_k1, cudaStream_t s);
 void launch_pgs(const Batch& b, int total, int k2_max, cudaStream_t s);
 void launch_kabsch(const Batch& b, int total, cudaStream_t s);
-void launch_kabsch_fp64_verify(const Batch& b, int total64, int total_verify, cudaStream_t s);
+void launch_kabsch_fp64_verify(const Batch& b, int total64, int total_verify, int pw, cudaStream_t s);
 void launch_kabsch_fp64(const Batch& b, int total64, cudaStream_t s);
 // Kabsch of caller-given k-cliques (k >= 4) into v.rt; idx [m][k] on the device.
 void launch_kabsch_n(const ProbView& v, const int32_t* idx, int k, int m, cudaStream_t s);
-void launch_verify(const Batch& b, int total, cudaStream_t s);
+void launch_verify(const Batch& b, int total, int pw, cudaStream_t s);
 void launch_finalize(const Batch& b, cudaStream_t s);
 
 // set kernel attributes (dynamic shared memory limits) once per device
