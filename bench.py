@@ -18,8 +18,11 @@ roofline: the SC^2 GEMM's mean duration from CUDA events recorded inside the
        replayed graph around that stage, in a third timed pass of the same
        workload (those in-graph events add ~40 us per registration, so the
        two throughput passes run without them).
-Multi-GPU: independent replicas per rank (the path does not shard); value is
-all ranks' registrations / the slowest rank's time.
+Multi-GPU (torchrun, one rank per GPU): a single problem does not shard, so
+each rank registers its own copies of the workload (value = all ranks'
+registrations / the slowest rank's time); the batched leg partitions
+256 x ranks independent problems over the ranks by estimated cost (no
+data-path collective; results gathered on the host).
 --impl reference: the FP64 CPU oracle as the reference arm, same workload.
 """
 from __future__ import annotations
@@ -235,21 +238,29 @@ def cpu_baseline(budget_s=12.0, gpu_results=None):
     return out
 
 
-def run_batched(trg, torch, stream, steps, warmup, flush):
+def run_batched(trg, torch, stream, steps, warmup, flush, ws=1, rank=0):
     """Batched form: 256 problems of uneven N (500..5000), indoor- or outdoor-shaped
     with probability 0.5, inlier ratio 2..20%, registered by one call (one launch
     per stage for all problems, replayed as one CUDA graph).  Timed twice: with
     the shapes' default K1 (2000 indoor, 1000 outdoor) and default tiles, and with
     the autotuner's schedule (tile shapes and K1 per class, tuned on 128 other
-    problems of the same distribution)."""
+    problems of the same distribution).  Under torchrun (ws > 1) the batch
+    holds 256 x ws problems, partitioned over the ranks by estimated cost
+    (no data-path collective); each rank times its share, the time is the
+    slowest rank's and the results are gathered on the host for the success
+    count (weak scaling: about 256 problems per GPU)."""
     import numpy as np
     import synth
-    from paper_2507_01439_gb300 import autotune
-    probs = synth.make_batch(256, seed=4)
+    from paper_2507_01439_gb300 import autotune, shard
+    allp = synth.make_batch(256 * ws, seed=4)
+    parts = shard.partition([shard.problem_cost(p.n, p.k1) for p in allp], ws)
+    probs = [allp[i] for i in parts[rank]]
     offs = np.cumsum([0] + [p.n for p in probs]).astype(np.int64)
     xs = torch.from_numpy(np.concatenate([p.x for p in probs])).cuda()
     ys = torch.from_numpy(np.concatenate([p.y for p in probs])).cuda()
-    ctx = trg.TurboReg(max_n=5000, max_batch=256, stream=stream.cuda_stream)
+    ctx = trg.TurboReg(max_n=5000, max_batch=max(256, len(probs)), stream=stream.cuda_stream)
+    if ws > 1:
+        import torch.distributed as dist
 
     def timed(params):
         out = None
@@ -259,6 +270,8 @@ def run_batched(trg, torch, stream, steps, warmup, flush):
                      and synth.translation_error(p.t_gt, r.t) < p.te_m) for p, r in zip(probs, out))
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
         for k in range(steps):
             with torch.cuda.stream(stream):
                 flush.zero_()
@@ -267,7 +280,14 @@ def run_batched(trg, torch, stream, steps, warmup, flush):
             ev[k][1].record(stream)
         torch.cuda.synchronize()
         mean_ms = sum(a.elapsed_time(b) for a, b in ev) / steps
-        return {"value": 256 / (mean_ms / 1e3), "ms_per_call": mean_ms, "success": f"{ok}/256"}
+        total = len(allp)
+        if ws > 1:
+            t = torch.tensor([mean_ms, float(ok)], device="cuda", dtype=torch.float64)
+            mx = t.clone()
+            dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+            dist.all_reduce(t, op=dist.ReduceOp.SUM)
+            mean_ms, ok = float(mx[0]), int(t[1])
+        return {"value": total / (mean_ms / 1e3), "ms_per_call": mean_ms, "success": f"{ok}/{total}"}
 
     try:
         default = timed([trg.default_params(p.tau, p.k1, p.theta) for p in probs])
@@ -282,8 +302,9 @@ def run_batched(trg, torch, stream, steps, warmup, flush):
     finally:
         ctx.close()
     return {"value": default["value"], "unit": "registrations/s", "problems_per_call": 256,
+            "ranks": ws, "problems_per_rank": [len(p) for p in parts],
             "ms_per_call": default["ms_per_call"], "calls": steps, "n_range": [500, 5000],
-            "mean_n": float(offs[-1] / 256),
+            "mean_n": float(sum(p.n for p in allp) / len(allp)),
             "success": default["success"] + " (indoor RE<15deg TE<0.3m, outdoor RE<5deg TE<0.6m)",
             "default_k1": "2000 indoor-shaped, 1000 outdoor-shaped", "autotuned": tuned,
             "gpu_launches_per_call": 13}
@@ -610,6 +631,11 @@ def run_ours(args):
                 "peak_source": f"{kind}: 2 x bf16_tflops_sustained (FP8/BF16 nominal ratio 4.5/2.25)",
                 "traffic": SC2_DRAM_BYTES, "sc2_ms": sc2_avg_s * 1e3,
                 "flops_per_launch": flops}
+    # the batched leg runs on every rank (its problems are sharded over them)
+    batched = None
+    if not args.no_batched:
+        batched = run_batched(trg, torch, stream, steps=max(3, args.steps // 20), warmup=2, flush=flush,
+                              ws=ws, rank=rank)
     if rank != 0:
         return
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -621,8 +647,8 @@ def run_ours(args):
             "gpu_launches": LAUNCHES_PER_STEP * (2 * args.steps + len(ms_stages)),
             "roofline": roofline, "clocks": clocks,
             "success_rate_check": f"{ok}/8 problems RE<15deg TE<0.3m"}
-    if not args.no_batched:
-        line["batched"] = run_batched(trg, torch, stream, steps=max(3, args.steps // 20), warmup=2, flush=flush)
+    if batched is not None:
+        line["batched"] = batched
         line["gpu_launches"] += line["batched"]["gpu_launches_per_call"] * line["batched"]["calls"] * 2
     if not args.no_learned:
         line["learned"] = run_learned(trg, torch, stream, flush)
