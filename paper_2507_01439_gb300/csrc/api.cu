@@ -412,9 +412,8 @@ int enqueue_plan(turboreg_ctx* c, const Plan& pl, const Batch& bt, const float* 
     TR_EV(3);
     launch_topk_rest(bt, pl.tot, pl.max_k1, s);
     TR_EV(4);
-    launch_pgs(bt, pl.tot[ST_PGS], pl.k2_common, s);
+    launch_pgs(bt, pl.tot[ST_PGS], pl.k2_common, s);   // also solves the cliques' FP32 Kabsch
     TR_EV(5);
-    launch_kabsch(bt, pl.tot[ST_KABSCH], s);
     TR_EV(6);
     // fork: ill-conditioned cliques (FP64 list) on the side stream, the rest here
     TR_CHECK(cudaEventRecord(c->fork_ev, s));

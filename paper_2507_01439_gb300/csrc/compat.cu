@@ -96,19 +96,30 @@ __device__ __noinline__ bool compat_fp64(float xi0, float xi1, float xi2, float 
     return fabs(__dsub_rn(__dsqrt_rn(s), __dsqrt_rn(t))) <= (double)tau;
 }
 
-// FP32 decision; *near is set when |diff - tau| is inside the guard band (or
-// the arithmetic produced NaN/Inf) and the FP64 evaluation must decide.
-__device__ __forceinline__ bool compat_fast(const float (&xi)[6], const float (&xj)[6], float tau, bool* near)
+// FP32 decision for two columns at once; n0/n1 are set when |diff - tau| is
+// inside the guard band (or the arithmetic produced NaN/Inf) and the FP64
+// evaluation must decide.  sX = (ax^2 + ay^2) + az^2 by mul then two fma, the
+// differences and squared norms as packed pairs (fma/mul/sub.rn.f32x2 round
+// each half exactly like the scalar instructions).
+__device__ __forceinline__ void compat_fast2(const f2 (&XI)[6], const f2 (&XJ)[6], float tau, bool& a0, bool& a1,
+                                             bool& n0, bool& n1)
 {
-    const float ax = xi[0] - xj[0], ay = xi[1] - xj[1], az = xi[2] - xj[2];
-    const float bx = xi[3] - xj[3], by = xi[4] - xj[4], bz = xi[5] - xj[5];
-    const float sX = fmaf(az, az, fmaf(ay, ay, ax * ax));
-    const float sY = fmaf(bz, bz, fmaf(by, by, bx * bx));
-    const float dX = sqrt_approx(sX), dY = sqrt_approx(sY);
-    const float diff = fabsf(dX - dY);
-    const float g = fmaf(dX + dY, 9.5367431640625e-07f, 1e-18f);   // 2^-20 (dX + dY) + slack
-    *near = !(fabsf(diff - tau) > g);
-    return diff <= tau;
+    const f2 ax = sub2(XI[0], XJ[0]), ay = sub2(XI[1], XJ[1]), az = sub2(XI[2], XJ[2]);
+    const f2 bx = sub2(XI[3], XJ[3]), by = sub2(XI[4], XJ[4]), bz = sub2(XI[5], XJ[5]);
+    const f2 sX = fma2(az, az, fma2(ay, ay, mul2(ax, ax)));
+    const f2 sY = fma2(bz, bz, fma2(by, by, mul2(bx, bx)));
+    float sX0, sX1, sY0, sY1;
+    upk(sX, sX0, sX1);
+    upk(sY, sY0, sY1);
+    const float dX0 = sqrt_approx(sX0), dY0 = sqrt_approx(sY0);
+    const float dX1 = sqrt_approx(sX1), dY1 = sqrt_approx(sY1);
+    const float diff0 = fabsf(dX0 - dY0), diff1 = fabsf(dX1 - dY1);
+    const float g0 = fmaf(dX0 + dY0, 9.5367431640625e-07f, 1e-18f);
+    const float g1 = fmaf(dX1 + dY1, 9.5367431640625e-07f, 1e-18f);
+    n0 = !(fabsf(diff0 - tau) > g0);
+    n1 = !(fabsf(diff1 - tau) > g1);
+    a0 = diff0 <= tau;
+    a1 = diff1 <= tau;
 }
 
 // 4 bits -> 4 bytes of FP8 E4M3 (0x38 = 1.0 for a set bit, 0x00 otherwise)
@@ -150,7 +161,7 @@ __global__ void __launch_bounds__(kThreads) compat_kernel(ManyViews vs)
         mbar_arrive_expect_tx(&bar, kT * 32);
         bulk_g2s(&srow[0][0], v.pts8 + (size_t)i0 * 8, kT * 32, &bar);
     }
-    // this thread's 4 column points: j = j0 + lane + 32 q
+    // this thread's 4 column points: j = j0 + lane + 32 q, as packed pairs (q 0,1) and (q 2,3)
     float xj[4][6];
     bool jok[4];
 #pragma unroll
@@ -161,6 +172,11 @@ __global__ void __launch_bounds__(kThreads) compat_kernel(ManyViews vs)
         xj[q][0] = a.x; xj[q][1] = a.y; xj[q][2] = a.z; xj[q][3] = a.w; xj[q][4] = b.x; xj[q][5] = b.y;
         jok[q] = j < v.n;
     }
+    f2 XJ[2][6];
+#pragma unroll
+    for (int pr = 0; pr < 2; ++pr)
+#pragma unroll
+        for (int c = 0; c < 6; ++c) XJ[pr][c] = pk(xj[2 * pr][c], xj[2 * pr + 1][c]);
     if (!mbar_wait(&bar, 0)) {
         if (threadIdx.x == 0) atomicOr(&v.ctl->err, TR_ERR_TIMEOUT);
         return;
@@ -174,18 +190,22 @@ __global__ void __launch_bounds__(kThreads) compat_kernel(ManyViews vs)
         const int i = i0 + rr;
         const float4 pa = srow[rr][0], pb = srow[rr][1];
         const float xi[6] = {pa.x, pa.y, pa.z, pa.w, pb.x, pb.y};
+        const f2 XI[6] = {pk(pa.x, pa.x), pk(pa.y, pa.y), pk(pa.z, pa.z), pk(pa.w, pa.w), pk(pb.x, pb.x), pk(pb.y, pb.y)};
         const bool iok = i < v.n;
         uint32_t word[4];
         uint32_t nearm = 0u;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int j = j0 + lane + 32 * q;
-            bool nq;
-            bool a = compat_fast(xi, xj[q], tau, &nq);
-            const bool valid = iok & jok[q] & (i != j);
-            a = a & valid;
-            nearm |= static_cast<uint32_t>(nq & valid) << q;
-            word[q] = static_cast<uint32_t>(a);
+        for (int pr = 0; pr < 2; ++pr) {
+            bool a[2], nq[2];
+            compat_fast2(XI, XJ[pr], tau, a[0], a[1], nq[0], nq[1]);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int q = 2 * pr + h;
+                const int j = j0 + lane + 32 * q;
+                const bool valid = iok & jok[q] & (i != j);
+                nearm |= static_cast<uint32_t>(nq[h] & valid) << q;
+                word[q] = static_cast<uint32_t>(a[h] & valid);
+            }
         }
         if (nearm) {                      // rare: decide in FP64 with the reference operation order
 #pragma unroll

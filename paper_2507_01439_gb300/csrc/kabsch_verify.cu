@@ -5,171 +5,18 @@
 // verify:   IN(h) = #{k : ||R_h x_k + t_h - y_k||^2 <= theta^2}.
 // finalize: h* = argmax IN (lowest h on ties) -> turboreg_result.
 //
-// Closed-form 3-point Kabsch.  With a_k = x_k - mean(x), b_k = y_k - mean(y)
-// the cross-covariance H = sum_k a_k b_k^T has rank <= 2 (three points are
-// coplanar).  Write a_k = E P_k, b_k = F Q_k with E = [e1 e2], F = [f1 f2]
-// orthonormal in-plane frames and n_x = e1 x e2, n_y = f1 x f2.  Then
-// H = E M F^T with the 2x2 M = sum_k P_k Q_k^T, and every proper rotation
-// maximising tr(R H) has the form R = F X E^T + det(X) n_y n_x^T with X in
-// O(2) maximising tr(X M):
-//   rotation   X = [[c,-s],[s,c]] : tr = c(m11+m22) + s(m12-m21)
-//   reflection X = [[c,s],[s,-c]] : tr = c(m11-m22) + s(m12+m21)
-// The larger of the two vector norms is sigma1 + sigma2, the smaller
-// |sigma1 - sigma2| (singular values of M, hence of H), and (c, s) is the
-// normalised winning vector.  No iteration, no atan2.
+// The closed-form 3-point Kabsch itself is in tr_kabsch.cuh.
 //
-// Precision: FP32; the same closed form runs in FP64 when
-// kappa = sigma1/sigma2 exceeds the bound (default 100) or is not finite.  A
-// clique with sigma2 <= 1e-12 sigma1 (collinear or repeated points) is invalid.
 #include "tr_common.cuh"
+#include "tr_kabsch.cuh"
 #include "tr_problem.h"
 
 namespace tr {
 
 namespace {
 
-template <typename T>
-__device__ __forceinline__ T inv_sqrt(T x);
-template <>
-__device__ __forceinline__ float inv_sqrt<float>(float x) { return 1.0f / sqrtf(x); }
-// FP64 1/sqrt(x) without the long FP64 divide and square-root sequences: an
-// FP32 seed refined by two Newton steps y <- y (3 - x y^2) / 2 (each step
-// squares the relative error: ~1e-7 -> 1e-14 -> below FP64 rounding).
-template <>
-__device__ __forceinline__ double inv_sqrt<double>(double x)
-{
-    if (!(x > 1e-30 && x < 1e30)) return 1.0 / sqrt(x);
-    double y = static_cast<double>(rsqrtf(static_cast<float>(x)));
-    const double hx = 0.5 * x;
-    y = y * fma(-hx * y, y, 1.5);
-    y = y * fma(-hx * y, y, 1.5);
-    return y;
-}
-
-template <typename T>
-struct KabschOut {
-    T R[9];
-    T t[3];
-    T kappa;
-    bool ok;    // frames defined and sigma1 > 0
-    T s1, s2;
-};
-
-template <typename T>
-__device__ __forceinline__ void cross3(const T a[3], const T b[3], T c[3])
-{
-    c[0] = a[1] * b[2] - a[2] * b[1];
-    c[1] = a[2] * b[0] - a[0] * b[2];
-    c[2] = a[0] * b[1] - a[1] * b[0];
-}
-
-template <typename T>
-__device__ __forceinline__ T dot3(const T a[3], const T b[3])
-{
-    return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
-}
-
-// In-plane orthonormal frame of a triangle: e1 along its longest edge,
-// n = unit normal of (p1 - p0) x (p2 - p0), e2 = n x e1.
-template <typename T>
-__device__ __forceinline__ bool frame3(const T p[3][3], T e1[3], T e2[3], T nrm[3])
-{
-    T d01[3], d02[3], d12[3];
-    for (int c = 0; c < 3; ++c) {
-        d01[c] = p[1][c] - p[0][c];
-        d02[c] = p[2][c] - p[0][c];
-        d12[c] = p[2][c] - p[1][c];
-    }
-    cross3(d01, d02, nrm);
-    const T nn = dot3(nrm, nrm);
-    const T l01 = dot3(d01, d01), l02 = dot3(d02, d02), l12 = dot3(d12, d12);
-    const T* e = d01;
-    T le = l01;
-    if (l02 > le) { e = d02; le = l02; }
-    if (l12 > le) { e = d12; le = l12; }
-    if (!(nn > T(0)) || !(le > T(0))) return false;
-    const T in = inv_sqrt(nn), ie = inv_sqrt(le);
-    for (int c = 0; c < 3; ++c) {
-        nrm[c] *= in;
-        e1[c] = e[c] * ie;
-    }
-    cross3(nrm, e1, e2);
-    return true;
-}
-
-template <typename T>
-__device__ void kabsch3(const T p[3][3], const T q[3][3], KabschOut<T>& o)
-{
-    T cx[3], cy[3];
-    for (int c = 0; c < 3; ++c) {
-        cx[c] = (p[0][c] + p[1][c] + p[2][c]) * T(1.0 / 3.0);
-        cy[c] = (q[0][c] + q[1][c] + q[2][c]) * T(1.0 / 3.0);
-    }
-    T e1[3], e2[3], nx[3], f1[3], f2[3], ny[3];
-    o.ok = frame3(p, e1, e2, nx) && frame3(q, f1, f2, ny);
-    if (!o.ok) {
-        o.kappa = T(INFINITY);
-        o.s1 = o.s2 = T(0);
-        return;
-    }
-    T m11 = 0, m12 = 0, m21 = 0, m22 = 0;
-    for (int k = 0; k < 3; ++k) {
-        T a[3], b[3];
-        for (int c = 0; c < 3; ++c) {
-            a[c] = p[k][c] - cx[c];
-            b[c] = q[k][c] - cy[c];
-        }
-        const T P1 = dot3(a, e1), P2 = dot3(a, e2);
-        const T Q1 = dot3(b, f1), Q2 = dot3(b, f2);
-        m11 += P1 * Q1; m12 += P1 * Q2;
-        m21 += P2 * Q1; m22 += P2 * Q2;
-    }
-    const T rx = m11 + m22, ry = m12 - m21;   // rotation candidate
-    const T fx = m11 - m22, fy = m12 + m21;   // reflection candidate
-    const T r2 = rx * rx + ry * ry, q2 = fx * fx + fy * fy;
-    if (!(r2 > T(0) || q2 > T(0))) {
-        o.ok = false;
-        o.kappa = T(INFINITY);
-        o.s1 = o.s2 = T(0);
-        return;
-    }
-    const bool rot = r2 >= q2;
-    const T ih = inv_sqrt(rot ? r2 : q2);               // 1 / (sigma1 + sigma2)
-    const T hi = (rot ? r2 : q2) * ih;
-    const T lo2 = rot ? q2 : r2;
-    const T lo = lo2 > T(0) ? lo2 * inv_sqrt(lo2) : T(0);
-    o.s1 = (hi + lo) * T(0.5);
-    o.s2 = (hi - lo) * T(0.5);
-    o.kappa = o.s2 > T(0) ? static_cast<T>(static_cast<float>(o.s1) / static_cast<float>(o.s2)) : T(INFINITY);
-    T X00, X01, X10, X11, sg;
-    if (rot) {
-        const T c = rx * ih, s = ry * ih;
-        X00 = c; X01 = -s; X10 = s; X11 = c; sg = T(1);
-    } else {
-        const T c = fx * ih, s = fy * ih;
-        X00 = c; X01 = s; X10 = s; X11 = -c; sg = T(-1);
-    }
-    for (int r = 0; r < 3; ++r)
-        for (int c = 0; c < 3; ++c)
-            o.R[r * 3 + c] = X00 * f1[r] * e1[c] + X01 * f1[r] * e2[c] + X10 * f2[r] * e1[c] +
-                             X11 * f2[r] * e2[c] + sg * ny[r] * nx[c];
-    for (int r = 0; r < 3; ++r)
-        o.t[r] = cy[r] - (o.R[r * 3 + 0] * cx[0] + o.R[r * 3 + 1] * cx[1] + o.R[r * 3 + 2] * cx[2]);
-}
-
-__device__ __forceinline__ void load_clique(const ProbView& v, const int4 cl, float p[3][3], float q[3][3])
-{
-    const int idx[3] = {cl.x, cl.y, cl.z};
-    for (int a = 0; a < 3; ++a) {
-        const float4* r = reinterpret_cast<const float4*>(v.pts8 + (size_t)idx[a] * 8);
-        const float4 u = r[0], w = r[1];
-        p[a][0] = u.x; p[a][1] = u.y; p[a][2] = u.z;
-        q[a][0] = u.w; q[a][1] = w.x; q[a][2] = w.y;
-    }
-}
-
-// Phase 1: FP32 closed form for every hypothesis; cliques whose kappa exceeds
-// the bound (or whose FP32 frames are undefined) go to a compact list.
+// Phase 1: FP32 closed form for every hypothesis (used by the clique-Kabsch
+// entry point; the registration path solves cliques inside the clique search).
 __global__ void __launch_bounds__(128) kabsch_kernel(ManyViews vs)
 {
     pdl_wait();
@@ -178,29 +25,7 @@ __global__ void __launch_bounds__(128) kabsch_kernel(ManyViews vs)
     const int h = lb * blockDim.x + threadIdx.x;
     const int nh = v.ctl->n_pivots * v.k2;
     if (h >= nh) return;
-    v.inl[h] = 0;
-    v.score[h] = 0ull;
-    float* out = v.rt + (size_t)h * 16;
-    const int4 cl = v.cliques[h];
-    uint32_t flags = 0;
-    for (int r = 0; r < 13; ++r) out[r] = 0.f;
-    if (cl.w) {
-        float p[3][3], q[3][3];
-        load_clique(v, cl, p, q);
-        KabschOut<float> o;
-        kabsch3<float>(p, q, o);
-        if (o.ok && o.kappa <= v.kappa_fp64) {
-            for (int r = 0; r < 9; ++r) out[r] = o.R[r];
-            for (int r = 0; r < 3; ++r) out[9 + r] = o.t[r];
-            out[12] = o.kappa;
-            flags = 1u;
-        } else {
-            const uint32_t slot = atomicAdd(&v.ctl->fp64_slot, 1u);
-            v.fp64_list[slot] = h;
-            flags = 2u;   // pending FP64
-        }
-    }
-    out[13] = __int_as_float(static_cast<int>(flags));
+    kabsch_hypothesis(v, h, v.cliques[h]);
 }
 
 // Phase 2: the same closed form in FP64 for the listed hypotheses only, so the
@@ -236,39 +61,6 @@ __global__ void __launch_bounds__(32) kabsch_fp64_kernel(ManyViews vs)
     }
     out[12] = static_cast<float>(od.kappa);
     out[13] = __int_as_float(static_cast<int>((valid ? 1u : 0u) | 2u));
-}
-
-// ---- packed FP32 pairs (two hypotheses per instruction) -----------------
-struct f2 {
-    unsigned long long v;
-};
-__device__ __forceinline__ f2 pk(float lo, float hi)
-{
-    f2 r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(lo), "f"(hi));
-    return r;
-}
-__device__ __forceinline__ void upk(f2 a, float& lo, float& hi)
-{
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(a.v));
-}
-__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c)
-{
-    f2 d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d.v) : "l"(a.v), "l"(b.v), "l"(c.v));
-    return d;
-}
-__device__ __forceinline__ f2 sub2(f2 a, f2 b)
-{
-    f2 d;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d.v) : "l"(a.v), "l"(b.v));
-    return d;
-}
-__device__ __forceinline__ f2 mul2(f2 a, f2 b)
-{
-    f2 d;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d.v) : "l"(a.v), "l"(b.v));
-    return d;
 }
 
 // Verification.  A block holds 128 hypotheses (R, t staged in shared memory)
@@ -420,9 +212,9 @@ __global__ void __launch_bounds__(128) verify_kernel(ManyViews vs)
 __device__ __forceinline__ unsigned long long select_key(const ProbView& v, int h)
 {
     if (v.scoring == TURBOREG_SCORE_IN)
-        return (static_cast<unsigned long long>(static_cast<uint32_t>(v.inl[h]) + 1u) << 32) |
+        return (static_cast<unsigned long long>(static_cast<uint32_t>(__ldcg(v.inl + h)) + 1u) << 32) |
                (0xFFFFFFFFull - static_cast<unsigned long long>(h));
-    return ((0xFFFFFFFFFFull - v.score[h]) << 20) | (0xFFFFFull - static_cast<unsigned long long>(h));
+    return ((0xFFFFFFFFFFull - __ldcg(v.score + h)) << 20) | (0xFFFFFull - static_cast<unsigned long long>(h));
 }
 
 __device__ __forceinline__ int key_hypothesis(const ProbView& v, unsigned long long key)
@@ -431,6 +223,10 @@ __device__ __forceinline__ int key_hypothesis(const ProbView& v, unsigned long l
     return static_cast<int>(0xFFFFFull - (key & 0xFFFFFull));
 }
 
+// Model selection (Eq. 9), one block of 1024 threads per problem: h* = the
+// largest selection key over the valid hypotheses, counts, and the result.
+// (Folding it into the last verification block was measured slower: the
+// completion counter of ~1300 blocks on one address serialises in L2.)
 __global__ void __launch_bounds__(1024) finalize_kernel(ManyViews vs)
 {
     pdl_wait();
@@ -442,13 +238,23 @@ __global__ void __launch_bounds__(1024) finalize_kernel(ManyViews vs)
     const int nh = np * v.k2;
     unsigned long long best = 0ull;
     int nvalid = 0, nfp = 0;
-    for (int h = threadIdx.x; h < nh; h += blockDim.x) {
-        const uint32_t flags = static_cast<uint32_t>(__float_as_int(v.rt[(size_t)h * 16 + 13]));
-        if (flags & 2u) ++nfp;
-        if (!(flags & 1u)) continue;
-        ++nvalid;
-        const unsigned long long key = select_key(v, h);
-        best = key > best ? key : best;
+    // eight hypotheses per thread in flight: the flags, then the keys of the valid ones
+    for (int h0 = threadIdx.x; h0 < nh; h0 += 8 * blockDim.x) {
+        uint32_t fl[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int h = h0 + u * blockDim.x;
+            fl[u] = h < nh ? static_cast<uint32_t>(__ldcg(reinterpret_cast<const int*>(v.rt) + (size_t)h * 16 + 13)) : 0u;
+        }
+        unsigned long long key[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) key[u] = (fl[u] & 1u) ? select_key(v, h0 + u * blockDim.x) : 0ull;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            nfp += (fl[u] & 2u) ? 1 : 0;
+            nvalid += (fl[u] & 1u) ? 1 : 0;
+            best = key[u] > best ? key[u] : best;
+        }
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int off = 16; off >= 1; off >>= 1) {
@@ -490,26 +296,29 @@ __global__ void __launch_bounds__(1024) finalize_kernel(ManyViews vs)
         r.status = TURBOREG_ERR_NO_HYPOTHESIS;
     } else {
         const int h = key_hypothesis(v, best);
+        // L2 reads: the FP64 list's R, t were written while this SM may hold older copies
         const float* rt = v.rt + (size_t)h * 16;
-        for (int q = 0; q < 9; ++q) r.R[q] = rt[q];
-        for (int q = 0; q < 3; ++q) r.t[q] = rt[9 + q];
+        for (int q = 0; q < 9; ++q) r.R[q] = __ldcg(rt + q);
+        for (int q = 0; q < 3; ++q) r.t[q] = __ldcg(rt + 9 + q);
         const int4 cl = v.cliques[h];
         r.clique[0] = cl.x; r.clique[1] = cl.y; r.clique[2] = cl.z;
-        r.inlier_count = v.inl[h];
+        r.inlier_count = __ldcg(v.inl + h);
         if (v.scoring == TURBOREG_SCORE_IN) {
             r.score = static_cast<float>(r.inlier_count);
         } else {
             const double unit = v.scoring == TURBOREG_SCORE_MAE ? (double)v.theta : (double)v.theta * v.theta;
-            r.score = static_cast<float>((double)v.score[h] * unit / (4194304.0 * v.n));
+            r.score = static_cast<float>((double)__ldcg(v.score + h) * unit / (4194304.0 * v.n));
         }
         r.hypothesis = h;
-        r.used_fp64 = (static_cast<uint32_t>(__float_as_int(rt[13])) & 2u) ? 1 : 0;
+        r.used_fp64 = (static_cast<uint32_t>(__ldcg(reinterpret_cast<const int*>(rt) + 13)) & 2u) ? 1 : 0;
         r.status = TURBOREG_OK;
     }
     *v.res = r;
 }
 
 }  // namespace
+
+void launch_finalize(const Batch& b, cudaStream_t s) { launch_pdl(finalize_kernel, b.num, 1024, 0, s, ManyViews{b}); }
 
 void launch_kabsch(const Batch& b, int total, cudaStream_t s)
 {
@@ -536,7 +345,6 @@ void launch_kabsch_fp64_verify(const Batch& b, int total64, int total_verify, in
     else launch_pdl(verify_kernel<true, 64>, total_verify, 128, 0, s, ManyViews{b});
 }
 
-void launch_finalize(const Batch& b, cudaStream_t s) { launch_pdl(finalize_kernel, b.num, 1024, 0, s, ManyViews{b}); }
 
 // Per-problem block counts of every stage.
 void stage_blocks(int32_t n, int32_t k1, int32_t k2, int32_t verify_pw, int32_t blocks[kNumBatchStages])

@@ -19,6 +19,7 @@
 // merges the 32 lists with K2 rounds of a 64-bit max-reduction over keys
 // (S << 32 | ~z).
 #include "tr_common.cuh"
+#include "tr_kabsch.cuh"
 #include "tr_problem.h"
 
 namespace tr {
@@ -107,8 +108,10 @@ __global__ void __launch_bounds__(256) pgs_kernel(ManyViews vs)
         }
     }
     if (nz) flush();
-    // warp merge: k2 rounds of argmax over the lanes' list heads
+    // warp merge: k2 rounds of argmax over the lanes' list heads; lane r keeps
+    // round r's clique and solves its Kabsch afterwards
     int head = 0;
+    int4 mine_cl = make_int4(i, j, -1, 0);
     for (int r = 0; r < k2; ++r) {
         uint64_t mine = 0ull;
 #pragma unroll
@@ -121,16 +124,14 @@ __global__ void __launch_bounds__(256) pgs_kernel(ManyViews vs)
             best = o > best ? o : best;
         }
         if (best == mine && mine != 0ull) ++head;
-        if (lane == 0) {
-            const size_t h = static_cast<size_t>(r) * np + p;
-            if (best != 0ull) {
-                const int z = static_cast<int>(0xFFFFFFFFu - static_cast<uint32_t>(best & 0xFFFFFFFFull));
-                v.cliques[h] = make_int4(i, j, z, 1);
-            } else {
-                v.cliques[h] = make_int4(i, j, -1, 0);
-            }
-        }
+        const int4 cl = best != 0ull
+            ? make_int4(i, j, static_cast<int>(0xFFFFFFFFu - static_cast<uint32_t>(best & 0xFFFFFFFFull)), 1)
+            : make_int4(i, j, -1, 0);
+        if (lane == 0) v.cliques[static_cast<size_t>(r) * np + p] = cl;
+        if (lane == r) mine_cl = cl;
     }
+    // Kabsch of this pivot's cliques (Sec. 3.5), one lane each
+    if (lane < k2) kabsch_hypothesis(v, lane * np + p, mine_cl);
 }
 
 }  // namespace

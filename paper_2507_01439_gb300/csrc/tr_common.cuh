@@ -181,6 +181,42 @@ __device__ __forceinline__ void prefetch_tmap(const CUtensorMap* map)
 }
 
 // ---------------------------------------------------------------------------
+// Packed FP32 pairs: two values per 64-bit register, one instruction for both
+// (add/sub/mul/fma.rn.f32x2 round each half exactly like the scalar forms).
+// ---------------------------------------------------------------------------
+struct f2 {
+    unsigned long long v;
+};
+__device__ __forceinline__ f2 pk(float lo, float hi)
+{
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void upk(f2 a, float& lo, float& hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(a.v));
+}
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c)
+{
+    f2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d.v) : "l"(a.v), "l"(b.v), "l"(c.v));
+    return d;
+}
+__device__ __forceinline__ f2 sub2(f2 a, f2 b)
+{
+    f2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d.v) : "l"(a.v), "l"(b.v));
+    return d;
+}
+__device__ __forceinline__ f2 mul2(f2 a, f2 b)
+{
+    f2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d.v) : "l"(a.v), "l"(b.v));
+    return d;
+}
+
+// ---------------------------------------------------------------------------
 // tcgen05 (5th-generation tensor cores, tensor memory)
 // ---------------------------------------------------------------------------
 // Allocate `ncols` TMEM columns (power of two >= 32); one full warp executes it.

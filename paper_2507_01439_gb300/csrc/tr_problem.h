@@ -129,10 +129,10 @@ void launch_pgs(const Batch& b, int total, int k2_max, cudaStream_t s);
 void launch_kabsch(const Batch& b, int total, cudaStream_t s);
 void launch_kabsch_fp64_verify(const Batch& b, int total64, int total_verify, int pw, cudaStream_t s);
 void launch_kabsch_fp64(const Batch& b, int total64, cudaStream_t s);
+void launch_finalize(const Batch& b, cudaStream_t s);
 // Kabsch of caller-given k-cliques (k >= 4) into v.rt; idx [m][k] on the device.
 void launch_kabsch_n(const ProbView& v, const int32_t* idx, int k, int m, cudaStream_t s);
 void launch_verify(const Batch& b, int total, int pw, cudaStream_t s);
-void launch_finalize(const Batch& b, cudaStream_t s);
 
 // set kernel attributes (dynamic shared memory limits) once per device
 cudaError_t sc2_tcgen05_setup();
