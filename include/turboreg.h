@@ -90,8 +90,10 @@ typedef struct {
     float inlier_thresh;  /* theta: a match is an inlier of (R,t) iff ||R x + t - y|| <= theta, > 0 */
     int32_t graph_mode;   /* TURBOREG_GRAPH_O2 or TURBOREG_GRAPH_SC2 */
     int32_t proposal;     /* TURBOREG_PROPOSAL_PLAIN or _LEARNED */
-    float kappa_fp64;     /* Kabsch runs in FP64 when sigma1/sigma2 of the 3x3 cross-covariance
-                             exceeds this bound (0 selects the default 100) */
+    float kappa_fp64;     /* when sigma1/sigma2 of a clique's 3x3 cross-covariance exceeds this
+                             bound (0 selects the default 100), its closed-form Kabsch is redone
+                             with the triangle normals computed in FP64 (the ill-conditioned
+                             step; the rest stays FP32) */
     uint32_t flags;       /* TURBOREG_FLAG_* */
     int32_t learned_min_inliers; /* learned proposal: if its best inlier number is below this (or it
                                     finds no hypothesis) the plain proposal decides the result;
@@ -107,7 +109,7 @@ typedef struct {
     int32_t hypothesis;     /* h* in Alg. 2 order h = r*|P| + p, lowest h on ties; -1 if none */
     int32_t n_pivots;       /* |P| = min(K1, number of O2Graph edges) */
     int32_t n_valid;        /* hypotheses with a TurboClique and a non-degenerate Kabsch */
-    int32_t used_fp64;      /* 1 if the winner's Kabsch ran in FP64 */
+    int32_t used_fp64;      /* 1 if the winner's Kabsch used the FP64 normals (see kappa_fp64) */
     int32_t used_fallback;  /* learned proposal: 1 if the plain path decided the result */
     int32_t status;         /* turboreg_status of this problem */
     float score;            /* the winner's selection score: the inlier number (SCORE_IN), or its

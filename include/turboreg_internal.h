@@ -74,8 +74,8 @@ int turboreg_score_transforms(turboreg_ctx* ctx, const float* src, const float* 
 /* Kabsch of caller-given cliques (Sec. 3.5; the 3-clique vs 10-clique
  * comparison of App. A.2): for each of m tuples of k match indices, the
  * proper rotation R and translation t minimising sum ||R x + t - y||^2 over
- * the tuple's matches.  k = 3 runs the registration path's kernels (FP32
- * closed form, FP64 above params->kappa_fp64); 4 <= k <= 32 runs Horn's
+ * the tuple's matches.  k = 3 runs the registration path's closed form (FP32,
+ * FP64 normals above params->kappa_fp64); 4 <= k <= 32 runs Horn's
  * quaternion method with Jacobi eigen-decomposition in FP64.
  * src, dst: float32 [n][3], host or device.  idx: HOST int32 [m][k], every
  * index in [0, n).  m >= 1 and m * k <= 4 * TURBOREG_K1_MAX * TURBOREG_K2_MAX.

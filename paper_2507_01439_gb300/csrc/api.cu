@@ -56,7 +56,6 @@ struct Workspace {
     float* rt = nullptr;             // [slots][nh * 16]
     int32_t* inl = nullptr;          // [slots][nh]
     unsigned long long* score = nullptr;  // [slots][nh]
-    int32_t* fp64_list = nullptr;    // [slots][nh]
     float* feat = nullptr;           // [slots][np][8] proposal features
     float* prob = nullptr;           // [slots][np] proposal probabilities
     Ctl* ctl = nullptr;              // [slots]
@@ -95,8 +94,6 @@ struct turboreg_ctx {
     int32_t max_n = 0, max_batch = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
-    cudaStream_t side = nullptr;                       // FP64 Kabsch + its verification run here,
-    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;  // concurrently with the main verification
     Workspace ws;
     turboreg_result* host_res = nullptr;   // pinned [max_batch]
     float* mlp_wbf = nullptr;              // proposal model (BF16-rounded FP32 values), device
@@ -152,7 +149,7 @@ cudaError_t halloc(T** p, size_t count)
 void free_ws(Workspace& ws)
 {
     void* dptrs[] = {ws.pts, ws.pts8, ws.a8, ws.bits, ws.w, ws.rows, ws.hist, ws.cand, ws.piv, ws.cliques,
-                     ws.rt, ws.inl, ws.score, ws.fp64_list, ws.feat, ws.prob, ws.ctl, ws.res, ws.in_src, ws.in_dst,
+                     ws.rt, ws.inl, ws.score, ws.feat, ws.prob, ws.ctl, ws.res, ws.in_src, ws.in_dst,
                      ws.desc};
     for (void* p : dptrs)
         if (p) cudaFree(p);
@@ -187,7 +184,6 @@ int alloc_ws(Workspace& ws, int32_t max_n, int32_t slots)
     if (e == cudaSuccess) e = dalloc(&ws.rt, S * nh * 16);
     if (e == cudaSuccess) e = dalloc(&ws.inl, S * nh);
     if (e == cudaSuccess) e = dalloc(&ws.score, S * nh);
-    if (e == cudaSuccess) e = dalloc(&ws.fp64_list, S * nh);
     if (e == cudaSuccess) e = dalloc(&ws.feat, S * np * 8);
     if (e == cudaSuccess) e = dalloc(&ws.prob, S * np);
     if (e == cudaSuccess) e = dalloc(&ws.ctl, S);
@@ -288,7 +284,6 @@ ProbView make_view(turboreg_ctx* c, int slot, int64_t in_off, int32_t n, const t
     v.rt = ws.rt + s * ws.nh * 16;
     v.inl = ws.inl + s * ws.nh;
     v.score = ws.score + s * ws.nh;
-    v.fp64_list = ws.fp64_list + s * ws.nh;
     v.feat = ws.feat + s * np * 8;
     v.prob = p->proposal == TURBOREG_PROPOSAL_LEARNED ? ws.prob + s * np : nullptr;
     v.ctl = ws.ctl + s;
@@ -412,16 +407,10 @@ int enqueue_plan(turboreg_ctx* c, const Plan& pl, const Batch& bt, const float* 
     TR_EV(3);
     launch_topk_rest(bt, pl.tot, pl.max_k1, s);
     TR_EV(4);
-    launch_pgs(bt, pl.tot[ST_PGS], pl.k2_common, s);   // also solves the cliques' FP32 Kabsch
+    launch_pgs(bt, pl.tot[ST_PGS], pl.k2_common, s);   // also solves the cliques' Kabsch
     TR_EV(5);
     TR_EV(6);
-    // fork: ill-conditioned cliques (FP64 list) on the side stream, the rest here
-    TR_CHECK(cudaEventRecord(c->fork_ev, s));
-    TR_CHECK(cudaStreamWaitEvent(c->side, c->fork_ev, 0));
-    launch_kabsch_fp64_verify(bt, pl.tot[ST_KABSCH64], pl.tot[ST_VERIFY], pl.vpw, c->side);
-    TR_CHECK(cudaEventRecord(c->join_ev, c->side));
     launch_verify(bt, pl.tot[ST_VERIFY], pl.vpw, s);
-    TR_CHECK(cudaStreamWaitEvent(s, c->join_ev, 0));
     TR_EV(7);
     launch_finalize(bt, s);
     TR_EV(8);
@@ -637,12 +626,6 @@ int turboreg_create(int device, int32_t max_n, int32_t max_batch, void* cuda_str
             return TURBOREG_ERR_CUDA;
         }
     }
-    if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&c->join_ev, cudaEventDisableTiming) != cudaSuccess) {
-        turboreg_destroy(c);
-        return TURBOREG_ERR_CUDA;
-    }
     cudaDriverEntryPointQueryResult q;
     void* fn = nullptr;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
@@ -670,13 +653,9 @@ void turboreg_destroy(turboreg_ctx* c)
     if (!c) return;
     cudaSetDevice(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
-    if (c->side) cudaStreamSynchronize(c->side);
     for (auto& sl : c->gslot) drop_slot(sl);
     for (int k = 0; k <= kNumStages; ++k)
         if (c->ev[k]) cudaEventDestroy(c->ev[k]);
-    if (c->fork_ev) cudaEventDestroy(c->fork_ev);
-    if (c->join_ev) cudaEventDestroy(c->join_ev);
-    if (c->side) cudaStreamDestroy(c->side);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     free_ws(c->ws);
     if (c->host_res) cudaFreeHost(c->host_res);
@@ -1064,7 +1043,6 @@ int turboreg_kabsch_cliques(turboreg_ctx* c, const float* src, const float* dst,
                                  c->stream));
         TR_CHECK(cudaMemcpyAsync(&v.ctl->n_pivots, &q.k1, sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
         launch_kabsch(bt, pl.tot[ST_KABSCH], c->stream);
-        launch_kabsch_fp64(bt, pl.tot[ST_KABSCH64], c->stream);
     } else {
         // the tuples go to the (otherwise unused here) clique buffer, as int32 [m][k]
         int32_t* didx = reinterpret_cast<int32_t*>(v.cliques);

@@ -15,8 +15,8 @@ namespace tr {
 
 namespace {
 
-// Phase 1: FP32 closed form for every hypothesis (used by the clique-Kabsch
-// entry point; the registration path solves cliques inside the clique search).
+// Closed form for every hypothesis (used by the clique-Kabsch entry point; the
+// registration path solves cliques inside the clique search).
 __global__ void __launch_bounds__(128) kabsch_kernel(ManyViews vs)
 {
     pdl_wait();
@@ -28,49 +28,13 @@ __global__ void __launch_bounds__(128) kabsch_kernel(ManyViews vs)
     kabsch_hypothesis(v, h, v.cliques[h]);
 }
 
-// Phase 2: the same closed form in FP64 for the listed hypotheses only, so the
-// slow FP64 pipe runs on dense warps instead of on every warp that holds one.
-// On this GPU one FP64 FMA warp instruction occupies the FP64 pipe for about
-// 69 cycles whatever the number of active lanes (measured), so the kernel is
-// latency-bound at ~15 us per warp; a float-float (paired FP32) version of the
-// same closed form measured no faster (its longer straight-line code stalls
-// on instruction fetch), so FP64 stays.
-__global__ void __launch_bounds__(32) kabsch_fp64_kernel(ManyViews vs)
-{
-    pdl_wait();
-    int lb;
-    const ProbView v = vs.get(ST_KABSCH64, blockIdx.x, lb);
-    const int k = lb * blockDim.x + threadIdx.x;
-    if (k >= static_cast<int>(v.ctl->fp64_slot)) return;
-    const int h = v.fp64_list[k];
-    float* out = v.rt + (size_t)h * 16;
-    float p[3][3], q[3][3];
-    load_clique(v, v.cliques[h], p, q);
-    double pd[3][3], qd[3][3];
-    for (int a = 0; a < 3; ++a)
-        for (int c = 0; c < 3; ++c) {
-            pd[a][c] = p[a][c];
-            qd[a][c] = q[a][c];
-        }
-    KabschOut<double> od;
-    kabsch3<double>(pd, qd, od);
-    const bool valid = od.ok && od.s1 > 0.0 && od.s2 > 1e-12 * od.s1;
-    if (valid) {
-        for (int r = 0; r < 9; ++r) out[r] = static_cast<float>(od.R[r]);
-        for (int r = 0; r < 3; ++r) out[9 + r] = static_cast<float>(od.t[r]);
-    }
-    out[12] = static_cast<float>(od.kappa);
-    out[13] = __int_as_float(static_cast<int>((valid ? 1u : 0u) | 2u));
-}
-
 // Verification.  A block holds 128 hypotheses (R, t staged in shared memory)
 // and 256 correspondences (32-byte records); each of its 4 warps takes 64 of
 // the correspondences for all 128 hypotheses, 4 per lane, evaluated as two
 // packed pairs: e = R x + (t - y), d2 = |e|^2 with fma.rn.f32x2 (the same
 // rounding as the scalar expression, two hypotheses per instruction).  The
 // warps' counts are summed in shared memory; one atomic per hypothesis.
-// kList: hypotheses are the entries of the FP64 Kabsch list; otherwise the
-// hypotheses whose FP32 Kabsch is valid (flags == 1).
+// Hypotheses whose Kabsch is valid (flags bit 1) are evaluated.
 //
 // Capped-error scores (MAE, MSE of the ranking study, Table 6): each match
 // adds min(e, theta) or min(e^2, theta^2), rounded to an integer number of
@@ -92,13 +56,13 @@ struct VerifyShared {
     int sok[kVHyp];
 };
 
-template <bool kList, int kScore, int PW>
+template <int kScore, int PW>
 __device__ __forceinline__ void verify_body(const ProbView& v, int lb, VerifyShared<PW>& sh)
 {
     constexpr int kVPtsWarp = PW;
     constexpr int kVPts = kVWarps * PW;
     const int npb = (v.n + kVPts - 1) / kVPts;          // point blocks of this problem
-    const int nh = kList ? static_cast<int>(v.ctl->fp64_slot) : v.ctl->n_pivots * v.k2;
+    const int nh = v.ctl->n_pivots * v.k2;
     const int h0 = (lb / npb) * kVHyp;
     if (h0 >= nh) return;
     const int k0 = (lb % npb) * kVPts;
@@ -110,11 +74,11 @@ __device__ __forceinline__ void verify_body(const ProbView& v, int lb, VerifySha
         float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0, r3 = r0;
         bool ok = false;
         if (slot < nh) {
-            const int h = kList ? v.fp64_list[slot] : slot;
+            const int h = slot;
             const float4* rt = reinterpret_cast<const float4*>(v.rt + (size_t)h * 16);
             r0 = rt[0]; r1 = rt[1]; r2 = rt[2]; r3 = rt[3];
             const int flags = __float_as_int(r3.y);
-            ok = kList ? (flags & 1) != 0 : flags == 1;
+            ok = (flags & 1) != 0;
             if (!ok) r2.y = r2.z = r2.w = __int_as_float(0x7fc00000);   // NaN t: never an inlier
         } else {
             r2.y = r2.z = r2.w = __int_as_float(0x7fc00000);
@@ -181,7 +145,7 @@ __device__ __forceinline__ void verify_body(const ProbView& v, int lb, VerifySha
     const int t = threadIdx.x;
     const int slot = h0 + t;
     if (slot >= nh) return;
-    const int hh = kList ? v.fp64_list[slot] : slot;
+    const int hh = slot;
     const int tot = sh.scnt[0][t] + sh.scnt[1][t] + sh.scnt[2][t] + sh.scnt[3][t];
     if (tot) atomicAdd(&v.inl[hh], tot);
     if (kScore != TURBOREG_SCORE_IN && sh.sok[t]) {
@@ -191,7 +155,7 @@ __device__ __forceinline__ void verify_body(const ProbView& v, int lb, VerifySha
     }
 }
 
-template <bool kList, int PW>
+template <int PW>
 __global__ void __launch_bounds__(128) verify_kernel(ManyViews vs)
 {
     pdl_wait();
@@ -199,9 +163,9 @@ __global__ void __launch_bounds__(128) verify_kernel(ManyViews vs)
     int lb;
     const ProbView v = vs.get(ST_VERIFY, blockIdx.x, lb);
     switch (v.scoring) {      // uniform over the block: a block serves one problem
-        case TURBOREG_SCORE_MAE: verify_body<kList, TURBOREG_SCORE_MAE, PW>(v, lb, sh); break;
-        case TURBOREG_SCORE_MSE: verify_body<kList, TURBOREG_SCORE_MSE, PW>(v, lb, sh); break;
-        default: verify_body<kList, TURBOREG_SCORE_IN, PW>(v, lb, sh); break;
+        case TURBOREG_SCORE_MAE: verify_body<TURBOREG_SCORE_MAE, PW>(v, lb, sh); break;
+        case TURBOREG_SCORE_MSE: verify_body<TURBOREG_SCORE_MSE, PW>(v, lb, sh); break;
+        default: verify_body<TURBOREG_SCORE_IN, PW>(v, lb, sh); break;
     }
 }
 
@@ -327,24 +291,10 @@ void launch_kabsch(const Batch& b, int total, cudaStream_t s)
 
 void launch_verify(const Batch& b, int total, int pw, cudaStream_t s)
 {
-    if (pw == 32) launch_pdl(verify_kernel<false, 32>, total, 128, 0, s, ManyViews{b});
-    else if (pw == 128) launch_pdl(verify_kernel<false, 128>, total, 128, 0, s, ManyViews{b});
-    else launch_pdl(verify_kernel<false, 64>, total, 128, 0, s, ManyViews{b});
+    if (pw == 32) launch_pdl(verify_kernel<32>, total, 128, 0, s, ManyViews{b});
+    else if (pw == 128) launch_pdl(verify_kernel<128>, total, 128, 0, s, ManyViews{b});
+    else launch_pdl(verify_kernel<64>, total, 128, 0, s, ManyViews{b});
 }
-
-void launch_kabsch_fp64(const Batch& b, int total64, cudaStream_t s)
-{
-    launch_pdl(kabsch_fp64_kernel, total64, 32, 0, s, ManyViews{b});
-}
-
-void launch_kabsch_fp64_verify(const Batch& b, int total64, int total_verify, int pw, cudaStream_t s)
-{
-    launch_pdl(kabsch_fp64_kernel, total64, 32, 0, s, ManyViews{b});
-    if (pw == 32) launch_pdl(verify_kernel<true, 32>, total_verify, 128, 0, s, ManyViews{b});
-    else if (pw == 128) launch_pdl(verify_kernel<true, 128>, total_verify, 128, 0, s, ManyViews{b});
-    else launch_pdl(verify_kernel<true, 64>, total_verify, 128, 0, s, ManyViews{b});
-}
-
 
 // Per-problem block counts of every stage.
 void stage_blocks(int32_t n, int32_t k1, int32_t k2, int32_t verify_pw, int32_t blocks[kNumBatchStages])
@@ -363,7 +313,6 @@ void stage_blocks(int32_t n, int32_t k1, int32_t k2, int32_t verify_pw, int32_t 
     blocks[ST_RANK] = (k1 + 31) / 32;
     blocks[ST_PGS] = (k1 + 7) / 8;
     blocks[ST_KABSCH] = (nh + 127) / 128;
-    blocks[ST_KABSCH64] = (nh + 31) / 32;
     blocks[ST_VERIFY] = ((nh + kVHyp - 1) / kVHyp) * ((n + vpts - 1) / vpts);
     blocks[ST_FINAL] = 1;
     blocks[ST_HIST] = (n + 63) / 64;

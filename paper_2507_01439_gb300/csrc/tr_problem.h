@@ -41,7 +41,6 @@ struct ProbView {
     float* rt;           // [K1_MAX*K2_MAX][16] R, t, kappa, flags
     int32_t* inl;        // [K1_MAX*K2_MAX] inlier numbers
     unsigned long long* score;  // [K1_MAX*K2_MAX] capped error sums in units of 2^-22 theta (^2)
-    int32_t* fp64_list;  // [K1_MAX*K2_MAX] hypotheses whose Kabsch needs FP64
     float* feat;         // [n_pad][8] proposal features (learned proposal only)
     float* prob;         // [n_pad] inlier probabilities; non-null selects the learned pivot weight
     Ctl* ctl;            // device scalars
@@ -52,7 +51,7 @@ struct ProbView {
 // are numbered consecutively over the problems: problem p owns blocks
 // [pre[k*(num+1) + p], pre[k*(num+1) + p + 1]).
 enum Stage {
-    ST_PACK = 0, ST_COMPAT, ST_SELECT, ST_COUNT, ST_SCAN, ST_EMIT, ST_RANK, ST_PGS, ST_KABSCH, ST_KABSCH64,
+    ST_PACK = 0, ST_COMPAT, ST_SELECT, ST_COUNT, ST_SCAN, ST_EMIT, ST_RANK, ST_PGS, ST_KABSCH,
     ST_VERIFY, ST_FINAL, ST_HIST, ST_BITSET, ST_GEMM, ST_FEAT, ST_MLP, kNumBatchStages
 };
 
@@ -127,8 +126,6 @@ void launch_select(const Batch& b, cudaStream_t s);
 void launch_topk_rest(const Batch& b, const int32_t tot[kNumBatchStages], int max_k1, cudaStream_t s);
 void launch_pgs(const Batch& b, int total, int k2_max, cudaStream_t s);
 void launch_kabsch(const Batch& b, int total, cudaStream_t s);
-void launch_kabsch_fp64_verify(const Batch& b, int total64, int total_verify, int pw, cudaStream_t s);
-void launch_kabsch_fp64(const Batch& b, int total64, cudaStream_t s);
 void launch_finalize(const Batch& b, cudaStream_t s);
 // Kabsch of caller-given k-cliques (k >= 4) into v.rt; idx [m][k] on the device.
 void launch_kabsch_n(const ProbView& v, const int32_t* idx, int k, int m, cudaStream_t s);

@@ -253,3 +253,42 @@ def test_kabsch_cliques_matches_oracle(ctx, k):
     bad[3, 1] = p.n
     with pytest.raises(RuntimeError):
         ctx.kabsch_cliques(p.x, p.y, bad)
+
+
+def test_ill_conditioned_cliques_accurate_with_fp64_normals(ctx):
+    """Thin triangles (kappa = sigma1/sigma2 up to ~1e5): with the normals taken
+    in FP64 above the kappa bound, the 3-point closed form stays within ~1e-6
+    of the oracle's FP64 SVD Kabsch whatever kappa is (all-FP32 would be off
+    by up to ~4e-3 at kappa 1e5)."""
+    rng = np.random.default_rng(77)
+    xs, ys, idx, want = [], [], [], []
+    for logk in (1, 2, 3, 4, 5):
+        for _ in range(60):
+            L, h = 2.0, 2.0 / 10 ** logk
+            base = rng.uniform(-3, 3, 3)
+            u = rng.normal(size=3); u /= np.linalg.norm(u)
+            w = rng.normal(size=3); w -= w.dot(u) * u; w /= np.linalg.norm(w)
+            p = np.stack([base, base + L * u, base + 0.5 * L * u + h * w])
+            Rg = np.linalg.qr(rng.normal(size=(3, 3)))[0]
+            if np.linalg.det(Rg) < 0:
+                Rg[:, 0] *= -1
+            q = p @ Rg.T + rng.uniform(-1, 1, 3) + rng.normal(scale=0.003, size=(3, 3))
+            k0 = 3 * len(idx)
+            xs.append(p); ys.append(q)
+            idx.append([k0, k0 + 1, k0 + 2])
+    x = np.concatenate(xs).astype(np.float32)
+    y = np.concatenate(ys).astype(np.float32)
+    idx = np.array(idx, dtype=np.int32)
+    rt, valid = ctx.kabsch_cliques(x, y, idx, trg.default_params(0.1, 10, 0.1))
+    worst = {}
+    for m in range(idx.shape[0]):
+        ok, Ro, to, kap = oracle.kabsch_n(x[idx[m]].astype(np.float64), y[idx[m]].astype(np.float64))
+        assert bool(valid[m]) == ok
+        if not ok:
+            continue
+        dR = float(np.linalg.norm(rt[m, :9].reshape(3, 3).astype(np.float64) - Ro))
+        band = int(np.floor(np.log10(max(kap, 1.0))))
+        worst[band] = max(worst.get(band, 0.0), dR)
+        assert dR <= 2e-6, (m, kap, dR)
+    print("max |dR| by decade of kappa", worst)
+    assert max(worst) >= 4          # the set reaches kappa >= 1e4
