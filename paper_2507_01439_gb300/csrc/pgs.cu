@@ -33,7 +33,9 @@ __global__ void __launch_bounds__(256) pgs_kernel(ManyViews vs)
     int lb;
     const ProbView v = vs.get(ST_PGS, blockIdx.x, lb);
     const int lane = threadIdx.x & 31;
-    const int p = lb * 8 + (threadIdx.x >> 5);
+    // pivots are in weight order and heavier pivots have more common neighbours:
+    // warp w of block b takes pivot w * blocks + b, spreading them over the SMs
+    const int p = (threadIdx.x >> 5) * ((v.k1 + 7) / 8) + lb;
     const int np = v.ctl->n_pivots;
     if (p >= np) return;
     const int k2 = K2C > 0 ? K2C : v.k2;

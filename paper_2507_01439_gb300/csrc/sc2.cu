@@ -76,7 +76,6 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar)
 template <bool kSingle, bool kPair>
 __global__ void __launch_bounds__(kThreads, 1) sc2_tcgen05_kernel(Batch bt, int total)
 {
-    pdl_wait();
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t* sA = smem;
@@ -117,6 +116,9 @@ __global__ void __launch_bounds__(kThreads, 1) sc2_tcgen05_kernel(Batch bt, int 
     const int u0 = kPair ? static_cast<int>(blockIdx.x >> 1) : static_cast<int>(blockIdx.x);
     const int us = kPair ? static_cast<int>(gridDim.x >> 1) : static_cast<int>(gridDim.x);
     const int nu = kPair ? total >> 1 : total;
+    // the set-up above (barriers, tensor memory, shared histogram) overlaps the
+    // previous stage; its outputs are read only from here on
+    pdl_wait();
 
     if (warp == 0) {
         if (lane == 0) {

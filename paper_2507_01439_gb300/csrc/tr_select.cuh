@@ -72,18 +72,31 @@ __device__ __forceinline__ void select_alpha(const ProbView& v, int* sbuf)
     if (n_sel == 0) return;
     const int excl = incl - mine;
     if (excl < n_sel && n_sel <= incl) {
+        // the thread holding the K1-th edge walks its bins from the top, eight
+        // loads in flight per step
         int run = excl;
-        for (int q = 0; q < per; ++q) {
-            const int wv = hi - q;
-            if (wv < 1) break;
-            const int h = static_cast<int>(v.hist[wv]);
-            if (run + h >= n_sel) {
-                v.ctl->alpha = wv;
-                v.ctl->c_gt = run;
-                v.ctl->m_ties = n_sel - run;
-                break;
+        bool done = false;
+        for (int q0 = 0; q0 < per && !done; q0 += 8) {
+            uint32_t h8[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int wv = hi - q0 - q;
+                h8[q] = (q0 + q < per && wv >= 1) ? v.hist[wv] : 0u;
             }
-            run += h;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int wv = hi - q0 - q;
+                if (done || q0 + q >= per || wv < 1) continue;
+                const int h = static_cast<int>(h8[q]);
+                if (run + h >= n_sel) {
+                    v.ctl->alpha = wv;
+                    v.ctl->c_gt = run;
+                    v.ctl->m_ties = n_sel - run;
+                    done = true;
+                } else {
+                    run += h;
+                }
+            }
         }
     }
 }
