@@ -177,8 +177,8 @@ def stage_rooflines(stage_log, peaks, kind):
       compat   n(n-1)/2 pairs x 17 FLOP (two 3-D distances, difference, compare)
       sc2      420 tiles x 2 x 128 x 256 x 5120 dense FP8 MMA FLOP
       topk     the upper triangle of W read once: n(n-1)/2 x 2 bytes
-      pgs      K1 x 2 bitset rows of n/8 bytes
-      kabsch   K1 K2 cliques x 300 FLOP
+      pgs      K1 x 2 bitset rows of n/8 bytes (the stage also solves each
+               clique's Kabsch, ~300 FLOP per clique, not counted)
       verify   K1 K2 x n residuals x 17 FLOP"""
     if not stage_log:
         return None
@@ -190,7 +190,6 @@ def stage_rooflines(stage_log, peaks, kind):
         "sc2": (420 * 2.0 * 128 * 256 * 5120, "tensor", 2 * peaks["bf16_tflops_sustained"], "TFLOP/s"),
         "topk": (pairs * 2, "hbm", peaks["hbm_gbs"], "GB/s"),
         "pgs": (k1 * 2 * n / 8, "hbm", peaks["hbm_gbs"], "GB/s"),
-        "kabsch": (k1 * k2 * 300, "alu", FP32_PEAK_TFLOPS, "TFLOP/s"),
         "verify": (k1 * k2 * n * 17.0, "alu", FP32_PEAK_TFLOPS, "TFLOP/s"),
     }
     out = {}
