@@ -50,8 +50,9 @@ WORKLOAD = {"workload": "indoor-shaped single problem", "n": 5000, "inlier_ratio
 # finalize
 LAUNCHES_PER_STEP = 9
 # DRAM bytes (read + write) of one SC^2 kernel launch on this workload, from one ncu
-# capture of the current kernel (profiles/sc2_tcgen05_indoor5000.txt)
-SC2_DRAM_BYTES = 28379648
+# capture of the current kernel (profiles/sc2_pair_mma_indoor5000.txt); None until
+# the current kernel has been captured
+SC2_DRAM_BYTES = None
 
 
 def _peaks():
@@ -512,12 +513,14 @@ def run_clique_stability(trg, per_tau=240):
 
 def run_sc2_paths(trg, probs, dx, dy):
     """SC^2 stage (with the edge-weight histogram and the pivot threshold) on
-    the benchmark workload: the tcgen05 FP8 GEMM (2-CTA clusters sharing B,
-    the default; and independent CTAs) vs the CUDA-core bitset AND + popcount
-    path (same integers); in-graph CUDA-event times."""
+    the benchmark workload: the tcgen05 FP8 GEMM (2-CTA pair MMAs, the
+    default; clusters sharing B by multicast; independent CTAs) vs the
+    CUDA-core bitset AND + popcount path (same integers); in-graph CUDA-event
+    times."""
     out = {}
     with trg.TurboReg(max_n=5000, max_batch=1) as ctx:
-        for name, fl in (("tcgen05_gemm", 0), ("tcgen05_gemm_single_cta", trg.FLAG_SC2_SINGLE_CTA),
+        for name, fl in (("tcgen05_gemm", 0), ("tcgen05_gemm_multicast", trg.FLAG_SC2_MULTICAST),
+                         ("tcgen05_gemm_single_cta", trg.FLAG_SC2_SINGLE_CTA),
                          ("bitset_popcount", trg.FLAG_SC2_BITSET)):
             prm = trg.default_params(0.1, 2000, 0.1, flags=trg.FLAG_STAGE_TIMES | fl)
             ms = []
@@ -625,7 +628,7 @@ def run_ours(args):
     sc2_avg_s = (sum(sc2_ms) / len(sc2_ms)) / 1e3
     achieved = flops / sc2_avg_s / 1e12
     peak = 2.0 * peaks["bf16_tflops_sustained"]    # FP8 dense = 2 x bf16 (nominal ratio)
-    roofline = {"bound": "tensor", "kernel": "sc2_tcgen05_kernel (FP8 E4M3 x E4M3 -> F32, 2-CTA clusters)",
+    roofline = {"bound": "tensor", "kernel": "sc2_pair_mma_kernel (FP8 E4M3 x E4M3 -> F32, cta_group::2 pair MMAs)",
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "peak_source": f"{kind}: 2 x bf16_tflops_sustained (FP8/BF16 nominal ratio 4.5/2.25)",
                 "traffic": SC2_DRAM_BYTES, "sc2_ms": sc2_avg_s * 1e3,

@@ -2,10 +2,11 @@
 
 It picks, by measurement on the device at hand:
 
-  tile shapes  the SC^2 GEMM tile (2-CTA clusters sharing the B operand, or
-               independent 128 x 256 CTAs) and the verification tile (128
-               hypotheses x 128 / 256 / 512 matches per block); every
-               candidate gives the same results, only the time differs;
+  tile shapes  the SC^2 GEMM form (2-CTA pair MMAs, clusters sharing the B
+               operand by multicast, or independent 128 x 256 CTAs) and the
+               verification tile (128 hypotheses x 128 / 256 / 512 matches per
+               block); every candidate gives the same results, only the time
+               differs;
   K schedule   the pivot count K1 per problem class (compatibility threshold
                tau and a bucket of N): the smallest candidate K1 whose success
                rate on calibration problems equals the best candidate's, i.e.
@@ -25,14 +26,15 @@ from dataclasses import asdict, dataclass, field
 
 import numpy as np
 
-from . import (FLAG_SC2_SINGLE_CTA, FLAG_VERIFY_PTS32, FLAG_VERIFY_PTS128, TurboReg, default_params)
+from . import (FLAG_SC2_MULTICAST, FLAG_SC2_SINGLE_CTA, FLAG_VERIFY_PTS32, FLAG_VERIFY_PTS128, TurboReg,
+               default_params)
 
 TILE_CANDIDATES = {
     "sc2_pair+verify256": 0,
     "sc2_pair+verify128": FLAG_VERIFY_PTS32,
     "sc2_pair+verify512": FLAG_VERIFY_PTS128,
+    "sc2_multicast+verify256": FLAG_SC2_MULTICAST,
     "sc2_single+verify256": FLAG_SC2_SINGLE_CTA,
-    "sc2_single+verify128": FLAG_SC2_SINGLE_CTA | FLAG_VERIFY_PTS32,
     "sc2_single+verify512": FLAG_SC2_SINGLE_CTA | FLAG_VERIFY_PTS128,
 }
 

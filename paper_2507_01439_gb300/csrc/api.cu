@@ -75,7 +75,8 @@ struct Workspace {
 struct Plan {
     int32_t num = 0;
     int32_t max_n = 0, max_k1 = 0, k2_common = 0;
-    int32_t bitset = 0, timed = 0, learned = 0, pair = 1;
+    int32_t bitset = 0, timed = 0, learned = 0;
+    int32_t gemm_form = 2;   // SC^2 GEMM: 0 independent CTAs, 1 multicast clusters, 2 pair MMAs
     int32_t vpw = 64;        // verification tile: points per warp
     int32_t tot[kNumBatchStages] = {};
 };
@@ -332,7 +333,7 @@ int build_plan(turboreg_ctx* c, int32_t num, const int64_t* in_off, const int32_
     plan.bitset = (prm[0]->flags & TURBOREG_FLAG_SC2_BITSET) != 0;
     plan.timed = num == 1 && (prm[0]->flags & TURBOREG_FLAG_STAGE_TIMES) != 0;
     plan.learned = prm[0]->proposal == TURBOREG_PROPOSAL_LEARNED;
-    plan.pair = (prm[0]->flags & TURBOREG_FLAG_SC2_SINGLE_CTA) ? 0 : 1;
+    plan.gemm_form = (prm[0]->flags & TURBOREG_FLAG_SC2_SINGLE_CTA) ? 0 : (prm[0]->flags & TURBOREG_FLAG_SC2_MULTICAST) ? 1 : 2;
     plan.vpw = (prm[0]->flags & TURBOREG_FLAG_VERIFY_PTS32) ? 32 : (prm[0]->flags & TURBOREG_FLAG_VERIFY_PTS128) ? 128 : 64;
     plan.k2_common = prm[0]->k2;
     for (int st = 0; st < kNumBatchStages; ++st) ws.h_pre[st * (num + 1)] = 0;
@@ -393,7 +394,7 @@ int enqueue_plan(turboreg_ctx* c, const Plan& pl, const Batch& bt, const float* 
     } else {
         // one problem: the GEMM builds the histogram in shared memory and its
         // last CTA chooses the threshold; a batch adds a select launch
-        launch_sc2_tcgen05(bt, pl.tot[ST_GEMM], pl.max_n, pl.pair != 0, s);
+        launch_sc2_tcgen05(bt, pl.tot[ST_GEMM], pl.max_n, pl.gemm_form, s);
         if (pl.num > 1 && !pl.learned) launch_select(bt, s);
     }
     if (pl.learned) {
@@ -1100,7 +1101,7 @@ int turboreg_features(turboreg_ctx* c, const float* src, const float* dst, int32
     TR_CHECK(cudaMemsetAsync(c->ws.ctl, 0, sizeof(Ctl), c->stream));
     launch_pack(bt, pl.tot[ST_PACK], s_in, d_in, c->stream);
     launch_compat(bt, pl.tot[ST_COMPAT], c->stream);
-    launch_sc2_tcgen05(bt, pl.tot[ST_GEMM], pl.max_n, true, c->stream);
+    launch_sc2_tcgen05(bt, pl.tot[ST_GEMM], pl.max_n, 2, c->stream);
     launch_features(bt, c->stream);
     TR_CHECK(cudaGetLastError());
     TR_CHECK(cudaMemcpyAsync(feat, c->ws.feat, static_cast<size_t>(n) * 8 * sizeof(float), cudaMemcpyDefault,
