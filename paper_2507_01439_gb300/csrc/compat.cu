@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(kThreads) compat_kernel(ManyViews vs)
 {
     pdl_wait();
     __shared__ __align__(128) float4 srow[kT][2];     // row points (x0,x1,x2,y0 | y1,y2,-,-)
-    __shared__ uint16_t colpart[8][kT];               // per warp: 16-row mask of each column
+    __shared__ __align__(16) uint16_t colpart[kT][8];  // column c: the 16-row masks of the 8 warps
     __shared__ __align__(8) uint64_t bar;
 
     // triangular tile index -> (I, J), I <= J
@@ -224,8 +224,7 @@ __global__ void __launch_bounds__(kThreads) compat_kernel(ManyViews vs)
             wrow_bits[0] = word[0]; wrow_bits[1] = word[1]; wrow_bits[2] = word[2]; wrow_bits[3] = word[3];
         }
     }
-    // direct rows i0 + 16 warp + r (r = 0..15): lanes 0..15 store the bitset words
-    // (16 B each); all 32 lanes expand two 64-byte halves of the FP8 rows
+    // direct rows i0 + 16 warp + r (r = 0..15): lanes 0..15 store the bitset words (16 B each)
     if (lane < 16) {
         const int i = i0 + warp * 16 + lane;
         *reinterpret_cast<uint4*>(v.bits + (size_t)i * v.ldb + (j0 >> 5)) =
@@ -233,11 +232,12 @@ __global__ void __launch_bounds__(kThreads) compat_kernel(ManyViews vs)
         const int d = __popc(wrow_bits[0]) + __popc(wrow_bits[1]) + __popc(wrow_bits[2]) + __popc(wrow_bits[3]);
         if (d) atomicAdd(&v.deg[i], d);
     }
+    // FP8 rows, 128 contiguous bytes per row: pass k writes rows 4k .. 4k + 3 of
+    // the warp's 16, lane l the 16-byte segment l % 8 of row 4k + l / 8
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        // row r = lane & 15, 16-byte segment seg = 4 (lane >> 4) + k of the 8 in a 128-byte row
-        const int r = lane & 15;
-        const int seg = 4 * (lane >> 4) + k;
+        const int r = 4 * k + (lane >> 3);
+        const int seg = lane & 7;
         const uint32_t w0 = __shfl_sync(0xffffffffu, wrow_bits[0], r);
         const uint32_t w1 = __shfl_sync(0xffffffffu, wrow_bits[1], r);
         const uint32_t w2 = __shfl_sync(0xffffffffu, wrow_bits[2], r);
@@ -248,28 +248,27 @@ __global__ void __launch_bounds__(kThreads) compat_kernel(ManyViews vs)
             bits16_to_fp8((w >> ((seg & 1) * 16)) & 0xFFFFu);
     }
     if (diag) return;
-    // mirrored tile: row j gets bits of rows i0 .. i0+127
+    // mirrored tile: row j gets bits of rows i0 .. i0+127; column c's 32-bit
+    // word k (rows 32k .. 32k+31) is colpart[c][2k] | colpart[c][2k+1] << 16
 #pragma unroll
-    for (int q = 0; q < 4; ++q) colpart[warp][lane + 32 * q] = static_cast<uint16_t>(cmask[q]);
+    for (int q = 0; q < 4; ++q) colpart[lane + 32 * q][warp] = static_cast<uint16_t>(cmask[q]);
     __syncthreads();
-    const int c = threadIdx.x & (kT - 1);   // column within the tile
-    const int half = threadIdx.x >> 7;      // two threads per column
-    const int j = j0 + c;
-    uint32_t w4[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
-        w4[k] = static_cast<uint32_t>(colpart[2 * k][c]) | (static_cast<uint32_t>(colpart[2 * k + 1][c]) << 16);
-    if (half == 0) {
-        *reinterpret_cast<uint4*>(v.bits + (size_t)j * v.ldb + (i0 >> 5)) = make_uint4(w4[0], w4[1], w4[2], w4[3]);
-        const int d = __popc(w4[0]) + __popc(w4[1]) + __popc(w4[2]) + __popc(w4[3]);
+    if (threadIdx.x < kT) {
+        const int c = threadIdx.x;
+        const uint4 cw = *reinterpret_cast<const uint4*>(colpart[c]);
+        const int j = j0 + c;
+        *reinterpret_cast<uint4*>(v.bits + (size_t)j * v.ldb + (i0 >> 5)) = cw;
+        const int d = __popc(cw.x) + __popc(cw.y) + __popc(cw.z) + __popc(cw.w);
         if (d) atomicAdd(&v.deg[j], d);
     }
-    uint8_t* dstrow = v.a8 + (size_t)j * v.n_pad + i0;
+    // FP8 rows: pass k writes rows j0 + 32k .. +31, eight threads per 128-byte row
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        const int seg = half * 4 + k;          // 16-byte segment 0..7 of the 128-byte row
-        const uint32_t w = w4[seg >> 1];
-        *reinterpret_cast<uint4*>(dstrow + seg * 16) = bits16_to_fp8((w >> ((seg & 1) * 16)) & 0xFFFFu);
+        const int c = 32 * k + (threadIdx.x >> 3);
+        const int seg = threadIdx.x & 7;
+        const uint32_t w = reinterpret_cast<const uint32_t*>(colpart[c])[seg >> 1];
+        *reinterpret_cast<uint4*>(v.a8 + (size_t)(j0 + c) * v.n_pad + i0 + seg * 16) =
+            bits16_to_fp8((w >> ((seg & 1) * 16)) & 0xFFFFu);
     }
 }
 

@@ -13,11 +13,19 @@
 // (z != i, j follows from the zero diagonal) and W read symmetrically,
 // W_ab = W_min(a,b),max(a,b) (only the upper triangle is stored).
 //
-// One warp per pivot: lane l ANDs bitset words l, l+32, ... of the two rows
-// (four words of each row in flight per sweep), looks up the weights of its
-// candidates eight at a time, keeps a private top-K2 list, and the warp
-// merges the 32 lists with K2 rounds of a 64-bit max-reduction over keys
-// (S << 32 | ~z).
+// One warp per pivot.  Candidates: every lane loads its share of both rows'
+// bitset words at once (eight words of each per lane in flight), and the
+// warp compacts the set bits of their AND into a per-warp list in shared
+// memory (popcount prefix sums).  Scoring: lanes take list entries
+// l, l + 32, ..., eight at a time so that their 16 weight loads are in
+// flight together (sixteen at a time measured slower), and keep private top-K2 lists of keys (S << 32 | ~z); the warp
+// merges the 32 lists with K2 rounds of a 64-bit max-reduction.  A list that
+// would overflow is scored and emptied first, so any graph density works.
+//
+// Kabsch (Sec. 3.5): lane r solves clique r in FP32; for ill-conditioned
+// cliques the warp computes the FP64 triangle normals with six lanes per
+// clique (triangle x or y, component 0..2) and lane r redoes the closed form
+// with them.
 #include "tr_common.cuh"
 #include "tr_kabsch.cuh"
 #include "tr_problem.h"
@@ -26,18 +34,24 @@ namespace tr {
 
 namespace {
 
+constexpr int kCand = 1024;   // per-warp candidate list (z indices)
+constexpr int kWords = 8;     // bitset words per lane per load round
+constexpr int kBatch = 8;     // list entries per lane per scoring round (16 weight loads in flight)
+
 template <int K2C>
-__global__ void __launch_bounds__(256) pgs_kernel(ManyViews vs)
+__global__ void __launch_bounds__(256, 2) pgs_kernel(ManyViews vs)
 {
+    __shared__ int scand[8][kCand];
     pdl_wait();
     int lb;
     const ProbView v = vs.get(ST_PGS, blockIdx.x, lb);
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     // pivots are in weight order and heavier pivots have more common neighbours:
     // warp w of block b takes pivot w * blocks + b, spreading them over the SMs
-    const int p = (threadIdx.x >> 5) * ((v.k1 + 7) / 8) + lb;
+    const int p = warp * ((v.k1 + 7) / 8) + lb;
     const int np = v.ctl->n_pivots;
     if (p >= np) return;
+    int* cand = scand[warp];
     const int k2 = K2C > 0 ? K2C : v.k2;
     const int4 pv = v.piv[p];
     const int i = pv.x, j = pv.y, wij = pv.z;
@@ -52,66 +66,103 @@ __global__ void __launch_bounds__(256) pgs_kernel(ManyViews vs)
 #pragma unroll
     for (int r = 0; r < L; ++r) top[r] = 0ull;
 
-    // candidate z are gathered 8 at a time so their 16 weight loads are in flight together
-    int zb[8];
-    int nz = 0;
-    auto flush = [&]() {
-        int wa[8], wb[8];
+    // score list entries [0, cnt): W_iz and W_jz (z > j > i on the O2Graph; the
+    // undirected search also meets z < j and reads W symmetrically)
+    auto score = [&](int cnt) {
+        for (int c0 = 0; c0 < cnt; c0 += 32 * kBatch) {
+            int zq[kBatch], wa[kBatch], wb[kBatch];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int z = zb[q];
-            if (q < nz) {
-                // z > j > i on the O2Graph; the undirected search also meets z < j
-                wa[q] = static_cast<int>(z > i ? wi[z] : v.w[(size_t)z * v.n_pad + i]);
-                wb[q] = static_cast<int>(z > j ? wj[z] : v.w[(size_t)z * v.n_pad + j]);
-            } else {
-                wa[q] = wb[q] = 0;
+            for (int b = 0; b < kBatch; ++b) {
+                const int c = c0 + lane + 32 * b;
+                zq[b] = c < cnt ? cand[c] : -1;
             }
-        }
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            if (q >= nz) break;
-            const int sz = wij + wa[q] + wb[q];
-            const uint64_t key = (static_cast<uint64_t>(sz) << 32) | (0xFFFFFFFFu - static_cast<uint32_t>(zb[q]));
-            if (key > top[L - 1]) {          // insertion into the descending list (keys are unique)
-                uint64_t cur = key;
+            for (int b = 0; b < kBatch; ++b) {
+                const int z = zq[b];
+                wa[b] = z < 0 ? 0 : static_cast<int>(z > i ? wi[z] : v.w[(size_t)z * v.n_pad + i]);
+                wb[b] = z < 0 ? 0 : static_cast<int>(z > j ? wj[z] : v.w[(size_t)z * v.n_pad + j]);
+            }
 #pragma unroll
-                for (int r = 0; r < L; ++r) {
-                    if (cur > top[r]) {
-                        const uint64_t t = top[r];
-                        top[r] = cur;
-                        cur = t;
+            for (int b = 0; b < kBatch; ++b) {
+                if (zq[b] < 0) continue;
+                const int sz = wij + wa[b] + wb[b];
+                const uint64_t key = (static_cast<uint64_t>(sz) << 32) | (0xFFFFFFFFu - static_cast<uint32_t>(zq[b]));
+                if (key > top[L - 1]) {          // insertion into the descending list (keys are unique)
+                    uint64_t cur = key;
+#pragma unroll
+                    for (int r = 0; r < L; ++r) {
+                        if (cur > top[r]) {
+                            const uint64_t t = top[r];
+                            top[r] = cur;
+                            cur = t;
+                        }
                     }
                 }
             }
         }
-        nz = 0;
     };
+
     const int zs = undirected ? 0 : j + 1;
     const int w0 = zs >> 5;
-    // lane l takes words w0 + l + 32 t; the 2 x 4 word loads of a sweep are in flight together
-    for (int wb = w0 + lane; wb < v.ldb; wb += 32 * 4) {
-        uint32_t mw[4];
+    int nlist = 0;
+    for (int wb = w0; wb < v.ldb; wb += 32 * kWords) {
+        uint32_t mw[kWords];
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
-            const int wd = wb + 32 * t;
-            mw[t] = wd < v.ldb ? (bi[wd] & bj[wd]) : 0u;
+        for (int t = 0; t < kWords; ++t) {
+            const int wd = wb + lane + 32 * t;
+            mw[t] = wd < v.ldb ? (__ldg(bi + wd) & __ldg(bj + wd)) : 0u;
+            if (wd == w0) mw[t] &= ~0u << (zs & 31);
         }
+        // one prefix sum per round: lane l writes its candidates (all its words)
+        // after those of lanes < l; the list order does not matter
+        int cnt = 0;
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
-            const int wd = wb + 32 * t;
-            uint32_t m = mw[t];
-            if (wd == w0) m &= ~0u << (zs & 31);
-            while (m) {
-                zb[nz++] = wd * 32 + __ffs(m) - 1;
-                m &= m - 1;
-                if (nz == 8) flush();
+        for (int t = 0; t < kWords; ++t) cnt += __popc(mw[t]);
+        int incl = cnt;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += y;
+        }
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        if (nlist + total <= kCand) {
+            int pos = nlist + incl - cnt;
+#pragma unroll
+            for (int t = 0; t < kWords; ++t) {
+                const int zb = (wb + lane + 32 * t) * 32;
+                for (uint32_t m = mw[t]; m != 0u; m &= m - 1u) cand[pos++] = zb + __ffs(m) - 1;
+            }
+            nlist += total;
+        } else {
+            // dense rows: word by word, scoring the list whenever it would overflow
+#pragma unroll 1
+            for (int t = 0; t < kWords; ++t) {
+                const int c1 = __popc(mw[t]);
+                int in1 = c1;
+#pragma unroll
+                for (int off = 1; off < 32; off <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, in1, off);
+                    if (lane >= off) in1 += y;
+                }
+                const int tot1 = __shfl_sync(0xffffffffu, in1, 31);
+                if (nlist + tot1 > kCand) {   // warp-uniform
+                    __syncwarp();
+                    score(nlist);
+                    nlist = 0;
+                    __syncwarp();
+                }
+                int pos = nlist + in1 - c1;
+                const int zb = (wb + lane + 32 * t) * 32;
+                for (uint32_t m = mw[t]; m != 0u; m &= m - 1u) cand[pos++] = zb + __ffs(m) - 1;
+                nlist += tot1;
             }
         }
     }
-    if (nz) flush();
+    __syncwarp();
+    score(nlist);
+
     // warp merge: k2 rounds of argmax over the lanes' list heads; lane r keeps
-    // round r's clique and solves its Kabsch afterwards
+    // round r's clique
     int head = 0;
     int4 mine_cl = make_int4(i, j, -1, 0);
     for (int r = 0; r < k2; ++r) {
@@ -132,8 +183,55 @@ __global__ void __launch_bounds__(256) pgs_kernel(ManyViews vs)
         if (lane == 0) v.cliques[static_cast<size_t>(r) * np + p] = cl;
         if (lane == r) mine_cl = cl;
     }
-    // Kabsch of this pivot's cliques (Sec. 3.5), one lane each
-    if (lane < k2) kabsch_hypothesis(v, lane * np + p, mine_cl);
+
+    // Kabsch of this pivot's cliques (Sec. 3.5): lane r < k2 solves clique r in FP32
+    float P[3][3], Q[3][3];
+    KabschOut<float> o;
+    o.ok = false;
+    bool need = false;
+    const bool present = lane < k2 && mine_cl.w != 0;
+    if (present) {
+        load_clique(v, mine_cl, P, Q);
+        kabsch3<float>(P, Q, o);
+        need = !(o.ok && o.kappa <= v.kappa_fp64);
+    }
+    const uint32_t needm = __ballot_sync(0xffffffffu, need);
+    if (needm != 0u) {
+        // FP64 normals, five cliques per round: lane L works for clique
+        // base + L / 6, triangle (L / 3) & 1 (x, y), component L % 3
+        float nx[3] = {0.f, 0.f, 0.f}, ny[3] = {0.f, 0.f, 0.f};
+        for (int base = 0; base < k2 && (needm >> base) != 0u; base += 5) {
+            const int r = base + lane / 6;
+            const int src = r < 32 ? r : 31;
+            const int cz = __shfl_sync(0xffffffffu, mine_cl.z, src);
+            const bool act = lane < 30 && r < k2 && ((needm >> src) & 1u);
+            float val = 0.f;
+            if (act) {
+                const int tri = (lane / 3) & 1, comp = lane % 3;
+                const int idx[3] = {i, j, cz};
+                float T3[3][3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    const float* pt = v.pts8 + (size_t)idx[a] * 8 + 3 * tri;
+                    T3[a][0] = pt[0]; T3[a][1] = pt[1]; T3[a][2] = pt[2];
+                }
+                val = exact_normal_comp(T3, comp);
+            }
+            // lane r of this round collects its six components from lanes 6 (r - base) ..
+            const int mine0 = 6 * (lane - base);
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+                const int from = (lane >= base && lane < base + 5) ? mine0 + k : 0;
+                const float g = __shfl_sync(0xffffffffu, val, from);
+                if (lane >= base && lane < base + 5) {
+                    if (k < 3) nx[k] = g;
+                    else ny[k - 3] = g;
+                }
+            }
+        }
+        if (need) kabsch3<float, true>(P, Q, o, nx, ny);
+    }
+    if (lane < k2) store_hypothesis(v, lane * np + p, present, o, need ? 2u : 0u);
 }
 
 }  // namespace

@@ -21,10 +21,12 @@
 // frames, projections and the 2x2 step are well conditioned.  So when kappa
 // exceeds the bound (default 100) or the FP32 frames are undefined, the two
 // normals are recomputed in FP64 from exact FP64 differences of the FP32
-// inputs (about 24 FP64 instructions) and the rest is redone in FP32: checked
-// against the FP64 SVD, the rotation then stays within ~4e-7 of it up to
-// kappa ~ 1e5, where the all-FP32 form is off by ~4e-3.  A clique with
-// sigma2 <= 1e-12 sigma1 (collinear or repeated points) is invalid.
+// inputs, rounded to FP32, and the rest is redone in FP32: checked against the
+// FP64 SVD, the rotation then stays within ~4e-7 of it up to kappa ~ 1e5,
+// where the all-FP32 form is off by ~4e-3.  The clique search computes these
+// FP64 components with six lanes per clique (one per triangle and component),
+// so a warp issues a dozen FP64 instructions instead of a hundred.  A clique
+// with sigma2 <= 1e-12 sigma1 (collinear or repeated points) is invalid.
 #pragma once
 
 #include "tr_common.cuh"
@@ -61,13 +63,24 @@ __device__ __forceinline__ T dot3(const T a[3], const T b[3])
     return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
 }
 
+// Component c of the normal (p1 - p0) x (p2 - p0) in FP64 from exact FP64
+// differences of the FP32 coordinates, rounded to FP32.
+__device__ __forceinline__ float exact_normal_comp(const float (&p)[3][3], int c)
+{
+    const int c1 = c == 2 ? 0 : c + 1, c2 = c == 0 ? 2 : c - 1;
+    const double a1 = static_cast<double>(p[1][c1]) - static_cast<double>(p[0][c1]);
+    const double a2 = static_cast<double>(p[1][c2]) - static_cast<double>(p[0][c2]);
+    const double b1 = static_cast<double>(p[2][c1]) - static_cast<double>(p[0][c1]);
+    const double b2 = static_cast<double>(p[2][c2]) - static_cast<double>(p[0][c2]);
+    return static_cast<float>(__fma_rn(a1, b2, -__dmul_rn(a2, b1)));
+}
+
 // In-plane orthonormal frame of a triangle: e1 along its longest edge,
-// n = unit normal of (p1 - p0) x (p2 - p0), e2 = n x e1.  exact_normal: the
-// normal's cross product is taken in FP64 on exact FP64 differences, and
-// *nlen receives its length |(p1 - p0) x (p2 - p0)| (twice the area).
-template <typename T>
-__device__ __forceinline__ bool frame3(const T p[3][3], T e1[3], T e2[3], T nrm[3], bool exact_normal,
-                                       double* nlen)
+// n = unit normal of (p1 - p0) x (p2 - p0), e2 = n x e1.  ng: the normal's
+// components given by the caller (FP64 cross product rounded to FP32), and
+// then *nlen receives their length |(p1 - p0) x (p2 - p0)| (twice the area).
+template <typename T, bool kGiven>
+__device__ __forceinline__ bool frame3(const T p[3][3], T e1[3], T e2[3], T nrm[3], const T* ng, T* nlen)
 {
     T d01[3], d02[3], d12[3];
     for (int c = 0; c < 3; ++c) {
@@ -75,40 +88,33 @@ __device__ __forceinline__ bool frame3(const T p[3][3], T e1[3], T e2[3], T nrm[
         d02[c] = p[2][c] - p[0][c];
         d12[c] = p[2][c] - p[1][c];
     }
-    if (exact_normal) {
-        double a[3], b[3];
-        for (int c = 0; c < 3; ++c) {
-            a[c] = static_cast<double>(p[1][c]) - static_cast<double>(p[0][c]);
-            b[c] = static_cast<double>(p[2][c]) - static_cast<double>(p[0][c]);
-        }
-        const double n0 = a[1] * b[2] - a[2] * b[1];
-        const double n1 = a[2] * b[0] - a[0] * b[2];
-        const double n2 = a[0] * b[1] - a[1] * b[0];
-        *nlen = sqrt(n0 * n0 + n1 * n1 + n2 * n2);
-        nrm[0] = static_cast<T>(n0);
-        nrm[1] = static_cast<T>(n1);
-        nrm[2] = static_cast<T>(n2);
+    if (kGiven) {
+        nrm[0] = ng[0]; nrm[1] = ng[1]; nrm[2] = ng[2];
     } else {
         cross3(d01, d02, nrm);
     }
     const T nn = dot3(nrm, nrm);
+    if (kGiven) *nlen = sqrt(nn);
     const T l01 = dot3(d01, d01), l02 = dot3(d02, d02), l12 = dot3(d12, d12);
-    const T* e = d01;
+    int sel = 0;   // longest edge, selected by value (no pointer into local arrays)
     T le = l01;
-    if (l02 > le) { e = d02; le = l02; }
-    if (l12 > le) { e = d12; le = l12; }
+    if (l02 > le) { sel = 1; le = l02; }
+    if (l12 > le) { sel = 2; le = l12; }
     if (!(nn > T(0)) || !(le > T(0))) return false;
     const T in = inv_sqrt(nn), ie = inv_sqrt(le);
     for (int c = 0; c < 3; ++c) {
         nrm[c] *= in;
-        e1[c] = e[c] * ie;
+        e1[c] = (sel == 0 ? d01[c] : sel == 1 ? d02[c] : d12[c]) * ie;
     }
     cross3(nrm, e1, e2);
     return true;
 }
 
-template <typename T>
-__device__ void kabsch3(const T p[3][3], const T q[3][3], KabschOut<T>& o, bool exact_normal = false)
+// kGiven: the two triangles' normals nxg, nyg are given by the caller (the
+// FP64 path); otherwise they are the FP32 cross products.
+template <typename T, bool kGiven = false>
+__device__ __forceinline__ void kabsch3(const T p[3][3], const T q[3][3], KabschOut<T>& o, const T* nxg = nullptr,
+                                        const T* nyg = nullptr)
 {
     T cx[3], cy[3];
     for (int c = 0; c < 3; ++c) {
@@ -116,8 +122,8 @@ __device__ void kabsch3(const T p[3][3], const T q[3][3], KabschOut<T>& o, bool 
         cy[c] = (q[0][c] + q[1][c] + q[2][c]) * T(1.0 / 3.0);
     }
     T e1[3], e2[3], nx[3], f1[3], f2[3], ny[3];
-    double lx = 0.0, ly = 0.0;
-    o.ok = frame3(p, e1, e2, nx, exact_normal, &lx) && frame3(q, f1, f2, ny, exact_normal, &ly);
+    T lx = T(0), ly = T(0);
+    o.ok = frame3<T, kGiven>(p, e1, e2, nx, nxg, &lx) && frame3<T, kGiven>(q, f1, f2, ny, nyg, &ly);
     if (!o.ok) {
         o.kappa = T(INFINITY);
         o.s1 = o.s2 = T(0);
@@ -151,11 +157,11 @@ __device__ void kabsch3(const T p[3][3], const T q[3][3], KabschOut<T>& o, bool 
     const T lo = lo2 > T(0) ? lo2 * inv_sqrt(lo2) : T(0);
     o.s1 = (hi + lo) * T(0.5);
     o.s2 = (hi - lo) * T(0.5);
-    if (exact_normal && o.s1 > T(0)) {
+    if (kGiven && o.s1 > T(0)) {
         // sigma2 of a thin clique from sigma1 sigma2 = |det M| = |n_x| |n_y| / 3
-        // (Cauchy-Binet over three centred points), with the FP64 normal lengths,
-        // instead of the cancelling difference (hi - lo) / 2
-        o.s2 = static_cast<T>(lx * ly / (3.0 * static_cast<double>(o.s1)));
+        // (Cauchy-Binet over three centred points), with the lengths of the
+        // accurate normals, instead of the cancelling difference (hi - lo) / 2
+        o.s2 = lx * ly / (T(3) * o.s1);
     }
     o.kappa = o.s2 > T(0) ? static_cast<T>(static_cast<float>(o.s1) / static_cast<float>(o.s2)) : T(INFINITY);
     T X00, X01, X10, X11, sg;
@@ -185,26 +191,18 @@ __device__ __forceinline__ void load_clique(const ProbView& v, const int4 cl, fl
     }
 }
 
-// Closed form of hypothesis h with clique cl; the inlier count and score are
-// cleared.  Flags: 1 valid, 2 the FP64 normals were used.
-__device__ __forceinline__ void kabsch_hypothesis(const ProbView& v, int h, int4 cl)
+// Writes hypothesis h: R, t and kappa of a solved clique (flags: 1 valid,
+// 2 the FP64 normals were used), zero for an empty slot; the inlier count
+// and score are cleared.
+__device__ __forceinline__ void store_hypothesis(const ProbView& v, int h, bool present, const KabschOut<float>& o,
+                                                 uint32_t flags)
 {
     v.inl[h] = 0;
     v.score[h] = 0ull;
-    float* out = v.rt + (size_t)h * 16;
-    uint32_t flags = 0;
     float o16[13];
 #pragma unroll
     for (int r = 0; r < 13; ++r) o16[r] = 0.f;
-    if (cl.w) {
-        float p[3][3], q[3][3];
-        load_clique(v, cl, p, q);
-        KabschOut<float> o;
-        kabsch3<float>(p, q, o);
-        if (!(o.ok && o.kappa <= v.kappa_fp64)) {   // ill-conditioned: FP64 normals
-            kabsch3<float>(p, q, o, true);
-            flags = 2u;
-        }
+    if (present) {
         if (o.ok && o.s1 > 0.f && o.s2 > 1e-12f * o.s1) {
 #pragma unroll
             for (int r = 0; r < 9; ++r) o16[r] = o.R[r];
@@ -213,12 +211,38 @@ __device__ __forceinline__ void kabsch_hypothesis(const ProbView& v, int h, int4
             flags |= 1u;
         }
         o16[12] = o.kappa;
+    } else {
+        flags = 0u;
     }
-    float4* o4 = reinterpret_cast<float4*>(out);
+    float4* o4 = reinterpret_cast<float4*>(v.rt + (size_t)h * 16);
     o4[0] = make_float4(o16[0], o16[1], o16[2], o16[3]);
     o4[1] = make_float4(o16[4], o16[5], o16[6], o16[7]);
     o4[2] = make_float4(o16[8], o16[9], o16[10], o16[11]);
     o4[3] = make_float4(o16[12], __int_as_float(static_cast<int>(flags)), 0.f, 0.f);
+}
+
+// Closed form of hypothesis h with clique cl by one thread (the FP64 normals,
+// when needed, computed by the same thread).
+__device__ __forceinline__ void kabsch_hypothesis(const ProbView& v, int h, int4 cl)
+{
+    KabschOut<float> o;
+    uint32_t flags = 0;
+    if (cl.w) {
+        float p[3][3], q[3][3];
+        load_clique(v, cl, p, q);
+        kabsch3<float>(p, q, o);
+        if (!(o.ok && o.kappa <= v.kappa_fp64)) {   // ill-conditioned: FP64 normals
+            float nx[3], ny[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                nx[c] = exact_normal_comp(p, c);
+                ny[c] = exact_normal_comp(q, c);
+            }
+            kabsch3<float, true>(p, q, o, nx, ny);
+            flags = 2u;
+        }
+    }
+    store_hypothesis(v, h, cl.w != 0, o, flags);
 }
 
 }  // namespace
