@@ -9,11 +9,16 @@ SO(3), t uniform in [-1,1]^3 m, 5% inliers with sigma = 0.01 m, outliers
 uniform in the transformed bounding box; tau = 0.1 m, K1 = 2000, K2 = 2,
 inlier threshold 0.1 m.  Eight problems (seeds 0..7) are cycled.
 
-value: registrations/s with inputs resident in device memory, CUDA events on
-       the library's stream around each call, L2 flushed (256 MB write)
-       between timed steps outside the events.
-e2e:   the same metric through the C ABI with pinned HOST inputs: the H2D
-       copies of x, y and the D2H copy of the result are inside the events.
+value: registrations/s with inputs resident in device memory, through the
+       stream call turboreg_register_async (the host enqueues the steps ahead,
+       as a throughput user would), CUDA events on the library's stream
+       around each step, L2 flushed (256 MB write) between timed steps
+       outside the events; each step's result is copied to page-locked host
+       memory inside its events.
+e2e:   the same metric through the C ABI with page-locked HOST inputs: the
+       H2D copies of x, y and the D2H copy of the result are inside the events.
+sync_call: the synchronous turboreg_register per call (host work, graph
+       launch and the wait for the result included), for latency.
 roofline: the SC^2 GEMM's mean duration from CUDA events recorded inside the
        replayed graph around that stage, in a third timed pass of the same
        workload (those in-graph events add ~40 us per registration, so the
@@ -573,9 +578,16 @@ def run_ours(args):
                   and synth.translation_error(p.t_gt, r.t) < 0.3)
 
     def timed(kind, steps, warmup):
+        """kind: "device" / "host" = the stream call (register_async) with
+        device-resident or page-locked host inputs, enqueued ahead by the host;
+        "sync" = the synchronous call (its per-call latency, host work included);
+        "stages" = the synchronous call with CUDA events around every stage.
+        Every step is bracketed by its own events after an L2 flush (outside
+        them); the step's result is copied to page-locked host memory inside."""
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         sc2 = []
         p_k = prm_ev if kind == "stages" else prm
+        slots = trg.ResultSlots(steps)
         for k in range(warmup):
             ctx.register(dx[k % 8], dy[k % 8], p_k)
         torch.cuda.synchronize()
@@ -586,8 +598,10 @@ def run_ours(args):
             with torch.cuda.stream(stream):
                 flush.zero_()
                 ev[k][0].record(stream)
-            if kind == "host":
-                ctx.register(hx[k % 8], hy[k % 8], p_k)
+            if kind == "device":
+                ctx.register_async(dx[k % 8], dy[k % 8], p_k, slots, k)
+            elif kind == "host":
+                ctx.register_async(hx[k % 8], hy[k % 8], p_k, slots, k)
             else:
                 ctx.register(dx[k % 8], dy[k % 8], p_k)
             ev[k][1].record(stream)
@@ -595,10 +609,15 @@ def run_ours(args):
                 st = ctx.stage_times()
                 sc2.append(st["sc2"])
                 stage_log.append(st)
+        ctx.synchronize()
         torch.cuda.synchronize()
         if ws > 1:
             dist.barrier()
         torch.cuda.synchronize()
+        if kind in ("device", "host"):
+            bad = [k for k in range(steps) if slots.result(k).status != 0]
+            if bad:
+                raise RuntimeError(f"registration failed in timed steps {bad[:5]}")
         ms = [a.elapsed_time(b) for a, b in ev]
         return ms, sc2
 
@@ -608,6 +627,7 @@ def run_ours(args):
     time.sleep(0.3)
     ms_dev, _ = timed("device", args.steps, args.warmup)
     ms_host, _ = timed("host", args.steps, args.warmup)
+    ms_sync, _ = timed("sync", args.steps, args.warmup)
     ms_stages, sc2_ms = timed("stages", max(20, args.steps // 4), args.warmup)
     clocks = sampler.stop()
 
@@ -646,7 +666,9 @@ def run_ours(args):
             "config": dict(WORKLOAD, parallelism=f"replicas x{ws}"),
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 2 * 5000 * 12,
                     "d2h_bytes_per_step": ctypes.sizeof(trg.turboreg_result)},
-            "gpu_launches": LAUNCHES_PER_STEP * (2 * args.steps + len(ms_stages)),
+            "sync_call": {"ms_per_call": statistics.mean(ms_sync),
+                          "value": 1e3 / statistics.mean(ms_sync), "unit": UNIT},
+            "gpu_launches": LAUNCHES_PER_STEP * (3 * args.steps + len(ms_stages)),
             "roofline": roofline, "clocks": clocks,
             "success_rate_check": f"{ok}/8 problems RE<15deg TE<0.3m"}
     if batched is not None:

@@ -144,6 +144,26 @@ int turboreg_create(int device, int32_t max_n, int32_t max_batch, void* cuda_str
 int turboreg_register(turboreg_ctx* ctx, const float* src, const float* dst, int32_t n,
                       const turboreg_params* params, turboreg_result* out);
 
+/* The same registration enqueued on the context's stream without waiting for
+ * it, so that consecutive registrations run back to back on the GPU while
+ * the host prepares the next ones (the paper has no counterpart: it is the
+ * stream form of turboreg_register).  src, dst: device memory or page-locked
+ * host memory (copied on the stream); out: device memory or page-locked host
+ * memory, receiving the result by a copy on the stream.  Inputs and out must
+ * stay valid and unchanged until turboreg_synchronize returns.  The learned
+ * proposal is not accepted (its plain fallback needs the result on the host)
+ * and stage times are not recorded.  Argument, size and host-side finiteness
+ * errors are returned at once and nothing is enqueued (out is not written);
+ * device-side outcomes (NO_HYPOTHESIS, TIMEOUT, NONFINITE of device inputs)
+ * arrive in out->status.
+ * Errors: INVALID_ARG (also: pageable host src, dst or out, or the learned
+ *         proposal), TOO_FEW, NONFINITE, CUDA. */
+int turboreg_register_async(turboreg_ctx* ctx, const float* src, const float* dst, int32_t n,
+                            const turboreg_params* params, turboreg_result* out);
+
+/* Wait for everything enqueued on the context's stream.  Errors: CUDA. */
+int turboreg_synchronize(turboreg_ctx* ctx);
+
 /* Register `num` independent problems in one batched pass.  Problem b uses
  * matches [offsets[b], offsets[b+1]) of src_cat / dst_cat (float32 [total][3]);
  * offsets is a HOST array of num+1 non-decreasing int64 with offsets[0] = 0.

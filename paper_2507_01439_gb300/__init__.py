@@ -48,7 +48,7 @@ EXPORTED = (
     "turboreg_set_proposal_model", "turboreg_features", "turboreg_mlp_create", "turboreg_mlp_destroy",
     "turboreg_mlp_get_params", "turboreg_mlp_set_params", "turboreg_mlp_get_state", "turboreg_mlp_set_state",
     "turboreg_mlp_forward", "turboreg_mlp_grad", "turboreg_mlp_train_step", "turboreg_score_transforms",
-    "turboreg_kabsch_cliques",
+    "turboreg_kabsch_cliques", "turboreg_register_async", "turboreg_synchronize",
 )
 TURBOREG_MLP_PARAMS = 17217
 TURBOREG_NOALLOC_MAX_N = 8192
@@ -91,6 +91,10 @@ def load_library(path: str = LIB_PATH):
     lib.turboreg_register_batched.argtypes = [P, P, P, P, i32, ctypes.POINTER(turboreg_params), i32,
                                               ctypes.POINTER(turboreg_result)]
     lib.turboreg_register_batched.restype = ctypes.c_int
+    lib.turboreg_register_async.argtypes = [P, P, P, i32, ctypes.POINTER(turboreg_params), P]
+    lib.turboreg_register_async.restype = ctypes.c_int
+    lib.turboreg_synchronize.argtypes = [P]
+    lib.turboreg_synchronize.restype = ctypes.c_int
     lib.turboreg_destroy.argtypes = [P]
     lib.turboreg_destroy.restype = None
     lib.turboreg_status_string.argtypes = [ctypes.c_int]
@@ -203,6 +207,24 @@ class Result:
                       int(r.used_fallback), float(r.score))
 
 
+class ResultSlots:
+    """Page-locked host memory for `count` results of register_async (read
+    them after TurboReg.synchronize())."""
+
+    def __init__(self, count: int):
+        import torch
+        self.count = int(count)
+        self._buf = torch.empty(self.count * ctypes.sizeof(turboreg_result), dtype=torch.uint8, pin_memory=True)
+
+    def address(self, k: int):
+        if not 0 <= k < self.count:
+            raise IndexError(k)
+        return ctypes.c_void_p(self._buf.data_ptr() + k * ctypes.sizeof(turboreg_result))
+
+    def result(self, k: int) -> "Result":
+        return Result.from_c(turboreg_result.from_address(self.address(k).value))
+
+
 class TurboReg:
     """One library context (device workspace sized for max_n); not thread-safe."""
 
@@ -240,6 +262,23 @@ class TurboReg:
         self._lib.turboreg_register(self.handle, _ptr(src), _ptr(dst), int(src.shape[0]),
                                     ctypes.byref(params), ctypes.byref(out))
         return Result.from_c(out)
+
+    def register_async(self, src, dst, params: turboreg_params, slots, k: int = 0) -> None:
+        """Enqueue one registration on the context's stream without waiting;
+        its result lands in slot k of `slots` (a ResultSlots) once
+        synchronize() returns.  src, dst: CUDA tensors or page-locked host
+        tensors, unchanged until then."""
+        _check_points(src)
+        _check_points(dst, src.shape[0])
+        rc = self._lib.turboreg_register_async(self.handle, _ptr(src), _ptr(dst), int(src.shape[0]),
+                                               ctypes.byref(params), slots.address(k))
+        if rc != OK:
+            raise RuntimeError(f"turboreg_register_async failed: {status_string(rc)}")
+
+    def synchronize(self) -> None:
+        rc = self._lib.turboreg_synchronize(self.handle)
+        if rc != OK:
+            raise RuntimeError(f"turboreg_synchronize failed: {status_string(rc)}")
 
     def register_batched(self, src_cat, dst_cat, offsets, params) -> list:
         _check_points(src_cat)

@@ -101,6 +101,11 @@ struct turboreg_ctx {
     bool has_model = false;
     EncodeTiledFn encode = nullptr;
     cudaEvent_t ev[kNumStages + 1] = {};
+    // the descriptor uploads read the page-locked staging (ws.h_views, h_pre,
+    // h_maps) when the stream reaches them; it is rewritten only after this
+    // event (recorded behind each upload) has completed
+    cudaEvent_t desc_done = nullptr;
+    bool desc_pending = false;
     float stage_ms[kNumStages] = {};
     int32_t last_n = 0, last_npad = 0, last_k1 = 0, last_k2 = 0;
     bool have_times = false;
@@ -328,6 +333,10 @@ int build_plan(turboreg_ctx* c, int32_t num, const int64_t* in_off, const int32_
                const turboreg_params* const* prm, Plan& plan)
 {
     Workspace& ws = c->ws;
+    if (c->desc_pending) {   // a queued upload may still read the staging rewritten below
+        TR_CHECK(cudaEventSynchronize(c->desc_done));
+        c->desc_pending = false;
+    }
     plan = Plan();
     plan.num = num;
     plan.bitset = (prm[0]->flags & TURBOREG_FLAG_SC2_BITSET) != 0;
@@ -367,6 +376,8 @@ int upload_desc(turboreg_ctx* c, int32_t num, void* dev, Batch& bt, cudaStream_t
     TR_CHECK(cudaMemcpyAsync(d, ws.h_views, v, cudaMemcpyHostToDevice, s));
     TR_CHECK(cudaMemcpyAsync(d + po, ws.h_pre, p, cudaMemcpyHostToDevice, s));
     TR_CHECK(cudaMemcpyAsync(d + mo, ws.h_maps, sizeof(CUtensorMap) * 2 * num, cudaMemcpyHostToDevice, s));
+    TR_CHECK(cudaEventRecord(c->desc_done, s));
+    c->desc_pending = true;
     bt.views = reinterpret_cast<const ProbView*>(d);
     bt.pre = reinterpret_cast<const int32_t*>(d + po);
     bt.maps = reinterpret_cast<const CUtensorMap*>(d + mo);
@@ -472,6 +483,8 @@ int run_plan(turboreg_ctx* c, const Plan& pl, bool no_graph, const float* dsrc, 
             if (!sl.used) { g = &sl; break; }
             if (sl.stamp < g->stamp) g = &sl;
         }
+        // an evicted graph may still have launches queued (asynchronous calls)
+        if (g->used) TR_CHECK(cudaStreamSynchronize(c->stream));
         drop_slot(*g);
         TR_CHECK(cudaMalloc(&g->desc, desc_bytes(pl.num)));
         int rc = upload_desc(c, pl.num, g->desc, g->batch, c->stream);
@@ -546,6 +559,56 @@ bool needs_fallback(const turboreg_result& r, int32_t n, const turboreg_params* 
     if (r.status != TURBOREG_OK) return false;
     const int32_t floor_in = p->learned_min_inliers > 0 ? p->learned_min_inliers : (n / 200 > 10 ? n / 200 : 10);
     return r.inlier_count < floor_in;
+}
+
+enum PtrKind { kPtrDevice, kPtrPinned, kPtrPageable };
+
+PtrKind pointer_kind(const void* p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return kPtrPageable;
+    }
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return kPtrDevice;
+    return a.type == cudaMemoryTypeHost ? kPtrPinned : kPtrPageable;
+}
+
+// Checks, input copies and the launch of one registration (graph replay or
+// direct launches); the result is left in ws.res.  async: host inputs must be
+// page-locked.  *s_in, *d_in receive the device inputs used.
+int enqueue_single(turboreg_ctx* c, const float* src, const float* dst, int32_t n, const turboreg_params* p,
+                   bool async, const float** s_in, const float** d_in, bool* timed)
+{
+    int rc = check_params(c, n, p);
+    if (rc != TURBOREG_OK) return rc;
+    TR_CHECK(cudaSetDevice(c->device));
+    const PtrKind ks = pointer_kind(src), kd = pointer_kind(dst);
+    if (async && (ks == kPtrPageable || kd == kPtrPageable)) return TURBOREG_ERR_INVALID_ARG;
+    const size_t bytes = static_cast<size_t>(n) * 3 * sizeof(float);
+    if (ks != kPtrDevice) {
+        if (!host_finite(src, static_cast<size_t>(n) * 3)) return TURBOREG_ERR_NONFINITE;
+        TR_CHECK(cudaMemcpyAsync(c->ws.in_src, src, bytes, cudaMemcpyHostToDevice, c->stream));
+        *s_in = c->ws.in_src;
+    }
+    if (kd != kPtrDevice) {
+        if (!host_finite(dst, static_cast<size_t>(n) * 3)) return TURBOREG_ERR_NONFINITE;
+        TR_CHECK(cudaMemcpyAsync(c->ws.in_dst, dst, bytes, cudaMemcpyHostToDevice, c->stream));
+        *d_in = c->ws.in_dst;
+    }
+    Plan pl;
+    const int64_t off0 = 0;
+    rc = build_plan(c, 1, &off0, &n, &p, pl);
+    if (rc != TURBOREG_OK) return rc;
+    const bool no_graph = (p->flags & TURBOREG_FLAG_NO_GRAPH) != 0;
+    rc = run_plan(c, pl, no_graph, *s_in, *d_in);
+    if (rc != TURBOREG_OK) return rc;
+    c->last_n = n;
+    c->last_npad = round_up(n, kSc2BN);
+    c->last_k1 = p->k1;
+    c->last_k2 = p->k2;
+    *timed = !async && pl.timed != 0;
+    return TURBOREG_OK;
 }
 
 }  // namespace
@@ -627,6 +690,10 @@ int turboreg_create(int device, int32_t max_n, int32_t max_batch, void* cuda_str
             return TURBOREG_ERR_CUDA;
         }
     }
+    if (cudaEventCreateWithFlags(&c->desc_done, cudaEventDisableTiming) != cudaSuccess) {
+        turboreg_destroy(c);
+        return TURBOREG_ERR_CUDA;
+    }
     cudaDriverEntryPointQueryResult q;
     void* fn = nullptr;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
@@ -657,6 +724,7 @@ void turboreg_destroy(turboreg_ctx* c)
     for (auto& sl : c->gslot) drop_slot(sl);
     for (int k = 0; k <= kNumStages; ++k)
         if (c->ev[k]) cudaEventDestroy(c->ev[k]);
+    if (c->desc_done) cudaEventDestroy(c->desc_done);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     free_ws(c->ws);
     if (c->host_res) cudaFreeHost(c->host_res);
@@ -668,48 +736,22 @@ int turboreg_register(turboreg_ctx* c, const float* src, const float* dst, int32
                       turboreg_result* out)
 {
     if (!c || !src || !dst || !out) return TURBOREG_ERR_INVALID_ARG;
-    int rc = check_params(c, n, p);
-    if (rc != TURBOREG_OK) {
-        fail_result(out, rc);
-        return rc;
-    }
-    TR_CHECK(cudaSetDevice(c->device));
-    const bool dsrc = is_device_ptr(src), ddst = is_device_ptr(dst);
     const float* s_in = src;
     const float* d_in = dst;
-    const size_t bytes = static_cast<size_t>(n) * 3 * sizeof(float);
-    if (!dsrc) {
-        if (!host_finite(src, static_cast<size_t>(n) * 3)) rc = TURBOREG_ERR_NONFINITE;
-        else {
-            TR_CHECK(cudaMemcpyAsync(c->ws.in_src, src, bytes, cudaMemcpyHostToDevice, c->stream));
-            s_in = c->ws.in_src;
-        }
-    }
-    if (!ddst && rc == TURBOREG_OK) {
-        if (!host_finite(dst, static_cast<size_t>(n) * 3)) rc = TURBOREG_ERR_NONFINITE;
-        else {
-            TR_CHECK(cudaMemcpyAsync(c->ws.in_dst, dst, bytes, cudaMemcpyHostToDevice, c->stream));
-            d_in = c->ws.in_dst;
-        }
-    }
-    if (rc != TURBOREG_OK) {
+    bool timed = false;
+    int rc = enqueue_single(c, src, dst, n, p, false, &s_in, &d_in, &timed);
+    if (rc == TURBOREG_ERR_NONFINITE) {   // host inputs rejected before any device work
         TR_CHECK(cudaStreamSynchronize(c->stream));
         fail_result(out, rc);
         return rc;
     }
-    Plan pl;
-    const int64_t off0 = 0;
-    rc = build_plan(c, 1, &off0, &n, &p, pl);
-    if (rc != TURBOREG_OK) return rc;
-    rc = run_plan(c, pl, (p->flags & TURBOREG_FLAG_NO_GRAPH) != 0, s_in, d_in);
-    if (rc != TURBOREG_OK) return rc;
+    if (rc != TURBOREG_OK) {
+        if (rc == TURBOREG_ERR_INVALID_ARG || rc == TURBOREG_ERR_TOO_FEW) fail_result(out, rc);
+        return rc;
+    }
     TR_CHECK(cudaMemcpyAsync(c->host_res, c->ws.res, sizeof(turboreg_result), cudaMemcpyDeviceToHost, c->stream));
     TR_CHECK(cudaStreamSynchronize(c->stream));
-    c->last_n = n;
-    c->last_npad = round_up(n, kSc2BN);
-    c->last_k1 = p->k1;
-    c->last_k2 = p->k2;
-    c->have_times = pl.timed != 0;
+    c->have_times = timed;
     rc = collect_times(c);
     if (rc != TURBOREG_OK) return rc;
     *out = c->host_res[0];
@@ -722,6 +764,30 @@ int turboreg_register(turboreg_ctx* c, const float* src, const float* dst, int32
         return rc2;
     }
     return out->status;
+}
+
+int turboreg_register_async(turboreg_ctx* c, const float* src, const float* dst, int32_t n,
+                            const turboreg_params* p, turboreg_result* out)
+{
+    if (!c || !src || !dst || !out || !p) return TURBOREG_ERR_INVALID_ARG;
+    if (p->proposal == TURBOREG_PROPOSAL_LEARNED) return TURBOREG_ERR_INVALID_ARG;
+    if (pointer_kind(out) == kPtrPageable) return TURBOREG_ERR_INVALID_ARG;
+    const float* s_in = src;
+    const float* d_in = dst;
+    bool timed = false;
+    const int rc = enqueue_single(c, src, dst, n, p, true, &s_in, &d_in, &timed);
+    if (rc != TURBOREG_OK) return rc;
+    TR_CHECK(cudaMemcpyAsync(out, c->ws.res, sizeof(turboreg_result), cudaMemcpyDefault, c->stream));
+    c->have_times = false;
+    return TURBOREG_OK;
+}
+
+int turboreg_synchronize(turboreg_ctx* c)
+{
+    if (!c) return TURBOREG_ERR_INVALID_ARG;
+    TR_CHECK(cudaSetDevice(c->device));
+    TR_CHECK(cudaStreamSynchronize(c->stream));
+    return TURBOREG_OK;
 }
 
 int turboreg_register_batched(turboreg_ctx* c, const float* src_cat, const float* dst_cat, const int64_t* offsets,
@@ -847,6 +913,8 @@ int64_t turboreg_debug_copy(turboreg_ctx* c, int which, void* dst, int64_t max_b
 {
     if (!c || !dst || max_bytes < 0) return -TURBOREG_ERR_INVALID_ARG;
     if (cudaSetDevice(c->device) != cudaSuccess) return -TURBOREG_ERR_CUDA;
+    // asynchronous registrations may still be running on the context's stream
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return -TURBOREG_ERR_CUDA;
     Ctl h;
     if (cudaMemcpy(&h, c->ws.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost) != cudaSuccess) return -TURBOREG_ERR_CUDA;
     turboreg_params p0;
