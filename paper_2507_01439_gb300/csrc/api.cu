@@ -48,7 +48,7 @@ struct Workspace {
     uint8_t* a8 = nullptr;           // [slots][np^2]
     uint32_t* bits = nullptr;        // [slots][np^2 / 32]
     uint16_t* w = nullptr;           // [slots][np^2]
-    int32_t* rows = nullptr;         // [slots][6][np]: rowscore, deg, active (int4 per row)
+    int32_t* rows = nullptr;         // [slots][7][np]: rowscore, deg, active (int4 per row), rowmax
     uint32_t* hist = nullptr;        // [slots][np + 1]
     uint64_t* cand = nullptr;        // [slots][K1_MAX]
     int4* piv = nullptr;             // [slots][K1_MAX]
@@ -182,7 +182,7 @@ int alloc_ws(Workspace& ws, int32_t max_n, int32_t slots)
     if (e == cudaSuccess) e = dalloc(&ws.a8, S * n2);
     if (e == cudaSuccess) e = dalloc(&ws.bits, S * n2 / 32);
     if (e == cudaSuccess) e = dalloc(&ws.w, S * n2);
-    if (e == cudaSuccess) e = dalloc(&ws.rows, S * 6 * np);
+    if (e == cudaSuccess) e = dalloc(&ws.rows, S * 7 * np);
     if (e == cudaSuccess) e = dalloc(&ws.hist, S * (np + 1));
     if (e == cudaSuccess) e = dalloc(&ws.cand, S * TURBOREG_K1_MAX);
     if (e == cudaSuccess) e = dalloc(&ws.piv, S * TURBOREG_K1_MAX);
@@ -279,10 +279,11 @@ ProbView make_view(turboreg_ctx* c, int slot, int64_t in_off, int32_t n, const t
     v.a8 = ws.a8 + s * n2;
     v.bits = ws.bits + s * n2 / 32;
     v.w = ws.w + s * n2;
-    int32_t* rows = ws.rows + s * 6 * np;
+    int32_t* rows = ws.rows + s * 7 * np;
     v.rowscore = rows;
     v.deg = rows + np;
     v.active = reinterpret_cast<int4*>(rows + 2 * np);   // np is a multiple of 256: 16-byte aligned
+    v.rowmax = rows + 6 * np;
     v.hist = ws.hist + s * (np + 1);
     v.cand = ws.cand + s * TURBOREG_K1_MAX;
     v.piv = ws.piv + s * TURBOREG_K1_MAX;
@@ -343,13 +344,23 @@ int build_plan(turboreg_ctx* c, int32_t num, const int64_t* in_off, const int32_
     plan.timed = num == 1 && (prm[0]->flags & TURBOREG_FLAG_STAGE_TIMES) != 0;
     plan.learned = prm[0]->proposal == TURBOREG_PROPOSAL_LEARNED;
     plan.gemm_form = (prm[0]->flags & TURBOREG_FLAG_SC2_SINGLE_CTA) ? 0 : (prm[0]->flags & TURBOREG_FLAG_SC2_MULTICAST) ? 1 : 2;
-    plan.vpw = (prm[0]->flags & TURBOREG_FLAG_VERIFY_PTS32) ? 32 : (prm[0]->flags & TURBOREG_FLAG_VERIFY_PTS128) ? 128 : 64;
+    // verification tile: the flags' width for every problem, or for a single
+    // problem without tile flags the balanced width (one even wave); the
+    // kernel's points per warp (plan.vpw) is the narrowest that holds them all
+    const bool vflag = (prm[0]->flags & (TURBOREG_FLAG_VERIFY_PTS32 | TURBOREG_FLAG_VERIFY_PTS128)) != 0;
+    const int32_t vpw_flag = (prm[0]->flags & TURBOREG_FLAG_VERIFY_PTS32) ? 32
+                             : (prm[0]->flags & TURBOREG_FLAG_VERIFY_PTS128) ? 128 : 64;
+    int32_t vppb_max = 0;
     plan.k2_common = prm[0]->k2;
     for (int st = 0; st < kNumBatchStages; ++st) ws.h_pre[st * (num + 1)] = 0;
     for (int32_t b = 0; b < num; ++b) {
         ws.h_views[b] = make_view(c, b, in_off[b], n[b], prm[b]);
+        const int32_t vppb = (num == 1 && !vflag) ? balanced_vppb(n[b], prm[b]->k1 * prm[b]->k2, device_sms())
+                                                  : 4 * vpw_flag;
+        ws.h_views[b].vppb = vppb;
+        if (vppb > vppb_max) vppb_max = vppb;
         int32_t blocks[kNumBatchStages];
-        stage_blocks(n[b], prm[b]->k1, prm[b]->k2, plan.vpw, blocks);
+        stage_blocks(n[b], prm[b]->k1, prm[b]->k2, vppb, blocks);
         for (int st = 0; st < kNumBatchStages; ++st) {
             plan.tot[st] += blocks[st];
             ws.h_pre[st * (num + 1) + b + 1] = plan.tot[st];
@@ -362,6 +373,7 @@ int build_plan(turboreg_ctx* c, int32_t num, const int64_t* in_off, const int32_
             if (rc != TURBOREG_OK) return rc;
         }
     }
+    plan.vpw = vppb_max <= 4 * 32 ? 32 : vppb_max <= 4 * 64 ? 64 : 128;
     return TURBOREG_OK;
 }
 
@@ -705,6 +717,7 @@ int turboreg_create(int device, int32_t max_n, int32_t max_batch, void* cuda_str
     c->encode = reinterpret_cast<EncodeTiledFn>(fn);
     cudaError_t se = sc2_tcgen05_setup();
     if (se == cudaSuccess) se = topk_setup();
+    if (se == cudaSuccess) se = verify_pgs_setup();
     if (se == cudaSuccess) se = mlp_setup();
     if (se != cudaSuccess) {
         std::fprintf(stderr, "turboreg: kernel set-up failed: %s\n", cudaGetErrorString(se));

@@ -64,6 +64,7 @@ __global__ void __launch_bounds__(256) pack_kernel(ManyViews vs, const float* __
         p8[1] = make_float4(a[4], a[5], 0.f, 0.f);
         v.rowscore[k] = 0;
         v.deg[k] = 0;
+        if (v.rowmax) v.rowmax[k] = 0;
         v.hist[k] = 0;
     }
     if (k == 0) v.hist[v.n_pad] = 0;
@@ -137,6 +138,7 @@ __device__ __forceinline__ uint4 bits16_to_fp8(uint32_t b16)
 __global__ void __launch_bounds__(kThreads) compat_kernel(ManyViews vs)
 {
     pdl_wait();
+    pdl_release();
     __shared__ __align__(128) float4 srow[kT][2];     // row points (x0,x1,x2,y0 | y1,y2,-,-)
     __shared__ __align__(16) uint16_t colpart[kT][8];  // column c: the 16-row masks of the 8 warps
     __shared__ __align__(8) uint64_t bar;

@@ -20,6 +20,7 @@ namespace {
 __global__ void __launch_bounds__(128) kabsch_kernel(ManyViews vs)
 {
     pdl_wait();
+    pdl_release();
     int lb;
     const ProbView v = vs.get(ST_KABSCH, blockIdx.x, lb);
     const int h = lb * blockDim.x + threadIdx.x;
@@ -29,7 +30,8 @@ __global__ void __launch_bounds__(128) kabsch_kernel(ManyViews vs)
 }
 
 // Verification.  A block holds 128 hypotheses (R, t staged in shared memory)
-// and 256 correspondences (32-byte records); each of its 4 warps takes 64 of
+// and 256 correspondences (as packed pairs (v, v), so a point feeds the
+// packed arithmetic straight from shared memory); each of its 4 warps takes 64 of
 // the correspondences for all 128 hypotheses, 4 per lane, evaluated as two
 // packed pairs: e = R x + (t - y), d2 = |e|^2 with fma.rn.f32x2 (the same
 // rounding as the scalar expression, two hypotheses per instruction).  The
@@ -49,7 +51,7 @@ constexpr float kScoreUnits = 4194304.f;   // 2^22 units per theta (MAE) or thet
 
 template <int PW>
 struct VerifyShared {
-    float4 sp[kVWarps * PW][2];
+    ulonglong2 sp[kVWarps * PW][3];   // points as packed pairs (v, v): x0 x1 | x2 y0 | y1 y2
     float4 srt[kVHyp][4];
     int scnt[kVWarps][kVHyp];
     uint32_t ssc[kVWarps][kVHyp];
@@ -59,17 +61,26 @@ struct VerifyShared {
 template <int kScore, int PW>
 __device__ __forceinline__ void verify_body(const ProbView& v, int lb, VerifyShared<PW>& sh)
 {
-    constexpr int kVPtsWarp = PW;
-    constexpr int kVPts = kVWarps * PW;
-    const int npb = (v.n + kVPts - 1) / kVPts;          // point blocks of this problem
+    const int vppb = v.vppb;                            // matches per block, <= kVWarps * PW
+    const int npb = (v.n + vppb - 1) / vppb;            // match blocks of this problem
     const int nh = v.ctl->n_pivots * v.k2;
     const int h0 = (lb / npb) * kVHyp;
     if (h0 >= nh) return;
-    const int k0 = (lb % npb) * kVPts;
+    const int k0 = (lb % npb) * vppb;
+    const int kn = min(vppb, v.n - k0);                 // matches of this block
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     {
         const float4* src = reinterpret_cast<const float4*>(v.pts8 + (size_t)k0 * 8);
-        for (int q = threadIdx.x; q < 2 * kVPts; q += blockDim.x) (&sh.sp[0][0])[q] = src[q];
+        for (int q = threadIdx.x; q < kn; q += blockDim.x) {
+            const float4 a = src[2 * q], b = src[2 * q + 1];
+            auto dup = [](float f) {
+                const unsigned long long u = __float_as_uint(f);
+                return (u << 32) | u;
+            };
+            sh.sp[q][0] = make_ulonglong2(dup(a.x), dup(a.y));
+            sh.sp[q][1] = make_ulonglong2(dup(a.z), dup(a.w));
+            sh.sp[q][2] = make_ulonglong2(dup(b.x), dup(b.y));
+        }
         const int slot = h0 + threadIdx.x;
         float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0, r3 = r0;
         bool ok = false;
@@ -101,16 +112,20 @@ __device__ __forceinline__ void verify_body(const ProbView& v, int lb, VerifySha
     }
     const float th = v.theta;
     const float th2 = th * th;
+    // d2 <= th2 compared on the bit patterns: both are non-negative (a sum of
+    // squares, a square), so the order is the integer order; NaN (an invalid
+    // hypothesis) is above every finite threshold
+    const uint32_t th2b = __float_as_uint(th2);
     const float qs = kScore == TURBOREG_SCORE_MAE ? kScoreUnits / th : kScoreUnits / th2;
-    const int kb = warp * kVPtsWarp;
-    const int cnt = max(0, min(kVPtsWarp, v.n - k0 - kb));
+    const int ppw = (vppb + kVWarps - 1) / kVWarps;     // matches per warp
+    const int kb = warp * ppw;
+    const int cnt = max(0, min(ppw, kn - kb));
     int in[4] = {0, 0, 0, 0};
     uint32_t sc[4] = {0u, 0u, 0u, 0u};
 #pragma unroll 2
     for (int k = 0; k < cnt; ++k) {
-        const float4 pa = sh.sp[kb + k][0], pb = sh.sp[kb + k][1];
-        const f2 X0 = pk(pa.x, pa.x), X1 = pk(pa.y, pa.y), X2 = pk(pa.z, pa.z);
-        const f2 Y0 = pk(pa.w, pa.w), Y1 = pk(pb.x, pb.x), Y2 = pk(pb.y, pb.y);
+        const ulonglong2 q0 = sh.sp[kb + k][0], q1 = sh.sp[kb + k][1], q2 = sh.sp[kb + k][2];
+        const f2 X0{q0.x}, X1{q0.y}, X2{q1.x}, Y0{q1.y}, Y1{q2.x}, Y2{q2.y};
 #pragma unroll
         for (int pr = 0; pr < 2; ++pr) {
             const f2 e0 = fma2(R[pr][0], X0, fma2(R[pr][1], X1, fma2(R[pr][2], X2, sub2(T[pr][0], Y0))));
@@ -119,8 +134,8 @@ __device__ __forceinline__ void verify_body(const ProbView& v, int lb, VerifySha
             const f2 d2 = fma2(e0, e0, fma2(e1, e1, mul2(e2, e2)));
             float lo, hi;
             upk(d2, lo, hi);
-            in[2 * pr] += lo <= th2 ? 1 : 0;
-            in[2 * pr + 1] += hi <= th2 ? 1 : 0;
+            in[2 * pr] += static_cast<int>((__float_as_uint(lo) - th2b - 1u) >> 31);
+            in[2 * pr + 1] += static_cast<int>((__float_as_uint(hi) - th2b - 1u) >> 31);
             if (kScore == TURBOREG_SCORE_MAE) {
                 // fminf(NaN, theta) = theta: an invalid hypothesis is never selected anyway
                 sc[2 * pr] += __float2uint_rn(fminf(sqrtf(lo), th) * qs);
@@ -159,6 +174,7 @@ template <int PW>
 __global__ void __launch_bounds__(128) verify_kernel(ManyViews vs)
 {
     pdl_wait();
+    pdl_release();
     __shared__ __align__(16) VerifyShared<PW> sh;
     int lb;
     const ProbView v = vs.get(ST_VERIFY, blockIdx.x, lb);
@@ -173,12 +189,12 @@ __global__ void __launch_bounds__(128) verify_kernel(ManyViews vs)
 // and ties of the score go to the lower h).  Inlier number: (IN + 1) << 32 |
 // ~h.  Capped error: (2^40 - 1 - units) << 20 | (2^20 - 1 - h); the unit sum
 // is at most N (2^22 + 1) < 2^38 and h < K1_MAX * K2_MAX = 2^17.
-__device__ __forceinline__ unsigned long long select_key(const ProbView& v, int h)
+__device__ __forceinline__ unsigned long long select_key(int scoring, int inl, unsigned long long score, int h)
 {
-    if (v.scoring == TURBOREG_SCORE_IN)
-        return (static_cast<unsigned long long>(static_cast<uint32_t>(__ldcg(v.inl + h)) + 1u) << 32) |
+    if (scoring == TURBOREG_SCORE_IN)
+        return (static_cast<unsigned long long>(static_cast<uint32_t>(inl) + 1u) << 32) |
                (0xFFFFFFFFull - static_cast<unsigned long long>(h));
-    return ((0xFFFFFFFFFFull - __ldcg(v.score + h)) << 20) | (0xFFFFFull - static_cast<unsigned long long>(h));
+    return ((0xFFFFFFFFFFull - score) << 20) | (0xFFFFFull - static_cast<unsigned long long>(h));
 }
 
 __device__ __forceinline__ int key_hypothesis(const ProbView& v, unsigned long long key)
@@ -194,30 +210,42 @@ __device__ __forceinline__ int key_hypothesis(const ProbView& v, unsigned long l
 __global__ void __launch_bounds__(1024) finalize_kernel(ManyViews vs)
 {
     pdl_wait();
+    pdl_release();
     int lb;
     const ProbView v = vs.get(ST_FINAL, blockIdx.x, lb);
     __shared__ unsigned long long sbest[32];
     __shared__ int scnt[32], sfp[32];
-    const int np = v.ctl->n_pivots;
-    const int nh = np * v.k2;
+    __shared__ float srec[16];
+    __shared__ int4 scl;
+    __shared__ int sinl;
+    __shared__ unsigned long long sscore;
+    // one round of loads: the pivot count with every slot's flags and inlier
+    // number (and score), slots up to K1 K2 (the buffers' capacity), masked
+    // by the pivot count afterwards
+    const int hmax = v.k1 * v.k2;
+    const int np = __ldcg(&v.ctl->n_pivots);
     unsigned long long best = 0ull;
     int nvalid = 0, nfp = 0;
-    // eight hypotheses per thread in flight: the flags, then the keys of the valid ones
-    for (int h0 = threadIdx.x; h0 < nh; h0 += 8 * blockDim.x) {
-        uint32_t fl[8];
+    for (int h0 = threadIdx.x; h0 < hmax; h0 += 4 * blockDim.x) {
+        uint32_t fl[4];
+        int in4[4];
+        unsigned long long sc4[4];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
+        for (int u = 0; u < 4; ++u) {
             const int h = h0 + u * blockDim.x;
-            fl[u] = h < nh ? static_cast<uint32_t>(__ldcg(reinterpret_cast<const int*>(v.rt) + (size_t)h * 16 + 13)) : 0u;
+            fl[u] = h < hmax ? static_cast<uint32_t>(__ldcg(reinterpret_cast<const int*>(v.rt) + (size_t)h * 16 + 13)) : 0u;
+            in4[u] = h < hmax ? __ldcg(v.inl + h) : 0;
+            sc4[u] = (h < hmax && v.scoring != TURBOREG_SCORE_IN) ? __ldcg(v.score + h) : 0ull;
         }
-        unsigned long long key[8];
+        const int nh = np * v.k2;
 #pragma unroll
-        for (int u = 0; u < 8; ++u) key[u] = (fl[u] & 1u) ? select_key(v, h0 + u * blockDim.x) : 0ull;
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            nfp += (fl[u] & 2u) ? 1 : 0;
-            nvalid += (fl[u] & 1u) ? 1 : 0;
-            best = key[u] > best ? key[u] : best;
+        for (int u = 0; u < 4; ++u) {
+            const int h = h0 + u * blockDim.x;
+            const uint32_t f = h < nh ? fl[u] : 0u;
+            const unsigned long long key = (f & 1u) ? select_key(v.scoring, in4[u], sc4[u], h) : 0ull;
+            nfp += (f & 2u) ? 1 : 0;
+            nvalid += (f & 1u) ? 1 : 0;
+            best = key > best ? key : best;
         }
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -229,13 +257,32 @@ __global__ void __launch_bounds__(1024) finalize_kernel(ManyViews vs)
     }
     if (lane == 0) { sbest[warp] = best; scnt[warp] = nvalid; sfp[warp] = nfp; }
     __syncthreads();
-    if (threadIdx.x != 0) return;
-    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
-        best = sbest[w] > best ? sbest[w] : best;
-        nvalid += scnt[w];
-        nfp += sfp[w];
+    if (warp == 0) {
+        const int nw = static_cast<int>(blockDim.x >> 5);
+        best = lane < nw ? sbest[lane] : 0ull;
+        nvalid = lane < nw ? scnt[lane] : 0;
+        nfp = lane < nw ? sfp[lane] : 0;
+        for (int off = 16; off >= 1; off >>= 1) {
+            const unsigned long long o = __shfl_xor_sync(0xffffffffu, best, off);
+            best = o > best ? o : best;
+            nvalid += __shfl_xor_sync(0xffffffffu, nvalid, off);
+            nfp += __shfl_xor_sync(0xffffffffu, nfp, off);
+        }
+        // second round: the winner's record, one load per lane
+        if (best != 0ull) {
+            const int h = key_hypothesis(v, best);
+            if (lane < 16) srec[lane] = __ldcg(v.rt + (size_t)h * 16 + lane);
+            else if (lane == 16) scl = v.cliques[h];
+            else if (lane == 17) sinl = __ldcg(v.inl + h);
+            else if (lane == 18 && v.scoring != TURBOREG_SCORE_IN) sscore = __ldcg(v.score + h);
+        }
+        if (lane == 0) { sbest[0] = best; scnt[0] = nvalid; sfp[0] = nfp; }
     }
-    best = sbest[0] > best ? sbest[0] : best;
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    best = sbest[0];
+    nvalid = scnt[0];
+    nfp = sfp[0];
     v.ctl->n_valid = nvalid;
     v.ctl->n_fp64 = nfp;
     turboreg_result r;
@@ -249,7 +296,7 @@ __global__ void __launch_bounds__(1024) finalize_kernel(ManyViews vs)
     r.n_valid = nvalid;
     r.used_fp64 = 0;
     r.used_fallback = 0;
-    const uint32_t err = v.ctl->err;
+    const uint32_t err = __ldcg(&v.ctl->err);
     if (err & TR_ERR_NONFINITE) {
         r.status = TURBOREG_ERR_NONFINITE;
     } else if (err & TR_ERR_TIMEOUT) {
@@ -260,21 +307,18 @@ __global__ void __launch_bounds__(1024) finalize_kernel(ManyViews vs)
         r.status = TURBOREG_ERR_NO_HYPOTHESIS;
     } else {
         const int h = key_hypothesis(v, best);
-        // L2 reads: the FP64 list's R, t were written while this SM may hold older copies
-        const float* rt = v.rt + (size_t)h * 16;
-        for (int q = 0; q < 9; ++q) r.R[q] = __ldcg(rt + q);
-        for (int q = 0; q < 3; ++q) r.t[q] = __ldcg(rt + 9 + q);
-        const int4 cl = v.cliques[h];
-        r.clique[0] = cl.x; r.clique[1] = cl.y; r.clique[2] = cl.z;
-        r.inlier_count = __ldcg(v.inl + h);
+        for (int q = 0; q < 9; ++q) r.R[q] = srec[q];
+        for (int q = 0; q < 3; ++q) r.t[q] = srec[9 + q];
+        r.clique[0] = scl.x; r.clique[1] = scl.y; r.clique[2] = scl.z;
+        r.inlier_count = sinl;
         if (v.scoring == TURBOREG_SCORE_IN) {
             r.score = static_cast<float>(r.inlier_count);
         } else {
             const double unit = v.scoring == TURBOREG_SCORE_MAE ? (double)v.theta : (double)v.theta * v.theta;
-            r.score = static_cast<float>((double)__ldcg(v.score + h) * unit / (4194304.0 * v.n));
+            r.score = static_cast<float>((double)sscore * unit / (4194304.0 * v.n));
         }
         r.hypothesis = h;
-        r.used_fp64 = (static_cast<uint32_t>(__ldcg(reinterpret_cast<const int*>(rt) + 13)) & 2u) ? 1 : 0;
+        r.used_fp64 = (__float_as_uint(srec[13]) & 2u) ? 1 : 0;
         r.status = TURBOREG_OK;
     }
     *v.res = r;
@@ -289,6 +333,19 @@ void launch_kabsch(const Batch& b, int total, cudaStream_t s)
     launch_pdl(kabsch_kernel, total, 128, 0, s, ManyViews{b});
 }
 
+cudaError_t verify_setup()
+{
+    cudaError_t e = cudaFuncSetAttribute(verify_kernel<32>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                         cudaSharedmemCarveoutMaxShared);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(verify_kernel<64>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 cudaSharedmemCarveoutMaxShared);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(verify_kernel<128>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 cudaSharedmemCarveoutMaxShared);
+    return e;
+}
+
 void launch_verify(const Batch& b, int total, int pw, cudaStream_t s)
 {
     if (pw == 32) launch_pdl(verify_kernel<32>, total, 128, 0, s, ManyViews{b});
@@ -297,9 +354,20 @@ void launch_verify(const Batch& b, int total, int pw, cudaStream_t s)
 }
 
 // Per-problem block counts of every stage.
-void stage_blocks(int32_t n, int32_t k1, int32_t k2, int32_t verify_pw, int32_t blocks[kNumBatchStages])
+int32_t balanced_vppb(int32_t n, int32_t nh, int32_t num_sms)
 {
-    const int32_t vpts = kVWarps * verify_pw;
+    const int32_t nhb = (nh + kVHyp - 1) / kVHyp;
+    const int32_t npb_min = (n + 4 * 128 - 1) / (4 * 128);             // capacity of the widest tile
+    int32_t npb = nhb > 0 ? (4 * num_sms) / nhb : npb_min;
+    if (npb < npb_min) npb = npb_min;
+    int32_t vppb = (n + npb - 1) / npb;
+    vppb = (vppb + kVWarps - 1) / kVWarps * kVWarps;
+    return vppb < 64 ? 64 : vppb;                                      // at least 16 matches per warp
+}
+
+void stage_blocks(int32_t n, int32_t k1, int32_t k2, int32_t vppb, int32_t blocks[kNumBatchStages])
+{
+    const int32_t vpts = vppb;
     const int32_t n_pad = (n + kSc2BN - 1) / kSc2BN * kSc2BN;
     const int32_t T = n_pad / 128;
     const int32_t nb = n_pad / kSc2BN;

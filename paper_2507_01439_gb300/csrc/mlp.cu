@@ -241,6 +241,7 @@ __global__ void __launch_bounds__(kRows, 1) mlp_fwd_kernel(const float* feat, in
 __global__ void __launch_bounds__(kRows, 1) mlp_proposal_kernel(ManyViews vs, const float* wbf)
 {
     pdl_wait();
+    pdl_release();
     extern __shared__ uint8_t smem_raw[];
     int lb;
     const ProbView v = vs.get(ST_MLP, blockIdx.x, lb);
@@ -252,6 +253,7 @@ __global__ void __launch_bounds__(kRows, 1) mlp_proposal_kernel(ManyViews vs, co
 __global__ void __launch_bounds__(1024) features_kernel(ManyViews vs)
 {
     pdl_wait();
+    pdl_release();
     __shared__ float red[32][8];
     __shared__ float tot[8];
     int lb;

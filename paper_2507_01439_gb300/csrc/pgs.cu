@@ -43,6 +43,8 @@ __global__ void __launch_bounds__(256, 2) pgs_kernel(ManyViews vs)
 {
     __shared__ int scand[8][kCand];
     pdl_wait();
+    // no early release: the verification blocks, placed while these still hold
+    // registers, would spread unevenly over the SMs (measured slower)
     int lb;
     const ProbView v = vs.get(ST_PGS, blockIdx.x, lb);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -236,6 +238,18 @@ __global__ void __launch_bounds__(256, 2) pgs_kernel(ManyViews vs)
 
 }  // namespace
 
+cudaError_t pgs_setup()
+{
+    cudaError_t e = cudaSuccess;
+    const void* fns[] = {reinterpret_cast<const void*>(pgs_kernel<0>), reinterpret_cast<const void*>(pgs_kernel<1>),
+                         reinterpret_cast<const void*>(pgs_kernel<2>), reinterpret_cast<const void*>(pgs_kernel<3>),
+                         reinterpret_cast<const void*>(pgs_kernel<4>)};
+    for (const void* f : fns)
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    return e;
+}
+
 // k2 is the common K2 of the batch, or 0 when problems differ (generic list)
 void launch_pgs(const Batch& b, int total, int k2, cudaStream_t s)
 {
@@ -247,6 +261,14 @@ void launch_pgs(const Batch& b, int total, int k2, cudaStream_t s)
         case 4: launch_pdl(pgs_kernel<4>, total, 256, 0, s, vs); break;
         default: launch_pdl(pgs_kernel<0>, total, 256, 0, s, vs); break;
     }
+}
+
+cudaError_t verify_setup();
+
+cudaError_t verify_pgs_setup()
+{
+    const cudaError_t e = verify_setup();
+    return e == cudaSuccess ? pgs_setup() : e;
 }
 
 }  // namespace tr

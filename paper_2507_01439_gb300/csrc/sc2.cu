@@ -77,7 +77,7 @@ __device__ __forceinline__ void sc2_epilogue_tile(const ProbView& v, uint32_t ta
 {
     const int row = bm * kSc2BM + quarter * 32 + lane;
     uint16_t* wrow = v.w + (size_t)row * v.n_pad;
-    int rsum = 0;
+    int rsum = 0, rmax = 0;
 #pragma unroll 1
     for (int c = 0; c < kEpiCols / 32; ++c) {
         const int cc = part * kEpiCols + c * 32;
@@ -94,6 +94,7 @@ __device__ __forceinline__ void sc2_epilogue_tile(const ProbView& v, uint32_t ta
         for (int q = 0; q < 32; ++q) {
             val[q] = ((word >> q) & 1u) ? static_cast<int>(__uint_as_float(acc[q])) : 0;
             rsum += val[q];
+            rmax = max(rmax, val[q]);
         }
         if (word) {
 #pragma unroll
@@ -130,6 +131,7 @@ __device__ __forceinline__ void sc2_epilogue_tile(const ProbView& v, uint32_t ta
         }
     }
     if (rsum != 0) atomicAdd(&v.rowscore[row], rsum);
+    if (rmax != 0 && v.rowmax) atomicMax(&v.rowmax[row], rmax);
 }
 
 // The same epilogue through the warp's 2 KB of shared memory `stg`, which
@@ -151,7 +153,7 @@ __device__ __forceinline__ void sc2_epilogue_tile_staged(const ProbView& v, uint
 {
     const int row0 = bm * kSc2BM + quarter * 32;
     const int row = row0 + lane;
-    int rsum = 0;
+    int rsum = 0, rmax = 0;
 #pragma unroll 1
     for (int c = 0; c < kEpiCols / 32; ++c) {
         const int cc = part * kEpiCols + c * 32;
@@ -172,6 +174,7 @@ __device__ __forceinline__ void sc2_epilogue_tile_staged(const ProbView& v, uint
                 const int lo = ((word >> a) & 1u) ? static_cast<int>(__uint_as_float(acc[a])) : 0;
                 const int hi = ((word >> (a + 1)) & 1u) ? static_cast<int>(__uint_as_float(acc[a + 1])) : 0;
                 rsum += lo + hi;
+                rmax = max(rmax, max(lo, hi));
                 h[e] = static_cast<uint32_t>(lo) | (static_cast<uint32_t>(hi) << 16);
             }
             stg[stg_slot(lane, q)] = make_uint4(h[0], h[1], h[2], h[3]);
@@ -220,6 +223,7 @@ __device__ __forceinline__ void sc2_epilogue_tile_staged(const ProbView& v, uint
         __syncwarp();   // the next chunk overwrites the staging area
     }
     if (rsum != 0) atomicAdd(&v.rowscore[row], rsum);
+    if (rmax != 0 && v.rowmax) atomicMax(&v.rowmax[row], rmax);
 }
 
 // Persistent, warp-specialised: CTA b handles global tiles b, b + grid, ...
@@ -285,6 +289,7 @@ __global__ void __launch_bounds__(kThreads, 1) sc2_tcgen05_kernel(Batch bt, int 
     // the set-up above (barriers, tensor memory, shared histogram) overlaps the
     // previous stage; its outputs are read only from here on
     pdl_wait();
+    pdl_release();
 
     if (warp == 0) {
         if (lane == 0) {
@@ -473,6 +478,7 @@ __global__ void __launch_bounds__(kThreads, 1) sc2_pair_mma_kernel(Batch bt, int
     const uint32_t full_l = mapa_shared(&full[0], 0);      // leader's barriers, cluster addresses
     const uint32_t tempty_l = mapa_shared(&tempty[0], 0);
     pdl_wait();
+    pdl_release();
 
     if (warp == 0) {
         if (lane == 0) {
@@ -587,6 +593,7 @@ __global__ void __launch_bounds__(kThreads, 1) sc2_pair_mma_kernel(Batch bt, int
 __global__ void __launch_bounds__(256) sc2_bitset_kernel(ManyViews vs)
 {
     pdl_wait();
+    pdl_release();
     extern __shared__ uint32_t srow[];
     int i;
     const ProbView v = vs.get(ST_BITSET, blockIdx.x, i);
@@ -594,7 +601,7 @@ __global__ void __launch_bounds__(256) sc2_bitset_kernel(ManyViews vs)
     for (int q = threadIdx.x; q < v.ldb; q += blockDim.x) srow[q] = bi[q];
     __syncthreads();
     uint16_t* wrow = v.w + (size_t)i * v.n_pad;
-    int rsum = 0;
+    int rsum = 0, rmax = 0;
     for (int j = threadIdx.x; j < v.n_pad; j += blockDim.x) {
         int c = 0;
         if (j > i && ((srow[j >> 5] >> (j & 31)) & 1u)) {
@@ -608,7 +615,9 @@ __global__ void __launch_bounds__(256) sc2_bitset_kernel(ManyViews vs)
         }
         wrow[j] = static_cast<uint16_t>(c);
         rsum += c;
+        rmax = max(rmax, c);
     }
+    if (rmax != 0 && v.rowmax) atomicMax(&v.rowmax[i], rmax);
     // block reduce of the row sum
     __shared__ int red[32];
     for (int off = 16; off >= 1; off >>= 1) rsum += __shfl_xor_sync(0xffffffffu, rsum, off);
@@ -648,6 +657,8 @@ cudaError_t launch_pair(const Batch& b, int total_tiles, size_t smem, bool pair_
 }
 
 }  // namespace
+
+int device_sms() { return g_sc2_sms > 0 ? g_sc2_sms : 148; }
 
 cudaError_t sc2_tcgen05_setup()
 {

@@ -13,6 +13,8 @@
 //           m = K1' - c_gt ties still needed (K1' = min(K1, |E+|))
 //   count   warp per row pair (i, n-1-i): #{j : W_ij > alpha} and
 //           #{j : W_ij == alpha}; rows with such edges join the active list
+//           (rows whose largest weight, recorded by the SC^2 pass, is below
+//           alpha are skipped without reading W)
 //   emit    blocks over the active rows: W > alpha edges take slots from one
 //           atomic per row (the rank pass orders them); ties get global tie
 //           ranks (tie prefix over the active rows above) + rank-in-row
@@ -66,6 +68,7 @@ template <class VS, bool kSmem>
 __global__ void __launch_bounds__(256) hist_kernel(VS vs)
 {
     pdl_wait();
+    pdl_release();
     extern __shared__ uint32_t sh[];
     int lb;
     const ProbView v = vs.get(ST_HIST, blockIdx.x, lb);
@@ -96,6 +99,7 @@ template <class VS>
 __global__ void __launch_bounds__(1024) select_kernel(VS vs)
 {
     pdl_wait();
+    pdl_release();
     __shared__ int sbuf[33];
     int lb;
     const ProbView v = vs.get(ST_SELECT, blockIdx.x, lb);
@@ -134,6 +138,7 @@ template <class VS>
 __global__ void __launch_bounds__(128) count_kernel(VS vs)
 {
     pdl_wait();
+    pdl_release();
     int lb;
     const ProbView v = vs.get(ST_COUNT, blockIdx.x, lb);
     const int lane = threadIdx.x & 31;
@@ -146,9 +151,14 @@ __global__ void __launch_bounds__(128) count_kernel(VS vs)
     const int ra = wp, rb = n - 1 - wp;           // rb == ra: middle row of an odd n
     const int c1 = (n - 1) >> 3;
     const int a0 = (ra + 1) >> 3, b0 = (rb + 1) >> 3;
-    const int la = ra + 1 < n ? c1 - a0 + 1 : 0;
-    const int lbn = (rb != ra && rb + 1 < n) ? c1 - b0 + 1 : 0;
+    // a row whose largest weight is below alpha holds no such edge (the learned
+    // pivot weight floor(W p_i p_j) never exceeds W): skip it without reading W
+    const bool ka = v.rowmax == nullptr || __ldg(v.rowmax + ra) >= alpha;
+    const bool kb = v.rowmax == nullptr || __ldg(v.rowmax + rb) >= alpha;
+    const int la = (ka && ra + 1 < n) ? c1 - a0 + 1 : 0;
+    const int lbn = (kb && rb != ra && rb + 1 < n) ? c1 - b0 + 1 : 0;
     const int tot = la + lbn;
+    if (tot == 0) return;
     int ga = 0, ea = 0, gb = 0, eb = 0;
     for (int base = lane; base < tot; base += 8 * 32) {
         uint4 q[8];
@@ -205,6 +215,7 @@ template <class VS>
 __global__ void __launch_bounds__(256) emit_kernel(VS vs)
 {
     pdl_wait();
+    pdl_release();
     __shared__ int sg[8], se[8];
     __shared__ int s_base;
     int lb;
@@ -304,6 +315,7 @@ template <class VS>
 __global__ void __launch_bounds__(256) rank_kernel(VS vs)
 {
     pdl_wait();
+    pdl_release();
     extern __shared__ uint64_t sk[];
     __shared__ int part[8][32];
     int lb;

@@ -102,10 +102,13 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
 // is processed while its predecessor drains; each kernel calls pdl_wait()
 // before it touches memory, which returns once the predecessor grid has
 // completed and its writes are visible (immediately when there is no
-// programmatic predecessor).  No kernel triggers its successor early: blocks
-// of the next stage waiting on the device slowed the step down (measured).
+// programmatic predecessor), and then pdl_release(): the successor's launch
+// may begin once every block of this grid has passed that point, so its
+// blocks are resident (waiting in their own pdl_wait) when this grid ends,
+// while no block of this grid is kept from being scheduled by them.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 #ifdef __CUDACC__
 template <typename... KArgs, typename... Args>

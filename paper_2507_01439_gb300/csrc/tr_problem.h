@@ -25,6 +25,7 @@ struct ProbView {
     float kappa_fp64;    // FP64 Kabsch above this sigma1/sigma2
     int32_t graph_mode;  // TURBOREG_GRAPH_O2 / _SC2: the graph the clique search runs on
     int32_t scoring;     // TURBOREG_SCORE_IN / _MAE / _MSE
+    int32_t vppb;        // verification tile: matches per block (<= 4 x the kernel's points per warp)
     float* pts;          // [6][n_pad]
     float* pts8;         // [n_pad][8] = (x0, x1, x2, y0, y1, y2, 0, 0)
     uint8_t* a8;         // [n_pad][n_pad] FP8 E4M3 0/1 adjacency
@@ -32,6 +33,8 @@ struct ProbView {
     uint16_t* w;         // [n_pad][n_pad] O2Graph weights (i < j only)
     int32_t* rowscore;   // [n_pad] SC^2 row sums
     int32_t* deg;        // [n_pad] degrees
+    int32_t* rowmax;     // [n_pad] largest O2Graph weight of each row (j > i), or null: rows
+                         // below the pivot threshold are skipped by the selection passes
     uint32_t* hist;      // [n_pad + 1] histogram of O2Graph edge weights
     int4* active;        // [n_pad] (row, #weight > alpha, #weight == alpha, 0) of the rows
                          // holding such edges, in any order
@@ -111,8 +114,12 @@ struct ManyViews {
 #endif
 
 // per-problem block counts of each stage (host side, from n, k1, k2)
-// verify_pw: points per warp of the verification tile (32, 64 or 128)
-void stage_blocks(int32_t n, int32_t k1, int32_t k2, int32_t verify_pw, int32_t blocks[kNumBatchStages]);
+// vppb: matches per verification block (ProbView::vppb)
+void stage_blocks(int32_t n, int32_t k1, int32_t k2, int32_t vppb, int32_t blocks[kNumBatchStages]);
+// Matches per verification block for a single problem: the block count
+// (hypothesis blocks x match blocks) close to 4 blocks per SM, so that one
+// wave covers the problem with every SM holding the same number of blocks.
+int32_t balanced_vppb(int32_t n, int32_t nh, int32_t num_sms);
 
 // stage launchers (all asynchronous on `s`); total = sum of the stage's blocks
 void launch_pack(const Batch& b, int total, const float* src, const float* dst, cudaStream_t s);
@@ -130,11 +137,17 @@ void launch_kabsch(const Batch& b, int total, cudaStream_t s);
 void launch_finalize(const Batch& b, cudaStream_t s);
 // Kabsch of caller-given k-cliques (k >= 4) into v.rt; idx [m][k] on the device.
 void launch_kabsch_n(const ProbView& v, const int32_t* idx, int k, int m, cudaStream_t s);
+// pw: the kernel's points per warp (32, 64, 128); every problem's vppb <= 4 pw
 void launch_verify(const Batch& b, int total, int pw, cudaStream_t s);
 
 // set kernel attributes (dynamic shared memory limits) once per device
 cudaError_t sc2_tcgen05_setup();
+// SM count of the device (after sc2_tcgen05_setup)
+int device_sms();
 cudaError_t topk_setup();
+// Shared-memory carveout of the verification and clique-search kernels: the
+// largest shared part, so that every block of a launch is resident at once
+cudaError_t verify_pgs_setup();
 
 // single-problem pivot selection used by the allocation-free entry point
 void launch_topk_single(const ProbView& v, cudaStream_t s);
