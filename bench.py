@@ -51,13 +51,13 @@ WORKLOAD = {"workload": "indoor-shaped single problem", "n": 5000, "inlier_ratio
             "tau_m": 0.1, "k1": 2000, "k2": 2, "inlier_thresh_m": 0.1, "problems_cycled": 8,
             "l2": "flushed between timed steps (256 MB write, outside the events)"}
 # kernels of ours launched per registration: pack, compat, sc2 (with the histogram and
-# the threshold choice), count, emit, rank, pgs (with the cliques' Kabsch), verify,
-# finalize
-LAUNCHES_PER_STEP = 9
+# the threshold choice), count, emit, pgs (with the pivot ranks and the cliques'
+# Kabsch), verify, finalize
+LAUNCHES_PER_STEP = 8
 # DRAM bytes (read + write) of one SC^2 kernel launch on this workload, from one ncu
-# capture of the current kernel (profiles/sc2_pair_mma_indoor5000.txt); None until
-# the current kernel has been captured
-SC2_DRAM_BYTES = None
+# capture of the current kernel (profiles/sc2_pair_mma_indoor5000.txt); set to None when
+# the kernel changes, until it has been captured again
+SC2_DRAM_BYTES = 28868864
 
 
 def _peaks():
@@ -312,7 +312,7 @@ def run_batched(trg, torch, stream, steps, warmup, flush, ws=1, rank=0):
             "mean_n": float(sum(p.n for p in allp) / len(allp)),
             "success": default["success"] + " (indoor RE<15deg TE<0.3m, outdoor RE<5deg TE<0.6m)",
             "default_k1": "2000 indoor-shaped, 1000 outdoor-shaped", "autotuned": tuned,
-            "gpu_launches_per_call": 10}
+            "gpu_launches_per_call": 9}
 
 
 def run_learned(trg, torch, stream, flush, ks=(1, 2, 4, 8, 100, 250, 500, 1000)):

@@ -429,9 +429,9 @@ int enqueue_plan(turboreg_ctx* c, const Plan& pl, const Batch& bt, const float* 
         launch_select(bt, s);
     }
     TR_EV(3);
-    launch_topk_rest(bt, pl.tot, pl.max_k1, s);
+    launch_count_emit(bt, pl.tot, s);
     TR_EV(4);
-    launch_pgs(bt, pl.tot[ST_PGS], pl.k2_common, s);   // also solves the cliques' Kabsch
+    launch_pgs(bt, pl.tot[ST_PGS], pl.k2_common, pl.max_k1, s);   // also ranks the pivots and solves the cliques' Kabsch
     TR_EV(5);
     TR_EV(6);
     launch_verify(bt, pl.tot[ST_VERIFY], pl.vpw, s);

@@ -13,7 +13,11 @@
 // (z != i, j follows from the zero diagonal) and W read symmetrically,
 // W_ab = W_min(a,b),max(a,b) (only the upper triangle is stored).
 //
-// One warp per pivot.  Candidates: every lane loads its share of both rows'
+// One warp per selected edge (Eq. 4, in the order the selection wrote
+// them): the warp first finds the edge's pivot index, its rank among the
+// selected keys (staged once per block in shared memory), and writes the
+// pivot list entry; all outputs go to that index.  Candidates: every lane
+// loads its share of both rows'
 // bitset words at once (eight words of each per lane in flight), and the
 // warp compacts the set bits of their AND into a per-warp list in shared
 // memory (popcount prefix sums).  Scoring: lanes take list entries
@@ -35,28 +39,45 @@ namespace tr {
 namespace {
 
 constexpr int kCand = 1024;   // per-warp candidate list (z indices)
+constexpr int kListBytes = 8 * kCand * 4;   // the 8 warps' lists
 constexpr int kWords = 8;     // bitset words per lane per load round
 constexpr int kBatch = 8;     // list entries per lane per scoring round (16 weight loads in flight)
 
 template <int K2C>
 __global__ void __launch_bounds__(256, 2) pgs_kernel(ManyViews vs)
 {
-    __shared__ int scand[8][kCand];
+    // dynamic shared memory: per-warp candidate lists, then the selected edge keys
+    extern __shared__ __align__(16) uint8_t pgs_smem[];
+    int (*scand)[kCand] = reinterpret_cast<int (*)[kCand]>(pgs_smem);
+    uint64_t* skey = reinterpret_cast<uint64_t*>(pgs_smem + kListBytes);
     pdl_wait();
     // no early release: the verification blocks, placed while these still hold
     // registers, would spread unevenly over the SMs (measured slower)
     int lb;
     const ProbView v = vs.get(ST_PGS, blockIdx.x, lb);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // pivots are in weight order and heavier pivots have more common neighbours:
-    // warp w of block b takes pivot w * blocks + b, spreading them over the SMs
-    const int p = warp * ((v.k1 + 7) / 8) + lb;
-    const int np = v.ctl->n_pivots;
-    if (p >= np) return;
+    // the selected edges (Eq. 4) in the order the selection wrote them; a
+    // pivot's index is its rank: the number of larger keys (W << 32 | ~(i n + j)
+    // are unique, larger = heavier, then lower (i, j))
+    const int np = v.ctl->n_sel;
+    if (lb == 0 && threadIdx.x == 0) v.ctl->n_pivots = np;
+    for (int q = threadIdx.x; q < np; q += blockDim.x) skey[q] = __ldcg(v.cand + q);
+    __syncthreads();
+    // warp w of block b takes selected edge w * blocks + b
+    const int c = warp * ((v.k1 + 7) / 8) + lb;
+    if (c >= np) return;
+    const uint64_t mykey = skey[c];
+    int p = 0;
+    for (int q = lane; q < np; q += 32) p += skey[q] > mykey ? 1 : 0;
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) p += __shfl_xor_sync(0xffffffffu, p, off);
+    const uint32_t lin = 0xFFFFFFFFu - static_cast<uint32_t>(mykey & 0xFFFFFFFFull);
+    const int i = static_cast<int>(lin / static_cast<uint32_t>(v.n));
+    const int j = static_cast<int>(lin % static_cast<uint32_t>(v.n));
+    const int wij = static_cast<int>(mykey >> 32);
+    if (lane == 0) v.piv[p] = make_int4(i, j, wij, 0);
     int* cand = scand[warp];
     const int k2 = K2C > 0 ? K2C : v.k2;
-    const int4 pv = v.piv[p];
-    const int i = pv.x, j = pv.y, wij = pv.z;
     const uint32_t* bi = v.bits + (size_t)i * v.ldb;
     const uint32_t* bj = v.bits + (size_t)j * v.ldb;
     const uint16_t* wi = v.w + (size_t)i * v.n_pad;
@@ -244,22 +265,28 @@ cudaError_t pgs_setup()
     const void* fns[] = {reinterpret_cast<const void*>(pgs_kernel<0>), reinterpret_cast<const void*>(pgs_kernel<1>),
                          reinterpret_cast<const void*>(pgs_kernel<2>), reinterpret_cast<const void*>(pgs_kernel<3>),
                          reinterpret_cast<const void*>(pgs_kernel<4>)};
-    for (const void* f : fns)
+    for (const void* f : fns) {
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     kListBytes + TURBOREG_K1_MAX * static_cast<int>(sizeof(uint64_t)));
+    }
     return e;
 }
 
-// k2 is the common K2 of the batch, or 0 when problems differ (generic list)
-void launch_pgs(const Batch& b, int total, int k2, cudaStream_t s)
+// k2 is the common K2 of the batch, or 0 when problems differ (generic list);
+// max_k1 sizes the shared copy of the selected keys
+void launch_pgs(const Batch& b, int total, int k2, int max_k1, cudaStream_t s)
 {
     const ManyViews vs{b};
+    const size_t smem = kListBytes + static_cast<size_t>(max_k1) * sizeof(uint64_t);
     switch (k2) {
-        case 1: launch_pdl(pgs_kernel<1>, total, 256, 0, s, vs); break;
-        case 2: launch_pdl(pgs_kernel<2>, total, 256, 0, s, vs); break;
-        case 3: launch_pdl(pgs_kernel<3>, total, 256, 0, s, vs); break;
-        case 4: launch_pdl(pgs_kernel<4>, total, 256, 0, s, vs); break;
-        default: launch_pdl(pgs_kernel<0>, total, 256, 0, s, vs); break;
+        case 1: launch_pdl(pgs_kernel<1>, total, 256, smem, s, vs); break;
+        case 2: launch_pdl(pgs_kernel<2>, total, 256, smem, s, vs); break;
+        case 3: launch_pdl(pgs_kernel<3>, total, 256, smem, s, vs); break;
+        case 4: launch_pdl(pgs_kernel<4>, total, 256, smem, s, vs); break;
+        default: launch_pdl(pgs_kernel<0>, total, 256, smem, s, vs); break;
     }
 }
 

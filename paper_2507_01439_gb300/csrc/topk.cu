@@ -20,7 +20,10 @@
 //           ranks (tie prefix over the active rows above) + rank-in-row
 //           (column order) and ranks < m are kept
 //   rank    candidate keys (W << 32 | ~(i*n+j)) are unique; each pivot's
-//           position is the number of larger keys.
+//           position is the number of larger keys.  In the registration
+//           pipeline the clique search computes these ranks itself (one warp
+//           per selected edge); rank_kernel serves the allocation-free
+//           selection entry point.
 #include "tr_common.cuh"
 #include "tr_problem.h"
 #include "tr_select.cuh"
@@ -388,12 +391,11 @@ void launch_hist(const Batch& b, int total, int max_n, cudaStream_t s)
 
 void launch_select(const Batch& b, cudaStream_t s) { launch_pdl(select_kernel<ManyViews>, b.num, 1024, 0, s, ManyViews{b}); }
 
-void launch_topk_rest(const Batch& b, const int32_t tot[kNumBatchStages], int max_k1, cudaStream_t s)
+void launch_count_emit(const Batch& b, const int32_t tot[kNumBatchStages], cudaStream_t s)
 {
     const ManyViews vs{b};
     launch_pdl(count_kernel<ManyViews>, tot[ST_COUNT], 128, 0, s, vs);
     launch_pdl(emit_kernel<ManyViews>, tot[ST_EMIT], 256, 0, s, vs);
-    launch_pdl(rank_kernel<ManyViews>, tot[ST_RANK], 256, max_k1 * 8, s, vs);
 }
 
 // One problem passed by value (no device-side problem table).

@@ -131,8 +131,10 @@ void launch_sc2_tcgen05(const Batch& b, int total_tiles, int max_n, int mode, cu
 void launch_sc2_bitset(const Batch& b, int total, cudaStream_t s);
 void launch_hist(const Batch& b, int total, int max_n, cudaStream_t s);
 void launch_select(const Batch& b, cudaStream_t s);
-void launch_topk_rest(const Batch& b, const int32_t tot[kNumBatchStages], int max_k1, cudaStream_t s);
-void launch_pgs(const Batch& b, int total, int k2_max, cudaStream_t s);
+// count and emit passes of the selection (the clique search ranks the pivots)
+void launch_count_emit(const Batch& b, const int32_t tot[kNumBatchStages], cudaStream_t s);
+// The clique search also orders the pivots (each warp ranks its selected edge)
+void launch_pgs(const Batch& b, int total, int k2_max, int max_k1, cudaStream_t s);
 void launch_kabsch(const Batch& b, int total, cudaStream_t s);
 void launch_finalize(const Batch& b, cudaStream_t s);
 // Kabsch of caller-given k-cliques (k >= 4) into v.rt; idx [m][k] on the device.
