@@ -52,7 +52,7 @@ constexpr float kScoreUnits = 4194304.f;   // 2^22 units per theta (MAE) or thet
 template <int PW>
 struct VerifyShared {
     ulonglong2 sp[kVWarps * PW][3];   // points as packed pairs (v, v): x0 x1 | x2 y0 | y1 y2
-    float4 srt[kVHyp][4];
+    float srt[kVHyp][17];   // R, t of each hypothesis; 17 floats apart: lanes hit distinct banks
     int scnt[kVWarps][kVHyp];
     uint32_t ssc[kVWarps][kVHyp];
     int sok[kVHyp];
@@ -94,8 +94,10 @@ __device__ __forceinline__ void verify_body(const ProbView& v, int lb, VerifySha
         } else {
             r2.y = r2.z = r2.w = __int_as_float(0x7fc00000);
         }
-        sh.srt[threadIdx.x][0] = r0; sh.srt[threadIdx.x][1] = r1;
-        sh.srt[threadIdx.x][2] = r2; sh.srt[threadIdx.x][3] = r3;
+        float* d = sh.srt[threadIdx.x];
+        d[0] = r0.x; d[1] = r0.y; d[2] = r0.z; d[3] = r0.w;
+        d[4] = r1.x; d[5] = r1.y; d[6] = r1.z; d[7] = r1.w;
+        d[8] = r2.x; d[9] = r2.y; d[10] = r2.z; d[11] = r2.w;
         sh.sok[threadIdx.x] = ok ? 1 : 0;
     }
     __syncthreads();
@@ -103,8 +105,8 @@ __device__ __forceinline__ void verify_body(const ProbView& v, int lb, VerifySha
     f2 R[2][9], T[2][3];
 #pragma unroll
     for (int pr = 0; pr < 2; ++pr) {
-        const float* A = reinterpret_cast<const float*>(&sh.srt[lane + 64 * pr][0]);
-        const float* B = reinterpret_cast<const float*>(&sh.srt[lane + 64 * pr + 32][0]);
+        const float* A = sh.srt[lane + 64 * pr];
+        const float* B = sh.srt[lane + 64 * pr + 32];
 #pragma unroll
         for (int c = 0; c < 9; ++c) R[pr][c] = pk(A[c], B[c]);
 #pragma unroll
