@@ -407,7 +407,7 @@ __global__ void __launch_bounds__(kThreads, 1) sc2_tcgen05_kernel(Batch bt, int 
     __syncthreads();
     if (!sel_buf[40]) return;
     __threadfence();
-    select_alpha(v0, sel_buf);
+    select_alpha(v0, sel_buf, shist);   // this CTA's histogram area, flushed above
 }
 
 // 2-SM form (cta_group::2): the two CTAs of a cluster compute one 256 x 256
@@ -571,22 +571,32 @@ __global__ void __launch_bounds__(kThreads, 1) sc2_pair_mma_kernel(Batch bt, int
     if (!ok && lane == 0) atomicOr(&bt.views[0].ctl->err, TR_ERR_TIMEOUT);
     tc_fence_before();
     __syncthreads();
-    cluster_sync_all();   // neither CTA exits or frees tensor memory while the other may still use it
+    if (kSingle && !leader) {
+        // the peer's histogram into the leader's (distributed shared memory), so
+        // that one CTA per cluster adds to the global bins
+        const uint32_t lead_hist = mapa_shared(shist, 0);
+        for (int b = threadIdx.x + 1; b < nbins; b += blockDim.x) {
+            const uint32_t h = shist[b];
+            if (h) red_add_cluster(lead_hist + 4u * static_cast<uint32_t>(b), h);
+        }
+    }
+    cluster_sync_all();   // neither CTA exits or frees tensor memory while the other may still use it;
+                          // orders the peer's additions before the leader's flush
     if (warp == 0) {
         tc_fence_after();
         tmem_dealloc_pair(tmem, kTmemCols);
     }
-    if (!kSingle) return;
+    if (!kSingle || !leader) return;
     const ProbView v0 = bt.views[0];
     for (int b = threadIdx.x + 1; b < nbins; b += blockDim.x)
         if (shist[b]) atomicAdd(&v0.hist[b], shist[b]);
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) sel_buf[40] = atomicAdd(&v0.ctl->done_blocks, 1u) == gridDim.x - 1;
+    if (threadIdx.x == 0) sel_buf[40] = atomicAdd(&v0.ctl->done_blocks, 1u) == (gridDim.x >> 1) - 1;
     __syncthreads();
     if (!sel_buf[40]) return;
     __threadfence();
-    select_alpha(v0, sel_buf);
+    select_alpha(v0, sel_buf, shist);   // this CTA's histogram area, flushed above
 }
 
 // CUDA-core alternative: block per row i; W_ij = popc(row_i & row_j) for j > i with G_ij.

@@ -259,6 +259,12 @@ __device__ __forceinline__ uint32_t mapa_shared(const void* p, uint32_t rank)
     return r;
 }
 
+// Atomic add to a 32-bit word given by its cluster-window address (possibly in the peer CTA).
+__device__ __forceinline__ void red_add_cluster(uint32_t addr_cluster, uint32_t v)
+{
+    asm volatile("red.shared::cluster.add.u32 [%0], %1;" ::"r"(addr_cluster), "r"(v) : "memory");
+}
+
 // Arrive on an mbarrier given by its cluster-window address (possibly in the peer CTA).
 __device__ __forceinline__ void mbar_arrive_cluster(uint32_t bar_cluster)
 {

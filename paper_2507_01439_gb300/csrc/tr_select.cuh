@@ -37,10 +37,30 @@ __device__ __forceinline__ int block_incl_scan(int x, int* sbuf)
 
 // From the weight histogram: |E+|, n_sel = min(K1, |E+|), alpha = the K1-th
 // largest weight, c_gt = #{W > alpha}, m = n_sel - c_gt ties still needed.
-// Every thread of the block must call it.
-__device__ __forceinline__ void select_alpha(const ProbView& v, int* sbuf)
+// Every thread of the block must call it.  stage: optional shared memory of
+// n + 1 words; the histogram is then copied there in one coalesced round and
+// both passes below read it from there.
+__device__ __forceinline__ void select_alpha(const ProbView& v, int* sbuf, uint32_t* stage = nullptr)
 {
     const int nb = v.n;                       // weights 1..n (W <= n - 2)
+    const uint32_t* H = v.hist;
+    if (stage != nullptr) {
+        for (int q0 = threadIdx.x + 1; q0 <= nb; q0 += 8 * blockDim.x) {
+            uint32_t h8[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int b = q0 + q * static_cast<int>(blockDim.x);
+                h8[q] = b <= nb ? __ldcg(v.hist + b) : 0u;
+            }
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int b = q0 + q * static_cast<int>(blockDim.x);
+                if (b <= nb) stage[b] = h8[q];
+            }
+        }
+        __syncthreads();
+        H = stage;
+    }
     const int per = (nb + blockDim.x - 1) / blockDim.x;
     // thread t owns weights (hi - per, hi], hi = n - t*per, scanned from the top
     const int hi = nb - static_cast<int>(threadIdx.x) * per;
@@ -50,7 +70,7 @@ __device__ __forceinline__ void select_alpha(const ProbView& v, int* sbuf)
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
             const int wv = hi - q0 - q;
-            h8[q] = (q0 + q < per && wv >= 1) ? v.hist[wv] : 0u;
+            h8[q] = (q0 + q < per && wv >= 1) ? H[wv] : 0u;
         }
 #pragma unroll
         for (int q = 0; q < 8; ++q) mine += static_cast<int>(h8[q]);
@@ -81,7 +101,7 @@ __device__ __forceinline__ void select_alpha(const ProbView& v, int* sbuf)
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
                 const int wv = hi - q0 - q;
-                h8[q] = (q0 + q < per && wv >= 1) ? v.hist[wv] : 0u;
+                h8[q] = (q0 + q < per && wv >= 1) ? H[wv] : 0u;
             }
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
