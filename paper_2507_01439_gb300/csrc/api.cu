@@ -415,10 +415,11 @@ int enqueue_plan(turboreg_ctx* c, const Plan& pl, const Batch& bt, const float* 
         launch_hist(bt, pl.tot[ST_HIST], pl.max_n, s);
         launch_select(bt, s);
     } else {
-        // one problem: the GEMM builds the histogram in shared memory and its
-        // last CTA chooses the threshold; a batch adds a select launch
-        launch_sc2_tcgen05(bt, pl.tot[ST_GEMM], pl.max_n, pl.gemm_form, s);
-        if (pl.num > 1 && !pl.learned) launch_select(bt, s);
+        // one problem whose histogram fits in shared memory: the GEMM's last
+        // CTA chooses the threshold; a batch or a larger problem (global
+        // histogram) adds a select launch
+        const bool fused = launch_sc2_tcgen05(bt, pl.tot[ST_GEMM], pl.max_n, pl.gemm_form, s);
+        if (!fused && !pl.learned) launch_select(bt, s);
     }
     if (pl.learned) {
         // learned proposal: features -> MLP -> histogram of floor(W p_i p_j) -> threshold

@@ -718,7 +718,7 @@ cudaError_t sc2_tcgen05_setup()
 
 // A single problem keeps its histogram in shared memory when it fits; a
 // batch (or a very large problem) uses global atomics.
-void launch_sc2_tcgen05(const Batch& b, int total_tiles, int max_n, int mode, cudaStream_t s)
+bool launch_sc2_tcgen05(const Batch& b, int total_tiles, int max_n, int mode, cudaStream_t s)
 {
     const bool pair = mode != 0;
     const bool pair_mma = mode == 2;
@@ -737,6 +737,7 @@ void launch_sc2_tcgen05(const Batch& b, int total_tiles, int max_n, int mode, cu
     } else {
         launch_pdl(sc2_tcgen05_kernel<false, false>, grid, kThreads, base, s, b, total_tiles);
     }
+    return single;
 }
 
 void launch_sc2_bitset(const Batch& b, int total, cudaStream_t s)

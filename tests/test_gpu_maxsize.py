@@ -1,0 +1,98 @@
+"""Registration at the largest problem size, N = TURBOREG_MAX_N = 32768 (and
+at N = 9000, just above the size whose edge-weight histogram still fits in
+the GEMM's shared memory).  The whole oracle cannot run at this size, so:
+
+  * the compatibility graph (Eq. 1) is compared bit for bit with the
+    oracle's (its C implementation handles the 537 M pairs);
+  * SC^2 entries (Eq. 2) are compared on samples, each computed from the
+    oracle's graph as G_ij * |N(i) ∩ N(j)|;
+  * the pivot list (Eq. 4) equals the oracle's selection run on the
+    library's SC^2 matrix (whose entries the samples check);
+  * every clique is a 3-clique of the oracle's graph above j (Def. 2), and
+    the clique rule (Eq. 5-7) is recomputed from the oracle's graph for
+    sampled pivots;
+  * the winner's inlier count equals the oracle's FP64 count (Eq. 9) up to
+    matches within 1e-5 m of the threshold.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2507_01439_gb300 as trg
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _w_oracle(G, i, j):
+    """SC^2 entry of the O2Graph from the oracle's graph: G_ij * common neighbours."""
+    return int(G[i, j]) * int(np.count_nonzero(G[i] & G[j]))
+
+
+def _check_large(n, seed, k1=2000, samples=400):
+    p = synth.make_problem("indoor", n, 0.05, seed)
+    prm = trg.default_params(p.tau, k1, p.theta)
+    with trg.TurboReg(max_n=n) as ctx:
+        res = ctx.register(p.x, p.y, prm)
+        assert res.status == 0
+        assert synth.rotation_error_deg(p.R_gt, res.R) < 15 and synth.translation_error(p.t_gt, res.t) < 0.3
+        nn, npad, npiv, nh = ctx.shape()
+        assert nn == n
+        bits = ctx.buffer(trg.BUF_ADJ_BITS)
+        W = ctx.buffer(trg.BUF_SC2)
+        P = ctx.buffer(trg.BUF_PIVOTS)[:npiv].copy()
+        CL = ctx.buffer(trg.BUF_CLIQUES)[: npiv * 2].copy()
+
+    G = oracle.compat(p.x, p.y, p.tau)                       # uint8 [n, n], zero diagonal
+    # Eq. 1: the whole bitset (bit j of word j / 32 of row i)
+    A = np.unpackbits(bits.view(np.uint8), axis=1, bitorder="little")[:n, :n]
+    assert np.array_equal(A, G), "compatibility graph differs from the oracle"
+    del A, bits
+
+    # Eq. 2 on samples (upper triangle), plus every pivot edge
+    rng = np.random.default_rng(seed + 1)
+    ii = rng.integers(0, n - 1, samples)
+    jj = np.array([rng.integers(i + 1, n) for i in ii])
+    for i, j in list(zip(ii, jj)) + [(int(a), int(b)) for a, b in P[:50, :2]]:
+        assert int(W[i, j]) == _w_oracle(G, i, j), (i, j)
+
+    # Eq. 4: the oracle's selection on the library's SC^2 matrix (i < j entries)
+    S = np.triu(W[:n, :n], 1).astype(np.int32)
+    pi, pj, pw = oracle.pivots(S, k1)
+    del S
+    assert npiv == len(pi)
+    assert np.array_equal(P[:, 0], pi) and np.array_equal(P[:, 1], pj) and np.array_equal(P[:, 2], pw)
+
+    # cliques: 3-cliques of the oracle's graph with z above j; the rule for sampled pivots
+    valid = CL[:, 3] != 0
+    c = CL[valid]
+    assert np.all(c[:, 2] > c[:, 1])
+    assert np.all(G[c[:, 0], c[:, 1]] & G[c[:, 0], c[:, 2]] & G[c[:, 1], c[:, 2]])
+    for q in rng.choice(npiv, size=min(12, npiv), replace=False):
+        i, j, wij = int(P[q, 0]), int(P[q, 1]), int(P[q, 2])
+        z = np.flatnonzero(G[i] & G[j])
+        z = z[z > j]
+        if z.size == 0:
+            assert CL[q, 3] == 0 and CL[npiv + q, 3] == 0
+            continue
+        wiz = np.array([_w_oracle(G, i, k) for k in z])
+        wjz = np.array([_w_oracle(G, j, k) for k in z])
+        S_z = wij + wiz + wjz
+        order = np.lexsort((z, -S_z))                 # S desc, then z asc
+        want = z[order[:2]]
+        got = [int(CL[r * npiv + q, 2]) for r in range(2) if CL[r * npiv + q, 3]]
+        assert got == list(want[: len(got)]) and len(got) == min(2, z.size), (q, got, want)
+
+    # Eq. 9: the winner's inlier count in FP64
+    cnt, near = oracle.inliers(p.x, p.y, res.R, res.t, p.theta, band=1e-5)
+    assert abs(res.inlier_count - cnt) <= near
+
+
+def test_max_size_registration():
+    _check_large(trg.TURBOREG_MAX_N, 700)
+
+
+def test_histogram_beyond_shared_memory():
+    # one problem whose edge-weight histogram no longer fits in the GEMM's
+    # shared memory: the threshold is chosen by the separate select launch
+    _check_large(9000, 701, k1=1500, samples=300)
