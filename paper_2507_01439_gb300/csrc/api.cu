@@ -122,6 +122,10 @@ struct turboreg_ctx {
         const float* src = nullptr;
         const float* dst = nullptr;
         void* args[3] = {};
+        cudaGraphNode_t fin_node = nullptr;   // finalize: its result pointer is patched per call
+        cudaKernelNodeParams fin_params = {};
+        turboreg_result* out = nullptr;
+        void* fin_args[2] = {};
         void* desc = nullptr;
         uint64_t stamp = 0;
     };
@@ -398,7 +402,8 @@ int upload_desc(turboreg_ctx* c, int32_t num, void* dev, Batch& bt, cudaStream_t
 }
 
 // Enqueue the whole path for the plan's problems (inputs on the device).
-int enqueue_plan(turboreg_ctx* c, const Plan& pl, const Batch& bt, const float* dsrc, const float* ddst)
+int enqueue_plan(turboreg_ctx* c, const Plan& pl, const Batch& bt, const float* dsrc, const float* ddst,
+                 turboreg_result* out)
 {
     cudaStream_t s = c->stream;
     const bool timed = pl.timed != 0;
@@ -437,7 +442,7 @@ int enqueue_plan(turboreg_ctx* c, const Plan& pl, const Batch& bt, const float* 
     TR_EV(6);
     launch_verify(bt, pl.tot[ST_VERIFY], pl.vpw, s);
     TR_EV(7);
-    launch_finalize(bt, s);
+    launch_finalize(bt, out, s);
     TR_EV(8);
 #undef TR_EV
     TR_CHECK(cudaGetLastError());
@@ -478,13 +483,14 @@ std::vector<uint8_t> plan_key(turboreg_ctx* c, const Plan& pl)
 
 // Run a plan: replay its captured graph (capturing it on first use) with the
 // given input pointers; TURBOREG_FLAG_NO_GRAPH launches the stages directly.
-int run_plan(turboreg_ctx* c, const Plan& pl, bool no_graph, const float* dsrc, const float* ddst)
+int run_plan(turboreg_ctx* c, const Plan& pl, bool no_graph, const float* dsrc, const float* ddst,
+             turboreg_result* out)
 {
     if (no_graph) {
         Batch bt;
         const int rc = upload_desc(c, pl.num, c->ws.desc, bt, c->stream);
         if (rc != TURBOREG_OK) return rc;
-        return enqueue_plan(c, pl, bt, dsrc, ddst);
+        return enqueue_plan(c, pl, bt, dsrc, ddst, out);
     }
     const std::vector<uint8_t> key = plan_key(c, pl);
     turboreg_ctx::GraphSlot* g = nullptr;
@@ -503,7 +509,7 @@ int run_plan(turboreg_ctx* c, const Plan& pl, bool no_graph, const float* dsrc, 
         int rc = upload_desc(c, pl.num, g->desc, g->batch, c->stream);
         if (rc != TURBOREG_OK) return rc;
         TR_CHECK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-        rc = enqueue_plan(c, pl, g->batch, dsrc, ddst);
+        rc = enqueue_plan(c, pl, g->batch, dsrc, ddst, out);
         cudaGraph_t graph = nullptr;
         const cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
         if (rc != TURBOREG_OK || e != cudaSuccess || !graph) {
@@ -527,9 +533,12 @@ int run_plan(turboreg_ctx* c, const Plan& pl, bool no_graph, const float* dsrc, 
             if (kp.func == pack_kernel_func()) {
                 g->pack_node = nodes[k];
                 g->pack_params = kp;
+            } else if (kp.func == finalize_kernel_func()) {
+                g->fin_node = nodes[k];
+                g->fin_params = kp;
             }
         }
-        if (!g->pack_node || cudaGraphInstantiate(&g->exec, graph, 0) != cudaSuccess) {
+        if (!g->pack_node || !g->fin_node || cudaGraphInstantiate(&g->exec, graph, 0) != cudaSuccess) {
             cudaGetLastError();
             drop_slot(*g);
             return TURBOREG_ERR_CUDA;
@@ -547,6 +556,13 @@ int run_plan(turboreg_ctx* c, const Plan& pl, bool no_graph, const float* dsrc, 
     kp.kernelParams = g->args;
     kp.extra = nullptr;
     TR_CHECK(cudaGraphExecKernelNodeSetParams(g->exec, g->pack_node, &kp));
+    g->out = out;
+    g->fin_args[0] = &g->batch;
+    g->fin_args[1] = &g->out;
+    cudaKernelNodeParams fp = g->fin_params;
+    fp.kernelParams = g->fin_args;
+    fp.extra = nullptr;
+    TR_CHECK(cudaGraphExecKernelNodeSetParams(g->exec, g->fin_node, &fp));
     TR_CHECK(cudaGraphLaunch(g->exec, c->stream));
     return TURBOREG_OK;
 }
@@ -588,10 +604,11 @@ PtrKind pointer_kind(const void* p)
 }
 
 // Checks, input copies and the launch of one registration (graph replay or
-// direct launches); the result is left in ws.res.  async: host inputs must be
-// page-locked.  *s_in, *d_in receive the device inputs used.
+// direct launches); finalize writes the result to `out` (page-locked host or
+// device memory).  async: host inputs must be page-locked.  *s_in, *d_in
+// receive the device inputs used.
 int enqueue_single(turboreg_ctx* c, const float* src, const float* dst, int32_t n, const turboreg_params* p,
-                   bool async, const float** s_in, const float** d_in, bool* timed)
+                   bool async, const float** s_in, const float** d_in, bool* timed, turboreg_result* out)
 {
     int rc = check_params(c, n, p);
     if (rc != TURBOREG_OK) return rc;
@@ -614,7 +631,7 @@ int enqueue_single(turboreg_ctx* c, const float* src, const float* dst, int32_t 
     rc = build_plan(c, 1, &off0, &n, &p, pl);
     if (rc != TURBOREG_OK) return rc;
     const bool no_graph = (p->flags & TURBOREG_FLAG_NO_GRAPH) != 0;
-    rc = run_plan(c, pl, no_graph, *s_in, *d_in);
+    rc = run_plan(c, pl, no_graph, *s_in, *d_in, out);
     if (rc != TURBOREG_OK) return rc;
     c->last_n = n;
     c->last_npad = round_up(n, kSc2BN);
@@ -753,7 +770,7 @@ int turboreg_register(turboreg_ctx* c, const float* src, const float* dst, int32
     const float* s_in = src;
     const float* d_in = dst;
     bool timed = false;
-    int rc = enqueue_single(c, src, dst, n, p, false, &s_in, &d_in, &timed);
+    int rc = enqueue_single(c, src, dst, n, p, false, &s_in, &d_in, &timed, c->host_res);
     if (rc == TURBOREG_ERR_NONFINITE) {   // host inputs rejected before any device work
         TR_CHECK(cudaStreamSynchronize(c->stream));
         fail_result(out, rc);
@@ -763,8 +780,7 @@ int turboreg_register(turboreg_ctx* c, const float* src, const float* dst, int32
         if (rc == TURBOREG_ERR_INVALID_ARG || rc == TURBOREG_ERR_TOO_FEW) fail_result(out, rc);
         return rc;
     }
-    TR_CHECK(cudaMemcpyAsync(c->host_res, c->ws.res, sizeof(turboreg_result), cudaMemcpyDeviceToHost, c->stream));
-    TR_CHECK(cudaStreamSynchronize(c->stream));
+    TR_CHECK(cudaStreamSynchronize(c->stream));   // finalize wrote c->host_res
     c->have_times = timed;
     rc = collect_times(c);
     if (rc != TURBOREG_OK) return rc;
@@ -789,9 +805,8 @@ int turboreg_register_async(turboreg_ctx* c, const float* src, const float* dst,
     const float* s_in = src;
     const float* d_in = dst;
     bool timed = false;
-    const int rc = enqueue_single(c, src, dst, n, p, true, &s_in, &d_in, &timed);
+    const int rc = enqueue_single(c, src, dst, n, p, true, &s_in, &d_in, &timed, out);
     if (rc != TURBOREG_OK) return rc;
-    TR_CHECK(cudaMemcpyAsync(out, c->ws.res, sizeof(turboreg_result), cudaMemcpyDefault, c->stream));
     c->have_times = false;
     return TURBOREG_OK;
 }
@@ -859,10 +874,9 @@ int turboreg_register_batched(turboreg_ctx* c, const float* src_cat, const float
     if (m > 0) {
         Plan pl;
         int rc = build_plan(c, m, off.data(), nn.data(), pp.data(), pl);
-        if (rc == TURBOREG_OK) rc = run_plan(c, pl, (mode & TURBOREG_FLAG_NO_GRAPH) != 0, s_in, d_in);
+        if (rc == TURBOREG_OK)
+            rc = run_plan(c, pl, (mode & TURBOREG_FLAG_NO_GRAPH) != 0, s_in, d_in, c->host_res);
         if (rc != TURBOREG_OK) return rc;
-        TR_CHECK(cudaMemcpyAsync(c->host_res, c->ws.res, sizeof(turboreg_result) * m, cudaMemcpyDeviceToHost,
-                                 c->stream));
     }
     TR_CHECK(cudaStreamSynchronize(c->stream));
     int32_t q = 0;
@@ -890,10 +904,9 @@ int turboreg_register_batched(turboreg_ctx* c, const float* src_cat, const float
         for (size_t k = 0; k < fq.size(); ++k) fp[k] = &fq[k];
         Plan pl;
         int rc = build_plan(c, static_cast<int32_t>(fb.size()), fo.data(), fn.data(), fp.data(), pl);
-        if (rc == TURBOREG_OK) rc = run_plan(c, pl, (mode & TURBOREG_FLAG_NO_GRAPH) != 0, s_in, d_in);
+        if (rc == TURBOREG_OK)
+            rc = run_plan(c, pl, (mode & TURBOREG_FLAG_NO_GRAPH) != 0, s_in, d_in, c->host_res);
         if (rc != TURBOREG_OK) return rc;
-        TR_CHECK(cudaMemcpyAsync(c->host_res, c->ws.res, sizeof(turboreg_result) * fb.size(),
-                                 cudaMemcpyDeviceToHost, c->stream));
         TR_CHECK(cudaStreamSynchronize(c->stream));
         for (size_t k = 0; k < fb.size(); ++k) {
             out[fb[k]] = c->host_res[k];

@@ -209,7 +209,7 @@ __device__ __forceinline__ int key_hypothesis(const ProbView& v, unsigned long l
 // largest selection key over the valid hypotheses, counts, and the result.
 // (Folding it into the last verification block was measured slower: the
 // completion counter of ~1300 blocks on one address serialises in L2.)
-__global__ void __launch_bounds__(1024) finalize_kernel(ManyViews vs)
+__global__ void __launch_bounds__(1024) finalize_kernel(ManyViews vs, turboreg_result* out)
 {
     pdl_wait();
     pdl_release();
@@ -323,12 +323,20 @@ __global__ void __launch_bounds__(1024) finalize_kernel(ManyViews vs)
         r.used_fp64 = (__float_as_uint(srec[13]) & 2u) ? 1 : 0;
         r.status = TURBOREG_OK;
     }
-    *v.res = r;
+    // the caller's result array (page-locked host or device memory, one entry
+    // per problem of the launch), or the workspace's
+    if (out != nullptr) out[blockIdx.x] = r;
+    else *v.res = r;
 }
 
 }  // namespace
 
-void launch_finalize(const Batch& b, cudaStream_t s) { launch_pdl(finalize_kernel, b.num, 1024, 0, s, ManyViews{b}); }
+void launch_finalize(const Batch& b, turboreg_result* out, cudaStream_t s)
+{
+    launch_pdl(finalize_kernel, b.num, 1024, 0, s, ManyViews{b}, out);
+}
+
+const void* finalize_kernel_func() { return reinterpret_cast<const void*>(&finalize_kernel); }
 
 void launch_kabsch(const Batch& b, int total, cudaStream_t s)
 {

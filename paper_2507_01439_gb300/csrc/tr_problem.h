@@ -138,7 +138,10 @@ void launch_count_emit(const Batch& b, const int32_t tot[kNumBatchStages], cudaS
 // The clique search also orders the pivots (each warp ranks its selected edge)
 void launch_pgs(const Batch& b, int total, int k2_max, int max_k1, cudaStream_t s);
 void launch_kabsch(const Batch& b, int total, cudaStream_t s);
-void launch_finalize(const Batch& b, cudaStream_t s);
+// out: results of the launch's problems in order (page-locked host or device
+// memory), or null for the workspace's result array
+void launch_finalize(const Batch& b, turboreg_result* out, cudaStream_t s);
+const void* finalize_kernel_func();
 // Kabsch of caller-given k-cliques (k >= 4) into v.rt; idx [m][k] on the device.
 void launch_kabsch_n(const ProbView& v, const int32_t* idx, int k, int m, cudaStream_t s);
 // pw: the kernel's points per warp (32, 64, 128); every problem's vppb <= 4 pw

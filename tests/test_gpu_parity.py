@@ -75,6 +75,18 @@ def test_k2_variants(ctx, k2):
     _full_parity(ctx, p, k1=300, k2=k2)
 
 
+def test_k1_max(ctx):
+    # K1 = K1_MAX: the clique search stages 8192 selected keys (64 KB of shared memory)
+    p = synth.make_problem("indoor", 3000, 0.1, 45)
+    _full_parity(ctx, p, k1=trg.TURBOREG_K1_MAX)
+
+
+def test_k2_max(ctx):
+    # K2 = K2_MAX: the generic clique-search variant (16 cliques per pivot)
+    p = synth.make_problem("cube", 1200, 0.2, 46)
+    _full_parity(ctx, p, k1=400, k2=trg.TURBOREG_K2_MAX)
+
+
 def test_bitset_sc2_matches(ctx):
     p = synth.make_problem("indoor", 3000, 0.05, 11)
     _full_parity(ctx, p, k1=1500, flags=trg.FLAG_SC2_BITSET)
