@@ -55,6 +55,7 @@ struct Workspace {
     int4* cliques = nullptr;         // [slots][nh]
     float* rt = nullptr;             // [slots][nh * 16]
     int32_t* inl = nullptr;          // [slots][nh]
+    uint32_t* hbits = nullptr;       // [slots][2][nh / 32]
     unsigned long long* score = nullptr;  // [slots][nh]
     float* feat = nullptr;           // [slots][np][8] proposal features
     float* prob = nullptr;           // [slots][np] proposal probabilities
@@ -159,7 +160,7 @@ cudaError_t halloc(T** p, size_t count)
 void free_ws(Workspace& ws)
 {
     void* dptrs[] = {ws.pts, ws.pts8, ws.a8, ws.bits, ws.w, ws.rows, ws.hist, ws.cand, ws.piv, ws.cliques,
-                     ws.rt, ws.inl, ws.score, ws.feat, ws.prob, ws.ctl, ws.res, ws.in_src, ws.in_dst,
+                     ws.rt, ws.inl, ws.hbits, ws.score, ws.feat, ws.prob, ws.ctl, ws.res, ws.in_src, ws.in_dst,
                      ws.desc};
     for (void* p : dptrs)
         if (p) cudaFree(p);
@@ -193,6 +194,7 @@ int alloc_ws(Workspace& ws, int32_t max_n, int32_t slots)
     if (e == cudaSuccess) e = dalloc(&ws.cliques, S * nh);
     if (e == cudaSuccess) e = dalloc(&ws.rt, S * nh * 16);
     if (e == cudaSuccess) e = dalloc(&ws.inl, S * nh);
+    if (e == cudaSuccess) e = dalloc(&ws.hbits, S * nh / 16);
     if (e == cudaSuccess) e = dalloc(&ws.score, S * nh);
     if (e == cudaSuccess) e = dalloc(&ws.feat, S * np * 8);
     if (e == cudaSuccess) e = dalloc(&ws.prob, S * np);
@@ -294,6 +296,7 @@ ProbView make_view(turboreg_ctx* c, int slot, int64_t in_off, int32_t n, const t
     v.cliques = ws.cliques + s * ws.nh;
     v.rt = ws.rt + s * ws.nh * 16;
     v.inl = ws.inl + s * ws.nh;
+    v.hbits = ws.hbits + s * ws.nh / 16;
     v.score = ws.score + s * ws.nh;
     v.feat = ws.feat + s * np * 8;
     v.prob = p->proposal == TURBOREG_PROPOSAL_LEARNED ? ws.prob + s * np : nullptr;

@@ -47,6 +47,7 @@ __global__ void __launch_bounds__(128) kabsch_kernel(ManyViews vs)
 // 4 PW points) are a tile-shape choice of the caller (TURBOREG_FLAG_VERIFY_*).
 constexpr int kVWarps = 4;
 constexpr int kVHyp = 128;
+constexpr int kHypWords = TURBOREG_K1_MAX * TURBOREG_K2_MAX / 32;   // words of one flag-bit array
 constexpr float kScoreUnits = 4194304.f;   // 2^22 units per theta (MAE) or theta^2 (MSE)
 
 template <int PW>
@@ -84,12 +85,13 @@ __device__ __forceinline__ void verify_body(const ProbView& v, int lb, VerifySha
         const int slot = h0 + threadIdx.x;
         float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0, r3 = r0;
         bool ok = false;
+        uint32_t flags = 0u;
         if (slot < nh) {
             const int h = slot;
             const float4* rt = reinterpret_cast<const float4*>(v.rt + (size_t)h * 16);
             r0 = rt[0]; r1 = rt[1]; r2 = rt[2]; r3 = rt[3];
-            const int flags = __float_as_int(r3.y);
-            ok = (flags & 1) != 0;
+            flags = __float_as_uint(r3.y);
+            ok = (flags & 1u) != 0u;
             if (!ok) r2.y = r2.z = r2.w = __int_as_float(0x7fc00000);   // NaN t: never an inlier
         } else {
             r2.y = r2.z = r2.w = __int_as_float(0x7fc00000);
@@ -99,6 +101,16 @@ __device__ __forceinline__ void verify_body(const ProbView& v, int lb, VerifySha
         d[4] = r1.x; d[5] = r1.y; d[6] = r1.z; d[7] = r1.w;
         d[8] = r2.x; d[9] = r2.y; d[10] = r2.z; d[11] = r2.w;
         sh.sok[threadIdx.x] = ok ? 1 : 0;
+        // the tile's first match block records, one bit per hypothesis, which
+        // are valid and which took the FP64 normals (read by the model selection)
+        if (k0 == 0) {
+            const uint32_t bv = __ballot_sync(0xffffffffu, ok);
+            const uint32_t bf = __ballot_sync(0xffffffffu, (flags & 2u) != 0u);
+            if (lane == 0) {
+                v.hbits[(h0 >> 5) + warp] = bv;
+                v.hbits[kHypWords + (h0 >> 5) + warp] = bf;
+            }
+        }
     }
     __syncthreads();
     // this lane's hypotheses: slots lane + 32 a, a = 0..3, as packed pairs (0,1), (2,3)
@@ -207,6 +219,8 @@ __device__ __forceinline__ int key_hypothesis(const ProbView& v, unsigned long l
 
 // Model selection (Eq. 9), one block of 1024 threads per problem: h* = the
 // largest selection key over the valid hypotheses, counts, and the result.
+// One round of loads: the inlier numbers (and scores) of every slot up to
+// K1 K2 and the verification's flag words, masked by the pivot count after.
 // (Folding it into the last verification block was measured slower: the
 // completion counter of ~1300 blocks on one address serialises in L2.)
 __global__ void __launch_bounds__(1024) finalize_kernel(ManyViews vs, turboreg_result* out)
@@ -221,21 +235,19 @@ __global__ void __launch_bounds__(1024) finalize_kernel(ManyViews vs, turboreg_r
     __shared__ int4 scl;
     __shared__ int sinl;
     __shared__ unsigned long long sscore;
-    // one round of loads: the pivot count with every slot's flags and inlier
-    // number (and score), slots up to K1 K2 (the buffers' capacity), masked
-    // by the pivot count afterwards
     const int hmax = v.k1 * v.k2;
     const int np = __ldcg(&v.ctl->n_pivots);
     unsigned long long best = 0ull;
     int nvalid = 0, nfp = 0;
     for (int h0 = threadIdx.x; h0 < hmax; h0 += 4 * blockDim.x) {
-        uint32_t fl[4];
+        uint32_t bv[4], bf[4];
         int in4[4];
         unsigned long long sc4[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int h = h0 + u * blockDim.x;
-            fl[u] = h < hmax ? static_cast<uint32_t>(__ldcg(reinterpret_cast<const int*>(v.rt) + (size_t)h * 16 + 13)) : 0u;
+            bv[u] = h < hmax ? __ldcg(v.hbits + (h >> 5)) : 0u;
+            bf[u] = h < hmax ? __ldcg(v.hbits + kHypWords + (h >> 5)) : 0u;
             in4[u] = h < hmax ? __ldcg(v.inl + h) : 0;
             sc4[u] = (h < hmax && v.scoring != TURBOREG_SCORE_IN) ? __ldcg(v.score + h) : 0ull;
         }
@@ -243,10 +255,10 @@ __global__ void __launch_bounds__(1024) finalize_kernel(ManyViews vs, turboreg_r
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int h = h0 + u * blockDim.x;
-            const uint32_t f = h < nh ? fl[u] : 0u;
-            const unsigned long long key = (f & 1u) ? select_key(v.scoring, in4[u], sc4[u], h) : 0ull;
-            nfp += (f & 2u) ? 1 : 0;
-            nvalid += (f & 1u) ? 1 : 0;
+            const bool valid = h < nh && ((bv[u] >> (h & 31)) & 1u);
+            const unsigned long long key = valid ? select_key(v.scoring, in4[u], sc4[u], h) : 0ull;
+            nfp += (h < nh && ((bf[u] >> (h & 31)) & 1u)) ? 1 : 0;
+            nvalid += valid ? 1 : 0;
             best = key > best ? key : best;
         }
     }

@@ -43,6 +43,8 @@ struct ProbView {
     int4* cliques;       // [K1_MAX*K2_MAX] (i, j, z, valid) in Alg. 2 order
     float* rt;           // [K1_MAX*K2_MAX][16] R, t, kappa, flags
     int32_t* inl;        // [K1_MAX*K2_MAX] inlier numbers
+    uint32_t* hbits;     // [2][K1_MAX*K2_MAX/32] bit h of word h/32: hypothesis h valid, and
+                         // (second half) solved with FP64 normals; written by verification
     unsigned long long* score;  // [K1_MAX*K2_MAX] capped error sums in units of 2^-22 theta (^2)
     float* feat;         // [n_pad][8] proposal features (learned proposal only)
     float* prob;         // [n_pad] inlier probabilities; non-null selects the learned pivot weight
