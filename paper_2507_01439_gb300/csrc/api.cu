@@ -79,6 +79,7 @@ struct Plan {
     int32_t bitset = 0, timed = 0, learned = 0;
     int32_t gemm_form = 2;   // SC^2 GEMM: 0 independent CTAs, 1 multicast clusters, 2 pair MMAs
     int32_t vpw = 64;        // verification tile: points per warp
+    int32_t vcap = 0;        // balanced tile: verification launched with at most four blocks per SM
     int32_t tot[kNumBatchStages] = {};
 };
 
@@ -381,6 +382,7 @@ int build_plan(turboreg_ctx* c, int32_t num, const int64_t* in_off, const int32_
         }
     }
     plan.vpw = vppb_max <= 4 * 32 ? 32 : vppb_max <= 4 * 64 ? 64 : 128;
+    plan.vcap = num == 1 && !vflag;
     return TURBOREG_OK;
 }
 
@@ -443,7 +445,7 @@ int enqueue_plan(turboreg_ctx* c, const Plan& pl, const Batch& bt, const float* 
     launch_pgs(bt, pl.tot[ST_PGS], pl.k2_common, pl.max_k1, s);   // also ranks the pivots and solves the cliques' Kabsch
     TR_EV(5);
     TR_EV(6);
-    launch_verify(bt, pl.tot[ST_VERIFY], pl.vpw, s);
+    launch_verify(bt, pl.tot[ST_VERIFY], pl.vpw, pl.vcap != 0, s);
     TR_EV(7);
     launch_finalize(bt, out, s);
     TR_EV(8);
@@ -1065,7 +1067,7 @@ int turboreg_score_transforms(turboreg_ctx* c, const float* src, const float* ds
     TR_CHECK(cudaMemcpyAsync(&v.ctl->n_pivots, &m, sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
     TR_CHECK(cudaMemsetAsync(v.inl, 0, sizeof(int32_t) * m, c->stream));
     TR_CHECK(cudaMemsetAsync(v.score, 0, sizeof(unsigned long long) * m, c->stream));
-    launch_verify(bt, pl.tot[ST_VERIFY], pl.vpw, c->stream);
+    launch_verify(bt, pl.tot[ST_VERIFY], pl.vpw, pl.vcap != 0, c->stream);
     TR_CHECK(cudaGetLastError());
     TR_CHECK(cudaMemcpyAsync(out_in, v.inl, sizeof(int32_t) * m, cudaMemcpyDeviceToHost, c->stream));
     if (out_units)

@@ -47,6 +47,8 @@ __global__ void __launch_bounds__(128) kabsch_kernel(ManyViews vs)
 // 4 PW points) are a tile-shape choice of the caller (TURBOREG_FLAG_VERIFY_*).
 constexpr int kVWarps = 4;
 constexpr int kVHyp = 128;
+constexpr int kCapPerSm = 4;    // blocks per SM of the balanced single-problem tile
+int g_cap_dyn[3] = {0, 0, 0};   // dynamic shared-memory padding for that cap (32, 64, 128 points per warp)
 constexpr int kHypWords = TURBOREG_K1_MAX * TURBOREG_K2_MAX / 32;   // words of one flag-bit array
 constexpr float kScoreUnits = 4194304.f;   // 2^22 units per theta (MAE) or theta^2 (MSE)
 
@@ -365,14 +367,40 @@ cudaError_t verify_setup()
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(verify_kernel<128>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  cudaSharedmemCarveoutMaxShared);
-    return e;
+    if (e != cudaSuccess) return e;
+    // padding that leaves room for kCapPerSm blocks per SM and no more: the
+    // balanced single-problem tile launches exactly kCapPerSm blocks per SM, and
+    // its blocks become resident while the clique search still runs (early
+    // launch); without the cap the first SMs to free up would take more than
+    // their share
+    int dev = 0, smem_sm = 0, reserved = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev)) != cudaSuccess) return e;
+    const void* fns[3] = {reinterpret_cast<const void*>(&verify_kernel<32>),
+                          reinterpret_cast<const void*>(&verify_kernel<64>),
+                          reinterpret_cast<const void*>(&verify_kernel<128>)};
+    for (int k = 0; k < 3; ++k) {
+        cudaFuncAttributes fa;
+        if ((e = cudaFuncGetAttributes(&fa, fns[k])) != cudaSuccess) return e;
+        const int per_block = smem_sm / (kCapPerSm + 1) + 1;       // kCapPerSm + 1 blocks no longer fit
+        int dyn = per_block - reserved - static_cast<int>(fa.sharedSizeBytes);
+        dyn = dyn <= 0 ? 0 : (dyn + 1023) / 1024 * 1024;
+        if (kCapPerSm * (static_cast<int>(fa.sharedSizeBytes) + dyn + reserved) > smem_sm) dyn = 0;
+        if ((e = cudaFuncSetAttribute(fns[k], cudaFuncAttributeMaxDynamicSharedMemorySize, dyn)) != cudaSuccess)
+            return e;
+        g_cap_dyn[k] = dyn;
+    }
+    return cudaSuccess;
 }
 
-void launch_verify(const Batch& b, int total, int pw, cudaStream_t s)
+void launch_verify(const Batch& b, int total, int pw, bool capped, cudaStream_t s)
 {
-    if (pw == 32) launch_pdl(verify_kernel<32>, total, 128, 0, s, ManyViews{b});
-    else if (pw == 128) launch_pdl(verify_kernel<128>, total, 128, 0, s, ManyViews{b});
-    else launch_pdl(verify_kernel<64>, total, 128, 0, s, ManyViews{b});
+    const int k = pw == 32 ? 0 : pw == 128 ? 2 : 1;
+    const size_t dyn = capped ? static_cast<size_t>(g_cap_dyn[k]) : 0;
+    if (pw == 32) launch_pdl(verify_kernel<32>, total, 128, dyn, s, ManyViews{b});
+    else if (pw == 128) launch_pdl(verify_kernel<128>, total, 128, dyn, s, ManyViews{b});
+    else launch_pdl(verify_kernel<64>, total, 128, dyn, s, ManyViews{b});
 }
 
 // Per-problem block counts of every stage.
@@ -380,7 +408,7 @@ int32_t balanced_vppb(int32_t n, int32_t nh, int32_t num_sms)
 {
     const int32_t nhb = (nh + kVHyp - 1) / kVHyp;
     const int32_t npb_min = (n + 4 * 128 - 1) / (4 * 128);             // capacity of the widest tile
-    int32_t npb = nhb > 0 ? (4 * num_sms) / nhb : npb_min;
+    int32_t npb = nhb > 0 ? (kCapPerSm * num_sms) / nhb : npb_min;
     if (npb < npb_min) npb = npb_min;
     int32_t vppb = (n + npb - 1) / npb;
     vppb = (vppb + kVWarps - 1) / kVWarps * kVWarps;

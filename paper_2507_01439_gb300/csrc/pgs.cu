@@ -51,8 +51,8 @@ __global__ void __launch_bounds__(256, 2) pgs_kernel(ManyViews vs)
     int (*scand)[kCand] = reinterpret_cast<int (*)[kCand]>(pgs_smem);
     uint64_t* skey = reinterpret_cast<uint64_t*>(pgs_smem + kListBytes);
     pdl_wait();
-    // no early release: the verification blocks, placed while these still hold
-    // registers, would spread unevenly over the SMs (measured slower)
+    pdl_release();   // the balanced verification tile caps itself at four blocks per SM, so
+                     // blocks placed beside these still end up evenly spread
     int lb;
     const ProbView v = vs.get(ST_PGS, blockIdx.x, lb);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;

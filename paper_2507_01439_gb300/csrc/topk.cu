@@ -34,6 +34,8 @@ namespace {
 
 constexpr int kHistSmemMaxBins = 24576;   // 96 KB of shared bins; larger N uses global atomics
 constexpr int kHistRowsPerBlock = 64;     // 8 warps x 8 rows
+constexpr int kCountThreads = 256;
+constexpr int kCountPairs = 8;            // row pairs per count block
 
 __device__ __forceinline__ uint64_t edge_key(int w, int i, int j, int n)
 {
@@ -132,55 +134,86 @@ __device__ __forceinline__ void count_chunk(uint4 q, uint32_t a2, int& g, int& e
           __popc(__vcmpeq2(q.w, a2))) >> 4;
 }
 
-// Per-row counts of the weight > alpha and weight == alpha edges.  Warp w
-// takes rows w and n-1-w, whose upper-triangle parts hold about n/8 16-byte
-// chunks together, so every warp has the same work; each lane keeps eight
-// 16-byte loads in flight.  Rows holding such edges are appended to the
-// active list as (row, #gt, #eq), in any order.
+// Per-row counts of the weight > alpha and weight == alpha edges.  A block
+// owns eight row pairs (w, n-1-w), whose upper-triangle parts hold about n/8
+// 16-byte chunks per pair, so every block has about the same span of rows.
+// Rows whose largest weight (recorded by the SC^2 pass) is below alpha hold
+// no such edge and are skipped without reading W (the learned pivot weight
+// floor(W p_i p_j) never exceeds W).  The chunks of the remaining rows are
+// spread over all the block's threads, eight 16-byte loads in flight each,
+// so a block with one or two such rows reads them in one round.  Rows
+// holding such edges are appended to the active list as (row, #gt, #eq), in
+// any order.
 template <class VS>
-__global__ void __launch_bounds__(128) count_kernel(VS vs)
+__global__ void __launch_bounds__(kCountThreads, 3) count_kernel(VS vs)
 {
     pdl_wait();
     pdl_release();
+    __shared__ int srow[16], sc0[16], soff[17], sg[16], se[16];
     int lb;
     const ProbView v = vs.get(ST_COUNT, blockIdx.x, lb);
-    const int lane = threadIdx.x & 31;
     const int n = v.n;
-    const int wp = lb * 4 + (threadIdx.x >> 5);
-    if (v.ctl->n_sel == 0 || wp >= (n + 1) / 2) return;
+    if (v.ctl->n_sel == 0) return;
     const int alpha = v.ctl->alpha;
+    const int t = threadIdx.x;
+    if (t < 32) {
+        // entry k = t (< 16): pair p = 8 lb + k / 2, side k % 2
+        const int p = lb * kCountPairs + (t >> 1);
+        const int row = (t & 1) ? n - 1 - p : p;
+        bool act = t < 16 && p < (n + 1) / 2 && !((t & 1) && row == p) && row + 1 < n;
+        if (act && v.rowmax != nullptr) act = __ldg(v.rowmax + row) >= alpha;
+        const int c0 = (row + 1) >> 3;
+        const int len = act ? ((n - 1) >> 3) - c0 + 1 : 0;
+        int incl = len;
+#pragma unroll
+        for (int off = 1; off < 16; off <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, off);
+            if (t >= off) incl += y;
+        }
+        if (t < 16) {
+            srow[t] = row;
+            sc0[t] = c0;
+            soff[t] = incl - len;
+            sg[t] = 0;
+            se[t] = 0;
+        }
+        if (t == 15) soff[16] = incl;
+    }
+    __syncthreads();
+    const int tot = soff[16];
+    if (tot == 0) return;                     // uniform over the block
     const uint32_t a2 = static_cast<uint32_t>(alpha) * 0x10001u;
     const bool learned = v.prob != nullptr;
-    const int ra = wp, rb = n - 1 - wp;           // rb == ra: middle row of an odd n
-    const int c1 = (n - 1) >> 3;
-    const int a0 = (ra + 1) >> 3, b0 = (rb + 1) >> 3;
-    // a row whose largest weight is below alpha holds no such edge (the learned
-    // pivot weight floor(W p_i p_j) never exceeds W): skip it without reading W
-    const bool ka = v.rowmax == nullptr || __ldg(v.rowmax + ra) >= alpha;
-    const bool kb = v.rowmax == nullptr || __ldg(v.rowmax + rb) >= alpha;
-    const int la = (ka && ra + 1 < n) ? c1 - a0 + 1 : 0;
-    const int lbn = (kb && rb != ra && rb + 1 < n) ? c1 - b0 + 1 : 0;
-    const int tot = la + lbn;
-    if (tot == 0) return;
-    int ga = 0, ea = 0, gb = 0, eb = 0;
-    for (int base = lane; base < tot; base += 8 * 32) {
+    int kcur = -1, g = 0, e = 0;              // running counts of entry kcur
+    for (int base = t; base < tot; base += 8 * kCountThreads) {
         uint4 q[8];
+        int kk[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
-            const int x = base + u * 32;
-            const int row = x < la ? ra : rb;
-            const int c = x < la ? a0 + x : b0 + (x - la);
-            q[u] = x < tot ? *reinterpret_cast<const uint4*>(v.w + (size_t)row * v.n_pad + c * 8)
+            const int x = base + u * kCountThreads;
+            int k = 0;
+#pragma unroll
+            for (int m = 1; m < 16; ++m) k += soff[m] <= x ? 1 : 0;
+            kk[u] = k;
+            q[u] = x < tot ? *reinterpret_cast<const uint4*>(v.w + (size_t)srow[k] * v.n_pad +
+                                                             (size_t)(sc0[k] + x - soff[k]) * 8)
                            : make_uint4(0u, 0u, 0u, 0u);
         }
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
-            const int x = base + u * 32;
-            const bool isa = x < la;
-            const int row = isa ? ra : rb;
-            const int c = isa ? a0 + x : b0 + (x - la);
+            const int x = base + u * kCountThreads;
+            if (x >= tot) break;
+            const int k = kk[u];
+            const int row = srow[k], c = sc0[k] + x - soff[k];
+            if (k != kcur) {
+                if (kcur >= 0) {
+                    if (g) atomicAdd(&sg[kcur], g);
+                    if (e) atomicAdd(&se[kcur], e);
+                }
+                kcur = k;
+                g = e = 0;
+            }
             const uint4 qm = mask_chunk(q[u], c, row, n);
-            int g = 0, e = 0;
             if (!learned) {
                 count_chunk(qm, a2, g, e);
             } else if ((qm.x | qm.y | qm.z | qm.w) != 0u) {
@@ -192,20 +225,15 @@ __global__ void __launch_bounds__(128) count_kernel(VS vs)
                     e += pw == alpha;
                 }
             }
-            if (isa) { ga += g; ea += e; } else { gb += g; eb += e; }
         }
     }
-#pragma unroll
-    for (int off = 16; off >= 1; off >>= 1) {
-        ga += __shfl_xor_sync(0xffffffffu, ga, off);
-        ea += __shfl_xor_sync(0xffffffffu, ea, off);
-        gb += __shfl_xor_sync(0xffffffffu, gb, off);
-        eb += __shfl_xor_sync(0xffffffffu, eb, off);
+    if (kcur >= 0) {
+        if (g) atomicAdd(&sg[kcur], g);
+        if (e) atomicAdd(&se[kcur], e);
     }
-    if (lane == 0) {
-        if (ga | ea) v.active[atomicAdd(&v.ctl->n_active, 1u)] = make_int4(ra, ga, ea, 0);
-        if (rb != ra && (gb | eb)) v.active[atomicAdd(&v.ctl->n_active, 1u)] = make_int4(rb, gb, eb, 0);
-    }
+    __syncthreads();
+    if (t < 16 && (sg[t] | se[t]))
+        v.active[atomicAdd(&v.ctl->n_active, 1u)] = make_int4(srow[t], sg[t], se[t], 0);
 }
 
 // Blocks take the active rows in any order.  W > alpha edges take slots
@@ -394,7 +422,7 @@ void launch_select(const Batch& b, cudaStream_t s) { launch_pdl(select_kernel<Ma
 void launch_count_emit(const Batch& b, const int32_t tot[kNumBatchStages], cudaStream_t s)
 {
     const ManyViews vs{b};
-    launch_pdl(count_kernel<ManyViews>, tot[ST_COUNT], 128, 0, s, vs);
+    launch_pdl(count_kernel<ManyViews>, tot[ST_COUNT], kCountThreads, 0, s, vs);
     launch_pdl(emit_kernel<ManyViews>, tot[ST_EMIT], 256, 0, s, vs);
 }
 
@@ -404,7 +432,7 @@ void launch_topk_single(const ProbView& v, cudaStream_t s)
     const OneView vs{v};
     launch_hist_vs(vs, (v.n + kHistRowsPerBlock - 1) / kHistRowsPerBlock, v.n, s);
     launch_pdl(select_kernel<OneView>, 1, 1024, 0, s, vs);
-    launch_pdl(count_kernel<OneView>, count_blocks(v.n), 128, 0, s, vs);
+    launch_pdl(count_kernel<OneView>, count_blocks(v.n), kCountThreads, 0, s, vs);
     launch_pdl(emit_kernel<OneView>, emit_blocks(v.n), 256, 0, s, vs);
     launch_pdl(rank_kernel<OneView>, (v.k1 + 31) / 32, 256, v.k1 * 8, s, vs);
 }

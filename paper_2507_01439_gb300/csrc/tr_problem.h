@@ -60,9 +60,9 @@ enum Stage {
     ST_VERIFY, ST_FINAL, ST_HIST, ST_BITSET, ST_GEMM, ST_FEAT, ST_MLP, kNumBatchStages
 };
 
-// Blocks of the per-row count pass (four row pairs per block, a warp each)
-// and of the emit pass (active rows strided over the blocks).
-__host__ __device__ inline int count_blocks(int n) { return ((n + 1) / 2 + 3) / 4; }
+// Blocks of the per-row count pass (eight row pairs per block) and of the
+// emit pass (active rows strided over the blocks).
+__host__ __device__ inline int count_blocks(int n) { return ((n + 1) / 2 + 7) / 8; }
 __host__ __device__ inline int emit_blocks(int n) { return (n + 7) / 8; }
 
 struct Batch {
@@ -147,7 +147,8 @@ const void* finalize_kernel_func();
 // Kabsch of caller-given k-cliques (k >= 4) into v.rt; idx [m][k] on the device.
 void launch_kabsch_n(const ProbView& v, const int32_t* idx, int k, int m, cudaStream_t s);
 // pw: the kernel's points per warp (32, 64, 128); every problem's vppb <= 4 pw
-void launch_verify(const Batch& b, int total, int pw, cudaStream_t s);
+// capped: at most four blocks per SM (the balanced single-problem tile)
+void launch_verify(const Batch& b, int total, int pw, bool capped, cudaStream_t s);
 
 // set kernel attributes (dynamic shared memory limits) once per device
 cudaError_t sc2_tcgen05_setup();
