@@ -420,15 +420,16 @@ int enqueue_plan(turboreg_ctx* c, const Plan& pl, const Batch& bt, const float* 
     TR_EV(1);
     launch_compat(bt, pl.tot[ST_COMPAT], s);
     TR_EV(2);
+    bool fused = false;
     if (pl.bitset) {
         launch_sc2_bitset(bt, pl.tot[ST_BITSET], s);
         launch_hist(bt, pl.tot[ST_HIST], pl.max_n, s);
         launch_select(bt, s);
     } else {
-        // one problem whose histogram fits in shared memory: the GEMM's last
-        // CTA chooses the threshold; a batch or a larger problem (global
-        // histogram) adds a select launch
-        const bool fused = launch_sc2_tcgen05(bt, pl.tot[ST_GEMM], pl.max_n, pl.gemm_form, s);
+        // one problem whose histogram fits in the GEMM's shared memory: the
+        // count blocks choose the threshold; a batch or a larger problem adds
+        // a select launch
+        fused = launch_sc2_tcgen05(bt, pl.tot[ST_GEMM], pl.max_n, pl.gemm_form, s);
         if (!fused && !pl.learned) launch_select(bt, s);
     }
     if (pl.learned) {
@@ -440,7 +441,13 @@ int enqueue_plan(turboreg_ctx* c, const Plan& pl, const Batch& bt, const float* 
         launch_select(bt, s);
     }
     TR_EV(3);
-    launch_count_emit(bt, pl.tot, s);
+    // the count blocks stage the histogram in (at most 48 KB of) shared memory
+    bool sel_in_count = fused && !pl.learned;
+    if (sel_in_count && static_cast<size_t>(pl.max_n + 4) * 4 > 48 * 1024) {
+        launch_select(bt, s);
+        sel_in_count = false;
+    }
+    launch_count_emit(bt, pl.tot, sel_in_count, pl.max_n, s);
     TR_EV(4);
     launch_pgs(bt, pl.tot[ST_PGS], pl.k2_common, pl.max_k1, s);   // also ranks the pivots and solves the cliques' Kabsch
     TR_EV(5);

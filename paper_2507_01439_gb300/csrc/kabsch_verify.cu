@@ -61,6 +61,29 @@ struct VerifyShared {
     int sok[kVHyp];
 };
 
+// Stages this block's matches as packed (v, v) pairs.  They were written by
+// the first stage of the registration, so this runs before the wait for the
+// clique search (whose hypotheses are staged after it).
+template <int PW>
+__device__ __forceinline__ void stage_matches(const ProbView& v, int lb, VerifyShared<PW>& sh)
+{
+    const int vppb = v.vppb;
+    const int npb = (v.n + vppb - 1) / vppb;
+    const int k0 = (lb % npb) * vppb;
+    const int kn = min(vppb, v.n - k0);
+    const float4* src = reinterpret_cast<const float4*>(v.pts8 + (size_t)k0 * 8);
+    for (int q = threadIdx.x; q < kn; q += blockDim.x) {
+        const float4 a = __ldcg(src + 2 * q), b = __ldcg(src + 2 * q + 1);   // from L2, past any stale L1 line
+        auto dup = [](float f) {
+            const unsigned long long u = __float_as_uint(f);
+            return (u << 32) | u;
+        };
+        sh.sp[q][0] = make_ulonglong2(dup(a.x), dup(a.y));
+        sh.sp[q][1] = make_ulonglong2(dup(a.z), dup(a.w));
+        sh.sp[q][2] = make_ulonglong2(dup(b.x), dup(b.y));
+    }
+}
+
 template <int kScore, int PW>
 __device__ __forceinline__ void verify_body(const ProbView& v, int lb, VerifyShared<PW>& sh)
 {
@@ -73,17 +96,6 @@ __device__ __forceinline__ void verify_body(const ProbView& v, int lb, VerifySha
     const int kn = min(vppb, v.n - k0);                 // matches of this block
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     {
-        const float4* src = reinterpret_cast<const float4*>(v.pts8 + (size_t)k0 * 8);
-        for (int q = threadIdx.x; q < kn; q += blockDim.x) {
-            const float4 a = src[2 * q], b = src[2 * q + 1];
-            auto dup = [](float f) {
-                const unsigned long long u = __float_as_uint(f);
-                return (u << 32) | u;
-            };
-            sh.sp[q][0] = make_ulonglong2(dup(a.x), dup(a.y));
-            sh.sp[q][1] = make_ulonglong2(dup(a.z), dup(a.w));
-            sh.sp[q][2] = make_ulonglong2(dup(b.x), dup(b.y));
-        }
         const int slot = h0 + threadIdx.x;
         float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0, r3 = r0;
         bool ok = false;
@@ -189,11 +201,12 @@ __device__ __forceinline__ void verify_body(const ProbView& v, int lb, VerifySha
 template <int PW>
 __global__ void __launch_bounds__(128) verify_kernel(ManyViews vs)
 {
-    pdl_wait();
-    pdl_release();
     __shared__ __align__(16) VerifyShared<PW> sh;
     int lb;
-    const ProbView v = vs.get(ST_VERIFY, blockIdx.x, lb);
+    const ProbView v = vs.get(ST_VERIFY, blockIdx.x, lb);   // descriptors: uploaded before the first stage
+    stage_matches(v, lb, sh);
+    pdl_wait();
+    pdl_release();
     switch (v.scoring) {      // uniform over the block: a block serves one problem
         case TURBOREG_SCORE_MAE: verify_body<TURBOREG_SCORE_MAE, PW>(v, lb, sh); break;
         case TURBOREG_SCORE_MSE: verify_body<TURBOREG_SCORE_MSE, PW>(v, lb, sh); break;

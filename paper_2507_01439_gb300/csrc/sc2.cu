@@ -255,7 +255,6 @@ __global__ void __launch_bounds__(kThreads, 1) sc2_tcgen05_kernel(Batch bt, int 
     uint64_t* tfull = empty + kStages;      // [2] accumulator ready
     uint64_t* tempty = tfull + 2;           // [2] accumulator drained
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
-    int* sel_buf = reinterpret_cast<int*>(smem + kPipeBytes + 256);   // 33 ints + last-CTA flag
     uint32_t* shist = reinterpret_cast<uint32_t*>(smem + kPipeBytes + kBarBytes);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -397,17 +396,11 @@ __global__ void __launch_bounds__(kThreads, 1) sc2_tcgen05_kernel(Batch bt, int 
         tmem_dealloc(tmem, kTmemCols);
     }
     if (!kSingle) return;
+    // this CTA's histogram into the global one, from which the count pass
+    // chooses the pivot threshold
     const ProbView v0 = bt.views[0];
     for (int b = threadIdx.x + 1; b < nbins; b += blockDim.x)
         if (shist[b]) atomicAdd(&v0.hist[b], shist[b]);
-    // the last CTA to finish sees the complete histogram: choose the pivot threshold
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) sel_buf[40] = atomicAdd(&v0.ctl->done_blocks, 1u) == gridDim.x - 1;
-    __syncthreads();
-    if (!sel_buf[40]) return;
-    __threadfence();
-    select_alpha(v0, sel_buf, shist);   // this CTA's histogram area, flushed above
 }
 
 // 2-SM form (cta_group::2): the two CTAs of a cluster compute one 256 x 256
@@ -443,7 +436,6 @@ __global__ void __launch_bounds__(kThreads, 1) sc2_pair_mma_kernel(Batch bt, int
     uint64_t* tfull = empty + kStages2;      // [2] accumulator ready
     uint64_t* tempty = tfull + 2;            // [2] accumulator drained (leader's counts both CTAs)
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
-    int* sel_buf = reinterpret_cast<int*>(smem + kPipeBytes2 + 256);
     uint4* stg = reinterpret_cast<uint4*>(smem + kPipeBytes2 + kBarBytes);
     uint32_t* shist = reinterpret_cast<uint32_t*>(smem + kPipeBytes2 + kBarBytes + kStageBytes2);
 
@@ -587,16 +579,11 @@ __global__ void __launch_bounds__(kThreads, 1) sc2_pair_mma_kernel(Batch bt, int
         tmem_dealloc_pair(tmem, kTmemCols);
     }
     if (!kSingle || !leader) return;
+    // the cluster's histogram into the global one, from which the count pass
+    // chooses the pivot threshold
     const ProbView v0 = bt.views[0];
     for (int b = threadIdx.x + 1; b < nbins; b += blockDim.x)
         if (shist[b]) atomicAdd(&v0.hist[b], shist[b]);
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) sel_buf[40] = atomicAdd(&v0.ctl->done_blocks, 1u) == (gridDim.x >> 1) - 1;
-    __syncthreads();
-    if (!sel_buf[40]) return;
-    __threadfence();
-    select_alpha(v0, sel_buf, shist);   // this CTA's histogram area, flushed above
 }
 
 // CUDA-core alternative: block per row i; W_ij = popc(row_i & row_j) for j > i with G_ij.

@@ -144,24 +144,47 @@ __device__ __forceinline__ void count_chunk(uint4 q, uint32_t a2, int& g, int& e
 // so a block with one or two such rows reads them in one round.  Rows
 // holding such edges are appended to the active list as (row, #gt, #eq), in
 // any order.
+// select_here (one problem whose histogram the SC^2 GEMM completed): every
+// block chooses the threshold itself from the histogram, staged in dynamic
+// shared memory while its row maxima load, and block 0 records it for the
+// later passes; otherwise it comes from the select launch.
 template <class VS>
-__global__ void __launch_bounds__(kCountThreads, 3) count_kernel(VS vs)
+__global__ void __launch_bounds__(kCountThreads, 3) count_kernel(VS vs, int select_here)
 {
     pdl_wait();
     pdl_release();
+    extern __shared__ __align__(16) uint32_t shist_stage[];   // select_here: n + 4 words
     __shared__ int srow[16], sc0[16], soff[17], sg[16], se[16];
+    __shared__ int ssel[40];
     int lb;
     const ProbView v = vs.get(ST_COUNT, blockIdx.x, lb);
     const int n = v.n;
-    if (v.ctl->n_sel == 0) return;
-    const int alpha = v.ctl->alpha;
     const int t = threadIdx.x;
+    // entry k = t (< 16): pair p = 8 lb + k / 2, side k % 2
+    const int p = lb * kCountPairs + (t >> 1);
+    const int row = (t & 1) ? n - 1 - p : p;
+    bool act = t < 16 && p < (n + 1) / 2 && !((t & 1) && row == p) && row + 1 < n;
+    const int rmax = (act && v.rowmax != nullptr) ? __ldg(v.rowmax + row) : 0;
+    int n_sel, alpha;
+    if (select_here) {
+        select_alpha(v, ssel, shist_stage, ssel + 33);
+        __syncthreads();
+        n_sel = ssel[34];
+        alpha = ssel[35];
+        if (lb == 0 && t == 0) {
+            v.ctl->n_edges = ssel[33];
+            v.ctl->n_sel = n_sel;
+            v.ctl->alpha = alpha;
+            v.ctl->c_gt = ssel[36];
+            v.ctl->m_ties = ssel[37];
+        }
+    } else {
+        n_sel = v.ctl->n_sel;
+        alpha = v.ctl->alpha;
+    }
+    if (n_sel == 0) return;                   // uniform over the block
     if (t < 32) {
-        // entry k = t (< 16): pair p = 8 lb + k / 2, side k % 2
-        const int p = lb * kCountPairs + (t >> 1);
-        const int row = (t & 1) ? n - 1 - p : p;
-        bool act = t < 16 && p < (n + 1) / 2 && !((t & 1) && row == p) && row + 1 < n;
-        if (act && v.rowmax != nullptr) act = __ldg(v.rowmax + row) >= alpha;
+        if (act && v.rowmax != nullptr) act = rmax >= alpha;
         const int c0 = (row + 1) >> 3;
         const int len = act ? ((n - 1) >> 3) - c0 + 1 : 0;
         int incl = len;
@@ -419,10 +442,12 @@ void launch_hist(const Batch& b, int total, int max_n, cudaStream_t s)
 
 void launch_select(const Batch& b, cudaStream_t s) { launch_pdl(select_kernel<ManyViews>, b.num, 1024, 0, s, ManyViews{b}); }
 
-void launch_count_emit(const Batch& b, const int32_t tot[kNumBatchStages], cudaStream_t s)
+void launch_count_emit(const Batch& b, const int32_t tot[kNumBatchStages], bool select_here, int max_n,
+                       cudaStream_t s)
 {
     const ManyViews vs{b};
-    launch_pdl(count_kernel<ManyViews>, tot[ST_COUNT], kCountThreads, 0, s, vs);
+    const size_t stage = select_here ? static_cast<size_t>((max_n + 4) / 4 * 4) * 4 : 0;
+    launch_pdl(count_kernel<ManyViews>, tot[ST_COUNT], kCountThreads, stage, s, vs, select_here ? 1 : 0);
     launch_pdl(emit_kernel<ManyViews>, tot[ST_EMIT], 256, 0, s, vs);
 }
 
@@ -432,7 +457,7 @@ void launch_topk_single(const ProbView& v, cudaStream_t s)
     const OneView vs{v};
     launch_hist_vs(vs, (v.n + kHistRowsPerBlock - 1) / kHistRowsPerBlock, v.n, s);
     launch_pdl(select_kernel<OneView>, 1, 1024, 0, s, vs);
-    launch_pdl(count_kernel<OneView>, count_blocks(v.n), kCountThreads, 0, s, vs);
+    launch_pdl(count_kernel<OneView>, count_blocks(v.n), kCountThreads, 0, s, vs, 0);
     launch_pdl(emit_kernel<OneView>, emit_blocks(v.n), 256, 0, s, vs);
     launch_pdl(rank_kernel<OneView>, (v.k1 + 31) / 32, 256, v.k1 * 8, s, vs);
 }

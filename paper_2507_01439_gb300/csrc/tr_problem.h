@@ -136,7 +136,10 @@ void launch_sc2_bitset(const Batch& b, int total, cudaStream_t s);
 void launch_hist(const Batch& b, int total, int max_n, cudaStream_t s);
 void launch_select(const Batch& b, cudaStream_t s);
 // count and emit passes of the selection (the clique search ranks the pivots)
-void launch_count_emit(const Batch& b, const int32_t tot[kNumBatchStages], cudaStream_t s);
+// select_here: the count blocks choose the threshold from the histogram the
+// SC^2 GEMM completed (one problem of at most max_n matches)
+void launch_count_emit(const Batch& b, const int32_t tot[kNumBatchStages], bool select_here, int max_n,
+                       cudaStream_t s);
 // The clique search also orders the pivots (each warp ranks its selected edge)
 void launch_pgs(const Batch& b, int total, int k2_max, int max_k1, cudaStream_t s);
 void launch_kabsch(const Batch& b, int total, cudaStream_t s);

@@ -38,13 +38,35 @@ __device__ __forceinline__ int block_incl_scan(int x, int* sbuf)
 // From the weight histogram: |E+|, n_sel = min(K1, |E+|), alpha = the K1-th
 // largest weight, c_gt = #{W > alpha}, m = n_sel - c_gt ties still needed.
 // Every thread of the block must call it.  stage: optional shared memory of
-// n + 1 words; the histogram is then copied there in one coalesced round and
-// both passes below read it from there.
-__device__ __forceinline__ void select_alpha(const ProbView& v, int* sbuf, uint32_t* stage = nullptr)
+// n + 4 words (16-byte aligned); the histogram is then copied there in one
+// coalesced round (16-byte loads when the histogram is 16-byte aligned) and
+// both passes below read it from there.  res: optional shared memory of five
+// words that receives (|E+|, n_sel, alpha, c_gt, m) instead of the problem's
+// control block; the caller synchronises the block before reading it.
+__device__ __forceinline__ void select_alpha(const ProbView& v, int* sbuf, uint32_t* stage = nullptr,
+                                             int* res = nullptr)
 {
     const int nb = v.n;                       // weights 1..n (W <= n - 2)
     const uint32_t* H = v.hist;
-    if (stage != nullptr) {
+    if (stage != nullptr && (reinterpret_cast<uintptr_t>(v.hist) & 15u) == 0u) {
+        const int nq = (nb + 4) >> 2;         // 16-byte words covering bins 0..n
+        const uint4* H4 = reinterpret_cast<const uint4*>(v.hist);
+        for (int q0 = threadIdx.x; q0 < nq; q0 += 8 * blockDim.x) {
+            uint4 h4[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int q = q0 + u * static_cast<int>(blockDim.x);
+                h4[u] = q < nq ? __ldcg(H4 + q) : make_uint4(0u, 0u, 0u, 0u);
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int q = q0 + u * static_cast<int>(blockDim.x);
+                if (q < nq) reinterpret_cast<uint4*>(stage)[q] = h4[u];
+            }
+        }
+        __syncthreads();
+        H = stage;
+    } else if (stage != nullptr) {
         for (int q0 = threadIdx.x + 1; q0 <= nb; q0 += 8 * blockDim.x) {
             uint32_t h8[8];
 #pragma unroll
@@ -80,13 +102,27 @@ __device__ __forceinline__ void select_alpha(const ProbView& v, int* sbuf, uint3
     __syncthreads();
     const int n_edges = sbuf[32];
     const int n_sel = n_edges < v.k1 ? n_edges : v.k1;
+    // result k of (n_edges, n_sel, alpha, c_gt, m_ties)
+    auto put = [&](int k, int val) {
+        if (res != nullptr) {
+            res[k] = val;
+            return;
+        }
+        switch (k) {
+            case 0: v.ctl->n_edges = val; break;
+            case 1: v.ctl->n_sel = val; break;
+            case 2: v.ctl->alpha = val; break;
+            case 3: v.ctl->c_gt = val; break;
+            default: v.ctl->m_ties = val; break;
+        }
+    };
     if (threadIdx.x == 0) {
-        v.ctl->n_edges = n_edges;
-        v.ctl->n_sel = n_sel;
+        put(0, n_edges);
+        put(1, n_sel);
         if (n_sel == 0) {
-            v.ctl->alpha = 0x7FFFFFFF;
-            v.ctl->c_gt = 0;
-            v.ctl->m_ties = 0;
+            put(2, 0x7FFFFFFF);
+            put(3, 0);
+            put(4, 0);
         }
     }
     if (n_sel == 0) return;
@@ -109,9 +145,9 @@ __device__ __forceinline__ void select_alpha(const ProbView& v, int* sbuf, uint3
                 if (done || q0 + q >= per || wv < 1) continue;
                 const int h = static_cast<int>(h8[q]);
                 if (run + h >= n_sel) {
-                    v.ctl->alpha = wv;
-                    v.ctl->c_gt = run;
-                    v.ctl->m_ties = n_sel - run;
+                    put(2, wv);
+                    put(3, run);
+                    put(4, n_sel - run);
                     done = true;
                 } else {
                     run += h;
