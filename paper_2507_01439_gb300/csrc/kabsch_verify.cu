@@ -89,21 +89,25 @@ __device__ __forceinline__ void verify_body(const ProbView& v, int lb, VerifySha
 {
     const int vppb = v.vppb;                            // matches per block, <= kVWarps * PW
     const int npb = (v.n + vppb - 1) / vppb;            // match blocks of this problem
-    const int nh = v.ctl->n_pivots * v.k2;
     const int h0 = (lb / npb) * kVHyp;
+    const int slot = h0 + threadIdx.x;
+    // this thread's hypothesis record, read in the same round as the pivot
+    // count (slots up to K1 K2 are inside the buffer; those past the count
+    // are ignored)
+    float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0, r3 = r0;
+    if (slot < v.k1 * v.k2) {
+        const float4* rt = reinterpret_cast<const float4*>(v.rt + (size_t)slot * 16);
+        r0 = __ldcg(rt); r1 = __ldcg(rt + 1); r2 = __ldcg(rt + 2); r3 = __ldcg(rt + 3);
+    }
+    const int nh = v.ctl->n_pivots * v.k2;   // through L1: every warp of every block reads it
     if (h0 >= nh) return;
     const int k0 = (lb % npb) * vppb;
     const int kn = min(vppb, v.n - k0);                 // matches of this block
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     {
-        const int slot = h0 + threadIdx.x;
-        float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0, r3 = r0;
         bool ok = false;
         uint32_t flags = 0u;
         if (slot < nh) {
-            const int h = slot;
-            const float4* rt = reinterpret_cast<const float4*>(v.rt + (size_t)h * 16);
-            r0 = rt[0]; r1 = rt[1]; r2 = rt[2]; r3 = rt[3];
             flags = __float_as_uint(r3.y);
             ok = (flags & 1u) != 0u;
             if (!ok) r2.y = r2.z = r2.w = __int_as_float(0x7fc00000);   // NaN t: never an inlier
@@ -186,7 +190,6 @@ __device__ __forceinline__ void verify_body(const ProbView& v, int lb, VerifySha
     }
     __syncthreads();
     const int t = threadIdx.x;
-    const int slot = h0 + t;
     if (slot >= nh) return;
     const int hh = slot;
     const int tot = sh.scnt[0][t] + sh.scnt[1][t] + sh.scnt[2][t] + sh.scnt[3][t];

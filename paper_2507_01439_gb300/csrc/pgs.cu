@@ -58,31 +58,56 @@ __global__ void __launch_bounds__(256, 2) pgs_kernel(ManyViews vs)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     // the selected edges (Eq. 4) in the order the selection wrote them; a
     // pivot's index is its rank: the number of larger keys (W << 32 | ~(i n + j)
-    // are unique, larger = heavier, then lower (i, j))
-    const int np = v.ctl->n_sel;
-    if (lb == 0 && threadIdx.x == 0) v.ctl->n_pivots = np;
-    for (int q = threadIdx.x; q < np; q += blockDim.x) skey[q] = __ldcg(v.cand + q);
-    __syncthreads();
+    // are unique, larger = heavier, then lower (i, j)).  All K1 key slots are
+    // staged in the same round of loads as the number of selected edges (the
+    // selection fills the first n_sel; the rest are ignored).
+    const int np = v.ctl->n_sel;   // through L1: every warp of every block reads it
+    const int kcap = v.k1;
     // warp w of block b takes selected edge w * blocks + b
-    const int c = warp * ((v.k1 + 7) / 8) + lb;
+    const int c = warp * ((kcap + 7) / 8) + lb;
+    const uint64_t mykey = c < kcap ? __ldcg(v.cand + c) : 0ull;
+    for (int q0 = threadIdx.x; q0 < kcap; q0 += 8 * static_cast<int>(blockDim.x)) {
+        uint64_t kk[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int q = q0 + u * static_cast<int>(blockDim.x);
+            kk[u] = q < kcap ? __ldcg(v.cand + q) : 0ull;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int q = q0 + u * static_cast<int>(blockDim.x);
+            if (q < kcap) skey[q] = kk[u];
+        }
+    }
+    if (lb == 0 && threadIdx.x == 0) v.ctl->n_pivots = np;
+    const uint32_t lin = 0xFFFFFFFFu - static_cast<uint32_t>(mykey & 0xFFFFFFFFull);
+    const int i = c < np ? static_cast<int>(lin / static_cast<uint32_t>(v.n)) : 0;
+    const int j = c < np ? static_cast<int>(lin % static_cast<uint32_t>(v.n)) : 0;
+    const int wij = static_cast<int>(mykey >> 32);
+    const bool undirected = v.graph_mode == TURBOREG_GRAPH_SC2;
+    const uint32_t* bi = v.bits + (size_t)i * v.ldb;
+    const uint32_t* bj = v.bits + (size_t)j * v.ldb;
+    // the first round of this pivot's bitset words, in flight across the
+    // block barrier and the rank count
+    const int zs = undirected ? 0 : j + 1;
+    const int w0 = zs >> 5;
+    uint32_t mw0[kWords];
+#pragma unroll
+    for (int t = 0; t < kWords; ++t) {
+        const int wd = w0 + lane + 32 * t;
+        mw0[t] = (c < np && wd < v.ldb) ? (__ldg(bi + wd) & __ldg(bj + wd)) : 0u;
+    }
+    __syncthreads();
     if (c >= np) return;
-    const uint64_t mykey = skey[c];
     int p = 0;
     for (int q = lane; q < np; q += 32) p += skey[q] > mykey ? 1 : 0;
 #pragma unroll
     for (int off = 16; off >= 1; off >>= 1) p += __shfl_xor_sync(0xffffffffu, p, off);
-    const uint32_t lin = 0xFFFFFFFFu - static_cast<uint32_t>(mykey & 0xFFFFFFFFull);
-    const int i = static_cast<int>(lin / static_cast<uint32_t>(v.n));
-    const int j = static_cast<int>(lin % static_cast<uint32_t>(v.n));
-    const int wij = static_cast<int>(mykey >> 32);
     if (lane == 0) v.piv[p] = make_int4(i, j, wij, 0);
     int* cand = scand[warp];
     const int k2 = K2C > 0 ? K2C : v.k2;
-    const uint32_t* bi = v.bits + (size_t)i * v.ldb;
-    const uint32_t* bj = v.bits + (size_t)j * v.ldb;
     const uint16_t* wi = v.w + (size_t)i * v.n_pad;
     const uint16_t* wj = v.w + (size_t)j * v.n_pad;
-    const bool undirected = v.graph_mode == TURBOREG_GRAPH_SC2;
 
     constexpr int L = K2C > 0 ? K2C : TURBOREG_K2_MAX;
     uint64_t top[L];
@@ -125,15 +150,13 @@ __global__ void __launch_bounds__(256, 2) pgs_kernel(ManyViews vs)
         }
     };
 
-    const int zs = undirected ? 0 : j + 1;
-    const int w0 = zs >> 5;
     int nlist = 0;
     for (int wb = w0; wb < v.ldb; wb += 32 * kWords) {
         uint32_t mw[kWords];
 #pragma unroll
         for (int t = 0; t < kWords; ++t) {
             const int wd = wb + lane + 32 * t;
-            mw[t] = wd < v.ldb ? (__ldg(bi + wd) & __ldg(bj + wd)) : 0u;
+            mw[t] = wb == w0 ? mw0[t] : wd < v.ldb ? (__ldg(bi + wd) & __ldg(bj + wd)) : 0u;
             if (wd == w0) mw[t] &= ~0u << (zs & 31);
         }
         // one prefix sum per round: lane l writes its candidates (all its words)

@@ -265,6 +265,9 @@ __global__ void __launch_bounds__(kCountThreads, 3) count_kernel(VS vs, int sele
 // a row with ties sums the tie counts of the active rows above it (its tie
 // prefix) and keeps tie ranks prefix + rank-in-row < m.  Thread t reads
 // chunks 4t .. 4t+3 of each 1024-chunk sweep (thread order = column order).
+// The block's first active row is read speculatively in the same round as
+// the counters, and the row's first sweep, its tie prefix and its slot
+// atomic go out together in the next.
 template <class VS>
 __global__ void __launch_bounds__(256) emit_kernel(VS vs)
 {
@@ -274,14 +277,30 @@ __global__ void __launch_bounds__(256) emit_kernel(VS vs)
     __shared__ int s_base;
     int lb;
     const ProbView v = vs.get(ST_EMIT, blockIdx.x, lb);
-    if (v.ctl->n_sel == 0) return;
+    // the counters through L1: every warp of every block reads them
+    const int n_sel = v.ctl->n_sel;
     const int nact = static_cast<int>(v.ctl->n_active);
+    const int m = v.ctl->m_ties, alpha = v.ctl->alpha;
+    const int4 ar0 = v.active[lb];                  // lb < n_pad: inside the list's capacity
+    if (n_sel == 0) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int m = v.ctl->m_ties, alpha = v.ctl->alpha, c_gt = v.ctl->c_gt;
     const int c1 = (v.n - 1) >> 3;
-    for (int a = lb; a < nact; a += emit_blocks(v.n)) {
-        const int4 ar = v.active[a];
+    const int eb = emit_blocks(v.n);
+    for (int a = lb; a < nact; a += eb) {
+        const int4 ar = a == lb ? ar0 : v.active[a];
         const int i = ar.x, ng = ar.y, ne = ar.z;
+        const uint16_t* wrow = v.w + (size_t)i * v.n_pad;
+        // first sweep of the row
+        const int cb0 = (i + 1) >> 3;
+        uint4 q[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int cc = cb0 + threadIdx.x * 4 + k;
+            q[k] = cc <= c1 ? *reinterpret_cast<const uint4*>(wrow + cc * 8) : make_uint4(0u, 0u, 0u, 0u);
+        }
+        // slots of the W > alpha edges
+        if (threadIdx.x == 0)
+            s_base = ng > 0 ? static_cast<int>(atomicAdd(&v.ctl->gt_slot, static_cast<uint32_t>(ng))) : 0;
         // tie prefix: ties in active rows above i
         int pe = 0;
         if (ne > 0) {
@@ -295,23 +314,22 @@ __global__ void __launch_bounds__(256) emit_kernel(VS vs)
             if (lane == 0) se[warp] = part;
             __syncthreads();
             for (int w8 = 0; w8 < 8; ++w8) pe += se[w8];
-            __syncthreads();
         }
+        __syncthreads();
         const bool want_eq = ne > 0 && pe < m;
         if (ng == 0 && !want_eq) continue;   // uniform over the block
-        if (threadIdx.x == 0) s_base = ng > 0 ? static_cast<int>(atomicAdd(&v.ctl->gt_slot, static_cast<uint32_t>(ng))) : 0;
-        __syncthreads();
         const int pg = s_base;
-        const uint16_t* wrow = v.w + (size_t)i * v.n_pad;
+        const int c_gt = v.ctl->c_gt;
         int base_g = pg, base_e = pe;
-        for (int cb = (i + 1) >> 3; cb <= c1; cb += blockDim.x * 4) {
+        for (int cb = cb0; cb <= c1; cb += blockDim.x * 4) {
             uint32_t gm = 0, em = 0;   // bit 8*k + e: chunk k, element e
             const int cfirst = cb + threadIdx.x * 4;
-            uint4 q[4];
+            if (cb != cb0) {
 #pragma unroll
-            for (int k = 0; k < 4; ++k)
-                q[k] = cfirst + k <= c1 ? *reinterpret_cast<const uint4*>(wrow + (cfirst + k) * 8)
-                                        : make_uint4(0u, 0u, 0u, 0u);
+                for (int k = 0; k < 4; ++k)
+                    q[k] = cfirst + k <= c1 ? *reinterpret_cast<const uint4*>(wrow + (cfirst + k) * 8)
+                                            : make_uint4(0u, 0u, 0u, 0u);
+            }
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 if ((q[k].x | q[k].y | q[k].z | q[k].w) == 0u) continue;
