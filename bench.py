@@ -16,7 +16,9 @@ value: registrations/s with inputs resident in device memory, through the
        outside the events; each step's result is copied to page-locked host
        memory inside its events.
 e2e:   the same metric through the C ABI with page-locked HOST inputs: the
-       H2D copies of x, y and the D2H copy of the result are inside the events.
+       transfer of x, y to the GPU (the first kernel reads the mapped
+       page-locked arrays in place over the CPU-GPU link) and the result's
+       write to page-locked host memory are inside the events.
 sync_call: the synchronous turboreg_register per call (host work, graph
        launch and the wait for the result included), for latency.
 roofline: the SC^2 GEMM's mean duration from CUDA events recorded inside the

@@ -604,15 +604,20 @@ bool needs_fallback(const turboreg_result& r, int32_t n, const turboreg_params* 
 
 enum PtrKind { kPtrDevice, kPtrPinned, kPtrPageable };
 
-PtrKind pointer_kind(const void* p)
+// mapped: for page-locked host memory mapped into the device's address space,
+// the address kernels read it at (else null)
+PtrKind pointer_kind(const void* p, const void** mapped = nullptr)
 {
+    if (mapped) *mapped = nullptr;
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return kPtrPageable;
     }
     if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return kPtrDevice;
-    return a.type == cudaMemoryTypeHost ? kPtrPinned : kPtrPageable;
+    if (a.type != cudaMemoryTypeHost) return kPtrPageable;
+    if (mapped) *mapped = a.devicePointer;
+    return kPtrPinned;
 }
 
 // Checks, input copies and the launch of one registration (graph replay or
@@ -625,18 +630,30 @@ int enqueue_single(turboreg_ctx* c, const float* src, const float* dst, int32_t 
     int rc = check_params(c, n, p);
     if (rc != TURBOREG_OK) return rc;
     TR_CHECK(cudaSetDevice(c->device));
-    const PtrKind ks = pointer_kind(src), kd = pointer_kind(dst);
+    const void *ms = nullptr, *md = nullptr;
+    const PtrKind ks = pointer_kind(src, &ms), kd = pointer_kind(dst, &md);
     if (async && (ks == kPtrPageable || kd == kPtrPageable)) return TURBOREG_ERR_INVALID_ARG;
     const size_t bytes = static_cast<size_t>(n) * 3 * sizeof(float);
+    // page-locked inputs mapped into the device's address space are read in
+    // place by the first kernel (over the CPU-GPU link, no copy-engine
+    // operation); other host inputs are copied to the workspace first
     if (ks != kPtrDevice) {
         if (!host_finite(src, static_cast<size_t>(n) * 3)) return TURBOREG_ERR_NONFINITE;
-        TR_CHECK(cudaMemcpyAsync(c->ws.in_src, src, bytes, cudaMemcpyHostToDevice, c->stream));
-        *s_in = c->ws.in_src;
+        if (ms != nullptr) {
+            *s_in = static_cast<const float*>(ms);
+        } else {
+            TR_CHECK(cudaMemcpyAsync(c->ws.in_src, src, bytes, cudaMemcpyHostToDevice, c->stream));
+            *s_in = c->ws.in_src;
+        }
     }
     if (kd != kPtrDevice) {
         if (!host_finite(dst, static_cast<size_t>(n) * 3)) return TURBOREG_ERR_NONFINITE;
-        TR_CHECK(cudaMemcpyAsync(c->ws.in_dst, dst, bytes, cudaMemcpyHostToDevice, c->stream));
-        *d_in = c->ws.in_dst;
+        if (md != nullptr) {
+            *d_in = static_cast<const float*>(md);
+        } else {
+            TR_CHECK(cudaMemcpyAsync(c->ws.in_dst, dst, bytes, cudaMemcpyHostToDevice, c->stream));
+            *d_in = c->ws.in_dst;
+        }
     }
     Plan pl;
     const int64_t off0 = 0;

@@ -43,6 +43,7 @@ constexpr int kThreads = 256;    // 8 warps x 16 rows; each lane 4 columns
 __global__ void __launch_bounds__(256) pack_kernel(ManyViews vs, const float* __restrict__ src_cat,
                                                    const float* __restrict__ dst_cat)
 {
+    pdl_release();   // the compatibility blocks may take their places (they wait for this grid)
     int lb;
     const ProbView v = vs.get(ST_PACK, blockIdx.x, lb);
     const float* src = src_cat + 3 * v.in_off;
