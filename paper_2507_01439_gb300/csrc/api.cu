@@ -101,6 +101,9 @@ struct turboreg_ctx {
     turboreg_result* host_res = nullptr;   // pinned [max_batch]
     float* mlp_wbf = nullptr;              // proposal model (BF16-rounded FP32 values), device
     bool has_model = false;
+    // the control blocks may hold nonzero counters or error bits (before the
+    // first registration, after an entry point that runs part of the path)
+    bool ctl_dirty = true;
     EncodeTiledFn encode = nullptr;
     cudaEvent_t ev[kNumStages + 1] = {};
     // the descriptor uploads read the page-locked staging (ws.h_views, h_pre,
@@ -415,7 +418,9 @@ int enqueue_plan(turboreg_ctx* c, const Plan& pl, const Batch& bt, const float* 
 #define TR_EV(k) \
     if (timed) TR_CHECK(cudaEventRecordWithFlags(c->ev[k], s, cudaEventRecordExternal))
     TR_EV(0);
-    TR_CHECK(cudaMemsetAsync(c->ws.ctl, 0, sizeof(Ctl) * pl.num, s));
+    // the control blocks start cleared: the finalize kernel of the previous
+    // registration resets the fields that must start at zero (run_plan clears
+    // them when another entry point may have left them set)
     launch_pack(bt, pl.tot[ST_PACK], dsrc, ddst, s);
     TR_EV(1);
     launch_compat(bt, pl.tot[ST_COMPAT], s);
@@ -498,11 +503,17 @@ std::vector<uint8_t> plan_key(turboreg_ctx* c, const Plan& pl)
 int run_plan(turboreg_ctx* c, const Plan& pl, bool no_graph, const float* dsrc, const float* ddst,
              turboreg_result* out)
 {
+    if (c->ctl_dirty)   // outside any capture: not part of the replayed graph
+        TR_CHECK(cudaMemsetAsync(c->ws.ctl, 0, sizeof(Ctl) * static_cast<size_t>(c->ws.slots), c->stream));
+    // clean again only once this registration, finalize included, is enqueued
+    c->ctl_dirty = true;
     if (no_graph) {
         Batch bt;
-        const int rc = upload_desc(c, pl.num, c->ws.desc, bt, c->stream);
+        int rc = upload_desc(c, pl.num, c->ws.desc, bt, c->stream);
         if (rc != TURBOREG_OK) return rc;
-        return enqueue_plan(c, pl, bt, dsrc, ddst, out);
+        rc = enqueue_plan(c, pl, bt, dsrc, ddst, out);
+        if (rc == TURBOREG_OK) c->ctl_dirty = false;
+        return rc;
     }
     const std::vector<uint8_t> key = plan_key(c, pl);
     turboreg_ctx::GraphSlot* g = nullptr;
@@ -576,6 +587,7 @@ int run_plan(turboreg_ctx* c, const Plan& pl, bool no_graph, const float* dsrc, 
     fp.extra = nullptr;
     TR_CHECK(cudaGraphExecKernelNodeSetParams(g->exec, g->fin_node, &fp));
     TR_CHECK(cudaGraphLaunch(g->exec, c->stream));
+    c->ctl_dirty = false;
     return TURBOREG_OK;
 }
 
@@ -1085,6 +1097,7 @@ int turboreg_score_transforms(turboreg_ctx* c, const float* src, const float* ds
         std::memcpy(&h[static_cast<size_t>(k) * 16], rt + static_cast<size_t>(k) * 12, 12 * sizeof(float));
         std::memcpy(&h[static_cast<size_t>(k) * 16 + 13], &valid, sizeof(valid));
     }
+    c->ctl_dirty = true;   // this entry point runs part of the path: no reset at its end
     TR_CHECK(cudaMemsetAsync(c->ws.ctl, 0, sizeof(Ctl), c->stream));
     launch_pack(bt, pl.tot[ST_PACK], s_in, d_in, c->stream);
     TR_CHECK(cudaMemcpyAsync(v.rt, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream));
@@ -1152,6 +1165,7 @@ int turboreg_kabsch_cliques(turboreg_ctx* c, const float* src, const float* dst,
     rc = upload_desc(c, 1, c->ws.desc, bt, c->stream);
     if (rc != TURBOREG_OK) return rc;
     const ProbView& v = c->ws.h_views[0];
+    c->ctl_dirty = true;   // this entry point runs part of the path: no reset at its end
     TR_CHECK(cudaMemsetAsync(c->ws.ctl, 0, sizeof(Ctl), c->stream));
     launch_pack(bt, pl.tot[ST_PACK], s_in, d_in, c->stream);
     if (k == 3) {
@@ -1222,6 +1236,7 @@ int turboreg_features(turboreg_ctx* c, const float* src, const float* dst, int32
     Batch bt;
     rc = upload_desc(c, 1, c->ws.desc, bt, c->stream);
     if (rc != TURBOREG_OK) return rc;
+    c->ctl_dirty = true;   // this entry point runs part of the path: no reset at its end
     TR_CHECK(cudaMemsetAsync(c->ws.ctl, 0, sizeof(Ctl), c->stream));
     launch_pack(bt, pl.tot[ST_PACK], s_in, d_in, c->stream);
     launch_compat(bt, pl.tot[ST_COMPAT], c->stream);

@@ -357,6 +357,13 @@ __global__ void __launch_bounds__(1024) finalize_kernel(ManyViews vs, turboreg_r
     // per problem of the launch), or the workspace's
     if (out != nullptr) out[blockIdx.x] = r;
     else *v.res = r;
+    // the next registration of this slot starts from cleared error bits and
+    // counters (every other control field is written before it is read; the
+    // pivot count stays readable for inspection)
+    v.ctl->err = 0u;
+    v.ctl->n_active = 0u;
+    v.ctl->gt_slot = 0u;
+    v.ctl->done_blocks = 0u;
 }
 
 }  // namespace
