@@ -424,8 +424,8 @@ constexpr int kPipeBytes2 = kStages2 * 2 * kABytes;   // 160 KB
 constexpr int kStageBytes2 = kEpiWarps * 2048;       // W staging: 32 x 32 uint16 per epilogue warp
 constexpr int kBase2 = kPipeBytes2 + kBarBytes + kStageBytes2 + 1024;   // before the shared histogram
 
-template <bool kSingle>
-__global__ void __launch_bounds__(kThreads, 1) sc2_pair_mma_kernel(Batch bt, int total)
+template <bool kHist>
+__global__ void __launch_bounds__(kThreads, 1) sc2_pair_mma_kernel(Batch bt, int total, int hist_bins)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -435,12 +435,13 @@ __global__ void __launch_bounds__(kThreads, 1) sc2_pair_mma_kernel(Batch bt, int
     uint64_t* empty = full + kStages2;
     uint64_t* tfull = empty + kStages2;      // [2] accumulator ready
     uint64_t* tempty = tfull + 2;            // [2] accumulator drained (leader's counts both CTAs)
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
+    uint64_t* hsync = tempty + 2;            // epilogue warps: a problem's bins complete / flushed
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 3);
     uint4* stg = reinterpret_cast<uint4*>(smem + kPipeBytes2 + kBarBytes);
     uint32_t* shist = reinterpret_cast<uint32_t*>(smem + kPipeBytes2 + kBarBytes + kStageBytes2);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nbins = kSingle ? bt.views[0].n + 1 : 0;
+    const int nbins = kHist ? hist_bins : 0;
     const uint32_t rank = cluster_ctarank();
     const bool leader = rank == 0;
 
@@ -453,9 +454,10 @@ __global__ void __launch_bounds__(kThreads, 1) sc2_pair_mma_kernel(Batch bt, int
             mbar_init(&tfull[b], 1);
             mbar_init(&tempty[b], 2 * kEpiWarps);
         }
+        mbar_init(hsync, kEpiWarps);
         fence_mbar_init();
     }
-    if (kSingle)
+    if (kHist)
         for (int b = threadIdx.x; b < nbins; b += blockDim.x) shist[b] = 0u;
     if (warp == 0) tmem_alloc_pair(tmem_slot, kTmemCols);
     tc_fence_before();
@@ -550,20 +552,52 @@ __global__ void __launch_bounds__(kThreads, 1) sc2_pair_mma_kernel(Batch bt, int
             const int buf = tc & 1;
             const uint32_t use = static_cast<uint32_t>(tc >> 1);
             const uint2 words = epi_words(v, bm, bn, quarter, part, lane);
+            // a batch: whether this CTA's next block belongs to another problem
+            bool flush_after = false;
+            if (kHist && u + us < nu) {
+                int ltn;
+                flush_after = locate(bt, ST_GEMM, 2 * (u + us) + static_cast<int>(rank), ltn) != p;
+            }
             const bool got = mbar_wait(&tfull[buf], use & 1u);
             if (!__all_sync(0xffffffffu, got)) { ok = false; break; }
             tc_fence_after();
-            sc2_epilogue_tile_staged<kSingle>(v, tmem + static_cast<uint32_t>(buf * kSc2BN), bm, bn, quarter, part,
-                                              lane, words, shist, stg + (warp - 2) * 128);
+            sc2_epilogue_tile_staged<kHist>(v, tmem + static_cast<uint32_t>(buf * kSc2BN), bm, bn, quarter, part,
+                                            lane, words, shist, stg + (warp - 2) * 128);
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive_cluster(tempty_l + static_cast<uint32_t>(buf * sizeof(uint64_t)));
+            if (flush_after) {
+                // the epilogue warps add this problem's bins to its global
+                // histogram and clear them (a rendezvous before and after)
+                const ProbView* vf = bt.views + p;
+                const int nf = vf->n;
+                uint32_t* hf = vf->hist;
+                if (lane == 0) mbar_arrive(hsync);
+                if (!__all_sync(0xffffffffu, mbar_wait(hsync, 0u))) { ok = false; break; }
+                for (int b = (warp - 2) * 32 + lane + 1; b <= nf; b += 32 * kEpiWarps) {
+                    const uint32_t h = shist[b];
+                    if (h) {
+                        atomicAdd(hf + b, h);
+                        shist[b] = 0u;
+                    }
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(hsync);
+                if (!__all_sync(0xffffffffu, mbar_wait(hsync, 1u))) { ok = false; break; }
+            }
         }
     }
     if (!ok && lane == 0) atomicOr(&bt.views[0].ctl->err, TR_ERR_TIMEOUT);
     tc_fence_before();
     __syncthreads();
-    if (kSingle && !leader) {
+    // the problem of this cluster's last block (both CTAs of a cluster take the
+    // same blocks): its bins are still in shared memory
+    int p_last = -1;
+    if (u0 < nu) {
+        int lt;
+        p_last = locate(bt, ST_GEMM, 2 * (u0 + ((nu - 1 - u0) / us) * us), lt);
+    }
+    if (kHist && !leader && p_last >= 0) {
         // the peer's histogram into the leader's (distributed shared memory), so
         // that one CTA per cluster adds to the global bins
         const uint32_t lead_hist = mapa_shared(shist, 0);
@@ -578,12 +612,12 @@ __global__ void __launch_bounds__(kThreads, 1) sc2_pair_mma_kernel(Batch bt, int
         tc_fence_after();
         tmem_dealloc_pair(tmem, kTmemCols);
     }
-    if (!kSingle || !leader) return;
+    if (!kHist || !leader || p_last < 0) return;
     // the cluster's histogram into the global one, from which the count pass
-    // chooses the pivot threshold
-    const ProbView v0 = bt.views[0];
-    for (int b = threadIdx.x + 1; b < nbins; b += blockDim.x)
-        if (shist[b]) atomicAdd(&v0.hist[b], shist[b]);
+    // (one problem) or the select launch (a batch) chooses the pivot threshold
+    const ProbView vl = bt.views[p_last];
+    for (int b = threadIdx.x + 1; b <= vl.n; b += blockDim.x)
+        if (shist[b]) atomicAdd(&vl.hist[b], shist[b]);
 }
 
 // CUDA-core alternative: block per row i; W_ij = popc(row_i & row_j) for j > i with G_ij.
@@ -630,8 +664,11 @@ __global__ void __launch_bounds__(256) sc2_bitset_kernel(ManyViews vs)
 int g_sc2_sms = 0;
 int g_sc2_pair_clusters = 0;   // co-resident 2-CTA clusters of the pair kernels (0: use single CTAs)
 
-template <bool kSingle>
-cudaError_t launch_pair(const Batch& b, int total_tiles, size_t smem, bool pair_mma, cudaStream_t s)
+// kHist: the blocks keep the edge-weight histogram in shared memory
+// (hist_bins bins; the pair-MMA form for any batch, the multicast form for
+// one problem)
+template <bool kHist>
+cudaError_t launch_pair(const Batch& b, int total_tiles, size_t smem, bool pair_mma, int hist_bins, cudaStream_t s)
 {
     int grid = 2 * g_sc2_pair_clusters;
     if (grid > total_tiles) grid = total_tiles;   // total_tiles is even
@@ -649,8 +686,8 @@ cudaError_t launch_pair(const Batch& b, int total_tiles, size_t smem, bool pair_
     attr[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 2;
-    if (pair_mma) return cudaLaunchKernelEx(&cfg, sc2_pair_mma_kernel<kSingle>, b, total_tiles);
-    return cudaLaunchKernelEx(&cfg, sc2_tcgen05_kernel<kSingle, true>, b, total_tiles);
+    if (pair_mma) return cudaLaunchKernelEx(&cfg, sc2_pair_mma_kernel<kHist>, b, total_tiles, hist_bins);
+    return cudaLaunchKernelEx(&cfg, sc2_tcgen05_kernel<kHist, true>, b, total_tiles);
 }
 
 }  // namespace
@@ -713,12 +750,13 @@ bool launch_sc2_tcgen05(const Batch& b, int total_tiles, int max_n, int mode, cu
     const int grid = total_tiles < sms ? total_tiles : sms;
     const size_t base = pair_mma ? static_cast<size_t>(kBase2) : static_cast<size_t>(kPipeBytes + kBarBytes + 1024);
     const size_t hist = static_cast<size_t>(max_n + 1) * 4;
-    const bool single = b.num == 1 && base + hist <= static_cast<size_t>(kSmemMax);
+    const bool fits = base + hist <= static_cast<size_t>(kSmemMax);
+    const bool single = b.num == 1 && fits;
     if (pair && g_sc2_pair_clusters > 0) {
-        if (single)
-            launch_pair<true>(b, total_tiles, base + hist, pair_mma, s);
+        if (pair_mma ? fits : single)
+            launch_pair<true>(b, total_tiles, base + hist, pair_mma, max_n + 1, s);
         else
-            launch_pair<false>(b, total_tiles, base, pair_mma, s);
+            launch_pair<false>(b, total_tiles, base, pair_mma, 0, s);
     } else if (single) {
         launch_pdl(sc2_tcgen05_kernel<true, false>, grid, kThreads, base + hist, s, b, total_tiles);
     } else {
