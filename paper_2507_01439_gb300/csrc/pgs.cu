@@ -43,8 +43,11 @@ constexpr int kListBytes = 8 * kCand * 4;   // the 8 warps' lists
 constexpr int kWords = 8;     // bitset words per lane per load round
 constexpr int kBatch = 8;     // list entries per lane per scoring round (16 weight loads in flight)
 
-template <int K2C>
-__global__ void __launch_bounds__(256, 2) pgs_kernel(ManyViews vs)
+// kDense: registers bounded for three blocks per SM (a batch: many waves of
+// blocks, latency hidden by occupancy); otherwise two, with more registers
+// per warp (one problem: a single wave)
+template <int K2C, bool kDense = false>
+__global__ void __launch_bounds__(256, kDense ? 3 : 2) pgs_kernel(ManyViews vs)
 {
     // dynamic shared memory: per-warp candidate lists, then the selected edge keys
     extern __shared__ __align__(16) uint8_t pgs_smem[];
@@ -287,7 +290,7 @@ cudaError_t pgs_setup()
     cudaError_t e = cudaSuccess;
     const void* fns[] = {reinterpret_cast<const void*>(pgs_kernel<0>), reinterpret_cast<const void*>(pgs_kernel<1>),
                          reinterpret_cast<const void*>(pgs_kernel<2>), reinterpret_cast<const void*>(pgs_kernel<3>),
-                         reinterpret_cast<const void*>(pgs_kernel<4>)};
+                         reinterpret_cast<const void*>(pgs_kernel<4>), reinterpret_cast<const void*>(pgs_kernel<2, true>)};
     for (const void* f : fns) {
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
@@ -306,7 +309,10 @@ void launch_pgs(const Batch& b, int total, int k2, int max_k1, cudaStream_t s)
     const size_t smem = kListBytes + static_cast<size_t>(max_k1) * sizeof(uint64_t);
     switch (k2) {
         case 1: launch_pdl(pgs_kernel<1>, total, 256, smem, s, vs); break;
-        case 2: launch_pdl(pgs_kernel<2>, total, 256, smem, s, vs); break;
+        case 2:
+            if (b.num > 1) launch_pdl(pgs_kernel<2, true>, total, 256, smem, s, vs);
+            else launch_pdl(pgs_kernel<2>, total, 256, smem, s, vs);
+            break;
         case 3: launch_pdl(pgs_kernel<3>, total, 256, smem, s, vs); break;
         case 4: launch_pdl(pgs_kernel<4>, total, 256, smem, s, vs); break;
         default: launch_pdl(pgs_kernel<0>, total, 256, smem, s, vs); break;
