@@ -233,7 +233,8 @@ __device__ __forceinline__ void sc2_epilogue_tile_staged(const ProbView& v, uint
 //   warp 1 lane 0   MMA issuer; accumulator buffer (tile count & 1)
 //   warps 2..17     epilogue of the previous tile while the next one runs
 // kSingle: one problem: the edge-weight histogram is kept in shared memory
-// and the last CTA to finish chooses the pivot threshold.
+// and added to the global one at the end (the count pass then chooses the
+// pivot threshold from it).
 // kPair: clusters of two CTAs take the two 128-row halves (tiles 2u, 2u + 1)
 // of one 256 x 256 output block, which share the B operand: each CTA loads
 // one 128-row half of B and multicasts it into both CTAs' shared memory, so

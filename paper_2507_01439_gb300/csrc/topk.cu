@@ -9,9 +9,11 @@
 // depend on the order in which blocks run:
 //   hist    histogram of edge weights (built by the SC^2 GEMM epilogue, or
 //           by hist_kernel for the CUDA-core SC^2 path and for callers)
-//   select  one block: alpha = K1-th largest weight, c_gt = #{W > alpha},
-//           m = K1' - c_gt ties still needed (K1' = min(K1, |E+|))
-//   count   warp per row pair (i, n-1-i): #{j : W_ij > alpha} and
+//   select  alpha = K1-th largest weight, c_gt = #{W > alpha}, m = K1' - c_gt
+//           ties still needed (K1' = min(K1, |E+|)): every count block for
+//           one problem whose histogram the GEMM completed, else one block
+//           per problem of the select launch
+//   count   blocks of eight row pairs (i, n-1-i): #{j : W_ij > alpha} and
 //           #{j : W_ij == alpha}; rows with such edges join the active list
 //           (rows whose largest weight, recorded by the SC^2 pass, is below
 //           alpha are skipped without reading W)

@@ -129,8 +129,9 @@ const void* pack_kernel_func();   // identifies the pack node inside a captured 
 void launch_compat(const Batch& b, int total, cudaStream_t s);
 // mode 0: independent CTAs; 1: 2-CTA clusters sharing the B operand by TMA
 // multicast; 2: 2-CTA clusters with pair MMAs (cta_group::2).  Returns true
-// when the GEMM itself chooses the pivot threshold (one problem whose weight
-// histogram fits in shared memory); otherwise the caller launches the select.
+// when the GEMM completed one problem's weight histogram from shared memory,
+// so that the count pass may choose the pivot threshold; otherwise the
+// caller launches the select.
 bool launch_sc2_tcgen05(const Batch& b, int total_tiles, int max_n, int mode, cudaStream_t s);
 void launch_sc2_bitset(const Batch& b, int total, cudaStream_t s);
 void launch_hist(const Batch& b, int total, int max_n, cudaStream_t s);

@@ -1,5 +1,5 @@
 // Threshold step of the exact top-K1 pivot selection (Eq. 4), shared by the
-// standalone select kernel and the last CTA of the SC^2 GEMM.
+// standalone select kernel and the count kernel's blocks.
 #pragma once
 
 #include "tr_common.cuh"
