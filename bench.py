@@ -59,7 +59,7 @@ LAUNCHES_PER_STEP = 8
 # DRAM bytes (read + write) of one SC^2 kernel launch on this workload, from one ncu
 # capture of the current kernel (profiles/sc2_pair_mma_indoor5000.txt); set to None when
 # the kernel changes, until it has been captured again
-SC2_DRAM_BYTES = 28734336
+SC2_DRAM_BYTES = 28775424
 
 
 def _peaks():
