@@ -14,8 +14,10 @@
  *  - Points are float32, row-major [N][3] (x, y, z of match i at 3*i).
  *  - Input pointers may be host or device memory; the kind is detected with
  *    cudaPointerGetAttributes.  Device pointers must be readable from the
- *    context's device and stay valid until the call returns.  Host inputs are
- *    copied to the device inside the call.
+ *    context's device and stay valid until the call returns.  Page-locked
+ *    host inputs mapped into the device's address space are read in place by
+ *    the first kernel (over the CPU-GPU link); other host inputs are copied to
+ *    the device inside the call.
  *  - The caller owns every input and output buffer.  The library never keeps
  *    a pointer to caller memory after a call returns.
  *  - Every call is synchronous with respect to the host: it enqueues its work
@@ -148,8 +150,9 @@ int turboreg_register(turboreg_ctx* ctx, const float* src, const float* dst, int
  * it, so that consecutive registrations run back to back on the GPU while
  * the host prepares the next ones (the paper has no counterpart: it is the
  * stream form of turboreg_register).  src, dst: device memory or page-locked
- * host memory (copied on the stream); out: device memory or page-locked host
- * memory, receiving the result by a copy on the stream.  Inputs and out must
+ * host memory (read in place by the first kernel when mapped, else copied on
+ * the stream); out: device memory or page-locked host memory, written by the
+ * last kernel.  Inputs and out must
  * stay valid and unchanged until turboreg_synchronize returns.  The learned
  * proposal is not accepted (its plain fallback needs the result on the host)
  * and stage times are not recorded.  Argument, size and host-side finiteness
