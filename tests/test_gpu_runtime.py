@@ -91,3 +91,22 @@ def test_histogram_at_shared_memory_limit():
     # 8576), so the GEMM keeps them in shared memory and the count blocks stage
     # all of them to choose the threshold
     _check_large(8500, 703, k1=1500, samples=300)
+
+
+def test_batched_many_small_problems_equal_plain():
+    # 64 problems of 50..400 matches: one or a few GEMM blocks each, so the
+    # GEMM's CTAs move between problems at almost every block and flush their
+    # shared-memory histograms each time
+    probs = synth.make_batch(64, seed=905, n_lo=50, n_hi=400)
+    c = trg.TurboReg(max_n=400, max_batch=64)
+    try:
+        params = [trg.default_params(p.tau, min(p.k1, 300), p.theta) for p in probs]
+        offs = np.cumsum([0] + [p.n for p in probs]).astype(np.int64)
+        out = c.register_batched(np.concatenate([p.x for p in probs]), np.concatenate([p.y for p in probs]),
+                                 offs, params)
+        for p, prm, rb in zip(probs, params, out):
+            rp = c.register(p.x, p.y, prm)
+            assert rb.n_pivots == rp.n_pivots, (p.n, p.shape)
+            _same(rb, rp)
+    finally:
+        c.close()
