@@ -521,13 +521,12 @@ def run_clique_stability(trg, per_tau=240):
 def run_sc2_paths(trg, probs, dx, dy):
     """SC^2 stage (with the edge-weight histogram and the pivot threshold) on
     the benchmark workload: the tcgen05 FP8 GEMM (2-CTA pair MMAs, the
-    default; clusters sharing B by multicast; independent CTAs) vs the
+    default; independent CTAs) vs the
     CUDA-core bitset AND + popcount path (same integers); in-graph CUDA-event
     times."""
     out = {}
     with trg.TurboReg(max_n=5000, max_batch=1) as ctx:
-        for name, fl in (("tcgen05_gemm", 0), ("tcgen05_gemm_multicast", trg.FLAG_SC2_MULTICAST),
-                         ("tcgen05_gemm_single_cta", trg.FLAG_SC2_SINGLE_CTA),
+        for name, fl in (("tcgen05_gemm", 0), ("tcgen05_gemm_single_cta", trg.FLAG_SC2_SINGLE_CTA),
                          ("bitset_popcount", trg.FLAG_SC2_BITSET)):
             prm = trg.default_params(0.1, 2000, 0.1, flags=trg.FLAG_STAGE_TIMES | fl)
             ms = []

@@ -81,8 +81,6 @@ typedef enum {
                                              2-CTA clusters compute 256 x 256 blocks with pair MMAs
                                              (cta_group::2), each CTA holding half of A and of B
                                              (same integers either way) */
-#define TURBOREG_FLAG_SC2_MULTICAST 0x40u  /* SC^2 GEMM on 2-CTA clusters that share the B tile by TMA
-                                              multicast, each CTA with its own 128 x 256 MMAs */
 #define TURBOREG_FLAG_VERIFY_PTS32 0x10u   /* verification tile of 128 hypotheses x 128 matches per block */
 #define TURBOREG_FLAG_VERIFY_PTS128 0x20u  /* ... x 512 matches per block (default: 256); tile shapes are
                                               chosen by the autotuner (same results either way); in a

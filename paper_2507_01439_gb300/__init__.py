@@ -32,7 +32,6 @@ FLAG_SC2_BITSET = 0x1
 FLAG_STAGE_TIMES = 0x2
 FLAG_NO_GRAPH = 0x4
 FLAG_SC2_SINGLE_CTA = 0x8
-FLAG_SC2_MULTICAST = 0x40
 FLAG_VERIFY_PTS32 = 0x10
 FLAG_VERIFY_PTS128 = 0x20
 

@@ -2,8 +2,8 @@
 
 It picks, by measurement on the device at hand:
 
-  tile shapes  the SC^2 GEMM form (2-CTA pair MMAs, clusters sharing the B
-               operand by multicast, or independent 128 x 256 CTAs) and the
+  tile shapes  the SC^2 GEMM form (2-CTA pair MMAs or independent
+               128 x 256 CTAs) and the
                verification tile (128 hypotheses x 128 / 256 / 512 matches per
                block); every candidate gives the same results, only the time
                differs;
@@ -26,14 +26,13 @@ from dataclasses import asdict, dataclass, field
 
 import numpy as np
 
-from . import (FLAG_SC2_MULTICAST, FLAG_SC2_SINGLE_CTA, FLAG_VERIFY_PTS32, FLAG_VERIFY_PTS128, TurboReg,
+from . import (FLAG_SC2_SINGLE_CTA, FLAG_VERIFY_PTS32, FLAG_VERIFY_PTS128, TurboReg,
                default_params)
 
 TILE_CANDIDATES = {
     "sc2_pair+verify256": 0,
     "sc2_pair+verify128": FLAG_VERIFY_PTS32,
     "sc2_pair+verify512": FLAG_VERIFY_PTS128,
-    "sc2_multicast+verify256": FLAG_SC2_MULTICAST,
     "sc2_single+verify256": FLAG_SC2_SINGLE_CTA,
     "sc2_single+verify512": FLAG_SC2_SINGLE_CTA | FLAG_VERIFY_PTS128,
 }

@@ -77,7 +77,7 @@ struct Plan {
     int32_t num = 0;
     int32_t max_n = 0, max_k1 = 0, k2_common = 0;
     int32_t bitset = 0, timed = 0, learned = 0;
-    int32_t gemm_form = 2;   // SC^2 GEMM: 0 independent CTAs, 1 multicast clusters, 2 pair MMAs
+    int32_t pair_mma = 1;    // SC^2 GEMM: 1 pair MMAs on 2-CTA clusters, 0 independent CTAs
     int32_t vpw = 64;        // verification tile: points per warp
     int32_t vcap = 0;        // balanced tile: verification launched with at most four blocks per SM
     int32_t tot[kNumBatchStages] = {};
@@ -354,7 +354,7 @@ int build_plan(turboreg_ctx* c, int32_t num, const int64_t* in_off, const int32_
     plan.bitset = (prm[0]->flags & TURBOREG_FLAG_SC2_BITSET) != 0;
     plan.timed = num == 1 && (prm[0]->flags & TURBOREG_FLAG_STAGE_TIMES) != 0;
     plan.learned = prm[0]->proposal == TURBOREG_PROPOSAL_LEARNED;
-    plan.gemm_form = (prm[0]->flags & TURBOREG_FLAG_SC2_SINGLE_CTA) ? 0 : (prm[0]->flags & TURBOREG_FLAG_SC2_MULTICAST) ? 1 : 2;
+    plan.pair_mma = (prm[0]->flags & TURBOREG_FLAG_SC2_SINGLE_CTA) ? 0 : 1;
     // verification tile: the flags' width for every problem, or for a single
     // problem without tile flags the balanced width (one even wave); the
     // kernel's points per warp (plan.vpw) is the narrowest that holds them all
@@ -434,7 +434,7 @@ int enqueue_plan(turboreg_ctx* c, const Plan& pl, const Batch& bt, const float* 
         // one problem whose histogram fits in the GEMM's shared memory: the
         // count blocks choose the threshold; a batch or a larger problem adds
         // a select launch
-        fused = launch_sc2_tcgen05(bt, pl.tot[ST_GEMM], pl.max_n, pl.gemm_form, s);
+        fused = launch_sc2_tcgen05(bt, pl.tot[ST_GEMM], pl.max_n, pl.pair_mma != 0, s);
         if (!fused && !pl.learned) launch_select(bt, s);
     }
     if (pl.learned) {

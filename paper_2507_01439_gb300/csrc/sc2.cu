@@ -235,16 +235,7 @@ __device__ __forceinline__ void sc2_epilogue_tile_staged(const ProbView& v, uint
 // kSingle: one problem: the edge-weight histogram is kept in shared memory
 // and added to the global one at the end (the count pass then chooses the
 // pivot threshold from it).
-// kPair: clusters of two CTAs take the two 128-row halves (tiles 2u, 2u + 1)
-// of one 256 x 256 output block, which share the B operand: each CTA loads
-// one 128-row half of B and multicasts it into both CTAs' shared memory, so
-// each CTA reads 32 KB per K stage from L2 instead of 48 KB.  A stage may be
-// refilled only when both CTAs' MMAs have read it: the MMA issuers commit to
-// the `empty` barriers of both CTAs (count 2), and before exit each producer
-// waits for the last releases so no arrival targets a finished CTA.  Every
-// problem's tile count nb(nb + 1) is even and its two halves are adjacent,
-// so pairs never straddle problems or column blocks.
-template <bool kSingle, bool kPair>
+template <bool kSingle>
 __global__ void __launch_bounds__(kThreads, 1) sc2_tcgen05_kernel(Batch bt, int total)
 {
     extern __shared__ uint8_t smem_raw[];
@@ -264,7 +255,7 @@ __global__ void __launch_bounds__(kThreads, 1) sc2_tcgen05_kernel(Batch bt, int 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], kPair ? 2 : 1);
+            mbar_init(&empty[s], 1);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&tfull[b], 1);
@@ -277,15 +268,12 @@ __global__ void __launch_bounds__(kThreads, 1) sc2_tcgen05_kernel(Batch bt, int 
     if (warp == 0) tmem_alloc(tmem_slot, kTmemCols);
     tc_fence_before();
     __syncthreads();
-    if (kPair) cluster_sync_all();   // the peer's barriers are initialised before any multicast
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
     bool ok = true;
-    // work units: single tiles, or tile pairs (2u, 2u + 1) of a cluster
-    const int rank = kPair ? static_cast<int>(cluster_ctarank()) : 0;
-    const int u0 = kPair ? static_cast<int>(blockIdx.x >> 1) : static_cast<int>(blockIdx.x);
-    const int us = kPair ? static_cast<int>(gridDim.x >> 1) : static_cast<int>(gridDim.x);
-    const int nu = kPair ? total >> 1 : total;
+    const int u0 = static_cast<int>(blockIdx.x);
+    const int us = static_cast<int>(gridDim.x);
+    const int nu = total;
     // the set-up above (barriers, tensor memory, shared histogram) overlaps the
     // previous stage; its outputs are read only from here on
     pdl_wait();
@@ -296,9 +284,8 @@ __global__ void __launch_bounds__(kThreads, 1) sc2_tcgen05_kernel(Batch bt, int 
             // ---------------- TMA producer ----------------
             int it = 0;
             for (int u = u0; u < nu && ok; u += us) {
-                const int t = kPair ? 2 * u + rank : u;
                 int lt;
-                const int p = locate(bt, ST_GEMM, t, lt);
+                const int p = locate(bt, ST_GEMM, u, lt);
                 const int KT = bt.views[p].n_pad / kSc2BK;
                 const CUtensorMap* mA = bt.maps + 2 * p;
                 const CUtensorMap* mB = mA + 1;
@@ -310,20 +297,7 @@ __global__ void __launch_bounds__(kThreads, 1) sc2_tcgen05_kernel(Batch bt, int 
                     if (!mbar_wait(&empty[s], ph ^ 1u)) { ok = false; break; }
                     mbar_arrive_expect_tx(&full[s], kABytes + kBBytes);
                     tma_load_2d(sA + s * kABytes, mA, kb * kSc2BK, bm * kSc2BM, &full[s]);
-                    if (kPair)   // this CTA's 128-row half of B, into both CTAs (A's map has 128-row boxes)
-                        tma_load_2d_mc(sB + s * kBBytes + rank * kABytes, mA, kb * kSc2BK,
-                                       bn * kSc2BN + rank * kSc2BM, &full[s], 0x3);
-                    else
-                        tma_load_2d(sB + s * kBBytes, mB, kb * kSc2BK, bn * kSc2BN, &full[s]);
-                }
-            }
-            if (kPair) {
-                // producer tail: wait for both MMAs' releases of the last uses of
-                // every stage, so no commit arrives after this CTA has exited
-                for (int q = 0; q < kStages; ++q, ++it) {
-                    const int s = it % kStages;
-                    const uint32_t ph = (it / kStages) & 1u;
-                    if (!mbar_wait(&empty[s], ph ^ 1u)) { ok = false; break; }
+                    tma_load_2d(sB + s * kBBytes, mB, kb * kSc2BK, bn * kSc2BN, &full[s]);
                 }
             }
         }
@@ -333,9 +307,8 @@ __global__ void __launch_bounds__(kThreads, 1) sc2_tcgen05_kernel(Batch bt, int 
             // ---------------- MMA issuer ----------------
             int it = 0, tc = 0;
             for (int u = u0; u < nu && ok; u += us, ++tc) {
-                const int t = kPair ? 2 * u + rank : u;
                 int lt;
-                const int p = locate(bt, ST_GEMM, t, lt);
+                const int p = locate(bt, ST_GEMM, u, lt);
                 const int KT = bt.views[p].n_pad / kSc2BK;
                 const int buf = tc & 1;
                 const uint32_t use = static_cast<uint32_t>(tc >> 1);
@@ -353,10 +326,7 @@ __global__ void __launch_bounds__(kThreads, 1) sc2_tcgen05_kernel(Batch bt, int 
                     for (int k = 0; k < kSc2BK / 32; ++k)   // K = 32 FP8 per MMA, 32-byte steps in the swizzle row
                         mma_f8f6f4(d, sdesc_k_sw128(a0 + k * 32), sdesc_k_sw128(b0 + k * 32), kIdesc,
                                    (kb | k) != 0 ? 1u : 0u);
-                    if (kPair)
-                        mma_commit_mc(&empty[s], 0x3);   // releases the stage in both CTAs
-                    else
-                        mma_commit(&empty[s]);
+                    mma_commit(&empty[s]);
                 }
                 if (!ok) break;
                 mma_commit(&tfull[buf]);
@@ -369,9 +339,8 @@ __global__ void __launch_bounds__(kThreads, 1) sc2_tcgen05_kernel(Batch bt, int 
         const int part = (warp - 2) >> 2;          // column part of the tile
         int tc = 0;
         for (int u = u0; u < nu; u += us, ++tc) {
-            const int t = kPair ? 2 * u + rank : u;
             int lt;
-            const int p = locate(bt, ST_GEMM, t, lt);
+            const int p = locate(bt, ST_GEMM, u, lt);
             const ProbView v = bt.views[p];
             int bm, bn;
             tile_of(lt, bm, bn);
@@ -391,7 +360,6 @@ __global__ void __launch_bounds__(kThreads, 1) sc2_tcgen05_kernel(Batch bt, int 
     if (!ok && lane == 0) atomicOr(&bt.views[0].ctl->err, TR_ERR_TIMEOUT);
     tc_fence_before();
     __syncthreads();
-    if (kPair) cluster_sync_all();   // neither CTA exits while the other may still signal it
     if (warp == 0) {
         tc_fence_after();
         tmem_dealloc(tmem, kTmemCols);
@@ -666,10 +634,9 @@ int g_sc2_sms = 0;
 int g_sc2_pair_clusters = 0;   // co-resident 2-CTA clusters of the pair kernels (0: use single CTAs)
 
 // kHist: the blocks keep the edge-weight histogram in shared memory
-// (hist_bins bins; the pair-MMA form for any batch, the multicast form for
-// one problem)
+// (hist_bins bins)
 template <bool kHist>
-cudaError_t launch_pair(const Batch& b, int total_tiles, size_t smem, bool pair_mma, int hist_bins, cudaStream_t s)
+cudaError_t launch_pair(const Batch& b, int total_tiles, size_t smem, int hist_bins, cudaStream_t s)
 {
     int grid = 2 * g_sc2_pair_clusters;
     if (grid > total_tiles) grid = total_tiles;   // total_tiles is even
@@ -687,8 +654,7 @@ cudaError_t launch_pair(const Batch& b, int total_tiles, size_t smem, bool pair_
     attr[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 2;
-    if (pair_mma) return cudaLaunchKernelEx(&cfg, sc2_pair_mma_kernel<kHist>, b, total_tiles, hist_bins);
-    return cudaLaunchKernelEx(&cfg, sc2_tcgen05_kernel<kHist, true>, b, total_tiles);
+    return cudaLaunchKernelEx(&cfg, sc2_pair_mma_kernel<kHist>, b, total_tiles, hist_bins);
 }
 
 }  // namespace
@@ -701,16 +667,10 @@ cudaError_t sc2_tcgen05_setup()
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g_sc2_sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(sc2_tcgen05_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(sc2_tcgen05_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  kSmemMax);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(sc2_tcgen05_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 kPipeBytes + kBarBytes + 1024);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(sc2_tcgen05_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 kSmemMax);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(sc2_tcgen05_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(sc2_tcgen05_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  kPipeBytes + kBarBytes + 1024);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(sc2_pair_mma_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax);
@@ -730,7 +690,7 @@ cudaError_t sc2_tcgen05_setup()
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         int nc = 0;
-        if (cudaOccupancyMaxActiveClusters(&nc, sc2_tcgen05_kernel<true, true>, &cfg) == cudaSuccess)
+        if (cudaOccupancyMaxActiveClusters(&nc, sc2_pair_mma_kernel<true>, &cfg) == cudaSuccess)
             g_sc2_pair_clusters = nc;
         else
             cudaGetLastError();   // no cluster support: the single-CTA kernel is used
@@ -743,25 +703,24 @@ cudaError_t sc2_tcgen05_setup()
 
 // A single problem keeps its histogram in shared memory when it fits; a
 // batch (or a very large problem) uses global atomics.
-bool launch_sc2_tcgen05(const Batch& b, int total_tiles, int max_n, int mode, cudaStream_t s)
+bool launch_sc2_tcgen05(const Batch& b, int total_tiles, int max_n, bool pair_mma, cudaStream_t s)
 {
-    const bool pair = mode != 0;
-    const bool pair_mma = mode == 2;
+    const bool pair = pair_mma && g_sc2_pair_clusters > 0;
     const int sms = g_sc2_sms > 0 ? g_sc2_sms : 148;
     const int grid = total_tiles < sms ? total_tiles : sms;
-    const size_t base = pair_mma ? static_cast<size_t>(kBase2) : static_cast<size_t>(kPipeBytes + kBarBytes + 1024);
+    const size_t base = pair ? static_cast<size_t>(kBase2) : static_cast<size_t>(kPipeBytes + kBarBytes + 1024);
     const size_t hist = static_cast<size_t>(max_n + 1) * 4;
     const bool fits = base + hist <= static_cast<size_t>(kSmemMax);
     const bool single = b.num == 1 && fits;
-    if (pair && g_sc2_pair_clusters > 0) {
-        if (pair_mma ? fits : single)
-            launch_pair<true>(b, total_tiles, base + hist, pair_mma, max_n + 1, s);
+    if (pair) {
+        if (fits)
+            launch_pair<true>(b, total_tiles, base + hist, max_n + 1, s);
         else
-            launch_pair<false>(b, total_tiles, base, pair_mma, 0, s);
+            launch_pair<false>(b, total_tiles, base, 0, s);
     } else if (single) {
-        launch_pdl(sc2_tcgen05_kernel<true, false>, grid, kThreads, base + hist, s, b, total_tiles);
+        launch_pdl(sc2_tcgen05_kernel<true>, grid, kThreads, base + hist, s, b, total_tiles);
     } else {
-        launch_pdl(sc2_tcgen05_kernel<false, false>, grid, kThreads, base, s, b, total_tiles);
+        launch_pdl(sc2_tcgen05_kernel<false>, grid, kThreads, base, s, b, total_tiles);
     }
     return single;
 }

@@ -142,7 +142,7 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
         : "memory");
 }
 
-// 2-D tiled tensor copy global -> shared (no multicast).  c0 = innermost coordinate.
+// 2-D tiled tensor copy global -> shared.  c0 = innermost coordinate.
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int32_t c0, int32_t c1,
                                             uint64_t* bar)
 {
@@ -150,18 +150,6 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
         "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
         "[%4];" ::"r"(smem_u32(dst)),
         "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(smem_u32(bar))
-        : "memory");
-}
-
-// The same copy delivered to every CTA of the cluster in `mask` (same CTA-relative
-// destination offset and mbarrier in each); the source tile is read from L2 once.
-__device__ __forceinline__ void tma_load_2d_mc(void* dst, const CUtensorMap* map, int32_t c0, int32_t c1,
-                                               uint64_t* bar, uint16_t mask)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster "
-        "[%0], [%1, {%2, %3}], [%4], %5;" ::"r"(smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(smem_u32(bar)), "h"(mask)
         : "memory");
 }
 
@@ -334,15 +322,6 @@ __device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t adesc, uint64_
         : "memory");
 }
 
-// Arrive once on the mbarrier at `bar`'s offset in every CTA of the cluster in
-// `mask` when all previously issued tcgen05.mma of this thread complete.
-__device__ __forceinline__ void mma_commit_mc(uint64_t* bar, uint16_t mask)
-{
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;"
-                 ::"r"(smem_u32(bar)), "h"(mask)
-                 : "memory");
-}
-
 // D[tmem] (+)= A * B^T over a CTA pair (cta_group::2): issued by one thread of
 // the leader CTA; A's M = 256 rows are this CTA's 128 and the peer's 128 at the
 // same shared-memory offset, B's N columns likewise, and each CTA's tensor
@@ -359,7 +338,9 @@ __device__ __forceinline__ void mma_f8f6f4_pair(uint32_t tmem_d, uint64_t adesc,
 }
 
 // Arrive on the mbarrier at `bar`'s offset in every CTA of `mask` when all
-// previously issued pair MMAs of this thread complete.
+// previously issued pair MMAs of this thread complete.  The `.multicast::cluster`
+// qualifier here selects which CTAs' mbarriers receive the arrival; it moves
+// no data (the library has no multicast load).
 __device__ __forceinline__ void mma_commit_pair_mc(uint64_t* bar, uint16_t mask)
 {
     asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;"

@@ -127,12 +127,11 @@ int32_t balanced_vppb(int32_t n, int32_t nh, int32_t num_sms);
 void launch_pack(const Batch& b, int total, const float* src, const float* dst, cudaStream_t s);
 const void* pack_kernel_func();   // identifies the pack node inside a captured graph
 void launch_compat(const Batch& b, int total, cudaStream_t s);
-// mode 0: independent CTAs; 1: 2-CTA clusters sharing the B operand by TMA
-// multicast; 2: 2-CTA clusters with pair MMAs (cta_group::2).  Returns true
-// when the GEMM completed one problem's weight histogram from shared memory,
-// so that the count pass may choose the pivot threshold; otherwise the
-// caller launches the select.
-bool launch_sc2_tcgen05(const Batch& b, int total_tiles, int max_n, int mode, cudaStream_t s);
+// pair_mma: 2-CTA clusters with pair MMAs (cta_group::2); otherwise
+// independent CTAs.  Returns true when the GEMM completed one problem's
+// weight histogram from shared memory, so that the count pass may choose the
+// pivot threshold; otherwise the caller launches the select.
+bool launch_sc2_tcgen05(const Batch& b, int total_tiles, int max_n, bool pair_mma, cudaStream_t s);
 void launch_sc2_bitset(const Batch& b, int total, cudaStream_t s);
 void launch_hist(const Batch& b, int total, int max_n, cudaStream_t s);
 void launch_select(const Batch& b, cudaStream_t s);

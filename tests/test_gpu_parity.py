@@ -92,23 +92,16 @@ def test_bitset_sc2_matches(ctx):
     _full_parity(ctx, p, k1=1500, flags=trg.FLAG_SC2_BITSET)
 
 
-@pytest.mark.parametrize("shape,n", [("indoor", 3000), ("cube", 777)])
+@pytest.mark.parametrize("shape,n", [("cube", 300), ("cube", 777), ("indoor", 3000), ("indoor", 5000)])
 def test_single_cta_sc2_matches(ctx, shape, n):
-    # the GEMM on independent CTAs (no clusters sharing B) gives the same integers
+    # the GEMM on independent CTAs (no 2-CTA pair MMAs) gives the same integers
     p = synth.make_problem(shape, n, 0.05, 17)
     _full_parity(ctx, p, k1=min(1500, 2 * n), flags=trg.FLAG_SC2_SINGLE_CTA)
 
 
-@pytest.mark.parametrize("shape,n", [("cube", 300), ("cube", 777), ("indoor", 3000), ("indoor", 5000)])
-def test_multicast_sc2_matches(ctx, shape, n):
-    # the GEMM on clusters sharing B by TMA multicast (128 x 256 MMAs per CTA) gives the same integers
-    p = synth.make_problem(shape, n, 0.05, 17)
-    _full_parity(ctx, p, k1=min(1500, 2 * n), flags=trg.FLAG_SC2_MULTICAST)
-
-
-@pytest.mark.parametrize("flags", [trg.FLAG_SC2_MULTICAST, trg.FLAG_SC2_SINGLE_CTA])
+@pytest.mark.parametrize("flags", [trg.FLAG_SC2_SINGLE_CTA])
 def test_sc2_forms_batched(ctx, flags):
-    # batched form (global histogram): the other GEMM forms equal the default (pair MMA) batched call
+    # batched form (global histogram): the other GEMM form equals the default (pair MMA) batched call
     probs = [synth.make_problem(s, n, r, 90 + b) for b, (s, n, r) in
              enumerate([("indoor", 1200, 0.1), ("outdoor", 900, 0.2), ("indoor", 3000, 0.05), ("cube", 257, 0.1)])]
     offs = np.cumsum([0] + [p.n for p in probs]).astype(np.int64)
@@ -122,7 +115,7 @@ def test_sc2_forms_batched(ctx, flags):
         assert np.array_equal(a.R, b.R) and np.array_equal(a.t, b.t) and a.inlier_count == b.inlier_count
 
 
-@pytest.mark.parametrize("flags", [0, trg.FLAG_SC2_MULTICAST, trg.FLAG_SC2_SINGLE_CTA])
+@pytest.mark.parametrize("flags", [0, trg.FLAG_SC2_SINGLE_CTA])
 def test_complete_graph_exactness(ctx, flags):
     # tau huge: G is complete, every SC^2 entry is N-2 (largest integer the FP8 GEMM accumulates)
     p = synth.make_problem("cube", 5000, 0.1, 12)
