@@ -17,9 +17,19 @@
 // different host threads) race on it.  Serialise calls per device.
 //
 // In host code the name g_pivot_scratch only stands in for the array; its
-// device address comes from cudaGetSymbolAddress, taken once per device with
-// that device current, on the first call made on that device.  That first
-// call should therefore be made before any stream capture begins.
+// device address comes from cudaGetSymbolAddress, taken with the device
+// current on the first call made on that device.  That first call should
+// therefore be made before any stream capture begins.  Every later call made
+// outside a stream capture looks the address up again and, if it changed (the
+// device was reset, or the host framework tore the context down and made a
+// new one), repeats the set-up, since the kernels' shared-memory attributes
+// went with the old context; a call made while its stream is being captured
+// uses the address recorded last, so the context must not be replaced between
+// the last uncaptured call and the end of a capture.
+//
+// A weight above n - 2 (no SC^2 count is larger) in the caller's matrix is
+// not counted: the call then selects nothing and writes -TURBOREG_ERR_INVALID_ARG
+// to *n_pivots_dev.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -52,18 +62,32 @@ std::mutex g_mu;
 uint8_t* g_dev_scratch[kMaxDevices] = {};
 bool g_dev_ready[kMaxDevices] = {};
 
-// Device address of the scratch array on `device` (current); set up on first use.
-int scratch_for(int device, uint8_t** out)
+// Device address of the scratch array on `device` (current); set up on first
+// use, and again when a call outside stream capture finds the address changed.
+int scratch_for(int device, cudaStream_t s, uint8_t** out)
 {
     if (device < 0 || device >= kMaxDevices) return TURBOREG_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_dev_ready[device]) {
+    bool recheck = !g_dev_ready[device];
+    if (!recheck) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+            cudaGetLastError();   // e.g. the legacy stream while another stream captures: keep the record
+            cs = cudaStreamCaptureStatusActive;
+        }
+        recheck = cs == cudaStreamCaptureStatusNone;
+    }
+    if (recheck) {
         void* p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_pivot_scratch);
         if (e != cudaSuccess || p == nullptr) {
             std::fprintf(stderr, "turboreg: cudaGetSymbolAddress of the pivot scratch failed: %s\n",
                          cudaGetErrorString(e));
             return TURBOREG_ERR_CUDA;
+        }
+        if (g_dev_ready[device] && g_dev_scratch[device] == static_cast<uint8_t*>(p)) {
+            *out = g_dev_scratch[device];
+            return TURBOREG_OK;
         }
         e = topk_setup();
         if (e != cudaSuccess) {
@@ -99,9 +123,9 @@ extern "C" int turboreg_select_pivots_noalloc(const uint16_t* w_dev, int32_t n, 
     int device = 0;
     if (cudaGetDevice(&device) != cudaSuccess) return TURBOREG_ERR_CUDA;
     uint8_t* scr = nullptr;
-    int rc = scratch_for(device, &scr);
-    if (rc != TURBOREG_OK) return rc;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    int rc = scratch_for(device, s, &scr);
+    if (rc != TURBOREG_OK) return rc;
 
     ProbView v = {};
     v.n = n;

@@ -70,7 +70,10 @@ __device__ __forceinline__ void for_row_chunks(const ProbView& v, int i, int lan
 }
 
 // Histogram of edge weights (used when SC^2 comes from the CUDA-core path or
-// from a caller): 64 rows per block, shared-memory bins when they fit.
+// from a caller): 64 rows per block, shared-memory bins when they fit.  A
+// caller's weight above n - 2 (no SC^2 count can be larger; the bins end at
+// n) is not counted: it sets TR_ERR_BAD_WEIGHT, and the select kernel then
+// selects nothing.
 template <class VS, bool kSmem>
 __global__ void __launch_bounds__(256) hist_kernel(VS vs)
 {
@@ -89,7 +92,9 @@ __global__ void __launch_bounds__(256) hist_kernel(VS vs)
         const int i = lb * kHistRowsPerBlock + warp * (kHistRowsPerBlock / 8) + r;
         if (i >= v.n) break;
         for_row_chunks(v, i, lane, [&](int, int w) {
-            if (w > 0) {
+            if (VS::kCallerWeights && w > v.n - 2) {
+                atomicOr(&v.ctl->err, TR_ERR_BAD_WEIGHT);
+            } else if (w > 0) {
                 if (kSmem) atomicAdd(&sh[w], 1u);
                 else atomicAdd(&v.hist[w], 1u);
             }
@@ -110,6 +115,18 @@ __global__ void __launch_bounds__(1024) select_kernel(VS vs)
     __shared__ int sbuf[33];
     int lb;
     const ProbView v = vs.get(ST_SELECT, blockIdx.x, lb);
+    if (VS::kCallerWeights && (v.ctl->err & TR_ERR_BAD_WEIGHT) != 0u) {
+        // out-of-range weights: select nothing, so that the count, emit and
+        // rank passes write no candidate (rank reports the error)
+        if (threadIdx.x == 0) {
+            v.ctl->n_edges = 0;
+            v.ctl->n_sel = 0;
+            v.ctl->alpha = 0x7FFFFFFF;
+            v.ctl->c_gt = 0;
+            v.ctl->m_ties = 0;
+        }
+        return;
+    }
     select_alpha(v, sbuf);
 }
 
@@ -396,7 +413,9 @@ __global__ void __launch_bounds__(256) rank_kernel(VS vs)
     const ProbView v = vs.get(ST_RANK, blockIdx.x, lb);
     const int n_sel = v.ctl->n_sel;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lb == 0 && threadIdx.x == 0) v.ctl->n_pivots = n_sel;
+    if (lb == 0 && threadIdx.x == 0)
+        v.ctl->n_pivots = (VS::kCallerWeights && (v.ctl->err & TR_ERR_BAD_WEIGHT) != 0u) ? -TURBOREG_ERR_INVALID_ARG
+                                                                                         : n_sel;
     if (lb * 32 >= n_sel) return;
     for (int q = threadIdx.x; q < n_sel; q += blockDim.x) sk[q] = v.cand[q];
     __syncthreads();
