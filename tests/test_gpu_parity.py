@@ -33,8 +33,12 @@ def _full_parity(ctx, p, k1, k2=2, flags=0, tau=None, theta=None):
     orc = oracle.register(p.x, p.y, tau, k1, theta, k2=k2)
     assert res.n_pivots == orc.n_pivots
     stats = check_hypotheses(ctx, p.x, p.y, theta, orc)
+    if p.shape in ("cube", "indoor"):
+        # room-scale coordinates: FP32 resolves the contract's 1e-5 m band, so no
+        # inlier decision may differ outside it
+        assert stats["outside_1e-5"] == 0, stats["mismatches"]
     assert res.n_valid == orc.n_valid
-    kind = check_final(res, ctx, orc)
+    kind = check_final(res, ctx, orc, p.x, p.y, theta)
     return res, orc, stats, kind
 
 

@@ -32,8 +32,10 @@ def _parity(ctx, p, k1, k2=2, graph_mode=0, scoring=0, flags=0):
     orc = oracle.register(p.x, p.y, p.tau, k1, p.theta, k2=k2, graph_mode=graph_mode, scoring=scoring)
     assert res.n_pivots == orc.n_pivots and res.n_valid == orc.n_valid
     stats = check_hypotheses(ctx, p.x, p.y, p.theta, orc)
+    if p.shape in ("cube", "indoor"):
+        assert stats["outside_1e-5"] == 0, stats["mismatches"]
     if scoring == 0:
-        kind = check_final(res, ctx, orc)
+        kind = check_final(res, ctx, orc, p.x, p.y, p.theta)
         if res.status == 0:
             assert res.score == float(res.inlier_count)
     else:
