@@ -37,6 +37,21 @@ typedef enum {
                                    2^-22 theta (MAE) or 2^-22 theta^2 (MSE); zero in SCORE_IN mode */
 } turboreg_buffer;
 
+/* Failure injection for tests (a turboreg_params flag; no counterpart in the
+ * paper).  Every compatibility-graph block of the registration skips the copy
+ * of its row points, so its bounded wait for that copy can only expire: after
+ * 20 ms (instead of the normal 2 s bound) the block records a timeout and
+ * leaves its tile of the graph empty, the later stages run on the empty graph,
+ * and the result's status is TURBOREG_ERR_TIMEOUT.  No device fault and no
+ * hang: the context stays usable and the next registration is unaffected. */
+#define TURBOREG_FLAG_DEBUG_STALL_COMPAT 0x10000u
+
+/* Allocation-failure injection for tests: when the environment variable
+ * TURBOREG_DEBUG_FAIL_ALLOC holds k >= 1, the k-th memory allocation made by
+ * turboreg_create (device, page-locked and plain host memory, counted per call
+ * and thread) fails; turboreg_create then frees what it had allocated and
+ * returns TURBOREG_ERR_OOM.  Unset or 0: no effect. */
+
 /* Shape of the most recent turboreg_register call: n, n_pad, |P| and the
  * number of hypotheses k2*|P|.  Any pointer may be NULL. */
 int turboreg_debug_shape(turboreg_ctx* ctx, int32_t* n, int32_t* n_pad, int32_t* n_pivots,
@@ -145,14 +160,18 @@ int turboreg_mlp_train_step(turboreg_mlp* t, const float* feat, const float* lab
  * the process exits; nothing is allocated or freed by this call.
  *
  *  w_dev       device, uint16 [n][ldw] row-major, 16-byte aligned; entry (i, j)
- *              for i < j < n is the O2Graph weight (an SC^2 count, 0..n-2; a
- *              larger value is outside the contract).  Entries with j <= i or
- *              j >= n are ignored.  ldw % 8 == 0 and ldw >= n rounded up to 8.
+ *              for i < j < n is the O2Graph weight (an SC^2 count, 0..n-2).
+ *              Entries with j <= i or j >= n are ignored.  ldw % 8 == 0 and
+ *              ldw >= n rounded up to 8.  If any entry (i < j < n) exceeds
+ *              n - 2, the call selects nothing and *n_pivots_dev receives
+ *              -TURBOREG_ERR_INVALID_ARG (the values are only seen on the GPU,
+ *              so the error arrives with the results, not as the return code).
  *  n           nodes, 1 .. TURBOREG_NOALLOC_MAX_N
  *  k1          pivots wanted, 1 .. TURBOREG_K1_MAX
  *  pivots_dev  device, int32 [k1][4] out: (i, j, weight, 0) in (weight desc,
  *              i asc, j asc) order; rows past *n_pivots_dev are untouched
- *  n_pivots_dev device, int32 out: min(k1, number of edges with weight > 0)
+ *  n_pivots_dev device, int32 out: min(k1, number of edges with weight > 0),
+ *              or -TURBOREG_ERR_INVALID_ARG for weights above n - 2
  *  cuda_stream cudaStream_t to run on (NULL = legacy default stream)
  *
  * Asynchronous on cuda_stream; results are ready when the stream reaches
@@ -161,7 +180,12 @@ int turboreg_mlp_train_step(turboreg_mlp* t, const float* feat, const float* lab
  * array, which keeps the last call's contents (the call clears what must
  * start at zero), so calls that overlap on the GPU race: serialise calls per
  * device.  The first call on a device looks up the array's device address
- * with that device current; make that first call before any stream capture. */
+ * with that device current; make that first call before any stream capture.
+ * Later calls outside a capture look the address up again and redo the
+ * set-up when it changed (a device reset, a context re-created by the host
+ * framework); a call under capture uses the address recorded last, so the
+ * context must not be replaced between the last uncaptured call and a
+ * captured one. */
 int turboreg_select_pivots_noalloc(const uint16_t* w_dev, int32_t n, int32_t ldw, int32_t k1,
                                    int32_t* pivots_dev, int32_t* n_pivots_dev, void* cuda_stream);
 

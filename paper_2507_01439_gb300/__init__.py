@@ -34,6 +34,7 @@ FLAG_NO_GRAPH = 0x4
 FLAG_SC2_SINGLE_CTA = 0x8
 FLAG_VERIFY_PTS32 = 0x10
 FLAG_VERIFY_PTS128 = 0x20
+FLAG_DEBUG_STALL_COMPAT = 0x10000   # test hook: every compat block's wait expires (TIMEOUT)
 
 (BUF_ADJ_BITS, BUF_ADJ_FP8, BUF_SC2, BUF_PIVOTS, BUF_CLIQUES, BUF_RT, BUF_INLIERS, BUF_ROWSCORE, BUF_DEGREE,
  BUF_FEATURES, BUF_PROB, BUF_SCORES) = range(1, 13)

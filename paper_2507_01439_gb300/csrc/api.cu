@@ -149,15 +149,25 @@ namespace {
         }                                                                                      \
     } while (0)
 
+// Failure injection for tests: with TURBOREG_DEBUG_FAIL_ALLOC=k in the
+// environment, the k-th allocation (1-based, counted per turboreg_create call
+// and thread) fails as if the device or host memory were exhausted.
+thread_local int t_alloc_seq = 0;
+thread_local int t_alloc_fail = 0;
+
+bool injected_alloc_failure() { return ++t_alloc_seq == t_alloc_fail; }
+
 template <typename T>
 cudaError_t dalloc(T** p, size_t count)
 {
+    if (injected_alloc_failure()) return cudaErrorMemoryAllocation;
     return cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T) + 256);
 }
 
 template <typename T>
 cudaError_t halloc(T** p, size_t count)
 {
+    if (injected_alloc_failure()) return cudaErrorMemoryAllocation;
     return cudaMallocHost(reinterpret_cast<void**>(p), count * sizeof(T) + 64);
 }
 
@@ -211,8 +221,9 @@ int alloc_ws(Workspace& ws, int32_t max_n, int32_t slots)
     if (e == cudaSuccess) e = halloc(&ws.h_pre, static_cast<size_t>(kNumBatchStages) * (S + 1));
     if (e == cudaSuccess) e = halloc(&ws.h_maps, 2 * S);
     if (e == cudaSuccess) {
-        ws.map_npad = static_cast<int32_t*>(std::calloc(S, sizeof(int32_t)));
-        ws.map_cache = static_cast<CUtensorMap*>(std::calloc(2 * S, sizeof(CUtensorMap)));
+        ws.map_npad = injected_alloc_failure() ? nullptr : static_cast<int32_t*>(std::calloc(S, sizeof(int32_t)));
+        ws.map_cache = injected_alloc_failure() ? nullptr
+                                                : static_cast<CUtensorMap*>(std::calloc(2 * S, sizeof(CUtensorMap)));
         if (!ws.map_npad || !ws.map_cache) e = cudaErrorMemoryAllocation;
     }
     if (e != cudaSuccess) {
@@ -284,6 +295,7 @@ ProbView make_view(turboreg_ctx* c, int slot, int64_t in_off, int32_t n, const t
     v.kappa_fp64 = p->kappa_fp64 > 0.f ? p->kappa_fp64 : 100.f;
     v.graph_mode = p->graph_mode;
     v.scoring = p->scoring;
+    v.dbg = (p->flags & TURBOREG_FLAG_DEBUG_STALL_COMPAT) ? TR_DBG_STALL_COMPAT : 0u;
     v.pts = ws.pts + s * 6 * np;
     v.pts8 = ws.pts8 + s * 8 * np;
     v.a8 = ws.a8 + s * n2;
@@ -494,6 +506,7 @@ std::vector<uint8_t> plan_key(turboreg_ctx* c, const Plan& pl)
         put(&v.kappa_fp64, sizeof(v.kappa_fp64));
         put(&v.graph_mode, sizeof(v.graph_mode));
         put(&v.scoring, sizeof(v.scoring));
+        put(&v.dbg, sizeof(v.dbg));
     }
     return k;
 }
@@ -731,7 +744,10 @@ int turboreg_create(int device, int32_t max_n, int32_t max_batch, void* cuda_str
         std::fprintf(stderr, "turboreg: device %d is not an sm_100-family GPU\n", device);
         return TURBOREG_ERR_CUDA;
     }
-    turboreg_ctx* c = new (std::nothrow) turboreg_ctx();
+    t_alloc_seq = 0;
+    const char* fail_env = std::getenv("TURBOREG_DEBUG_FAIL_ALLOC");
+    t_alloc_fail = fail_env ? std::atoi(fail_env) : 0;
+    turboreg_ctx* c = injected_alloc_failure() ? nullptr : new (std::nothrow) turboreg_ctx();
     if (!c) return TURBOREG_ERR_OOM;
     c->device = device;
     c->max_n = max_n;
@@ -741,7 +757,7 @@ int turboreg_create(int device, int32_t max_n, int32_t max_batch, void* cuda_str
         delete c;
         return rc;
     }
-    if (cudaMallocHost(reinterpret_cast<void**>(&c->host_res), sizeof(turboreg_result) * max_batch) != cudaSuccess) {
+    if (halloc(&c->host_res, static_cast<size_t>(max_batch)) != cudaSuccess) {
         free_ws(c->ws);
         delete c;
         return TURBOREG_ERR_OOM;

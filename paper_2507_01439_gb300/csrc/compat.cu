@@ -160,7 +160,10 @@ __global__ void __launch_bounds__(kThreads) compat_kernel(ManyViews vs)
         fence_mbar_init();
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    // failure injection (tests only): the row copy is never issued, so the
+    // wait below can only expire (after the short kStallWaitNs)
+    const bool stall = (v.dbg & TR_DBG_STALL_COMPAT) != 0u;
+    if (threadIdx.x == 0 && !stall) {
         mbar_arrive_expect_tx(&bar, kT * 32);
         bulk_g2s(&srow[0][0], v.pts8 + (size_t)i0 * 8, kT * 32, &bar);
     }
@@ -180,15 +183,15 @@ __global__ void __launch_bounds__(kThreads) compat_kernel(ManyViews vs)
     for (int pr = 0; pr < 2; ++pr)
 #pragma unroll
         for (int c = 0; c < 6; ++c) XJ[pr][c] = pk(xj[2 * pr][c], xj[2 * pr + 1][c]);
-    if (!mbar_wait(&bar, 0)) {
-        if (threadIdx.x == 0) atomicOr(&v.ctl->err, TR_ERR_TIMEOUT);
-        return;
-    }
+    // a wait that gave up (in any thread) leaves the tile empty: the later
+    // stages then see no edge here, and the registration reports the timeout
+    const bool got = __syncthreads_and(mbar_wait(&bar, 0, stall ? kStallWaitNs : kWaitNs)) != 0;
+    if (!got && threadIdx.x == 0) atomicOr(&v.ctl->err, TR_ERR_TIMEOUT);
     const float tau = v.tau;
     uint32_t cmask[4] = {0u, 0u, 0u, 0u};   // bit r: G(i0 + 16 warp + r, j_q)
     uint32_t wrow_bits[4] = {0u, 0u, 0u, 0u};
 #pragma unroll 2
-    for (int r = 0; r < 16; ++r) {
+    for (int r = 0; r < 16 && got; ++r) {
         const int rr = warp * 16 + r;
         const int i = i0 + rr;
         const float4 pa = srow[rr][0], pb = srow[rr][1];

@@ -17,8 +17,13 @@ namespace tr {
 constexpr uint32_t TR_ERR_NONFINITE = 1u;
 constexpr uint32_t TR_ERR_TIMEOUT = 2u;
 constexpr uint32_t TR_ERR_OVERFLOW = 4u;
+constexpr uint32_t TR_ERR_BAD_WEIGHT = 8u;   // a caller's weight outside 0..n-2 (allocation-free selection)
 
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s bound on any device wait
+// bound of the one wait that the failure-injection hook (ProbView::dbg) leaves
+// without an arrival, so that a test sees it expire quickly
+constexpr unsigned long long kStallWaitNs = 20000000ull;   // 20 ms
+constexpr uint32_t TR_DBG_STALL_COMPAT = 1u;
 
 // Scalars that flow between stages on the device (no host round trip).
 struct Ctl {
@@ -86,13 +91,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
 }
 
 // Bounded wait for the phase of parity `parity` to complete.  False on timeout.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, unsigned long long limit_ns = kWaitNs)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = globaltimer();
     while (true) {
         if (mbar_try_wait(bar, parity)) return true;
-        if (globaltimer() - t0 > kWaitNs) return false;
+        if (globaltimer() - t0 > limit_ns) return false;
     }
 }
 

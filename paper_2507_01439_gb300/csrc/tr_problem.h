@@ -26,6 +26,7 @@ struct ProbView {
     int32_t graph_mode;  // TURBOREG_GRAPH_O2 / _SC2: the graph the clique search runs on
     int32_t scoring;     // TURBOREG_SCORE_IN / _MAE / _MSE
     int32_t vppb;        // verification tile: matches per block (<= 4 x the kernel's points per warp)
+    uint32_t dbg;        // failure injection for tests (TR_DBG_*), 0 in normal use
     float* pts;          // [6][n_pad]
     float* pts8;         // [n_pad][8] = (x0, x1, x2, y0, y1, y2, 0, 0)
     uint8_t* a8;         // [n_pad][n_pad] FP8 E4M3 0/1 adjacency
@@ -96,8 +97,11 @@ __device__ __forceinline__ int pivot_weight(const ProbView& v, int i, int j, int
     return static_cast<int>(__fmul_rn(__fmul_rn(static_cast<float>(w), v.prob[i]), v.prob[j]));
 }
 
-// Where a kernel finds its problem: one problem passed by value ...
+// Where a kernel finds its problem: one problem passed by value (the
+// allocation-free selection on a caller's weight matrix, whose weights are
+// checked against the range 0..n-2 of an SC^2 count) ...
 struct OneView {
+    static constexpr bool kCallerWeights = true;
     ProbView v;
     __device__ __forceinline__ ProbView get(int, int b, int& local) const
     {
@@ -107,6 +111,7 @@ struct OneView {
 };
 // ... or a group of problems, located per block.
 struct ManyViews {
+    static constexpr bool kCallerWeights = false;   // weights come from the library's own SC^2 pass
     Batch bt;
     __device__ __forceinline__ ProbView get(int st, int b, int& local) const
     {

@@ -1,0 +1,181 @@
+"""Eq. 1 at the threshold: pairs whose |dX - dY| lies within a few units in
+the last place of tau, where the GPU's FP32 decision alone could flip a bit.
+
+The compatibility kernel decides in FP32 and re-decides in FP64 (the oracle's
+operation order) every pair whose FP32 |dX - dY| lies within its guard band
+of tau; random data puts only a few dozen pairs per problem there.  These
+inputs are built to sit on the threshold, at coordinates up to 35 m:
+
+  exact ties    difference vectors along a coordinate axis with dyadic
+                lengths, so dX - dY = +-tau exactly in FP64 (tau dyadic),
+                then moved by k = 1..8 units in the last place of one
+                coordinate of y_j (FP64 margins of exactly k ulp of it);
+  FP32 ties     random directions, y_j searched over 9^3 unit-in-the-last-
+                place moves of its coordinates for the candidate whose
+                FP64 margin |dX - dY| - tau is nearest a target in
+                {0, +-1e-9, ..., +-3e-5} m, which includes pairs whose FP32
+                evaluation lands within a few ulp of tau.
+
+The CPU tests check the construction (the margins are what they claim, and a
+plain FP32 evaluation misclassifies some pairs, so the set really tests the
+FP64 re-decision); the GPU test requires the library's adjacency to equal the
+oracle's FP64 evaluation bit for bit.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2507_01439_gb300 as trg
+
+F32 = np.float32
+F64 = np.float64
+
+
+def dist64(a, b):
+    """The oracle's FP64 operation order: ((dx*dx + dy*dy) + dz*dz), sqrt."""
+    d = a.astype(F64) - b.astype(F64)
+    s = d[..., 0] * d[..., 0]
+    s = s + d[..., 1] * d[..., 1]
+    s = s + d[..., 2] * d[..., 2]
+    return np.sqrt(s)
+
+
+def _fma32(a, b, c):
+    return (a.astype(F64) * b.astype(F64) + c.astype(F64)).astype(F32)
+
+
+def dist32(a, b):
+    """An FP32 evaluation in the kernel's order (mul, then two fused multiply-adds)."""
+    d = (a.astype(F32) - b.astype(F32)).astype(F32)
+    s = (d[..., 0] * d[..., 0]).astype(F32)
+    s = _fma32(d[..., 1], d[..., 1], s)
+    s = _fma32(d[..., 2], d[..., 2], s)
+    return np.sqrt(s).astype(F32)
+
+
+def exact_ties(tau, n_base, seed):
+    """Pairs (xi, xj, yi, yj) with |dX - dY| = tau exactly, and ulp moves of them."""
+    rng = np.random.default_rng(seed)
+    X, Y, margin = [], [], []
+    for b in range(n_base):
+        xi = np.round(rng.uniform(-35, 35, 3) * 4096) / 4096           # multiples of 2^-12: sums stay exact
+        yi = np.round(rng.uniform(-35, 35, 3) * 4096) / 4096
+        xi[2] = np.round(rng.uniform(-2, 3) * 4096) / 4096
+        yi[2] = np.round(rng.uniform(-2, 3) * 4096) / 4096
+        L = rng.integers(64, 64 * 35) / 64.0                           # 1 .. 35 m, dyadic (> tau)
+        ax, ay = rng.integers(0, 3, 2)
+        sx = -1.0 if xi[ax] > 0 else 1.0                               # towards the origin: |coords| <= 35
+        sy = -1.0 if yi[ay] > 0 else 1.0
+        sign = 1.0 if b % 2 == 0 else -1.0                             # dX - dY = +tau or -tau
+        xj = xi.copy()
+        xj[ax] += sx * L
+        yj = yi.copy()
+        yj[ay] += sy * (L - sign * tau)
+        xi, xj, yi, yj = (v.astype(F32) for v in (xi, xj, yi, yj))
+        assert dist64(xi, xj) - dist64(yi, yj) == sign * tau, "construction not exact"
+        for k in range(-8, 9):                                         # k ulp moves of y_j along its axis
+            yk = yj.copy()
+            for _ in range(abs(k)):
+                yk[ay] = np.nextafter(yk[ay], F32(np.inf) if k > 0 else F32(-np.inf))
+            X += [xi, xj]
+            Y += [yi, yk]
+            margin.append(abs(dist64(xi, xj) - dist64(yi, yk)) - tau)
+    return np.array(X, F32), np.array(Y, F32), np.array(margin)
+
+
+def searched_ties(tau, targets, per_target, seed, reach=4):
+    """Random directions; y_j chosen among ulp moves for an FP64 margin near each target."""
+    rng = np.random.default_rng(seed)
+    moves = np.stack(np.meshgrid(*[np.arange(-reach, reach + 1)] * 3, indexing="ij"), -1).reshape(-1, 3)
+    X, Y, margin = [], [], []
+    tau64 = F64(F32(tau))
+    for tgt in targets:
+        for _ in range(per_target):
+            lo = np.array([-35.0, -35.0, -2.0])
+            hi = np.array([35.0, 35.0, 3.0])
+            xi = rng.uniform(lo, hi).astype(F32)
+            xj = np.clip(xi + rng.normal(size=3) * rng.choice([0.3, 3.0, 20.0]), -35, 35).astype(F32)
+            yi = rng.uniform(lo, hi).astype(F32)
+            dX = dist64(xi, xj)
+            if dX <= tau64 + 1e-3:
+                continue
+            sgn = rng.choice([-1.0, 1.0])                              # dY = dX - tau or dX + tau
+            for _ in range(64):                                        # a direction that keeps y_j in the box
+                u = rng.normal(size=3)
+                u /= np.linalg.norm(u)
+                yj0 = (yi + u * (dX - sgn * (tau64 + tgt))).astype(F32)
+                if np.abs(yj0).max() < 34.9:
+                    break
+            else:
+                continue
+            cand = np.empty((moves.shape[0], 3), F32)
+            for c in range(3):
+                step = np.nextafter(yj0[c], F32(np.inf)) - yj0[c]
+                cand[:, c] = (yj0[c].astype(F64) + moves[:, c] * F64(step)).astype(F32)
+            m = np.abs(dX - dist64(yi[None, :], cand)) - tau64
+            best = int(np.argmin(np.abs(m - tgt)))
+            X += [xi, xj]
+            Y += [yi, cand[best]]
+            margin.append(m[best])
+    return np.array(X, F32), np.array(Y, F32), np.array(margin)
+
+
+TARGETS = [0.0, 1e-9, -1e-9, 1e-8, -1e-8, 1e-7, -1e-7, 1e-6, -1e-6, 3e-6, -3e-6, 1e-5, -1e-5, 3e-5, -3e-5]
+
+
+def tie_problem(kind, tau, seed):
+    if kind == "exact":
+        return exact_ties(tau, 70, seed)
+    return searched_ties(tau, TARGETS, 80, seed)
+
+
+def pair_decisions(X, Y, tau):
+    """(FP64 decision, plain FP32 decision) of each constructed pair (2m, 2m+1)."""
+    xi, xj, yi, yj = X[0::2], X[1::2], Y[0::2], Y[1::2]
+    d64 = np.abs(dist64(xi, xj) - dist64(yi, yj)) <= F64(F32(tau))
+    d32 = np.abs(dist32(xi, xj) - dist32(yi, yj)) <= F32(tau)
+    return d64, d32
+
+
+CASES = [("exact", 0.09375, 1), ("exact", 0.59375, 2), ("searched", 0.1, 3), ("searched", 0.6, 4)]
+
+
+@pytest.mark.parametrize("kind,tau,seed", CASES)
+def test_tie_construction_cpu(kind, tau, seed):
+    X, Y, margin = tie_problem(kind, tau, seed)
+    assert np.abs(X).max() <= 35.0 and np.abs(Y).max() <= 35.0
+    if kind == "exact":
+        # the unmoved pairs tie exactly; a k-ulp move changes the margin by k ulp of the coordinate
+        m = margin.reshape(-1, 17)
+        assert (m[:, 8] == 0).all()
+        assert (m[:, :8] != 0).all() and (m[:, 9:] != 0).all()
+        assert (np.abs(m[:, 9:]) < 1e-4).all()
+    else:
+        # every target is reached within a few micrometres; many pairs lie within 1e-8 m of tau
+        assert (np.abs(margin) < 6e-5).all()
+        assert (np.abs(margin) < 1e-8).sum() >= 50
+        assert (margin > 0).sum() > 100 and (margin <= 0).sum() > 100
+    d64, d32 = pair_decisions(X, Y, tau)
+    # both decisions occur, and the plain FP32 evaluation gets some pairs wrong
+    assert d64.sum() > 50 and (~d64).sum() > 50
+    assert (d64 != d32).sum() >= 5, "construction does not reach FP32's misclassification range"
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("kind,tau,seed", CASES)
+def test_compat_bit_exact_at_threshold(kind, tau, seed):
+    from paper_2507_01439_gb300 import build
+    build.build()
+    X, Y, _ = tie_problem(kind, tau, seed)
+    n = X.shape[0]
+    with trg.TurboReg(max_n=n) as ctx:
+        ctx.register(X, Y, trg.default_params(tau, 100, 0.1))
+        bits = ctx.buffer(trg.BUF_ADJ_BITS)
+    A = oracle.compat(X, Y, tau)
+    G = np.unpackbits(bits.view(np.uint8), axis=1, bitorder="little")[:n, :n]
+    bad = np.argwhere(G != A)
+    assert bad.size == 0, f"{len(bad)} adjacency bits differ, first {bad[:5].tolist()}"
+    # the constructed pairs themselves, explicitly
+    d64, _ = pair_decisions(X, Y, tau)
+    m = np.arange(n // 2)
+    assert np.array_equal(G[2 * m, 2 * m + 1].astype(bool), d64)
