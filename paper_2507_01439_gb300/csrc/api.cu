@@ -75,7 +75,7 @@ struct Workspace {
 // A plan: the problems of one call (in slots 0..num-1) and per-stage block totals.
 struct Plan {
     int32_t num = 0;
-    int32_t max_n = 0, max_k1 = 0, k2_common = 0;
+    int32_t max_n = 0, min_n = 0, max_k1 = 0, k2_common = 0;
     int32_t bitset = 0, timed = 0, learned = 0;
     int32_t pair_mma = 1;    // SC^2 GEMM: 1 pair MMAs on 2-CTA clusters, 0 independent CTAs
     int32_t vpw = 64;        // verification tile: points per warp
@@ -113,6 +113,7 @@ struct turboreg_ctx {
     bool desc_pending = false;
     float stage_ms[kNumStages] = {};
     int32_t last_n = 0, last_npad = 0, last_k1 = 0, last_k2 = 0;
+    bool last_fp8 = false;   // the last plan materialised the FP8 adjacency (tensor-core SC^2)
     bool have_times = false;
     // Captured pipelines.  Each slot owns a private copy of its descriptors in
     // device memory, so replays of different shapes never see each other's.
@@ -378,6 +379,7 @@ int build_plan(turboreg_ctx* c, int32_t num, const int64_t* in_off, const int32_
     for (int st = 0; st < kNumBatchStages; ++st) ws.h_pre[st * (num + 1)] = 0;
     for (int32_t b = 0; b < num; ++b) {
         ws.h_views[b] = make_view(c, b, in_off[b], n[b], prm[b]);
+        if (plan.bitset) ws.h_views[b].a8 = nullptr;   // the CUDA-core SC^2 reads the bitset only
         const int32_t vppb = (num == 1 && !vflag) ? balanced_vppb(n[b], prm[b]->k1 * prm[b]->k2, device_sms())
                                                   : 4 * vpw_flag;
         ws.h_views[b].vppb = vppb;
@@ -389,6 +391,7 @@ int build_plan(turboreg_ctx* c, int32_t num, const int64_t* in_off, const int32_
             ws.h_pre[st * (num + 1) + b + 1] = plan.tot[st];
         }
         if (n[b] > plan.max_n) plan.max_n = n[b];
+        if (b == 0 || n[b] < plan.min_n) plan.min_n = n[b];
         if (prm[b]->k1 > plan.max_k1) plan.max_k1 = prm[b]->k1;
         if (prm[b]->k2 != plan.k2_common) plan.k2_common = 0;
         if (!plan.bitset) {
@@ -397,6 +400,7 @@ int build_plan(turboreg_ctx* c, int32_t num, const int64_t* in_off, const int32_
         }
     }
     plan.vpw = vppb_max <= 4 * 32 ? 32 : vppb_max <= 4 * 64 ? 64 : 128;
+    c->last_fp8 = !plan.bitset;
     plan.vcap = num == 1 && !vflag;
     return TURBOREG_OK;
 }
@@ -439,9 +443,10 @@ int enqueue_plan(turboreg_ctx* c, const Plan& pl, const Batch& bt, const float* 
     TR_EV(2);
     bool fused = false;
     if (pl.bitset) {
-        launch_sc2_bitset(bt, pl.tot[ST_BITSET], s);
-        launch_hist(bt, pl.tot[ST_HIST], pl.max_n, s);
-        launch_select(bt, s);
+        // the histogram is complete in global memory at the end of the kernel;
+        // one problem: the count blocks choose the threshold from it
+        fused = launch_sc2_bitset(bt, pl.tot[ST_BITSET], pl.max_n, pl.min_n, s) && pl.num == 1;
+        if (!fused && !pl.learned) launch_select(bt, s);
     } else {
         // one problem whose histogram fits in the GEMM's shared memory: the
         // count blocks choose the threshold; a batch or a larger problem adds
@@ -791,6 +796,7 @@ int turboreg_create(int device, int32_t max_n, int32_t max_batch, void* cuda_str
     }
     c->encode = reinterpret_cast<EncodeTiledFn>(fn);
     cudaError_t se = sc2_tcgen05_setup();
+    if (se == cudaSuccess) se = sc2_bitset_setup();
     if (se == cudaSuccess) se = topk_setup();
     if (se == cudaSuccess) se = verify_pgs_setup();
     if (se == cudaSuccess) se = mlp_setup();
@@ -1011,7 +1017,11 @@ int64_t turboreg_debug_copy(turboreg_ctx* c, int which, void* dst, int64_t max_b
     size_t bytes = 0;
     switch (which) {
         case TURBOREG_BUF_ADJ_BITS: src = v.bits; bytes = np * np / 8; break;
-        case TURBOREG_BUF_ADJ_FP8: src = v.a8; bytes = np * np; break;
+        case TURBOREG_BUF_ADJ_FP8:
+            if (!c->last_fp8) return -TURBOREG_ERR_INVALID_ARG;   // not materialised by that plan
+            src = v.a8;
+            bytes = np * np;
+            break;
         case TURBOREG_BUF_SC2: src = v.w; bytes = np * np * 2; break;
         case TURBOREG_BUF_PIVOTS: src = v.piv; bytes = static_cast<size_t>(h.n_pivots) * 16; break;
         case TURBOREG_BUF_CLIQUES: src = v.cliques; bytes = nh * 16; break;

@@ -238,10 +238,12 @@ __global__ void __launch_bounds__(kThreads) compat_kernel(ManyViews vs)
         const int d = __popc(wrow_bits[0]) + __popc(wrow_bits[1]) + __popc(wrow_bits[2]) + __popc(wrow_bits[3]);
         if (d) atomicAdd(&v.deg[i], d);
     }
-    // FP8 rows, 128 contiguous bytes per row: pass k writes rows 4k .. 4k + 3 of
-    // the warp's 16, lane l the 16-byte segment l % 8 of row 4k + l / 8
+    // FP8 rows (only for the tensor-core SC^2), 128 contiguous bytes per row:
+    // pass k writes rows 4k .. 4k + 3 of the warp's 16, lane l the 16-byte
+    // segment l % 8 of row 4k + l / 8
+    const bool fp8 = v.a8 != nullptr;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < 4 && fp8; ++k) {
         const int r = 4 * k + (lane >> 3);
         const int seg = lane & 7;
         const uint32_t w0 = __shfl_sync(0xffffffffu, wrow_bits[0], r);
@@ -269,7 +271,7 @@ __global__ void __launch_bounds__(kThreads) compat_kernel(ManyViews vs)
     }
     // FP8 rows: pass k writes rows j0 + 32k .. +31, eight threads per 128-byte row
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < 4 && fp8; ++k) {
         const int c = 32 * k + (threadIdx.x >> 3);
         const int seg = threadIdx.x & 7;
         const uint32_t w = reinterpret_cast<const uint32_t*>(colpart[c])[seg >> 1];

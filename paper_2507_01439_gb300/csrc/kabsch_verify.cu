@@ -457,7 +457,7 @@ void stage_blocks(int32_t n, int32_t k1, int32_t k2, int32_t vppb, int32_t block
     blocks[ST_VERIFY] = ((nh + kVHyp - 1) / kVHyp) * ((n + vpts - 1) / vpts);
     blocks[ST_FINAL] = 1;
     blocks[ST_HIST] = (n + 63) / 64;
-    blocks[ST_BITSET] = n_pad;
+    blocks[ST_BITSET] = bitset_tiles(n_pad);
     blocks[ST_GEMM] = nb * (nb + 1);
     blocks[ST_FEAT] = 1;
     blocks[ST_MLP] = (n + 127) / 128;

@@ -19,8 +19,8 @@
 //                  bitset and i < j, store uint16 W, and add the row and
 //                  column sums into the SC^2 row scores.
 //
-// Alternative (TURBOREG_FLAG_SC2_BITSET): the same integers from the
-// adjacency bitset with AND + popcount on CUDA cores, one block per row.
+// Alternative (sc2_bitset.cu): the same integers from the adjacency bitset
+// with AND + popcount on CUDA cores, work only on the edges.
 #include "tr_common.cuh"
 #include "tr_problem.h"
 #include "tr_select.cuh"
@@ -589,47 +589,6 @@ __global__ void __launch_bounds__(kThreads, 1) sc2_pair_mma_kernel(Batch bt, int
         if (shist[b]) atomicAdd(&vl.hist[b], shist[b]);
 }
 
-// CUDA-core alternative: block per row i; W_ij = popc(row_i & row_j) for j > i with G_ij.
-__global__ void __launch_bounds__(256) sc2_bitset_kernel(ManyViews vs)
-{
-    pdl_wait();
-    pdl_release();
-    extern __shared__ uint32_t srow[];
-    int i;
-    const ProbView v = vs.get(ST_BITSET, blockIdx.x, i);
-    const uint32_t* bi = v.bits + (size_t)i * v.ldb;
-    for (int q = threadIdx.x; q < v.ldb; q += blockDim.x) srow[q] = bi[q];
-    __syncthreads();
-    uint16_t* wrow = v.w + (size_t)i * v.n_pad;
-    int rsum = 0, rmax = 0;
-    for (int j = threadIdx.x; j < v.n_pad; j += blockDim.x) {
-        int c = 0;
-        if (j > i && ((srow[j >> 5] >> (j & 31)) & 1u)) {
-            const uint4* bj = reinterpret_cast<const uint4*>(v.bits + (size_t)j * v.ldb);
-            const uint4* si = reinterpret_cast<const uint4*>(srow);
-            for (int q = 0; q < v.ldb / 4; ++q) {
-                const uint4 a = si[q], b = bj[q];
-                c += __popc(a.x & b.x) + __popc(a.y & b.y) + __popc(a.z & b.z) + __popc(a.w & b.w);
-            }
-            if (c) atomicAdd(&v.rowscore[j], c);
-        }
-        wrow[j] = static_cast<uint16_t>(c);
-        rsum += c;
-        rmax = max(rmax, c);
-    }
-    if (rmax != 0 && v.rowmax) atomicMax(&v.rowmax[i], rmax);
-    // block reduce of the row sum
-    __shared__ int red[32];
-    for (int off = 16; off >= 1; off >>= 1) rsum += __shfl_xor_sync(0xffffffffu, rsum, off);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = rsum;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int t = 0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-        if (t) atomicAdd(&v.rowscore[i], t);
-    }
-}
-
 int g_sc2_sms = 0;
 int g_sc2_pair_clusters = 0;   // co-resident 2-CTA clusters of the pair kernels (0: use single CTAs)
 
@@ -695,9 +654,6 @@ cudaError_t sc2_tcgen05_setup()
         else
             cudaGetLastError();   // no cluster support: the single-CTA kernel is used
     }
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(sc2_bitset_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 TURBOREG_MAX_N / 8);
     return e;
 }
 
@@ -725,9 +681,5 @@ bool launch_sc2_tcgen05(const Batch& b, int total_tiles, int max_n, bool pair_mm
     return single;
 }
 
-void launch_sc2_bitset(const Batch& b, int total, cudaStream_t s)
-{
-    launch_pdl(sc2_bitset_kernel, total, 256, TURBOREG_MAX_N / 8, s, ManyViews{b});
-}
 
 }  // namespace tr

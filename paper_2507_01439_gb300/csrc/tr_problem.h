@@ -137,7 +137,12 @@ void launch_compat(const Batch& b, int total, cudaStream_t s);
 // weight histogram from shared memory, so that the count pass may choose the
 // pivot threshold; otherwise the caller launches the select.
 bool launch_sc2_tcgen05(const Batch& b, int total_tiles, int max_n, bool pair_mma, cudaStream_t s);
-void launch_sc2_bitset(const Batch& b, int total, cudaStream_t s);
+// SC^2 by AND + popcount over the bitset (sc2_bitset.cu); total = the batch's
+// tiles (bitset_tiles per problem).  Returns true when every problem's
+// edge-weight histogram is complete in global memory at its end (always).
+bool launch_sc2_bitset(const Batch& b, int total_tiles, int max_n, int min_n, cudaStream_t s);
+int bitset_tiles(int n_pad);
+cudaError_t sc2_bitset_setup();
 void launch_hist(const Batch& b, int total, int max_n, cudaStream_t s);
 void launch_select(const Batch& b, cudaStream_t s);
 // count and emit passes of the selection (the clique search ranks the pivots)

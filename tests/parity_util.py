@@ -47,10 +47,14 @@ def check_graph_stages(ctx: trg.TurboReg, A, S, n):
     assert np.array_equal(Ag, A), f"adjacency mismatch at {np.argwhere(Ag != A)[:5]}"
     full = unpack_bits(bits, npad)
     assert not full[n:, :].any() and not full[:, n:].any(), "padding bits set"
-    a8 = ctx.buffer(trg.BUF_ADJ_FP8)
-    assert np.array_equal(a8[:n, :n] == 0x38, A.astype(bool))
-    assert not a8[n:, :].any() and not a8[:, n:].any()
-    assert set(np.unique(a8[:n, :n]).tolist()) <= {0, 0x38}
+    try:
+        a8 = ctx.buffer(trg.BUF_ADJ_FP8)      # only the tensor-core SC^2 path materialises it
+    except RuntimeError:
+        a8 = None
+    if a8 is not None:
+        assert np.array_equal(a8[:n, :n] == 0x38, A.astype(bool))
+        assert not a8[n:, :].any() and not a8[:, n:].any()
+        assert set(np.unique(a8[:n, :n]).tolist()) <= {0, 0x38}
     assert np.array_equal(ctx.buffer(trg.BUF_DEGREE), A.sum(1).astype(np.int32))
     W = ctx.buffer(trg.BUF_SC2)[:n, :n].astype(np.int32)
     iu = np.triu_indices(n, 1)

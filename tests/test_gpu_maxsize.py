@@ -29,9 +29,9 @@ def _w_oracle(G, i, j):
     return int(G[i, j]) * int(np.count_nonzero(G[i] & G[j]))
 
 
-def _check_large(n, seed, k1=2000, samples=400):
+def _check_large(n, seed, k1=2000, samples=400, flags=0):
     p = synth.make_problem("indoor", n, 0.05, seed)
-    prm = trg.default_params(p.tau, k1, p.theta)
+    prm = trg.default_params(p.tau, k1, p.theta, flags=flags)
     with trg.TurboReg(max_n=n) as ctx:
         res = ctx.register(p.x, p.y, prm)
         assert res.status == 0
@@ -88,11 +88,14 @@ def _check_large(n, seed, k1=2000, samples=400):
     assert abs(res.inlier_count - cnt) <= near
 
 
-def test_max_size_registration():
-    _check_large(trg.TURBOREG_MAX_N, 700)
+@pytest.mark.parametrize("flags", [0, trg.FLAG_SC2_BITSET])
+def test_max_size_registration(flags):
+    # the bitset path reads its row blocks from global memory at this size
+    _check_large(trg.TURBOREG_MAX_N, 700, flags=flags)
 
 
-def test_histogram_beyond_shared_memory():
+@pytest.mark.parametrize("flags", [0, trg.FLAG_SC2_BITSET])
+def test_histogram_beyond_shared_memory(flags):
     # one problem whose edge-weight histogram no longer fits in the GEMM's
     # shared memory: the threshold is chosen by the separate select launch
-    _check_large(9000, 701, k1=1500, samples=300)
+    _check_large(9000, 701, k1=1500, samples=300, flags=flags)
