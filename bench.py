@@ -212,11 +212,37 @@ def stage_rooflines(stage_log, peaks, kind):
     return out
 
 
-def cpu_baseline(budget_s=12.0, gpu_results=None):
+def count_mismatch_report(p, orc, gpu_in, gpu_rt):
+    """Per-hypothesis inlier-number differences between the GPU and the oracle
+    on one problem: for every hypothesis whose counts differ, the matches
+    decided the other way (identified by evaluating both transforms in FP64),
+    each with its oracle residual minus theta (m), and whether it lies within
+    the 1e-5 m band of the registration contract."""
+    import numpy as np
+    th = float(np.float32(p.theta))
+    x64, y64 = p.x.astype(np.float64), p.y.astype(np.float64)
+    out = []
+    nh = min(len(gpu_in), len(orc.in_counts))
+    for h in np.flatnonzero((gpu_in[:nh] != orc.in_counts[:nh]) & orc.hyp_valid[:nh]):
+        Ro, to = orc.rt[h, :9].reshape(3, 3), orc.rt[h, 9:12]
+        Rg, tg = gpu_rt[h, :9].astype(np.float64).reshape(3, 3), gpu_rt[h, 9:12].astype(np.float64)
+        ro = np.linalg.norm(x64 @ Ro.T + to - y64, axis=1)
+        rg = np.linalg.norm(x64 @ Rg.T + tg - y64, axis=1)
+        ks = np.flatnonzero((rg <= th) != (ro <= th))
+        out.append({"h": int(h), "in_gpu": int(gpu_in[h]), "in_oracle": int(orc.in_counts[h]),
+                    "matches": [{"k": int(k), "oracle_residual_minus_theta_m": float(ro[k] - th),
+                                 "within_1e-5": bool(abs(ro[k] - th) <= 1e-5)} for k in ks]})
+    return out
+
+
+def cpu_baseline(budget_s=12.0, gpu_results=None, gpu_hyps=None):
     """The oracle on one host thread over the benchmark's problems (seeds 0..7
     cycled) for about budget_s seconds.  With gpu_results (the GPU's results on
     the same eight problems) it also reports each result's error against the
-    oracle's: the Frobenius norm of the R difference and the t difference."""
+    oracle's: the Frobenius norm of the R difference and the t difference; with
+    gpu_hyps (each problem's per-hypothesis inlier numbers and R, t) every
+    hypothesis whose inlier number differs from the oracle's, with the
+    distance to theta of each match decided the other way."""
     import numpy as np
     import oracle
     oracle.build()
@@ -242,6 +268,16 @@ def cpu_baseline(budget_s=12.0, gpu_results=None):
                         "dt_m": float(np.linalg.norm(g.t.astype(np.float64) - o.t)),
                         "inliers_gpu": g.inlier_count, "inliers_oracle": o.inlier_count})
         out["per_result_error_vs_oracle"] = per
+    if gpu_hyps:
+        rep, nhyp, outside = [], 0, 0
+        for k, (o, (gin, grt)) in enumerate(zip(first, gpu_hyps)):
+            r = count_mismatch_report(probs[k], o, gin, grt)
+            nhyp += int(o.hyp_valid.sum())
+            outside += sum(1 for h in r for m in h["matches"] if not m["within_1e-5"])
+            rep.append({"problem_seed": k, "hypotheses_with_count_differences": r})
+        out["inlier_count_differences"] = {
+            "hypotheses_compared": nhyp, "matches_outside_1e-5_m": outside,
+            "per_problem": rep}
     return out
 
 
@@ -275,6 +311,8 @@ def run_batched(trg, torch, stream, steps, warmup, flush, ws=1, rank=0):
             out = ctx.register_batched(xs, ys, offs, params)
         ok = sum(int(r.status == 0 and synth.rotation_error_deg(p.R_gt, r.R) < p.re_deg
                      and synth.translation_error(p.t_gt, r.t) < p.te_m) for p, r in zip(probs, out))
+        # the C call on arguments marshalled once (a C caller's cost), not the list conversions
+        marsh = ctx.marshal_batched(offs, params)
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         torch.cuda.synchronize()
         if ws > 1:
@@ -283,7 +321,8 @@ def run_batched(trg, torch, stream, steps, warmup, flush, ws=1, rank=0):
             with torch.cuda.stream(stream):
                 flush.zero_()
                 ev[k][0].record(stream)
-            ctx.register_batched(xs, ys, offs, params)
+            if ctx.register_batched_raw(xs, ys, marsh) != trg.OK:
+                raise RuntimeError("batched registration failed")
             ev[k][1].record(stream)
         torch.cuda.synchronize()
         mean_ms = sum(a.elapsed_time(b) for a, b in ev) / steps
@@ -298,6 +337,16 @@ def run_batched(trg, torch, stream, steps, warmup, flush, ws=1, rank=0):
 
     try:
         default = timed([trg.default_params(p.tau, p.k1, p.theta) for p in probs])
+        # per-stage device times of the same batched call (CUDA events between the stages'
+        # launches inside the captured graph; a third pass, not part of the timed value)
+        prm_t = [trg.default_params(p.tau, p.k1, p.theta, flags=trg.FLAG_STAGE_TIMES) for p in probs]
+        st_runs = []
+        for _ in range(4):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            ctx.register_batched(xs, ys, offs, prm_t)
+            st_runs.append(ctx.stage_times())
+        stage_ms = {k: sum(r[k] for r in st_runs[1:]) / (len(st_runs) - 1) for k in st_runs[0]}
         calib = [autotune.Calib(p.x, p.y, p.R_gt, p.t_gt, p.tau, p.theta, p.re_deg, p.te_m)
                  for p in synth.make_batch(128, seed=40)]
         t0 = time.perf_counter()
@@ -314,7 +363,7 @@ def run_batched(trg, torch, stream, steps, warmup, flush, ws=1, rank=0):
             "mean_n": float(sum(p.n for p in allp) / len(allp)),
             "success": default["success"] + " (indoor RE<15deg TE<0.3m, outdoor RE<5deg TE<0.6m)",
             "default_k1": "2000 indoor-shaped, 1000 outdoor-shaped", "autotuned": tuned,
-            "gpu_launches_per_call": 9}
+            "stage_ms": stage_ms, "gpu_launches_per_call": 9}
 
 
 def run_learned(trg, torch, stream, flush, ks=(1, 2, 4, 8, 100, 250, 500, 1000)):
@@ -341,17 +390,31 @@ def run_learned(trg, torch, stream, flush, ks=(1, 2, 4, 8, 100, 250, 500, 1000))
                 ok = sum(int(r.status == 0 and synth.rotation_error_deg(p.R_gt, r.R) < 15
                              and synth.translation_error(p.t_gt, r.t) < 0.3) for p, r in zip(probs, out))
                 fb = sum(r.used_fallback for r in out)
+                marsh = ctx.marshal_batched(offs, prm)
                 ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(2)]
                 for a, b in ev:
                     with torch.cuda.stream(stream):
                         flush.zero_()
                         a.record(stream)
-                    ctx.register_batched(xs, ys, offs, prm)
+                    ctx.register_batched_raw(xs, ys, marsh)
                     b.record(stream)
                 torch.cuda.synchronize()
                 ms = sum(a.elapsed_time(b) for a, b in ev) / len(ev)
                 row[name] = {"success": ok / 256, "regs_per_s": 256 / (ms / 1e3), "fallbacks": fb}
             rows.append(row)
+        # where the learned proposal's time goes: per-stage device times of one batched
+        # call of each method at K1 = 100 (in-graph CUDA events between the stages)
+        stages = {}
+        for name, prop in (("plain", trg.PROPOSAL_PLAIN), ("learned", trg.PROPOSAL_LEARNED)):
+            prm = [trg.default_params(p.tau, 100, p.theta, proposal=prop, flags=trg.FLAG_STAGE_TIMES)
+                   for p in probs]
+            runs = []
+            for _ in range(3):
+                with torch.cuda.stream(stream):
+                    flush.zero_()
+                ctx.register_batched(xs, ys, offs, prm)
+                runs.append(ctx.stage_times())
+            stages[name] = {k: sum(r[k] for r in runs[1:]) / (len(runs) - 1) for k in runs[0]}
     finally:
         ctx.close()
     full = max(r["plain"]["success"] for r in rows)
@@ -361,7 +424,8 @@ def run_learned(trg, torch, stream, flush, ks=(1, 2, 4, 8, 100, 250, 500, 1000))
                 return r["k1"]
         return None
     return {"workload": "256 indoor problems, N=5000, inlier ratio U[1%,5%]", "k_sweep": rows,
-            "k1_reaching_best_plain_success": {"plain": smallest("plain"), "learned": smallest("learned")}}
+            "k1_reaching_best_plain_success": {"plain": smallest("plain"), "learned": smallest("learned")},
+            "stage_ms_at_k1_100": stages}
 
 
 def _batched_success(probs, out):
@@ -406,12 +470,13 @@ def run_ablation(trg, torch, stream, flush):
             prm = [trg.default_params(c["tau"], c["k1"], p.theta, k2=c["k2"], graph_mode=gm) for p in probs]
             out = ctx.register_batched(xs, ys, offs, prm)
             ok, re_m, te_m = _batched_success(probs, out)
+            marsh = ctx.marshal_batched(offs, prm)
             ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(2)]
             for a_, b_ in ev:
                 with torch.cuda.stream(stream):
                     flush.zero_()
                     a_.record(stream)
-                ctx.register_batched(xs, ys, offs, prm)
+                ctx.register_batched_raw(xs, ys, marsh)
                 b_.record(stream)
             torch.cuda.synchronize()
             ms = sum(a_.elapsed_time(b_) for a_, b_ in ev) / len(ev)
@@ -685,7 +750,12 @@ def run_ours(args):
     line["stage_rooflines"] = stage_rooflines(stage_log, peaks, kind)
     line["paper_context"] = PAPER_CONTEXT
     if ws == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(gpu_results=first_results)
+        # the GPU's per-hypothesis inlier numbers and transforms of the eight problems
+        hyps = []
+        for k in range(len(probs)):
+            ctx.register(dx[k], dy[k], prm)
+            hyps.append((ctx.buffer(trg.BUF_INLIERS).copy(), ctx.buffer(trg.BUF_RT).copy()))
+        line["cpu_baseline"] = cpu_baseline(gpu_results=first_results, gpu_hyps=hyps)
     print(json.dumps(line), flush=True)
 
 

@@ -62,8 +62,12 @@ int turboreg_debug_shape(turboreg_ctx* ctx, int32_t* n, int32_t* n_pad, int32_t*
 int64_t turboreg_debug_copy(turboreg_ctx* ctx, int which, void* dst, int64_t max_bytes);
 
 /* Per-stage device times (ms) of the most recent call made with
- * TURBOREG_FLAG_STAGE_TIMES: pack, compat, sc2, topk, pgs, kabsch, verify,
- * finalize.  Writes up to `max` floats; returns the number of stages. */
+ * TURBOREG_FLAG_STAGE_TIMES (a single registration or a batch): pack, compat,
+ * sc2, proposal (the threshold's select launch when the SC^2 stage did not
+ * choose it, and the learned proposal's features, network, weight histogram
+ * and select), topk (count and emit), pgs (with the pivot ranks and the
+ * cliques' Kabsch), verify, finalize.  Writes up to `max` floats; returns the
+ * number of stages. */
 int turboreg_stage_times(turboreg_ctx* ctx, float* ms, int32_t max);
 
 /* Names of the stages reported by turboreg_stage_times. */

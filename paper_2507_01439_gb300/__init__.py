@@ -296,6 +296,26 @@ class TurboReg:
             raise RuntimeError(f"turboreg_register_batched failed: {status_string(rc)}")
         return [Result.from_c(out[b]) for b in range(num)]
 
+    def marshal_batched(self, offsets, params):
+        """Pre-built arguments of register_batched_raw: (offsets int64 array,
+        ctypes params array, its count, ctypes result array)."""
+        offs = np.ascontiguousarray(offsets, dtype=np.int64)
+        num = offs.shape[0] - 1
+        if isinstance(params, turboreg_params):
+            parr, pc = (turboreg_params * 1)(params), 1
+        else:
+            parr, pc = (turboreg_params * len(params))(*params), len(params)
+        return offs, parr, pc, (turboreg_result * num)()
+
+    def register_batched_raw(self, src_cat, dst_cat, marshalled) -> int:
+        """turboreg_register_batched on arguments prepared once by
+        marshal_batched (no per-call conversion); returns the status code,
+        results in marshalled[3]."""
+        offs, parr, pc, out = marshalled
+        return self._lib.turboreg_register_batched(self.handle, _ptr(src_cat), _ptr(dst_cat),
+                                                   ctypes.c_void_p(offs.ctypes.data), offs.shape[0] - 1,
+                                                   parr, pc, out)
+
     # ---- inspection (internal header) ----
     def shape(self):
         n, npad, npiv, nh = (ctypes.c_int32() for _ in range(4))

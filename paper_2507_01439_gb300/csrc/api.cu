@@ -29,7 +29,9 @@ using namespace tr;
 namespace {
 
 constexpr int kNumStages = 8;
-const char* kStageNames[kNumStages] = {"pack", "compat", "sc2", "topk", "pgs", "kabsch", "verify", "finalize"};
+// "proposal": the threshold's select launch when the SC^2 stage did not fuse
+// it, and the learned proposal's features, network, histogram and select
+const char* kStageNames[kNumStages] = {"pack", "compat", "sc2", "proposal", "topk", "pgs", "verify", "finalize"};
 constexpr int kGraphSlots = 8;
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -365,7 +367,7 @@ int build_plan(turboreg_ctx* c, int32_t num, const int64_t* in_off, const int32_
     plan = Plan();
     plan.num = num;
     plan.bitset = (prm[0]->flags & TURBOREG_FLAG_SC2_BITSET) != 0;
-    plan.timed = num == 1 && (prm[0]->flags & TURBOREG_FLAG_STAGE_TIMES) != 0;
+    plan.timed = (prm[0]->flags & TURBOREG_FLAG_STAGE_TIMES) != 0;
     plan.learned = prm[0]->proposal == TURBOREG_PROPOSAL_LEARNED;
     plan.pair_mma = (prm[0]->flags & TURBOREG_FLAG_SC2_SINGLE_CTA) ? 0 : 1;
     // verification tile: the flags' width for every problem, or for a single
@@ -446,14 +448,14 @@ int enqueue_plan(turboreg_ctx* c, const Plan& pl, const Batch& bt, const float* 
         // the histogram is complete in global memory at the end of the kernel;
         // one problem: the count blocks choose the threshold from it
         fused = launch_sc2_bitset(bt, pl.tot[ST_BITSET], pl.max_n, pl.min_n, s) && pl.num == 1;
-        if (!fused && !pl.learned) launch_select(bt, s);
     } else {
         // one problem whose histogram fits in the GEMM's shared memory: the
         // count blocks choose the threshold; a batch or a larger problem adds
         // a select launch
         fused = launch_sc2_tcgen05(bt, pl.tot[ST_GEMM], pl.max_n, pl.pair_mma != 0, s);
-        if (!fused && !pl.learned) launch_select(bt, s);
     }
+    TR_EV(3);
+    if (!fused && !pl.learned) launch_select(bt, s);
     if (pl.learned) {
         // learned proposal: features -> MLP -> histogram of floor(W p_i p_j) -> threshold
         TR_CHECK(cudaMemsetAsync(c->ws.hist, 0, sizeof(uint32_t) * (c->ws.np + 1) * pl.num, s));
@@ -462,7 +464,7 @@ int enqueue_plan(turboreg_ctx* c, const Plan& pl, const Batch& bt, const float* 
         launch_hist(bt, pl.tot[ST_HIST], pl.max_n, s);
         launch_select(bt, s);
     }
-    TR_EV(3);
+    TR_EV(4);
     // the count blocks stage the histogram in (at most 48 KB of) shared memory
     bool sel_in_count = fused && !pl.learned;
     if (sel_in_count && static_cast<size_t>(pl.max_n + 4) * 4 > 48 * 1024) {
@@ -470,9 +472,8 @@ int enqueue_plan(turboreg_ctx* c, const Plan& pl, const Batch& bt, const float* 
         sel_in_count = false;
     }
     launch_count_emit(bt, pl.tot, sel_in_count, pl.max_n, s);
-    TR_EV(4);
-    launch_pgs(bt, pl.tot[ST_PGS], pl.k2_common, pl.max_k1, s);   // also ranks the pivots and solves the cliques' Kabsch
     TR_EV(5);
+    launch_pgs(bt, pl.tot[ST_PGS], pl.k2_common, pl.max_k1, s);   // also ranks the pivots and solves the cliques' Kabsch
     TR_EV(6);
     launch_verify(bt, pl.tot[ST_VERIFY], pl.vpw, pl.vcap != 0, s);
     TR_EV(7);
@@ -934,14 +935,18 @@ int turboreg_register_batched(turboreg_ctx* c, const float* src_cat, const float
         pp.push_back(p);
     }
     const int32_t m = static_cast<int32_t>(nn.size());
+    bool timed = false;
     if (m > 0) {
         Plan pl;
         int rc = build_plan(c, m, off.data(), nn.data(), pp.data(), pl);
         if (rc == TURBOREG_OK)
             rc = run_plan(c, pl, (mode & TURBOREG_FLAG_NO_GRAPH) != 0, s_in, d_in, c->host_res);
         if (rc != TURBOREG_OK) return rc;
+        timed = pl.timed != 0;
     }
     TR_CHECK(cudaStreamSynchronize(c->stream));
+    c->have_times = timed;   // stage times of the batch's pipeline (the fallback's are not kept)
+    if (timed) collect_times(c);
     int32_t q = 0;
     std::vector<int32_t> fb;   // problems the plain proposal must decide (learned fallback)
     for (int32_t b = 0; b < num; ++b) {
@@ -981,7 +986,6 @@ int turboreg_register_batched(turboreg_ctx* c, const float* src_cat, const float
         c->last_npad = round_up(nn[0], kSc2BN);
         c->last_k1 = pp[0]->k1;
         c->last_k2 = pp[0]->k2;
-        c->have_times = false;
     }
     return TURBOREG_OK;
 }

@@ -231,7 +231,7 @@ def test_stage_times_reported(ctx):
     prm = trg.default_params(p.tau, 2000, p.theta, flags=trg.FLAG_STAGE_TIMES)
     ctx.register(p.x, p.y, prm)
     st = ctx.stage_times()
-    assert list(st) == ["pack", "compat", "sc2", "topk", "pgs", "kabsch", "verify", "finalize"]
+    assert list(st) == ["pack", "compat", "sc2", "proposal", "topk", "pgs", "verify", "finalize"]
     assert all(v >= 0 for v in st.values())
     print(st)
 
