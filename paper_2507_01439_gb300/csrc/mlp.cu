@@ -60,12 +60,12 @@ struct FwdOut {
     __nv_bfloat16* h3;         // [m][64]
 };
 
-__device__ void mlp_forward_tile(const float* __restrict__ feat, int m, int row0, const float* __restrict__ wbf,
-                                 FwdOut out, uint8_t* smem, uint32_t* err)
+// Set-up of a forward CTA: the weights into shared memory (B operands in the
+// swizzled layout), the mbarrier and 256 tensor-memory columns; returns the
+// tensor-memory address.  All threads of the CTA call it.
+__device__ uint32_t mlp_setup_cta(const float* __restrict__ wbf, uint8_t* smem)
 {
-    uint8_t* sH1 = smem + kOffH1;
     uint8_t* sW2 = smem + kOffW2;
-    uint8_t* sH2 = smem + kOffH2;
     uint8_t* sW3 = smem + kOffW3;
     float* sW1 = reinterpret_cast<float*>(smem + kOffSmall);
     float* sb1 = sW1 + 512;
@@ -106,7 +106,27 @@ __device__ void mlp_forward_tile(const float* __restrict__ feat, int m, int row0
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    const uint32_t tmem = *tslot;
+    return *tslot;
+}
+
+// One tile of 128 rows (row0 ..) after mlp_setup_cta: completes two phases of
+// the CTA's mbarrier (parities 0 then 1), so tiles can follow one another.
+// Returns this thread's probability (0 for rows past m).
+__device__ float mlp_tile(const float* __restrict__ feat, int m, int row0, FwdOut out, uint8_t* smem, uint32_t tmem,
+                          uint32_t* err)
+{
+    uint8_t* sH1 = smem + kOffH1;
+    uint8_t* sW2 = smem + kOffW2;
+    uint8_t* sH2 = smem + kOffH2;
+    uint8_t* sW3 = smem + kOffW3;
+    float* sW1 = reinterpret_cast<float*>(smem + kOffSmall);
+    float* sb1 = sW1 + 512;
+    float* sb2 = sb1 + 64;
+    float* sb3 = sb2 + 128;
+    float* sW4 = sb3 + 64;
+    float* sb4 = sW4 + 64;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kOffBar);
+    const int t = threadIdx.x, warp = t >> 5;
 
     // layer 1 on CUDA cores: row = t
     const int row = row0 + t;
@@ -212,16 +232,32 @@ __device__ void mlp_forward_tile(const float* __restrict__ feat, int m, int row0
                                    pack_bf16(hv[8 * c4 + 4], hv[8 * c4 + 5]), pack_bf16(hv[8 * c4 + 6], hv[8 * c4 + 7]));
         }
     }
+    float pr = 0.f;
     if (row < m) {
+        pr = 1.f / (1.f + __expf(-z4));
         if (out.z4) out.z4[row] = z4;
-        if (out.prob) out.prob[row] = 1.f / (1.f + __expf(-z4));
+        if (out.prob) out.prob[row] = pr;
     }
+    // the tile's tensor-memory reads are complete before the next tile's MMAs
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) {
+    return pr;
+}
+
+__device__ void mlp_teardown_cta(uint32_t tmem)
+{
+    if ((threadIdx.x >> 5) == 0) {
         tc_fence_after();
         tmem_dealloc(tmem, 256);
     }
+}
+
+__device__ void mlp_forward_tile(const float* __restrict__ feat, int m, int row0, const float* __restrict__ wbf,
+                                 FwdOut out, uint8_t* smem, uint32_t* err)
+{
+    const uint32_t tmem = mlp_setup_cta(wbf, smem);
+    mlp_tile(feat, m, row0, out, smem, tmem, err);
+    mlp_teardown_cta(tmem);
 }
 
 __device__ __forceinline__ uint8_t* aligned_smem(uint8_t* raw)
@@ -237,16 +273,28 @@ __global__ void __launch_bounds__(kRows, 1) mlp_fwd_kernel(const float* feat, in
     mlp_forward_tile(feat, m, blockIdx.x * kRows, wbf, out, aligned_smem(smem_raw), err);
 }
 
-// Registration path: per problem, rows of its feature buffer -> its prob buffer.
-__global__ void __launch_bounds__(kRows, 1) mlp_proposal_kernel(ManyViews vs, const float* wbf)
+// Registration path: persistent CTAs (weights, mbarrier and tensor memory set
+// up once, before the wait for the features) take the 128-row tiles of all
+// problems in turn: rows of a problem's feature buffer -> its prob buffer,
+// and the problem's largest probability into its control block (bounds of
+// the learned pivot weights for the selection passes).
+__global__ void __launch_bounds__(kRows, 2) mlp_proposal_kernel(Batch bt, int total, const float* wbf)
 {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = aligned_smem(smem_raw);
+    const uint32_t tmem = mlp_setup_cta(wbf, smem);
     pdl_wait();
     pdl_release();
-    extern __shared__ uint8_t smem_raw[];
-    int lb;
-    const ProbView v = vs.get(ST_MLP, blockIdx.x, lb);
-    FwdOut out = {v.prob, nullptr, nullptr, nullptr, nullptr};
-    mlp_forward_tile(v.feat, v.n, lb * kRows, wbf, out, aligned_smem(smem_raw), &v.ctl->err);
+    for (int tile = blockIdx.x; tile < total; tile += gridDim.x) {
+        int lb;
+        const ProbView v = bt.views[locate(bt, ST_MLP, tile, lb)];
+        FwdOut out = {v.prob, nullptr, nullptr, nullptr, nullptr};
+        float pm = mlp_tile(v.feat, v.n, lb * kRows, out, smem, tmem, &v.ctl->err);
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) pm = fmaxf(pm, __shfl_xor_sync(0xffffffffu, pm, off));
+        if ((threadIdx.x & 31) == 0 && pm > 0.f) atomicMax(&v.ctl->pmax_bits, __float_as_uint(pm));
+    }
+    mlp_teardown_cta(tmem);
 }
 
 // Features of one problem (one block of 1024 threads per problem).
@@ -474,7 +522,10 @@ void launch_features(const Batch& b, cudaStream_t s) { launch_pdl(features_kerne
 
 void launch_mlp_proposal(const Batch& b, int total, const float* wbf, cudaStream_t s)
 {
-    launch_pdl(mlp_proposal_kernel, total, kRows, kFwdSmem, s, ManyViews{b}, wbf);
+    int dev = 0, sms = 148;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = total < 2 * sms ? total : 2 * sms;
+    launch_pdl(mlp_proposal_kernel, grid, kRows, kFwdSmem, s, b, total, wbf);
 }
 
 void launch_mlp_forward(const float* feat, int m, const float* wbf, float* prob, float* z4, __nv_bfloat16* h1,

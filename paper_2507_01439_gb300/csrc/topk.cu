@@ -45,6 +45,18 @@ __device__ __forceinline__ uint64_t edge_key(int w, int i, int j, int n)
     return (static_cast<uint64_t>(w) << 32) | static_cast<uint64_t>(0xFFFFFFFFu - lin);
 }
 
+// Largest learned pivot weight a row can hold, before truncation: every entry
+// of row i has floor(W_ij p_i p_j) with W_ij <= rowmax_i and p_j <= max p, and
+// correctly rounded products of non-negative factors are monotonic, so
+// fl(fl(W_ij p_i) p_j) <= fl(fl(rowmax_i p_i) pmax).  Infinite when no bound
+// is available (plain weights, or no row maxima).
+__device__ __forceinline__ float learned_row_bound(const ProbView& v, int i)
+{
+    if (v.prob == nullptr || v.rowmax == nullptr) return __int_as_float(0x7f800000);
+    const float pmax = __uint_as_float(__ldcg(&v.ctl->pmax_bits));
+    return __fmul_rn(__fmul_rn(static_cast<float>(__ldcg(v.rowmax + i)), __ldcg(v.prob + i)), pmax);
+}
+
 // Iterate row i's upper-triangle entries j in (i, n) in chunks of 8 uint16
 // (16-byte loads); lane l takes chunks c0 + l, c0 + l + 32, ..., two loads in
 // flight per lane.  Chunks whose 8 weights are all zero are skipped.
@@ -91,6 +103,8 @@ __global__ void __launch_bounds__(256) hist_kernel(VS vs)
     for (int r = 0; r < kHistRowsPerBlock / 8; ++r) {
         const int i = lb * kHistRowsPerBlock + warp * (kHistRowsPerBlock / 8) + r;
         if (i >= v.n) break;
+        // learned weights: a row whose bound is below 1 holds only zeros (not counted)
+        if (!(learned_row_bound(v, i) >= 1.f)) continue;
         for_row_chunks(v, i, lane, [&](int, int w) {
             if (VS::kCallerWeights && w > v.n - 2) {
                 atomicOr(&v.ctl->err, TR_ERR_BAD_WEIGHT);
@@ -204,6 +218,7 @@ __global__ void __launch_bounds__(kCountThreads, 3) count_kernel(VS vs, int sele
     if (n_sel == 0) return;                   // uniform over the block
     if (t < 32) {
         if (act && v.rowmax != nullptr) act = rmax >= alpha;
+        if (act && v.prob != nullptr) act = learned_row_bound(v, row) >= static_cast<float>(alpha);
         const int c0 = (row + 1) >> 3;
         const int len = act ? ((n - 1) >> 3) - c0 + 1 : 0;
         int incl = len;

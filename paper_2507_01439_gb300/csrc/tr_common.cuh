@@ -37,7 +37,7 @@ struct Ctl {
     int32_t n_pivots;    // |P|
     int32_t n_valid;     // valid hypotheses (clique + non-degenerate Kabsch)
     int32_t n_fp64;      // hypotheses whose Kabsch ran in FP64
-    uint32_t pad0;
+    uint32_t pmax_bits;  // learned proposal: bits of the largest inlier probability (non-negative float)
     uint32_t done_blocks;  // completion counter (reserved; cleared with the other counters)
     uint32_t n_active;   // rows holding an edge of weight >= alpha (pivot selection)
     int32_t pad[3];
