@@ -778,6 +778,48 @@ def run_ours(args):
     print(json.dumps(line), flush=True)
 
 
+def run_profile_case(case):
+    """Small fixed workloads for profiler captures (no timing, no JSON line):
+      sc2-bitset   four registrations of the benchmark's seed-0 problem on the
+                   CUDA-core SC^2 path
+      batched      three batched calls of the 256-problem workload
+      learned      two learned-proposal batched calls (256 indoor problems,
+                   N = 5000, 1-5 % inliers, K1 = 100)"""
+    import numpy as np
+    import torch
+    import paper_2507_01439_gb300 as trg
+    from paper_2507_01439_gb300 import build as trbuild
+    import synth
+    trbuild.build()
+    if case == "sc2-bitset":
+        p = _problems(1)[0]
+        with trg.TurboReg(max_n=5000) as ctx:
+            prm = trg.default_params(p.tau, p.k1, p.theta, flags=trg.FLAG_SC2_BITSET)
+            for _ in range(4):
+                r = ctx.register(p.x, p.y, prm)
+        print("sc2-bitset", r.status, r.inlier_count)
+        return
+    if case == "batched":
+        probs = synth.make_batch(256, seed=4)
+        prm = [trg.default_params(p.tau, p.k1, p.theta) for p in probs]
+        calls = 3
+    else:
+        rng = np.random.Generator(np.random.PCG64(5))
+        probs = [synth.make_problem("indoor", 5000, float(rng.uniform(0.01, 0.05)), 50_000 + s) for s in range(256)]
+        prm = [trg.default_params(p.tau, 100, p.theta, proposal=trg.PROPOSAL_LEARNED) for p in probs]
+        calls = 2
+    offs = np.cumsum([0] + [p.n for p in probs]).astype(np.int64)
+    xs = torch.from_numpy(np.concatenate([p.x for p in probs])).cuda()
+    ys = torch.from_numpy(np.concatenate([p.y for p in probs])).cuda()
+    with trg.TurboReg(max_n=5000, max_batch=256) as ctx:
+        if case == "learned":
+            from paper_2507_01439_gb300 import train_proposal as tp
+            ctx.set_proposal_model(tp.load_model())
+        for _ in range(calls):
+            out = ctx.register_batched(xs, ys, offs, prm)
+    print(case, sum(r.status == 0 for r in out), "of", len(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -789,7 +831,12 @@ def main():
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-studies", action="store_true",
                     help="skip the SC^2 path comparison, the ablation sweep and the ranking study")
+    ap.add_argument("--profile-case", choices=["sc2-bitset", "batched", "learned"],
+                    help="run a small fixed workload for a profiler capture instead of the benchmark")
     args = ap.parse_args()
+    if args.profile_case:
+        run_profile_case(args.profile_case)
+        return
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
