@@ -52,11 +52,6 @@ __device__ __forceinline__ void tile_of(int t, int& bm, int& bn)
     bm = t - b * (b + 1);
 }
 
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
 // Epilogue of one 128 x 256 output tile whose FP32 accumulator is at TMEM
 // column tacc: warp (quarter, part) reads TMEM lanes 32 quarter .. +31 (tile
 // rows) and the kEpiCols columns of its part, masks with the adjacency bitset

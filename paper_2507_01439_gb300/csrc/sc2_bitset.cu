@@ -10,17 +10,14 @@
 // 4 % density, about 16 us on 152 SMs.
 //
 // Work tiles: row blocks of 128 rows i by column chunks of 256 columns j of
-// the upper triangle (j > i).  Two forms (the pipelined one for N_pad <= 5120):
-//   pipelined  halves of the tiles (128 x 128) as units; a CTA's rows i are
-//              one bulk copy into shared memory, every warp streams its rows j
-//              through a private queue of bulk copies; edges by warp-wide AND +
-//              popc with one redux.sync each (below);
-//   general    64-row halves; rows j loaded by the warps from global memory,
-//              rows i staged in shared memory when they fit.
-// Both write the W block staged in shared memory as full row segments (zeros
-// included, so W needs no clearing), and accumulate row sums, row maxima and
-// the edge-weight histogram in shared memory, with the same results as the
-// GEMM's epilogue.
+// the upper triangle (j > i).  Two forms:
+//   lane     (N_pad <= 5120) quarters of the tiles (128 x 64) as units, both
+//            row sets in shared memory, one edge per group of 8 lanes (below);
+//   general  64-row halves; rows j loaded by the warps from global memory,
+//            rows i staged in shared memory when they fit, one edge per warp.
+// Both write every W entry of their tiles (zeros included, so W needs no
+// clearing), and accumulate row sums, row maxima and the edge-weight
+// histogram in shared memory, with the same results as the GEMM's epilogue.
 #include "tr_common.cuh"
 #include "tr_problem.h"
 
@@ -91,195 +88,403 @@ __device__ __forceinline__ void record_edge(uint16_t* tile, int* rsum, int* rmax
 }
 
 // ---------------------------------------------------------------------------
-// Pipelined form (N_pad <= 5120).  Work units are halves of the tiles: 128
-// rows i by 128 columns j; a CTA takes a contiguous run of units in row-block-
-// major order, so its 128 bitset rows i (one bulk copy into shared memory)
-// change about once per CTA.  Each of the 24 warps takes the columns
-// j = jlo + warp + 24 k of a unit and streams their bitset rows through a
-// private three-slot queue in shared memory: lane 0 issues the 1-D bulk copy
-// of a row three rows ahead, completion counted on the slot's mbarrier, so no
-// warp waits for another.  For its row j a warp reads the four words over
-// columns i0 .. i0+127 (the adjacent rows i < j) and computes each edge's
-// popc(row_i & row_j) with kW words of AND + popc per lane and one
-// redux.sync, two edges interleaved.  Row sums, row maxima and the histogram
-// come from one pass over the finished unit in shared memory.
+// Lane form (N_pad <= 5120).  Work units are quarters of the tiles: 128 rows
+// i by 64 columns j, taken by a CTA of 16 warps as a contiguous run in row-
+// block-major order.  Its 128 bitset rows i (one bulk copy, about once per
+// CTA) and the 64 rows j of two units (one bulk copy each, double-buffered)
+// are in shared memory.  Each unit's edges (i < j, ordered by column, then
+// row) are listed one unit ahead, in a double-buffered list; the list is cut
+// into 64 equal runs, one per group of 8 lanes.  A group computes
+// popc(row_i & row_j) for one edge at a time with 20 words per lane (8 lanes
+// x 5 uint4 = 160 words; lane l of the group reads uint4 l + 8k, so the 8
+// lanes of a shared-memory phase hit distinct banks), keeps row j in
+// registers while consecutive edges share it and adds the lanes' counts with
+// three shuffles; lane 0 of the group stores the weight into W and adds it to
+// the row and column sums, the row maximum and the histogram in shared memory.
+// One CTA barrier per unit: before it, warps 0-7 count the next unit's edges
+// from its adjacency words (loaded from global memory a unit earlier); after
+// it, they write that list, one lane issues the next unit's rows j, the
+// finished unit's column sums go to global memory, and every thread writes
+// zeros over a part of the W block of the unit after next (the weights are
+// stored over them two barriers later).  kCsa: a lane's 20 words are first
+// added bit-sliced through a carry-save adder tree (full adders, 28 logic
+// operations), leaving six words of weights 1, 2, 4 and 8 for the population
+// count, so that the logic pipe takes most of the work of the slower
+// population-count pipe.  A unit's time varies little with its number of
+// edges (a split of the units by edge count was measured slower), so a CTA
+// takes an equal number of units.
 // ---------------------------------------------------------------------------
-constexpr int kUC = 128;                          // columns of a work unit
-constexpr int kPWarps = 24;
-constexpr int kQ = 3;                             // queue slots per warp
-constexpr int kPipeThreads = 32 * kPWarps;
+constexpr int kLUC = 64;                    // columns of a unit
+constexpr int kLWarps = 16;
+constexpr int kLThreads = 32 * kLWarps;
+constexpr int kLGroups = kLThreads / 8;     // groups of 8 lanes, one edge at a time each
+constexpr int kLMaxLdb = 160;
+constexpr int kLList = kBT * kLUC;          // list capacity of a unit (every pair an edge)
+constexpr int kLCountThreads = kLUC * 4;    // listing: one thread per column and 32-row word
 
-__host__ __device__ inline size_t pipe_smem_bytes(int ldb_max, int hist_bins)
+__host__ __device__ inline size_t lane_smem_bytes(int ldb_max, int hist_bins)
 {
-    return static_cast<size_t>(kBT) * ldb_max * 4 + static_cast<size_t>(kPWarps) * kQ * ldb_max * 4 +
-           static_cast<size_t>(kBT) * kUC * 2 + (kPWarps * kQ + 2) * 8 + static_cast<size_t>(hist_bins) * 4;
+    return static_cast<size_t>(kBT) * ldb_max * 4 + static_cast<size_t>(2 * kLUC) * ldb_max * 4 +
+           static_cast<size_t>(2 * kLList) * 2 + (2 * kBT + 2 * kLUC) * 4 + 32 + 128 + 256 +
+           static_cast<size_t>(hist_bins) * 4;
 }
 
-// popc(row_i & row_j) summed over the warp for two rows i at once (si0, si1);
-// r: this lane's words of row j (word lane + 32 q); kExact: ldb == 32 WPL
-template <int WPL, bool kExact>
-__device__ __forceinline__ void edge_pair(const uint32_t* si0, const uint32_t* si1, const uint32_t (&r)[WPL], int ldb,
-                                          int lane, int& c0, int& c1)
+struct LaneUnit {
+    int p, i0, j0;
+};
+
+__device__ __forceinline__ LaneUnit lane_unit(const Batch& bt, int u)
 {
-    uint32_t a = 0u, b = 0u;
-#pragma unroll
-    for (int q = 0; q < WPL; ++q) {
-        if (kExact || lane + 32 * q < ldb) {
-            a += __popc(si0[lane + 32 * q] & r[q]);
-            b += __popc(si1[lane + 32 * q] & r[q]);
+    int lt;
+    const int p = locate(bt, ST_BITSET, u >> 2, lt);
+    int bi, bj;
+    bitset_tile_of(lt, bt.views[p].n_pad, bi, bj);
+    return {p, bi * kBT, bj * kBC + (u & 3) * kLUC};
+}
+
+// The fields of a problem the lane form reads, kept in shared memory (a ring
+// of four slots by problem index: the units k-1 .. k+2 a CTA has in hand
+// belong to at most four consecutive problems), so that no descriptor read
+// from global memory sits on a unit's critical path.
+struct LaneView {
+    uint32_t* bits;
+    uint16_t* w;
+    int32_t* rowscore;
+    int32_t* rowmax;
+    uint32_t* hist;
+    int32_t n, n_pad, ldb, pad;
+};
+static_assert(sizeof(LaneView) <= 64, "four views in 256 bytes of shared memory");
+
+__device__ __forceinline__ void lane_view_load(LaneView& d, const ProbView& v)
+{
+    d.bits = v.bits;
+    d.w = v.w;
+    d.rowscore = v.rowscore;
+    d.rowmax = v.rowmax;
+    d.hist = v.hist;
+    d.n = v.n;
+    d.n_pad = v.n_pad;
+    d.ldb = v.ldb;
+}
+
+// Adds a CTA's histogram bins of a problem to its global histogram and clears them.
+__device__ __forceinline__ void lane_flush_hist(const LaneView& v, uint32_t* sh, int tid)
+{
+    for (int b = tid + 1; b <= v.n; b += blockDim.x) {
+        const uint32_t h = sh[b];
+        if (h) {
+            atomicAdd(v.hist + b, h);
+            sh[b] = 0u;
         }
     }
-    c0 = static_cast<int>(__reduce_add_sync(0xffffffffu, a));
-    c1 = static_cast<int>(__reduce_add_sync(0xffffffffu, b));
 }
 
-template <int WPL, bool kExact>
-__global__ void __launch_bounds__(kPipeThreads, 1) sc2_bitset_pipe_kernel(Batch bt, int total, int ldb_max, int hist_bins)
+// The unit after `un` in unit order (row blocks in turn, each from its first
+// tile to the last column; then the next problem's first unit); n_pad: un's problem.
+__device__ __forceinline__ LaneUnit lane_next(LaneUnit un, int n_pad)
 {
-    extern __shared__ __align__(16) uint8_t ps_raw[];
-    uint8_t* q8 = ps_raw;
-    uint32_t* srows = reinterpret_cast<uint32_t*>(q8);   q8 += static_cast<size_t>(kBT) * ldb_max * 4;
-    uint32_t* squeue = reinterpret_cast<uint32_t*>(q8);  q8 += static_cast<size_t>(kPWarps) * kQ * ldb_max * 4;
-    uint16_t* stile = reinterpret_cast<uint16_t*>(q8);   q8 += static_cast<size_t>(kBT) * kUC * 2;
-    uint64_t* qbar = reinterpret_cast<uint64_t*>(q8);    q8 += kPWarps * kQ * 8;
-    uint64_t* rows_bar = reinterpret_cast<uint64_t*>(q8); q8 += 16;
+    un.j0 += kLUC;
+    if (un.j0 < n_pad) return un;
+    un.i0 += kBT;
+    if (un.i0 < n_pad) {
+        un.j0 = (un.i0 / kBT >> 1) * kBC;
+        return un;
+    }
+    return {un.p + 1, 0, 0};
+}
+
+// full adder on every bit position: a + b + d = s + 2 c, one three-input
+// logic operation each (truth tables 0x96: a ^ b ^ d, 0xE8: majority)
+__device__ __forceinline__ void full_add(uint32_t& c, uint32_t& s, uint32_t a, uint32_t b, uint32_t d)
+{
+    asm("lop3.b32 %0, %1, %2, %3, 0x96;" : "=r"(s) : "r"(a), "r"(b), "r"(d));
+    asm("lop3.b32 %0, %1, %2, %3, 0xE8;" : "=r"(c) : "r"(a), "r"(b), "r"(d));
+}
+
+// sum over this lane's words of popc(row_i word & row_j word)
+template <int NQ, bool kCsa>
+__device__ __forceinline__ uint32_t and_popc(const uint4 (&a)[NQ], const uint4 (&b)[NQ])
+{
+    uint32_t w[4 * NQ];
+#pragma unroll
+    for (int k = 0; k < NQ; ++k) {
+        w[4 * k + 0] = a[k].x & b[k].x;
+        w[4 * k + 1] = a[k].y & b[k].y;
+        w[4 * k + 2] = a[k].z & b[k].z;
+        w[4 * k + 3] = a[k].w & b[k].w;
+    }
+    if constexpr (!kCsa || NQ != 5) {
+        uint32_t s = 0u;
+#pragma unroll
+        for (int k = 0; k < 4 * NQ; ++k) s += __popc(w[k]);
+        return s;
+    } else {
+        // 20 words of weight 1 -> o8, w19 (1), u3 (2), g0, f3 (4), e0 (8)
+        uint32_t t0, o0, t1, o1, t2, o2, t3, o3, t4, o4, t5, o5;
+        full_add(t0, o0, w[0], w[1], w[2]);
+        full_add(t1, o1, w[3], w[4], w[5]);
+        full_add(t2, o2, w[6], w[7], w[8]);
+        full_add(t3, o3, w[9], w[10], w[11]);
+        full_add(t4, o4, w[12], w[13], w[14]);
+        full_add(t5, o5, w[15], w[16], w[17]);
+        uint32_t t6, o6, t7, o7, t8, o8;
+        full_add(t6, o6, o0, o1, o2);
+        full_add(t7, o7, o3, o4, o5);
+        full_add(t8, o8, o6, o7, w[18]);
+        uint32_t f0, u0, f1, u1, f2, u2, f3, u3, e0, g0;
+        full_add(f0, u0, t0, t1, t2);
+        full_add(f1, u1, t3, t4, t5);
+        full_add(f2, u2, t6, t7, t8);
+        full_add(f3, u3, u0, u1, u2);
+        full_add(e0, g0, f0, f1, f2);
+        return __popc(o8) + __popc(w[19]) + 2u * __popc(u3) + 4u * (__popc(g0) + __popc(f3)) + 8u * __popc(e0);
+    }
+}
+
+template <int NQ, bool kExact, bool kCsa>
+__global__ void __launch_bounds__(kLThreads, 1)
+    sc2_bitset_lane_kernel(Batch bt, int total, int ldb_max, int hist_bins)
+{
+    extern __shared__ __align__(16) uint8_t ls_raw[];
+    uint8_t* q8 = ls_raw;
+    uint32_t* srows = reinterpret_cast<uint32_t*>(q8);  q8 += static_cast<size_t>(kBT) * ldb_max * 4;
+    uint32_t* scols = reinterpret_cast<uint32_t*>(q8);  q8 += static_cast<size_t>(2 * kLUC) * ldb_max * 4;
+    uint16_t* slist = reinterpret_cast<uint16_t*>(q8);  q8 += static_cast<size_t>(2 * kLList) * 2;
+    int* srsum = reinterpret_cast<int*>(q8);            q8 += kBT * 4;
+    int* srmax = reinterpret_cast<int*>(q8);            q8 += kBT * 4;
+    int* scsum = reinterpret_cast<int*>(q8);            q8 += 2 * kLUC * 4;   // [unit parity][column]
+    uint64_t* bars = reinterpret_cast<uint64_t*>(q8);   q8 += 32;            // rows i, rows j [2]
+    int* sw = reinterpret_cast<int*>(q8);               q8 += 128;           // list scans: [parity][warp]
+    LaneView* lv = reinterpret_cast<LaneView*>(q8);     q8 += 256;           // [problem & 3]
     uint32_t* shist = reinterpret_cast<uint32_t*>(q8);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (threadIdx.x < kPWarps * kQ + 1) mbar_init(threadIdx.x < kPWarps * kQ ? &qbar[threadIdx.x] : rows_bar, 1);
-    if (threadIdx.x == 0) fence_mbar_init();
-    for (int b = threadIdx.x; b < hist_bins; b += kPipeThreads) shist[b] = 0u;
-    for (int q = threadIdx.x; q < kBT * kUC / 8; q += kPipeThreads) reinterpret_cast<uint4*>(stile)[q] = make_uint4(0, 0, 0, 0);
-    const int units = 2 * total;
-    const int u0 = static_cast<int>((static_cast<long long>(units) * blockIdx.x) / gridDim.x);
-    const int u1 = static_cast<int>((static_cast<long long>(units) * (blockIdx.x + 1)) / gridDim.x);
+    uint64_t* rows_full = bars;
+    uint64_t* cols_full = bars + 1;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int grp = tid >> 3, gl = tid & 7;
+    if (tid < 3) mbar_init(&bars[tid], 1);
+    if (tid == 0) fence_mbar_init();
+    for (int b = tid; b < hist_bins; b += kLThreads) shist[b] = 0u;
+    if (tid < kBT) {
+        srsum[tid] = 0;
+        srmax[tid] = 0;
+    }
+    if (tid < 2 * kLUC) scsum[tid] = 0;
     __syncthreads();
     pdl_wait();
     pdl_release();
+    // this CTA's units: a contiguous run (the time of a unit varies little with its edges)
+    const int units = 4 * total;
+    const int u0 = static_cast<int>((static_cast<long long>(units) * blockIdx.x) / gridDim.x);
+    const int u1 = static_cast<int>((static_cast<long long>(units) * (blockIdx.x + 1)) / gridDim.x);
+    if (u0 >= u1) return;
+    const int K = u1 - u0;
     bool ok = true;
-    int cur_p = -1, cur_bi = -1;
-    uint32_t rows_uses = 0, qn = 0;     // row-block loads (all threads); this warp's queue uses
-    uint32_t* myq = squeue + static_cast<size_t>(warp) * kQ * ldb_max;
-    uint64_t* mybar = qbar + warp * kQ;
-    for (int u = u0; u < u1; ++u) {
-        int lt;
-        const int p = locate(bt, ST_BITSET, u >> 1, lt);
-        const ProbView v = bt.views[p];
-        int bi, bj;
-        bitset_tile_of(lt, v.n_pad, bi, bj);
-        const int i0 = bi * kBT, j0 = bj * kBC + (u & 1) * kUC;
-        const int n = v.n, ldb = v.ldb, n_pad = v.n_pad;
-        const int jlo = j0 > i0 + 1 ? j0 : i0 + 1;
-        const int jhi = j0 + kUC < n ? j0 + kUC : n;
-        if (p != cur_p && cur_p >= 0 && hist_bins > 0) {
-            flush_hist(bt.views[cur_p], shist, threadIdx.x, kPipeThreads);
-            __syncthreads();
-        }
-        const bool new_rows = p != cur_p || bi != cur_bi;
-        cur_p = p;
-        cur_bi = bi;
-        if (new_rows && threadIdx.x == 0) {
-            fence_proxy_async();   // the previous rows were read through the generic proxy
-            mbar_arrive_expect_tx(rows_bar, kBT * ldb * 4);
-            bulk_g2s(srows, v.bits + (size_t)i0 * ldb, kBT * ldb * 4, rows_bar);
-        }
-        // this warp's rows j, kQ in flight
-        const int nj = jhi > jlo + warp ? (jhi - jlo - warp + kPWarps - 1) / kPWarps : 0;
-        if (lane == 0) {
-            for (int k = 0; k < kQ && k < nj; ++k) {
-                const uint32_t sl = (qn + k) % kQ;
-                mbar_arrive_expect_tx(&mybar[sl], ldb * 4);
-                bulk_g2s(myq + sl * ldb_max, v.bits + (size_t)(jlo + warp + k * kPWarps) * ldb, ldb * 4, &mybar[sl]);
-            }
-        }
-        if (new_rows) ok &= mbar_wait(rows_bar, rows_uses & 1u);
-        const int wi = i0 >> 5;   // first word of the block's rows (multiple of 4)
-        for (int k = 0; k < nj; ++k) {
-            const uint32_t sl = (qn + k) % kQ, ph = ((qn + k) / kQ) & 1u;
-            const bool got = mbar_wait(&mybar[sl], ph);
-            ok &= got;
-            const int j = jlo + warp + k * kPWarps;
-            const uint32_t* rj = myq + sl * ldb_max;
-            uint32_t r[WPL];
+
+    auto issue_cols = [&](const LaneUnit& un, int slot) {
+        const LaneView& v = lv[un.p & 3];
+        const uint32_t bytes = static_cast<uint32_t>(kLUC * v.ldb * 4);
+        mbar_arrive_expect_tx(&cols_full[slot], bytes);
+        bulk_g2s(scols + static_cast<size_t>(slot) * kLUC * ldb_max, v.bits + static_cast<size_t>(un.j0) * v.ldb,
+                 bytes, &cols_full[slot]);
+    };
+    auto issue_rows = [&](const LaneUnit& un) {
+        const LaneView& v = lv[un.p & 3];
+        const uint32_t bytes = static_cast<uint32_t>(kBT * v.ldb * 4);
+        mbar_arrive_expect_tx(rows_full, bytes);
+        bulk_g2s(srows, v.bits + static_cast<size_t>(un.i0) * v.ldb, bytes, rows_full);
+    };
+    // zeros over a unit's W block (128 rows x 128 B)
+    auto zero_w = [&](const LaneUnit& un) {
+        const LaneView& v = lv[un.p & 3];
+        for (int q = tid; q < kBT * kLUC / 8; q += kLThreads)
+            *reinterpret_cast<uint4*>(v.w + static_cast<size_t>(un.i0 + (q >> 3)) * v.n_pad + un.j0 + (q & 7) * 8) =
+                make_uint4(0u, 0u, 0u, 0u);
+    };
+    // listing, thread t < 256: column jl = t / 4, rows 32 (t % 4) .. +31 of the unit
+    auto mask_word = [&](const LaneUnit& un) -> uint32_t {
+        const LaneView& v = lv[un.p & 3];
+        const int jl = tid >> 2, h = tid & 3;
+        const int j = un.j0 + jl;
+        const uint32_t w = __ldg(v.bits + static_cast<size_t>(j) * v.ldb + (un.i0 >> 5) + h);
+        const int lh = (j < v.n ? j - un.i0 : 0) - 32 * h;   // rows 32 h + r, r < lh
+        return lh <= 0 ? 0u : lh < 32 ? w & ((1u << lh) - 1u) : w;
+    };
+    // warps 0-7: counts and warp scan of a list (totals in sw[par][warp]); returns the inclusive count
+    auto list_count = [&](uint32_t m, int par) -> int {
+        const int cnt = __popc(m);
+        int inc = cnt;
 #pragma unroll
-            for (int q = 0; q < WPL; ++q) r[q] = (kExact || lane + 32 * q < ldb) ? rj[lane + 32 * q] : 0u;
-            const uint4 mw = *reinterpret_cast<const uint4*>(rj + wi);   // adjacency of j to rows i0 .. i0+127
-            __syncwarp();
-            if (lane == 0 && k + kQ < nj) {   // the slot is read: refill it with the row kQ ahead
+        for (int off = 1; off < 32; off <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, inc, off);
+            if (lane >= off) inc += y;
+        }
+        if (lane == 31) sw[par * 16 + warp] = inc;
+        return inc;
+    };
+    // after the barrier: the list's entries (warps 0-7) and its total (all threads)
+    auto list_write = [&](uint32_t m, int inc, int par, uint16_t* lst) -> int {
+        int base = inc - __popc(m), E = 0;
+#pragma unroll
+        for (int w = 0; w < kLCountThreads / 32; ++w) {
+            const int x = sw[par * 16 + w];
+            if (w < warp) base += x;
+            E += x;
+        }
+        if (tid < kLCountThreads) {
+            const int jl = tid >> 2, h = tid & 3;
+            for (; m; m &= m - 1u) lst[base++] = static_cast<uint16_t>((jl << 7) | (32 * h + __ffs(m) - 1));
+        }
+        return E;
+    };
+
+    uint32_t rows_uses = 0;
+    LaneUnit cur = lane_unit(bt, u0), prev = cur;
+    LaneUnit nxt = K > 1 ? lane_next(cur, bt.views[cur.p].n_pad) : cur;
+    LaneUnit ahead = K > 2 ? lane_next(nxt, bt.views[nxt.p].n_pad) : nxt;   // unit k + 2
+    if (tid == 0) {
+        lane_view_load(lv[cur.p & 3], bt.views[cur.p]);
+        if (nxt.p != cur.p) lane_view_load(lv[nxt.p & 3], bt.views[nxt.p]);
+        if (ahead.p != nxt.p) lane_view_load(lv[ahead.p & 3], bt.views[ahead.p]);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        issue_rows(cur);
+        issue_cols(cur, 0);
+    }
+    zero_w(cur);
+    if (K > 1) zero_w(nxt);
+    // the first unit's list
+    uint32_t m = tid < kLCountThreads ? mask_word(cur) : 0u;
+    int inc = tid < kLCountThreads ? list_count(m, 1) : 0;
+    __syncthreads();
+    int E = list_write(m, inc, 1, slist);
+    m = (tid < kLCountThreads && K > 1) ? mask_word(nxt) : 0u;   // the next unit's words, ahead of use
+    for (int k = 0; k < K; ++k) {
+        const int slot = k & 1, par = k & 1;
+        // ---- count the next unit's edges, then the unit barrier ----
+        if (k + 1 < K && tid < kLCountThreads) inc = list_count(m, par);
+        __syncthreads();   // unit k-1's items, unit k's list and zeros are complete; the next list's counts are in
+        const bool new_rows = k > 0 && (cur.p != prev.p || cur.i0 != prev.i0);
+        if (tid == kLThreads - 32) {
+            // the bulk copies, from a thread with no memory operation of its own in flight
+            // (the proxy fence would wait for them)
+            if (new_rows) {
                 fence_proxy_async();
-                mbar_arrive_expect_tx(&mybar[sl], ldb * 4);
-                bulk_g2s(myq + sl * ldb_max, v.bits + (size_t)(j + kQ * kPWarps) * ldb, ldb * 4, &mybar[sl]);
+                issue_rows(cur);
             }
-            if (!got) continue;
-            uint32_t m[4] = {mw.x, mw.y, mw.z, mw.w};
-            const int lim = j - i0;            // rows i < j
-#pragma unroll
-            for (int h = 0; h < 4; ++h) {
-                const int lh = lim - 32 * h;
-                if (lh <= 0) m[h] = 0u;
-                else if (lh < 32) m[h] &= (1u << lh) - 1u;
+            if (k + 1 < K) {
+                fence_proxy_async();
+                issue_cols(nxt, slot ^ 1);   // its buffer held unit k-1
             }
-            int colsum = 0;
-            uint16_t* tcol = stile + (j - j0);
+        }
+        if (k > 0) {
+            // unit k-1: column sums; at a new row block its row sums and maxima (and histogram)
+            const LaneView& pv = lv[prev.p & 3];
+            if (tid < kLUC) {
+                int* cs = scsum + ((k - 1) & 1) * kLUC;
+                const int x = cs[tid];
+                if (x) atomicAdd(&pv.rowscore[prev.j0 + tid], x);
+                cs[tid] = 0;
+            }
+            if (new_rows) {
+                const int r = tid - kLUC;
+                if (r >= 0 && r < kBT) {
+                    const int x = srsum[r], mx = srmax[r];
+                    if (x) atomicAdd(&pv.rowscore[prev.i0 + r], x);
+                    if (mx && pv.rowmax) atomicMax(&pv.rowmax[prev.i0 + r], mx);
+                    srsum[r] = 0;
+                    srmax[r] = 0;
+                }
+                if (cur.p != prev.p && hist_bins > 0) lane_flush_hist(pv, shist, tid);
+            }
+        }
+        int E_next = 0;
+        if (k + 1 < K) E_next = list_write(m, inc, par, slist + (slot ^ 1) * kLList);
+        if (k + 2 < K) {
+            zero_w(ahead);
+            if (tid < kLCountThreads) m = mask_word(ahead);
+        }
+        if (new_rows) __syncthreads();   // the old row block's sums are taken before the new block's additions
+        // ---- unit k's edges: group grp takes list entries [lo, hi) ----
+        ok &= mbar_wait(&cols_full[slot], static_cast<uint32_t>(k >> 1) & 1u);
+        if (k == 0 || new_rows) {
+            ok &= mbar_wait(rows_full, rows_uses & 1u);
+            ++rows_uses;
+        }
+        {
+            const LaneView& v = lv[cur.p & 3];
+            const int ldb = v.ldb;
+            const int l4 = ldb >> 2;
+            const int lo = (grp * E) / kLGroups, hi = ((grp + 1) * E) / kLGroups;
+            const int cnt = hi - lo;
+            const int T = static_cast<int>(__reduce_max_sync(0xffffffffu, static_cast<unsigned>(cnt)));
+            const uint32_t* cols = scols + static_cast<size_t>(slot) * kLUC * ldb_max;
+            const uint16_t* lst = slist + slot * kLList;
+            int* csum = scsum + par * kLUC;
+            uint32_t* hh = hist_bins > 0 ? shist : v.hist;
+            uint16_t* wblk = v.w + static_cast<size_t>(cur.i0) * v.n_pad + cur.j0;
+            const int e_last = cnt > 0 ? hi - 1 : 0;
+            int cj = -1;
+            uint4 jr[NQ];
 #pragma unroll
-            for (int h = 0; h < 4; ++h) {
-                uint32_t mask = m[h];
-                while (mask) {
-                    const int ra = 32 * h + __ffs(mask) - 1;
-                    mask &= mask - 1u;
-                    const int rb = mask ? 32 * h + __ffs(mask) - 1 : ra;   // second edge (or a repeat)
-                    mask &= mask - 1u;
-                    int ca, cb;
-                    edge_pair<WPL, kExact>(srows + ra * ldb, srows + rb * ldb, r, ldb, lane, ca, cb);
-                    if (rb == ra) cb = 0;
-                    colsum += ca + cb;
-                    if (lane == 0) tcol[ra * kUC] = static_cast<uint16_t>(ca);
-                    if (lane == 1 && rb != ra) tcol[rb * kUC] = static_cast<uint16_t>(cb);
+            for (int q = 0; q < NQ; ++q) jr[q] = make_uint4(0u, 0u, 0u, 0u);
+            int ent = T > 0 ? lst[cnt > 0 ? lo : 0] : 0;
+            for (int t = 0; t < T; ++t) {
+                const bool valid = t < cnt;
+                const int il = ent & 127, jl = ent >> 7;
+                ent = lst[t + 1 < cnt ? lo + t + 1 : e_last];   // the next entry, ahead of its use
+                if (jl != cj) {
+                    cj = jl;
+                    const uint4* r4 = reinterpret_cast<const uint4*>(cols + static_cast<size_t>(jl) * ldb);
+#pragma unroll
+                    for (int q = 0; q < NQ; ++q)
+                        jr[q] = (kExact || gl + 8 * q < l4) ? r4[gl + 8 * q] : make_uint4(0u, 0u, 0u, 0u);
+                }
+                const uint4* a4 = reinterpret_cast<const uint4*>(srows + static_cast<size_t>(il) * ldb);
+                uint4 a[NQ];
+#pragma unroll
+                for (int q = 0; q < NQ; ++q)
+                    a[q] = (kExact || gl + 8 * q < l4) ? a4[gl + 8 * q] : make_uint4(0u, 0u, 0u, 0u);
+                uint32_t s = and_popc<NQ, kCsa>(a, jr);
+                s += __shfl_xor_sync(0xffffffffu, s, 4);
+                s += __shfl_xor_sync(0xffffffffu, s, 2);
+                s += __shfl_xor_sync(0xffffffffu, s, 1);
+                if (gl == 0 && valid && s) {
+                    wblk[static_cast<size_t>(il) * v.n_pad + jl] = static_cast<uint16_t>(s);
+                    atomicAdd(&srsum[il], static_cast<int>(s));
+                    atomicMax(&srmax[il], static_cast<int>(s));
+                    atomicAdd(&csum[jl], static_cast<int>(s));
+                    atomicAdd(&hh[s], 1u);
                 }
             }
-            if (lane == 0 && colsum) atomicAdd(&v.rowscore[j], colsum);
         }
-        qn += static_cast<uint32_t>(nj);
-        rows_uses += new_rows ? 1u : 0u;
-        __syncthreads();   // the unit is complete in shared memory
-        // W rows i0 .. i0+127 (256-byte segments), row sums, row maxima, histogram
-        for (int q = threadIdx.x; q < kBT * kUC / 8; q += kPipeThreads) {
-            const int rr = q >> 4, c8 = (q & 15) * 8;
-            *reinterpret_cast<uint4*>(v.w + (size_t)(i0 + rr) * n_pad + j0 + c8) = reinterpret_cast<const uint4*>(stile)[q];
+        E = E_next;
+        prev = cur;
+        cur = nxt;
+        nxt = ahead;
+        if (k + 3 < K) {
+            const int pa = ahead.p;
+            ahead = lane_next(ahead, lv[pa & 3].n_pad);
+            if (tid == 0 && ahead.p != pa) lane_view_load(lv[ahead.p & 3], bt.views[ahead.p]);   // seen after the next barrier
         }
-        if (threadIdx.x < 4 * kBT) {
-            const int rr = threadIdx.x >> 2, qt = threadIdx.x & 3;
-            const uint4* src = reinterpret_cast<const uint4*>(stile + rr * kUC + qt * 32);
-            int sum = 0, mx = 0;
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const uint4 w4 = src[c];
-                const uint32_t wv[4] = {w4.x, w4.y, w4.z, w4.w};
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    if (wv[e] == 0u) continue;
-                    const int lo = static_cast<int>(wv[e] & 0xFFFFu), hi = static_cast<int>(wv[e] >> 16);
-                    sum += lo + hi;
-                    mx = max(mx, max(lo, hi));
-                    uint32_t* hh = hist_bins > 0 ? shist : v.hist;
-                    if (lo) atomicAdd(&hh[lo], 1u);
-                    if (hi) atomicAdd(&hh[hi], 1u);
-                }
-            }
-            sum += __shfl_xor_sync(0xffffffffu, sum, 1);
-            sum += __shfl_xor_sync(0xffffffffu, sum, 2);
-            mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
-            mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
-            if (qt == 0) {
-                if (sum) atomicAdd(&v.rowscore[i0 + rr], sum);
-                if (mx && v.rowmax) atomicMax(&v.rowmax[i0 + rr], mx);
-            }
+    }
+    __syncthreads();
+    {
+        // the last unit's column sums, its row block's sums and maxima, its problem's histogram
+        const LaneView& pv = lv[prev.p & 3];
+        if (tid < kLUC) {
+            const int x = scsum[((K - 1) & 1) * kLUC + tid];
+            if (x) atomicAdd(&pv.rowscore[prev.j0 + tid], x);
         }
-        __syncthreads();
-        for (int q = threadIdx.x; q < kBT * kUC / 8; q += kPipeThreads) reinterpret_cast<uint4*>(stile)[q] = make_uint4(0, 0, 0, 0);
-        __syncthreads();   // cleared for the next unit; the row block may be replaced
+        const int r = tid - kLUC;
+        if (r >= 0 && r < kBT) {
+            if (srsum[r]) atomicAdd(&pv.rowscore[prev.i0 + r], srsum[r]);
+            if (srmax[r] && pv.rowmax) atomicMax(&pv.rowmax[prev.i0 + r], srmax[r]);
+        }
+        if (hist_bins > 0) lane_flush_hist(pv, shist, tid);
     }
     if (!ok && lane == 0) atomicOr(&bt.views[0].ctl->err, TR_ERR_TIMEOUT);
-    if (cur_p >= 0 && hist_bins > 0) flush_hist(bt.views[cur_p], shist, threadIdx.x, kPipeThreads);
 }
 
 // ---------------------------------------------------------------------------
@@ -398,7 +603,6 @@ size_t bitset_smem(int rows_ldb, int hist_bins)
 }
 
 constexpr int kBsSmemMax = 232448;
-constexpr int kPipeMaxLdb = 160;   // the pipelined form: N_pad <= 5120
 
 template <int WPL>
 cudaError_t bs_attr()
@@ -406,12 +610,14 @@ cudaError_t bs_attr()
     return cudaFuncSetAttribute(sc2_bitset_kernel<WPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBsSmemMax);
 }
 
-template <int WPL, bool kExact>
-cudaError_t pipe_attr()
+template <int NQ, bool kExact, bool kCsa>
+cudaError_t lane_attr()
 {
-    return cudaFuncSetAttribute(sc2_bitset_pipe_kernel<WPL, kExact>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(sc2_bitset_lane_kernel<NQ, kExact, kCsa>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 kBsSmemMax);
 }
+
+
 
 }  // namespace
 
@@ -425,9 +631,9 @@ cudaError_t sc2_bitset_setup()
     if (e == cudaSuccess) e = bs_attr<8>();
     if (e == cudaSuccess) e = bs_attr<16>();
     if (e == cudaSuccess) e = bs_attr<32>();
-    if (e == cudaSuccess) e = pipe_attr<2, false>();
-    if (e == cudaSuccess) e = pipe_attr<5, false>();
-    if (e == cudaSuccess) e = pipe_attr<5, true>();
+    if (e == cudaSuccess) e = lane_attr<2, false, false>();
+    if (e == cudaSuccess) e = lane_attr<5, false, true>();
+    if (e == cudaSuccess) e = lane_attr<5, true, true>();
     return e;
 }
 
@@ -436,20 +642,20 @@ bool launch_sc2_bitset(const Batch& b, int total_tiles, int max_n, int min_n, cu
     const int max_npad = (max_n + kSc2BN - 1) / kSc2BN * kSc2BN;
     const int max_ldb = max_npad / 32;
     const int sms = g_bs_sms > 0 ? g_bs_sms : 148;
-    if (max_ldb <= kPipeMaxLdb) {
+    if (max_ldb <= kLMaxLdb) {
         int hist_bins = max_n + 1;
-        if (pipe_smem_bytes(max_ldb, hist_bins) > static_cast<size_t>(kBsSmemMax)) hist_bins = 0;
-        const size_t smem = pipe_smem_bytes(max_ldb, hist_bins);
-        const int grid = sms < 2 * total_tiles ? sms : 2 * total_tiles;
+        if (lane_smem_bytes(max_ldb, hist_bins) > static_cast<size_t>(kBsSmemMax)) hist_bins = 0;
+        const size_t smem = lane_smem_bytes(max_ldb, hist_bins);
+        const int grid = sms < 4 * total_tiles ? sms : 4 * total_tiles;
         // kExact (no per-lane word guard) when every problem's rows are 5 x 32 words
         const int min_ldb = (min_n + kSc2BN - 1) / kSc2BN * kSc2BN / 32;
-        const int exact_ldb = min_ldb == max_ldb ? max_ldb : 0;
+        const bool exact = min_ldb == max_ldb && max_ldb == kLMaxLdb;
         if (max_ldb <= 64)
-            launch_pdl(sc2_bitset_pipe_kernel<2, false>, grid, kPipeThreads, smem, s, b, total_tiles, max_ldb, hist_bins);
-        else if (exact_ldb == 160)
-            launch_pdl(sc2_bitset_pipe_kernel<5, true>, grid, kPipeThreads, smem, s, b, total_tiles, max_ldb, hist_bins);
+            launch_pdl(sc2_bitset_lane_kernel<2, false, false>, grid, kLThreads, smem, s, b, total_tiles, max_ldb, hist_bins);
+        else if (exact)
+            launch_pdl(sc2_bitset_lane_kernel<5, true, true>, grid, kLThreads, smem, s, b, total_tiles, max_ldb, hist_bins);
         else
-            launch_pdl(sc2_bitset_pipe_kernel<5, false>, grid, kPipeThreads, smem, s, b, total_tiles, max_ldb, hist_bins);
+            launch_pdl(sc2_bitset_lane_kernel<5, false, true>, grid, kLThreads, smem, s, b, total_tiles, max_ldb, hist_bins);
         return true;
     }
     // shared memory for the row block and the histogram bins, as far as they fit
