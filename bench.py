@@ -608,8 +608,16 @@ def run_sc2_paths(trg, probs, dx, dy):
     default; independent CTAs) vs the
     CUDA-core bitset AND + popcount path (same integers); in-graph CUDA-event
     times."""
+    import numpy as np
     out = {}
     with trg.TurboReg(max_n=5000, max_batch=1) as ctx:
+        # upper edges |E+| of each problem (the useful work of SC^2: |E+| N_pad
+        # multiply-adds, |E+| N_pad / 32 words of AND + popc)
+        edges = []
+        for k in range(8):
+            ctx.register(dx[k], dy[k], trg.default_params(0.1, 2000, 0.1))
+            bits = ctx.buffer(trg.BUF_ADJ_BITS)
+            edges.append(int(np.unpackbits(bits.view(np.uint8)).sum()) // 2)
         for name, fl in (("tcgen05_gemm", 0), ("tcgen05_gemm_single_cta", trg.FLAG_SC2_SINGLE_CTA),
                          ("bitset_popcount", trg.FLAG_SC2_BITSET)):
             prm = trg.default_params(0.1, 2000, 0.1, flags=trg.FLAG_STAGE_TIMES | fl)
@@ -619,6 +627,20 @@ def run_sc2_paths(trg, probs, dx, dy):
                 if k >= 4:
                     ms.append(ctx.stage_times()["sc2"])
             out[name + "_ms"] = sum(ms) / len(ms)
+    npad = 5120
+    e_mean = sum(edges) / len(edges)
+    useful_flops = 2.0 * e_mean * npad
+    nb = npad // 256
+    dense_flops = nb * (nb + 1) * 2.0 * 128 * 256 * npad
+    words = e_mean * npad / 32
+    floor_ms = words / (16 * 152 * 2.07e9) * 1e3     # population count: 16 per clock per SM, 152 SMs, 2.07 GHz
+    out["upper_edges_mean"] = e_mean
+    out["useful_flops"] = useful_flops
+    out["gemm_useful_fraction_of_executed"] = useful_flops / dense_flops
+    out["gemm_useful_tflops"] = useful_flops / (out["tcgen05_gemm_ms"] * 1e-3) / 1e12
+    out["bitset_words"] = words
+    out["bitset_popc_floor_ms"] = floor_ms
+    out["bitset_frac_of_popc_floor"] = floor_ms / out["bitset_popcount_ms"]
     return out
 
 
@@ -763,6 +785,14 @@ def run_ours(args):
         line["learned"] = run_learned(trg, torch, stream, flush)
     if not args.no_studies:
         line["sc2_paths"] = run_sc2_paths(trg, probs, dx, dy)
+        sp = line["sc2_paths"]
+        # the method's own work beside the dense figure: the GEMM's useful
+        # fraction and the CUDA-core path against its population-count floor
+        line["roofline"]["useful_work"] = {
+            "useful_flops": sp["useful_flops"], "gemm_useful_fraction_of_executed": sp["gemm_useful_fraction_of_executed"],
+            "gemm_frac_on_useful_work": sp["gemm_useful_tflops"] / peak,
+            "bitset_ms": sp["bitset_popcount_ms"], "bitset_frac_of_popc_floor": sp["bitset_frac_of_popc_floor"],
+            "popc_floor": "16 population counts per clock per SM, 152 SMs, 2.07 GHz"}
         line["ablation"] = run_ablation(trg, torch, stream, flush)
         line["ranking"] = run_ranking(trg)
         line["clique_stability"] = run_clique_stability(trg)
