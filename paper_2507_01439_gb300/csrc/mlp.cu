@@ -13,8 +13,11 @@
 // on the tensor cores (tcgen05.mma kind::f16, BF16 operands, FP32 TMEM
 // accumulators) with operands written to shared memory in the 128-byte
 // swizzled K-major layout by the threads themselves.
-// Backward and Adam run on CUDA cores (FP32 arithmetic on the BF16 weights
-// and activations the forward used).
+// Backward: the activation gradients of layers 3 and 2 and the weight
+// gradients of layers 2 and 3 on the tensor cores (BF16 operands, FP32
+// accumulation, the weight gradients accumulated in tensor memory over a
+// CTA's sample tiles); layers 1 and 4 and the biases on CUDA cores.  Adam on
+// CUDA cores.
 #include <cuda_bf16.h>
 
 #include "tr_common.cuh"
@@ -365,116 +368,340 @@ __global__ void __launch_bounds__(1024) features_kernel(ManyViews vs)
     }
 }
 
-// ---------------- training: backward and Adam (CUDA cores) ----------------
+// ---------------- training: backward on the tensor cores ----------------
+//
+// Persistent CTAs of 128 threads take 128-sample tiles (thread t: sample
+// row0 + t).  Per sample:
+//   dz4 = (sigmoid(z4) - y) / m                  (mean binary cross-entropy)
+//   dz3 = W4 dz4 * [h3 > 0]                      (CUDA cores)
+//   dz2 = (dz3 W3) * [h2 > 0]                    MMA1: D1[128 x 128] = DZ3[128 x 64] W3
+//   dz1 = (dz2 W2) * [h1 > 0]                    MMA2: D2[128 x 64] = DZ2[128 x 128] W2
+// and the weight gradients, summed over the samples and kept in tensor memory
+// over all tiles of the CTA:
+//   dW3^T[128 in x 64 out] += H2^T[128 x 128 s] DZ3[128 s x 64]     MMA3 (G3)
+//   dW2[128 out x 64 in]    += DZ2^T[128 x 128 s] H1[128 s x 64]     MMA4 (G2)
+// dW1 = dz1^T x, dW4 = h3^T dz4 and the biases (sums of dz over the samples)
+// on CUDA cores, in registers over the tiles.  The MMAs take BF16 operands (dz
+// rounded to BF16; weights and activations are the forward's BF16 values) and
+// accumulate in FP32; every operand is written by the threads into shared
+// memory in the 128-byte swizzled K-major layout of the forward (transposed
+// operands element by element), and every MMA has a shape of the forward's
+// layers 2 and 3 (M 128, N 128 or 64, K 64 or 128).
+constexpr int kBOffDz3 = 0;                      // A  MMA1: 128 samples x 64 (dz3)
+constexpr int kBOffW3t = kBOffDz3 + 16384;       // B  MMA1: 128 (in3) x 64 (out3)
+constexpr int kBOffDz2 = kBOffW3t + 16384;       // A  MMA2: 2 K-blocks x 128 samples x 64 (dz2)
+constexpr int kBOffW2t = kBOffDz2 + 32768;       // B  MMA2: 2 K-blocks x 64 (in2) x 64 (out2)
+constexpr int kBOffH2t = kBOffW2t + 16384;       // A  MMA3: 2 K-blocks x 128 (in3) x 64 samples
+constexpr int kBOffDz3t = kBOffH2t + 32768;      // B  MMA3: 2 K-blocks x 64 (out3) x 64 samples
+constexpr int kBOffDz2t = kBOffDz3t + 16384;     // A  MMA4: 2 K-blocks x 128 (out2) x 64 samples
+constexpr int kBOffH1t = kBOffDz2t + 32768;      // B  MMA4: 2 K-blocks x 64 (in2) x 64 samples
+constexpr int kBRedLd = 129;                     // FP32 [64][129] scratch (column sums over samples)
+constexpr int kBOffRed = kBOffH1t + 16384;
+constexpr int kBOffX = kBOffRed + 64 * kBRedLd * 4;   // FP32 [8][128] features of the tile
+constexpr int kBOffG4 = kBOffX + 8 * 128 * 4;         // FP32 [128] dz4 of the tile
+constexpr int kBOffW4 = kBOffG4 + 128 * 4;            // FP32 [64] W4
+constexpr int kBOffLoss = kBOffW4 + 64 * 4;           // FP32 [4] per-warp loss
+constexpr int kBOffBar = (kBOffLoss + 16 + 127) / 128 * 128;
+constexpr int kBwdTcSmem = kBOffBar + 128 + 1024;
+constexpr uint32_t kBwdTmemCols = 512;   // D1 0..127, D2 128..191, G3 192..255, G2 256..319
 
-// Per sample: dz4 = (sigmoid(z4) - y) / m (mean binary cross-entropy), then
-// dz3 = W4 dz4 * [h3 > 0], dz2 = W3^T dz3 * [h2 > 0], dz1 = W2^T dz2 * [h1 > 0].
-constexpr int kBwdSmem = (64 * 128 * 2 + 64) * 4;
-
-__global__ void __launch_bounds__(128) mlp_bwd_act_kernel(const float* z4, const float* label, int m,
-                                                          const float* wbf, const __nv_bfloat16* h1,
-                                                          const __nv_bfloat16* h2, const __nv_bfloat16* h3,
-                                                          float* dz1, float* dz2, float* dz3, float* dz4,
-                                                          float* loss)
+// element (row r, column k) of a K-major 128-byte-swizzled BF16 operand made
+// of K-blocks of 64 columns, each `blk` bytes: byte offset
+__device__ __forceinline__ int sw128_elem(int r, int k, int blk)
 {
-    extern __shared__ float bsm[];
-    float* sW3 = bsm;                  // [64][128]
-    float* sW2t = bsm + 64 * 128;      // W2 transposed: [in 64][out 128]
-    float* sW4 = bsm + 2 * 64 * 128;   // [64]
-    __shared__ float sl[4];
-    for (int q = threadIdx.x; q < 64 * 128; q += blockDim.x) {
-        sW3[q] = wbf[kW3 + q];
-        const int o = q / 64, i = q % 64;   // W2[o][i]
-        sW2t[i * 128 + o] = wbf[kW2 + q];
-    }
-    for (int q = threadIdx.x; q < 64; q += blockDim.x) sW4[q] = wbf[kW4 + q];
-    __syncthreads();
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    float l = 0.f;
-    if (s < m) {
-        const float z = z4[s], y = label[s];
-        const float p = 1.f / (1.f + __expf(-z));
-        // log(1 + e^-|z|) + max(z, 0) - y z
-        l = log1pf(__expf(-fabsf(z))) + fmaxf(z, 0.f) - y * z;
-        const float g4 = (p - y) / static_cast<float>(m);
-        dz4[s] = g4;
-        float d3[64];
-#pragma unroll
-        for (int c = 0; c < 64; ++c) {
-            d3[c] = __bfloat162float(h3[(size_t)s * 64 + c]) > 0.f ? sW4[c] * g4 : 0.f;
-            dz3[(size_t)s * 64 + c] = d3[c];
-        }
-        for (int i = 0; i < 128; ++i) {
-            float a = 0.f;
-#pragma unroll
-            for (int c = 0; c < 64; ++c) a = fmaf(sW3[c * 128 + i], d3[c], a);
-            dz2[(size_t)s * 128 + i] = __bfloat162float(h2[(size_t)s * 128 + i]) > 0.f ? a : 0.f;
-        }
-        for (int i = 0; i < 64; ++i) {
-            float a = 0.f;
-            for (int o = 0; o < 128; ++o) a = fmaf(sW2t[i * 128 + o], dz2[(size_t)s * 128 + o], a);
-            dz1[(size_t)s * 64 + i] = __bfloat162float(h1[(size_t)s * 64 + i]) > 0.f ? a : 0.f;
-        }
-    }
-    for (int off = 16; off >= 1; off >>= 1) l += __shfl_xor_sync(0xffffffffu, l, off);
-    if ((threadIdx.x & 31) == 0) sl[threadIdx.x >> 5] = l;
-    __syncthreads();
-    if (threadIdx.x == 0) atomicAdd(loss, (sl[0] + sl[1] + sl[2] + sl[3]) / static_cast<float>(m));
+    return (k >> 6) * blk + sw128(r, (k & 63) >> 3) + (k & 7) * 2;
 }
 
-// dW[o][i] += sum over a sample chunk of dz[s][o] * a[s][i]; db[o] += sum dz[s][o].
-// Block: 16 x 16 output tile; grid.z splits the samples.
-template <typename TA>
-__global__ void __launch_bounds__(256) mlp_wgrad_kernel(const float* dz, int O, const TA* a, int I, int m,
-                                                        int chunk, float* dW, float* db)
+__device__ __forceinline__ void st_bf16(uint8_t* base, int off, float v)
 {
-    __shared__ float sdz[64][17];
-    __shared__ float sa[64][17];
-    const int o0 = blockIdx.y * 16, i0 = blockIdx.x * 16;
-    const int to = threadIdx.x / 16, ti = threadIdx.x % 16;
-    const int s0 = blockIdx.z * chunk, s1 = min(m, s0 + chunk);
-    float acc = 0.f, accb = 0.f;
-    for (int sb = s0; sb < s1; sb += 64) {
-        for (int q = threadIdx.x; q < 64 * 16; q += blockDim.x) {
-            const int r = q / 16, c = q % 16, s = sb + r;
-            sdz[r][c] = (s < s1 && o0 + c < O) ? dz[(size_t)s * O + o0 + c] : 0.f;
-            float av = 0.f;
-            if (s < s1 && i0 + c < I) {
-                if constexpr (sizeof(TA) == 2) av = __bfloat162float(a[(size_t)s * I + i0 + c]);
-                else av = __bfloat162float(__float2bfloat16_rn(static_cast<float>(a[(size_t)s * I + i0 + c])));
+    *reinterpret_cast<__nv_bfloat16*>(base + off) = __float2bfloat16_rn(v);
+}
+
+// sum over the 128 samples of row r of a transposed operand (2 K-blocks of blk bytes)
+__device__ __forceinline__ float sum_row_bf16(const uint8_t* base, int r, int blk)
+{
+    float s = 0.f;
+#pragma unroll
+    for (int c16 = 0; c16 < 16; ++c16) {
+        const uint4 q = *reinterpret_cast<const uint4*>(base + (c16 >> 3) * blk + sw128(r, c16 & 7));
+        const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            s += __uint_as_float(w[e] << 16);
+            s += __uint_as_float(w[e] & 0xFFFF0000u);
+        }
+    }
+    return s;
+}
+
+__global__ void __launch_bounds__(kRows, 1)
+    mlp_bwd_kernel(const float* feat, const float* label, int m, const float* wbf, const float* z4,
+                   const __nv_bfloat16* h1, const __nv_bfloat16* h2, const __nv_bfloat16* h3, float* grad,
+                   float* loss, uint32_t* err)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = aligned_smem(smem_raw);
+    uint8_t* sDz3 = smem + kBOffDz3;
+    uint8_t* sW3t = smem + kBOffW3t;
+    uint8_t* sDz2 = smem + kBOffDz2;
+    uint8_t* sW2t = smem + kBOffW2t;
+    uint8_t* sH2t = smem + kBOffH2t;
+    uint8_t* sDz3t = smem + kBOffDz3t;
+    uint8_t* sDz2t = smem + kBOffDz2t;
+    uint8_t* sH1t = smem + kBOffH1t;
+    float* sRed = reinterpret_cast<float*>(smem + kBOffRed);
+    float* sX = reinterpret_cast<float*>(smem + kBOffX);
+    float* sG4 = reinterpret_cast<float*>(smem + kBOffG4);
+    float* sW4 = reinterpret_cast<float*>(smem + kBOffW4);
+    float* sLoss = reinterpret_cast<float*>(smem + kBOffLoss);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kBOffBar);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + kBOffBar + 16);
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const int ntiles = (m + kRows - 1) / kRows;
+    if (static_cast<int>(blockIdx.x) >= ntiles) return;
+
+    // weights: W3^T (B of MMA1: row n = input of layer 3, K = its 64 outputs) and
+    // W2^T (B of MMA2: row n = input of layer 2, K = its 128 outputs), W4
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        float w8[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) w8[q] = wbf[kW3 + (8 * c + q) * 128 + t];
+        *reinterpret_cast<uint4*>(sW3t + sw128(t, c)) =
+            make_uint4(pack_bf16(w8[0], w8[1]), pack_bf16(w8[2], w8[3]), pack_bf16(w8[4], w8[5]),
+                       pack_bf16(w8[6], w8[7]));
+    }
+    if (t < 64) {
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+            float w8[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) w8[q] = wbf[kW2 + (8 * c + q) * 64 + t];
+            *reinterpret_cast<uint4*>(sW2t + (c >> 3) * 8192 + sw128(t, c & 7)) =
+                make_uint4(pack_bf16(w8[0], w8[1]), pack_bf16(w8[2], w8[3]), pack_bf16(w8[4], w8[5]),
+                           pack_bf16(w8[6], w8[7]));
+        }
+        sW4[t] = wbf[kW4 + t];
+    }
+    if (t == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+    }
+    if (warp == 0) tmem_alloc(tslot, kBwdTmemCols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+    const uint32_t lane_base = static_cast<uint32_t>(warp * 32) << 16;
+    const float inv_m = 1.f / static_cast<float>(m);
+
+    // per-thread gradient sums over the tiles: dW1 row o = t & 63, inputs
+    // 4 (t >> 6) .. +3 and (t < 64) b1[o]; b2[t]; t < 64: b3[t]; t >= 64: W4[t - 64], b4
+    const int o1 = t & 63, k1 = 4 * (t >> 6);
+    float gW1[4] = {0.f, 0.f, 0.f, 0.f};
+    float gb1 = 0.f, gb2 = 0.f, gb3w4 = 0.f, gb4 = 0.f, lsum = 0.f;
+    bool first = true;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int s = tile * kRows + t;
+        const bool valid = s < m;
+        // ---- sample t: dz4, dz3, masks; operands of MMA1 and MMA3 ----
+#pragma unroll
+        for (int k = 0; k < 8; ++k) sX[k * 128 + t] = valid ? bf16r(feat[(size_t)s * 8 + k]) : 0.f;
+        float g4 = 0.f;
+        if (valid) {
+            const float z = z4[s], y = label[s];
+            const float p = 1.f / (1.f + __expf(-z));
+            lsum += log1pf(__expf(-fabsf(z))) + fmaxf(z, 0.f) - y * z;
+            g4 = (p - y) * inv_m;
+        }
+        sG4[t] = g4;
+        const uint4* h3r = reinterpret_cast<const uint4*>(h3 + (size_t)(valid ? s : 0) * 64);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const uint4 q = valid ? h3r[c] : make_uint4(0u, 0u, 0u, 0u);
+            const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+            float d8[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const float hv = __uint_as_float(e & 1 ? (w[e >> 1] & 0xFFFF0000u) : (w[e >> 1] << 16));
+                const int col = 8 * c + e;
+                d8[e] = bf16r(hv > 0.f ? sW4[col] * g4 : 0.f);
+                sRed[col * kBRedLd + t] = g4 * hv;                       // for dW4
+                st_bf16(sDz3t, sw128_elem(col, t, 8192), d8[e]);         // B of MMA3: row out3, column sample
             }
-            sa[r][c] = av;
+            *reinterpret_cast<uint4*>(sDz3 + sw128(t, c)) =
+                make_uint4(pack_bf16(d8[0], d8[1]), pack_bf16(d8[2], d8[3]), pack_bf16(d8[4], d8[5]),
+                           pack_bf16(d8[6], d8[7]));
         }
-        __syncthreads();
-#pragma unroll 8
-        for (int r = 0; r < 64; ++r) {
-            acc = fmaf(sdz[r][to], sa[r][ti], acc);
-            accb += sdz[r][to];
+        uint32_t mask2[4] = {0u, 0u, 0u, 0u}, mask1[2] = {0u, 0u};
+        const uint4* h2r = reinterpret_cast<const uint4*>(h2 + (size_t)(valid ? s : 0) * 128);
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+            const uint4 q = valid ? h2r[c] : make_uint4(0u, 0u, 0u, 0u);
+            const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const uint16_t hb = static_cast<uint16_t>(e & 1 ? (w[e >> 1] >> 16) : (w[e >> 1] & 0xFFFFu));
+                const int col = 8 * c + e;
+                mask2[col >> 5] |= (hb != 0 && !(hb & 0x8000u) ? 1u : 0u) << (col & 31);   // h2 > 0
+                *reinterpret_cast<uint16_t*>(sH2t + sw128_elem(col, t, 16384)) = hb;     // A of MMA3
+            }
         }
+        const uint4* h1r = reinterpret_cast<const uint4*>(h1 + (size_t)(valid ? s : 0) * 64);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const uint4 q = valid ? h1r[c] : make_uint4(0u, 0u, 0u, 0u);
+            const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const uint16_t hb = static_cast<uint16_t>(e & 1 ? (w[e >> 1] >> 16) : (w[e >> 1] & 0xFFFFu));
+                const int col = 8 * c + e;
+                mask1[col >> 5] |= (hb != 0 && !(hb & 0x8000u) ? 1u : 0u) << (col & 31);   // h1 > 0
+                *reinterpret_cast<uint16_t*>(sH1t + sw128_elem(col, t, 8192)) = hb;      // B of MMA4
+            }
+        }
+        fence_async_smem();
+        tc_fence_before();
         __syncthreads();
+        // MMA1 (D1 = DZ3 W3) and MMA3 (G3 += H2^T DZ3)
+        if (t == 0) {
+            tc_fence_after();
+            const uint32_t a1 = smem_u32(sDz3), b1 = smem_u32(sW3t);
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks)
+                mma_f16(tmem, sdesc_k_sw128(a1 + ks * 32), sdesc_k_sw128(b1 + ks * 32), kIdescL2, ks > 0 ? 1u : 0u);
+            const uint32_t a3 = smem_u32(sH2t), b3 = smem_u32(sDz3t);
+#pragma unroll
+            for (int kb = 0; kb < 2; ++kb)
+#pragma unroll
+                for (int ks = 0; ks < 4; ++ks)
+                    mma_f16(tmem + 192, sdesc_k_sw128(a3 + kb * 16384 + ks * 32),
+                            sdesc_k_sw128(b3 + kb * 8192 + ks * 32), kIdescL3, (first && kb == 0 && ks == 0) ? 0u : 1u);
+            mma_commit(bar);
+        }
+        __syncwarp();
+        // meanwhile: dW4, b4, b3 column sums of this tile
+        if (t < 64) {
+            gb3w4 += sum_row_bf16(sDz3t, t, 8192);
+        } else {
+            const float* r = sRed + (t - 64) * kBRedLd;
+            float a = 0.f;
+            for (int u = 0; u < 128; ++u) a += r[u];
+            gb3w4 += a;
+            if (t == 64)
+                for (int u = 0; u < 128; ++u) gb4 += sG4[u];
+        }
+        if (!mbar_wait(bar, 0)) atomicOr(err, TR_ERR_TIMEOUT);
+        tc_fence_after();
+        // ---- dz2 = D1 * [h2 > 0]: A of MMA2 (row = sample) and A of MMA4 (row = output of layer 2) ----
+#pragma unroll 1
+        for (int cb = 0; cb < 4; ++cb) {
+            uint32_t acc[32];
+            tmem_ld32(tmem + lane_base + cb * 32, acc);
+            tmem_ld_wait();
+            const uint32_t mk = cb == 0 ? mask2[0] : cb == 1 ? mask2[1] : cb == 2 ? mask2[2] : mask2[3];
+            float dv[32];
+#pragma unroll
+            for (int q = 0; q < 32; ++q) {
+                const int col = cb * 32 + q;
+                dv[q] = bf16r((mk >> q) & 1u ? __uint_as_float(acc[q]) : 0.f);
+                st_bf16(sDz2t, sw128_elem(col, t, 16384), dv[q]);
+            }
+#pragma unroll
+            for (int c4 = 0; c4 < 4; ++c4) {
+                const int k8 = cb * 4 + c4;   // 16-byte chunk over the 128 outputs of layer 2
+                *reinterpret_cast<uint4*>(sDz2 + (k8 >> 3) * 16384 + sw128(t, k8 & 7)) =
+                    make_uint4(pack_bf16(dv[8 * c4 + 0], dv[8 * c4 + 1]), pack_bf16(dv[8 * c4 + 2], dv[8 * c4 + 3]),
+                               pack_bf16(dv[8 * c4 + 4], dv[8 * c4 + 5]), pack_bf16(dv[8 * c4 + 6], dv[8 * c4 + 7]));
+            }
+        }
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        // MMA2 (D2 = DZ2 W2) and MMA4 (G2 += DZ2^T H1)
+        if (t == 0) {
+            tc_fence_after();
+            const uint32_t a2 = smem_u32(sDz2), b2 = smem_u32(sW2t);
+            const uint32_t a4 = smem_u32(sDz2t), b4 = smem_u32(sH1t);
+#pragma unroll
+            for (int kb = 0; kb < 2; ++kb)
+#pragma unroll
+                for (int ks = 0; ks < 4; ++ks)
+                    mma_f16(tmem + 128, sdesc_k_sw128(a2 + kb * 16384 + ks * 32),
+                            sdesc_k_sw128(b2 + kb * 8192 + ks * 32), kIdescL3, (kb | ks) != 0 ? 1u : 0u);
+#pragma unroll
+            for (int kb = 0; kb < 2; ++kb)
+#pragma unroll
+                for (int ks = 0; ks < 4; ++ks)
+                    mma_f16(tmem + 256, sdesc_k_sw128(a4 + kb * 16384 + ks * 32),
+                            sdesc_k_sw128(b4 + kb * 8192 + ks * 32), kIdescL3, (first && kb == 0 && ks == 0) ? 0u : 1u);
+            mma_commit(bar);
+        }
+        __syncwarp();
+        gb2 += sum_row_bf16(sDz2t, t, 16384);   // b2: the 128 samples of output t of layer 2
+        if (!mbar_wait(bar, 1)) atomicOr(err, TR_ERR_TIMEOUT);
+        tc_fence_after();
+        // ---- dz1 = D2 * [h1 > 0] (FP32) -> dW1, b1 on CUDA cores ----
+#pragma unroll 1
+        for (int cb = 0; cb < 2; ++cb) {
+            uint32_t acc[32];
+            tmem_ld32(tmem + lane_base + 128 + cb * 32, acc);
+            tmem_ld_wait();
+            const uint32_t mk = cb == 0 ? mask1[0] : mask1[1];
+#pragma unroll
+            for (int q = 0; q < 32; ++q)
+                sRed[(cb * 32 + q) * kBRedLd + t] = (mk >> q) & 1u ? __uint_as_float(acc[q]) : 0.f;
+        }
+        tc_fence_before();
+        __syncthreads();   // sRed holds dz1 (rows: outputs of layer 1); tensor memory D1, D2 read
+        {
+            const float* r = sRed + o1 * kBRedLd;
+            for (int u = 0; u < 128; ++u) {
+                const float a = r[u];
+                if (t < 64) gb1 += a;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) gW1[k] = fmaf(a, sX[(k1 + k) * 128 + u], gW1[k]);
+            }
+        }
+        __syncthreads();   // the tile's shared operands and scratch are consumed
+        first = false;
     }
-    if (o0 + to < O && i0 + ti < I) atomicAdd(&dW[(o0 + to) * I + i0 + ti], acc);
-    if (blockIdx.x == 0 && ti == 0 && o0 + to < O) atomicAdd(&db[o0 + to], accb);
+    // ---- the CTA's sums into the global gradient ----
+#pragma unroll
+    for (int k = 0; k < 4; ++k) atomicAdd(&grad[kW1 + o1 * 8 + k1 + k], gW1[k]);
+    if (t < 64) {
+        atomicAdd(&grad[kB1 + t], gb1);
+        atomicAdd(&grad[kB3 + t], gb3w4);
+    } else {
+        atomicAdd(&grad[kW4 + t - 64], gb3w4);
+        if (t == 64) atomicAdd(&grad[kB4], gb4);
+    }
+    atomicAdd(&grad[kB2 + t], gb2);
+    tc_fence_after();
+#pragma unroll 1
+    for (int cb = 0; cb < 2; ++cb) {
+        uint32_t g3[32], g2[32];
+        tmem_ld32(tmem + lane_base + 192 + cb * 32, g3);   // dW3[out = column][in = t]
+        tmem_ld32(tmem + lane_base + 256 + cb * 32, g2);   // dW2[out = t][in = column]
+        tmem_ld_wait();
+#pragma unroll
+        for (int q = 0; q < 32; ++q) {
+            atomicAdd(&grad[kW3 + (cb * 32 + q) * 128 + t], __uint_as_float(g3[q]));
+            atomicAdd(&grad[kW2 + t * 64 + cb * 32 + q], __uint_as_float(g2[q]));
+        }
+    }
+    for (int off = 16; off >= 1; off >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, off);
+    if (lane == 0) sLoss[warp] = lsum;
+    tc_fence_before();
+    __syncthreads();
+    if (t == 0) atomicAdd(loss, (sLoss[0] + sLoss[1] + sLoss[2] + sLoss[3]) * inv_m);
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, kBwdTmemCols);
+    }
 }
 
-// dW4[c] += sum dz4 h3[c]; db4 += sum dz4 (one block per 1024-sample chunk)
-__global__ void __launch_bounds__(256) mlp_wgrad4_kernel(const float* dz4, const __nv_bfloat16* h3, int m,
-                                                         float* g)
-{
-    __shared__ float acc[65];
-    if (threadIdx.x < 65) acc[threadIdx.x] = 0.f;
-    __syncthreads();
-    const int s0 = blockIdx.x * 1024;
-    for (int q = threadIdx.x; q < 1024 * 65; q += blockDim.x) {
-        const int r = q / 65, c = q % 65, s = s0 + r;
-        if (s >= m) continue;
-        const float d = dz4[s];
-        atomicAdd(&acc[c], c < 64 ? d * __bfloat162float(h3[(size_t)s * 64 + c]) : d);
-    }
-    __syncthreads();
-    if (threadIdx.x < 64) atomicAdd(&g[kW4 + threadIdx.x], acc[threadIdx.x]);
-    if (threadIdx.x == 64) atomicAdd(&g[kB4], acc[64]);
-}
+// ---------------- training: Adam (CUDA cores) ----------------
 
 // Adam (bias-corrected), FP32 master weights; the forward's BF16-rounded copy
 // is refreshed from them.
@@ -509,7 +736,7 @@ cudaError_t mlp_setup()
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(mlp_proposal_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kFwdSmem);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(mlp_bwd_act_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kBwdSmem);
+        e = cudaFuncSetAttribute(mlp_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kBwdTcSmem);
     return e;
 }
 
@@ -536,18 +763,13 @@ void launch_mlp_forward(const float* feat, int m, const float* wbf, float* prob,
 }
 
 void launch_mlp_backward(const float* feat, const float* label, int m, const float* wbf, const float* z4,
-                         const __nv_bfloat16* h1, const __nv_bfloat16* h2, const __nv_bfloat16* h3, float* dz1,
-                         float* dz2, float* dz3, float* dz4, float* grad, float* loss, cudaStream_t s)
+                         const __nv_bfloat16* h1, const __nv_bfloat16* h2, const __nv_bfloat16* h3, float* grad,
+                         float* loss, uint32_t* err, cudaStream_t s)
 {
-    mlp_bwd_act_kernel<<<(m + 127) / 128, 128, kBwdSmem, s>>>(z4, label, m, wbf, h1, h2, h3, dz1, dz2, dz3, dz4,
-                                                               loss);
-    const int chunk = 4096;
-    const int zc = (m + chunk - 1) / chunk;
-    // layer 1: dW1 [64][8] from dz1 and the (BF16-rounded) features
-    mlp_wgrad_kernel<float><<<dim3(1, 4, zc), 256, 0, s>>>(dz1, 64, feat, 8, m, chunk, grad + kW1, grad + kB1);
-    mlp_wgrad_kernel<__nv_bfloat16><<<dim3(4, 8, zc), 256, 0, s>>>(dz2, 128, h1, 64, m, chunk, grad + kW2, grad + kB2);
-    mlp_wgrad_kernel<__nv_bfloat16><<<dim3(8, 4, zc), 256, 0, s>>>(dz3, 64, h2, 128, m, chunk, grad + kW3, grad + kB3);
-    mlp_wgrad4_kernel<<<(m + 1023) / 1024, 256, 0, s>>>(dz4, h3, m, grad);
+    const int ntiles = (m + kRows - 1) / kRows;
+    const int sms = device_sms();
+    const int grid = ntiles < sms ? ntiles : sms;   // one CTA per SM (shared memory and tensor memory)
+    mlp_bwd_kernel<<<grid, kRows, kBwdTcSmem, s>>>(feat, label, m, wbf, z4, h1, h2, h3, grad, loss, err);
 }
 
 void launch_mlp_adam(float* w, float* mom, float* vel, const float* g, float* wbf, int step, float lr,

@@ -32,7 +32,6 @@ struct turboreg_mlp {
     uint32_t* err = nullptr;
     float* z4 = nullptr;     // [max_samples]
     __nv_bfloat16 *h1 = nullptr, *h2 = nullptr, *h3 = nullptr;
-    float *dz1 = nullptr, *dz2 = nullptr, *dz3 = nullptr, *dz4 = nullptr;
 };
 
 namespace {
@@ -48,8 +47,7 @@ namespace {
 
 void free_all(turboreg_mlp* t)
 {
-    void* ptrs[] = {t->w, t->wbf, t->mom, t->vel, t->grad, t->loss, t->err, t->z4, t->h1, t->h2, t->h3,
-                    t->dz1, t->dz2, t->dz3, t->dz4};
+    void* ptrs[] = {t->w, t->wbf, t->mom, t->vel, t->grad, t->loss, t->err, t->z4, t->h1, t->h2, t->h3};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -60,8 +58,7 @@ int backward(turboreg_mlp* t, const float* feat, const float* label, int32_t m)
     TM_CHECK(cudaMemsetAsync(t->grad, 0, sizeof(float) * kMlpParams, t->stream));
     TM_CHECK(cudaMemsetAsync(t->loss, 0, sizeof(float), t->stream));
     launch_mlp_forward(feat, m, t->wbf, nullptr, t->z4, t->h1, t->h2, t->h3, t->err, t->stream);
-    launch_mlp_backward(feat, label, m, t->wbf, t->z4, t->h1, t->h2, t->h3, t->dz1, t->dz2, t->dz3, t->dz4, t->grad,
-                        t->loss, t->stream);
+    launch_mlp_backward(feat, label, m, t->wbf, t->z4, t->h1, t->h2, t->h3, t->grad, t->loss, t->err, t->stream);
     TM_CHECK(cudaGetLastError());
     return TURBOREG_OK;
 }
@@ -95,10 +92,6 @@ int turboreg_mlp_create(int device, int32_t max_samples, uint64_t seed, void* cu
     al(reinterpret_cast<void**>(&t->h1), sizeof(__nv_bfloat16) * M * 64);
     al(reinterpret_cast<void**>(&t->h2), sizeof(__nv_bfloat16) * M * 128);
     al(reinterpret_cast<void**>(&t->h3), sizeof(__nv_bfloat16) * M * 64);
-    al(reinterpret_cast<void**>(&t->dz1), sizeof(float) * M * 64);
-    al(reinterpret_cast<void**>(&t->dz2), sizeof(float) * M * 128);
-    al(reinterpret_cast<void**>(&t->dz3), sizeof(float) * M * 64);
-    al(reinterpret_cast<void**>(&t->dz4), sizeof(float) * M);
     if (e == cudaSuccess) e = mlp_setup();
     if (e == cudaSuccess) {
         if (cuda_stream) t->stream = static_cast<cudaStream_t>(cuda_stream);
@@ -213,10 +206,12 @@ int turboreg_mlp_grad(turboreg_mlp* t, const float* feat, const float* label, in
     if (rc != TURBOREG_OK) return rc;
     TM_CHECK(cudaMemcpyAsync(grad, t->grad, sizeof(float) * kMlpParams, cudaMemcpyDeviceToHost, t->stream));
     float l = 0.f;
+    uint32_t err = 0;
     TM_CHECK(cudaMemcpyAsync(&l, t->loss, sizeof(float), cudaMemcpyDeviceToHost, t->stream));
+    TM_CHECK(cudaMemcpyAsync(&err, t->err, sizeof(uint32_t), cudaMemcpyDeviceToHost, t->stream));
     TM_CHECK(cudaStreamSynchronize(t->stream));
     if (loss) *loss = l;
-    return TURBOREG_OK;
+    return err ? TURBOREG_ERR_TIMEOUT : TURBOREG_OK;
 }
 
 int turboreg_mlp_train_step(turboreg_mlp* t, const float* feat, const float* label, int32_t m, float lr,

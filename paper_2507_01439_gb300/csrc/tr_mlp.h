@@ -27,8 +27,8 @@ void launch_mlp_proposal(const Batch& b, int total, const float* wbf, cudaStream
 void launch_mlp_forward(const float* feat, int m, const float* wbf, float* prob, float* z4, __nv_bfloat16* h1,
                         __nv_bfloat16* h2, __nv_bfloat16* h3, uint32_t* err, cudaStream_t s);
 void launch_mlp_backward(const float* feat, const float* label, int m, const float* wbf, const float* z4,
-                         const __nv_bfloat16* h1, const __nv_bfloat16* h2, const __nv_bfloat16* h3, float* dz1,
-                         float* dz2, float* dz3, float* dz4, float* grad, float* loss, cudaStream_t s);
+                         const __nv_bfloat16* h1, const __nv_bfloat16* h2, const __nv_bfloat16* h3, float* grad,
+                         float* loss, uint32_t* err, cudaStream_t s);
 void launch_mlp_adam(float* w, float* mom, float* vel, const float* g, float* wbf, int step, float lr,
                      cudaStream_t s);
 void launch_learned_hist(const Batch& b, int total, int max_n, cudaStream_t s);
