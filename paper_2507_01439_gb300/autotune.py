@@ -26,7 +26,7 @@ from dataclasses import asdict, dataclass, field
 
 import numpy as np
 
-from . import (FLAG_SC2_SINGLE_CTA, FLAG_VERIFY_PTS32, FLAG_VERIFY_PTS128, TurboReg,
+from . import (FLAG_SC2_BITSET, FLAG_SC2_SINGLE_CTA, FLAG_VERIFY_PTS32, FLAG_VERIFY_PTS128, TurboReg,
                default_params)
 
 TILE_CANDIDATES = {
@@ -35,6 +35,7 @@ TILE_CANDIDATES = {
     "sc2_pair+verify512": FLAG_VERIFY_PTS128,
     "sc2_single+verify256": FLAG_SC2_SINGLE_CTA,
     "sc2_single+verify512": FLAG_SC2_SINGLE_CTA | FLAG_VERIFY_PTS128,
+    "sc2_bitset+verify256": FLAG_SC2_BITSET,
 }
 
 

@@ -32,4 +32,4 @@ def test_schedule_lookup_and_json():
 
 def test_tile_candidates_are_distinct_flag_sets():
     vals = list(autotune.TILE_CANDIDATES.values())
-    assert len(set(vals)) == len(vals) == 5
+    assert len(set(vals)) == len(vals) == 6
