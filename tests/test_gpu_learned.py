@@ -72,6 +72,26 @@ def test_gradient_matches_oracle(torch):
     t.close()
 
 
+def test_gradient_many_tiles_matches_oracle(torch):
+    # more 128-sample tiles than CTAs and a ragged last tile: the tensor-core
+    # backward accumulates its weight gradients over several tiles per CTA
+    m = 60_000 + 37
+    f, lab = _rand_feat(m, 5)
+    t = trg.MLPTrainer(max_samples=m, seed=6)
+    th = t.get_params().astype(np.float64)
+    g, loss = t.grad(torch.from_numpy(f).cuda(), torch.from_numpy(lab).cuda())
+    gw, lw = omlp.grad(th, f, lab, bf16_round=True)
+    assert abs(loss - lw) < 1e-3 * max(1.0, abs(lw))
+    o = 0
+    for name, shape in omlp.SIZES:
+        k = int(np.prod(shape))
+        a, b = g[o:o + k].astype(np.float64), gw[o:o + k]
+        rel = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-12)
+        assert rel <= 1e-2, (name, rel)
+        o += k
+    t.close()
+
+
 def test_training_reduces_loss_and_resumes(torch, tmp_path):
     from paper_2507_01439_gb300 import train_proposal as tp
     feat, label = tp.make_samples(120, base_seed=9, log=None)

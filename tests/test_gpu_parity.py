@@ -210,6 +210,32 @@ def test_deterministic_repeats(ctx):
     assert np.array_equal(ctx.buffer(trg.BUF_SC2)[:n, :n][iu], W0[:n, :n][iu])
 
 
+def test_bitset_sc2_many_small_problems():
+    # the CUDA-core SC^2 over a batch of small problems: a CTA's run of work
+    # units crosses many problems (one to four tiles each), so problem changes,
+    # histogram flushes and the per-problem descriptors are exercised; the
+    # results equal the tensor-core GEMM's batch, and single calls on the same
+    # path give the oracle's stage buffers
+    sizes = [3, 17, 64, 65, 128, 200, 256, 257, 300, 511, 512, 640] * 4
+    probs = [synth.make_problem(("indoor", "outdoor", "cube")[b % 3], n, 0.2, 300 + b)
+             for b, n in enumerate(sizes)]
+    offs = np.cumsum([0] + [p.n for p in probs]).astype(np.int64)
+    xs = np.concatenate([p.x for p in probs])
+    ys = np.concatenate([p.y for p in probs])
+    with trg.TurboReg(max_n=640, max_batch=len(probs)) as c:
+        ref = c.register_batched(xs, ys, offs, [trg.default_params(p.tau, min(p.k1, 100), p.theta) for p in probs])
+        out = c.register_batched(xs, ys, offs, [trg.default_params(p.tau, min(p.k1, 100), p.theta,
+                                                                    flags=trg.FLAG_SC2_BITSET) for p in probs])
+        for a, b in zip(ref, out):
+            assert a.status == b.status and a.hypothesis == b.hypothesis and a.n_pivots == b.n_pivots
+            assert np.array_equal(a.R, b.R) and np.array_equal(a.t, b.t) and a.inlier_count == b.inlier_count
+        for k in (0, 1, 7, 10, 11):   # single calls on the same path: the stage buffers against the oracle
+            p = probs[k]
+            c.register(p.x, p.y, trg.default_params(p.tau, min(p.k1, 100), p.theta, flags=trg.FLAG_SC2_BITSET))
+            A, S, _, _ = oracle_stages(p.x, p.y, p.tau, 100, 2)
+            check_graph_stages(c, A, S, p.n)
+
+
 def test_batched_equals_plain(ctx):
     probs = [synth.make_problem(s, n, r, 50 + b) for b, (s, n, r) in
              enumerate([("indoor", 1200, 0.1), ("outdoor", 900, 0.2), ("indoor", 3000, 0.05),
