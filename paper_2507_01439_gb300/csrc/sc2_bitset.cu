@@ -89,30 +89,27 @@ __device__ __forceinline__ void record_edge(uint16_t* tile, int* rsum, int* rmax
 
 // ---------------------------------------------------------------------------
 // Lane form (N_pad <= 5120).  Work units are quarters of the tiles: 128 rows
-// i by 64 columns j, taken by a CTA of 16 warps as a contiguous run in row-
-// block-major order.  Its 128 bitset rows i (one bulk copy, about once per
-// CTA) and the 64 rows j of two units (one bulk copy each, double-buffered)
-// are in shared memory.  Each unit's edges (i < j, ordered by column, then
-// row) are listed one unit ahead, in a double-buffered list; the list is cut
-// into 64 equal runs, one per group of 8 lanes.  A group computes
-// popc(row_i & row_j) for one edge at a time with 20 words per lane (8 lanes
-// x 5 uint4 = 160 words; lane l of the group reads uint4 l + 8k, so the 8
-// lanes of a shared-memory phase hit distinct banks), keeps row j in
-// registers while consecutive edges share it and adds the lanes' counts with
-// three shuffles; lane 0 of the group stores the weight into W and adds it to
-// the row and column sums, the row maximum and the histogram in shared memory.
-// One CTA barrier per unit: before it, warps 0-7 count the next unit's edges
-// from its adjacency words (loaded from global memory a unit earlier); after
-// it, they write that list, one lane issues the next unit's rows j, the
-// finished unit's column sums go to global memory, and every thread writes
-// zeros over a part of the W block of the unit after next (the weights are
-// stored over them two barriers later).  kCsa: a lane's 20 words are first
-// added bit-sliced through a carry-save adder tree (full adders, 28 logic
-// operations), leaving six words of weights 1, 2, 4 and 8 for the population
-// count, so that the logic pipe takes most of the work of the slower
-// population-count pipe.  A unit's time varies little with its number of
-// edges (a split of the units by edge count was measured slower), so a CTA
-// takes an equal number of units.
+// i by 64 columns j, an equal contiguous run of them per CTA of 16 warps (a
+// unit's time varies little with its number of edges; a split by edge count
+// was measured slower).  The CTA's 128 bitset rows i (one bulk copy, about
+// once per CTA) are in shared memory.  The CTA works as two halves of 8
+// warps that take alternate units, each with its own buffer of 64 rows j (one
+// bulk copy per unit) and its own edge list, synchronised by its own named
+// barrier, so that one half's preparation of a unit (the copy, zeros over the
+// unit's W block, the list) overlaps the other half's edge work; the halves
+// meet only where a new row block begins, to exchange the rows i.  A unit's
+// edges (i < j, ordered by column, then row) are listed from the adjacency
+// words of its columns, the list cut into 32 equal runs, one per group of 8
+// lanes of the half.  A group computes popc(row_i & row_j) for one edge at a
+// time with 20 words per lane (8 lanes x 5 uint4 = 160 words; lane l of the
+// group reads uint4 l + 8k, so the 8 lanes of a shared-memory phase hit
+// distinct banks), keeps row j in registers while consecutive edges share
+// it, and adds the lanes' counts with three shuffles; lane 0 of the group
+// stores the weight into W and adds it to the row and column sums, the row
+// maximum and the histogram in shared memory.  kCsa: a lane's 20 words are
+// first added bit-sliced through a carry-save adder tree (full adders, 28
+// logic operations), leaving six words of weights 1, 2, 4 and 8 for the
+// population count.
 // ---------------------------------------------------------------------------
 constexpr int kLUC = 64;                    // columns of a unit
 constexpr int kLWarps = 16;
@@ -120,7 +117,6 @@ constexpr int kLThreads = 32 * kLWarps;
 constexpr int kLGroups = kLThreads / 8;     // groups of 8 lanes, one edge at a time each
 constexpr int kLMaxLdb = 160;
 constexpr int kLList = kBT * kLUC;          // list capacity of a unit (every pair an edge)
-constexpr int kLCountThreads = kLUC * 4;    // listing: one thread per column and 32-row word
 
 __host__ __device__ inline size_t lane_smem_bytes(int ldb_max, int hist_bins)
 {
@@ -253,15 +249,16 @@ __global__ void __launch_bounds__(kLThreads, 1)
     uint16_t* slist = reinterpret_cast<uint16_t*>(q8);  q8 += static_cast<size_t>(2 * kLList) * 2;
     int* srsum = reinterpret_cast<int*>(q8);            q8 += kBT * 4;
     int* srmax = reinterpret_cast<int*>(q8);            q8 += kBT * 4;
-    int* scsum = reinterpret_cast<int*>(q8);            q8 += 2 * kLUC * 4;   // [unit parity][column]
-    uint64_t* bars = reinterpret_cast<uint64_t*>(q8);   q8 += 32;            // rows i, rows j [2]
-    int* sw = reinterpret_cast<int*>(q8);               q8 += 128;           // list scans: [parity][warp]
+    int* scsum = reinterpret_cast<int*>(q8);            q8 += 2 * kLUC * 4;   // [half][column]
+    uint64_t* bars = reinterpret_cast<uint64_t*>(q8);   q8 += 32;            // rows i, rows j [half]
+    int* sw = reinterpret_cast<int*>(q8);               q8 += 128;           // list scans: [half][warp of half]
     LaneView* lv = reinterpret_cast<LaneView*>(q8);     q8 += 256;           // [problem & 3]
     uint32_t* shist = reinterpret_cast<uint32_t*>(q8);
     uint64_t* rows_full = bars;
     uint64_t* cols_full = bars + 1;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int grp = tid >> 3, gl = tid & 7;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int half = tid >> 8, ht = tid & 255, hwarp = ht >> 5;   // two halves of 8 warps
+    const int grp = ht >> 3, gl = tid & 7;                          // groups of 8 lanes within the half
     if (tid < 3) mbar_init(&bars[tid], 1);
     if (tid == 0) fence_mbar_init();
     for (int b = tid; b < hist_bins; b += kLThreads) shist[b] = 0u;
@@ -270,17 +267,20 @@ __global__ void __launch_bounds__(kLThreads, 1)
         srmax[tid] = 0;
     }
     if (tid < 2 * kLUC) scsum[tid] = 0;
-    __syncthreads();
-    pdl_wait();
-    pdl_release();
     // this CTA's units: a contiguous run (the time of a unit varies little with its edges)
     const int units = 4 * total;
     const int u0 = static_cast<int>((static_cast<long long>(units) * blockIdx.x) / gridDim.x);
     const int u1 = static_cast<int>((static_cast<long long>(units) * (blockIdx.x + 1)) / gridDim.x);
+    pdl_wait();
+    pdl_release();
     if (u0 >= u1) return;
+    LaneUnit cur = lane_unit(bt, u0), prev = cur;
+    if (tid == 0) lane_view_load(lv[cur.p & 3], bt.views[cur.p]);
+    __syncthreads();
     const int K = u1 - u0;
     bool ok = true;
 
+    auto half_sync = [&]() { asm volatile("bar.sync %0, 256;" ::"r"(1 + half) : "memory"); };
     auto issue_cols = [&](const LaneUnit& un, int slot) {
         const LaneView& v = lv[un.p & 3];
         const uint32_t bytes = static_cast<uint32_t>(kLUC * v.ldb * 4);
@@ -294,134 +294,92 @@ __global__ void __launch_bounds__(kLThreads, 1)
         mbar_arrive_expect_tx(rows_full, bytes);
         bulk_g2s(srows, v.bits + static_cast<size_t>(un.i0) * v.ldb, bytes, rows_full);
     };
-    // zeros over a unit's W block (128 rows x 128 B)
-    auto zero_w = [&](const LaneUnit& un) {
-        const LaneView& v = lv[un.p & 3];
-        for (int q = tid; q < kBT * kLUC / 8; q += kLThreads)
-            *reinterpret_cast<uint4*>(v.w + static_cast<size_t>(un.i0 + (q >> 3)) * v.n_pad + un.j0 + (q & 7) * 8) =
+    auto flush_rows = [&](const LaneUnit& un, bool hist) {   // a finished row block (and problem)
+        const LaneView& pv = lv[un.p & 3];
+        if (tid < kBT) {
+            const int x = srsum[tid], mx = srmax[tid];
+            if (x) atomicAdd(&pv.rowscore[un.i0 + tid], x);
+            if (mx && pv.rowmax) atomicMax(&pv.rowmax[un.i0 + tid], mx);
+            srsum[tid] = 0;
+            srmax[tid] = 0;
+        }
+        if (hist && hist_bins > 0) lane_flush_hist(pv, shist, tid);
+    };
+    if (tid == 0) issue_rows(cur);
+    uint32_t rows_uses = 0, cols_uses = 0;   // this half's uses of its rows-j buffer
+    // Every thread walks all units in order; half h takes the units k with
+    // k % 2 == h.  The halves meet only where a new row block begins (both
+    // have finished every earlier unit there), to exchange the rows i.
+    for (int k = 0; k < K; ++k) {
+        if (k > 0) cur = lane_next(prev, lv[prev.p & 3].n_pad);
+        const bool new_rows = k > 0 && (cur.p != prev.p || cur.i0 != prev.i0);
+        if (new_rows) {
+            __syncthreads();   // both halves are past every unit of the old row block
+            flush_rows(prev, cur.p != prev.p);
+            if (tid == 0) {
+                if (cur.p != prev.p) lane_view_load(lv[cur.p & 3], bt.views[cur.p]);
+                fence_proxy_async();
+                issue_rows(cur);
+            }
+            __syncthreads();   // the old block's sums are taken; the new problem's fields are in place
+        }
+        if (k == 0 || new_rows) {
+            ok &= mbar_wait(rows_full, rows_uses & 1u);
+            ++rows_uses;
+        }
+        prev = cur;
+        if ((k & 1) != half) continue;
+        // ---------------- unit k, by this half ----------------
+        const LaneView& v = lv[cur.p & 3];
+        const int slot = half;
+        if (ht == 0) {
+            fence_proxy_async();   // the buffer's previous rows were read by this half's threads
+            issue_cols(cur, slot);
+        }
+        // zeros over the unit's W block (the weights are stored over them after the next barrier)
+        for (int q = ht; q < kBT * kLUC / 8; q += 256)
+            *reinterpret_cast<uint4*>(v.w + static_cast<size_t>(cur.i0 + (q >> 3)) * v.n_pad + cur.j0 + (q & 7) * 8) =
                 make_uint4(0u, 0u, 0u, 0u);
-    };
-    // listing, thread t < 256: column jl = t / 4, rows 32 (t % 4) .. +31 of the unit
-    auto mask_word = [&](const LaneUnit& un) -> uint32_t {
-        const LaneView& v = lv[un.p & 3];
-        const int jl = tid >> 2, h = tid & 3;
-        const int j = un.j0 + jl;
-        const uint32_t w = __ldg(v.bits + static_cast<size_t>(j) * v.ldb + (un.i0 >> 5) + h);
-        const int lh = (j < v.n ? j - un.i0 : 0) - 32 * h;   // rows 32 h + r, r < lh
-        return lh <= 0 ? 0u : lh < 32 ? w & ((1u << lh) - 1u) : w;
-    };
-    // warps 0-7: counts and warp scan of a list (totals in sw[par][warp]); returns the inclusive count
-    auto list_count = [&](uint32_t m, int par) -> int {
-        const int cnt = __popc(m);
-        int inc = cnt;
+        // the unit's edges: thread ht takes column j0 + ht / 4, rows 32 (ht % 4) .. +31
+        uint32_t m;
+        {
+            const int jl = ht >> 2, h = ht & 3;
+            const int j = cur.j0 + jl;
+            const uint32_t w = __ldg(v.bits + static_cast<size_t>(j) * v.ldb + (cur.i0 >> 5) + h);
+            const int lh = (j < v.n ? j - cur.i0 : 0) - 32 * h;   // rows 32 h + r, r < lh
+            m = lh <= 0 ? 0u : lh < 32 ? w & ((1u << lh) - 1u) : w;
+        }
+        int inc = __popc(m);
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
             const int y = __shfl_up_sync(0xffffffffu, inc, off);
             if (lane >= off) inc += y;
         }
-        if (lane == 31) sw[par * 16 + warp] = inc;
-        return inc;
-    };
-    // after the barrier: the list's entries (warps 0-7) and its total (all threads)
-    auto list_write = [&](uint32_t m, int inc, int par, uint16_t* lst) -> int {
-        int base = inc - __popc(m), E = 0;
+        if (lane == 31) sw[half * 8 + hwarp] = inc;
+        half_sync();
+        int E = 0, base = inc - __popc(m);
 #pragma unroll
-        for (int w = 0; w < kLCountThreads / 32; ++w) {
-            const int x = sw[par * 16 + w];
-            if (w < warp) base += x;
+        for (int w = 0; w < 8; ++w) {
+            const int x = sw[half * 8 + w];
+            if (w < hwarp) base += x;
             E += x;
         }
-        if (tid < kLCountThreads) {
-            const int jl = tid >> 2, h = tid & 3;
+        uint16_t* lst = slist + slot * kLList;
+        {
+            const int jl = ht >> 2, h = ht & 3;
             for (; m; m &= m - 1u) lst[base++] = static_cast<uint16_t>((jl << 7) | (32 * h + __ffs(m) - 1));
         }
-        return E;
-    };
-
-    uint32_t rows_uses = 0;
-    LaneUnit cur = lane_unit(bt, u0), prev = cur;
-    LaneUnit nxt = K > 1 ? lane_next(cur, bt.views[cur.p].n_pad) : cur;
-    LaneUnit ahead = K > 2 ? lane_next(nxt, bt.views[nxt.p].n_pad) : nxt;   // unit k + 2
-    if (tid == 0) {
-        lane_view_load(lv[cur.p & 3], bt.views[cur.p]);
-        if (nxt.p != cur.p) lane_view_load(lv[nxt.p & 3], bt.views[nxt.p]);
-        if (ahead.p != nxt.p) lane_view_load(lv[ahead.p & 3], bt.views[ahead.p]);
-    }
-    __syncthreads();
-    if (tid == 0) {
-        issue_rows(cur);
-        issue_cols(cur, 0);
-    }
-    zero_w(cur);
-    if (K > 1) zero_w(nxt);
-    // the first unit's list
-    uint32_t m = tid < kLCountThreads ? mask_word(cur) : 0u;
-    int inc = tid < kLCountThreads ? list_count(m, 1) : 0;
-    __syncthreads();
-    int E = list_write(m, inc, 1, slist);
-    m = (tid < kLCountThreads && K > 1) ? mask_word(nxt) : 0u;   // the next unit's words, ahead of use
-    for (int k = 0; k < K; ++k) {
-        const int slot = k & 1, par = k & 1;
-        // ---- count the next unit's edges, then the unit barrier ----
-        if (k + 1 < K && tid < kLCountThreads) inc = list_count(m, par);
-        __syncthreads();   // unit k-1's items, unit k's list and zeros are complete; the next list's counts are in
-        const bool new_rows = k > 0 && (cur.p != prev.p || cur.i0 != prev.i0);
-        if (tid == kLThreads - 32) {
-            // the bulk copies, from a thread with no memory operation of its own in flight
-            // (the proxy fence would wait for them)
-            if (new_rows) {
-                fence_proxy_async();
-                issue_rows(cur);
-            }
-            if (k + 1 < K) {
-                fence_proxy_async();
-                issue_cols(nxt, slot ^ 1);   // its buffer held unit k-1
-            }
-        }
-        if (k > 0) {
-            // unit k-1: column sums; at a new row block its row sums and maxima (and histogram)
-            const LaneView& pv = lv[prev.p & 3];
-            if (tid < kLUC) {
-                int* cs = scsum + ((k - 1) & 1) * kLUC;
-                const int x = cs[tid];
-                if (x) atomicAdd(&pv.rowscore[prev.j0 + tid], x);
-                cs[tid] = 0;
-            }
-            if (new_rows) {
-                const int r = tid - kLUC;
-                if (r >= 0 && r < kBT) {
-                    const int x = srsum[r], mx = srmax[r];
-                    if (x) atomicAdd(&pv.rowscore[prev.i0 + r], x);
-                    if (mx && pv.rowmax) atomicMax(&pv.rowmax[prev.i0 + r], mx);
-                    srsum[r] = 0;
-                    srmax[r] = 0;
-                }
-                if (cur.p != prev.p && hist_bins > 0) lane_flush_hist(pv, shist, tid);
-            }
-        }
-        int E_next = 0;
-        if (k + 1 < K) E_next = list_write(m, inc, par, slist + (slot ^ 1) * kLList);
-        if (k + 2 < K) {
-            zero_w(ahead);
-            if (tid < kLCountThreads) m = mask_word(ahead);
-        }
-        if (new_rows) __syncthreads();   // the old row block's sums are taken before the new block's additions
-        // ---- unit k's edges: group grp takes list entries [lo, hi) ----
-        ok &= mbar_wait(&cols_full[slot], static_cast<uint32_t>(k >> 1) & 1u);
-        if (k == 0 || new_rows) {
-            ok &= mbar_wait(rows_full, rows_uses & 1u);
-            ++rows_uses;
-        }
+        half_sync();   // the list and the zeros are complete
+        ok &= mbar_wait(&cols_full[slot], cols_uses & 1u);
+        ++cols_uses;
         {
-            const LaneView& v = lv[cur.p & 3];
             const int ldb = v.ldb;
             const int l4 = ldb >> 2;
-            const int lo = (grp * E) / kLGroups, hi = ((grp + 1) * E) / kLGroups;
+            const int lo = (grp * E) / (kLGroups / 2), hi = ((grp + 1) * E) / (kLGroups / 2);
             const int cnt = hi - lo;
             const int T = static_cast<int>(__reduce_max_sync(0xffffffffu, static_cast<unsigned>(cnt)));
             const uint32_t* cols = scols + static_cast<size_t>(slot) * kLUC * ldb_max;
-            const uint16_t* lst = slist + slot * kLList;
-            int* csum = scsum + par * kLUC;
+            int* csum = scsum + half * kLUC;
             uint32_t* hh = hist_bins > 0 ? shist : v.hist;
             uint16_t* wblk = v.w + static_cast<size_t>(cur.i0) * v.n_pad + cur.j0;
             const int e_last = cnt > 0 ? hi - 1 : 0;
@@ -459,31 +417,16 @@ __global__ void __launch_bounds__(kLThreads, 1)
                 }
             }
         }
-        E = E_next;
-        prev = cur;
-        cur = nxt;
-        nxt = ahead;
-        if (k + 3 < K) {
-            const int pa = ahead.p;
-            ahead = lane_next(ahead, lv[pa & 3].n_pad);
-            if (tid == 0 && ahead.p != pa) lane_view_load(lv[ahead.p & 3], bt.views[ahead.p]);   // seen after the next barrier
+        half_sync();   // the unit's items are done: its buffers are free, its column sums complete
+        if (ht < kLUC) {
+            int* cs = scsum + half * kLUC;
+            const int x = cs[ht];
+            if (x) atomicAdd(&v.rowscore[cur.j0 + ht], x);
+            cs[ht] = 0;
         }
     }
     __syncthreads();
-    {
-        // the last unit's column sums, its row block's sums and maxima, its problem's histogram
-        const LaneView& pv = lv[prev.p & 3];
-        if (tid < kLUC) {
-            const int x = scsum[((K - 1) & 1) * kLUC + tid];
-            if (x) atomicAdd(&pv.rowscore[prev.j0 + tid], x);
-        }
-        const int r = tid - kLUC;
-        if (r >= 0 && r < kBT) {
-            if (srsum[r]) atomicAdd(&pv.rowscore[prev.i0 + r], srsum[r]);
-            if (srmax[r] && pv.rowmax) atomicMax(&pv.rowmax[prev.i0 + r], srmax[r]);
-        }
-        if (hist_bins > 0) lane_flush_hist(pv, shist, tid);
-    }
+    flush_rows(prev, true);   // the last row block and problem
     if (!ok && lane == 0) atomicOr(&bt.views[0].ctl->err, TR_ERR_TIMEOUT);
 }
 
