@@ -74,6 +74,12 @@ typedef enum {
 /* flags */
 #define TURBOREG_FLAG_SC2_BITSET 0x1u  /* SC^2 by bitset AND+popcount on CUDA cores
                                           instead of the tcgen05 FP8 GEMM (same integers) */
+#define TURBOREG_FLAG_SC2_GEMM 0x40u   /* SC^2 by the tcgen05 FP8 GEMM.  Without either flag a single
+                                          problem with N <= 5120 (and pair MMAs available) gets the
+                                          path chosen on the device after the compatibility graph,
+                                          from N and the edge count (the CUDA-core path up to about
+                                          5 % density at N = 5000); batches and larger problems use
+                                          the GEMM.  Same integers on every path */
 #define TURBOREG_FLAG_STAGE_TIMES 0x2u /* record per-stage CUDA-event times (turboreg_stage_times) */
 #define TURBOREG_FLAG_NO_GRAPH 0x4u    /* launch the stages one by one instead of replaying the
                                           captured CUDA graph of this problem shape */

@@ -57,6 +57,11 @@ typedef enum {
 int turboreg_debug_shape(turboreg_ctx* ctx, int32_t* n, int32_t* n_pad, int32_t* n_pivots,
                          int32_t* n_hyp);
 
+/* SC^2 path of the most recent registration call: 1 the CUDA-core bitset
+ * form, 2 the tensor-core GEMM (chosen on the device for one problem without
+ * an SC^2 flag, from N and the edge count).  Returns a turboreg_status. */
+int turboreg_debug_sc2_path(turboreg_ctx* ctx, int32_t* path);
+
 /* Copy stage buffer `which` of the most recent call to host memory `dst`
  * (at most max_bytes).  Returns the byte count copied (>= 0) or -status. */
 int64_t turboreg_debug_copy(turboreg_ctx* ctx, int which, void* dst, int64_t max_bytes);

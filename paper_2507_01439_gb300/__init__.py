@@ -34,6 +34,7 @@ FLAG_NO_GRAPH = 0x4
 FLAG_SC2_SINGLE_CTA = 0x8
 FLAG_VERIFY_PTS32 = 0x10
 FLAG_VERIFY_PTS128 = 0x20
+FLAG_SC2_GEMM = 0x40
 FLAG_DEBUG_STALL_COMPAT = 0x10000   # test hook: every compat block's wait expires (TIMEOUT)
 
 (BUF_ADJ_BITS, BUF_ADJ_FP8, BUF_SC2, BUF_PIVOTS, BUF_CLIQUES, BUF_RT, BUF_INLIERS, BUF_ROWSCORE, BUF_DEGREE,
@@ -44,6 +45,7 @@ SCORE_UNITS = 1 << 22   # BUF_SCORES units per theta (MAE) or theta^2 (MSE)
 EXPORTED = (
     "turboreg_default_params", "turboreg_create", "turboreg_register", "turboreg_register_batched",
     "turboreg_destroy", "turboreg_status_string", "turboreg_debug_shape", "turboreg_debug_copy",
+    "turboreg_debug_sc2_path",
     "turboreg_stage_times", "turboreg_stage_name", "turboreg_select_pivots_noalloc",
     "turboreg_set_proposal_model", "turboreg_features", "turboreg_mlp_create", "turboreg_mlp_destroy",
     "turboreg_mlp_get_params", "turboreg_mlp_set_params", "turboreg_mlp_get_state", "turboreg_mlp_set_state",
@@ -102,6 +104,8 @@ def load_library(path: str = LIB_PATH):
     lib.turboreg_debug_shape.argtypes = [P, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
                                          ctypes.POINTER(i32)]
     lib.turboreg_debug_shape.restype = ctypes.c_int
+    lib.turboreg_debug_sc2_path.argtypes = [P, ctypes.POINTER(i32)]
+    lib.turboreg_debug_sc2_path.restype = ctypes.c_int
     lib.turboreg_debug_copy.argtypes = [P, ctypes.c_int, P, i64]
     lib.turboreg_debug_copy.restype = i64
     lib.turboreg_stage_times.argtypes = [P, ctypes.POINTER(ctypes.c_float), i32]
@@ -324,6 +328,14 @@ class TurboReg:
         if rc != OK:
             raise RuntimeError(status_string(rc))
         return n.value, npad.value, npiv.value, nh.value
+
+    def sc2_path(self):
+        """SC^2 path of the last registration: 1 CUDA-core bitset form, 2 tensor-core GEMM."""
+        p = ctypes.c_int32()
+        rc = self._lib.turboreg_debug_sc2_path(self.handle, ctypes.byref(p))
+        if rc != OK:
+            raise RuntimeError(status_string(rc))
+        return p.value
 
     def buffer(self, which: int) -> np.ndarray:
         n, npad, npiv, nh = self.shape()

@@ -79,6 +79,7 @@ struct Plan {
     int32_t num = 0;
     int32_t max_n = 0, min_n = 0, max_k1 = 0, k2_common = 0;
     int32_t bitset = 0, timed = 0, learned = 0;
+    int32_t sc2_auto = 0;    // one problem: the SC^2 path is chosen on the device (CUDA-core or GEMM)
     int32_t pair_mma = 1;    // SC^2 GEMM: 1 pair MMAs on 2-CTA clusters, 0 independent CTAs
     int32_t vpw = 64;        // verification tile: points per warp
     int32_t vcap = 0;        // balanced tile: verification launched with at most four blocks per SM
@@ -116,6 +117,7 @@ struct turboreg_ctx {
     float stage_ms[kNumStages] = {};
     int32_t last_n = 0, last_npad = 0, last_k1 = 0, last_k2 = 0;
     bool last_fp8 = false;   // the last plan materialised the FP8 adjacency (tensor-core SC^2)
+    bool last_auto = false;  // ... or left the choice to the device (the FP8 matrix exists if the GEMM ran)
     bool have_times = false;
     // Captured pipelines.  Each slot owns a private copy of its descriptors in
     // device memory, so replays of different shapes never see each other's.
@@ -370,6 +372,9 @@ int build_plan(turboreg_ctx* c, int32_t num, const int64_t* in_off, const int32_
     plan.timed = (prm[0]->flags & TURBOREG_FLAG_STAGE_TIMES) != 0;
     plan.learned = prm[0]->proposal == TURBOREG_PROPOSAL_LEARNED;
     plan.pair_mma = (prm[0]->flags & TURBOREG_FLAG_SC2_SINGLE_CTA) ? 0 : 1;
+    plan.sc2_auto = num == 1 && !plan.bitset &&
+                    !(prm[0]->flags & (TURBOREG_FLAG_SC2_SINGLE_CTA | TURBOREG_FLAG_SC2_GEMM)) &&
+                    round_up(n[0], kSc2BN) <= kSc2AutoMaxNpad && sc2_pair_clusters() > 0;
     // verification tile: the flags' width for every problem, or for a single
     // problem without tile flags the balanced width (one even wave); the
     // kernel's points per warp (plan.vpw) is the narrowest that holds them all
@@ -382,6 +387,10 @@ int build_plan(turboreg_ctx* c, int32_t num, const int64_t* in_off, const int32_
     for (int32_t b = 0; b < num; ++b) {
         ws.h_views[b] = make_view(c, b, in_off[b], n[b], prm[b]);
         if (plan.bitset) ws.h_views[b].a8 = nullptr;   // the CUDA-core SC^2 reads the bitset only
+        if (plan.sc2_auto) {   // the FP8 operand only if the device chooses the GEMM
+            ws.h_views[b].a8_auto = ws.h_views[b].a8;
+            ws.h_views[b].a8 = nullptr;
+        }
         const int32_t vppb = (num == 1 && !vflag) ? balanced_vppb(n[b], prm[b]->k1 * prm[b]->k2, device_sms())
                                                   : 4 * vpw_flag;
         ws.h_views[b].vppb = vppb;
@@ -402,7 +411,8 @@ int build_plan(turboreg_ctx* c, int32_t num, const int64_t* in_off, const int32_
         }
     }
     plan.vpw = vppb_max <= 4 * 32 ? 32 : vppb_max <= 4 * 64 ? 64 : 128;
-    c->last_fp8 = !plan.bitset;
+    c->last_fp8 = !plan.bitset && !plan.sc2_auto;
+    c->last_auto = plan.sc2_auto != 0;
     plan.vcap = num == 1 && !vflag;
     return TURBOREG_OK;
 }
@@ -441,13 +451,20 @@ int enqueue_plan(turboreg_ctx* c, const Plan& pl, const Batch& bt, const float* 
     // them when another entry point may have left them set)
     launch_pack(bt, pl.tot[ST_PACK], dsrc, ddst, s);
     TR_EV(1);
-    launch_compat(bt, pl.tot[ST_COMPAT], s);
+    launch_compat(bt, pl.tot[ST_COMPAT], s, pl.sc2_auto != 0);
     TR_EV(2);
     bool fused = false;
-    if (pl.bitset) {
+    if (pl.sc2_auto) {
+        // one problem: the CUDA-core kernel chooses the path from the degrees and
+        // either computes SC^2 or expands the FP8 operand; the GEMM then runs or
+        // returns at once.  Both keep the histogram for the count blocks.
+        launch_sc2_bitset(bt, pl.tot[ST_BITSET], pl.max_n, pl.min_n, sc2_pair_clusters(), s);
+        launch_sc2_tcgen05(bt, pl.tot[ST_GEMM], pl.max_n, true, s, true);
+        fused = true;
+    } else if (pl.bitset) {
         // the histogram is complete in global memory at the end of the kernel;
         // one problem: the count blocks choose the threshold from it
-        fused = launch_sc2_bitset(bt, pl.tot[ST_BITSET], pl.max_n, pl.min_n, s) && pl.num == 1;
+        fused = launch_sc2_bitset(bt, pl.tot[ST_BITSET], pl.max_n, pl.min_n, 0, s) && pl.num == 1;
     } else {
         // one problem whose histogram fits in the GEMM's shared memory: the
         // count blocks choose the threshold; a batch or a larger problem adds
@@ -990,6 +1007,21 @@ int turboreg_register_batched(turboreg_ctx* c, const float* src_cat, const float
     return TURBOREG_OK;
 }
 
+int turboreg_debug_sc2_path(turboreg_ctx* c, int32_t* path)
+{
+    if (!c || !path) return TURBOREG_ERR_INVALID_ARG;
+    TR_CHECK(cudaSetDevice(c->device));
+    TR_CHECK(cudaStreamSynchronize(c->stream));
+    if (c->last_auto) {
+        Ctl h;
+        TR_CHECK(cudaMemcpy(&h, c->ws.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
+        *path = static_cast<int32_t>(h.sc2_path);
+    } else {
+        *path = c->last_fp8 ? 2 : 1;
+    }
+    return TURBOREG_OK;
+}
+
 int turboreg_debug_shape(turboreg_ctx* c, int32_t* n, int32_t* n_pad, int32_t* n_pivots, int32_t* n_hyp)
 {
     if (!c) return TURBOREG_ERR_INVALID_ARG;
@@ -1022,7 +1054,8 @@ int64_t turboreg_debug_copy(turboreg_ctx* c, int which, void* dst, int64_t max_b
     switch (which) {
         case TURBOREG_BUF_ADJ_BITS: src = v.bits; bytes = np * np / 8; break;
         case TURBOREG_BUF_ADJ_FP8:
-            if (!c->last_fp8) return -TURBOREG_ERR_INVALID_ARG;   // not materialised by that plan
+            if (!c->last_fp8 && !(c->last_auto && h.sc2_path == 2u))
+                return -TURBOREG_ERR_INVALID_ARG;   // not materialised by that plan (or that choice)
             src = v.a8;
             bytes = np * np;
             break;
@@ -1242,6 +1275,7 @@ int turboreg_features(turboreg_ctx* c, const float* src, const float* dst, int32
     turboreg_params q = *p;
     q.proposal = TURBOREG_PROPOSAL_PLAIN;
     q.flags &= ~(TURBOREG_FLAG_SC2_BITSET | TURBOREG_FLAG_STAGE_TIMES);
+    q.flags |= TURBOREG_FLAG_SC2_GEMM;   // this entry point launches the GEMM directly
     int rc = check_params(c, n, &q);
     if (rc != TURBOREG_OK) return rc;
     TR_CHECK(cudaSetDevice(c->device));

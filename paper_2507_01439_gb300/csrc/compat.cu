@@ -136,6 +136,9 @@ __device__ __forceinline__ uint4 bits16_to_fp8(uint32_t b16)
                       nibble_to_fp8((b16 >> 12) & 0xF));
 }
 
+// kAuto: the SC^2 path is chosen on the device (one problem): no FP8 matrix,
+// and the degree sum 2 |E| is added up in the control block
+template <bool kAuto>
 __global__ void __launch_bounds__(kThreads) compat_kernel(ManyViews vs)
 {
     pdl_wait();
@@ -237,11 +240,15 @@ __global__ void __launch_bounds__(kThreads) compat_kernel(ManyViews vs)
             make_uint4(wrow_bits[0], wrow_bits[1], wrow_bits[2], wrow_bits[3]);
         const int d = __popc(wrow_bits[0]) + __popc(wrow_bits[1]) + __popc(wrow_bits[2]) + __popc(wrow_bits[3]);
         if (d) atomicAdd(&v.deg[i], d);
+        if (kAuto && diag) {   // the diagonal tile's rows (off the diagonal: twice the columns, below)
+            const unsigned ds = __reduce_add_sync(0x0000FFFFu, static_cast<unsigned>(d));
+            if (lane == 0 && ds) atomicAdd(&v.ctl->deg_sum, ds);
+        }
     }
     // FP8 rows (only for the tensor-core SC^2), 128 contiguous bytes per row:
     // pass k writes rows 4k .. 4k + 3 of the warp's 16, lane l the 16-byte
     // segment l % 8 of row 4k + l / 8
-    const bool fp8 = v.a8 != nullptr;
+    const bool fp8 = !kAuto && v.a8 != nullptr;
 #pragma unroll
     for (int k = 0; k < 4 && fp8; ++k) {
         const int r = 4 * k + (lane >> 3);
@@ -268,6 +275,10 @@ __global__ void __launch_bounds__(kThreads) compat_kernel(ManyViews vs)
         *reinterpret_cast<uint4*>(v.bits + (size_t)j * v.ldb + (i0 >> 5)) = cw;
         const int d = __popc(cw.x) + __popc(cw.y) + __popc(cw.z) + __popc(cw.w);
         if (d) atomicAdd(&v.deg[j], d);
+        if (kAuto) {
+            const unsigned ds = __reduce_add_sync(0xffffffffu, static_cast<unsigned>(d));
+            if (lane == 0 && ds) atomicAdd(&v.ctl->deg_sum, 2u * ds);
+        }
     }
     // FP8 rows: pass k writes rows j0 + 32k .. +31, eight threads per 128-byte row
 #pragma unroll
@@ -289,9 +300,10 @@ void launch_pack(const Batch& b, int total, const float* src, const float* dst, 
     pack_kernel<<<total, 256, 0, s>>>(ManyViews{b}, src, dst);
 }
 
-void launch_compat(const Batch& b, int total, cudaStream_t s)
+void launch_compat(const Batch& b, int total, cudaStream_t s, bool auto_sc2)
 {
-    launch_pdl(compat_kernel, total, kThreads, 0, s, ManyViews{b});
+    if (auto_sc2) launch_pdl(compat_kernel<true>, total, kThreads, 0, s, ManyViews{b});
+    else launch_pdl(compat_kernel<false>, total, kThreads, 0, s, ManyViews{b});
 }
 
 }  // namespace tr

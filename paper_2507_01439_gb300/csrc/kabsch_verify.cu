@@ -365,6 +365,7 @@ __global__ void __launch_bounds__(1024) finalize_kernel(ManyViews vs, turboreg_r
     v.ctl->gt_slot = 0u;
     v.ctl->done_blocks = 0u;
     v.ctl->pmax_bits = 0u;
+    v.ctl->deg_sum = 0u;
 }
 
 }  // namespace

@@ -388,9 +388,18 @@ constexpr int kPipeBytes2 = kStages2 * 2 * kABytes;   // 160 KB
 constexpr int kStageBytes2 = kEpiWarps * 2048;       // W staging: 32 x 32 uint16 per epilogue warp
 constexpr int kBase2 = kPipeBytes2 + kBarBytes + kStageBytes2 + 1024;   // before the shared histogram
 
+// auto_mode: one problem whose SC^2 path the CUDA-core kernel before this one
+// chose; when it chose itself, every CTA returns at once (before any set-up).
 template <bool kHist>
-__global__ void __launch_bounds__(kThreads, 1) sc2_pair_mma_kernel(Batch bt, int total, int hist_bins)
+__global__ void __launch_bounds__(kThreads, 1) sc2_pair_mma_kernel(Batch bt, int total, int hist_bins, int auto_mode)
 {
+    if (auto_mode) {
+        pdl_wait();
+        if (__ldcg(&bt.views[0].ctl->sc2_path) != 2u) {
+            pdl_release();
+            return;
+        }
+    }
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t* sA = smem;                                  // [stage] 128 rows x 128 B
@@ -590,7 +599,7 @@ int g_sc2_pair_clusters = 0;   // co-resident 2-CTA clusters of the pair kernels
 // kHist: the blocks keep the edge-weight histogram in shared memory
 // (hist_bins bins)
 template <bool kHist>
-cudaError_t launch_pair(const Batch& b, int total_tiles, size_t smem, int hist_bins, cudaStream_t s)
+cudaError_t launch_pair(const Batch& b, int total_tiles, size_t smem, int hist_bins, cudaStream_t s, int auto_mode)
 {
     int grid = 2 * g_sc2_pair_clusters;
     if (grid > total_tiles) grid = total_tiles;   // total_tiles is even
@@ -608,12 +617,14 @@ cudaError_t launch_pair(const Batch& b, int total_tiles, size_t smem, int hist_b
     attr[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 2;
-    return cudaLaunchKernelEx(&cfg, sc2_pair_mma_kernel<kHist>, b, total_tiles, hist_bins);
+    return cudaLaunchKernelEx(&cfg, sc2_pair_mma_kernel<kHist>, b, total_tiles, hist_bins, auto_mode);
 }
 
 }  // namespace
 
 int device_sms() { return g_sc2_sms > 0 ? g_sc2_sms : 148; }
+
+int sc2_pair_clusters() { return g_sc2_pair_clusters; }
 
 cudaError_t sc2_tcgen05_setup()
 {
@@ -654,7 +665,7 @@ cudaError_t sc2_tcgen05_setup()
 
 // A single problem keeps its histogram in shared memory when it fits; a
 // batch (or a very large problem) uses global atomics.
-bool launch_sc2_tcgen05(const Batch& b, int total_tiles, int max_n, bool pair_mma, cudaStream_t s)
+bool launch_sc2_tcgen05(const Batch& b, int total_tiles, int max_n, bool pair_mma, cudaStream_t s, bool auto_mode)
 {
     const bool pair = pair_mma && g_sc2_pair_clusters > 0;
     const int sms = g_sc2_sms > 0 ? g_sc2_sms : 148;
@@ -665,9 +676,9 @@ bool launch_sc2_tcgen05(const Batch& b, int total_tiles, int max_n, bool pair_mm
     const bool single = b.num == 1 && fits;
     if (pair) {
         if (fits)
-            launch_pair<true>(b, total_tiles, base + hist, max_n + 1, s);
+            launch_pair<true>(b, total_tiles, base + hist, max_n + 1, s, auto_mode ? 1 : 0);
         else
-            launch_pair<false>(b, total_tiles, base, 0, s);
+            launch_pair<false>(b, total_tiles, base, 0, s, auto_mode ? 1 : 0);
     } else if (single) {
         launch_pdl(sc2_tcgen05_kernel<true>, grid, kThreads, base + hist, s, b, total_tiles);
     } else {

@@ -238,9 +238,43 @@ __device__ __forceinline__ uint32_t and_popc(const uint4 (&a)[NQ], const uint4 (
     }
 }
 
+// The SC^2 path for one problem, chosen on the device after the compatibility
+// graph: predicted times (us) fitted to measurements on GB300 at N = 1000 ..
+// 5000 and 1.7 .. 14 % density.  This CUDA-core form: a + b |E+| / 1e6, with
+// (a, b) = (21.5, 49) at n_pad = 5120 and (13.9, 70.8) at 3072, linear in
+// between (fewer units per CTA for smaller N), and always the faster one up
+// to n_pad = 2048; the tensor-core GEMM: 12.5 + waves x K-stages x 0.368 (its
+// 2-CTA clusters over the 256 x 256 upper-triangle tiles, 0.368 us per
+// 128-deep stage) plus 4 (n_pad / 5120)^2 for the FP8 matrix it then needs.
+__device__ __forceinline__ bool sc2_bitset_faster(int n_pad, unsigned long long deg_sum, int clusters)
+{
+    if (n_pad <= 2048) return true;
+    const float d = static_cast<float>(5120 - n_pad) / 2048.f;
+    const float edges_m = static_cast<float>(deg_sum) * 0.5e-6f;
+    const float t_bitset = (21.5f - 7.6f * d) + (49.f + 21.8f * d) * edges_m;
+    const int nb = n_pad / 256;
+    const int tiles = nb * (nb + 1) / 2;
+    const int waves = (tiles + clusters - 1) / clusters;
+    const float r = static_cast<float>(n_pad) / 5120.f;
+    const float t_gemm = 12.5f + static_cast<float>(waves * (n_pad / 128)) * 0.368f + 4.f * r * r;
+    return t_bitset <= t_gemm;
+}
+
+// 4 adjacency bits -> 4 bytes of FP8 E4M3 (0x38 = 1.0 for a set bit, 0 otherwise)
+__device__ __forceinline__ uint32_t nib_fp8(uint32_t nib) { return ((nib * 0x00204081u) & 0x01010101u) * 0x38u; }
+
+__device__ __forceinline__ uint4 half_word_fp8(uint32_t b16)
+{
+    return make_uint4(nib_fp8(b16 & 0xFu), nib_fp8((b16 >> 4) & 0xFu), nib_fp8((b16 >> 8) & 0xFu),
+                      nib_fp8((b16 >> 12) & 0xFu));
+}
+
+// auto_clusters > 0: one problem whose SC^2 path is chosen here (the GEMM's
+// co-resident 2-CTA clusters); if the GEMM is the faster path, the CTAs expand
+// the bitset into its FP8 operand and leave the rest to it.
 template <int NQ, bool kExact, bool kCsa>
 __global__ void __launch_bounds__(kLThreads, 1)
-    sc2_bitset_lane_kernel(Batch bt, int total, int ldb_max, int hist_bins)
+    sc2_bitset_lane_kernel(Batch bt, int total, int ldb_max, int hist_bins, int auto_clusters)
 {
     extern __shared__ __align__(16) uint8_t ls_raw[];
     uint8_t* q8 = ls_raw;
@@ -273,6 +307,26 @@ __global__ void __launch_bounds__(kLThreads, 1)
     const int u1 = static_cast<int>((static_cast<long long>(units) * (blockIdx.x + 1)) / gridDim.x);
     pdl_wait();
     pdl_release();
+    if (auto_clusters > 0) {
+        // the degree sum 2 |E| of the problem (added up by the compatibility blocks)
+        const ProbView& v0 = bt.views[0];
+        const unsigned long long deg_sum = __ldcg(&v0.ctl->deg_sum);
+        const bool bitset = sc2_bitset_faster(v0.n_pad, deg_sum, auto_clusters);
+        if (blockIdx.x == 0 && tid == 0) v0.ctl->sc2_path = bitset ? 1u : 2u;
+        if (!bitset) {
+            // the GEMM's FP8 operand from the bitset: word q of the matrix -> 32 bytes
+            const size_t words = static_cast<size_t>(v0.n_pad) * v0.ldb;
+            for (size_t q = static_cast<size_t>(blockIdx.x) * kLThreads + tid; q < words;
+                 q += static_cast<size_t>(gridDim.x) * kLThreads) {
+                const uint32_t w = __ldcg(v0.bits + q);
+                const size_t row = q / static_cast<size_t>(v0.ldb), col = (q % static_cast<size_t>(v0.ldb)) * 32;
+                uint4* dst = reinterpret_cast<uint4*>(v0.a8_auto + row * v0.n_pad + col);
+                dst[0] = half_word_fp8(w & 0xFFFFu);
+                dst[1] = half_word_fp8(w >> 16);
+            }
+            return;
+        }
+    }
     if (u0 >= u1) return;
     LaneUnit cur = lane_unit(bt, u0), prev = cur;
     if (tid == 0) lane_view_load(lv[cur.p & 3], bt.views[cur.p]);
@@ -580,7 +634,7 @@ cudaError_t sc2_bitset_setup()
     return e;
 }
 
-bool launch_sc2_bitset(const Batch& b, int total_tiles, int max_n, int min_n, cudaStream_t s)
+bool launch_sc2_bitset(const Batch& b, int total_tiles, int max_n, int min_n, int auto_clusters, cudaStream_t s)
 {
     const int max_npad = (max_n + kSc2BN - 1) / kSc2BN * kSc2BN;
     const int max_ldb = max_npad / 32;
@@ -594,11 +648,11 @@ bool launch_sc2_bitset(const Batch& b, int total_tiles, int max_n, int min_n, cu
         const int min_ldb = (min_n + kSc2BN - 1) / kSc2BN * kSc2BN / 32;
         const bool exact = min_ldb == max_ldb && max_ldb == kLMaxLdb;
         if (max_ldb <= 64)
-            launch_pdl(sc2_bitset_lane_kernel<2, false, false>, grid, kLThreads, smem, s, b, total_tiles, max_ldb, hist_bins);
+            launch_pdl(sc2_bitset_lane_kernel<2, false, false>, grid, kLThreads, smem, s, b, total_tiles, max_ldb, hist_bins, auto_clusters);
         else if (exact)
-            launch_pdl(sc2_bitset_lane_kernel<5, true, true>, grid, kLThreads, smem, s, b, total_tiles, max_ldb, hist_bins);
+            launch_pdl(sc2_bitset_lane_kernel<5, true, true>, grid, kLThreads, smem, s, b, total_tiles, max_ldb, hist_bins, auto_clusters);
         else
-            launch_pdl(sc2_bitset_lane_kernel<5, false, true>, grid, kLThreads, smem, s, b, total_tiles, max_ldb, hist_bins);
+            launch_pdl(sc2_bitset_lane_kernel<5, false, true>, grid, kLThreads, smem, s, b, total_tiles, max_ldb, hist_bins, auto_clusters);
         return true;
     }
     // shared memory for the row block and the histogram bins, as far as they fit

@@ -40,7 +40,9 @@ struct Ctl {
     uint32_t pmax_bits;  // learned proposal: bits of the largest inlier probability (non-negative float)
     uint32_t done_blocks;  // completion counter (reserved; cleared with the other counters)
     uint32_t n_active;   // rows holding an edge of weight >= alpha (pivot selection)
-    int32_t pad[3];
+    uint32_t sc2_path;   // SC^2 path chosen on the device: 1 CUDA-core (bitset), 2 tensor-core GEMM
+    uint32_t deg_sum;    // with that choice: the degree sum 2 |E|, added up by the compatibility blocks
+    int32_t pad[1];
 };
 
 // ---------------------------------------------------------------------------

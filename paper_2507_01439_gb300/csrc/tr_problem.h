@@ -27,6 +27,10 @@ struct ProbView {
     int32_t scoring;     // TURBOREG_SCORE_IN / _MAE / _MSE
     int32_t vppb;        // verification tile: matches per block (<= 4 x the kernel's points per warp)
     uint32_t dbg;        // failure injection for tests (TR_DBG_*), 0 in normal use
+    uint8_t* a8_auto;    // non-null: the SC^2 path is chosen on the device from the degrees (one
+                         // problem, n_pad <= 5120); a8 is then null, so the compatibility kernel
+                         // writes the bitset only, and the FP8 matrix is expanded into a8_auto
+                         // if the tensor-core GEMM is chosen
     float* pts;          // [6][n_pad]
     float* pts8;         // [n_pad][8] = (x0, x1, x2, y0, y1, y2, 0, 0)
     uint8_t* a8;         // [n_pad][n_pad] FP8 E4M3 0/1 adjacency
@@ -131,16 +135,19 @@ int32_t balanced_vppb(int32_t n, int32_t nh, int32_t num_sms);
 // stage launchers (all asynchronous on `s`); total = sum of the stage's blocks
 void launch_pack(const Batch& b, int total, const float* src, const float* dst, cudaStream_t s);
 const void* pack_kernel_func();   // identifies the pack node inside a captured graph
-void launch_compat(const Batch& b, int total, cudaStream_t s);
+void launch_compat(const Batch& b, int total, cudaStream_t s, bool auto_sc2 = false);
 // pair_mma: 2-CTA clusters with pair MMAs (cta_group::2); otherwise
 // independent CTAs.  Returns true when the GEMM completed one problem's
 // weight histogram from shared memory, so that the count pass may choose the
 // pivot threshold; otherwise the caller launches the select.
-bool launch_sc2_tcgen05(const Batch& b, int total_tiles, int max_n, bool pair_mma, cudaStream_t s);
+bool launch_sc2_tcgen05(const Batch& b, int total_tiles, int max_n, bool pair_mma, cudaStream_t s,
+                        bool auto_mode = false);
+// co-resident 2-CTA clusters of the pair-MMA GEMM (0: none)
+int sc2_pair_clusters();
 // SC^2 by AND + popcount over the bitset (sc2_bitset.cu); total = the batch's
 // tiles (bitset_tiles per problem).  Returns true when every problem's
 // edge-weight histogram is complete in global memory at its end (always).
-bool launch_sc2_bitset(const Batch& b, int total_tiles, int max_n, int min_n, cudaStream_t s);
+bool launch_sc2_bitset(const Batch& b, int total_tiles, int max_n, int min_n, int auto_clusters, cudaStream_t s);
 int bitset_tiles(int n_pad);
 cudaError_t sc2_bitset_setup();
 void launch_hist(const Batch& b, int total, int max_n, cudaStream_t s);
@@ -178,5 +185,6 @@ void launch_topk_single(const ProbView& v, cudaStream_t s);
 constexpr int kSc2BM = 128;   // GEMM tile rows  (TMEM lanes)
 constexpr int kSc2BN = 256;   // GEMM tile cols  (TMEM columns)
 constexpr int kSc2BK = 128;   // K bytes per pipeline stage (one 128-byte swizzle row)
+constexpr int kSc2AutoMaxNpad = 5120;   // the device-side choice of the SC^2 path: n_pad <= 5120
 
 }  // namespace tr

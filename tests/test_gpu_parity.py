@@ -210,6 +210,27 @@ def test_deterministic_repeats(ctx):
     assert np.array_equal(ctx.buffer(trg.BUF_SC2)[:n, :n][iu], W0[:n, :n][iu])
 
 
+@pytest.mark.parametrize("n,tau,want", [(5000, 0.1, 1), (5000, 0.4, 2), (3000, 0.3, 2), (1500, 0.4, 1)])
+def test_sc2_path_chosen_on_the_device(ctx, n, tau, want):
+    # one problem without an SC^2 flag: the path is chosen on the device from N
+    # and the edge count (CUDA-core on sparse graphs, the GEMM on dense ones, the
+    # FP8 operand then expanded from the bitset); results and W equal both forced paths
+    p = synth.make_problem("indoor", n, 0.05, 23)
+    r = ctx.register(p.x, p.y, trg.default_params(tau, 1000, p.theta))
+    assert ctx.sc2_path() == want
+    W = ctx.buffer(trg.BUF_SC2)[:n, :n].copy()
+    if want == 2 and n <= 3000:   # the expanded FP8 operand and every graph stage against the oracle
+        A, S, _, _ = oracle_stages(p.x, p.y, tau, 1000, 2)
+        check_graph_stages(ctx, A, S, n)
+    iu = np.triu_indices(n, 1)
+    for fl, path in ((trg.FLAG_SC2_GEMM, 2), (trg.FLAG_SC2_BITSET, 1)):
+        rf = ctx.register(p.x, p.y, trg.default_params(tau, 1000, p.theta, flags=fl))
+        assert ctx.sc2_path() == path
+        assert rf.status == r.status and rf.hypothesis == r.hypothesis and rf.n_pivots == r.n_pivots
+        assert np.array_equal(rf.R, r.R) and np.array_equal(rf.t, r.t) and rf.inlier_count == r.inlier_count
+        assert np.array_equal(ctx.buffer(trg.BUF_SC2)[:n, :n][iu], W[iu])
+
+
 def test_bitset_sc2_many_small_problems():
     # the CUDA-core SC^2 over a batch of small problems: a CTA's run of work
     # units crosses many problems (one to four tiles each), so problem changes,
