@@ -53,13 +53,18 @@ WORKLOAD = {"workload": "indoor-shaped single problem", "n": 5000, "inlier_ratio
             "tau_m": 0.1, "k1": 2000, "k2": 2, "inlier_thresh_m": 0.1, "problems_cycled": 8,
             "l2": "flushed between timed steps (256 MB write, outside the events)"}
 # kernels of ours launched per registration: pack, compat, sc2 (with the histogram and
-# the threshold choice), count, emit, pgs (with the pivot ranks and the cliques'
-# Kabsch), verify, finalize
-LAUNCHES_PER_STEP = 8
-# DRAM bytes (read + write) of one SC^2 kernel launch on this workload, from one ncu
-# capture of the current kernel (profiles/sc2_pair_mma_indoor5000.txt); set to None when
-# the kernel changes, until it has been captured again
+# the threshold choice; one problem without an SC^2 flag: the CUDA-core kernel, which
+# chooses the path, then the GEMM kernel, which runs or returns at once), count, emit,
+# pgs (with the pivot ranks and the cliques' Kabsch), verify, finalize
+LAUNCHES_PER_STEP = 9
+# DRAM bytes (read + write) of one launch of each SC^2 kernel on this workload, from one
+# ncu capture of the current kernel (profiles/sc2_pair_mma_indoor5000.txt,
+# profiles/sc2_bitset_indoor5000.txt); None when the kernel has changed since, until
+# it has been captured again
 SC2_DRAM_BYTES = 28775424
+SC2_BITSET_DRAM_BYTES = 3352576
+# the population count's rate: 16 per clock per SM on 152 SMs at the 2.07 GHz maximum clock
+POPC_PEAK_TWORDS = 16 * 152 * 2.07e9 / 1e12
 
 
 def _peaks():
@@ -177,13 +182,14 @@ PAPER_CONTEXT = {
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
-def stage_rooflines(stage_log, peaks, kind):
+def stage_rooflines(stage_log, peaks, kind, sc2_path=2, words=0.0):
     """Achieved fraction of each stage's bound from the in-graph stage times of
     the roofline pass (means; each stage time includes one in-graph event
     record, a few microseconds, so short stages read low).  Algorithmic work
     per registration of the N = 5000, K1 = 2000, K2 = 2 workload:
       compat   n(n-1)/2 pairs x 17 FLOP (two 3-D distances, difference, compare)
-      sc2      420 tiles x 2 x 128 x 256 x 5120 dense FP8 MMA FLOP
+      sc2      420 tiles x 2 x 128 x 256 x 5120 dense FP8 MMA FLOP (GEMM), or
+               |E+| x 5120 / 32 words of AND + popcount (CUDA-core form)
       topk     the upper triangle of W read once: n(n-1)/2 x 2 bytes
       pgs      K1 x 2 bitset rows of n/8 bytes (the stage also solves each
                clique's Kabsch, ~300 FLOP per clique, not counted)
@@ -195,7 +201,8 @@ def stage_rooflines(stage_log, peaks, kind):
     pairs = n * (n - 1) / 2
     work = {
         "compat": (pairs * 17, "alu", FP32_PEAK_TFLOPS, "TFLOP/s"),
-        "sc2": (420 * 2.0 * 128 * 256 * 5120, "tensor", 2 * peaks["bf16_tflops_sustained"], "TFLOP/s"),
+        "sc2": ((420 * 2.0 * 128 * 256 * 5120, "tensor", 2 * peaks["bf16_tflops_sustained"], "TFLOP/s")
+                if sc2_path == 2 else (words, "alu", POPC_PEAK_TWORDS, "Tword/s")),
         "topk": (pairs * 2, "hbm", peaks["hbm_gbs"], "GB/s"),
         "pgs": (k1 * 2 * n / 8, "hbm", peaks["hbm_gbs"], "GB/s"),
         "verify": (k1 * k2 * n * 17.0, "alu", FP32_PEAK_TFLOPS, "TFLOP/s"),
@@ -205,7 +212,7 @@ def stage_rooflines(stage_log, peaks, kind):
         ms = mean.get(st)
         if not ms or ms <= 0:
             continue
-        scale = 1e12 if unit == "TFLOP/s" else 1e9
+        scale = 1e12 if unit in ("TFLOP/s", "Tword/s") else 1e9
         ach = w / (ms / 1e3) / scale
         out[st] = {"ms": ms, "bound": bound, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak}
     out["peak_source"] = f"{kind} MEASURED_PEAKS.json for tensor (2 x bf16 sustained) and HBM; FP32 from unit counts"
@@ -604,10 +611,9 @@ def run_clique_stability(trg, per_tau=240):
 
 def run_sc2_paths(trg, probs, dx, dy):
     """SC^2 stage (with the edge-weight histogram and the pivot threshold) on
-    the benchmark workload: the tcgen05 FP8 GEMM (2-CTA pair MMAs, the
-    default; independent CTAs) vs the
-    CUDA-core bitset AND + popcount path (same integers); in-graph CUDA-event
-    times."""
+    the benchmark workload: the default (path chosen on the device), the
+    tcgen05 FP8 GEMM (2-CTA pair MMAs; independent CTAs) and the CUDA-core
+    bitset AND + popcount path (same integers); in-graph CUDA-event times."""
     import numpy as np
     out = {}
     with trg.TurboReg(max_n=5000, max_batch=1) as ctx:
@@ -618,7 +624,8 @@ def run_sc2_paths(trg, probs, dx, dy):
             ctx.register(dx[k], dy[k], trg.default_params(0.1, 2000, 0.1))
             bits = ctx.buffer(trg.BUF_ADJ_BITS)
             edges.append(int(np.unpackbits(bits.view(np.uint8)).sum()) // 2)
-        for name, fl in (("tcgen05_gemm", 0), ("tcgen05_gemm_single_cta", trg.FLAG_SC2_SINGLE_CTA),
+        for name, fl in (("chosen_on_device", 0), ("tcgen05_gemm", trg.FLAG_SC2_GEMM),
+                         ("tcgen05_gemm_single_cta", trg.FLAG_SC2_SINGLE_CTA),
                          ("bitset_popcount", trg.FLAG_SC2_BITSET)):
             prm = trg.default_params(0.1, 2000, 0.1, flags=trg.FLAG_STAGE_TIMES | fl)
             ms = []
@@ -678,11 +685,16 @@ def run_ours(args):
     import synth
     ok = 0
     first_results = []
+    edges, paths = [], []
     for k, p in enumerate(probs):
         r = ctx.register(dx[k], dy[k], prm)
         first_results.append(r)
         ok += int(r.status == 0 and synth.rotation_error_deg(p.R_gt, r.R) < 15.0
                   and synth.translation_error(p.t_gt, r.t) < 0.3)
+        paths.append(ctx.sc2_path())   # the SC^2 path the device chose for this problem
+        edges.append(int(np.unpackbits(ctx.buffer(trg.BUF_ADJ_BITS).view(np.uint8)).sum()) // 2)
+    sc2_path = max(set(paths), key=paths.count)
+    words = (sum(edges) / len(edges)) * 5120 / 32   # |E+| x n_pad / 32 words of AND + popc
 
     def timed(kind, steps, warmup):
         """kind: "device" / "host" = the stream call (register_async) with
@@ -753,13 +765,23 @@ def run_ours(args):
     nb = npad // 256
     flops = nb * (nb + 1) * 2.0 * 128 * 256 * npad
     sc2_avg_s = (sum(sc2_ms) / len(sc2_ms)) / 1e3
-    achieved = flops / sc2_avg_s / 1e12
     peak = 2.0 * peaks["bf16_tflops_sustained"]    # FP8 dense = 2 x bf16 (nominal ratio)
-    roofline = {"bound": "tensor", "kernel": "sc2_pair_mma_kernel (FP8 E4M3 x E4M3 -> F32, cta_group::2 pair MMAs)",
-                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "peak_source": f"{kind}: 2 x bf16_tflops_sustained (FP8/BF16 nominal ratio 4.5/2.25)",
-                "traffic": SC2_DRAM_BYTES, "sc2_ms": sc2_avg_s * 1e3,
-                "flops_per_launch": flops}
+    if sc2_path == 1:
+        # the CUDA-core form ran: |E+| x n_pad / 32 words of AND + population count
+        achieved = words / sc2_avg_s / 1e12
+        roofline = {"bound": "alu", "kernel": "sc2_bitset_lane_kernel (AND + population count on CUDA cores, "
+                                              "chosen on the device for this density)",
+                    "achieved": achieved, "peak": POPC_PEAK_TWORDS, "unit": "Tword/s", "frac": achieved / POPC_PEAK_TWORDS,
+                    "peak_source": "unit counts: 16 population counts per clock per SM x 152 SMs x 2.07 GHz",
+                    "traffic": SC2_BITSET_DRAM_BYTES, "sc2_ms": sc2_avg_s * 1e3, "words_per_launch": words,
+                    "sc2_path_counts": {"cuda_core": paths.count(1), "tensor_core_gemm": paths.count(2)}}
+    else:
+        achieved = flops / sc2_avg_s / 1e12
+        roofline = {"bound": "tensor", "kernel": "sc2_pair_mma_kernel (FP8 E4M3 x E4M3 -> F32, cta_group::2 pair MMAs)",
+                    "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                    "peak_source": f"{kind}: 2 x bf16_tflops_sustained (FP8/BF16 nominal ratio 4.5/2.25)",
+                    "traffic": SC2_DRAM_BYTES, "sc2_ms": sc2_avg_s * 1e3,
+                    "flops_per_launch": flops}
     # the batched leg runs on every rank (its problems are sharded over them)
     batched = None
     if not args.no_batched:
@@ -769,7 +791,8 @@ def run_ours(args):
         return
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * tot_dev / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "fp8+f32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32+f32" if sc2_path == 1 else "fp8+f32",
+            "data": "synthetic",
             "config": dict(WORKLOAD, parallelism=f"replicas x{ws}"),
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 2 * 5000 * 12,
                     "d2h_bytes_per_step": ctypes.sizeof(trg.turboreg_result)},
@@ -796,7 +819,7 @@ def run_ours(args):
         line["ablation"] = run_ablation(trg, torch, stream, flush)
         line["ranking"] = run_ranking(trg)
         line["clique_stability"] = run_clique_stability(trg)
-    line["stage_rooflines"] = stage_rooflines(stage_log, peaks, kind)
+    line["stage_rooflines"] = stage_rooflines(stage_log, peaks, kind, sc2_path, words)
     line["paper_context"] = PAPER_CONTEXT
     if ws == 1 and not args.no_cpu_baseline:
         # the GPU's per-hypothesis inlier numbers and transforms of the eight problems
