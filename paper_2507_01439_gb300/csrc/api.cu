@@ -375,6 +375,10 @@ int build_plan(turboreg_ctx* c, int32_t num, const int64_t* in_off, const int32_
     plan.sc2_auto = num == 1 && !plan.bitset &&
                     !(prm[0]->flags & (TURBOREG_FLAG_SC2_SINGLE_CTA | TURBOREG_FLAG_SC2_GEMM)) &&
                     round_up(n[0], kSc2BN) <= kSc2AutoMaxNpad && sc2_pair_clusters() > 0;
+    if (plan.sc2_auto && round_up(n[0], kSc2BN) <= kSc2BitsetAlwaysNpad) {
+        plan.sc2_auto = 0;   // the CUDA-core path is the faster one at any density: no choice to make
+        plan.bitset = 1;
+    }
     // verification tile: the flags' width for every problem, or for a single
     // problem without tile flags the balanced width (one even wave); the
     // kernel's points per warp (plan.vpw) is the narrowest that holds them all

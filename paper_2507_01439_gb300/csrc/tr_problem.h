@@ -186,5 +186,6 @@ constexpr int kSc2BM = 128;   // GEMM tile rows  (TMEM lanes)
 constexpr int kSc2BN = 256;   // GEMM tile cols  (TMEM columns)
 constexpr int kSc2BK = 128;   // K bytes per pipeline stage (one 128-byte swizzle row)
 constexpr int kSc2AutoMaxNpad = 5120;   // the device-side choice of the SC^2 path: n_pad <= 5120
+constexpr int kSc2BitsetAlwaysNpad = 2048;   // ... below which the CUDA-core path is taken directly
 
 }  // namespace tr

@@ -42,12 +42,13 @@ def _full_parity(ctx, p, k1, k2=2, flags=0, tau=None, theta=None):
     return res, orc, stats, kind
 
 
-@pytest.mark.parametrize("flags", [0, trg.FLAG_SC2_BITSET])
+@pytest.mark.parametrize("flags", [0, trg.FLAG_SC2_GEMM, trg.FLAG_SC2_BITSET])
 @pytest.mark.parametrize("n,seed", [(3, 1), (7, 2), (33, 3), (63, 11), (64, 12), (65, 13), (127, 4), (128, 5),
                                     (129, 6), (255, 7), (256, 8), (257, 9), (600, 10)])
 def test_small_ragged_sizes(ctx, n, seed, flags):
     # dense enough to have edges at tiny N: generous tau on a small cube; the
-    # tensor-core GEMM (128/256 tiles) and the bitset path (64 x 256 tiles)
+    # default (the CUDA-core path at these sizes), the tensor-core GEMM
+    # (128/256 tiles) and the bitset path forced
     p = synth.make_problem("cube", n, 0.5, seed, tau=0.3, theta=0.1)
     _full_parity(ctx, p, k1=min(200, 4 * n), k2=2, flags=flags)
 
@@ -93,12 +94,14 @@ def test_k2_max(ctx):
     _full_parity(ctx, p, k1=400, k2=trg.TURBOREG_K2_MAX)
 
 
+@pytest.mark.parametrize("flags", [trg.FLAG_SC2_BITSET, trg.FLAG_SC2_GEMM])
 @pytest.mark.parametrize("shape,n,k1", [("indoor", 3000, 1500), ("indoor", 5000, 2000), ("outdoor", 2500, 1000),
                                         ("cube", 1000, 1000)])
-def test_bitset_sc2_matches(ctx, shape, n, k1):
-    # SC^2 by AND + popcount over the bitset: the same integers as the GEMM
+def test_forced_sc2_path_matches(ctx, shape, n, k1, flags):
+    # each SC^2 path forced: AND + popcount over the bitset, and the pair-MMA
+    # GEMM with the FP8 matrix from the compatibility kernel (same integers)
     p = synth.make_problem(shape, n, 0.05 if shape == "indoor" else 0.2, 11)
-    _full_parity(ctx, p, k1=k1, flags=trg.FLAG_SC2_BITSET)
+    _full_parity(ctx, p, k1=k1, flags=flags)
 
 
 @pytest.mark.parametrize("shape,n", [("cube", 300), ("cube", 777), ("indoor", 3000), ("indoor", 5000)])
@@ -124,8 +127,9 @@ def test_sc2_forms_batched(ctx, flags):
         assert np.array_equal(a.R, b.R) and np.array_equal(a.t, b.t) and a.inlier_count == b.inlier_count
 
 
-@pytest.mark.parametrize("flags", [0, trg.FLAG_SC2_SINGLE_CTA, trg.FLAG_SC2_BITSET])
+@pytest.mark.parametrize("flags", [0, trg.FLAG_SC2_GEMM, trg.FLAG_SC2_SINGLE_CTA, trg.FLAG_SC2_BITSET])
 def test_complete_graph_exactness(ctx, flags):
+    # (the default chooses the GEMM here, on the FP8 operand expanded from the bitset)
     # tau huge: G is complete, every SC^2 entry is N-2 (largest integer the FP8 GEMM accumulates)
     p = synth.make_problem("cube", 5000, 0.1, 12)
     prm = trg.default_params(1e6, 50, 0.1, flags=flags)
