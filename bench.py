@@ -833,6 +833,8 @@ def run_ours(args):
 
 def run_profile_case(case):
     """Small fixed workloads for profiler captures (no timing, no JSON line):
+      default      four registrations of the benchmark's seed-0 problem on the
+                   default path (SC^2 form chosen on the device)
       sc2-bitset   four registrations of the benchmark's seed-0 problem on the
                    CUDA-core SC^2 path
       batched      three batched calls of the 256-problem workload
@@ -844,13 +846,14 @@ def run_profile_case(case):
     from paper_2507_01439_gb300 import build as trbuild
     import synth
     trbuild.build()
-    if case == "sc2-bitset":
+    if case in ("default", "sc2-bitset"):
         p = _problems(1)[0]
+        flags = trg.FLAG_SC2_BITSET if case == "sc2-bitset" else 0
         with trg.TurboReg(max_n=5000) as ctx:
-            prm = trg.default_params(p.tau, p.k1, p.theta, flags=trg.FLAG_SC2_BITSET)
+            prm = trg.default_params(p.tau, p.k1, p.theta, flags=flags)
             for _ in range(4):
                 r = ctx.register(p.x, p.y, prm)
-        print("sc2-bitset", r.status, r.inlier_count)
+        print(case, r.status, r.inlier_count)
         return
     if case == "batched":
         probs = synth.make_batch(256, seed=4)
@@ -884,7 +887,7 @@ def main():
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-studies", action="store_true",
                     help="skip the SC^2 path comparison, the ablation sweep and the ranking study")
-    ap.add_argument("--profile-case", choices=["sc2-bitset", "batched", "learned"],
+    ap.add_argument("--profile-case", choices=["default", "sc2-bitset", "batched", "learned"],
                     help="run a small fixed workload for a profiler capture instead of the benchmark")
     args = ap.parse_args()
     if args.profile_case:
