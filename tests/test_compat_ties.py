@@ -179,3 +179,48 @@ def test_compat_bit_exact_at_threshold(kind, tau, seed):
     d64, _ = pair_decisions(X, Y, tau)
     m = np.arange(n // 2)
     assert np.array_equal(G[2 * m, 2 * m + 1].astype(bool), d64)
+
+
+def _all_fp64_case(case):
+    """Inputs for which the kernel decides every pair in FP64: coordinates
+    beyond 2^24, tau below 2^-20 and tau above 2^20."""
+    import synth
+    p = synth.make_problem("cube", 700, 0.3, 21)
+    x, y = p.x.astype(F64), p.y.astype(F64)
+    if case == "coordinates":                 # 1e7-scaled cube: |c| up to 3e7 > 2^24, tau = 1e6 < 2^20
+        return (x * 1e7).astype(F32), (y * 1e7).astype(F32), 1e6
+    if case == "tiny_tau":                    # half the matches copied exactly: their pairs tie at dX = dY
+        y2 = y.copy()
+        y2[:350] = x[:350]
+        return x.astype(F32), y2.astype(F32), 2.0 ** -21
+    return x.astype(F32), y.astype(F32), 2.0 ** 21   # every pair compatible
+
+
+@pytest.mark.parametrize("case", ["coordinates", "tiny_tau", "huge_tau"])
+def test_all_fp64_cases_cpu(case):
+    X, Y, tau = _all_fp64_case(case)
+    A = oracle.compat(X, Y, tau)
+    n = X.shape[0]
+    off = A[~np.eye(n, dtype=bool)]
+    if case == "coordinates":
+        assert np.abs(X).max() > 2.0 ** 24 and 0.01 < off.mean() < 0.5
+    elif case == "tiny_tau":
+        assert off.sum() >= 350 * 349                      # the copied block is complete
+    else:
+        assert off.all()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("case", ["coordinates", "tiny_tau", "huge_tau"])
+def test_compat_bit_exact_when_every_pair_takes_fp64(case):
+    from paper_2507_01439_gb300 import build
+    build.build()
+    X, Y, tau = _all_fp64_case(case)
+    n = X.shape[0]
+    with trg.TurboReg(max_n=n) as ctx:
+        ctx.register(X, Y, trg.default_params(tau, 100, 0.1))
+        bits = ctx.buffer(trg.BUF_ADJ_BITS)
+    A = oracle.compat(X, Y, tau)
+    G = np.unpackbits(bits.view(np.uint8), axis=1, bitorder="little")[:n, :n]
+    bad = np.argwhere(G != A)
+    assert bad.size == 0, f"{len(bad)} adjacency bits differ, first {bad[:5].tolist()}"
