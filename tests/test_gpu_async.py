@@ -55,6 +55,42 @@ def test_async_pinned_host_inputs_match_sync(ctx):
         _same(slots.result(k), ctx.register(p.x, p.y, prm))
 
 
+def test_reused_buffers_and_result_slots(ctx):
+    """The replayed graph keeps the input and result pointers of its last call
+    and patches them only when they change: the same buffers refilled, and
+    buffers and result slots alternating, give what a fresh context gives."""
+    import torch
+    probs = [synth.make_problem("indoor", 4000, 0.05, 320 + k) for k in range(3)]
+    prm = trg.default_params(probs[0].tau, 1500, probs[0].theta)
+    ref = []
+    for p in probs:
+        with trg.TurboReg(max_n=5000, max_batch=1) as fresh:
+            ref.append(fresh.register(p.x, p.y, prm))
+    bx = [torch.empty((4000, 3), dtype=torch.float32, device="cuda") for _ in range(2)]
+    by = [torch.empty((4000, 3), dtype=torch.float32, device="cuda") for _ in range(2)]
+    slots = trg.ResultSlots(2)
+    # one buffer pair and one result slot, refilled for every problem
+    for k, p in enumerate(probs):
+        bx[0].copy_(torch.from_numpy(p.x)); by[0].copy_(torch.from_numpy(p.y))
+        torch.cuda.synchronize()
+        ctx.register_async(bx[0], by[0], prm, slots, 0)
+        ctx.synchronize()
+        _same(slots.result(0), ref[k])
+        _same(ctx.register(bx[0], by[0], prm), ref[k])        # the synchronous call on the same buffers
+    # buffers and slots alternating: A, B, A
+    order = [0, 1, 2]
+    for k in order:
+        b = k % 2
+        bx[b].copy_(torch.from_numpy(probs[k].x)); by[b].copy_(torch.from_numpy(probs[k].y))
+        torch.cuda.synchronize()
+        ctx.register_async(bx[b], by[b], prm, slots, b)
+        ctx.synchronize()
+        _same(slots.result(b), ref[k])
+    # host inputs staged through the workspace (the same staging pointer every call)
+    for k, p in enumerate(probs):
+        _same(ctx.register(p.x, p.y, prm), ref[k])
+
+
 def test_async_rejections(ctx):
     import torch
     p = synth.make_problem("cube", 300, 0.2, 320)
