@@ -89,9 +89,12 @@ __device__ __forceinline__ void record_edge(uint16_t* tile, int* rsum, int* rmax
 
 // ---------------------------------------------------------------------------
 // Lane form (N_pad <= 5120).  Work units are quarters of the tiles: 128 rows
-// i by 64 columns j, an equal contiguous run of them per CTA of 16 warps (a
-// unit's time varies little with its number of edges; a split by edge count
-// was measured slower).  The CTA's 128 bitset rows i (one bulk copy, about
+// i by 64 columns j, an equal contiguous run of them per CTA of 16 warps.  A
+// unit costs a half about 2 us plus 12 ns per edge (2.6 us more where a row
+// block begins), so CTAs end unevenly; a contiguous split weighted by that
+// cost gains only ~2 us, because a unit is coarse against the halves'
+// alternation, which is less than the split itself costs at the start of
+// every CTA.  The CTA's 128 bitset rows i (one bulk copy, about
 // once per CTA) are in shared memory.  The CTA works as two halves of 8
 // warps that take alternate units, each with its own buffer of 64 rows j (one
 // bulk copy per unit) and its own edge list, synchronised by its own named
@@ -301,7 +304,7 @@ __global__ void __launch_bounds__(kLThreads, 1)
         srmax[tid] = 0;
     }
     if (tid < 2 * kLUC) scsum[tid] = 0;
-    // this CTA's units: a contiguous run (the time of a unit varies little with its edges)
+    // this CTA's units: an equal contiguous run
     const int units = 4 * total;
     const int u0 = static_cast<int>((static_cast<long long>(units) * blockIdx.x) / gridDim.x);
     const int u1 = static_cast<int>((static_cast<long long>(units) * (blockIdx.x + 1)) / gridDim.x);
