@@ -364,6 +364,8 @@ __global__ void __launch_bounds__(kLThreads, 1)
     };
     if (tid == 0) issue_rows(cur);
     uint32_t rows_uses = 0, cols_uses = 0;   // this half's uses of its rows-j buffer
+    uint32_t pref = 0u;                       // this thread's adjacency word of the half's next unit,
+    bool have_pref = false;                   // loaded during the current unit's edge loop
     // Every thread walks all units in order; half h takes the units k with
     // k % 2 == h.  The halves meet only where a new row block begins (both
     // have finished every earlier unit there), to exchange the rows i.
@@ -402,7 +404,7 @@ __global__ void __launch_bounds__(kLThreads, 1)
         {
             const int jl = ht >> 2, h = ht & 3;
             const int j = cur.j0 + jl;
-            const uint32_t w = __ldg(v.bits + static_cast<size_t>(j) * v.ldb + (cur.i0 >> 5) + h);
+            const uint32_t w = have_pref ? pref : __ldg(v.bits + static_cast<size_t>(j) * v.ldb + (cur.i0 >> 5) + h);
             const int lh = (j < v.n ? j - cur.i0 : 0) - 32 * h;   // rows 32 h + r, r < lh
             m = lh <= 0 ? 0u : lh < 32 ? w & ((1u << lh) - 1u) : w;
         }
@@ -427,6 +429,13 @@ __global__ void __launch_bounds__(kLThreads, 1)
             for (; m; m &= m - 1u) lst[base++] = static_cast<uint16_t>((jl << 7) | (32 * h + __ffs(m) - 1));
         }
         half_sync();   // the list and the zeros are complete
+        {   // the half's next unit (two ahead): its adjacency word, in flight during the edge loop
+            const LaneUnit n1 = lane_next(cur, v.n_pad);
+            const LaneUnit n2 = n1.p == cur.p ? lane_next(n1, v.n_pad) : n1;
+            have_pref = k + 2 < K && n2.p == cur.p;
+            if (have_pref)
+                pref = __ldg(v.bits + static_cast<size_t>(n2.j0 + (ht >> 2)) * v.ldb + (n2.i0 >> 5) + (ht & 3));
+        }
         ok &= mbar_wait(&cols_full[slot], cols_uses & 1u);
         ++cols_uses;
         {
