@@ -308,32 +308,6 @@ __global__ void __launch_bounds__(kLThreads, 1)
     const int units = 4 * total;
     const int u0 = static_cast<int>((static_cast<long long>(units) * blockIdx.x) / gridDim.x);
     const int u1 = static_cast<int>((static_cast<long long>(units) * (blockIdx.x + 1)) / gridDim.x);
-    pdl_wait();
-    pdl_release();
-    if (auto_clusters > 0) {
-        // the degree sum 2 |E| of the problem (added up by the compatibility blocks)
-        const ProbView& v0 = bt.views[0];
-        const unsigned long long deg_sum = __ldcg(&v0.ctl->deg_sum);
-        const bool bitset = sc2_bitset_faster(v0.n_pad, deg_sum, auto_clusters);
-        if (blockIdx.x == 0 && tid == 0) v0.ctl->sc2_path = bitset ? 1u : 2u;
-        if (!bitset) {
-            // the GEMM's FP8 operand from the bitset: word q of the matrix -> 32 bytes
-            const size_t words = static_cast<size_t>(v0.n_pad) * v0.ldb;
-            for (size_t q = static_cast<size_t>(blockIdx.x) * kLThreads + tid; q < words;
-                 q += static_cast<size_t>(gridDim.x) * kLThreads) {
-                const uint32_t w = __ldcg(v0.bits + q);
-                const size_t row = q / static_cast<size_t>(v0.ldb), col = (q % static_cast<size_t>(v0.ldb)) * 32;
-                uint4* dst = reinterpret_cast<uint4*>(v0.a8_auto + row * v0.n_pad + col);
-                dst[0] = half_word_fp8(w & 0xFFFFu);
-                dst[1] = half_word_fp8(w >> 16);
-            }
-            return;
-        }
-    }
-    if (u0 >= u1) return;
-    LaneUnit cur = lane_unit(bt, u0), prev = cur;
-    if (tid == 0) lane_view_load(lv[cur.p & 3], bt.views[cur.p]);
-    __syncthreads();
     const int K = u1 - u0;
     bool ok = true;
 
@@ -362,7 +336,53 @@ __global__ void __launch_bounds__(kLThreads, 1)
         }
         if (hist && hist_bins > 0) lane_flush_hist(pv, shist, tid);
     };
-    if (tid == 0) issue_rows(cur);
+    // The first unit and its problem's fields come from the launch's
+    // descriptors only, so they are read before the dependency wait; the
+    // first row block and each half's first unit are then copied at once
+    // after it (the degree-sum read of the path choice overlaps the copies).
+    LaneUnit cur = {0, 0, 0};
+    if (K > 0) {
+        cur = lane_unit(bt, u0);
+        if (tid == 0) lane_view_load(lv[cur.p & 3], bt.views[cur.p]);
+    }
+    __syncthreads();   // barriers initialised, the first problem's fields in place
+    LaneUnit prev = cur;
+    // this half's first unit (unit `half` of the run) when it is copied early
+    const LaneUnit first1 = K > 1 ? lane_next(cur, lv[cur.p & 3].n_pad) : cur;
+    const bool early_cols = K > half && (half == 0 || first1.p == cur.p);
+    pdl_wait();
+    pdl_release();
+    if (K > 0) {
+        if (tid == 0) issue_rows(cur);
+        if (ht == 0 && early_cols) issue_cols(half == 0 ? cur : first1, half);
+    }
+    if (auto_clusters > 0) {
+        // the degree sum 2 |E| of the problem (added up by the compatibility blocks)
+        const ProbView& v0 = bt.views[0];
+        const unsigned long long deg_sum = __ldcg(&v0.ctl->deg_sum);
+        const bool bitset = sc2_bitset_faster(v0.n_pad, deg_sum, auto_clusters);
+        if (blockIdx.x == 0 && tid == 0) v0.ctl->sc2_path = bitset ? 1u : 2u;
+        if (!bitset) {
+            // no copy may still be landing in shared memory when the CTA leaves
+            if (K > 0) {
+                bool landed = mbar_wait(rows_full, 0u);
+                if (early_cols) landed &= mbar_wait(&cols_full[half], 0u);
+                if (!landed) atomicOr(&v0.ctl->err, TR_ERR_TIMEOUT);
+            }
+            // the GEMM's FP8 operand from the bitset: word q of the matrix -> 32 bytes
+            const size_t words = static_cast<size_t>(v0.n_pad) * v0.ldb;
+            for (size_t q = static_cast<size_t>(blockIdx.x) * kLThreads + tid; q < words;
+                 q += static_cast<size_t>(gridDim.x) * kLThreads) {
+                const uint32_t w = __ldcg(v0.bits + q);
+                const size_t row = q / static_cast<size_t>(v0.ldb), col = (q % static_cast<size_t>(v0.ldb)) * 32;
+                uint4* dst = reinterpret_cast<uint4*>(v0.a8_auto + row * v0.n_pad + col);
+                dst[0] = half_word_fp8(w & 0xFFFFu);
+                dst[1] = half_word_fp8(w >> 16);
+            }
+            return;
+        }
+    }
+    if (K <= 0) return;
     uint32_t rows_uses = 0, cols_uses = 0;   // this half's uses of its rows-j buffer
     uint32_t pref = 0u;                       // this thread's adjacency word of the half's next unit,
     bool have_pref = false;                   // loaded during the current unit's edge loop
@@ -391,7 +411,7 @@ __global__ void __launch_bounds__(kLThreads, 1)
         // ---------------- unit k, by this half ----------------
         const LaneView& v = lv[cur.p & 3];
         const int slot = half;
-        if (ht == 0) {
+        if (ht == 0 && !(k == half && early_cols)) {
             fence_proxy_async();   // the buffer's previous rows were read by this half's threads
             issue_cols(cur, slot);
         }
