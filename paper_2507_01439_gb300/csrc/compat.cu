@@ -184,6 +184,10 @@ __device__ __forceinline__ uint4 bits16_to_fp8(uint32_t b16)
 template <bool kAuto>
 __global__ void __launch_bounds__(kThreads, 8) compat_kernel(ManyViews vs)
 {
+    // the block's problem from the launch's descriptors (static for the launch):
+    // read while the predecessor still runs
+    int t;
+    const ProbView v = vs.get(ST_COMPAT, blockIdx.x, t);
     pdl_wait();
     pdl_release();
     __shared__ __align__(128) float4 srow[kT][2];        // row points as copied (x0,x1,x2,y0 | y1,y2,w,0)
@@ -194,8 +198,6 @@ __global__ void __launch_bounds__(kThreads, 8) compat_kernel(ManyViews vs)
     __shared__ int s_wide;
 
     // triangular tile index -> (I, J), I <= J
-    int t;
-    const ProbView v = vs.get(ST_COMPAT, blockIdx.x, t);
     int J = static_cast<int>((sqrtf(8.0f * t + 1.0f) - 1.0f) * 0.5f);
     while (J * (J + 1) / 2 > t) --J;
     while ((J + 1) * (J + 2) / 2 <= t) ++J;

@@ -19,10 +19,10 @@ namespace {
 // registration path solves cliques inside the clique search).
 __global__ void __launch_bounds__(128) kabsch_kernel(ManyViews vs)
 {
+    int lb;
+    const ProbView v = vs.get(ST_KABSCH, blockIdx.x, lb);   // launch descriptors: before the wait
     pdl_wait();
     pdl_release();
-    int lb;
-    const ProbView v = vs.get(ST_KABSCH, blockIdx.x, lb);
     const int h = lb * blockDim.x + threadIdx.x;
     const int nh = v.ctl->n_pivots * v.k2;
     if (h >= nh) return;
@@ -243,10 +243,10 @@ __device__ __forceinline__ int key_hypothesis(const ProbView& v, unsigned long l
 // completion counter of ~1300 blocks on one address serialises in L2.)
 __global__ void __launch_bounds__(1024) finalize_kernel(ManyViews vs, turboreg_result* out)
 {
+    int lb;
+    const ProbView v = vs.get(ST_FINAL, blockIdx.x, lb);   // launch descriptors: before the wait
     pdl_wait();
     pdl_release();
-    int lb;
-    const ProbView v = vs.get(ST_FINAL, blockIdx.x, lb);
     __shared__ unsigned long long sbest[32];
     __shared__ int scnt[32], sfp[32];
     __shared__ float srec[16];

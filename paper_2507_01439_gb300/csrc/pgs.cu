@@ -53,11 +53,11 @@ __global__ void __launch_bounds__(256, kDense ? 3 : 2) pgs_kernel(ManyViews vs)
     extern __shared__ __align__(16) uint8_t pgs_smem[];
     int (*scand)[kCand] = reinterpret_cast<int (*)[kCand]>(pgs_smem);
     uint64_t* skey = reinterpret_cast<uint64_t*>(pgs_smem + kListBytes);
+    int lb;
+    const ProbView v = vs.get(ST_PGS, blockIdx.x, lb);   // launch descriptors: before the wait
     pdl_wait();
     pdl_release();   // the balanced verification tile caps itself at four blocks per SM, so
                      // blocks placed beside these still end up evenly spread
-    int lb;
-    const ProbView v = vs.get(ST_PGS, blockIdx.x, lb);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     // the selected edges (Eq. 4) in the order the selection wrote them; a
     // pivot's index is its rank: the number of larger keys (W << 32 | ~(i n + j)

@@ -394,8 +394,9 @@ template <bool kHist>
 __global__ void __launch_bounds__(kThreads, 1) sc2_pair_mma_kernel(Batch bt, int total, int hist_bins, int auto_mode)
 {
     if (auto_mode) {
+        const Ctl* ctl = bt.views[0].ctl;   // the descriptor before the wait, the flag after it
         pdl_wait();
-        if (__ldcg(&bt.views[0].ctl->sc2_path) != 2u) {
+        if (__ldcg(&ctl->sc2_path) != 2u) {
             pdl_release();
             return;
         }

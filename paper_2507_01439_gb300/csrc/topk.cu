@@ -89,11 +89,11 @@ __device__ __forceinline__ void for_row_chunks(const ProbView& v, int i, int lan
 template <class VS, bool kSmem>
 __global__ void __launch_bounds__(256) hist_kernel(VS vs)
 {
+    int lb;
+    const ProbView v = vs.get(ST_HIST, blockIdx.x, lb);   // launch descriptors: before the wait
     pdl_wait();
     pdl_release();
     extern __shared__ uint32_t sh[];
-    int lb;
-    const ProbView v = vs.get(ST_HIST, blockIdx.x, lb);
     const int nb = v.n + 1;
     if (kSmem) {
         for (int q = threadIdx.x; q < nb; q += blockDim.x) sh[q] = 0;
@@ -124,11 +124,11 @@ __global__ void __launch_bounds__(256) hist_kernel(VS vs)
 template <class VS>
 __global__ void __launch_bounds__(1024) select_kernel(VS vs)
 {
+    int lb;
+    const ProbView v = vs.get(ST_SELECT, blockIdx.x, lb);   // launch descriptors: before the wait
     pdl_wait();
     pdl_release();
     __shared__ int sbuf[33];
-    int lb;
-    const ProbView v = vs.get(ST_SELECT, blockIdx.x, lb);
     if (VS::kCallerWeights && (v.ctl->err & TR_ERR_BAD_WEIGHT) != 0u) {
         // out-of-range weights: select nothing, so that the count, emit and
         // rank passes write no candidate (rank reports the error)
@@ -184,13 +184,13 @@ __device__ __forceinline__ void count_chunk(uint4 q, uint32_t a2, int& g, int& e
 template <class VS>
 __global__ void __launch_bounds__(kCountThreads, 3) count_kernel(VS vs, int select_here)
 {
+    int lb;
+    const ProbView v = vs.get(ST_COUNT, blockIdx.x, lb);   // launch descriptors: before the wait
     pdl_wait();
     pdl_release();
     extern __shared__ __align__(16) uint32_t shist_stage[];   // select_here: n + 4 words
     __shared__ int srow[16], sc0[16], soff[17], sg[16], se[16];
     __shared__ int ssel[40];
-    int lb;
-    const ProbView v = vs.get(ST_COUNT, blockIdx.x, lb);
     const int n = v.n;
     const int t = threadIdx.x;
     // entry k = t (< 16): pair p = 8 lb + k / 2, side k % 2
@@ -305,12 +305,12 @@ __global__ void __launch_bounds__(kCountThreads, 3) count_kernel(VS vs, int sele
 template <class VS>
 __global__ void __launch_bounds__(256) emit_kernel(VS vs)
 {
+    int lb;
+    const ProbView v = vs.get(ST_EMIT, blockIdx.x, lb);   // launch descriptors: before the wait
     pdl_wait();
     pdl_release();
     __shared__ int sg[8], se[8];
     __shared__ int s_base;
-    int lb;
-    const ProbView v = vs.get(ST_EMIT, blockIdx.x, lb);
     // the counters through L1: every warp of every block reads them
     const int n_sel = v.ctl->n_sel;
     const int nact = static_cast<int>(v.ctl->n_active);
@@ -420,12 +420,12 @@ __global__ void __launch_bounds__(256) emit_kernel(VS vs)
 template <class VS>
 __global__ void __launch_bounds__(256) rank_kernel(VS vs)
 {
+    int lb;
+    const ProbView v = vs.get(ST_RANK, blockIdx.x, lb);   // launch descriptors: before the wait
     pdl_wait();
     pdl_release();
     extern __shared__ uint64_t sk[];
     __shared__ int part[8][32];
-    int lb;
-    const ProbView v = vs.get(ST_RANK, blockIdx.x, lb);
     const int n_sel = v.ctl->n_sel;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (lb == 0 && threadIdx.x == 0)
