@@ -62,7 +62,7 @@ LAUNCHES_PER_STEP = 9
 # profiles/sc2_bitset_indoor5000.txt); None when the kernel has changed since, until
 # it has been captured again
 SC2_DRAM_BYTES = 28775424
-SC2_BITSET_DRAM_BYTES = 3352576
+SC2_BITSET_DRAM_BYTES = 3346176
 # the population count's rate: 16 per clock per SM on 152 SMs at the 2.07 GHz maximum clock
 POPC_PEAK_TWORDS = 16 * 152 * 2.07e9 / 1e12
 
